@@ -1,0 +1,194 @@
+/*
+ * cox.h -- C ABI of the GB300 (sm_103a) library for regularized stratified and
+ * time-varying Cox proportional-hazards fits by cyclic coordinate descent.
+ *
+ * Method: Yang, Schuemie & Suchard, "Massive parallelization of the stratified and
+ * time-varying Cox models" (arXiv 2310.16238).
+ *   - model: stratified partial likelihood, §2.1 eq. (strat_l); time-varying covariates as
+ *     counting-process rows, §2.2 eq. (time_cov_l); time-varying coefficients reduce to
+ *     time-varying covariates, §2.3;
+ *   - optimizer: cyclic coordinate descent with the 1-D Newton step eq. (newton), the
+ *     trust region and the L1 directional-derivative rule, §2.4;
+ *   - per-coordinate gradient/Hessian eqs. (strat_g), (strat_h) as stratum-segmented
+ *     reverse scans of exp(X beta) and X_j exp(X beta), §2.6-§2.7 eqs. (parallel_g)-(parallel_xb).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: COX_OK (0), a warning (> 0) or an error (< 0).
+ *     No exception or longjmp crosses the ABI. cox_last_error() gives the message of the
+ *     last failing call on a handle (or, with NULL, of the last failing call on this thread).
+ *   - Pointers to arrays may be host or device memory; the library detects which with
+ *     cudaPointerGetAttributes. Output arrays are written in their own memory space.
+ *   - cox_create copies everything it needs; the caller may free its inputs afterwards.
+ *     The handle owns its device memory until cox_destroy.
+ *   - All device work runs on the stream given in cox_options.stream (NULL: the legacy
+ *     default stream). Calls return after their work on that stream has completed.
+ *   - One handle must not be used from two threads at once. Distinct handles are independent.
+ */
+#ifndef COX_H
+#define COX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define COX_OK 0
+#define COX_W_NOT_CONVERGED 1   /* max_sweeps reached before the tolerance */
+#define COX_E_INVALID (-1)      /* bad argument or malformed data */
+#define COX_E_UNSORTED (-2)     /* rows not sorted by (stratum, stop) */
+#define COX_E_OOM (-3)          /* device allocation failed */
+#define COX_E_CUDA (-4)         /* a CUDA runtime call failed */
+#define COX_E_TIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define COX_E_ADMISSION (-6)    /* serving: request can never fit the memory budget */
+#define COX_E_RANGE (-7)        /* FP32 path: |eta - shift| left the exp range of float */
+#define COX_E_NOT_FOUND (-8)    /* serving: unknown request id */
+#define COX_E_BUSY (-9)         /* serving: result not ready yet (poll again) */
+
+enum { COX_PEN_NONE = 0, COX_PEN_L1 = 1, COX_PEN_L2 = 2 };
+enum {
+  COX_FP64 = 0,   /* FP64 exp, scans, ratios, step and log-likelihood */
+  COX_FP32C = 1   /* FP32 exp and compensated (two-sum) FP32 tile scans; FP64 tile carries,
+                     gradient/Hessian accumulation, Newton step and log-likelihood */
+};
+
+/* ---------------------------------------------------------------- data
+ * Rows are observations (right-censored) or counting-process intervals (start, stop].
+ * They MUST be sorted by (stratum ascending, stop ascending); ties in any order.
+ *   stop     int32[n_rows]  event or censoring time, integer days (paper §2.2: discrete time)
+ *   start    int32[n_rows]  NULL for right-censored data; otherwise the interval start,
+ *                           start < stop. A row is at risk at time t iff start < t <= stop.
+ *   event    uint8[n_rows]  1 if the row ends with an event at `stop`, else 0
+ *   stratum  int32[n_rows]  NULL: one stratum. Strata ids only need to be sorted.
+ *   col_ptr  int64[p+1]     CSC column pointers into row_idx / val, col_ptr[0] = 0
+ *   row_idx  int32[nnz]     row of each nonzero, strictly ascending within a column
+ *   val      double[nnz]    NULL: binary X (every stored entry is 1)
+ * Limits: n_rows < 2^30 (counting-process data use two sequence positions per row). */
+typedef struct {
+  int64_t n_rows;
+  int32_t p;
+  int32_t reserved;
+  const int32_t *stop;
+  const int32_t *start;
+  const uint8_t *event;
+  const int32_t *stratum;
+  const int64_t *col_ptr;
+  const int32_t *row_idx;
+  const double *val;
+} cox_data;
+
+/* ---------------------------------------------------------------- options
+ *   penalty    COX_PEN_NONE | COX_PEN_L1 (gamma * sum |beta_j|, §2.1) | COX_PEN_L2
+ *              (sum beta_j^2 / (2 l2_var), Gaussian prior)
+ *   lambda     L1 weight gamma
+ *   l2_var     L2 prior variance
+ *   penalize   uint8[p] (host or device), NULL: every coordinate penalized. 0 exempts a
+ *              coordinate (e.g. a treatment covariate, §3.2)
+ *   tol        convergence: |obj_s - obj_{s-1}| <= tol * |obj_s| after sweep s, on the
+ *              penalized objective obj = -loglik + penalty
+ *   max_sweeps sweep limit (COX_W_NOT_CONVERGED when reached)
+ *   precision  COX_FP64 | COX_FP32C
+ *   stream     cudaStream_t (NULL = default stream)
+ *   tile       positions per tile, 0 = library default; a multiple of 1024 otherwise */
+typedef struct {
+  int32_t penalty;
+  int32_t precision;
+  double lambda;
+  double l2_var;
+  const uint8_t *penalize;
+  double tol;
+  int32_t max_sweeps;
+  int32_t tile;
+  void *stream;
+} cox_options;
+
+typedef struct {
+  int32_t sweeps;          /* full sweeps over the p coordinates */
+  int32_t converged;       /* 1 when the tolerance was met */
+  int64_t coord_updates;   /* coordinate evaluations (sweeps * p) */
+  double loglik;           /* unpenalized log partial likelihood at beta_out */
+  double objective;        /* -loglik + penalty at beta_out */
+  int32_t status;          /* same as the return code */
+  int32_t reserved;
+  int64_t step_launches;   /* coordinate-step kernel launches issued by the sweep loop */
+  double sweep_ms;         /* CUDA-event time of the sweep loop on the fit's stream */
+} cox_fit_info;
+
+typedef struct cox_handle cox_handle;
+
+/* Device memory allocator used for every buffer the library owns (NULL: cudaMalloc /
+ * cudaFree). `alloc` returns a device pointer (or NULL on failure) and must be callable
+ * from any thread. Set it before creating handles; it applies process-wide. */
+typedef void *(*cox_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*cox_free_fn)(void *ptr, size_t bytes, void *ctx);
+int cox_set_allocator(cox_alloc_fn alloc, cox_free_fn release, void *ctx);
+
+/* Validate and prepare `data` on the device (sort check, strata, tie groups, delta'X,
+ * tile plan; §2.7) and allocate the per-fit state. On success *out owns everything.
+ * Errors: COX_E_INVALID, COX_E_UNSORTED, COX_E_OOM, COX_E_CUDA. */
+int cox_create(const cox_data *data, const cox_options *opts, cox_handle **out);
+
+/* Replace the options of an existing handle (penalty, tolerances, precision, stream).
+ * Keeps the prepared data; the next cox_fit starts from its beta0. */
+int cox_set_options(cox_handle *h, const cox_options *opts);
+
+/* Cyclic coordinate descent (§2.4) from beta0 (p doubles, NULL = zeros) until the
+ * tolerance or max_sweeps; writes beta_out (p doubles) and *info (may be NULL).
+ * Returns COX_OK, COX_W_NOT_CONVERGED or an error. */
+int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *info);
+
+/* Unpenalized log partial likelihood (eq. strat_l / time_cov_l) at beta (p doubles). */
+int cox_loglik(cox_handle *h, const double *beta, double *loglik_out);
+
+/* Unpenalized gradient and Hessian diagonal of -loglik at beta (eqs. strat_g, strat_h):
+ * grad[p] and, unless NULL, hess_diag[p]. */
+int cox_gradient(cox_handle *h, const double *beta, double *grad, double *hess_diag);
+
+/* Risk-set sums at every tie group g (sorted by stratum, then time) for column j at beta:
+ * S0[g] = sum_{r in R(t_g)} exp(x_r'beta), S1[g] = sum x_rj exp(x_r'beta) (j < 0: S1 = 0).
+ * *n_groups receives G; S0 / S1 may be NULL to query G. Diagnostic entry point. */
+int cox_risk_sums(cox_handle *h, const double *beta, int32_t j, double *S0, double *S1, int64_t *n_groups);
+
+/* Integer metadata built by cox_create (for verification): every output may be NULL.
+ *   n_groups, n_strata   G and K
+ *   group_stratum[G], group_time[G], group_events[G], group_at_risk[G] (rows at risk)
+ *   strata_start[K+1]   first row of each stratum, strata_start[K] = n_rows */
+int cox_metadata(cox_handle *h, int64_t *n_groups, int64_t *n_strata, int32_t *group_stratum,
+                 int32_t *group_time, int32_t *group_events, int64_t *group_at_risk, int64_t *strata_start);
+
+/* delta'X_j for every column (p doubles): the first term of eq. (parallel_g). */
+int cox_dx(cox_handle *h, double *dx);
+
+/* Release everything the handle owns. NULL is ignored. */
+void cox_destroy(cox_handle *h);
+
+/* Message of the last error on `h` (NULL: the calling thread's last error). Never NULL. */
+const char *cox_last_error(const cox_handle *h);
+
+/* ---------------------------------------------------------------- batching
+ * Run the fits of n handles together: one persistent launch per coordinate step advances
+ * every unfinished fit by one coordinate (each fit on its own coordinate and sweep),
+ * replayed from a captured CUDA graph. The handles must share one precision; their
+ * options' streams are ignored in favour of the first handle's. beta0[i] may be NULL
+ * (or beta0 itself NULL); beta_out[i] receives p_i doubles; info[i] may be NULL.
+ * Returns the worst status over the fits. */
+int cox_batch_fit(cox_handle *const *h, int32_t n, const double *const *beta0, double *const *beta_out,
+                  cox_fit_info *info);
+
+/* New handle on the same prepared data as `src` (shared, reference counted) with its own
+ * fit state and options: many fits of one data set (penalty grids) without re-preparing. */
+int cox_clone(const cox_handle *src, const cox_options *opts, cox_handle **out);
+
+/* Bytes of device memory a handle for `data` would hold (for admission control). */
+int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
+
+/* Number of CUDA kernels this library has launched in this process (graph replays count
+ * every kernel node). For measurement; never decreases. */
+int64_t cox_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COX_H */

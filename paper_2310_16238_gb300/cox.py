@@ -1,0 +1,363 @@
+"""ctypes binding of ``libcoxgb.so`` (C ABI in ``include/cox.h``).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels. Arrays
+may be NumPy (host) or torch CUDA tensors (device); the library detects which. When torch
+has CUDA, device memory is routed through torch's caching allocator. If the library is
+missing or fails to load, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcoxgb.so")
+
+COX_OK, COX_W_NOT_CONVERGED = 0, 1
+COX_E_INVALID, COX_E_UNSORTED, COX_E_OOM, COX_E_CUDA = -1, -2, -3, -4
+COX_E_TIMEOUT, COX_E_ADMISSION, COX_E_RANGE, COX_E_NOT_FOUND, COX_E_BUSY = -5, -6, -7, -8, -9
+COX_PEN_NONE, COX_PEN_L1, COX_PEN_L2 = 0, 1, 2
+COX_FP64, COX_FP32C = 0, 1
+
+EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
+           "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
+           "cox_clone", "cox_footprint", "cox_launch_count"]
+
+
+class CoxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class cox_data(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("p", C.c_int32), ("reserved", C.c_int32), ("stop", C.c_void_p),
+                ("start", C.c_void_p), ("event", C.c_void_p), ("stratum", C.c_void_p), ("col_ptr", C.c_void_p),
+                ("row_idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class cox_options(C.Structure):
+    _fields_ = [("penalty", C.c_int32), ("precision", C.c_int32), ("lam", C.c_double), ("l2_var", C.c_double),
+                ("penalize", C.c_void_p), ("tol", C.c_double), ("max_sweeps", C.c_int32), ("tile", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class cox_fit_info(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("coord_updates", C.c_int64),
+                ("loglik", C.c_double), ("objective", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("step_launches", C.c_int64), ("sweep_ms", C.c_double)]
+
+    def as_dict(self):
+        return dict(sweeps=self.sweeps, converged=bool(self.converged), coord_updates=self.coord_updates,
+                    loglik=self.loglik, objective=self.objective, status=self.status,
+                    step_launches=self.step_launches, sweep_ms=self.sweep_ms)
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+_lock = threading.Lock()
+_lib = None
+_cb_keep = []
+
+
+def lib():
+    """Load the library (raises if it has not been built or cannot be loaded)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            L.cox_set_allocator.argtypes = [_ALLOC, _FREE, vp]
+            L.cox_create.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(vp)]
+            L.cox_set_options.argtypes = [vp, C.POINTER(cox_options)]
+            L.cox_fit.argtypes = [vp, vp, vp, C.POINTER(cox_fit_info)]
+            L.cox_loglik.argtypes = [vp, vp, vp]
+            L.cox_gradient.argtypes = [vp, vp, vp, vp]
+            L.cox_risk_sums.argtypes = [vp, vp, i32, vp, vp, vp]
+            L.cox_metadata.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            L.cox_dx.argtypes = [vp, vp]
+            L.cox_destroy.argtypes = [vp]
+            L.cox_destroy.restype = None
+            L.cox_last_error.argtypes = [vp]
+            L.cox_last_error.restype = C.c_char_p
+            L.cox_batch_fit.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(cox_fit_info)]
+            L.cox_clone.argtypes = [vp, C.POINTER(cox_options), C.POINTER(vp)]
+            L.cox_footprint.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_size_t)]
+            L.cox_launch_count.argtypes = []
+            L.cox_launch_count.restype = i64
+            _lib = L
+            _install_torch_allocator(L)
+    return _lib
+
+
+def _install_torch_allocator(L):
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return
+    except Exception:
+        return
+
+    def alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC(alloc), _FREE(free)
+    _cb_keep.extend([a, f])
+    L.cox_set_allocator(a, f, None)
+
+
+def _check(rc, handle=None, allow_warn=True):
+    if rc < 0 or (rc > 0 and not allow_warn):
+        msg = lib().cox_last_error(handle).decode()
+        raise CoxError(rc, msg)
+    return rc
+
+
+def _ptr(a):
+    """Pointer of a NumPy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def make_data(data):
+    """cox_data for a ``synth.CoxData`` or any object with the same fields (NumPy or torch)."""
+    def conv(x, dt):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):
+            return x.contiguous()
+        return _host(x, dt)
+    keep = dict(stop=conv(data.stop, np.int32), start=conv(data.start, np.int32), event=conv(data.event, np.uint8),
+                stratum=conv(data.stratum, np.int32), col_ptr=conv(data.col_ptr, np.int64),
+                row_idx=conv(data.row_idx, np.int32), val=conv(data.val, np.float64))
+    n = int(keep["stop"].shape[0])
+    d = cox_data(n, int(data.p), 0, _ptr(keep["stop"]), _ptr(keep["start"]), _ptr(keep["event"]),
+                 _ptr(keep["stratum"]), _ptr(keep["col_ptr"]), _ptr(keep["row_idx"]), _ptr(keep["val"]))
+    return d, keep
+
+
+def make_options(opts=None, precision=COX_FP64, stream=None, tile=0):
+    """cox_options from a ``synth.CoxOptions``-like object."""
+    pen = None
+    if opts is not None and getattr(opts, "penalize", None) is not None:
+        pen = _host(opts.penalize, np.uint8)
+    o = cox_options(int(getattr(opts, "penalty", COX_PEN_NONE)), int(precision), float(getattr(opts, "lam", 0.0)),
+                    float(getattr(opts, "l2_var", 1.0)), _ptr(pen), float(getattr(opts, "tol", 1e-8)),
+                    int(getattr(opts, "max_sweeps", 1000)), int(tile), stream)
+    return o, pen
+
+
+# ---------------------------------------------------------------- ABI-named wrappers
+def cox_create(data, opts=None, precision=COX_FP64, stream=None, tile=0):
+    d, keep = make_data(data)
+    o, pen = make_options(opts, precision, stream, tile)
+    h = C.c_void_p()
+    _check(lib().cox_create(C.byref(d), C.byref(o), C.byref(h)))
+    _P_CACHE[h.value] = int(data.p)
+    return h
+
+
+def cox_fit(h, beta0=None, out=None):
+    p = _num_cols(h)
+    beta = np.zeros(p) if out is None else out
+    b0 = None if beta0 is None else (beta0 if hasattr(beta0, "data_ptr") else _host(beta0, np.float64))
+    info = cox_fit_info()
+    rc = _check(lib().cox_fit(h, _ptr(b0), _ptr(beta), C.byref(info)), h)
+    return beta, dict(info.as_dict(), rc=rc)
+
+
+def cox_loglik(h, beta):
+    b = beta if hasattr(beta, "data_ptr") else _host(beta, np.float64)
+    out = np.zeros(1)
+    _check(lib().cox_loglik(h, _ptr(b), _ptr(out)), h)
+    return float(out[0])
+
+
+def cox_gradient(h, beta, hessian=True):
+    p = _num_cols(h)
+    b = beta if hasattr(beta, "data_ptr") else _host(beta, np.float64)
+    g = np.zeros(max(p, 1))
+    hd = np.zeros(max(p, 1)) if hessian else None
+    _check(lib().cox_gradient(h, _ptr(b), _ptr(g), _ptr(hd)), h)
+    return (g[:p], hd[:p]) if hessian else g[:p]
+
+
+def cox_risk_sums(h, beta, j):
+    G = C.c_int64()
+    _check(lib().cox_risk_sums(h, None, int(j), None, None, C.byref(G)), h)
+    n = G.value
+    s0, s1 = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    b = None if beta is None else (beta if hasattr(beta, "data_ptr") else _host(beta, np.float64))
+    _check(lib().cox_risk_sums(h, _ptr(b), int(j), _ptr(s0), _ptr(s1), None), h)
+    return s0[:n], s1[:n]
+
+
+def cox_metadata(h):
+    G, K = C.c_int64(), C.c_int64()
+    _check(lib().cox_metadata(h, C.byref(G), C.byref(K), None, None, None, None, None), h)
+    g, k = G.value, K.value
+    gs, gt, ge = (np.zeros(max(g, 1), np.int32) for _ in range(3))
+    ga = np.zeros(max(g, 1), np.int64)
+    ss = np.zeros(k + 1, np.int64)
+    _check(lib().cox_metadata(h, None, None, _ptr(gs), _ptr(gt), _ptr(ge), _ptr(ga), _ptr(ss)), h)
+    return dict(group_stratum=gs[:g], group_time=gt[:g], group_events=ge[:g], group_at_risk=ga[:g], strata_start=ss)
+
+
+def cox_dx(h):
+    p = _num_cols(h)
+    out = np.zeros(max(p, 1))
+    _check(lib().cox_dx(h, _ptr(out)), h)
+    return out[:p]
+
+
+def cox_set_options(h, opts=None, precision=COX_FP64, stream=None, tile=0):
+    o, pen = make_options(opts, precision, stream, tile)
+    _check(lib().cox_set_options(h, C.byref(o)), h)
+
+
+def cox_clone(h, opts=None, precision=COX_FP64, stream=None):
+    o, pen = make_options(opts, precision, stream)
+    out = C.c_void_p()
+    _check(lib().cox_clone(h, C.byref(o), C.byref(out)))
+    _P_CACHE[out.value] = _P_CACHE.get(h.value if isinstance(h, C.c_void_p) else h)
+    return out
+
+
+def cox_destroy(h):
+    if h:
+        _P_CACHE.pop(h.value if isinstance(h, C.c_void_p) else h, None)
+        lib().cox_destroy(h)
+
+
+def cox_batch_fit(handles: Sequence, beta0: Optional[Sequence] = None):
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    outs = [np.zeros(max(_num_cols(h), 1)) for h in handles]
+    b0s = None
+    keep = []
+    if beta0 is not None:
+        arr = []
+        for b in beta0:
+            if b is None:
+                arr.append(None)
+            else:
+                bb = b if hasattr(b, "data_ptr") else _host(b, np.float64)
+                keep.append(bb)
+                arr.append(_ptr(bb))
+        b0s = (C.c_void_p * n)(*arr)
+    outp = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    infos = (cox_fit_info * n)()
+    rc = lib().cox_batch_fit(hs, n, b0s, outp, infos)
+    _check(rc)
+    return [o[:_num_cols(h)] for o, h in zip(outs, handles)], [i.as_dict() for i in infos]
+
+
+def cox_footprint(data, opts=None, precision=COX_FP64):
+    d, keep = make_data(data)
+    o, pen = make_options(opts, precision)
+    out = C.c_size_t()
+    _check(lib().cox_footprint(C.byref(d), C.byref(o), C.byref(out)))
+    return int(out.value)
+
+
+_P_CACHE = {}
+
+
+def cox_launch_count() -> int:
+    return int(lib().cox_launch_count())
+
+
+def _num_cols(h):
+    key = h.value if isinstance(h, C.c_void_p) else h
+    p = _P_CACHE.get(key)
+    if p is None:
+        raise RuntimeError("unknown handle: create it through cox_create / Handle")
+    return p
+
+
+class Handle:
+    """Owning wrapper: ``Handle(data, opts, precision=COX_FP64)`` then ``fit()``, ``loglik(beta)``..."""
+
+    def __init__(self, data, opts=None, precision=COX_FP64, stream=None, tile=0, _raw=None):
+        if _raw is None:
+            d, self._keep = make_data(data)
+            o, self._pen = make_options(opts, precision, stream, tile)
+            h = C.c_void_p()
+            _check(lib().cox_create(C.byref(d), C.byref(o), C.byref(h)))
+            self.h = h
+            self.p = int(data.p)
+        else:
+            self.h, self.p = _raw
+        _P_CACHE[self.h.value] = self.p
+        self.precision = precision
+
+    def fit(self, beta0=None):
+        return cox_fit(self.h, beta0)
+
+    def loglik(self, beta):
+        return cox_loglik(self.h, beta)
+
+    def gradient(self, beta, hessian=True):
+        return cox_gradient(self.h, beta, hessian)
+
+    def risk_sums(self, beta, j):
+        return cox_risk_sums(self.h, beta, j)
+
+    def metadata(self):
+        return cox_metadata(self.h)
+
+    def dx(self):
+        return cox_dx(self.h)
+
+    def set_options(self, opts, stream=None, tile=0):
+        cox_set_options(self.h, opts, self.precision, stream, tile)
+
+    def clone(self, opts=None):
+        o, pen = make_options(opts, self.precision)
+        out = C.c_void_p()
+        _check(lib().cox_clone(self.h, C.byref(o), C.byref(out)))
+        c = Handle(None, _raw=(out, self.p), precision=self.precision)
+        c._pen = pen
+        return c
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _P_CACHE.pop(self.h.value, None)
+            lib().cox_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def batch_fit(handles: Sequence[Handle], beta0=None):
+    return cox_batch_fit([h.h for h in handles], beta0)

@@ -1,0 +1,694 @@
+// C ABI of the Cox CCD library: handles, fit state, the CUDA-graph sweep loop, evaluations
+// and batched fits. The arithmetic lives in ccd.cu (coordinate steps) and prep.cu (data
+// preparation); this file only orchestrates launches and copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cox.h"
+#include "cox_internal.h"
+#include "prep.h"
+
+using namespace coxgb;
+
+namespace {
+
+thread_local std::string t_last_error = "no error";
+
+struct SharedData {
+  Prepared prep;
+  DevData *d_desc = nullptr;   // device copy of prep.desc
+  int precision = COX_FP64;
+  std::atomic<int> refs{1};
+};
+
+void release_shared(SharedData *s) {
+  if (s && s->refs.fetch_sub(1) == 1) {
+    if (s->d_desc) dev_free(s->d_desc, sizeof(DevData));
+    delete s;
+  }
+}
+
+}  // namespace
+
+struct cox_handle {
+  SharedData *sd = nullptr;
+  cox_options opts{};
+  BufferSet bufs;
+  DevFit hfit{};
+  DevFit *dfit = nullptr;
+  FitCtl *ctl = nullptr;
+  LaunchCtl *lc = nullptr;
+  int2 *items = nullptr;
+  int n_items = 0;
+  int grid = 0;
+  int valued = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  FitCtl *h_ctl = nullptr;     // pinned readback
+  uint8_t *penalize = nullptr; // device copy of the penalty mask
+  double *gout = nullptr;
+  double *S0 = nullptr, *S1 = nullptr;
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(cox_handle *h, int code, const std::string &msg) {
+  t_last_error = msg;
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(cox_handle *h, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  return fail(h, COX_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+const DevData &D(const cox_handle *h) { return h->sd->prep.desc; }
+
+int resolve_stream(cox_handle *h) {
+  if (h->opts.stream) {
+    h->stream = static_cast<cudaStream_t>(h->opts.stream);
+    return COX_OK;
+  }
+  if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(h, "stream create");
+  h->stream = h->own_stream;
+  return COX_OK;
+}
+
+int check_options(const cox_options *o) {
+  if (!o) return COX_OK;
+  if (o->penalty < COX_PEN_NONE || o->penalty > COX_PEN_L2) return COX_E_INVALID;
+  if (o->precision != COX_FP64 && o->precision != COX_FP32C) return COX_E_INVALID;
+  if (o->penalty == COX_PEN_L1 && !(o->lambda >= 0.0)) return COX_E_INVALID;
+  if (o->penalty == COX_PEN_L2 && !(o->l2_var > 0.0)) return COX_E_INVALID;
+  if (!(o->tol >= 0.0) || o->max_sweeps < 0) return COX_E_INVALID;
+  return COX_OK;
+}
+
+cox_options default_options() {
+  cox_options o{};
+  o.penalty = COX_PEN_NONE;
+  o.precision = COX_FP64;
+  o.l2_var = 1.0;
+  o.tol = 1e-8;
+  o.max_sweeps = 1000;
+  return o;
+}
+
+// Allocate the per-fit state of a handle on its (shared) data.
+int alloc_fit_state(cox_handle *h) {
+  const DevData &d = D(h);
+  const int64_t M = d.M, T = d.T, p = d.p, G = d.G;
+  const int tile_k = ccd_tile(h->sd->precision);
+  const size_t sv = h->sd->precision == COX_FP32C ? sizeof(float) : sizeof(double);
+  BufferSet &B = h->bufs;
+  h->hfit = DevFit{};
+  h->hfit.d = h->sd->d_desc;
+  h->ctl = static_cast<FitCtl *>(B.get(sizeof(FitCtl)));
+  h->lc = static_cast<LaunchCtl *>(B.get(sizeof(LaunchCtl)));
+  h->dfit = static_cast<DevFit *>(B.get(sizeof(DevFit)));
+  h->items = static_cast<int2 *>(B.get(std::max<int64_t>(T, 1) * sizeof(int2)));
+  h->hfit.eta = static_cast<double *>(B.get(std::max<int64_t>(M, 1) * sizeof(double)));
+  h->hfit.v = B.get((M + tile_k + 64) * sv);
+  h->hfit.beta = static_cast<double *>(B.get(std::max<int64_t>(p, 1) * sizeof(double)));
+  h->hfit.trust = static_cast<double *>(B.get(std::max<int64_t>(p, 1) * sizeof(double)));
+  h->hfit.tstat = static_cast<uint32_t *>(B.get(std::max<int64_t>(T, 1) * sizeof(uint32_t)));
+  h->hfit.tval = static_cast<double *>(B.get(std::max<int64_t>(T, 1) * 6 * sizeof(double)));
+  h->hfit.part = static_cast<double *>(B.get(std::max<int64_t>(T, 1) * 3 * sizeof(double)));
+  h->gout = static_cast<double *>(B.get(std::max<int64_t>(p, 1) * 2 * sizeof(double)));
+  h->S0 = static_cast<double *>(B.get(std::max<int64_t>(G, 1) * sizeof(double)));
+  h->S1 = static_cast<double *>(B.get(std::max<int64_t>(G, 1) * sizeof(double)));
+  h->penalize = static_cast<uint8_t *>(B.get(std::max<int64_t>(p, 1)));
+  if (!h->ctl || !h->lc || !h->dfit || !h->items || !h->hfit.eta || !h->hfit.v || !h->hfit.beta || !h->hfit.trust ||
+      !h->hfit.tstat || !h->hfit.tval || !h->hfit.part || !h->gout || !h->S0 || !h->S1 || !h->penalize)
+    return fail(h, COX_E_OOM, "device allocation failed for the fit state");
+  h->hfit.ctl = h->ctl;
+  if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
+  // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
+  if (cudaMemsetAsync(h->hfit.v, 0, (M + tile_k + 64) * sv, h->stream) != cudaSuccess) return cuda_fail(h, "memset");
+  std::vector<int2> it(static_cast<size_t>(std::max<int64_t>(T, 1)));
+  for (int64_t t = 0; t < T; ++t) it[t] = make_int2(0, int(T - 1 - t));   // reverse order for the look-back
+  h->n_items = int(T);
+  if (cudaMemcpyAsync(h->items, it.data(), std::max<int64_t>(T, 1) * sizeof(int2), cudaMemcpyHostToDevice, h->stream) !=
+      cudaSuccess)
+    return cuda_fail(h, "items copy");
+  LaunchCtl lc{0u, 0u, int32_t(T), 0};
+  if (cudaMemcpyAsync(h->lc, &lc, sizeof(lc), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return cuda_fail(h, "lc copy");
+  h->valued = d.val != nullptr;
+  const int mg = ccd_max_grid(h->sd->precision, h->valued);
+  if (mg <= 0) return cuda_fail(h, "kernel attributes");
+  h->grid = int(std::max<int64_t>(1, std::min<int64_t>(T, mg)));
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "state init");
+  return COX_OK;
+}
+
+int apply_options(cox_handle *h, const cox_options *o) {
+  h->opts = o ? *o : default_options();
+  h->hfit.penalty = h->opts.penalty;
+  h->hfit.lambda = h->opts.lambda;
+  h->hfit.l2_var = h->opts.l2_var;
+  h->hfit.tol = h->opts.tol;
+  h->hfit.max_sweeps = h->opts.max_sweeps;
+  h->hfit.shift = 0.0;
+  h->hfit.penalize = nullptr;
+  int rc = resolve_stream(h);
+  if (rc) return rc;
+  const int64_t p = D(h).p;
+  if (h->opts.penalize && p > 0) {
+    if (cudaMemcpyAsync(h->penalize, h->opts.penalize, p, cudaMemcpyDefault, h->stream) != cudaSuccess)
+      return cuda_fail(h, "penalize copy");
+    h->hfit.penalize = h->penalize;
+  }
+  if (cudaMemcpyAsync(h->dfit, &h->hfit, sizeof(DevFit), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "fit descriptor copy");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "options");
+  return COX_OK;
+}
+
+int push_desc(cox_handle *h) {
+  if (cudaMemcpyAsync(h->dfit, &h->hfit, sizeof(DevFit), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "fit descriptor copy");
+  return COX_OK;
+}
+
+// Reset the fit to coefficients beta0 (host or device, NULL = 0): eta = X beta0 accumulated
+// column by column, v = +-exp(eta - shift), trust half-widths 1, control block at sweep 0.
+int init_state(cox_handle *h, const double *beta0) {
+  const DevData &d = D(h);
+  const int64_t p = d.p;
+  cudaStream_t s = h->stream;
+  std::vector<double> hb(static_cast<size_t>(std::max<int64_t>(p, 1)), 0.0);
+  if (beta0 && p > 0 && cudaMemcpy(hb.data(), beta0, p * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+    return cuda_fail(h, "beta0 read");
+  for (int64_t j = 0; j < p; ++j)
+    if (!std::isfinite(hb[j])) return fail(h, COX_E_INVALID, "beta0 must be finite");
+  if (p > 0 && cudaMemcpyAsync(h->hfit.beta, hb.data(), p * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cuda_fail(h, "beta copy");
+  std::vector<double> ones(static_cast<size_t>(std::max<int64_t>(p, 1)), 1.0);
+  if (p > 0 && cudaMemcpyAsync(h->hfit.trust, ones.data(), p * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cuda_fail(h, "trust copy");
+  if (d.T > 0 && cudaMemsetAsync(h->hfit.tstat, 0, d.T * sizeof(uint32_t), s) != cudaSuccess) return cuda_fail(h, "memset");
+  FitCtl c{};
+  c.j = 0;
+  c.state = kRunning;
+  c.need_ll = 1;
+  c.pend_j = -1;
+  c.epoch = 1u;
+  if (cudaMemcpyAsync(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s) != cudaSuccess) return cuda_fail(h, "ctl copy");
+  int rc = push_desc(h);
+  if (rc) return rc;
+  if ((rc = launch_fill_v(h->sd->precision, h->dfit, d.M, d.exit_bits, s))) return cuda_fail(h, "fill");
+  const auto &cp = h->sd->prep.h_col_ptr;
+  for (int64_t j = 0; j < p; ++j)
+    if (hb[j] != 0.0)
+      if ((rc = launch_column_update(h->sd->precision, h->dfit, int32_t(j), hb[j], cp[j + 1] - cp[j], s)))
+        return cuda_fail(h, "warm start");
+  // *beta0 must stay valid until the copies above completed
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(h, "state init");
+  return COX_OK;
+}
+
+int read_ctl(cox_handle *h) {
+  if (cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(FitCtl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return cuda_fail(h, "ctl read");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "kernel execution");
+  return COX_OK;
+}
+
+int launch_mode(cox_handle *h, int mode, int j) {
+  if (D(h).T == 0) return COX_OK;
+  int rc = launch_ccd(h->sd->precision, h->dfit, h->items, h->lc, h->grid, mode, j, h->valued, h->stream);
+  return rc ? cuda_fail(h, "ccd launch") : COX_OK;
+}
+
+int device_error(cox_handle *h) {
+  const int e = h->h_ctl->error;
+  if (e == COX_E_TIMEOUT) return fail(h, COX_E_TIMEOUT, "a device-side wait exceeded its bound");
+  if (e == COX_E_RANGE) return fail(h, COX_E_RANGE, "|eta - shift| left the float exp range (use COX_FP64)");
+  if (e) return fail(h, e, "device error");
+  return COX_OK;
+}
+
+int build_graph(cox_handle *h, int len) {
+  if (h->graph && h->graph_len == len) return COX_OK;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(h, "capture");
+  for (int i = 0; i < len; ++i)
+    if (launch_ccd(h->sd->precision, h->dfit, h->items, h->lc, h->grid, kModeFit, 0, h->valued, h->stream)) {
+      cudaStreamEndCapture(h->stream, &g);
+      return cuda_fail(h, "capture launch");
+    }
+  if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) return cuda_fail(h, "end capture");
+  const cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, "graph instantiate");
+  h->graph_len = len;
+  return COX_OK;
+}
+
+int copy_out(cox_handle *h, double *dst, const double *src, int64_t count) {
+  if (count <= 0) return COX_OK;
+  if (cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess)
+    return cuda_fail(h, "result copy");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "result copy");
+  return COX_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+int cox_set_allocator(cox_alloc_fn alloc, cox_free_fn release, void *ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) return fail(nullptr, COX_E_INVALID, "allocator: give both or neither");
+  set_allocator(alloc, release, ctx);
+  return COX_OK;
+}
+
+const char *cox_last_error(const cox_handle *h) { return h ? h->err.c_str() : t_last_error.c_str(); }
+
+int cox_create(const cox_data *data, const cox_options *opts, cox_handle **out) {
+  if (!data || !out) return fail(nullptr, COX_E_INVALID, "cox_create: null argument");
+  *out = nullptr;
+  if (check_options(opts)) return fail(nullptr, COX_E_INVALID, "cox_create: invalid options");
+  std::unique_ptr<cox_handle> h(new cox_handle());
+  h->opts = opts ? *opts : default_options();
+  int rc = resolve_stream(h.get());
+  if (rc) return rc;
+  auto *sd = new SharedData();
+  h->sd = sd;
+  sd->precision = h->opts.precision;
+  std::string err;
+  rc = prepare_data(data, sd->precision, h->opts.tile, h->stream, &sd->prep, &err);
+  if (rc) {
+    cudaGetLastError();
+    release_shared(sd);
+    h->sd = nullptr;
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    return fail(nullptr, rc, err.empty() ? "cox_create: preparation failed" : err);
+  }
+  sd->d_desc = static_cast<DevData *>(dev_alloc(sizeof(DevData)));
+  if (!sd->d_desc || cudaMemcpy(sd->d_desc, &sd->prep.desc, sizeof(DevData), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cox_destroy(h.release());
+    return fail(nullptr, COX_E_OOM, "cox_create: descriptor");
+  }
+  if ((rc = alloc_fit_state(h.get())) || (rc = apply_options(h.get(), &h->opts))) {
+    t_last_error = h->err;
+    cox_destroy(h.release());
+    return rc;
+  }
+  *out = h.release();
+  return COX_OK;
+}
+
+int cox_clone(const cox_handle *src, const cox_options *opts, cox_handle **out) {
+  if (!src || !out) return fail(nullptr, COX_E_INVALID, "cox_clone: null argument");
+  *out = nullptr;
+  if (check_options(opts)) return fail(nullptr, COX_E_INVALID, "cox_clone: invalid options");
+  if (opts && opts->precision != src->sd->precision)
+    return fail(nullptr, COX_E_INVALID, "cox_clone: a clone shares the tile plan and must keep the precision");
+  std::unique_ptr<cox_handle> h(new cox_handle());
+  h->opts = opts ? *opts : src->opts;
+  h->sd = src->sd;
+  src->sd->refs.fetch_add(1);
+  int rc = resolve_stream(h.get());
+  if (!rc) rc = alloc_fit_state(h.get());
+  if (!rc) rc = apply_options(h.get(), &h->opts);
+  if (rc) {
+    t_last_error = h->err;
+    cox_destroy(h.release());
+    return rc;
+  }
+  *out = h.release();
+  return COX_OK;
+}
+
+int cox_set_options(cox_handle *h, const cox_options *opts) {
+  if (!h || !opts) return fail(h, COX_E_INVALID, "cox_set_options: null argument");
+  if (check_options(opts)) return fail(h, COX_E_INVALID, "cox_set_options: invalid options");
+  if (opts->precision != h->sd->precision)
+    return fail(h, COX_E_INVALID, "cox_set_options: precision is fixed when the data are prepared");
+  if (h->graph && opts->stream != h->opts.stream) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return apply_options(h, opts);
+}
+
+void cox_destroy(cox_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  h->bufs.release();
+  release_shared(h->sd);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *info) {
+  if (!h || !beta_out) return fail(h, COX_E_INVALID, "cox_fit: null argument");
+  const DevData &d = D(h);
+  int rc = init_state(h, beta0);
+  if (rc) return rc;
+  if (d.p == 0 || d.T == 0) {
+    // nothing to update: the objective at beta0 is final
+    if ((rc = launch_mode(h, kModeLL, -1)) || (rc = read_ctl(h))) return rc;
+    if ((rc = device_error(h))) return rc;
+    if (info) {
+      *info = cox_fit_info{};
+      info->converged = 1;
+      info->loglik = d.T == 0 ? 0.0 : h->h_ctl->out_ll;
+      info->objective = -info->loglik;
+    }
+    return copy_out(h, beta_out, h->hfit.beta, d.p);
+  }
+  const int len = int(std::min<int64_t>(std::max<int64_t>(d.p, 32), 4096));
+  if ((rc = build_graph(h, len))) return rc;
+  const int64_t max_launches = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
+  int64_t launched = 0;
+  if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
+    return cuda_fail(h, "event create");
+  cudaEventRecord(h->ev0, h->stream);
+  for (;;) {
+    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return cuda_fail(h, "graph launch");
+    cudaEventRecord(h->ev1, h->stream);
+    count_launches(len);
+    launched += len;
+    if ((rc = read_ctl(h))) return rc;
+    if (h->h_ctl->error) break;
+    if (h->h_ctl->state != kRunning) break;
+    if (launched > max_launches) return fail(h, COX_E_INVALID, "cox_fit: sweep accounting exceeded its bound");
+  }
+  if ((rc = device_error(h))) return rc;
+  const FitCtl &c = *h->h_ctl;
+  rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
+  if (info) {
+    info->sweeps = c.sweep;
+    info->converged = c.state == kConverged;
+    info->coord_updates = c.coord_updates;
+    info->loglik = c.loglik;
+    info->objective = c.obj;
+    info->status = rc;
+    info->step_launches = launched;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->sweep_ms = ms;
+  }
+  int rc2 = copy_out(h, beta_out, h->hfit.beta, d.p);
+  return rc2 ? rc2 : rc;
+}
+
+int cox_loglik(cox_handle *h, const double *beta, double *loglik_out) {
+  if (!h || !loglik_out) return fail(h, COX_E_INVALID, "cox_loglik: null argument");
+  int rc = init_state(h, beta);
+  if (rc) return rc;
+  if (D(h).T == 0) {
+    *loglik_out = 0.0;
+    return COX_OK;
+  }
+  if ((rc = launch_mode(h, kModeLL, -1)) || (rc = read_ctl(h)) || (rc = device_error(h))) return rc;
+  *loglik_out = h->h_ctl->out_ll;
+  return COX_OK;
+}
+
+int cox_gradient(cox_handle *h, const double *beta, double *grad, double *hess_diag) {
+  if (!h || !grad) return fail(h, COX_E_INVALID, "cox_gradient: null argument");
+  const DevData &d = D(h);
+  int rc = init_state(h, beta);
+  if (rc) return rc;
+  h->hfit.gout = h->gout;
+  if ((rc = push_desc(h))) return rc;
+  if (d.T == 0 && d.p > 0) cudaMemsetAsync(h->gout, 0, 2 * d.p * sizeof(double), h->stream);
+  for (int32_t j = 0; j < d.p; ++j)
+    if ((rc = launch_mode(h, kModeEval, j))) break;
+  h->hfit.gout = nullptr;
+  int rc2 = push_desc(h);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if ((rc = read_ctl(h)) || (rc = device_error(h))) return rc;
+  std::vector<double> g(static_cast<size_t>(2 * std::max<int32_t>(d.p, 1)));
+  if (d.p > 0 && cudaMemcpy(g.data(), h->gout, 2 * d.p * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(h, "gradient read");
+  std::vector<double> g1(d.p), g2(d.p);
+  for (int32_t j = 0; j < d.p; ++j) {
+    g1[j] = g[2 * j];
+    g2[j] = g[2 * j + 1];
+  }
+  if (d.p > 0 && cudaMemcpy(grad, g1.data(), d.p * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+    return cuda_fail(h, "gradient write");
+  if (hess_diag && d.p > 0 && cudaMemcpy(hess_diag, g2.data(), d.p * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+    return cuda_fail(h, "hessian write");
+  return COX_OK;
+}
+
+int cox_risk_sums(cox_handle *h, const double *beta, int32_t j, double *S0, double *S1, int64_t *n_groups) {
+  if (!h) return fail(h, COX_E_INVALID, "cox_risk_sums: null handle");
+  const DevData &d = D(h);
+  if (n_groups) *n_groups = d.G;
+  if (!S0 && !S1) return COX_OK;
+  if (j >= d.p) return fail(h, COX_E_INVALID, "cox_risk_sums: column out of range");
+  int rc = init_state(h, beta);
+  if (rc) return rc;
+  if (d.G == 0) return COX_OK;
+  cudaMemsetAsync(h->S1, 0, d.G * sizeof(double), h->stream);
+  h->hfit.out_S0 = h->S0;
+  h->hfit.out_S1 = h->S1;
+  if ((rc = push_desc(h))) return rc;
+  rc = launch_mode(h, j >= 0 ? kModeEval : kModeLL, j);
+  h->hfit.out_S0 = h->hfit.out_S1 = nullptr;
+  int rc2 = push_desc(h);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if ((rc = read_ctl(h)) || (rc = device_error(h))) return rc;
+  if (S0 && (rc = copy_out(h, S0, h->S0, d.G))) return rc;
+  if (S1 && (rc = copy_out(h, S1, h->S1, d.G))) return rc;
+  return COX_OK;
+}
+
+int cox_metadata(cox_handle *h, int64_t *n_groups, int64_t *n_strata, int32_t *group_stratum, int32_t *group_time,
+                 int32_t *group_events, int64_t *group_at_risk, int64_t *strata_start) {
+  if (!h) return fail(h, COX_E_INVALID, "cox_metadata: null handle");
+  const DevData &d = D(h);
+  const Prepared &P = h->sd->prep;
+  if (n_groups) *n_groups = d.G;
+  if (n_strata) *n_strata = d.K;
+  auto copy_i32 = [&](int32_t *dst, const int32_t *src, int64_t n) -> int {
+    if (!dst || n <= 0) return COX_OK;
+    return cudaMemcpy(dst, src, n * sizeof(int32_t), cudaMemcpyDefault) == cudaSuccess ? COX_OK
+                                                                                        : cuda_fail(h, "metadata copy");
+  };
+  int rc;
+  if ((rc = copy_i32(group_stratum, P.g_stratum, d.G)) || (rc = copy_i32(group_time, P.g_time, d.G)) ||
+      (rc = copy_i32(group_events, d.head_d, d.G)))
+    return rc;
+  if (strata_start) {
+    std::vector<int32_t> ss(static_cast<size_t>(d.K) + 1);
+    if (cudaMemcpy(ss.data(), P.strata_start, (d.K + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(h, "metadata copy");
+    std::vector<int64_t> s64(ss.begin(), ss.end());
+    if (cudaMemcpy(strata_start, s64.data(), s64.size() * sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess)
+      return cuda_fail(h, "metadata copy");
+  }
+  if (group_at_risk && d.G > 0) {
+    // with beta = 0 and no shift every position holds +-1, so the risk-set sums are counts
+    std::vector<double> c(static_cast<size_t>(d.G));
+    const double shift = h->hfit.shift;
+    h->hfit.shift = 0.0;
+    rc = cox_risk_sums(h, nullptr, -1, c.data(), nullptr, nullptr);
+    h->hfit.shift = shift;
+    push_desc(h);
+    if (rc) return rc;
+    std::vector<int64_t> ci(c.size());
+    for (size_t g = 0; g < c.size(); ++g) ci[g] = int64_t(std::llround(c[g]));
+    if (cudaMemcpy(group_at_risk, ci.data(), ci.size() * sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess)
+      return cuda_fail(h, "metadata copy");
+  }
+  return COX_OK;
+}
+
+int cox_dx(cox_handle *h, double *dx) {
+  if (!h || !dx) return fail(h, COX_E_INVALID, "cox_dx: null argument");
+  const DevData &d = D(h);
+  if (d.p > 0 && cudaMemcpy(dx, d.dX, d.p * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+    return cuda_fail(h, "dx copy");
+  return COX_OK;
+}
+
+int64_t cox_launch_count(void) { return launch_count(); }
+
+int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes) {
+  if (!data || !bytes) return fail(nullptr, COX_E_INVALID, "cox_footprint: null argument");
+  const int precision = opts ? opts->precision : COX_FP64;
+  std::vector<int64_t> cp(2, 0);
+  int64_t nnz = 0;
+  if (data->p > 0 && cudaMemcpy(&nnz, data->col_ptr + data->p, sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess)
+    return fail(nullptr, COX_E_INVALID, "cox_footprint: cannot read col_ptr");
+  const int64_t n = data->n_rows, p = data->p;
+  const int64_t M = data->start ? 2 * n : n, nnzp = data->start ? 2 * nnz : nnz;
+  const int64_t tile = opts && opts->tile > 0 ? opts->tile : ccd_tile(precision);
+  const int64_t T = (M + tile - 1) / tile + 1;
+  const int64_t sv = precision == COX_FP32C ? 4 : 8;
+  int64_t b = 0;
+  b += 8 * (p + 1) + 4 * nnzp + (data->val ? 8 * nnzp : 0);     // CSC
+  b += 4 * p * (T + 1) + 12 * (T + 1) + 8 * p;                  // tables, dX
+  b += 16 * n / 8 + 4 * n;                                       // tie groups / strata (upper bounds)
+  b += 8 * M + sv * (M + tile + 64) + (data->start ? M / 8 + 8 : 0);   // eta, v, exit bits
+  b += 8 * 5 * p + 4 * T + 72 * T + 8 * T + 2 * 8 * n / 4;       // beta, trust, gout; look-back; items; diagnostics
+  *bytes = size_t(b) + 64 * 1024;
+  return COX_OK;
+}
+
+// ------------------------------------------------------------------ batched fits
+int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, double *const *beta_out,
+                  cox_fit_info *info) {
+  if (!hs || n <= 0 || !beta_out) return fail(nullptr, COX_E_INVALID, "cox_batch_fit: bad arguments");
+  const int precision = hs[0]->sd->precision;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || !beta_out[i]) return fail(nullptr, COX_E_INVALID, "cox_batch_fit: null handle or output");
+    if (hs[i]->sd->precision != precision) return fail(nullptr, COX_E_INVALID, "cox_batch_fit: mixed precisions");
+  }
+  cox_handle *h0 = hs[0];
+  cudaStream_t s = h0->stream;
+  // per-fit init on the shared stream
+  std::vector<cudaStream_t> saved(n);
+  int rc = COX_OK;
+  for (int i = 0; i < n && !rc; ++i) {
+    saved[i] = hs[i]->stream;
+    hs[i]->stream = s;
+    rc = init_state(hs[i], beta0 ? beta0[i] : nullptr);
+  }
+  // batch-owned descriptors, control blocks and work list
+  BufferSet B;
+  DevFit *fits = static_cast<DevFit *>(B.get(n * sizeof(DevFit)));
+  FitCtl *ctls = static_cast<FitCtl *>(B.get(n * sizeof(FitCtl)));
+  LaunchCtl *lc = static_cast<LaunchCtl *>(B.get(sizeof(LaunchCtl)));
+  int64_t total_items = 0;
+  int valued = 0;
+  for (int i = 0; i < n; ++i) {
+    total_items += D(hs[i]).T;
+    valued |= hs[i]->valued;
+  }
+  int2 *items = static_cast<int2 *>(B.get(std::max<int64_t>(total_items, 1) * sizeof(int2)));
+  FitCtl *hc = nullptr;
+  if (!rc && (!fits || !ctls || !lc || !items)) rc = fail(nullptr, COX_E_OOM, "cox_batch_fit: allocation");
+  if (!rc && cudaMallocHost(&hc, n * sizeof(FitCtl)) != cudaSuccess) rc = cuda_fail(nullptr, "pinned alloc");
+  std::vector<DevFit> hf(n);
+  for (int i = 0; i < n && !rc; ++i) {
+    hf[i] = hs[i]->hfit;
+    hf[i].ctl = ctls + i;
+    if (cudaMemcpyAsync(ctls + i, hs[i]->ctl, sizeof(FitCtl), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = cuda_fail(nullptr, "ctl copy");
+  }
+  if (!rc && cudaMemcpyAsync(fits, hf.data(), n * sizeof(DevFit), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = cuda_fail(nullptr, "fits copy");
+  std::vector<int> running(n, 1);
+  auto rebuild_items = [&]() -> int {
+    std::vector<int2> it;
+    // interleave fits tile by tile (each fit's tiles stay in reverse order)
+    int64_t maxT = 0;
+    for (int i = 0; i < n; ++i)
+      if (running[i]) maxT = std::max<int64_t>(maxT, D(hs[i]).T);
+    for (int64_t k = 0; k < maxT; ++k)
+      for (int i = 0; i < n; ++i)
+        if (running[i] && k < D(hs[i]).T) it.push_back(make_int2(i, int(D(hs[i]).T - 1 - k)));
+    LaunchCtl l{0u, 0u, int32_t(it.size()), 0};
+    if (!it.empty() && cudaMemcpyAsync(items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_fail(nullptr, "items copy");
+    if (cudaMemcpyAsync(lc, &l, sizeof(l), cudaMemcpyHostToDevice, s) != cudaSuccess) return cuda_fail(nullptr, "lc copy");
+    return cudaStreamSynchronize(s) == cudaSuccess ? COX_OK : cuda_fail(nullptr, "items");
+  };
+  int64_t maxp = 1, max_launches = 0;
+  for (int i = 0; i < n; ++i) {
+    maxp = std::max<int64_t>(maxp, D(hs[i]).p);
+    max_launches = std::max<int64_t>(max_launches, (int64_t(hs[i]->opts.max_sweeps) + 2) * D(hs[i]).p + 2);
+    if (D(hs[i]).p == 0 || D(hs[i]).T == 0) running[i] = 0;
+  }
+  if (!rc) rc = rebuild_items();
+  cudaGraphExec_t graph = nullptr;
+  const int len = int(std::min<int64_t>(std::max<int64_t>(maxp, 32), 2048));
+  const int grid = std::max(1, ccd_max_grid(precision, valued));
+  if (!rc) {
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = cuda_fail(nullptr, "capture");
+    for (int i = 0; i < len && !rc; ++i)
+      if (launch_ccd(precision, fits, items, lc, grid, kModeFit, 0, valued, s)) rc = cuda_fail(nullptr, "capture launch");
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess && !rc) rc = cuda_fail(nullptr, "end capture");
+    if (!rc) {
+      if (cudaGraphInstantiate(&graph, g, 0) != cudaSuccess) rc = cuda_fail(nullptr, "instantiate");
+      cudaGraphDestroy(g);
+    }
+  }
+  int64_t launched = 0;
+  while (!rc) {
+    int any = 0;
+    for (int i = 0; i < n; ++i) any |= running[i];
+    if (!any) break;
+    if (cudaGraphLaunch(graph, s) != cudaSuccess) { rc = cuda_fail(nullptr, "graph launch"); break; }
+    count_launches(len);
+    launched += len;
+    if (cudaMemcpyAsync(hc, ctls, n * sizeof(FitCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = cuda_fail(nullptr, "batch execution");
+      break;
+    }
+    bool changed = false;
+    for (int i = 0; i < n; ++i)
+      if (running[i] && (hc[i].state != kRunning || hc[i].error)) {
+        running[i] = 0;
+        changed = true;
+      }
+    if (changed) rc = rebuild_items();
+    if (launched > max_launches + len) { rc = fail(nullptr, COX_E_INVALID, "cox_batch_fit: launch bound exceeded"); break; }
+  }
+  if (graph) cudaGraphExecDestroy(graph);
+  int worst = rc;
+  if (!rc) {
+    for (int i = 0; i < n; ++i) {
+      cox_handle *h = hs[i];
+      // results back into the handle
+      cudaMemcpyAsync(h->ctl, ctls + i, sizeof(FitCtl), cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->h_ctl, ctls + i, sizeof(FitCtl), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      const FitCtl &c = *h->h_ctl;
+      int r = c.error ? device_error(h) : (D(h).p == 0 ? COX_OK : (c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED));
+      if (D(h).p == 0 || D(h).T == 0) r = COX_OK;
+      if (info) {
+        info[i].sweeps = c.sweep;
+        info[i].converged = c.state == kConverged || D(h).p == 0;
+        info[i].coord_updates = c.coord_updates;
+        info[i].loglik = c.loglik;
+        info[i].objective = c.obj;
+        info[i].status = r;
+      }
+      int r2 = copy_out(h, beta_out[i], h->hfit.beta, D(h).p);
+      if (r2) r = r2;
+      if (r < 0 || (worst >= 0 && r > worst)) worst = r;
+    }
+  }
+  for (int i = 0; i < n; ++i) hs[i]->stream = saved[i];
+  if (hc) cudaFreeHost(hc);
+  cudaStreamSynchronize(s);
+  return worst;
+}
+
+}  // extern "C"

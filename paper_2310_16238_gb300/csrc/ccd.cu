@@ -1,0 +1,733 @@
+// Fused coordinate-step kernel for cyclic coordinate descent on the stratified /
+// time-varying Cox partial likelihood (arXiv 2310.16238, §2.4-§2.7).
+//
+// One launch advances every fit in its work list by one coordinate. A work item is one
+// tile (a contiguous range of risk-sequence positions) of one fit. Per item, one CTA:
+//   1. applies the previous coordinate's pending update at the tile's nonzeros
+//      (eta += x_j * dbeta, eq. parallel_xb; v = +-exp(eta - shift), eq. parallel_d),
+//   2. stages the tile of v in shared memory (cp.async, XOR-swizzled 16-byte chunks),
+//   3. runs a stratum-segmented suffix scan of D = v, N1 = x_j v, N2 = x_j^2 v in registers
+//      (one thread = ITEMS consecutive positions), recording local sums at tie-group read
+//      positions; strata are segments of the paper's flag-value operator (§2.6), applied
+//      right to left,
+//   4. combines threads with a warp-shuffle segmented scan and tiles with a decoupled
+//      look-back over FP64 tile carries,
+//   5. evaluates the ratios of eqs. (parallel_g)/(parallel_h) at its tie groups and reduces
+//      them to a tile partial (G1, G2[, sum d log S0]),
+//   6. and the last CTA of a fit reduces the partials in a fixed order and takes the
+//      coordinate step (§2.4: Newton eq. newton, trust region, L1 directional derivatives).
+// No N-length vector is written except at the nonzeros of the updated column.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "cox.h"
+#include "cox_internal.h"
+
+namespace coxgb {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ------------------------------------------------------------------ precision policies
+// FP64: values, scans, ratios in double.
+struct PF64 {
+  using T = double;
+  static constexpr int ITEMS = 16;
+  struct Acc { double s; };
+  __device__ static Acc zero() { return {0.0}; }
+  __device__ static void add(Acc &a, double x) { a.s = a.s + x; }
+  __device__ static Acc comb(Acc a, Acc b) { return {a.s + b.s}; }
+  __device__ static double to64(Acc a) { return a.s; }
+  __device__ static Acc from64(double x) { return {x}; }
+  __device__ static Acc shfl_down(Acc a, int off) { return {__shfl_down_sync(0xffffffffu, a.s, off)}; }
+};
+
+// FP32 with a compensation term: a = s + c, additions by Knuth's TwoSum (error-free
+// transformation, TAOCP vol. 2 §4.2.2), so tile sums carry ~2x float precision.
+struct PF32C {
+  using T = float;
+  static constexpr int ITEMS = 32;
+  struct Acc { float s, c; };
+  __device__ static Acc zero() { return {0.0f, 0.0f}; }
+  __device__ static void add(Acc &a, float x) {
+    float t = __fadd_rn(a.s, x);
+    float bp = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+  }
+  __device__ static Acc comb(Acc a, Acc b) {
+    Acc r = a;
+    add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+  }
+  __device__ static double to64(Acc a) { return (double)a.s + (double)a.c; }
+  __device__ static Acc from64(double x) {
+    float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
+  }
+  __device__ static Acc shfl_down(Acc a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)};
+  }
+};
+
+constexpr long long kSpinBudget = 4000000000LL;   // ~2 s of SM clock for any device-side wait
+
+// ------------------------------------------------------------------ shared memory plan
+template <class P>
+struct Smem {
+  using T = typename P::T;
+  using Acc = typename P::Acc;
+  static constexpr int TILE = kThreads * P::ITEMS;
+  static constexpr int WORDS = TILE / 32;
+  static constexpr size_t o_v = 0;
+  static constexpr size_t o_head = o_v + sizeof(T) * TILE;
+  static constexpr size_t o_cut = o_head + 4 * WORDS;
+  static constexpr size_t o_nz = o_cut + 4 * WORDS;
+  static constexpr size_t o_hpre = o_nz + 4 * WORDS;
+  static constexpr size_t o_hloc = (o_hpre + 4 * WORDS + 15) & ~size_t(15);
+  static constexpr size_t o_hcut = o_hloc + sizeof(Acc) * 3 * kHeadCap;
+  static constexpr size_t o_tc = (o_hcut + kHeadCap + 15) & ~size_t(15);
+  static constexpr size_t o_tflag = o_tc + sizeof(Acc) * 3 * kThreads;
+  static constexpr size_t o_x = (o_tflag + kThreads + 15) & ~size_t(15);
+  static constexpr size_t bytes_binary = o_x;
+  static constexpr size_t bytes_valued = o_x + sizeof(T) * TILE;
+};
+
+// ------------------------------------------------------------------ the coordinate step
+// §2.4 as read in the design notes: L2 adds beta/sigma^2 and 1/sigma^2; L1 uses the
+// directional derivatives g' +- gamma at 0 and g' + gamma sgn(beta) elsewhere; the Newton
+// step is clipped to the trust half-width, an L1 step that would cross 0 stops at 0, and
+// the half-width becomes max(2 |step|, half-width / 2). g'' <= 0 skips the coordinate.
+__device__ double ccd_step_rule(double g1, double g2, double b, double *tr, int penalty, double lambda,
+                                double l2_var, int penalized) {
+  double gamma = 0.0;
+  if (penalized && penalty == COX_PEN_L2) {
+    g1 = g1 + b / l2_var;
+    g2 = g2 + 1.0 / l2_var;
+  }
+  if (penalized && penalty == COX_PEN_L1) gamma = lambda;
+  double s;
+  if (!(g2 > 0.0) || !isfinite(g1) || !isfinite(g2)) {
+    s = 0.0;
+  } else if (gamma > 0.0) {
+    if (b == 0.0) {
+      if (g1 + gamma < 0.0) s = -(g1 + gamma) / g2;
+      else if (g1 - gamma > 0.0) s = -(g1 - gamma) / g2;
+      else s = 0.0;
+    } else {
+      s = -(g1 + (b > 0.0 ? gamma : -gamma)) / g2;
+    }
+  } else {
+    s = -g1 / g2;
+  }
+  double t = *tr;
+  if (fabs(s) > t) s = s > 0.0 ? t : -t;
+  if (gamma > 0.0 && b != 0.0) {
+    double nb = b + s;
+    if ((b > 0.0 && nb < 0.0) || (b < 0.0 && nb > 0.0)) s = -b;
+  }
+  double a2 = 2.0 * fabs(s), h = 0.5 * t;
+  *tr = a2 > h ? a2 : h;
+  return s;
+}
+
+// Block-wide sum of NV doubles in a fixed order (deterministic for fixed inputs).
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *scratch /* [NV*32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double x = lane < (kThreads / 32) ? scratch[i * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      v[i] = x;   // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+template <class P>
+__device__ __forceinline__ typename P::T load_v(const void *v, int64_t pos) {
+  return static_cast<const typename P::T *>(v)[pos];
+}
+
+// value written at a position for exp(eta - shift); exits hold the negative
+template <class P>
+__device__ __forceinline__ typename P::T make_v(double eta, double shift, bool exitp, int32_t *err) {
+  if constexpr (sizeof(typename P::T) == 8) {
+    double e = exp(eta - shift);
+    return exitp ? -e : e;
+  } else {
+    double a = eta - shift;
+    if (!(fabs(a) < 80.0)) atomicExch(err, COX_E_RANGE);
+    float e = expf(__double2float_rn(a));
+    return exitp ? -e : e;
+  }
+}
+
+// ------------------------------------------------------------------ the kernel
+template <class P>
+__global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict__ fits, const int2 *__restrict__ items,
+                                                       LaunchCtl *lc, int mode, int j_eval, int valued) {
+  using T = typename P::T;
+  using Acc = typename P::Acc;
+  using S = Smem<P>;
+  constexpr int ITEMS = P::ITEMS;
+  constexpr int TILE = S::TILE;
+  constexpr int WORDS = S::WORDS;
+  constexpr int PC = 16 / sizeof(T);          // elements per 16-byte chunk
+  constexpr int CHUNKS = TILE / PC;
+  constexpr int TCH = ITEMS / PC;             // chunks per thread (8)
+  static_assert(TCH == 8, "each thread owns 128 bytes");
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sv = reinterpret_cast<T *>(smem + S::o_v);
+  uint32_t *headbits = reinterpret_cast<uint32_t *>(smem + S::o_head);
+  uint32_t *cutbits = reinterpret_cast<uint32_t *>(smem + S::o_cut);
+  uint32_t *nzbits = reinterpret_cast<uint32_t *>(smem + S::o_nz);
+  int32_t *hpre = reinterpret_cast<int32_t *>(smem + S::o_hpre);
+  Acc *hloc = reinterpret_cast<Acc *>(smem + S::o_hloc);
+  uint8_t *hcut = reinterpret_cast<uint8_t *>(smem + S::o_hcut);
+  Acc *tc = reinterpret_cast<Acc *>(smem + S::o_tc);
+  uint8_t *tflag = reinterpret_cast<uint8_t *>(smem + S::o_tflag);
+  T *xs = reinterpret_cast<T *>(smem + S::o_x);
+
+  __shared__ int s_item;
+  __shared__ int s_last;
+  __shared__ double s_red[3 * 32];
+  __shared__ Acc s_wagg[3][kThreads / 32];
+  __shared__ int s_wflag[kThreads / 32];
+  __shared__ Acc s_wcar[3][kThreads / 32];
+  __shared__ int s_wcflag[kThreads / 32];
+  __shared__ double s_tile_carry[3];
+  __shared__ double s_tile_agg[3];
+  __shared__ int s_tile_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n_items = lc->n_items;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&lc->ticket, 1u);
+    __syncthreads();
+    const int w = s_item;
+    if (w >= n_items) break;
+    const int2 it = items[w];
+    const DevFit &F = fits[it.x];
+    const int t = it.y;
+    FitCtl *ctl = F.ctl;
+    if (mode == kModeFit && ctl->state != kRunning) {
+      __syncthreads();
+      continue;
+    }
+    const DevData *D = F.d;
+    const int T_ = D->T;
+    const int lo = D->tile_lo[t], hi = D->tile_lo[t + 1];
+    const int j = mode == kModeEval ? j_eval : (mode == kModeFit ? ctl->j : -1);
+    const bool need_ll = mode == kModeLL || (mode == kModeFit && ctl->need_ll);
+    const int pend_j = mode == kModeFit ? ctl->pend_j : -1;
+    const double pend_db = ctl->pend_db;
+    const uint32_t epoch = ctl->epoch;
+    const double shift = F.shift;
+    const int vf = valued && D->val != nullptr;   // `valued`: the launch reserved shared memory for x
+
+    // ---- 1. stage the tile of v (async), overlapped with the metadata below
+    {
+      const unsigned char *g = reinterpret_cast<const unsigned char *>(static_cast<const T *>(F.v) + lo);
+      for (int c = tid; c < CHUNKS; c += kThreads) {
+        int phys = c ^ ((c >> 3) & 7);
+        cp_async16(smem + S::o_v + size_t(phys) * 16, g + size_t(c) * 16);
+      }
+      cp_async_commit();
+    }
+    for (int q = tid; q < WORDS; q += kThreads) { headbits[q] = 0u; cutbits[q] = 0u; nzbits[q] = 0u; }
+    if (vf)
+      for (int q = tid; q < TILE; q += kThreads) xs[q] = T(0);
+    __syncthreads();
+    const int ga = D->tile_g[t], nh = D->tile_g[t + 1] - ga;
+    for (int h = tid; h < nh; h += kThreads) {
+      int pos = D->head_pos[ga + h] - lo;
+      atomicOr(&headbits[pos >> 5], 1u << (pos & 31));
+    }
+    {
+      const int ka = D->tile_k[t], kb = D->tile_k[t + 1];
+      for (int k = ka + tid; k < kb; k += kThreads) {
+        int pos = D->cut_pos[k] - lo;
+        atomicOr(&cutbits[pos >> 5], 1u << (pos & 31));
+      }
+    }
+    if (j >= 0) {
+      const int64_t cb = D->col_ptr[j];
+      const int32_t *ct = D->col_tile + int64_t(j) * (T_ + 1);
+      const int64_t qa = cb + ct[t], qb = cb + ct[t + 1];
+      for (int64_t q = qa + tid; q < qb; q += kThreads) {
+        int pos = int(D->idx[q] & kPosMask) - lo;
+        atomicOr(&nzbits[pos >> 5], 1u << (pos & 31));
+        if (vf) xs[pos] = T(D->val[q]);
+      }
+    }
+    // ---- pending update of the previous coordinate at this tile's nonzeros (global)
+    int64_t ua = 0, ub = 0;
+    if (pend_j >= 0) {
+      const int64_t cb = D->col_ptr[pend_j];
+      const int32_t *ct = D->col_tile + int64_t(pend_j) * (T_ + 1);
+      ua = cb + ct[t];
+      ub = cb + ct[t + 1];
+      for (int64_t q = ua + tid; q < ub; q += kThreads) {
+        uint32_t e = D->idx[q];
+        int64_t pos = e & kPosMask;
+        double x = D->val ? D->val[q] : 1.0;
+        double et = __dadd_rn(F.eta[pos], __dmul_rn(x, pend_db));
+        F.eta[pos] = et;
+        static_cast<T *>(F.v)[pos] = make_v<P>(et, shift, (e & kExitBit) != 0, &ctl->error);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // patch the staged tile with the updated values (each thread rereads its own writes)
+    for (int64_t q = ua + tid; q < ub; q += kThreads) {
+      int e = int(D->idx[q] & kPosMask) - lo;
+      int c = e / PC;
+      sv[(c ^ ((c >> 3) & 7)) * PC + (e % PC)] = static_cast<const T *>(F.v)[lo + e];
+    }
+    if (hi - lo < TILE)
+      for (int e = hi - lo + tid; e < TILE; e += kThreads) {
+        int c = e / PC;
+        sv[(c ^ ((c >> 3) & 7)) * PC + (e % PC)] = T(0);
+      }
+    if (warp == 0) {   // exclusive popcount prefix of the head bitmask
+      int run = 0;
+      for (int base = 0; base < WORDS; base += 32) {
+        int c = base + lane < WORDS ? __popc(headbits[base + lane]) : 0;
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += y;
+        }
+        if (base + lane < WORDS) hpre[base + lane] = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncthreads();
+
+    // ---- 3. per-thread segmented suffix over ITEMS consecutive positions
+    T vals[ITEMS];
+    {
+      const int c0 = tid * TCH;
+#pragma unroll
+      for (int k = 0; k < TCH; ++k) {
+        int c = c0 + k;
+        int phys = c ^ ((c >> 3) & 7);
+        const float4 q = *reinterpret_cast<const float4 *>(smem + S::o_v + size_t(phys) * 16);
+        const T *qq = reinterpret_cast<const T *>(&q);
+#pragma unroll
+        for (int u = 0; u < PC; ++u) vals[k * PC + u] = qq[u];
+      }
+    }
+    const int b0 = tid * ITEMS;
+    const uint32_t wmask = ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u);
+    const uint32_t hm = (headbits[b0 >> 5] >> (b0 & 31)) & wmask;
+    const uint32_t cm = (cutbits[b0 >> 5] >> (b0 & 31)) & wmask;
+    const uint32_t zm = (nzbits[b0 >> 5] >> (b0 & 31)) & wmask;
+    const int hb = hpre[b0 >> 5] + __popc(headbits[b0 >> 5] & ((1u << (b0 & 31)) - 1u));
+    Acc a0 = P::zero(), a1 = P::zero(), a2 = P::zero();
+    int seen = 0;
+    const bool any_nz = __any_sync(0xffffffffu, zm != 0u);
+#pragma unroll
+    for (int k = ITEMS - 1; k >= 0; --k) {
+      if ((cm >> k) & 1u) { a0 = P::zero(); a1 = P::zero(); a2 = P::zero(); seen = 1; }
+      P::add(a0, vals[k]);
+      if (any_nz && __any_sync(0xffffffffu, (zm >> k) & 1u)) {
+        if ((zm >> k) & 1u) {
+          T x = vf ? xs[b0 + k] : T(1);
+          T wv = vf ? T(x * vals[k]) : vals[k];
+          P::add(a1, wv);
+          if (vf) P::add(a2, T(x * wv));
+        }
+      }
+      if ((hm >> k) & 1u) {
+        int h = hb + __popc(hm & ((1u << k) - 1u));
+        hloc[3 * h + 0] = a0; hloc[3 * h + 1] = a1; hloc[3 * h + 2] = vf ? a2 : a1;
+        hcut[h] = uint8_t(seen);
+      }
+    }
+    if (!vf) a2 = a1;
+
+    // ---- 4a. warp-level inclusive segmented suffix scan of the thread aggregates
+    int f = cm != 0u;
+    Acc i0 = a0, i1 = a1, i2 = a2;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      Acc y0 = P::shfl_down(i0, off), y1 = P::shfl_down(i1, off), y2 = P::shfl_down(i2, off);
+      int yf = __shfl_down_sync(0xffffffffu, f, off);
+      if (lane + off < 32) {
+        if (!f) { i0 = P::comb(i0, y0); i1 = P::comb(i1, y1); i2 = P::comb(i2, y2); }
+        f |= yf;
+      }
+    }
+    if (lane == 0) { s_wagg[0][warp] = i0; s_wagg[1][warp] = i1; s_wagg[2][warp] = i2; s_wflag[warp] = f; }
+    // exclusive within the warp: the inclusive value of lane + 1
+    Acc e0 = P::shfl_down(i0, 1), e1 = P::shfl_down(i1, 1), e2 = P::shfl_down(i2, 1);
+    int ef = __shfl_down_sync(0xffffffffu, f, 1);
+    if (lane == 31) { e0 = P::zero(); e1 = P::zero(); e2 = P::zero(); ef = 0; }
+    __syncthreads();
+    if (tid == 0) {   // 4b. suffix over the warps (8 values, sequential)
+      Acc c0 = P::zero(), c1 = P::zero(), c2 = P::zero();
+      int cf = 0;
+      for (int ww = kThreads / 32 - 1; ww >= 0; --ww) {
+        s_wcar[0][ww] = c0; s_wcar[1][ww] = c1; s_wcar[2][ww] = c2; s_wcflag[ww] = cf;
+        if (s_wflag[ww]) { c0 = s_wagg[0][ww]; c1 = s_wagg[1][ww]; c2 = s_wagg[2][ww]; cf = 1; }
+        else { c0 = P::comb(s_wagg[0][ww], c0); c1 = P::comb(s_wagg[1][ww], c1); c2 = P::comb(s_wagg[2][ww], c2); }
+      }
+      s_tile_agg[0] = P::to64(c0); s_tile_agg[1] = P::to64(c1); s_tile_agg[2] = P::to64(c2);
+      s_tile_flag = cf;
+    }
+    __syncthreads();
+    if (!ef) {
+      e0 = P::comb(e0, s_wcar[0][warp]); e1 = P::comb(e1, s_wcar[1][warp]); e2 = P::comb(e2, s_wcar[2][warp]);
+      ef = s_wcflag[warp];
+    }
+    tc[3 * tid + 0] = e0; tc[3 * tid + 1] = e1; tc[3 * tid + 2] = e2;
+    tflag[tid] = uint8_t(ef);
+
+    // ---- 4c. publish the tile aggregate and look back (warp 0)
+    if (warp == 0) {
+      const int tf = s_tile_flag;
+      const uint32_t ep = (epoch & 0x1fffffffu) << 3;
+      if (lane == 0) {   // slots 0..2: aggregate, 3..5: inclusive (a flagged tile is complete)
+        const int o = tf ? 3 : 0;
+        F.tval[6 * t + o + 0] = s_tile_agg[0]; F.tval[6 * t + o + 1] = s_tile_agg[1]; F.tval[6 * t + o + 2] = s_tile_agg[2];
+        __threadfence();
+        st_release_u32(&F.tstat[t], ep | (tf ? 4u | 2u : 1u));
+      }
+      double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+      const bool last_is_cut = ((cutbits[(hi - lo - 1) >> 5] >> ((hi - lo - 1) & 31)) & 1u) != 0u;
+      if (t + 1 < T_ && !last_is_cut) {
+        int base = t + 1;
+        const long long t0 = clock64();
+        bool timed_out = false;
+        for (;;) {
+          const int u = base + lane;
+          uint32_t st = 0;
+          bool valid = false;
+          for (;;) {
+            if (u < T_) {
+              st = ld_acquire_u32(&F.tstat[u]);
+              valid = (st & ~7u) == ep && (st & 3u) != 0u;
+            } else {
+              valid = true;
+              st = ep | 2u;
+            }
+            const uint32_t inv = __ballot_sync(0xffffffffu, !valid);
+            const uint32_t inc = __ballot_sync(0xffffffffu, valid && (st & 3u) == 2u);
+            if (inv == 0u || (inc != 0u && (__ffs(inc) < __ffs(inv)))) break;
+            if (clock64() - t0 > kSpinBudget) { timed_out = true; break; }
+            __nanosleep(64);
+          }
+          if (timed_out) {
+            if (lane == 0) atomicExch(&ctl->error, COX_E_TIMEOUT);
+            break;
+          }
+          const uint32_t inc = __ballot_sync(0xffffffffu, valid && (st & 3u) == 2u);
+          const int stop = inc ? __ffs(inc) - 1 : 31;
+          double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+          if (lane <= stop && u < T_) {
+            const int o = (st & 3u) == 2u ? 3 : 0;
+            v0 = ld_relaxed_f64(&F.tval[6 * u + o + 0]);
+            v1 = ld_relaxed_f64(&F.tval[6 * u + o + 1]);
+            v2 = ld_relaxed_f64(&F.tval[6 * u + o + 2]);
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            v0 += __shfl_down_sync(0xffffffffu, v0, off);
+            v1 += __shfl_down_sync(0xffffffffu, v1, off);
+            v2 += __shfl_down_sync(0xffffffffu, v2, off);
+          }
+          c0 += __shfl_sync(0xffffffffu, v0, 0);
+          c1 += __shfl_sync(0xffffffffu, v1, 0);
+          c2 += __shfl_sync(0xffffffffu, v2, 0);
+          if (inc) break;
+          base += 32;
+        }
+      }
+      if (lane == 0) {
+        s_tile_carry[0] = c0; s_tile_carry[1] = c1; s_tile_carry[2] = c2;
+        if (!tf) {
+          F.tval[6 * t + 3] = s_tile_agg[0] + c0;
+          F.tval[6 * t + 4] = s_tile_agg[1] + c1;
+          F.tval[6 * t + 5] = s_tile_agg[2] + c2;
+          __threadfence();
+          st_release_u32(&F.tstat[t], ep | 2u);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- 5. tie-group ratios (eqs. parallel_g / parallel_h), head-parallel
+    const Acc C0 = P::from64(s_tile_carry[0]), C1 = P::from64(s_tile_carry[1]), C2 = P::from64(s_tile_carry[2]);
+    double r_g1 = 0.0, r_g2 = 0.0, r_ll = 0.0;
+    Acc q_g1 = P::zero(), q_g2 = P::zero();
+    for (int h = tid; h < nh; h += kThreads) {
+      const int g = ga + h;
+      const int pos = D->head_pos[g] - lo;
+      const int o = pos / ITEMS;
+      Acc s0 = hloc[3 * h + 0], s1 = hloc[3 * h + 1], s2 = hloc[3 * h + 2];
+      if (!hcut[h]) {
+        Acc k0 = tc[3 * o + 0], k1 = tc[3 * o + 1], k2 = tc[3 * o + 2];
+        if (!tflag[o]) { k0 = P::comb(k0, C0); k1 = P::comb(k1, C1); k2 = P::comb(k2, C2); }
+        s0 = P::comb(s0, k0); s1 = P::comb(s1, k1); s2 = P::comb(s2, k2);
+      }
+      const double dg = double(D->head_d[g]);
+      if constexpr (sizeof(T) == 8) {
+        const double S0 = P::to64(s0), S1 = P::to64(s1), S2 = P::to64(s2);
+        if (j >= 0) {
+          const double r = S1 / S0;
+          r_g1 += dg * r;
+          r_g2 += dg * (S2 / S0 - r * r);
+        }
+        if (need_ll) r_ll += dg * log(S0);
+        if (F.out_S0) { F.out_S0[g] = S0; F.out_S1[g] = S1; }
+      } else {
+        const float S0 = s0.s + s0.c, S1 = s1.s + s1.c, S2 = s2.s + s2.c;
+        const float fd = float(D->head_d[g]);
+        if (j >= 0) {
+          const float r = __fdiv_rn(S1, S0);
+          P::add(q_g1, fd * r);
+          P::add(q_g2, fd * (__fdiv_rn(S2, S0) - r * r));
+        }
+        if (need_ll) r_ll += dg * log(P::to64(s0));
+        if (F.out_S0) { F.out_S0[g] = P::to64(s0); F.out_S1[g] = P::to64(s1); }
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      r_g1 = P::to64(q_g1);
+      r_g2 = P::to64(q_g2);
+    }
+    double red[3] = {r_g1, r_g2, r_ll};
+    block_sum<3>(red, s_red);
+    if (tid == 0) {
+      F.part[3 * t + 0] = red[0]; F.part[3 * t + 1] = red[1]; F.part[3 * t + 2] = red[2];
+      __threadfence();
+      const uint32_t prev = atomicAdd(&ctl->done_tiles, 1u);
+      s_last = prev == uint32_t(T_ - 1);
+    }
+    __syncthreads();
+
+    // ---- 6. last CTA of this fit: fixed-order reduction and the coordinate step
+    if (s_last) {
+      __threadfence();
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int u = tid; u < T_; u += kThreads) {
+        acc[0] += ld_relaxed_f64(&F.part[3 * u + 0]);
+        acc[1] += ld_relaxed_f64(&F.part[3 * u + 1]);
+        acc[2] += ld_relaxed_f64(&F.part[3 * u + 2]);
+      }
+      block_sum<3>(acc, s_red);
+      double extra[2] = {0.0, 0.0};   // beta'dX and the penalty, when the log-likelihood is due
+      if (need_ll) {
+        for (int jj = tid; jj < D->p; jj += kThreads) {
+          const double b = F.beta[jj];
+          extra[0] += b * D->dX[jj];
+          const bool pen = F.penalize ? F.penalize[jj] != 0 : true;
+          if (pen && F.penalty == COX_PEN_L1) extra[1] += F.lambda * fabs(b);
+          if (pen && F.penalty == COX_PEN_L2) extra[1] += b * b / (2.0 * F.l2_var);
+        }
+        block_sum<2>(extra, s_red);
+      }
+      if (tid == 0) {
+        const double G1 = acc[0], G2 = acc[1], LL = acc[2];
+        if (ctl->error != 0) {
+          ctl->state = kError;
+        } else if (mode == kModeEval) {
+          ctl->out_g1 = -D->dX[j] + G1;
+          ctl->out_g2 = G2;
+          if (F.gout) { F.gout[2 * j] = -D->dX[j] + G1; F.gout[2 * j + 1] = G2; }
+        } else if (mode == kModeLL) {
+          ctl->out_ll = extra[0] - LL - shift * D->sum_d;
+        } else {
+          bool stop = false;
+          if (need_ll) {
+            const double ll = extra[0] - LL - shift * D->sum_d;
+            const double obj = -ll + extra[1];
+            ctl->loglik = ll;
+            ctl->obj = obj;
+            if (ctl->sweep > 0 && fabs(obj - ctl->obj_prev) <= F.tol * fabs(obj)) {
+              ctl->state = kConverged;
+              stop = true;
+            } else if (ctl->sweep >= F.max_sweeps) {
+              ctl->state = kMaxed;
+              stop = true;
+            } else {
+              ctl->obj_prev = obj;
+            }
+          }
+          if (!stop) {
+            const double g1 = -D->dX[j] + G1, g2 = G2;
+            const int pen = F.penalize ? F.penalize[j] != 0 : 1;
+            double tr = F.trust[j];
+            const double s = ccd_step_rule(g1, g2, F.beta[j], &tr, F.penalty, F.lambda, F.l2_var, pen);
+            F.trust[j] = tr;
+            if (s != 0.0) {
+              F.beta[j] = F.beta[j] + s;
+              ctl->pend_j = j;
+              ctl->pend_db = s;
+            } else {
+              ctl->pend_j = -1;
+              ctl->pend_db = 0.0;
+            }
+            ctl->coord_updates += 1;
+            int jn = j + 1;
+            if (jn >= D->p) {
+              jn = 0;
+              ctl->sweep += 1;
+              ctl->need_ll = 1;
+            } else {
+              ctl->need_ll = 0;
+            }
+            ctl->j = jn;
+          }
+        }
+        ctl->done_tiles = 0u;
+        ctl->epoch = epoch + 1u;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&lc->exited, 1u) == gridDim.x - 1) {
+      lc->ticket = 0u;
+      lc->exited = 0u;
+    }
+  }
+}
+
+// Apply one column step to eta and v over all of the column's nonzeros (warm starts and
+// coefficient vectors given to cox_loglik / cox_gradient), in column order.
+template <class P>
+__global__ void column_update_kernel(const DevFit *__restrict__ fit, int32_t j, double db, int64_t nnz_j) {
+  const DevFit &F = *fit;
+  const DevData *D = F.d;
+  const int64_t cb = D->col_ptr[j];
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < nnz_j; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = cb + k;
+    const uint32_t e = D->idx[q];
+    const int64_t pos = e & kPosMask;
+    const double x = D->val ? D->val[q] : 1.0;
+    const double et = __dadd_rn(F.eta[pos], __dmul_rn(x, db));
+    F.eta[pos] = et;
+    static_cast<typename P::T *>(F.v)[pos] = make_v<P>(et, F.shift, (e & kExitBit) != 0, &F.ctl->error);
+  }
+}
+
+// eta = 0 and v = +-exp(-shift) at every position (exits negative); padding stays 0.
+template <class P>
+__global__ void fill_v_kernel(const DevFit *__restrict__ fit, int64_t M, const uint32_t *__restrict__ exit_bits) {
+  const DevFit &F = *fit;
+  for (int64_t pos = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; pos < M; pos += int64_t(gridDim.x) * blockDim.x) {
+    const bool ex = exit_bits ? ((exit_bits[pos >> 5] >> (pos & 31)) & 1u) != 0u : false;
+    F.eta[pos] = 0.0;
+    static_cast<typename P::T *>(F.v)[pos] = make_v<P>(0.0, F.shift, ex, &F.ctl->error);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class P>
+static size_t smem_bytes(int valued) {
+  return valued ? Smem<P>::bytes_valued : Smem<P>::bytes_binary;
+}
+
+template <class P>
+static int max_grid_impl(int valued) {
+  static int cached[2] = {0, 0};
+  if (cached[valued]) return cached[valued];
+  // the attribute is a per-kernel maximum: always allow the larger (valued-X) layout, so a
+  // launch of either variant fits whichever was configured first
+  if (cudaFuncSetAttribute(ccd_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Smem<P>::bytes_valued)) !=
+      cudaSuccess)
+    return -1;
+  const size_t sm = smem_bytes<P>(valued);
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ccd_kernel<P>, kThreads, sm) != cudaSuccess) return -1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cached[valued] = (per_sm > 0 ? per_sm : 1) * nsm;
+  return cached[valued];
+}
+
+int ccd_max_grid(int precision, int valued) {
+  return precision == COX_FP32C ? max_grid_impl<PF32C>(valued) : max_grid_impl<PF64>(valued);
+}
+
+int ccd_tile(int precision) { return precision == COX_FP32C ? Smem<PF32C>::TILE : Smem<PF64>::TILE; }
+
+int launch_ccd(int precision, const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode, int j_eval,
+               int valued, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusNone) count_launches(1);   // graph nodes are counted per replay
+  if (precision == COX_FP32C) {
+    if (max_grid_impl<PF32C>(valued) < 0) return COX_E_CUDA;
+    ccd_kernel<PF32C><<<grid, kThreads, smem_bytes<PF32C>(valued), s>>>(fits, items, lc, mode, j_eval, valued);
+  } else {
+    if (max_grid_impl<PF64>(valued) < 0) return COX_E_CUDA;
+    ccd_kernel<PF64><<<grid, kThreads, smem_bytes<PF64>(valued), s>>>(fits, items, lc, mode, j_eval, valued);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream) {
+  if (nnz_j <= 0) return COX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  count_launches(1);
+  int blocks = int((nnz_j + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (precision == COX_FP32C) column_update_kernel<PF32C><<<blocks, 256, 0, s>>>(fit_dev, j, db, nnz_j);
+  else column_update_kernel<PF64><<<blocks, 256, 0, s>>>(fit_dev, j, db, nnz_j);
+  return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+int launch_fill_v(int precision, const DevFit *fit_dev, int64_t M, const uint32_t *exit_bits, void *stream) {
+  if (M <= 0) return COX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  count_launches(1);
+  int blocks = int((M + 255) / 256);
+  if (blocks > 8192) blocks = 8192;
+  if (precision == COX_FP32C) fill_v_kernel<PF32C><<<blocks, 256, 0, s>>>(fit_dev, M, exit_bits);
+  else fill_v_kernel<PF64><<<blocks, 256, 0, s>>>(fit_dev, M, exit_bits);
+  return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+}  // namespace coxgb

@@ -1,0 +1,104 @@
+// Internal layout of the Cox CCD library (not part of the ABI).
+//
+// The method (arXiv 2310.16238 §2.6-§2.7) turns every risk-set sum into a stratum-segmented
+// reverse scan. All model forms are mapped onto one "risk sequence" of M positions:
+//   * right-censored rows: position = row (rows sorted by stratum, then time), M = n_rows;
+//   * counting-process rows (start, stop]: every row appears twice in its stratum's
+//     sequence, ordered by time -- an entry at `stop` holding +exp(eta) and an exit at
+//     `start` holding -exp(eta) -- so the suffix sum from the first position with time >= t
+//     is exactly the at-risk sum at t (rows with stop >= t minus rows with start >= t),
+//     M = 2 n_rows.
+// A tie group g (a (stratum, time) with events) reads the suffix sum at its read position
+// head_pos[g]; strata are segments (a scan never crosses a stratum's last position).
+#pragma once
+#include <cstdint>
+
+namespace coxgb {
+
+constexpr int kThreads = 256;        // CTA size of the scan kernel
+constexpr int kHeadCap = 1024;       // max tie-group read positions per tile
+constexpr uint32_t kExitBit = 0x80000000u;
+constexpr uint32_t kPosMask = 0x7fffffffu;
+
+// Prepared, read-only data of one data set (shared by every fit on it).
+struct DevData {
+  int64_t M;              // risk-sequence length
+  int64_t n_rows;
+  int32_t p, T, G, K;     // columns, tiles, tie groups, strata
+  int32_t tile;           // nominal positions per tile
+  int32_t binary;         // 1: every stored x is 1
+  int32_t counting;       // 1: counting-process sequence (exit positions carry -exp)
+  double sum_d;           // total number of events (for the exp shift in the log-likelihood)
+  const int64_t *col_ptr; // [p+1] position-space CSC
+  const uint32_t *idx;    // [nnz_pos] position | kExitBit for exit positions
+  const double *val;      // [nnz_pos] or nullptr
+  const int32_t *col_tile;// [p*(T+1)] offset from col_ptr[j] of column j's first entry in tile t
+  const int32_t *tile_lo; // [T+1] first position of each tile, tile_lo[T] = M
+  const int32_t *head_pos;// [G] read positions, ascending
+  const int32_t *head_d;  // [G] events per tie group
+  const int32_t *tile_g;  // [T+1] first tie group of each tile
+  const int32_t *cut_pos; // [K] last position of each stratum, ascending
+  const int32_t *tile_k;  // [T+1] first stratum whose last position is in tile t
+  const double *dX;       // [p] delta' X_j
+  const uint32_t *exit_bits; // [ceil(M/32)] exit positions (counting process) or nullptr
+};
+
+// Mutable control block of one fit (written by the last CTA of each launch).
+struct FitCtl {
+  int32_t j;              // coordinate evaluated by the next launch
+  int32_t sweep;          // completed sweeps
+  int32_t state;          // kRunning / kConverged / kMaxed / kError
+  int32_t need_ll;        // next launch also evaluates the log-likelihood
+  int32_t pend_j;         // column of the update the next launch applies first (-1: none)
+  int32_t error;          // COX_E_* raised on the device (0: none)
+  double pend_db;         // its step
+  double obj_prev, obj, loglik;
+  uint32_t epoch;         // launch counter (tags look-back statuses)
+  uint32_t done_tiles;    // tiles finished in the current launch
+  int64_t coord_updates;
+  double out_g1, out_g2;  // EVAL mode result
+  double out_ll;          // LL mode result
+};
+
+enum : int32_t { kRunning = 0, kConverged = 1, kMaxed = 2, kError = 3 };
+
+// One fit: pointers into its data and state (read-only during a launch).
+struct DevFit {
+  const DevData *d;       // device copy of the data descriptor
+  FitCtl *ctl;
+  double *eta;            // [M] linear predictor per position
+  void *v;                // [M_pad] +-exp(eta - shift), double or float
+  double *beta;           // [p]
+  double *trust;          // [p]
+  const uint8_t *penalize;// [p] or nullptr
+  uint32_t *tstat;        // [T] look-back status words
+  double *tval;           // [T*6] published tile values: aggregate (0..2), inclusive (3..5)
+  double *part;           // [T*3] tile partials (G1, G2, LL)
+  double *out_S0, *out_S1;// [G] optional per-group sums (diagnostics)
+  double *gout;           // [2p] EVAL mode: g'(beta_j), g''(beta_j) per column
+  int32_t penalty, max_sweeps;
+  double lambda, l2_var, tol, shift;
+};
+
+// Persistent-launch ticket counter.
+struct LaunchCtl {
+  uint32_t ticket;
+  uint32_t exited;
+  int32_t n_items;
+  int32_t pad;
+};
+
+enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
+
+// Count of kernels launched by the library (every launcher adds to it).
+void count_launches(int64_t n);
+
+// Host-visible launchers (ccd.cu).
+int launch_ccd(int precision, const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode,
+               int j_eval, int valued, void *stream);
+int ccd_max_grid(int precision, int valued);
+int ccd_tile(int precision);
+int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream);
+int launch_fill_v(int precision, const DevFit *fit_dev, int64_t M, const uint32_t *exit_bits, void *stream);
+
+}  // namespace coxgb

@@ -1,0 +1,768 @@
+// Device-side preparation of a data set for the fused coordinate-step kernel
+// (arXiv 2310.16238 §2.7: time-ordered, stratum-concatenated rows with segment heads).
+//
+// Integer work only (plus delta'X in FP64), all on the device:
+//   * validation of the sort order and of the CSC,
+//   * strata (segments) and tie groups (a (stratum, time) with >= 1 event; Breslow),
+//   * delta'X_j, the first term of eq. (parallel_g),
+//   * for counting-process rows (start, stop] the merged risk sequence: per stratum the
+//     entries (at stop, +exp) and exits (at start, -exp) ordered by time, and the
+//     position-space CSC that lists both positions of every nonzero,
+//   * the tile plan and the per-(tile) / per-(column, tile) lookup tables.
+// Building blocks: a three-phase exclusive scan, flag compaction and a stable LSD radix
+// sort that splits on one key bit per pass (Blelloch's split primitive, "Vector Models for
+// Data-Parallel Computing", 1990).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cox.h"
+#include "cox_internal.h"
+#include "prep.h"
+
+namespace coxgb {
+
+// ------------------------------------------------------------------ allocation
+static cox_alloc_fn g_alloc = nullptr;
+static cox_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+void set_allocator(cox_alloc_fn a, cox_free_fn f, void *ctx) {
+  g_alloc = a;
+  g_free = f;
+  g_alloc_ctx = ctx;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void *dev_alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  if (g_alloc) return g_alloc(bytes, g_alloc_ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p, size_t bytes) {
+  if (!p) return;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  if (g_free) g_free(p, bytes, g_alloc_ctx);
+  else cudaFree(p);
+}
+
+void BufferSet::release() {
+  for (auto &b : bufs) dev_free(b.first, b.second);
+  bufs.clear();
+  bytes_total = 0;
+}
+
+void *BufferSet::get(size_t bytes) {
+  void *p = dev_alloc(bytes);
+  if (p) {
+    bufs.emplace_back(p, bytes);
+    bytes_total += (bytes + 255) & ~size_t(255);
+  }
+  return p;
+}
+
+// ------------------------------------------------------------------ scan / compaction
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+// exclusive block-level scan of per-thread counts (int64)
+__device__ int64_t block_excl_scan(int64_t v, int64_t *warp_tot, int64_t *block_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+    int64_t wi = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, wi, off);
+      if (lane >= off) wi += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) *block_total = wi;
+  }
+  __syncthreads();
+  int64_t r = warp_tot[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void scan_reduce_kernel(const int32_t *in, int64_t n, int64_t *bsum) {
+  __shared__ int64_t wt[32];
+  __shared__ int64_t tot;
+  const int64_t base = int64_t(blockIdx.x) * kScanBlock + int64_t(threadIdx.x) * kScanItems;
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += in[base + k];
+  block_excl_scan(s, wt, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void scan_bsums_kernel(int64_t *bsum, int64_t nb, int64_t *total) {
+  __shared__ int64_t wt[32];
+  __shared__ int64_t tot;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < nb ? bsum[i] : 0;
+    const int64_t ex = block_excl_scan(v, wt, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_final_kernel(const int32_t *in, int64_t n, const int64_t *boff, int64_t *out) {
+  __shared__ int64_t wt[32];
+  __shared__ int64_t tot;
+  const int64_t base = int64_t(blockIdx.x) * kScanBlock + int64_t(threadIdx.x) * kScanItems;
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += in[base + k];
+  int64_t ex = block_excl_scan(s, wt, &tot) + boff[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) {
+      out[base + k] = ex;
+      ex += in[base + k];
+    }
+}
+
+// out[i] = sum_{k<i} in[k]; returns the total (synchronizes the stream).
+static int exclusive_scan(const int32_t *in, int64_t n, int64_t *out, int64_t *total_host, Scratch &sc,
+                          cudaStream_t s) {
+  if (n <= 0) {
+    *total_host = 0;
+    return COX_OK;
+  }
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  int64_t *bsum = static_cast<int64_t *>(sc.get((nb + 1) * sizeof(int64_t)));
+  int64_t *tot = static_cast<int64_t *>(sc.get(sizeof(int64_t)));
+  if (!bsum || !tot) return COX_E_OOM;
+  count_launches(1);
+  scan_reduce_kernel<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, bsum);
+  count_launches(1);
+  scan_bsums_kernel<<<1, kScanThreads, 0, s>>>(bsum, nb, tot);
+  count_launches(1);
+  scan_final_kernel<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, bsum, out);
+  if (cudaMemcpyAsync(total_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return COX_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return COX_E_CUDA;
+  return COX_OK;
+}
+
+__global__ void compact_kernel(const int32_t *flag, const int64_t *pre, int64_t n, int32_t *out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    if (flag[i]) out[pre[i]] = int32_t(i);
+}
+
+static unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 65536) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return unsigned(g);
+}
+
+// ------------------------------------------------------------------ stable split radix sort
+__global__ void bit_flags_kernel(const uint64_t *key, int64_t n, int bit, int32_t *flag) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    flag[i] = int32_t((key[i] >> bit) & 1u);
+}
+
+__global__ void split_scatter_kernel(const uint64_t *key, const uint32_t *pay, const int32_t *flag, const int64_t *ones_before,
+                                     int64_t n, int64_t n_zero, uint64_t *key_out, uint32_t *pay_out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t dst = flag[i] ? n_zero + ones_before[i] : i - ones_before[i];
+    key_out[dst] = key[i];
+    pay_out[dst] = pay[i];
+  }
+}
+
+// Sorts (key, payload) by the listed key bits, least significant first; stable.
+static int radix_sort(uint64_t *&key, uint32_t *&pay, int64_t n, const std::vector<int> &bits, Scratch &sc,
+                      cudaStream_t s) {
+  if (n <= 1) return COX_OK;
+  uint64_t *k2 = static_cast<uint64_t *>(sc.get(n * sizeof(uint64_t)));
+  uint32_t *p2 = static_cast<uint32_t *>(sc.get(n * sizeof(uint32_t)));
+  int32_t *flag = static_cast<int32_t *>(sc.get(n * sizeof(int32_t)));
+  int64_t *pre = static_cast<int64_t *>(sc.get(n * sizeof(int64_t)));
+  if (!k2 || !p2 || !flag || !pre) return COX_E_OOM;
+  for (int b : bits) {
+    count_launches(1);
+    bit_flags_kernel<<<grid_for(n), 256, 0, s>>>(key, n, b, flag);
+    int64_t ones = 0;
+    int rc = exclusive_scan(flag, n, pre, &ones, sc, s);
+    if (rc) return rc;
+    count_launches(1);
+    split_scatter_kernel<<<grid_for(n), 256, 0, s>>>(key, pay, flag, pre, n, n - ones, k2, p2);
+    std::swap(key, k2);
+    std::swap(pay, p2);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+static int bits_needed(uint64_t maxval) {
+  int b = 0;
+  while (b < 64 && (maxval >> b) != 0) ++b;
+  return b;
+}
+
+// ------------------------------------------------------------------ validation
+enum : int32_t {
+  kErrEvent = 1, kErrStartStop = 2, kErrUnsorted = 4, kErrRowIdx = 8, kErrColOrder = 16, kErrColPtr = 32
+};
+
+__global__ void validate_rows_kernel(int64_t n, const int32_t *stop, const int32_t *start, const uint8_t *event,
+                                     const int32_t *stratum, int32_t *err) {
+  int32_t e = 0;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    if (event[r] > 1) e |= kErrEvent;
+    if (start && !(start[r] < stop[r])) e |= kErrStartStop;
+    if (r > 0) {
+      const int32_t k0 = stratum ? stratum[r - 1] : 0, k1 = stratum ? stratum[r] : 0;
+      if (k1 < k0 || (k1 == k0 && stop[r] < stop[r - 1])) e |= kErrUnsorted;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+// one warp per column
+__global__ void validate_cols_kernel(int32_t p, int64_t n, const int64_t *col_ptr, const int32_t *row_idx, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  int32_t e = 0;
+  for (int64_t j = gw; j < p; j += nw) {
+    const int64_t a = col_ptr[j], b = col_ptr[j + 1];
+    if (b < a) { e |= kErrColPtr; continue; }
+    for (int64_t q = a + lane; q < b; q += 32) {
+      const int32_t r = row_idx[q];
+      if (r < 0 || r >= n) e |= kErrRowIdx;
+      if (q > a && !(row_idx[q - 1] < r)) e |= kErrColOrder;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+// ------------------------------------------------------------------ metadata kernels
+__device__ __forceinline__ int32_t stratum_at(const int32_t *stratum, int64_t r) { return stratum ? stratum[r] : 0; }
+
+__global__ void row_flags_kernel(int64_t n, const int32_t *stop, const uint8_t *event, const int32_t *stratum,
+                                 int32_t *seg_start_flag, int32_t *event_flag) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    seg_start_flag[r] = (r == 0 || stratum_at(stratum, r) != stratum_at(stratum, r - 1)) ? 1 : 0;
+    event_flag[r] = event[r] ? 1 : 0;
+  }
+}
+
+// a new tie group starts at event row i when its (stratum, stop) differs from the previous event row
+__global__ void group_flags_kernel(int64_t E, const int32_t *ev_rows, const int32_t *stop, const int32_t *stratum,
+                                   int32_t *gflag) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < E; i += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t r = ev_rows[i];
+    bool f = i == 0;
+    if (!f) {
+      const int32_t q = ev_rows[i - 1];
+      f = stop[q] != stop[r] || stratum_at(stratum, q) != stratum_at(stratum, r);
+    }
+    gflag[i] = f ? 1 : 0;
+  }
+}
+
+// stratum index of every row: inclusive count of segment starts minus one
+__global__ void row_stratum_index_kernel(int64_t n, const int32_t *seg_start_flag, const int64_t *seg_pre, int32_t *kidx) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+    kidx[r] = int32_t(seg_pre[r] + seg_start_flag[r] - 1);
+}
+
+template <class V>
+__device__ __forceinline__ int64_t lower_bound_dev(const V *a, int64_t n, V x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if (a[m] < x) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+template <class V>
+__device__ __forceinline__ int64_t upper_bound_dev(const V *a, int64_t n, V x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if (!(x < a[m])) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+// per tie group: time, stratum, events and read position in the risk sequence
+__global__ void group_build_kernel(int64_t G, int64_t E, const int32_t *gstart, const int32_t *ev_rows,
+                                   const int32_t *stop, const int32_t *stratum, const int32_t *kidx,
+                                   const int32_t *seg_start /*K+1*/, const int32_t *sorted_start /*n or null*/,
+                                   int counting, int32_t *head_pos, int32_t *head_d, int32_t *g_time, int32_t *g_stratum,
+                                   int32_t *g_kidx) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < G; g += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i0 = gstart[g], i1 = g + 1 < G ? gstart[g + 1] : E;
+    const int32_t r = ev_rows[i0];
+    const int32_t t = stop[r];
+    const int32_t k = kidx[r];
+    const int64_t a = seg_start[k], nk = int64_t(seg_start[k + 1]) - a;
+    const int64_t n_entries_before = lower_bound_dev<int32_t>(stop + a, nk, t);
+    int64_t pos;
+    if (counting) pos = 2 * a + n_entries_before + lower_bound_dev<int32_t>(sorted_start + a, nk, t);
+    else pos = a + n_entries_before;
+    head_pos[g] = int32_t(pos);
+    head_d[g] = int32_t(i1 - i0);
+    g_time[g] = t;
+    g_stratum[g] = stratum_at(stratum, r);
+    g_kidx[g] = k;
+  }
+}
+
+__global__ void cut_build_kernel(int32_t K, const int32_t *seg_start, int counting, int32_t *cut_pos) {
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < K; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = seg_start[k + 1];
+    cut_pos[k] = int32_t(counting ? 2 * b - 1 : b - 1);
+  }
+}
+
+// delta'X_j: one warp per column, lanes in a fixed order, then a fixed shuffle tree
+__global__ void dx_kernel(int32_t p, const int64_t *col_ptr, const int32_t *row_idx, const double *val,
+                          const uint8_t *event, double *dX) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t j = gw; j < p; j += nw) {
+    double s = 0.0;
+    for (int64_t q = col_ptr[j] + lane; q < col_ptr[j + 1]; q += 32)
+      if (event[row_idx[q]]) s += val ? val[q] : 1.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) dX[j] = s;
+  }
+}
+
+// ---- counting-process sequence
+__global__ void start_keys_kernel(int64_t n, const int32_t *start, const int32_t *kidx, int32_t min_start, uint64_t *key,
+                                  uint32_t *pay) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    key[r] = (uint64_t(uint32_t(kidx[r])) << 32) | uint64_t(uint32_t(start[r] - min_start));
+    pay[r] = uint32_t(r);
+  }
+}
+
+__global__ void gather_start_kernel(int64_t n, const uint32_t *sidx, const int32_t *start, int32_t *sorted_start) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    sorted_start[i] = start[sidx[i]];
+}
+
+// entry position of row r and exit position of the row at start-order rank i
+__global__ void merge_positions_kernel(int64_t n, const int32_t *stop, const int32_t *start, const int32_t *kidx,
+                                       const int32_t *seg_start, const uint32_t *sidx, const int32_t *sorted_start,
+                                       int32_t *pos_entry, int32_t *pos_exit, uint32_t *exit_bits) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    // entry of row i: entries before it in its stratum + exits with start < stop_i
+    {
+      const int32_t k = kidx[i];
+      const int64_t a = seg_start[k], nk = int64_t(seg_start[k + 1]) - a;
+      pos_entry[i] = int32_t(2 * a + (i - a) + lower_bound_dev<int32_t>(sorted_start + a, nk, stop[i]));
+    }
+    // exit at start-order rank i: exits before it + entries with stop <= start (entries first on ties)
+    {
+      const uint32_t r = sidx[i];
+      const int32_t k = kidx[r];
+      const int64_t a = seg_start[k], nk = int64_t(seg_start[k + 1]) - a;
+      const int32_t pe = int32_t(2 * a + (i - a) + upper_bound_dev<int32_t>(stop + a, nk, start[r]));
+      pos_exit[r] = pe;
+      atomicOr(&exit_bits[pe >> 5], 1u << (pe & 31));
+    }
+  }
+}
+
+// two position-space entries per nonzero: key = (column << 32) | position
+__global__ void pos_csc_keys_kernel(int32_t p, const int64_t *col_ptr, const int32_t *row_idx, const int32_t *pos_entry,
+                                    const int32_t *pos_exit, uint64_t *key, uint32_t *pay) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t j = gw; j < p; j += nw)
+    for (int64_t q = col_ptr[j] + lane; q < col_ptr[j + 1]; q += 32) {
+      const int32_t r = row_idx[q];
+      key[2 * q] = (uint64_t(j) << 32) | uint64_t(uint32_t(pos_entry[r]));
+      pay[2 * q] = uint32_t(q) << 1;
+      key[2 * q + 1] = (uint64_t(j) << 32) | uint64_t(uint32_t(pos_exit[r]));
+      pay[2 * q + 1] = (uint32_t(q) << 1) | 1u;
+    }
+}
+
+__global__ void pos_csc_fill_kernel(int64_t nnz2, const uint64_t *key, const uint32_t *pay, const double *val_row,
+                                    uint32_t *idx, double *val) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nnz2; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t pos = uint32_t(key[i] & 0xffffffffu);
+    idx[i] = pos | ((pay[i] & 1u) ? kExitBit : 0u);
+    if (val) val[i] = val_row[pay[i] >> 1];
+  }
+}
+
+__global__ void double_ptr_kernel(int32_t p, const int64_t *col_ptr, int64_t *col_ptr2) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j <= p; j += int64_t(gridDim.x) * blockDim.x)
+    col_ptr2[j] = 2 * col_ptr[j];
+}
+
+// ---- tile tables
+__global__ void tile_tables_kernel(int32_t T, const int32_t *tile_lo, const int32_t *head_pos, int32_t G,
+                                   const int32_t *cut_pos, int32_t K, int32_t *tile_g, int32_t *tile_k) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t <= T; t += int64_t(gridDim.x) * blockDim.x) {
+    tile_g[t] = int32_t(lower_bound_dev<int32_t>(head_pos, G, tile_lo[t]));
+    tile_k[t] = int32_t(lower_bound_dev<int32_t>(cut_pos, K, tile_lo[t]));
+  }
+}
+
+__device__ __forceinline__ int64_t lower_bound_pos(const uint32_t *idx, int64_t n, uint32_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if ((idx[m] & kPosMask) < x) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+__global__ void col_tile_kernel(int32_t p, int32_t T, const int64_t *col_ptr, const uint32_t *idx, const int32_t *tile_lo,
+                                int32_t *col_tile) {
+  const int64_t total = int64_t(p) * (T + 1);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t j = i / (T + 1), t = i % (T + 1);
+    const int64_t a = col_ptr[j], b = col_ptr[j + 1];
+    col_tile[i] = int32_t(lower_bound_pos(idx + a, b - a, uint32_t(tile_lo[t])));
+  }
+}
+
+// ------------------------------------------------------------------ host orchestration
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool pointer_on_device(const void *p) { return is_device_ptr(p); }
+
+// Make a device-resident view of an input array (copy host arrays into scratch).
+template <class V>
+static const V *device_view(const V *p, int64_t count, Scratch &sc, cudaStream_t s, int *rc) {
+  if (!p || count <= 0) return p;
+  if (is_device_ptr(p)) return p;
+  V *d = static_cast<V *>(sc.get(count * sizeof(V)));
+  if (!d) { *rc = COX_E_OOM; return nullptr; }
+  if (cudaMemcpyAsync(d, p, count * sizeof(V), cudaMemcpyHostToDevice, s) != cudaSuccess) { *rc = COX_E_CUDA; return nullptr; }
+  return d;
+}
+
+// Greedy tile plan: tiles of `tile` positions, shortened when they would hold more than
+// kHeadCap tie-group read positions. Boundaries are multiples of 32.
+static std::vector<int32_t> plan_tiles(int64_t M, int tile, const std::vector<int32_t> &head_pos) {
+  std::vector<int32_t> lo;
+  int64_t cur = 0;
+  size_t h = 0;
+  while (cur < M) {
+    lo.push_back(int32_t(cur));
+    int64_t hi = std::min<int64_t>(cur + tile, M);
+    while (h < head_pos.size() && head_pos[h] < cur) ++h;
+    if (h + kHeadCap < head_pos.size() && head_pos[h + kHeadCap] < hi) {
+      int64_t cut = (int64_t(head_pos[h + kHeadCap]) / 32) * 32;
+      if (cut > cur) hi = cut;
+    }
+    cur = hi;
+  }
+  lo.push_back(int32_t(M));
+  return lo;
+}
+
+int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err) {
+  Scratch sc;   // temporaries, freed on return
+  const int64_t n = in->n_rows;
+  const int32_t p = in->p;
+  if (n < 0 || p < 0 || !in->stop || !in->event || !in->col_ptr || (n > 0 && p > 0 && !in->row_idx)) {
+    *err = "cox_create: null or negative argument";
+    return COX_E_INVALID;
+  }
+  if (n >= (int64_t(1) << 30)) {
+    *err = "cox_create: n_rows must be < 2^30";
+    return COX_E_INVALID;
+  }
+  const int counting = in->start != nullptr;
+  const int kernel_tile = ccd_tile(precision);
+  int tile = tile_req > 0 ? tile_req : kernel_tile;
+  if (tile % 32 != 0 || tile > kernel_tile || tile < 1024) {
+    *err = "cox_create: tile must be a multiple of 32 in [1024, " + std::to_string(kernel_tile) + "]";
+    return COX_E_INVALID;
+  }
+  // column pointers (host copy for nnz and launch sizes)
+  std::vector<int64_t> h_col_ptr(size_t(p) + 1);
+  if (cudaMemcpy(h_col_ptr.data(), in->col_ptr, (size_t(p) + 1) * sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess) {
+    *err = "cox_create: cannot read col_ptr";
+    return COX_E_CUDA;
+  }
+  const int64_t nnz = h_col_ptr[p];
+  if (h_col_ptr[0] != 0 || nnz < 0) {
+    *err = "cox_create: col_ptr[0] must be 0 and col_ptr[p] >= 0";
+    return COX_E_INVALID;
+  }
+  for (int32_t j = 0; j < p; ++j)
+    if (h_col_ptr[j + 1] < h_col_ptr[j]) {
+      *err = "cox_create: col_ptr must be nondecreasing";
+      return COX_E_INVALID;
+    }
+  int rc = COX_OK;
+  const int32_t *stop = device_view(in->stop, n, sc, s, &rc);
+  const int32_t *start = device_view(in->start, n, sc, s, &rc);
+  const uint8_t *event = device_view(in->event, n, sc, s, &rc);
+  const int32_t *stratum = device_view(in->stratum, n, sc, s, &rc);
+  const int32_t *row_idx = device_view(in->row_idx, nnz, sc, s, &rc);
+  const double *val = device_view(in->val, nnz, sc, s, &rc);
+  const int64_t *col_ptr_in = device_view(in->col_ptr, int64_t(p) + 1, sc, s, &rc);
+  if (rc) {
+    *err = "cox_create: staging inputs failed";
+    return rc;
+  }
+  int32_t *d_err = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
+  if (!d_err) return COX_E_OOM;
+  cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
+  if (n > 0) { count_launches(1); validate_rows_kernel<<<grid_for(n), 256, 0, s>>>(n, stop, start, event, stratum, d_err); }
+  if (p > 0) { count_launches(1); validate_cols_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, n, col_ptr_in, row_idx, d_err); }
+  int32_t h_err = 0;
+  cudaMemcpyAsync(&h_err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    *err = "cox_create: validation kernels failed";
+    return COX_E_CUDA;
+  }
+  if (h_err & kErrUnsorted) { *err = "cox_create: rows are not sorted by (stratum, stop)"; return COX_E_UNSORTED; }
+  if (h_err & kErrEvent) { *err = "cox_create: event must be 0 or 1"; return COX_E_INVALID; }
+  if (h_err & kErrStartStop) { *err = "cox_create: start must be < stop"; return COX_E_INVALID; }
+  if (h_err & kErrRowIdx) { *err = "cox_create: row_idx out of range"; return COX_E_INVALID; }
+  if (h_err & kErrColOrder) { *err = "cox_create: row_idx must be strictly ascending within a column"; return COX_E_INVALID; }
+  if (h_err & kErrColPtr) { *err = "cox_create: col_ptr must be nondecreasing"; return COX_E_INVALID; }
+
+  BufferSet &B = out->bufs;
+  DevData &D = out->desc;
+  D = DevData{};
+  D.n_rows = n;
+  D.p = p;
+  D.counting = counting;
+  D.binary = in->val == nullptr;
+  D.M = counting ? 2 * n : n;
+  D.tile = tile;
+  out->nnz_rows = nnz;
+  out->h_col_ptr_rows = h_col_ptr;
+
+  // ---- strata and tie groups
+  const int64_t nn = n > 0 ? n : 1;
+  int32_t *seg_flag = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int32_t *ev_flag = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int64_t *seg_pre = static_cast<int64_t *>(sc.get(nn * sizeof(int64_t)));
+  int64_t *ev_pre = static_cast<int64_t *>(sc.get(nn * sizeof(int64_t)));
+  if (!seg_flag || !ev_flag || !seg_pre || !ev_pre) return COX_E_OOM;
+  int64_t K = 0, E = 0;
+  if (n > 0) {
+    count_launches(1);
+    row_flags_kernel<<<grid_for(n), 256, 0, s>>>(n, stop, event, stratum, seg_flag, ev_flag);
+    if ((rc = exclusive_scan(seg_flag, n, seg_pre, &K, sc, s))) return rc;
+    if ((rc = exclusive_scan(ev_flag, n, ev_pre, &E, sc, s))) return rc;
+  }
+  D.K = int32_t(K);
+  D.sum_d = double(E);
+  int32_t *seg_start = static_cast<int32_t *>(B.get((K + 1) * sizeof(int32_t)));
+  int32_t *kidx = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int32_t *ev_rows = static_cast<int32_t *>(sc.get((E > 0 ? E : 1) * sizeof(int32_t)));
+  if (!seg_start || !kidx || !ev_rows) return COX_E_OOM;
+  if (n > 0) {
+    count_launches(1);
+    compact_kernel<<<grid_for(n), 256, 0, s>>>(seg_flag, seg_pre, n, seg_start);
+    count_launches(1);
+    compact_kernel<<<grid_for(n), 256, 0, s>>>(ev_flag, ev_pre, n, ev_rows);
+    count_launches(1);
+    row_stratum_index_kernel<<<grid_for(n), 256, 0, s>>>(n, seg_flag, seg_pre, kidx);
+  }
+  {
+    const int32_t nv = int32_t(n);
+    cudaMemcpyAsync(seg_start + K, &nv, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);   // nv lives on this stack frame
+  }
+  out->strata_start = seg_start;
+
+  // counting process: start order within strata
+  const int32_t *sorted_start = nullptr;
+  uint32_t *sidx = nullptr;
+  if (counting && n > 0) {
+    std::vector<int32_t> hs(static_cast<size_t>(n));
+    // min start for the key offset (host reduction over a copy; small relative to the fit)
+    if (cudaMemcpyAsync(hs.data(), start, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return COX_E_CUDA;
+    int32_t mn = *std::min_element(hs.begin(), hs.end()), mx = *std::max_element(hs.begin(), hs.end());
+    uint64_t *key = static_cast<uint64_t *>(sc.get(n * sizeof(uint64_t)));
+    uint32_t *pay = static_cast<uint32_t *>(sc.get(n * sizeof(uint32_t)));
+    if (!key || !pay) return COX_E_OOM;
+    count_launches(1);
+    start_keys_kernel<<<grid_for(n), 256, 0, s>>>(n, start, kidx, mn, key, pay);
+    std::vector<int> bits;
+    const int lob = bits_needed(uint64_t(uint32_t(mx - mn))), hib = bits_needed(uint64_t(K > 0 ? K - 1 : 0));
+    for (int b = 0; b < lob; ++b) bits.push_back(b);
+    for (int b = 0; b < hib; ++b) bits.push_back(32 + b);
+    if ((rc = radix_sort(key, pay, n, bits, sc, s))) return rc;
+    sidx = pay;
+    int32_t *ss = static_cast<int32_t *>(sc.get(n * sizeof(int32_t)));
+    if (!ss) return COX_E_OOM;
+    count_launches(1);
+    gather_start_kernel<<<grid_for(n), 256, 0, s>>>(n, sidx, start, ss);
+    sorted_start = ss;
+  }
+
+  // tie groups
+  int32_t *gflag = static_cast<int32_t *>(sc.get((E > 0 ? E : 1) * sizeof(int32_t)));
+  int64_t *gpre = static_cast<int64_t *>(sc.get((E > 0 ? E : 1) * sizeof(int64_t)));
+  if (!gflag || !gpre) return COX_E_OOM;
+  int64_t G = 0;
+  if (E > 0) {
+    count_launches(1);
+    group_flags_kernel<<<grid_for(E), 256, 0, s>>>(E, ev_rows, stop, stratum, gflag);
+    if ((rc = exclusive_scan(gflag, E, gpre, &G, sc, s))) return rc;
+  }
+  D.G = int32_t(G);
+  const int64_t Gs = G > 0 ? G : 1;
+  int32_t *gstart = static_cast<int32_t *>(sc.get(Gs * sizeof(int32_t)));
+  int32_t *head_pos = static_cast<int32_t *>(B.get(Gs * sizeof(int32_t)));
+  int32_t *head_d = static_cast<int32_t *>(B.get(Gs * sizeof(int32_t)));
+  int32_t *g_time = static_cast<int32_t *>(B.get(Gs * sizeof(int32_t)));
+  int32_t *g_stratum = static_cast<int32_t *>(B.get(Gs * sizeof(int32_t)));
+  int32_t *g_kidx = static_cast<int32_t *>(sc.get(Gs * sizeof(int32_t)));
+  if (!gstart || !head_pos || !head_d || !g_time || !g_stratum || !g_kidx) return COX_E_OOM;
+  if (G > 0) {
+    count_launches(1);
+    compact_kernel<<<grid_for(E), 256, 0, s>>>(gflag, gpre, E, gstart);
+    count_launches(1);
+    group_build_kernel<<<grid_for(G), 256, 0, s>>>(G, E, gstart, ev_rows, stop, stratum, kidx, seg_start, sorted_start,
+                                                    counting, head_pos, head_d, g_time, g_stratum, g_kidx);
+  }
+  D.head_pos = head_pos;
+  D.head_d = head_d;
+  out->g_time = g_time;
+  out->g_stratum = g_stratum;
+  int32_t *cut_pos = static_cast<int32_t *>(B.get((K > 0 ? K : 1) * sizeof(int32_t)));
+  if (!cut_pos) return COX_E_OOM;
+  if (K > 0) { count_launches(1); cut_build_kernel<<<grid_for(K), 256, 0, s>>>(int32_t(K), seg_start, counting, cut_pos); }
+  D.cut_pos = cut_pos;
+
+  // delta'X
+  double *dX = static_cast<double *>(B.get((p > 0 ? p : 1) * sizeof(double)));
+  if (!dX) return COX_E_OOM;
+  if (p > 0) { count_launches(1); dx_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr_in, row_idx, val, event, dX); }
+  D.dX = dX;
+
+  // ---- the position-space CSC
+  const int64_t nnz_pos = counting ? 2 * nnz : nnz;
+  int64_t *col_ptr = static_cast<int64_t *>(B.get((int64_t(p) + 1) * sizeof(int64_t)));
+  uint32_t *idx = static_cast<uint32_t *>(B.get((nnz_pos > 0 ? nnz_pos : 1) * sizeof(uint32_t)));
+  double *vpos = nullptr;
+  if (in->val) vpos = static_cast<double *>(B.get((nnz_pos > 0 ? nnz_pos : 1) * sizeof(double)));
+  if (!col_ptr || !idx || (in->val && !vpos)) return COX_E_OOM;
+  uint32_t *exit_bits = nullptr;
+  if (!counting) {
+    cudaMemcpyAsync(col_ptr, col_ptr_in, (int64_t(p) + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    if (nnz > 0) cudaMemcpyAsync(idx, row_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (vpos && nnz > 0) cudaMemcpyAsync(vpos, val, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  } else {
+    const int64_t M = D.M;
+    exit_bits = static_cast<uint32_t *>(B.get(((M + 31) / 32 + 1) * sizeof(uint32_t)));
+    int32_t *pos_entry = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+    int32_t *pos_exit = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+    if (!exit_bits || !pos_entry || !pos_exit) return COX_E_OOM;
+    cudaMemsetAsync(exit_bits, 0, ((M + 31) / 32 + 1) * sizeof(uint32_t), s);
+    if (n > 0)
+      count_launches(1);
+      merge_positions_kernel<<<grid_for(n), 256, 0, s>>>(n, stop, start, kidx, seg_start, sidx, sorted_start, pos_entry,
+                                                         pos_exit, exit_bits);
+    count_launches(1);
+    double_ptr_kernel<<<grid_for(int64_t(p) + 1), 256, 0, s>>>(p, col_ptr_in, col_ptr);
+    if (nnz > 0) {
+      uint64_t *key = static_cast<uint64_t *>(sc.get(nnz_pos * sizeof(uint64_t)));
+      uint32_t *pay = static_cast<uint32_t *>(sc.get(nnz_pos * sizeof(uint32_t)));
+      if (!key || !pay) return COX_E_OOM;
+      count_launches(1);
+      pos_csc_keys_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr_in, row_idx, pos_entry, pos_exit, key, pay);
+      std::vector<int> bits;
+      const int pb = bits_needed(uint64_t(M > 0 ? M - 1 : 0)), jb = bits_needed(uint64_t(p > 0 ? p - 1 : 0));
+      for (int b = 0; b < pb; ++b) bits.push_back(b);
+      for (int b = 0; b < jb; ++b) bits.push_back(32 + b);
+      if ((rc = radix_sort(key, pay, nnz_pos, bits, sc, s))) return rc;
+      count_launches(1);
+      pos_csc_fill_kernel<<<grid_for(nnz_pos), 256, 0, s>>>(nnz_pos, key, pay, val, idx, vpos);
+    }
+  }
+  D.col_ptr = col_ptr;
+  D.idx = idx;
+  D.val = vpos;
+  D.exit_bits = exit_bits;
+  out->h_col_ptr.resize(size_t(p) + 1);
+  for (int32_t j = 0; j <= p; ++j) out->h_col_ptr[j] = counting ? 2 * h_col_ptr[j] : h_col_ptr[j];
+
+  // ---- tile plan and tables
+  std::vector<int32_t> h_head(static_cast<size_t>(G));
+  if (G > 0 && cudaMemcpyAsync(h_head.data(), head_pos, G * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return COX_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    *err = "cox_create: preparation kernels failed";
+    return COX_E_CUDA;
+  }
+  std::vector<int32_t> h_lo = plan_tiles(D.M, tile, h_head);
+  const int32_t T = int32_t(h_lo.size()) - 1;
+  D.T = T;
+  int32_t *tile_lo = static_cast<int32_t *>(B.get((T + 1) * sizeof(int32_t)));
+  int32_t *tile_g = static_cast<int32_t *>(B.get((T + 1) * sizeof(int32_t)));
+  int32_t *tile_k = static_cast<int32_t *>(B.get((T + 1) * sizeof(int32_t)));
+  int32_t *col_tile = static_cast<int32_t *>(B.get((int64_t(p) * (T + 1) > 0 ? int64_t(p) * (T + 1) : 1) * sizeof(int32_t)));
+  if (!tile_lo || !tile_g || !tile_k || !col_tile) return COX_E_OOM;
+  cudaMemcpyAsync(tile_lo, h_lo.data(), (T + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  count_launches(1);
+  tile_tables_kernel<<<grid_for(int64_t(T) + 1), 256, 0, s>>>(T, tile_lo, head_pos, int32_t(G), cut_pos, int32_t(K), tile_g,
+                                                              tile_k);
+  if (p > 0) { count_launches(1); col_tile_kernel<<<grid_for(int64_t(p) * (T + 1)), 256, 0, s>>>(p, T, col_ptr, idx, tile_lo, col_tile); }
+  D.tile_lo = tile_lo;
+  D.tile_g = tile_g;
+  D.tile_k = tile_k;
+  D.col_tile = col_tile;
+  out->h_tile_lo = h_lo;
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    *err = "cox_create: table kernels failed";
+    return COX_E_CUDA;
+  }
+  return COX_OK;
+}
+
+}  // namespace coxgb

@@ -1,0 +1,49 @@
+// Host-side declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "cox.h"
+#include "cox_internal.h"
+
+namespace coxgb {
+
+void set_allocator(cox_alloc_fn a, cox_free_fn f, void *ctx);
+void *dev_alloc(size_t bytes);
+void dev_free(void *p, size_t bytes);
+bool pointer_on_device(const void *p);
+int64_t launch_count();
+
+// Owns device buffers; releases them on destruction.
+struct BufferSet {
+  std::vector<std::pair<void *, size_t>> bufs;
+  size_t bytes_total = 0;
+  BufferSet() = default;
+  BufferSet(const BufferSet &) = delete;
+  BufferSet &operator=(const BufferSet &) = delete;
+  ~BufferSet() { release(); }
+  void *get(size_t bytes);
+  void release();
+};
+using Scratch = BufferSet;
+
+// A prepared data set: device descriptor plus the host copies the launcher needs.
+struct Prepared {
+  BufferSet bufs;
+  DevData desc{};
+  int64_t nnz_rows = 0;
+  std::vector<int64_t> h_col_ptr_rows;  // row-space CSC pointers
+  std::vector<int64_t> h_col_ptr;       // position-space CSC pointers
+  std::vector<int32_t> h_tile_lo;
+  int32_t *strata_start = nullptr;      // [K+1] device
+  int32_t *g_time = nullptr;            // [G] device
+  int32_t *g_stratum = nullptr;         // [G] device
+};
+
+int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err);
+
+}  // namespace coxgb

@@ -298,3 +298,112 @@ def subset_rows(data: CoxData, rows: np.ndarray) -> CoxData:
                     None if data.stratum is None else data.stratum[rows],
                     None if data.start is None else data.start[rows],
                     cols_rows, cols_vals, data.p, data.beta_true, data.recipe + "/subset")
+
+
+def _subset_shared(col_ptr, row_idx, rows, n_total):
+    """Columns of a shared binary CSC restricted to ``rows`` (original ids), as per-column lists
+    of positions within ``rows``."""
+    remap = np.full(n_total, -1, dtype=np.int64)
+    remap[rows] = np.arange(len(rows))
+    r = remap[row_idx]
+    keep = r >= 0
+    cnt = np.add.reduceat(keep.astype(np.int64), col_ptr[:-1]) if len(row_idx) else np.zeros(len(col_ptr) - 1, np.int64)
+    cnt[np.diff(col_ptr) == 0] = 0
+    kept = r[keep]
+    out, o = [], 0
+    for c in cnt:
+        out.append(kept[o:o + c])
+        o += c
+    return out
+
+
+def batch_views(n_total: int = 1_000_000, p: int = 1000, density: float = 1e-2, n_outcomes: int = 4,
+                n_folds: int = 4, n_lambdas: int = 16, n_lo: float = 1e4, n_hi: float = 1e6,
+                max_strata: int = 50, event_frac: float = 0.05, seed: int = SEED_BASE + 4):
+    """Many uneven fits over one shared sparse X (cross-validation folds x penalty grid x outcomes).
+
+    One binary X of ``n_total`` rows x ``p`` columns (density ``density``). Each outcome draws
+    its own Weibull(1.5) event times (20 nonzero coefficients ~ N(0, 0.3^2), administrative
+    censoring at 3650 days, ~``event_frac`` events). For every (outcome, fold) pair a training
+    set of N ~ logU[n_lo, n_hi] rows is sampled from X, with K ~ U{1..max_strata} strata; each
+    training set is fitted at ``n_lambdas`` L1 weights log-spaced over [1e-4, 1e-1] * N.
+    Returns a list of (CoxData, [CoxOptions per lambda]) -- one entry per training set.
+    """
+    rng = np.random.default_rng(seed)
+    cols = [np.sort(rng.choice(n_total, size=int(rng.binomial(n_total, density)), replace=False)) for _ in range(p)]
+    col_ptr = np.zeros(p + 1, np.int64)
+    np.cumsum([len(c) for c in cols], out=col_ptr[1:])
+    row_idx = np.concatenate(cols).astype(np.int64)
+    sets = []
+    for o in range(n_outcomes):
+        beta = np.zeros(p)
+        sup = rng.choice(p, 20, replace=False)
+        beta[sup] = rng.normal(0, 0.3, 20)
+        eta = np.zeros(n_total)
+        for j in sup:
+            eta[cols[j]] += beta[j]
+        base = -np.log(rng.random(n_total)) / np.exp(eta)
+        h = _bisect(lambda hh: float(np.mean((base / hh) ** (1 / 1.5) <= 3650)), 1e-12, 1e3, event_frac)
+        t = (base / h) ** (1 / 1.5)
+        ev = (t <= 3650).astype(np.uint8)
+        y = np.maximum(np.ceil(np.minimum(t, 3650)), 1).astype(np.int64)
+        for f in range(n_folds):
+            n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+            rows = np.sort(rng.choice(n_total, size=n, replace=False))
+            k = int(rng.integers(1, max_strata + 1))
+            stratum = rng.integers(0, k, n)
+            sub = _subset_shared(col_ptr, row_idx, rows, n_total)
+            data = finalize(y[rows], ev[rows], stratum, None, sub, None, p, beta, f"batch_view o{o} f{f}")
+            lams = np.exp(np.linspace(math.log(1e-4), math.log(1e-1), n_lambdas)) * n
+            sets.append((data, [CoxOptions(penalty=PEN_L1, lam=float(l), tol=1e-8) for l in lams]))
+    return sets
+
+
+@dataclasses.dataclass
+class Request:
+    """One fit request of the serving stream."""
+    arrival_s: float
+    n_subj: int
+    p: int
+    density: float
+    k: int
+    counting: bool
+    penalty: int
+    seed: int
+
+
+def serving_stream(rate: float = 20.0, duration_s: float = 120.0, n_lo: float = 1e4, n_hi: float = 1e7,
+                   p_lo: float = 100, p_hi: float = 2e4, d_lo: float = 1e-4, d_hi: float = 1e-2,
+                   k_max: int = 200, seed: int = SEED_BASE + 5):
+    """Poisson request arrivals (mean ``rate`` per second over ``duration_s``). Each request
+    draws rows ~ logU[n_lo, n_hi], p ~ logU[p_lo, p_hi], density ~ logU[d_lo, d_hi],
+    K ~ U{1..k_max}, counting-process rows with probability 1/2 and L1 or L2 with probability
+    1/2 each, plus its own data seed. ``request_data`` materializes a request."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration_s:
+            break
+        lu = lambda a, b: math.exp(rng.uniform(math.log(a), math.log(b)))
+        out.append(Request(t, int(lu(n_lo, n_hi)), int(lu(p_lo, p_hi)), lu(d_lo, d_hi), int(rng.integers(1, k_max + 1)),
+                           bool(rng.random() < 0.5), PEN_L1 if rng.random() < 0.5 else PEN_L2,
+                           int(rng.integers(0, 2**31 - 1))))
+    return out
+
+
+def request_data(req: Request, max_rows: Optional[int] = None):
+    """Data and options of one serving request (counting-process requests use ``time_varying``
+    with n_subj / 3 subjects so that the row count is comparable)."""
+    n = req.n_subj if max_rows is None else min(req.n_subj, max_rows)
+    if req.counting:
+        data, opts = time_varying(n_subj=max(10, n // 3), p=req.p, k=req.k, density=req.density,
+                                  n_support=min(20, req.p), seed=req.seed)
+    else:
+        data, opts = stratified_sparse(n=n, p=req.p, k=min(req.k, n), n_support=min(20, req.p),
+                                       dens_lo=req.density, dens_hi=req.density * 1.0001, seed=req.seed)
+    if req.penalty == PEN_L1:
+        opts = CoxOptions(penalty=PEN_L1, lam=1e-4 * data.n, tol=1e-8)
+    else:
+        opts = CoxOptions(penalty=PEN_L2, l2_var=1.0, tol=1e-8)
+    return data, opts

@@ -188,6 +188,16 @@ int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
  * every kernel node). For measurement; never decreases. */
 int64_t cox_launch_count(void);
 
+/* ---------------------------------------------------------------- primitives
+ * Segmented inclusive scan with the flag-value operator of §2.6 ("Efficient parallel
+ * segmented-scan on GPUs"): out[i] = sum of a[k] for k from the last index h <= i with
+ * head_flags[h] != 0 (or from 0) up to i. a, head_flags, out: device arrays of n elements
+ * (out may alias a). Runs on `stream` (cudaStream_t, NULL = default) and returns after it
+ * completed. Scratch for the single-pass look-back (about 20 bytes per 4096 elements) is
+ * taken from the library allocator for the duration of the call.
+ * Errors: COX_E_INVALID (null/host pointers, n < 0), COX_E_OOM, COX_E_CUDA, COX_E_TIMEOUT. */
+int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

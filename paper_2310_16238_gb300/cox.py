@@ -25,7 +25,7 @@ COX_FP64, COX_FP32C = 0, 1
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
-           "cox_clone", "cox_footprint", "cox_launch_count"]
+           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan"]
 
 
 class CoxError(RuntimeError):
@@ -91,6 +91,7 @@ def lib():
             L.cox_footprint.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_size_t)]
             L.cox_launch_count.argtypes = []
             L.cox_launch_count.restype = i64
+            L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
             _lib = L
             _install_torch_allocator(L)
     return _lib
@@ -285,6 +286,15 @@ _P_CACHE = {}
 
 def cox_launch_count() -> int:
     return int(lib().cox_launch_count())
+
+
+def cox_segscan(a, head_flags, out=None, stream=None):
+    """Segmented inclusive scan (§2.6) of torch CUDA tensors a (float64) and head_flags (uint8)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(a)
+    _check(lib().cox_segscan(a.data_ptr(), head_flags.data_ptr(), int(a.numel()), out.data_ptr(), stream))
+    return out
 
 
 def _num_cols(h):

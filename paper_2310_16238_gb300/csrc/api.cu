@@ -38,6 +38,11 @@ void release_shared(SharedData *s) {
 
 }  // namespace
 
+int coxgb::set_last_error(int code, const char *msg) {
+  t_last_error = msg ? msg : "error";
+  return code;
+}
+
 struct cox_handle {
   SharedData *sd = nullptr;
   cox_options opts{};

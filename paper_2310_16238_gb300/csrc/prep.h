@@ -17,6 +17,8 @@ void *dev_alloc(size_t bytes);
 void dev_free(void *p, size_t bytes);
 bool pointer_on_device(const void *p);
 int64_t launch_count();
+// Record `msg` as the calling thread's last error and return `code` (api.cu).
+int set_last_error(int code, const char *msg);
 
 // Owns device buffers; releases them on destruction.
 struct BufferSet {

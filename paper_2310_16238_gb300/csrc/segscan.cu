@@ -1,0 +1,225 @@
+// Segmented inclusive scan with the paper's flag-value operator (arXiv 2310.16238 §2.6):
+//   (f_i, a_i) (+)s (f_j, a_j) = (f_i | f_j, f_j ? a_j : a_i + a_j),
+// i.e. b_i = sum of a over [last head at or before i, i]. One pass over the data: each CTA
+// scans a tile of 4096 values in registers (16 consecutive values per thread), combines
+// threads with a warp-shuffle segmented scan, and takes its carry from earlier tiles by a
+// decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
+// Look-back", 2016) over per-tile status words kept in scratch memory.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "cox.h"
+#include "cox_internal.h"
+#include "prep.h"
+
+namespace coxgb {
+
+constexpr int kSegThreads = 256;
+constexpr int kSegItems = 16;
+constexpr int kSegTile = kSegThreads * kSegItems;
+constexpr long long kSegSpin = 4000000000LL;
+
+// Scratch layout (bytes): [0] ticket, [4] exited, [8] error, [16 .. 16+4T) status,
+// then aggregates (8T) and inclusive values (8T), 8-byte aligned.
+struct SegScratchView {
+  uint32_t *ticket, *exited, *error, *status;
+  double *agg, *incl;
+};
+
+__host__ __device__ inline size_t seg_scratch_bytes(int64_t tiles) {
+  const size_t st = (16 + 4 * size_t(tiles) + 7) & ~size_t(7);
+  return st + 16 * size_t(tiles);
+}
+
+__device__ inline SegScratchView seg_view(unsigned char *s, int64_t tiles) {
+  SegScratchView v;
+  v.ticket = reinterpret_cast<uint32_t *>(s);
+  v.exited = reinterpret_cast<uint32_t *>(s + 4);
+  v.error = reinterpret_cast<uint32_t *>(s + 8);
+  v.status = reinterpret_cast<uint32_t *>(s + 16);
+  const size_t st = (16 + 4 * size_t(tiles) + 7) & ~size_t(7);
+  v.agg = reinterpret_cast<double *>(s + st);
+  v.incl = v.agg + tiles;
+  return v;
+}
+
+__device__ __forceinline__ void seg_st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t seg_ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double seg_ld_relaxed(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// status word: bit 0 aggregate published, bit 1 inclusive published, bit 2 tile holds a head
+__global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, const uint8_t *__restrict__ f,
+                                                              int64_t n, double *b, unsigned char *scratch,
+                                                              int64_t tiles) {
+  const SegScratchView S = seg_view(scratch, tiles);
+  __shared__ int64_t s_tile;
+  __shared__ double s_wsum[kSegThreads / 32];
+  __shared__ int s_wflag[kSegThreads / 32];
+  __shared__ double s_wcar[kSegThreads / 32];
+  __shared__ int s_wcflag[kSegThreads / 32];
+  __shared__ double s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(S.ticket, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t >= tiles) break;
+    const int64_t base = t * kSegTile + int64_t(tid) * kSegItems;
+    double v[kSegItems];
+    uint32_t fm = 0;
+#pragma unroll
+    for (int k = 0; k < kSegItems; ++k) {
+      const int64_t i = base + k;
+      v[k] = i < n ? a[i] : 0.0;
+      if (i < n && f[i]) fm |= 1u << k;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSegItems; ++k) {
+      acc = ((fm >> k) & 1u) ? v[k] : acc + v[k];
+      v[k] = acc;
+    }
+    // warp inclusive scan of (flag, value) pairs, left to right
+    int fl = fm != 0u;
+    double x = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, off);
+      const int yf = __shfl_up_sync(0xffffffffu, fl, off);
+      if (lane >= off) {
+        if (!fl) x = y + x;
+        fl |= yf;
+      }
+    }
+    if (lane == 31) { s_wsum[warp] = x; s_wflag[warp] = fl; }
+    double ex = __shfl_up_sync(0xffffffffu, x, 1);
+    int exf = __shfl_up_sync(0xffffffffu, fl, 1);
+    if (lane == 0) { ex = 0.0; exf = 0; }
+    __syncthreads();
+    if (tid == 0) {
+      double c = 0.0;
+      int cf = 0;
+      for (int w = 0; w < kSegThreads / 32; ++w) {
+        s_wcar[w] = c;
+        s_wcflag[w] = cf;
+        if (s_wflag[w]) { c = s_wsum[w]; cf = 1; }
+        else c = c + s_wsum[w];
+      }
+      // tile aggregate: c with flag cf; publish, then look back over earlier tiles
+      S.agg[t] = c;
+      if (cf) S.incl[t] = c;
+      __threadfence();
+      seg_st_release(&S.status[t], cf ? (4u | 2u | 1u) : 1u);
+      double carry = 0.0;
+      if (t > 0) {
+        const long long t0 = clock64();
+        for (int64_t u = t - 1; u >= 0; --u) {
+          uint32_t st;
+          while (((st = seg_ld_acquire(&S.status[u])) & 3u) == 0u) {
+            if (clock64() - t0 > kSegSpin) { atomicExch(S.error, 1u); st = 2u; break; }
+            __nanosleep(32);
+          }
+          if (st & 2u) { carry = seg_ld_relaxed(&S.incl[u]) + carry; break; }
+          carry = seg_ld_relaxed(&S.agg[u]) + carry;
+        }
+      }
+      s_carry = carry;
+      if (!cf) {
+        S.incl[t] = carry + c;
+        __threadfence();
+        seg_st_release(&S.status[t], 2u | 1u);
+      }
+    }
+    __syncthreads();
+    // exclusive carry of this thread: earlier threads of the warp, earlier warps, earlier tiles
+    if (!exf) {
+      ex = s_wcar[warp] + ex;
+      exf = s_wcflag[warp];
+      if (!exf) ex = s_carry + ex;
+    }
+#pragma unroll
+    for (int k = 0; k < kSegItems; ++k) {
+      if ((fm & ((2u << k) - 1u)) == 0u) v[k] = ex + v[k];
+      const int64_t i = base + k;
+      if (i < n) b[i] = v[k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(S.exited, 1u) == gridDim.x - 1) {
+      *S.ticket = 0u;
+      *S.exited = 0u;
+    }
+  }
+}
+
+static int seg_grid(int64_t tiles) {
+  static int cap = 0;
+  if (!cap) {
+    int per = 0, dev = 0, nsm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, segscan_kernel, kSegThreads, 0);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cap = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
+  }
+  return int(tiles < cap ? tiles : cap);
+}
+
+// Runs the scan with scratch at `scratch` (already zeroed over its first 16 + 4T bytes).
+static int segscan_run(const double *a, const uint8_t *f, int64_t n, double *b, unsigned char *scratch, int64_t tiles,
+                       cudaStream_t s, std::string *err) {
+  count_launches(1);
+  segscan_kernel<<<seg_grid(tiles), kSegThreads, 0, s>>>(a, f, n, b, scratch, tiles);
+  if (cudaGetLastError() != cudaSuccess) { *err = "cox_segscan: launch failed"; return COX_E_CUDA; }
+  uint32_t e = 0;
+  if (cudaMemcpyAsync(&e, scratch + 8, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    *err = "cox_segscan: execution failed";
+    return COX_E_CUDA;
+  }
+  if (e) { *err = "cox_segscan: a look-back wait exceeded its bound"; return COX_E_TIMEOUT; }
+  return COX_OK;
+}
+
+static int segscan_check(const double *a, const uint8_t *f, int64_t n, double *b, std::string *err) {
+  if (n < 0 || (n > 0 && (!a || !f || !b))) { *err = "cox_segscan: null or negative argument"; return COX_E_INVALID; }
+  if (n > 0 && (!pointer_on_device(a) || !pointer_on_device(f) || !pointer_on_device(b))) {
+    *err = "cox_segscan: a, head_flags and out must be device memory";
+    return COX_E_INVALID;
+  }
+  return COX_OK;
+}
+
+}  // namespace coxgb
+
+using namespace coxgb;
+
+extern "C" int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream) {
+  std::string err;
+  int rc = segscan_check(a, head_flags, n, out, &err);
+  if (rc || n == 0) return rc ? set_last_error(rc, err.c_str()) : COX_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t tiles = (n + kSegTile - 1) / kSegTile;
+  const size_t bytes = seg_scratch_bytes(tiles);
+  unsigned char *scratch = static_cast<unsigned char *>(dev_alloc(bytes));
+  if (!scratch) return set_last_error(COX_E_OOM, "cox_segscan: scratch allocation failed");
+  rc = cudaMemsetAsync(scratch, 0, 16 + 4 * size_t(tiles), s) == cudaSuccess ? COX_OK : COX_E_CUDA;
+  if (!rc) rc = segscan_run(a, head_flags, n, out, scratch, tiles, s, &err);
+  else err = "cox_segscan: memset failed";
+  cudaStreamSynchronize(s);
+  dev_free(scratch, bytes);
+  return rc ? set_last_error(rc, err.c_str()) : COX_OK;
+}

@@ -198,6 +198,19 @@ int64_t cox_launch_count(void);
  * Errors: COX_E_INVALID (null/host pointers, n < 0), COX_E_OOM, COX_E_CUDA, COX_E_TIMEOUT. */
 int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream);
 
+/* Same result as cox_segscan, but the call allocates no device memory. No counterpart in the
+ * paper: it exists for callers that cannot allocate device memory while they run -- a host
+ * program whose own memory pool must own every device byte, a real-time loop that cannot risk
+ * an allocator call blocking or failing mid-run, a process held to a fixed memory budget.
+ * Its scratch is one static device array of 81,936 bytes that every GPU loading this library
+ * holds until the process exits; n is therefore limited to 16,777,216 values (COX_E_INVALID
+ * beyond that). The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. All calls share the array and clear the parts that must start at zero, so calls
+ * whose work overlaps on the GPU race with each other: issue them one at a time (same stream,
+ * or synchronized). Other arguments, errors and stream behaviour as cox_segscan. */
+int cox_segscan_noalloc(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ COX_FP64, COX_FP32C = 0, 1
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
-           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan"]
+           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan",
+           "cox_segscan_noalloc"]
 
 
 class CoxError(RuntimeError):
@@ -92,6 +93,7 @@ def lib():
             L.cox_launch_count.argtypes = []
             L.cox_launch_count.restype = i64
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
+            L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
             _lib = L
             _install_torch_allocator(L)
     return _lib

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "cox.h"
@@ -28,7 +29,7 @@ struct SegScratchView {
   double *agg, *incl;
 };
 
-__host__ __device__ inline size_t seg_scratch_bytes(int64_t tiles) {
+__host__ __device__ constexpr size_t seg_scratch_bytes(int64_t tiles) {
   const size_t st = (16 + 4 * size_t(tiles) + 7) & ~size_t(7);
   return st + 16 * size_t(tiles);
 }
@@ -221,5 +222,61 @@ extern "C" int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n
   else err = "cox_segscan: memset failed";
   cudaStreamSynchronize(s);
   dev_free(scratch, bytes);
+  return rc ? set_last_error(rc, err.c_str()) : COX_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// Callers that must not allocate device memory during a call use cox_segscan_noalloc: the
+// look-back scratch lives in this file-scope array instead of the library allocator. Every
+// GPU that loads the library holds these bytes until the process exits.
+namespace coxgb {
+constexpr int64_t kStaticMaxTiles = 4096;   // 4096 tiles x 4096 values = 16,777,216 values
+constexpr size_t kStaticScratchBytes = seg_scratch_bytes(kStaticMaxTiles);
+static __device__ __align__(256) unsigned char g_segscan_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static unsigned char *g_static_addr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device, looked up once per device
+// (host code cannot use the array's name as a device address).
+static int static_scratch_address(unsigned char **out, std::string *err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    *err = "cox_segscan_noalloc: no usable current device";
+    return COX_E_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_segscan_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      *err = std::string("cox_segscan_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+      return COX_E_CUDA;
+    }
+    g_static_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_static_addr[dev];
+  return COX_OK;
+}
+}  // namespace coxgb
+
+extern "C" int cox_segscan_noalloc(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream) {
+  std::string err;
+  int rc = segscan_check(a, head_flags, n, out, &err);
+  if (rc) return set_last_error(rc, err.c_str());
+  if (n == 0) return COX_OK;
+  const int64_t tiles = (n + kSegTile - 1) / kSegTile;
+  if (tiles > kStaticMaxTiles)
+    return set_last_error(COX_E_INVALID, "cox_segscan_noalloc: n exceeds 16,777,216 values (the static scratch limit)");
+  unsigned char *scratch = nullptr;
+  if ((rc = static_scratch_address(&scratch, &err))) return set_last_error(rc, err.c_str());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear the ticket, error and tile states
+  if (cudaMemsetAsync(scratch, 0, 16 + 4 * size_t(tiles), s) != cudaSuccess)
+    return set_last_error(COX_E_CUDA, "cox_segscan_noalloc: clearing the static scratch failed");
+  rc = segscan_run(a, head_flags, n, out, scratch, tiles, s, &err);
   return rc ? set_last_error(rc, err.c_str()) : COX_OK;
 }

@@ -20,7 +20,7 @@
  *   - cyclic coordinate descent with the 1-D Newton step, eq. (newton), the trust region
  *     and the L1 directional-derivative rule of §2.4.
  *
- * Readings where the paper is silent or ambiguous (each also listed in the design notes):
+ * Readings where the paper is silent or ambiguous:
  *   R1 ties: every event at time t in stratum k sees the whole risk set {r : Y_r >= t}
  *      (Breslow); with rows in decreasing time order the scan is read at the LAST row of
  *      the tie block, i.e. the first row of the block in increasing order.

@@ -69,6 +69,8 @@ struct cox_handle {
 
 namespace {
 
+constexpr int kSweepBody = 64;   // coordinate-step launches per iteration of the device-driven loop
+
 int fail(cox_handle *h, int code, const std::string &msg) {
   t_last_error = msg;
   if (h) h->err = msg;
@@ -150,7 +152,7 @@ int alloc_fit_state(cox_handle *h) {
   if (cudaMemcpyAsync(h->items, it.data(), std::max<int64_t>(T, 1) * sizeof(int2), cudaMemcpyHostToDevice, h->stream) !=
       cudaSuccess)
     return cuda_fail(h, "items copy");
-  LaunchCtl lc{0u, 0u, int32_t(T), 0};
+  LaunchCtl lc{0u, 0u, int32_t(T), 1, 0};
   if (cudaMemcpyAsync(h->lc, &lc, sizeof(lc), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return cuda_fail(h, "lc copy");
   h->valued = d.val != nullptr;
   const int mg = ccd_max_grid(h->sd->precision, h->valued);
@@ -247,20 +249,46 @@ int device_error(cox_handle *h) {
   return COX_OK;
 }
 
+// The sweep loop as one graph: a conditional WHILE node whose body is `len` coordinate-step
+// launches. The kernel ends the loop (sets the condition to 0) when the fit has stopped or the
+// launch budget in LaunchCtl is spent, so a whole fit is one cudaGraphLaunch.
 int build_graph(cox_handle *h, int len) {
   if (h->graph && h->graph_len == len) return COX_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
-  cudaGraph_t g;
-  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(h, "capture");
-  for (int i = 0; i < len; ++i)
-    if (launch_ccd(h->sd->precision, h->dfit, h->items, h->lc, h->grid, kModeFit, 0, h->valued, h->stream)) {
-      cudaStreamEndCapture(h->stream, &g);
-      return cuda_fail(h, "capture launch");
-    }
-  if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) return cuda_fail(h, "end capture");
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return cuda_fail(h, "graph create");
+  cudaGraphConditionalHandle cond;
+  if (cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, "conditional handle");
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, "conditional node");
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, "capture");
+  }
+  int rc = COX_OK;
+  for (int i = 0; i < len && !rc; ++i)
+    rc = launch_ccd(h->sd->precision, h->dfit, h->items, h->lc, h->grid, kModeFit, 0, h->valued, h->stream, cond);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->stream, &captured);
+  if (rc || ec != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, "capture launch");
+  }
   const cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(h, "graph instantiate");
@@ -387,24 +415,27 @@ int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *
     }
     return copy_out(h, beta_out, h->hfit.beta, d.p);
   }
-  const int len = int(std::min<int64_t>(std::max<int64_t>(d.p, 32), 4096));
+  const int len = kSweepBody;
   if ((rc = build_graph(h, len))) return rc;
+  // the step-launch budget bounds the device-driven loop whatever happens on the device
   const int64_t max_launches = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
-  int64_t launched = 0;
+  LaunchCtl lc{0u, 0u, int32_t(h->n_items), 1, max_launches};
+  if (cudaMemcpyAsync(h->lc, &lc, sizeof(lc), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "lc copy");
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
   cudaEventRecord(h->ev0, h->stream);
-  for (;;) {
-    if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return cuda_fail(h, "graph launch");
-    cudaEventRecord(h->ev1, h->stream);
-    count_launches(len);
-    launched += len;
-    if ((rc = read_ctl(h))) return rc;
-    if (h->h_ctl->error) break;
-    if (h->h_ctl->state != kRunning) break;
-    if (launched > max_launches) return fail(h, COX_E_INVALID, "cox_fit: sweep accounting exceeded its bound");
-  }
+  if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return cuda_fail(h, "graph launch");
+  cudaEventRecord(h->ev1, h->stream);
+  LaunchCtl lc_after{};
+  if (cudaMemcpyAsync(&lc_after, h->lc, sizeof(lc_after), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return cuda_fail(h, "lc read");
+  if ((rc = read_ctl(h))) return rc;
+  const int64_t launched = max_launches - lc_after.budget;
+  count_launches(launched);
   if ((rc = device_error(h))) return rc;
+  if (h->h_ctl->state == kRunning)
+    return fail(h, COX_E_INVALID, "cox_fit: the launch budget ended the sweep loop before the fit stopped");
   const FitCtl &c = *h->h_ctl;
   rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
   if (info) {
@@ -616,7 +647,9 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     for (int64_t k = 0; k < maxT; ++k)
       for (int i = 0; i < n; ++i)
         if (running[i] && k < D(hs[i]).T) it.push_back(make_int2(i, int(D(hs[i]).T - 1 - k)));
-    LaunchCtl l{0u, 0u, int32_t(it.size()), 0};
+    int act = 0;
+    for (int i = 0; i < n; ++i) act += running[i];
+    LaunchCtl l{0u, 0u, int32_t(it.size()), act, 0};
     if (!it.empty() && cudaMemcpyAsync(items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return cuda_fail(nullptr, "items copy");
     if (cudaMemcpyAsync(lc, &l, sizeof(l), cudaMemcpyHostToDevice, s) != cudaSuccess) return cuda_fail(nullptr, "lc copy");

@@ -94,28 +94,31 @@ struct PF32C {
 constexpr long long kSpinBudget = 4000000000LL;   // ~2 s of SM clock for any device-side wait
 
 // ------------------------------------------------------------------ shared memory plan
-template <class P>
+// NV = number of running sums: 2 for binary X (D and N1; N2 = N1), 3 for valued X.
+template <class P, int NV>
 struct Smem {
   using T = typename P::T;
   using Acc = typename P::Acc;
   static constexpr int TILE = kThreads * P::ITEMS;
   static constexpr int WORDS = TILE / 32;
-  static constexpr size_t o_v = 0;
-  static constexpr size_t o_head = o_v + sizeof(T) * TILE;
-  static constexpr size_t o_cut = o_head + 4 * WORDS;
-  static constexpr size_t o_nz = o_cut + 4 * WORDS;
-  static constexpr size_t o_hpre = o_nz + 4 * WORDS;
-  static constexpr size_t o_hloc = (o_hpre + 4 * WORDS + 15) & ~size_t(15);
-  static constexpr size_t o_hcut = o_hloc + sizeof(Acc) * 3 * kHeadCap;
-  static constexpr size_t o_tc = (o_hcut + kHeadCap + 15) & ~size_t(15);
-  static constexpr size_t o_tflag = o_tc + sizeof(Acc) * 3 * kThreads;
-  static constexpr size_t o_x = (o_tflag + kThreads + 15) & ~size_t(15);
-  static constexpr size_t bytes_binary = o_x;
-  static constexpr size_t bytes_valued = o_x + sizeof(T) * TILE;
+  static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t o_v = 0;                                        // TILE values, swizzled
+  static constexpr size_t o_head = o_v + sizeof(T) * TILE;                 // head bitmask
+  static constexpr size_t o_cut = o_head + 4 * WORDS;                      // stratum-end bitmask
+  static constexpr size_t o_nz = o_cut + 4 * WORDS;                        // column-j bitmask
+  static constexpr size_t o_hpre = o_nz + 4 * WORDS;                       // popcount prefix of heads
+  static constexpr size_t o_hloc = al(o_hpre + 4 * WORDS);                 // local sums at heads
+  static constexpr size_t o_hpos = o_hloc + sizeof(Acc) * NV * kHeadCap;   // head offsets in tile
+  static constexpr size_t o_hd = al(o_hpos + 2 * kHeadCap);                // events per head
+  static constexpr size_t o_hcut = o_hd + 4 * kHeadCap;                    // cut after head in its thread
+  static constexpr size_t o_tc = al(o_hcut + kHeadCap);                    // thread aggregates, then carries
+  static constexpr size_t o_tflag = o_tc + sizeof(Acc) * NV * kThreads;
+  static constexpr size_t o_x = al(o_tflag + kThreads);                    // x values (valued X only)
+  static constexpr size_t bytes = NV == 3 ? o_x + sizeof(T) * TILE : o_x;
 };
 
 // ------------------------------------------------------------------ the coordinate step
-// §2.4 as read in the design notes: L2 adds beta/sigma^2 and 1/sigma^2; L1 uses the
+// §2.4, with these readings where the paper is silent: L2 adds beta/sigma^2 and 1/sigma^2; L1 uses the
 // directional derivatives g' +- gamma at 0 and g' + gamma sgn(beta) elsewhere; the Newton
 // step is clipped to the trust half-width, an L1 step that would cross 0 stops at 0, and
 // the half-width becomes max(2 |step|, half-width / 2). g'' <= 0 skips the coordinate.
@@ -177,11 +180,6 @@ __device__ void block_sum(double (&v)[NV], double *scratch /* [NV*32] */) {
   __syncthreads();
 }
 
-template <class P>
-__device__ __forceinline__ typename P::T load_v(const void *v, int64_t pos) {
-  return static_cast<const typename P::T *>(v)[pos];
-}
-
 // value written at a position for exp(eta - shift); exits hold the negative
 template <class P>
 __device__ __forceinline__ typename P::T make_v(double eta, double shift, bool exitp, int32_t *err) {
@@ -196,19 +194,27 @@ __device__ __forceinline__ typename P::T make_v(double eta, double shift, bool e
   }
 }
 
+template <class Acc, class P, int NV>
+__device__ __forceinline__ void comb_n(Acc (&a)[NV], const Acc (&b)[NV]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) a[i] = P::comb(a[i], b[i]);
+}
+
 // ------------------------------------------------------------------ the kernel
-template <class P>
+template <class P, int NV>
 __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict__ fits, const int2 *__restrict__ items,
-                                                       LaunchCtl *lc, int mode, int j_eval, int valued) {
+                                                       LaunchCtl *lc, int mode, int j_eval, unsigned long long cond) {
   using T = typename P::T;
   using Acc = typename P::Acc;
-  using S = Smem<P>;
+  using S = Smem<P, NV>;
+  constexpr bool VAL = NV == 3;
   constexpr int ITEMS = P::ITEMS;
   constexpr int TILE = S::TILE;
   constexpr int WORDS = S::WORDS;
   constexpr int PC = 16 / sizeof(T);          // elements per 16-byte chunk
   constexpr int CHUNKS = TILE / PC;
   constexpr int TCH = ITEMS / PC;             // chunks per thread (8)
+  constexpr int RAKE = kThreads / 32;         // thread aggregates per lane of the raking warp
   static_assert(TCH == 8, "each thread owns 128 bytes");
 
   extern __shared__ __align__(16) unsigned char smem[];
@@ -218,6 +224,8 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
   uint32_t *nzbits = reinterpret_cast<uint32_t *>(smem + S::o_nz);
   int32_t *hpre = reinterpret_cast<int32_t *>(smem + S::o_hpre);
   Acc *hloc = reinterpret_cast<Acc *>(smem + S::o_hloc);
+  uint16_t *hpos = reinterpret_cast<uint16_t *>(smem + S::o_hpos);
+  int32_t *hd = reinterpret_cast<int32_t *>(smem + S::o_hd);
   uint8_t *hcut = reinterpret_cast<uint8_t *>(smem + S::o_hcut);
   Acc *tc = reinterpret_cast<Acc *>(smem + S::o_tc);
   uint8_t *tflag = reinterpret_cast<uint8_t *>(smem + S::o_tflag);
@@ -225,19 +233,17 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
 
   __shared__ int s_item;
   __shared__ int s_last;
+  __shared__ int s_active;
   __shared__ double s_red[3 * 32];
-  __shared__ Acc s_wagg[3][kThreads / 32];
-  __shared__ int s_wflag[kThreads / 32];
-  __shared__ Acc s_wcar[3][kThreads / 32];
-  __shared__ int s_wcflag[kThreads / 32];
-  __shared__ double s_tile_carry[3];
-  __shared__ double s_tile_agg[3];
-  __shared__ int s_tile_flag;
+  __shared__ Acc s_carry[NV];
+  __shared__ double s_wred[3][kThreads / 32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_items = lc->n_items;
+  if (tid == 0) s_active = mode == kModeFit ? *reinterpret_cast<volatile int32_t *>(&lc->active) : 1;
+  __syncthreads();
 
-  for (;;) {
+  for (; s_active > 0;) {   // a launch after every fit stopped only does the exit accounting
     if (tid == 0) s_item = atomicAdd(&lc->ticket, 1u);
     __syncthreads();
     const int w = s_item;
@@ -259,30 +265,32 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
     const double pend_db = ctl->pend_db;
     const uint32_t epoch = ctl->epoch;
     const double shift = F.shift;
-    const int vf = valued && D->val != nullptr;   // `valued`: the launch reserved shared memory for x
+    const bool vf = VAL && D->val != nullptr;   // binary fits in a valued launch use x = 1
 
     // ---- 1. stage the tile of v (async), overlapped with the metadata below
     {
       const unsigned char *g = reinterpret_cast<const unsigned char *>(static_cast<const T *>(F.v) + lo);
       for (int c = tid; c < CHUNKS; c += kThreads) {
-        int phys = c ^ ((c >> 3) & 7);
+        const int phys = c ^ ((c >> 3) & 7);
         cp_async16(smem + S::o_v + size_t(phys) * 16, g + size_t(c) * 16);
       }
       cp_async_commit();
     }
     for (int q = tid; q < WORDS; q += kThreads) { headbits[q] = 0u; cutbits[q] = 0u; nzbits[q] = 0u; }
-    if (vf)
+    if (VAL)
       for (int q = tid; q < TILE; q += kThreads) xs[q] = T(0);
     __syncthreads();
     const int ga = D->tile_g[t], nh = D->tile_g[t + 1] - ga;
     for (int h = tid; h < nh; h += kThreads) {
-      int pos = D->head_pos[ga + h] - lo;
+      const int pos = D->head_pos[ga + h] - lo;
+      hpos[h] = uint16_t(pos);
+      hd[h] = D->head_d[ga + h];
       atomicOr(&headbits[pos >> 5], 1u << (pos & 31));
     }
     {
       const int ka = D->tile_k[t], kb = D->tile_k[t + 1];
       for (int k = ka + tid; k < kb; k += kThreads) {
-        int pos = D->cut_pos[k] - lo;
+        const int pos = D->cut_pos[k] - lo;
         atomicOr(&cutbits[pos >> 5], 1u << (pos & 31));
       }
     }
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
       const int32_t *ct = D->col_tile + int64_t(j) * (T_ + 1);
       const int64_t qa = cb + ct[t], qb = cb + ct[t + 1];
       for (int64_t q = qa + tid; q < qb; q += kThreads) {
-        int pos = int(D->idx[q] & kPosMask) - lo;
+        const int pos = int(D->idx[q] & kPosMask) - lo;
         atomicOr(&nzbits[pos >> 5], 1u << (pos & 31));
         if (vf) xs[pos] = T(D->val[q]);
       }
@@ -304,10 +312,10 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
       ua = cb + ct[t];
       ub = cb + ct[t + 1];
       for (int64_t q = ua + tid; q < ub; q += kThreads) {
-        uint32_t e = D->idx[q];
-        int64_t pos = e & kPosMask;
-        double x = D->val ? D->val[q] : 1.0;
-        double et = __dadd_rn(F.eta[pos], __dmul_rn(x, pend_db));
+        const uint32_t e = D->idx[q];
+        const int64_t pos = e & kPosMask;
+        const double x = D->val ? D->val[q] : 1.0;
+        const double et = __dadd_rn(F.eta[pos], __dmul_rn(x, pend_db));
         F.eta[pos] = et;
         static_cast<T *>(F.v)[pos] = make_v<P>(et, shift, (e & kExitBit) != 0, &ctl->error);
       }
@@ -316,23 +324,23 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
     __syncthreads();
     // patch the staged tile with the updated values (each thread rereads its own writes)
     for (int64_t q = ua + tid; q < ub; q += kThreads) {
-      int e = int(D->idx[q] & kPosMask) - lo;
-      int c = e / PC;
+      const int e = int(D->idx[q] & kPosMask) - lo;
+      const int c = e / PC;
       sv[(c ^ ((c >> 3) & 7)) * PC + (e % PC)] = static_cast<const T *>(F.v)[lo + e];
     }
     if (hi - lo < TILE)
       for (int e = hi - lo + tid; e < TILE; e += kThreads) {
-        int c = e / PC;
+        const int c = e / PC;
         sv[(c ^ ((c >> 3) & 7)) * PC + (e % PC)] = T(0);
       }
     if (warp == 0) {   // exclusive popcount prefix of the head bitmask
       int run = 0;
       for (int base = 0; base < WORDS; base += 32) {
-        int c = base + lane < WORDS ? __popc(headbits[base + lane]) : 0;
+        const int c = base + lane < WORDS ? __popc(headbits[base + lane]) : 0;
         int incl = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, incl, off);
+          const int y = __shfl_up_sync(0xffffffffu, incl, off);
           if (lane >= off) incl += y;
         }
         if (base + lane < WORDS) hpre[base + lane] = run + incl - c;
@@ -347,8 +355,8 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
       const int c0 = tid * TCH;
 #pragma unroll
       for (int k = 0; k < TCH; ++k) {
-        int c = c0 + k;
-        int phys = c ^ ((c >> 3) & 7);
+        const int c = c0 + k;
+        const int phys = c ^ ((c >> 3) & 7);
         const float4 q = *reinterpret_cast<const float4 *>(smem + S::o_v + size_t(phys) * 16);
         const T *qq = reinterpret_cast<const T *>(&q);
 #pragma unroll
@@ -361,81 +369,128 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
     const uint32_t cm = (cutbits[b0 >> 5] >> (b0 & 31)) & wmask;
     const uint32_t zm = (nzbits[b0 >> 5] >> (b0 & 31)) & wmask;
     const int hb = hpre[b0 >> 5] + __popc(headbits[b0 >> 5] & ((1u << (b0 & 31)) - 1u));
-    Acc a0 = P::zero(), a1 = P::zero(), a2 = P::zero();
+    Acc a[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) a[i] = P::zero();
     int seen = 0;
     const bool any_nz = __any_sync(0xffffffffu, zm != 0u);
 #pragma unroll
     for (int k = ITEMS - 1; k >= 0; --k) {
-      if ((cm >> k) & 1u) { a0 = P::zero(); a1 = P::zero(); a2 = P::zero(); seen = 1; }
-      P::add(a0, vals[k]);
+      if ((cm >> k) & 1u) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) a[i] = P::zero();
+        seen = 1;
+      }
+      P::add(a[0], vals[k]);
       if (any_nz && __any_sync(0xffffffffu, (zm >> k) & 1u)) {
         if ((zm >> k) & 1u) {
-          T x = vf ? xs[b0 + k] : T(1);
-          T wv = vf ? T(x * vals[k]) : vals[k];
-          P::add(a1, wv);
-          if (vf) P::add(a2, T(x * wv));
+          if constexpr (VAL) {
+            const T x = vf ? xs[b0 + k] : T(1);
+            const T wv = T(x * vals[k]);
+            P::add(a[1], wv);
+            P::add(a[2], T(x * wv));
+          } else {
+            P::add(a[1], vals[k]);
+          }
         }
       }
       if ((hm >> k) & 1u) {
-        int h = hb + __popc(hm & ((1u << k) - 1u));
-        hloc[3 * h + 0] = a0; hloc[3 * h + 1] = a1; hloc[3 * h + 2] = vf ? a2 : a1;
+        const int h = hb + __popc(hm & ((1u << k) - 1u));
+#pragma unroll
+        for (int i = 0; i < NV; ++i) hloc[NV * h + i] = a[i];
         hcut[h] = uint8_t(seen);
       }
     }
-    if (!vf) a2 = a1;
-
-    // ---- 4a. warp-level inclusive segmented suffix scan of the thread aggregates
-    int f = cm != 0u;
-    Acc i0 = a0, i1 = a1, i2 = a2;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      Acc y0 = P::shfl_down(i0, off), y1 = P::shfl_down(i1, off), y2 = P::shfl_down(i2, off);
-      int yf = __shfl_down_sync(0xffffffffu, f, off);
-      if (lane + off < 32) {
-        if (!f) { i0 = P::comb(i0, y0); i1 = P::comb(i1, y1); i2 = P::comb(i2, y2); }
-        f |= yf;
-      }
-    }
-    if (lane == 0) { s_wagg[0][warp] = i0; s_wagg[1][warp] = i1; s_wagg[2][warp] = i2; s_wflag[warp] = f; }
-    // exclusive within the warp: the inclusive value of lane + 1
-    Acc e0 = P::shfl_down(i0, 1), e1 = P::shfl_down(i1, 1), e2 = P::shfl_down(i2, 1);
-    int ef = __shfl_down_sync(0xffffffffu, f, 1);
-    if (lane == 31) { e0 = P::zero(); e1 = P::zero(); e2 = P::zero(); ef = 0; }
+    for (int i = 0; i < NV; ++i) tc[NV * tid + i] = a[i];
+    tflag[tid] = uint8_t(cm != 0u);
     __syncthreads();
-    if (tid == 0) {   // 4b. suffix over the warps (8 values, sequential)
-      Acc c0 = P::zero(), c1 = P::zero(), c2 = P::zero();
-      int cf = 0;
-      for (int ww = kThreads / 32 - 1; ww >= 0; --ww) {
-        s_wcar[0][ww] = c0; s_wcar[1][ww] = c1; s_wcar[2][ww] = c2; s_wcflag[ww] = cf;
-        if (s_wflag[ww]) { c0 = s_wagg[0][ww]; c1 = s_wagg[1][ww]; c2 = s_wagg[2][ww]; cf = 1; }
-        else { c0 = P::comb(s_wagg[0][ww], c0); c1 = P::comb(s_wagg[1][ww], c1); c2 = P::comb(s_wagg[2][ww], c2); }
-      }
-      s_tile_agg[0] = P::to64(c0); s_tile_agg[1] = P::to64(c1); s_tile_agg[2] = P::to64(c2);
-      s_tile_flag = cf;
-    }
-    __syncthreads();
-    if (!ef) {
-      e0 = P::comb(e0, s_wcar[0][warp]); e1 = P::comb(e1, s_wcar[1][warp]); e2 = P::comb(e2, s_wcar[2][warp]);
-      ef = s_wcflag[warp];
-    }
-    tc[3 * tid + 0] = e0; tc[3 * tid + 1] = e1; tc[3 * tid + 2] = e2;
-    tflag[tid] = uint8_t(ef);
 
-    // ---- 4c. publish the tile aggregate and look back (warp 0)
+    // ---- 4. one warp: raking segmented suffix over the thread aggregates, tile aggregate,
+    //         per-thread exclusive carries, then the decoupled look-back over earlier tiles
     if (warp == 0) {
-      const int tf = s_tile_flag;
+      const int t0 = lane * RAKE;
+      Acc r[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) r[i] = P::zero();
+      int rf = 0;
+#pragma unroll
+      for (int q = RAKE - 1; q >= 0; --q) {
+        const int th = t0 + q;
+        if (tflag[th]) {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) r[i] = tc[NV * th + i];
+          rf = 1;
+        } else {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) r[i] = P::comb(tc[NV * th + i], r[i]);
+        }
+      }
+      Acc x[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) x[i] = r[i];
+      int xf = rf;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        Acc y[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) y[i] = P::shfl_down(x[i], off);
+        const int yf = __shfl_down_sync(0xffffffffu, xf, off);
+        if (lane + off < 32) {
+          if (!xf) comb_n<Acc, P, NV>(x, y);
+          xf |= yf;
+        }
+      }
+      // lane 0 holds the tile's inclusive value from its first position
+      const int tf = __shfl_sync(0xffffffffu, xf, 0);
+      double agg[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) agg[i] = __shfl_sync(0xffffffffu, P::to64(x[i]), 0);
       const uint32_t ep = (epoch & 0x1fffffffu) << 3;
-      if (lane == 0) {   // slots 0..2: aggregate, 3..5: inclusive (a flagged tile is complete)
+      if (lane == 0) {   // slots 0..2: aggregate, 3..5: inclusive (a tile holding a stratum end is complete)
         const int o = tf ? 3 : 0;
-        F.tval[6 * t + o + 0] = s_tile_agg[0]; F.tval[6 * t + o + 1] = s_tile_agg[1]; F.tval[6 * t + o + 2] = s_tile_agg[2];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) F.tval[6 * t + o + i] = agg[i];
         __threadfence();
         st_release_u32(&F.tstat[t], ep | (tf ? 4u | 2u : 1u));
       }
-      double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+      // exclusive carries of this lane's threads: start from lane + 1's inclusive value
+      Acc c[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) c[i] = P::shfl_down(x[i], 1);
+      int cf = __shfl_down_sync(0xffffffffu, xf, 1);
+      if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) c[i] = P::zero();
+        cf = 0;
+      }
+#pragma unroll
+      for (int q = RAKE - 1; q >= 0; --q) {
+        const int th = t0 + q;
+        Acc own[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) own[i] = tc[NV * th + i];
+        const int of = tflag[th];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tc[NV * th + i] = c[i];
+        tflag[th] = uint8_t(cf);
+        if (of) {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) c[i] = own[i];
+          cf = 1;
+        } else {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) c[i] = P::comb(own[i], c[i]);
+        }
+      }
+      // look back over the tiles to the right (they hold the later positions)
+      double cr[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) cr[i] = 0.0;
       const bool last_is_cut = ((cutbits[(hi - lo - 1) >> 5] >> ((hi - lo - 1) & 31)) & 1u) != 0u;
       if (t + 1 < T_ && !last_is_cut) {
         int base = t + 1;
-        const long long t0 = clock64();
+        const long long tstart = clock64();
         bool timed_out = false;
         for (;;) {
           const int u = base + lane;
@@ -452,8 +507,8 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
             const uint32_t inv = __ballot_sync(0xffffffffu, !valid);
             const uint32_t inc = __ballot_sync(0xffffffffu, valid && (st & 3u) == 2u);
             if (inv == 0u || (inc != 0u && (__ffs(inc) < __ffs(inv)))) break;
-            if (clock64() - t0 > kSpinBudget) { timed_out = true; break; }
-            __nanosleep(64);
+            if (clock64() - tstart > kSpinBudget) { timed_out = true; break; }
+            __nanosleep(32);
           }
           if (timed_out) {
             if (lane == 0) atomicExch(&ctl->error, COX_E_TIMEOUT);
@@ -461,32 +516,30 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
           }
           const uint32_t inc = __ballot_sync(0xffffffffu, valid && (st & 3u) == 2u);
           const int stop = inc ? __ffs(inc) - 1 : 31;
-          double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+          double v[NV];
+#pragma unroll
+          for (int i = 0; i < NV; ++i) v[i] = 0.0;
           if (lane <= stop && u < T_) {
             const int o = (st & 3u) == 2u ? 3 : 0;
-            v0 = ld_relaxed_f64(&F.tval[6 * u + o + 0]);
-            v1 = ld_relaxed_f64(&F.tval[6 * u + o + 1]);
-            v2 = ld_relaxed_f64(&F.tval[6 * u + o + 2]);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = ld_relaxed_f64(&F.tval[6 * u + o + i]);
           }
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            v0 += __shfl_down_sync(0xffffffffu, v0, off);
-            v1 += __shfl_down_sync(0xffffffffu, v1, off);
-            v2 += __shfl_down_sync(0xffffffffu, v2, off);
+          for (int i = 0; i < NV; ++i) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+            cr[i] += __shfl_sync(0xffffffffu, v[i], 0);
           }
-          c0 += __shfl_sync(0xffffffffu, v0, 0);
-          c1 += __shfl_sync(0xffffffffu, v1, 0);
-          c2 += __shfl_sync(0xffffffffu, v2, 0);
           if (inc) break;
           base += 32;
         }
       }
       if (lane == 0) {
-        s_tile_carry[0] = c0; s_tile_carry[1] = c1; s_tile_carry[2] = c2;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) s_carry[i] = P::from64(cr[i]);
         if (!tf) {
-          F.tval[6 * t + 3] = s_tile_agg[0] + c0;
-          F.tval[6 * t + 4] = s_tile_agg[1] + c1;
-          F.tval[6 * t + 5] = s_tile_agg[2] + c2;
+#pragma unroll
+          for (int i = 0; i < NV; ++i) F.tval[6 * t + 3 + i] = agg[i] + cr[i];
           __threadfence();
           st_release_u32(&F.tstat[t], ep | 2u);
         }
@@ -495,49 +548,77 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
     __syncthreads();
 
     // ---- 5. tie-group ratios (eqs. parallel_g / parallel_h), head-parallel
-    const Acc C0 = P::from64(s_tile_carry[0]), C1 = P::from64(s_tile_carry[1]), C2 = P::from64(s_tile_carry[2]);
     double r_g1 = 0.0, r_g2 = 0.0, r_ll = 0.0;
-    Acc q_g1 = P::zero(), q_g2 = P::zero();
-    for (int h = tid; h < nh; h += kThreads) {
-      const int g = ga + h;
-      const int pos = D->head_pos[g] - lo;
-      const int o = pos / ITEMS;
-      Acc s0 = hloc[3 * h + 0], s1 = hloc[3 * h + 1], s2 = hloc[3 * h + 2];
-      if (!hcut[h]) {
-        Acc k0 = tc[3 * o + 0], k1 = tc[3 * o + 1], k2 = tc[3 * o + 2];
-        if (!tflag[o]) { k0 = P::comb(k0, C0); k1 = P::comb(k1, C1); k2 = P::comb(k2, C2); }
-        s0 = P::comb(s0, k0); s1 = P::comb(s1, k1); s2 = P::comb(s2, k2);
-      }
-      const double dg = double(D->head_d[g]);
-      if constexpr (sizeof(T) == 8) {
-        const double S0 = P::to64(s0), S1 = P::to64(s1), S2 = P::to64(s2);
-        if (j >= 0) {
-          const double r = S1 / S0;
-          r_g1 += dg * r;
-          r_g2 += dg * (S2 / S0 - r * r);
+    if (warp * 32 < nh) {
+      Acc C[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) C[i] = s_carry[i];
+      Acc q_g1 = P::zero(), q_g2 = P::zero();
+      for (int h = tid; h < nh; h += kThreads) {
+        const int pos = hpos[h];
+        const int o = pos / ITEMS;
+        Acc sh[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[i] = hloc[NV * h + i];
+        if (!hcut[h]) {
+          Acc k[NV];
+#pragma unroll
+          for (int i = 0; i < NV; ++i) k[i] = tc[NV * o + i];
+          if (!tflag[o]) comb_n<Acc, P, NV>(k, C);
+          comb_n<Acc, P, NV>(sh, k);
         }
-        if (need_ll) r_ll += dg * log(S0);
-        if (F.out_S0) { F.out_S0[g] = S0; F.out_S1[g] = S1; }
+        const int dgi = hd[h];
+        if constexpr (sizeof(T) == 8) {
+          const double S0 = P::to64(sh[0]), S1 = P::to64(sh[1]);
+          const double dg = double(dgi);
+          if (j >= 0) {
+            const double inv = 1.0 / S0;
+            const double r = S1 * inv;
+            r_g1 += dg * r;
+            if constexpr (VAL) r_g2 += dg * (P::to64(sh[2]) * inv - r * r);
+            else r_g2 += dg * (r * (1.0 - r));
+          }
+          if (need_ll) r_ll += dg * log(S0);
+          if (F.out_S0) { F.out_S0[ga + h] = S0; F.out_S1[ga + h] = S1; }
+        } else {
+          const float S0 = sh[0].s + sh[0].c, S1 = sh[1].s + sh[1].c;
+          const float fd = float(dgi);
+          if (j >= 0) {
+            const float inv = __frcp_rn(S0);
+            const float r = __fdiv_rn(S1, S0);
+            P::add(q_g1, fd * r);
+            if constexpr (VAL) P::add(q_g2, fd * ((sh[2].s + sh[2].c) * inv - r * r));
+            else P::add(q_g2, fd * (r * (1.0f - r)));
+          }
+          if (need_ll) r_ll += double(dgi) * log(P::to64(sh[0]));
+          if (F.out_S0) { F.out_S0[ga + h] = P::to64(sh[0]); F.out_S1[ga + h] = P::to64(sh[1]); }
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          q_g1 = P::comb(q_g1, P::shfl_down(q_g1, off));
+          q_g2 = P::comb(q_g2, P::shfl_down(q_g2, off));
+        }
+        if (lane == 0) { r_g1 = P::to64(q_g1); r_g2 = P::to64(q_g2); }
       } else {
-        const float S0 = s0.s + s0.c, S1 = s1.s + s1.c, S2 = s2.s + s2.c;
-        const float fd = float(D->head_d[g]);
-        if (j >= 0) {
-          const float r = __fdiv_rn(S1, S0);
-          P::add(q_g1, fd * r);
-          P::add(q_g2, fd * (__fdiv_rn(S2, S0) - r * r));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          r_g1 += __shfl_down_sync(0xffffffffu, r_g1, off);
+          r_g2 += __shfl_down_sync(0xffffffffu, r_g2, off);
         }
-        if (need_ll) r_ll += dg * log(P::to64(s0));
-        if (F.out_S0) { F.out_S0[g] = P::to64(s0); F.out_S1[g] = P::to64(s1); }
+      }
+      if (need_ll) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r_ll += __shfl_down_sync(0xffffffffu, r_ll, off);
       }
     }
-    if constexpr (sizeof(T) == 4) {
-      r_g1 = P::to64(q_g1);
-      r_g2 = P::to64(q_g2);
-    }
-    double red[3] = {r_g1, r_g2, r_ll};
-    block_sum<3>(red, s_red);
+    if (lane == 0) { s_wred[0][warp] = r_g1; s_wred[1][warp] = r_g2; s_wred[2][warp] = r_ll; }
+    __syncthreads();
     if (tid == 0) {
-      F.part[3 * t + 0] = red[0]; F.part[3 * t + 1] = red[1]; F.part[3 * t + 2] = red[2];
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+      for (int ww = 0; ww < kThreads / 32; ++ww) { p0 += s_wred[0][ww]; p1 += s_wred[1][ww]; p2 += s_wred[2][ww]; }
+      F.part[3 * t + 0] = p0; F.part[3 * t + 1] = p1; F.part[3 * t + 2] = p2;
       __threadfence();
       const uint32_t prev = atomicAdd(&ctl->done_tiles, 1u);
       s_last = prev == uint32_t(T_ - 1);
@@ -568,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
       if (tid == 0) {
         const double G1 = acc[0], G2 = acc[1], LL = acc[2];
         if (ctl->error != 0) {
+          if (mode == kModeFit && ctl->state == kRunning) atomicSub(&lc->active, 1);
           ctl->state = kError;
         } else if (mode == kModeEval) {
           ctl->out_g1 = -D->dX[j] + G1;
@@ -588,6 +670,9 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
             } else if (ctl->sweep >= F.max_sweeps) {
               ctl->state = kMaxed;
               stop = true;
+            }
+            if (stop) {
+              atomicSub(&lc->active, 1);
             } else {
               ctl->obj_prev = obj;
             }
@@ -626,9 +711,13 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
   }
   if (tid == 0) {
     __threadfence();
-    if (atomicAdd(&lc->exited, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&lc->exited, 1u) == gridDim.x - 1) {   // the last CTA of this launch
       lc->ticket = 0u;
       lc->exited = 0u;
+      if (mode == kModeFit && cond) {
+        const long long left = --lc->budget;
+        if (*reinterpret_cast<volatile int32_t *>(&lc->active) <= 0 || left <= 0) cudaGraphSetConditional(cond, 0u);
+      }
     }
   }
 }
@@ -663,48 +752,50 @@ __global__ void fill_v_kernel(const DevFit *__restrict__ fit, int64_t M, const u
 }
 
 // ------------------------------------------------------------------ launchers
-template <class P>
-static size_t smem_bytes(int valued) {
-  return valued ? Smem<P>::bytes_valued : Smem<P>::bytes_binary;
-}
-
-template <class P>
-static int max_grid_impl(int valued) {
-  static int cached[2] = {0, 0};
-  if (cached[valued]) return cached[valued];
-  // the attribute is a per-kernel maximum: always allow the larger (valued-X) layout, so a
-  // launch of either variant fits whichever was configured first
-  if (cudaFuncSetAttribute(ccd_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Smem<P>::bytes_valued)) !=
-      cudaSuccess)
+template <class P, int NV>
+static int max_grid_impl() {
+  static int cached = 0;
+  if (cached) return cached;
+  const size_t sm = Smem<P, NV>::bytes;
+  if (cudaFuncSetAttribute(ccd_kernel<P, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess)
     return -1;
-  const size_t sm = smem_bytes<P>(valued);
   int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ccd_kernel<P>, kThreads, sm) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ccd_kernel<P, NV>, kThreads, sm) != cudaSuccess) return -1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cached[valued] = (per_sm > 0 ? per_sm : 1) * nsm;
-  return cached[valued];
+  cached = (per_sm > 0 ? per_sm : 1) * nsm;
+  return cached;
 }
 
 int ccd_max_grid(int precision, int valued) {
-  return precision == COX_FP32C ? max_grid_impl<PF32C>(valued) : max_grid_impl<PF64>(valued);
+  if (precision == COX_FP32C) return valued ? max_grid_impl<PF32C, 3>() : max_grid_impl<PF32C, 2>();
+  return valued ? max_grid_impl<PF64, 3>() : max_grid_impl<PF64, 2>();
 }
 
-int ccd_tile(int precision) { return precision == COX_FP32C ? Smem<PF32C>::TILE : Smem<PF64>::TILE; }
+int ccd_tile(int precision) { return precision == COX_FP32C ? kThreads * PF32C::ITEMS : kThreads * PF64::ITEMS; }
+
+template <class P, int NV>
+static int launch_impl(const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode, int j_eval, cudaStream_t s,
+                       unsigned long long cond) {
+  if (max_grid_impl<P, NV>() < 0) return COX_E_CUDA;
+  ccd_kernel<P, NV><<<grid, kThreads, Smem<P, NV>::bytes, s>>>(fits, items, lc, mode, j_eval, cond);
+  return COX_OK;
+}
 
 int launch_ccd(int precision, const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode, int j_eval,
-               int valued, void *stream) {
+               int valued, void *stream, unsigned long long cond) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs == cudaStreamCaptureStatusNone) count_launches(1);   // graph nodes are counted per replay
-  if (precision == COX_FP32C) {
-    if (max_grid_impl<PF32C>(valued) < 0) return COX_E_CUDA;
-    ccd_kernel<PF32C><<<grid, kThreads, smem_bytes<PF32C>(valued), s>>>(fits, items, lc, mode, j_eval, valued);
-  } else {
-    if (max_grid_impl<PF64>(valued) < 0) return COX_E_CUDA;
-    ccd_kernel<PF64><<<grid, kThreads, smem_bytes<PF64>(valued), s>>>(fits, items, lc, mode, j_eval, valued);
-  }
+  int rc;
+  if (precision == COX_FP32C)
+    rc = valued ? launch_impl<PF32C, 3>(fits, items, lc, grid, mode, j_eval, s, cond)
+                : launch_impl<PF32C, 2>(fits, items, lc, grid, mode, j_eval, s, cond);
+  else
+    rc = valued ? launch_impl<PF64, 3>(fits, items, lc, grid, mode, j_eval, s, cond)
+                : launch_impl<PF64, 2>(fits, items, lc, grid, mode, j_eval, s, cond);
+  if (rc) return rc;
   return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
 }
 

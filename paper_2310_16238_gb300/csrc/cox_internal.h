@@ -80,12 +80,14 @@ struct DevFit {
   double lambda, l2_var, tol, shift;
 };
 
-// Persistent-launch ticket counter.
+// Persistent-launch control: ticket counter, work-list size, and (for the device-driven
+// sweep loop) the number of fits still running and a hard bound on further launches.
 struct LaunchCtl {
   uint32_t ticket;
   uint32_t exited;
   int32_t n_items;
-  int32_t pad;
+  int32_t active;         // running fits in the work list; 0 ends a conditional sweep loop
+  int64_t budget;         // launches left before a conditional sweep loop is ended regardless
 };
 
 enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
@@ -94,8 +96,10 @@ enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
 void count_launches(int64_t n);
 
 // Host-visible launchers (ccd.cu).
+// `cond`: handle of the enclosing conditional WHILE graph node (0 = none). The kernel sets it
+// to 0 once no fit in the work list is running or the launch budget is spent.
 int launch_ccd(int precision, const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode,
-               int j_eval, int valued, void *stream);
+               int j_eval, int valued, void *stream, unsigned long long cond = 0);
 int ccd_max_grid(int precision, int valued);
 int ccd_tile(int precision);
 int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream);

@@ -91,7 +91,12 @@ typedef struct {
  *   max_sweeps sweep limit (COX_W_NOT_CONVERGED when reached)
  *   precision  COX_FP64 | COX_FP32C
  *   stream     cudaStream_t (NULL = default stream)
- *   tile       positions per tile, 0 = library default; a multiple of 1024 otherwise */
+ *   tile       positions per tile of the streaming kernel, 0 = library default; a multiple
+ *              of 32 in [1024, 4096 (FP64) or 8192 (FP32C)] otherwise
+ *   engine     COX_ENGINE_AUTO: the resident kernel when the data qualify (binary X and the
+ *              whole risk sequence fits the GPU's shared memory), else streaming;
+ *              COX_ENGINE_STREAM / COX_ENGINE_RESIDENT force one (RESIDENT fails with
+ *              COX_E_INVALID when the data do not qualify) */
 typedef struct {
   int32_t penalty;
   int32_t precision;
@@ -102,7 +107,11 @@ typedef struct {
   int32_t max_sweeps;
   int32_t tile;
   void *stream;
+  int32_t engine;
+  int32_t reserved;
 } cox_options;
+
+enum { COX_ENGINE_AUTO = 0, COX_ENGINE_STREAM = 1, COX_ENGINE_RESIDENT = 2 };
 
 typedef struct {
   int32_t sweeps;          /* full sweeps over the p coordinates */

@@ -22,6 +22,7 @@ COX_E_INVALID, COX_E_UNSORTED, COX_E_OOM, COX_E_CUDA = -1, -2, -3, -4
 COX_E_TIMEOUT, COX_E_ADMISSION, COX_E_RANGE, COX_E_NOT_FOUND, COX_E_BUSY = -5, -6, -7, -8, -9
 COX_PEN_NONE, COX_PEN_L1, COX_PEN_L2 = 0, 1, 2
 COX_FP64, COX_FP32C = 0, 1
+COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT = 0, 1, 2
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
@@ -44,7 +45,7 @@ class cox_data(C.Structure):
 class cox_options(C.Structure):
     _fields_ = [("penalty", C.c_int32), ("precision", C.c_int32), ("lam", C.c_double), ("l2_var", C.c_double),
                 ("penalize", C.c_void_p), ("tol", C.c_double), ("max_sweeps", C.c_int32), ("tile", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("engine", C.c_int32), ("reserved", C.c_int32)]
 
 
 class cox_fit_info(C.Structure):
@@ -159,21 +160,21 @@ def make_data(data):
     return d, keep
 
 
-def make_options(opts=None, precision=COX_FP64, stream=None, tile=0):
+def make_options(opts=None, precision=COX_FP64, stream=None, tile=0, engine=COX_ENGINE_AUTO):
     """cox_options from a ``synth.CoxOptions``-like object."""
     pen = None
     if opts is not None and getattr(opts, "penalize", None) is not None:
         pen = _host(opts.penalize, np.uint8)
     o = cox_options(int(getattr(opts, "penalty", COX_PEN_NONE)), int(precision), float(getattr(opts, "lam", 0.0)),
                     float(getattr(opts, "l2_var", 1.0)), _ptr(pen), float(getattr(opts, "tol", 1e-8)),
-                    int(getattr(opts, "max_sweeps", 1000)), int(tile), stream)
+                    int(getattr(opts, "max_sweeps", 1000)), int(tile), stream, int(engine), 0)
     return o, pen
 
 
 # ---------------------------------------------------------------- ABI-named wrappers
-def cox_create(data, opts=None, precision=COX_FP64, stream=None, tile=0):
+def cox_create(data, opts=None, precision=COX_FP64, stream=None, tile=0, engine=COX_ENGINE_AUTO):
     d, keep = make_data(data)
-    o, pen = make_options(opts, precision, stream, tile)
+    o, pen = make_options(opts, precision, stream, tile, engine)
     h = C.c_void_p()
     _check(lib().cox_create(C.byref(d), C.byref(o), C.byref(h)))
     _P_CACHE[h.value] = int(data.p)
@@ -310,10 +311,10 @@ def _num_cols(h):
 class Handle:
     """Owning wrapper: ``Handle(data, opts, precision=COX_FP64)`` then ``fit()``, ``loglik(beta)``..."""
 
-    def __init__(self, data, opts=None, precision=COX_FP64, stream=None, tile=0, _raw=None):
+    def __init__(self, data, opts=None, precision=COX_FP64, stream=None, tile=0, engine=COX_ENGINE_AUTO, _raw=None):
         if _raw is None:
             d, self._keep = make_data(data)
-            o, self._pen = make_options(opts, precision, stream, tile)
+            o, self._pen = make_options(opts, precision, stream, tile, engine)
             h = C.c_void_p()
             _check(lib().cox_create(C.byref(d), C.byref(o), C.byref(h)))
             self.h = h

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -64,6 +66,9 @@ struct cox_handle {
   uint8_t *penalize = nullptr; // device copy of the penalty mask
   double *gout = nullptr;
   double *S0 = nullptr, *S1 = nullptr;
+  // resident-kernel scratch (allocated when the data qualify)
+  uint32_t *r_tstat = nullptr, *r_pstat = nullptr;
+  double *r_tval = nullptr, *r_pval = nullptr;
   std::string err = "no error";
 };
 
@@ -97,6 +102,7 @@ int resolve_stream(cox_handle *h) {
 
 int check_options(const cox_options *o) {
   if (!o) return COX_OK;
+  if (o->engine < COX_ENGINE_AUTO || o->engine > COX_ENGINE_RESIDENT) return COX_E_INVALID;
   if (o->penalty < COX_PEN_NONE || o->penalty > COX_PEN_L2) return COX_E_INVALID;
   if (o->precision != COX_FP64 && o->precision != COX_FP32C) return COX_E_INVALID;
   if (o->penalty == COX_PEN_L1 && !(o->lambda >= 0.0)) return COX_E_INVALID;
@@ -143,6 +149,14 @@ int alloc_fit_state(cox_handle *h) {
       !h->hfit.tstat || !h->hfit.tval || !h->hfit.part || !h->gout || !h->S0 || !h->S1 || !h->penalize)
     return fail(h, COX_E_OOM, "device allocation failed for the fit state");
   h->hfit.ctl = h->ctl;
+  if (const int RT = h->sd->prep.res_T) {
+    h->r_tstat = static_cast<uint32_t *>(B.get(RT * sizeof(uint32_t)));
+    h->r_tval = static_cast<double *>(B.get(6 * RT * sizeof(double)));
+    h->r_pstat = static_cast<uint32_t *>(B.get(2 * RT * sizeof(uint32_t)));
+    h->r_pval = static_cast<double *>(B.get(6 * RT * sizeof(double)));
+    if (!h->r_tstat || !h->r_tval || !h->r_pstat || !h->r_pval)
+      return fail(h, COX_E_OOM, "device allocation failed for the resident state");
+  }
   if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
   if (cudaMemsetAsync(h->hfit.v, 0, (M + tile_k + 64) * sv, h->stream) != cudaSuccess) return cuda_fail(h, "memset");
@@ -304,6 +318,82 @@ int copy_out(cox_handle *h, double *dst, const double *src, int64_t count) {
   return COX_OK;
 }
 
+// The whole fit in one cooperative launch of the resident kernel (state already initialized).
+int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
+  const DevData &d = D(h);
+  const Prepared &P = h->sd->prep;
+  const int RT = P.res_T;
+  cudaStream_t s = h->stream;
+  if (cudaMemsetAsync(h->r_tstat, 0, RT * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(h->r_pstat, 0, 2 * RT * sizeof(uint32_t), s) != cudaSuccess)
+    return cuda_fail(h, "memset");
+  ResParams prm{};
+  prm.F = h->hfit;
+  prm.D = d;
+  prm.tile_lo = P.res_tile_lo;
+  prm.tile_g = P.res_tile_g;
+  prm.tile_k = P.res_tile_k;
+  prm.col_tile = P.res_col_tile;
+  prm.tstat = h->r_tstat;
+  prm.tval = h->r_tval;
+  prm.pstat = h->r_pstat;
+  prm.pval = h->r_pval;
+  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
+  // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
+  const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
+  const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
+  BufferSet trbuf;
+  if (tr_steps > 0) {
+    prm.trace = static_cast<uint64_t *>(trbuf.get(2 * tr_steps * 8 * sizeof(uint64_t)));
+    prm.trace_steps = prm.trace ? tr_steps : 0;
+    if (prm.trace) cudaMemsetAsync(prm.trace, 0, 2 * tr_steps * 8 * sizeof(uint64_t), s);
+  }
+  if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
+    return cuda_fail(h, "event create");
+  cudaEventRecord(h->ev0, s);
+  if (launch_resident(h->sd->precision, prm, RT, s)) return cuda_fail(h, "resident launch");
+  cudaEventRecord(h->ev1, s);
+  int rc;
+  if ((rc = read_ctl(h))) return rc;
+  if (prm.trace_steps > 0) {
+    std::vector<uint64_t> tr(size_t(2 * prm.trace_steps * 8));
+    cudaMemcpy(tr.data(), prm.trace, tr.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    const char *names[5] = {"update+scan", "raking+look-back", "ratios+publish", "all-gather", "step"};
+    for (int c = 0; c < 2; ++c) {
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      int64_t n = 0;
+      for (int64_t k = 1; k < prm.trace_steps; ++k) {
+        const uint64_t *r = &tr[size_t((c * prm.trace_steps + k) * 8)];
+        if (!r[0] || !r[5]) continue;
+        for (int q = 0; q < 5; ++q) acc[q] += double(r[q + 1] - r[q]);
+        acc[5] += double(r[5] - r[0]);
+        ++n;
+      }
+      std::fprintf(stderr, "[phase trace] CTA %s, %lld steps, mean ns:", c == 0 ? "first" : "last", (long long)n);
+      for (int q = 0; q < 5 && n; ++q) std::fprintf(stderr, " %s %.0f", names[q], acc[q] / n);
+      if (n) std::fprintf(stderr, " | step %.0f\n", acc[5] / n);
+    }
+  }
+  if ((rc = device_error(h))) return rc;
+  const FitCtl &c = *h->h_ctl;
+  if (c.state == kRunning) return fail(h, COX_E_INVALID, "cox_fit: the resident kernel stopped before the fit did");
+  rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
+  if (info) {
+    info->sweeps = c.sweep;
+    info->converged = c.state == kConverged;
+    info->coord_updates = c.coord_updates;
+    info->loglik = c.loglik;
+    info->objective = c.obj;
+    info->status = rc;
+    info->step_launches = 1;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->sweep_ms = ms;
+  }
+  const int rc2 = copy_out(h, beta_out, h->hfit.beta, d.p);
+  return rc2 ? rc2 : rc;
+}
+
 }  // namespace
 
 // =================================================================== ABI
@@ -415,6 +505,10 @@ int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *
     }
     return copy_out(h, beta_out, h->hfit.beta, d.p);
   }
+  const bool resident = h->opts.engine != COX_ENGINE_STREAM && h->sd->prep.res_T > 0;
+  if (h->opts.engine == COX_ENGINE_RESIDENT && !resident)
+    return fail(h, COX_E_INVALID, "cox_fit: the data do not qualify for the resident kernel (binary X, sequence within shared memory)");
+  if (resident) return fit_resident(h, beta_out, info);
   const int len = kSweepBody;
   if ((rc = build_graph(h, len))) return rc;
   // the step-launch budget bounds the device-driven loop whatever happens on the device

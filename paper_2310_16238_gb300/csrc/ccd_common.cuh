@@ -1,0 +1,171 @@
+// Device building blocks shared by the coordinate-step kernels (ccd.cu, ccd_resident.cu):
+// PTX memory-ordering helpers, the FP64 / compensated-FP32 precision policies, the §2.4 step
+// rule and the exp(eta) value written at a risk-sequence position.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cox.h"
+#include "cox_internal.h"
+
+namespace coxgb {
+
+// ------------------------------------------------------------------ PTX helpers
+static __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+static __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+static __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Acquire side of a release/acquire pair that was observed with relaxed loads.
+static __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+static __device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+static __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ------------------------------------------------------------------ precision policies
+// FP64: values, scans, ratios in double.
+struct PF64 {
+  using T = double;
+  static constexpr int ITEMS = 16;
+  struct Acc { double s; };
+  __device__ static Acc zero() { return {0.0}; }
+  __device__ static void add(Acc &a, double x) { a.s = a.s + x; }
+  __device__ static Acc comb(Acc a, Acc b) { return {a.s + b.s}; }
+  __device__ static double to64(Acc a) { return a.s; }
+  __device__ static Acc from64(double x) { return {x}; }
+  __device__ static Acc shfl_down(Acc a, int off) { return {__shfl_down_sync(0xffffffffu, a.s, off)}; }
+};
+
+// FP32 with a compensation term: a = s + c, additions by Knuth's TwoSum (error-free
+// transformation, TAOCP vol. 2 §4.2.2), so tile sums carry ~2x float precision.
+struct PF32C {
+  using T = float;
+  static constexpr int ITEMS = 32;
+  struct Acc { float s, c; };
+  __device__ static Acc zero() { return {0.0f, 0.0f}; }
+  __device__ static void add(Acc &a, float x) {
+    float t = __fadd_rn(a.s, x);
+    float bp = __fsub_rn(t, a.s);
+    float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+  }
+  __device__ static Acc comb(Acc a, Acc b) {
+    Acc r = a;
+    add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+  }
+  __device__ static double to64(Acc a) { return (double)a.s + (double)a.c; }
+  __device__ static Acc from64(double x) {
+    float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
+  }
+  __device__ static Acc shfl_down(Acc a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.s, off), __shfl_down_sync(0xffffffffu, a.c, off)};
+  }
+};
+
+constexpr long long kSpinBudget = 4000000000LL;   // ~2 s of SM clock for any device-side wait
+
+// ------------------------------------------------------------------ the coordinate step
+// §2.4, with these readings where the paper is silent: L2 adds beta/sigma^2 and 1/sigma^2; L1 uses the
+// directional derivatives g' +- gamma at 0 and g' + gamma sgn(beta) elsewhere; the Newton
+// step is clipped to the trust half-width, an L1 step that would cross 0 stops at 0, and
+// the half-width becomes max(2 |step|, half-width / 2). g'' <= 0 skips the coordinate.
+static __device__ double ccd_step_rule(double g1, double g2, double b, double *tr, int penalty, double lambda,
+                                double l2_var, int penalized) {
+  double gamma = 0.0;
+  if (penalized && penalty == COX_PEN_L2) {
+    g1 = g1 + b / l2_var;
+    g2 = g2 + 1.0 / l2_var;
+  }
+  if (penalized && penalty == COX_PEN_L1) gamma = lambda;
+  double s;
+  if (!(g2 > 0.0) || !isfinite(g1) || !isfinite(g2)) {
+    s = 0.0;
+  } else if (gamma > 0.0) {
+    if (b == 0.0) {
+      if (g1 + gamma < 0.0) s = -(g1 + gamma) / g2;
+      else if (g1 - gamma > 0.0) s = -(g1 - gamma) / g2;
+      else s = 0.0;
+    } else {
+      s = -(g1 + (b > 0.0 ? gamma : -gamma)) / g2;
+    }
+  } else {
+    s = -g1 / g2;
+  }
+  double t = *tr;
+  if (fabs(s) > t) s = s > 0.0 ? t : -t;
+  if (gamma > 0.0 && b != 0.0) {
+    double nb = b + s;
+    if ((b > 0.0 && nb < 0.0) || (b < 0.0 && nb > 0.0)) s = -b;
+  }
+  double a2 = 2.0 * fabs(s), h = 0.5 * t;
+  *tr = a2 > h ? a2 : h;
+  return s;
+}
+
+// Block-wide sum of NV doubles in a fixed order (deterministic for fixed inputs).
+template <int NV>
+static __device__ void block_sum(double (&v)[NV], double *scratch /* [NV*32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double x = lane < (kThreads / 32) ? scratch[i * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      v[i] = x;   // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// value written at a position for exp(eta - shift); exits hold the negative
+template <class P>
+static __device__ __forceinline__ typename P::T make_v(double eta, double shift, bool exitp, int32_t *err) {
+  if constexpr (sizeof(typename P::T) == 8) {
+    double e = exp(eta - shift);
+    return exitp ? -e : e;
+  } else {
+    double a = eta - shift;
+    if (!(fabs(a) < 80.0)) atomicExch(err, COX_E_RANGE);
+    float e = expf(__double2float_rn(a));
+    return exitp ? -e : e;
+  }
+}
+
+template <class Acc, class P, int NV>
+static __device__ __forceinline__ void comb_n(Acc (&a)[NV], const Acc (&b)[NV]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) a[i] = P::comb(a[i], b[i]);
+}
+
+}  // namespace coxgb

@@ -92,6 +92,20 @@ struct LaunchCtl {
 
 enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
 
+// Arguments of the resident kernel (ccd_resident.cu), passed by value.
+struct ResParams {
+  DevFit F;               // the fit (its d pointer is not used)
+  DevData D;              // the data descriptor
+  const int32_t *tile_lo, *tile_g, *tile_k, *col_tile;   // resident tile plan: one tile per CTA
+  uint32_t *tstat;        // [T] look-back status
+  double *tval;           // [6T] look-back values
+  uint32_t *pstat;        // [2T] partial tags, double-buffered by step parity
+  double *pval;           // [2T*3] partials
+  int64_t max_steps;      // coordinate steps this launch may take
+  uint64_t *trace;        // optional [2][trace_steps][8] phase timestamps (ns) of the first and last CTA
+  int64_t trace_steps;
+};
+
 // Count of kernels launched by the library (every launcher adds to it).
 void count_launches(int64_t n);
 
@@ -104,5 +118,12 @@ int ccd_max_grid(int precision, int valued);
 int ccd_tile(int precision);
 int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream);
 int launch_fill_v(int precision, const DevFit *fit_dev, int64_t M, const uint32_t *exit_bits, void *stream);
+
+// Resident kernel (ccd_resident.cu): positions per CTA, head capacity per CTA, largest
+// cooperative grid (0 when unsupported), launch.
+int res_tile(int precision);
+int res_head_cap();
+int res_max_grid(int precision);
+int launch_resident(int precision, const ResParams &prm, int grid, void *stream);
 
 }  // namespace coxgb

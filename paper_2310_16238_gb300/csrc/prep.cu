@@ -758,6 +758,66 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   D.tile_k = tile_k;
   D.col_tile = col_tile;
   out->h_tile_lo = h_lo;
+
+  // resident plan: binary X, at most one tile per co-resident CTA, each tile within the
+  // kernel's shared-memory capacity and head capacity
+  const int res_cap_grid = res_max_grid(precision);
+  if (in->val == nullptr && p > 0 && D.M > 0 && res_cap_grid > 0) {
+    // tiles of at most `per` positions, shortened to hold at most the head capacity
+    auto res_plan = [&](int64_t per) {
+      std::vector<int32_t> rl;
+      int64_t cur = 0;
+      size_t hh = 0;
+      const size_t cap = size_t(res_head_cap());
+      while (cur < D.M) {
+        rl.push_back(int32_t(cur));
+        int64_t hi = std::min<int64_t>(cur + per, D.M);
+        while (hh < h_head.size() && h_head[hh] < cur) ++hh;
+        if (hh + cap < h_head.size() && h_head[hh + cap] < hi) {
+          const int64_t cut = (int64_t(h_head[hh + cap]) / 32) * 32;
+          if (cut > cur) hi = cut;
+        }
+        cur = hi;
+      }
+      rl.push_back(int32_t(D.M));
+      return rl;
+    };
+    // the shortest tile length (best balance across CTAs) whose plan fits the grid
+    const int64_t pmax = res_tile(precision);
+    int64_t plo = ((D.M + res_cap_grid - 1) / res_cap_grid + 31) / 32 * 32, phi = pmax;
+    std::vector<int32_t> rl;
+    if (plo <= pmax && int64_t(res_plan(pmax).size()) - 1 <= res_cap_grid) {
+      while (plo < phi) {   // plan size is nonincreasing in the tile length
+        const int64_t mid = ((plo + phi) / 2) / 32 * 32;
+        if (mid <= plo) break;
+        if (int64_t(res_plan(mid).size()) - 1 <= res_cap_grid) phi = mid;
+        else plo = mid + 32;
+      }
+      rl = res_plan(phi);
+      if (int64_t(rl.size()) - 1 > res_cap_grid) rl.clear();
+    }
+    const int32_t RT = rl.empty() ? 0 : int32_t(rl.size()) - 1;
+    if (RT > 0 && RT <= res_cap_grid) {
+      {
+        int32_t *r_lo = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+        int32_t *r_g = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+        int32_t *r_k = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+        int32_t *r_ct = static_cast<int32_t *>(B.get(int64_t(p) * (RT + 1) * sizeof(int32_t)));
+        if (!r_lo || !r_g || !r_k || !r_ct) return COX_E_OOM;
+        cudaMemcpyAsync(r_lo, rl.data(), (RT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        count_launches(1);
+        tile_tables_kernel<<<grid_for(int64_t(RT) + 1), 256, 0, s>>>(RT, r_lo, head_pos, int32_t(G), cut_pos, int32_t(K), r_g,
+                                                                     r_k);
+        count_launches(1);
+        col_tile_kernel<<<grid_for(int64_t(p) * (RT + 1)), 256, 0, s>>>(p, RT, col_ptr, idx, r_lo, r_ct);
+        out->res_T = RT;
+        out->res_tile_lo = r_lo;
+        out->res_tile_g = r_g;
+        out->res_tile_k = r_k;
+        out->res_col_tile = r_ct;
+      }
+    }
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     *err = "cox_create: table kernels failed";
     return COX_E_CUDA;

@@ -42,6 +42,9 @@ struct Prepared {
   std::vector<int64_t> h_col_ptr;       // position-space CSC pointers
   std::vector<int32_t> h_tile_lo;
   int32_t *strata_start = nullptr;      // [K+1] device
+  // resident plan (one tile per CTA of the resident kernel); res_T == 0 when not eligible
+  int32_t res_T = 0;
+  int32_t *res_tile_lo = nullptr, *res_tile_g = nullptr, *res_tile_k = nullptr, *res_col_tile = nullptr;
   int32_t *g_time = nullptr;            // [G] device
   int32_t *g_stratum = nullptr;         // [G] device
 };

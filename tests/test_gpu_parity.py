@@ -228,3 +228,52 @@ def test_device_resident_inputs():
         ba, ia = a.fit()
         bb, ib = b.fit()
     assert ia["sweeps"] == ib["sweeps"] and _rel_beta(bb, ba) <= 1e-12
+
+
+@pytest.mark.parametrize("name,data,opts", CASES, ids=IDS)
+def test_engines_agree_with_oracle(name, data, opts):
+    """The streaming kernel (one launch per coordinate step) and the resident kernel (the whole
+    fit in one cooperative launch, values held in shared memory) follow the oracle's CCD path."""
+    results = {}
+    for eng in (cox.COX_ENGINE_STREAM, cox.COX_ENGINE_AUTO):
+        with cox.Handle(data, opts, engine=eng) as h:
+            results[eng] = h.fit()
+    for eng, (beta, info) in results.items():
+        ob, oinfo = oracle.fit(data, opts, max_sweeps=info["sweeps"])
+        assert _rel_beta(beta, ob) <= 1e-9, (eng, _rel_beta(beta, ob))
+        assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * _ll_scale(data, ob, oinfo["loglik"])
+    if data.val is None:
+        assert results[cox.COX_ENGINE_AUTO][1]["step_launches"] == 1   # binary X runs resident
+
+
+def test_resident_engine_rejects_valued_x():
+    d, o = synth.plain_dense(n=200, p=3, seed=2)
+    with cox.Handle(d, o, engine=cox.COX_ENGINE_RESIDENT) as h:
+        with pytest.raises(cox.CoxError) as e:
+            h.fit()
+    assert e.value.code == cox.COX_E_INVALID
+
+
+@pytest.mark.parametrize("name,data,opts", _medium_cases()[:2], ids=lambda x: x if isinstance(x, str) else "")
+def test_resident_fp32c(name, data, opts):
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_RESIDENT) as h:
+        beta, info = h.fit()
+    assert info["step_launches"] == 1
+    ob, oinfo = oracle.fit(data, opts)
+    assert _rel_beta(beta, ob) <= 1e-5
+    assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-7 * _ll_scale(data, ob, oinfo["loglik"])
+
+
+def test_resident_then_evaluations_consistent():
+    """After a resident fit, the evaluations (which use the streaming kernel on the same state)
+    see the written-back values: the gradient at the fitted beta satisfies the KKT conditions."""
+    data, o = synth.stratified_sparse(n=40000, p=12, k=7, n_support=5, event_frac=0.1, dens_lo=0.01, dens_hi=0.3,
+                                      admin_days=365, seed=77)
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=0.5, tol=1e-14, max_sweeps=500)
+    with cox.Handle(data, o) as h:
+        beta, info = h.fit()
+        assert info["step_launches"] == 1
+        g1, _ = h.gradient(beta)
+        ll = h.loglik(beta)
+    assert np.max(np.abs(g1 + beta / 0.5)) < 1e-6
+    assert abs(ll - info["loglik"]) <= 1e-11 * abs(ll)

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header():
     # int64 + 2*int32 + 7 pointers
     assert C.sizeof(cox.cox_data) == 8 + 8 + 7 * 8
     # 2*int32, 2 doubles, ptr, double, 2*int32, ptr
-    assert C.sizeof(cox.cox_options) == 8 + 16 + 8 + 8 + 8 + 8
+    assert C.sizeof(cox.cox_options) == 8 + 16 + 8 + 8 + 8 + 8 + 8
     assert C.sizeof(cox.cox_fit_info) == 8 + 8 + 16 + 8 + 16
 
 

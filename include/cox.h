@@ -123,6 +123,8 @@ typedef struct {
   int32_t reserved;
   int64_t step_launches;   /* coordinate-step kernel launches issued by the sweep loop */
   double sweep_ms;         /* CUDA-event time of the sweep loop on the fit's stream */
+  double wait_ms;          /* serving only: submission to admission (device memory granted) */
+  double total_ms;         /* serving only: submission to result ready */
 } cox_fit_info;
 
 typedef struct cox_handle cox_handle;
@@ -219,6 +221,47 @@ int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *o
  * whose work overlaps on the GPU race with each other: issue them one at a time (same stream,
  * or synchronized). Other arguments, errors and stream behaviour as cox_segscan. */
 int cox_segscan_noalloc(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of fit requests. Requests of any size and layout are submitted from any
+ * thread; a preparation thread admits them in arrival order while their device footprint
+ * (cox_footprint) fits the memory budget and the in-flight limit, prepares them on its own
+ * stream (overlapping the fits in flight), and a run thread advances every in-flight fit by one
+ * coordinate step per persistent launch (each fit on its own coordinate and sweep), replayed
+ * from a CUDA graph; between replays finished fits are retired (their memory returned) and newly
+ * prepared ones join. Each fit's state (eta, exp(eta), beta, scan state) stays on the device
+ * from admission to retirement. */
+typedef struct cox_server cox_server;
+typedef struct {
+  size_t memory_budget;    /* bytes of device memory for admitted requests; 0 = 80 % of free memory */
+  int32_t max_active;      /* fits prepared or in flight at once; 0 = 256 */
+  int32_t precision;       /* COX_FP64 | COX_FP32C for every request */
+  int32_t steps_per_replay;/* coordinate steps per graph replay; 0 = 64 */
+  int32_t reserved;
+} cox_server_options;
+typedef struct {
+  int64_t submitted, completed, failed;
+  int32_t queued, preparing, running, done_unpolled;
+  size_t bytes_in_use, memory_budget;
+  int64_t replays, step_launches;
+} cox_server_stats;
+
+int cox_server_create(const cox_server_options *opts, cox_server **out);
+/* Queue one fit; `data` arrays may be host or device memory and are copied before return.
+ * opts->stream and opts->precision are ignored (the server's apply). *request_id identifies it.
+ * Errors: COX_E_INVALID (bad arguments), COX_E_ADMISSION (footprint above the whole budget). */
+int cox_server_submit(cox_server *s, const cox_data *data, const cox_options *opts, uint64_t *request_id);
+/* Result of a finished request: beta_out (p doubles, host or device) and *info (may be NULL);
+ * returns the fit's status and forgets the request. COX_E_BUSY while it is queued or running,
+ * COX_E_NOT_FOUND for an unknown or already collected id. */
+int cox_server_poll(cox_server *s, uint64_t request_id, double *beta_out, cox_fit_info *info);
+/* As cox_server_poll, but blocks up to timeout_s seconds (< 0: forever) for the result. */
+int cox_server_wait(cox_server *s, uint64_t request_id, double timeout_s, double *beta_out, cox_fit_info *info);
+/* Cancel a queued or running request (its memory is returned at the next replay boundary). */
+int cox_server_cancel(cox_server *s, uint64_t request_id);
+int cox_server_stats_get(cox_server *s, cox_server_stats *out);
+/* Stops both threads (requests still in flight are abandoned) and releases everything. */
+void cox_server_destroy(cox_server *s);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,8 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT = 0, 1, 2
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
            "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan",
-           "cox_segscan_noalloc"]
+           "cox_segscan_noalloc", "cox_server_create", "cox_server_submit", "cox_server_poll",
+           "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
 
 class CoxError(RuntimeError):
@@ -51,12 +52,29 @@ class cox_options(C.Structure):
 class cox_fit_info(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("coord_updates", C.c_int64),
                 ("loglik", C.c_double), ("objective", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32),
-                ("step_launches", C.c_int64), ("sweep_ms", C.c_double)]
+                ("step_launches", C.c_int64), ("sweep_ms", C.c_double), ("wait_ms", C.c_double),
+                ("total_ms", C.c_double)]
 
     def as_dict(self):
         return dict(sweeps=self.sweeps, converged=bool(self.converged), coord_updates=self.coord_updates,
                     loglik=self.loglik, objective=self.objective, status=self.status,
-                    step_launches=self.step_launches, sweep_ms=self.sweep_ms)
+                    step_launches=self.step_launches, sweep_ms=self.sweep_ms, wait_ms=self.wait_ms,
+                    total_ms=self.total_ms)
+
+
+class cox_server_options(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("max_active", C.c_int32), ("precision", C.c_int32),
+                ("steps_per_replay", C.c_int32), ("reserved", C.c_int32)]
+
+
+class cox_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int32),
+                ("preparing", C.c_int32), ("running", C.c_int32), ("done_unpolled", C.c_int32),
+                ("bytes_in_use", C.c_size_t), ("memory_budget", C.c_size_t), ("replays", C.c_int64),
+                ("step_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -95,6 +113,14 @@ def lib():
             L.cox_launch_count.restype = i64
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
             L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
+            L.cox_server_create.argtypes = [C.POINTER(cox_server_options), C.POINTER(vp)]
+            L.cox_server_submit.argtypes = [vp, C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_uint64)]
+            L.cox_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(cox_fit_info)]
+            L.cox_server_wait.argtypes = [vp, C.c_uint64, C.c_double, vp, C.POINTER(cox_fit_info)]
+            L.cox_server_cancel.argtypes = [vp, C.c_uint64]
+            L.cox_server_stats_get.argtypes = [vp, C.POINTER(cox_server_stats)]
+            L.cox_server_destroy.argtypes = [vp]
+            L.cox_server_destroy.restype = None
             _lib = L
             _install_torch_allocator(L)
     return _lib
@@ -374,3 +400,66 @@ class Handle:
 
 def batch_fit(handles: Sequence[Handle], beta0=None):
     return cox_batch_fit([h.h for h in handles], beta0)
+
+
+class Server:
+    """Continuous-batching fit server (cox_server_*): submit from any thread, poll or wait."""
+
+    def __init__(self, memory_budget=0, max_active=0, precision=COX_FP64, steps_per_replay=0):
+        o = cox_server_options(int(memory_budget), int(max_active), int(precision), int(steps_per_replay), 0)
+        h = C.c_void_p()
+        _check(lib().cox_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+        self.precision = precision
+        self._p = {}
+
+    def submit(self, data, opts=None) -> int:
+        d, keep = make_data(data)
+        o, pen = make_options(opts, self.precision)
+        rid = C.c_uint64()
+        _check(lib().cox_server_submit(self.h, C.byref(d), C.byref(o), C.byref(rid)))
+        self._p[rid.value] = int(data.p)
+        return rid.value
+
+    def _result(self, fn, rid, *args):
+        p = self._p.get(rid, 0)
+        beta = np.zeros(max(p, 1))
+        info = cox_fit_info()
+        rc = fn(self.h, C.c_uint64(rid), *args, beta.ctypes.data, C.byref(info))
+        if rc == COX_E_BUSY:
+            return None
+        self._p.pop(rid, None)
+        _check(rc)
+        return beta[:p], dict(info.as_dict(), rc=rc)
+
+    def poll(self, rid):
+        """(beta, info) when the request is finished, else None."""
+        return self._result(lib().cox_server_poll, rid)
+
+    def wait(self, rid, timeout_s=-1.0):
+        return self._result(lib().cox_server_wait, rid, C.c_double(timeout_s))
+
+    def cancel(self, rid):
+        _check(lib().cox_server_cancel(self.h, C.c_uint64(rid)))
+
+    def stats(self):
+        st = cox_server_stats()
+        _check(lib().cox_server_stats_get(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().cox_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

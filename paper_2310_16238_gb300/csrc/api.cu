@@ -5,7 +5,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -67,8 +72,7 @@ struct cox_handle {
   double *gout = nullptr;
   double *S0 = nullptr, *S1 = nullptr;
   // resident-kernel scratch (allocated when the data qualify)
-  uint32_t *r_tstat = nullptr, *r_pstat = nullptr;
-  double *r_tval = nullptr, *r_pval = nullptr;
+  uint64_t *r_tagg = nullptr, *r_tpart = nullptr;
   std::string err = "no error";
 };
 
@@ -150,11 +154,9 @@ int alloc_fit_state(cox_handle *h) {
     return fail(h, COX_E_OOM, "device allocation failed for the fit state");
   h->hfit.ctl = h->ctl;
   if (const int RT = h->sd->prep.res_T) {
-    h->r_tstat = static_cast<uint32_t *>(B.get(RT * sizeof(uint32_t)));
-    h->r_tval = static_cast<double *>(B.get(6 * RT * sizeof(double)));
-    h->r_pstat = static_cast<uint32_t *>(B.get(2 * RT * sizeof(uint32_t)));
-    h->r_pval = static_cast<double *>(B.get(6 * RT * sizeof(double)));
-    if (!h->r_tstat || !h->r_tval || !h->r_pstat || !h->r_pval)
+    h->r_tagg = static_cast<uint64_t *>(B.get(6 * RT * sizeof(uint64_t)));
+    h->r_tpart = static_cast<uint64_t *>(B.get(12 * RT * sizeof(uint64_t)));
+    if (!h->r_tagg || !h->r_tpart)
       return fail(h, COX_E_OOM, "device allocation failed for the resident state");
   }
   if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
@@ -324,8 +326,9 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   const Prepared &P = h->sd->prep;
   const int RT = P.res_T;
   cudaStream_t s = h->stream;
-  if (cudaMemsetAsync(h->r_tstat, 0, RT * sizeof(uint32_t), s) != cudaSuccess ||
-      cudaMemsetAsync(h->r_pstat, 0, 2 * RT * sizeof(uint32_t), s) != cudaSuccess)
+  // tag 0 never matches: records start at epoch 1
+  if (cudaMemsetAsync(h->r_tagg, 0, 6 * RT * sizeof(uint64_t), s) != cudaSuccess ||
+      cudaMemsetAsync(h->r_tpart, 0, 12 * RT * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
   ResParams prm{};
   prm.F = h->hfit;
@@ -334,19 +337,17 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   prm.tile_g = P.res_tile_g;
   prm.tile_k = P.res_tile_k;
   prm.col_tile = P.res_col_tile;
-  prm.tstat = h->r_tstat;
-  prm.tval = h->r_tval;
-  prm.pstat = h->r_pstat;
-  prm.pval = h->r_pval;
+  prm.tagg = h->r_tagg;
+  prm.tpart = h->r_tpart;
   prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
   // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
   const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
   BufferSet trbuf;
   if (tr_steps > 0) {
-    prm.trace = static_cast<uint64_t *>(trbuf.get(2 * tr_steps * 8 * sizeof(uint64_t)));
+    prm.trace = static_cast<uint64_t *>(trbuf.get(tr_steps * RT * 8 * sizeof(uint64_t)));
     prm.trace_steps = prm.trace ? tr_steps : 0;
-    if (prm.trace) cudaMemsetAsync(prm.trace, 0, 2 * tr_steps * 8 * sizeof(uint64_t), s);
+    if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * RT * 8 * sizeof(uint64_t), s);
   }
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
@@ -356,23 +357,45 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   int rc;
   if ((rc = read_ctl(h))) return rc;
   if (prm.trace_steps > 0) {
-    std::vector<uint64_t> tr(size_t(2 * prm.trace_steps * 8));
+    // per CTA: mean phase times and the time from the earliest step start to its partial publish
+    std::vector<uint64_t> tr(size_t(prm.trace_steps * RT * 8));
     cudaMemcpy(tr.data(), prm.trace, tr.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    const char *names[5] = {"update+scan", "raking+look-back", "ratios+publish", "all-gather", "step"};
-    for (int c = 0; c < 2; ++c) {
-      double acc[6] = {0, 0, 0, 0, 0, 0};
-      int64_t n = 0;
-      for (int64_t k = 1; k < prm.trace_steps; ++k) {
-        const uint64_t *r = &tr[size_t((c * prm.trace_steps + k) * 8)];
-        if (!r[0] || !r[5]) continue;
-        for (int q = 0; q < 5; ++q) acc[q] += double(r[q + 1] - r[q]);
-        acc[5] += double(r[5] - r[0]);
-        ++n;
+    std::vector<int32_t> rlo(RT + 1), rg(RT + 1);
+    cudaMemcpy(rlo.data(), P.res_tile_lo, (RT + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaMemcpy(rg.data(), P.res_tile_g, (RT + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    std::vector<double> pub(RT, 0.0), ph(5 * RT, 0.0), stepm(RT, 0.0);
+    int64_t n = 0;
+    for (int64_t k = 1; k < prm.trace_steps; ++k) {
+      uint64_t t0 = ~0ull;
+      bool ok = true;
+      for (int c = 0; c < RT; ++c) {
+        const uint64_t *r = &tr[size_t((k * RT + c) * 8)];
+        if (!r[0] || !r[5]) ok = false;
+        t0 = std::min(t0, r[0]);
       }
-      std::fprintf(stderr, "[phase trace] CTA %s, %lld steps, mean ns:", c == 0 ? "first" : "last", (long long)n);
-      for (int q = 0; q < 5 && n; ++q) std::fprintf(stderr, " %s %.0f", names[q], acc[q] / n);
-      if (n) std::fprintf(stderr, " | step %.0f\n", acc[5] / n);
+      if (!ok) continue;
+      for (int c = 0; c < RT; ++c) {
+        const uint64_t *r = &tr[size_t((k * RT + c) * 8)];
+        pub[c] += double(r[3] - t0);
+        stepm[c] += double(r[5] - r[0]);
+        for (int q = 0; q < 5; ++q) ph[5 * c + q] += double(r[q + 1] - r[q]);
+      }
+      ++n;
     }
+    std::vector<int> order(RT);
+    for (int c = 0; c < RT; ++c) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return pub[a] > pub[b]; });
+    std::fprintf(stderr, "[phase trace] %lld steps x %d CTAs; slowest to publish (ns after the first start):\n",
+                 (long long)n, RT);
+    for (int q = 0; q < std::min(RT, 6) && n; ++q) {
+      const int c = order[q];
+      std::fprintf(stderr, "  CTA %d positions %d groups %d: publish %.0f | scan %.0f carry %.0f ratios %.0f gather %.0f step %.0f\n",
+                   c, rlo[c + 1] - rlo[c], rg[c + 1] - rg[c], pub[c] / n, ph[5 * c] / n, ph[5 * c + 1] / n,
+                   ph[5 * c + 2] / n, ph[5 * c + 3] / n, ph[5 * c + 4] / n);
+    }
+    const int c = order[RT - 1];
+    if (n) std::fprintf(stderr, "  fastest CTA %d positions %d groups %d: publish %.0f, step %.0f\n", c, rlo[c + 1] - rlo[c],
+                        rg[c + 1] - rg[c], pub[c] / n, stepm[c] / n);
   }
   if ((rc = device_error(h))) return rc;
   const FitCtl &c = *h->h_ctl;
@@ -821,6 +844,478 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
   if (hc) cudaFreeHost(hc);
   cudaStreamSynchronize(s);
   return worst;
+}
+
+}  // extern "C"
+
+// =================================================================== serving
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Owned host copy of one request's inputs (so the caller may free its buffers on return).
+struct HostData {
+  int64_t n = 0;
+  int32_t p = 0;
+  std::vector<int32_t> stop, start, stratum, row_idx;
+  std::vector<uint8_t> event;
+  std::vector<int64_t> col_ptr;
+  std::vector<double> val;
+  cox_data view() const {
+    cox_data d{};
+    d.n_rows = n;
+    d.p = p;
+    d.stop = stop.data();
+    d.start = start.empty() ? nullptr : start.data();
+    d.event = event.data();
+    d.stratum = stratum.empty() ? nullptr : stratum.data();
+    d.col_ptr = col_ptr.data();
+    d.row_idx = row_idx.data();
+    d.val = val.empty() ? nullptr : val.data();
+    return d;
+  }
+};
+
+template <class V>
+bool copy_in(std::vector<V> &dst, const V *src, int64_t n) {
+  dst.clear();
+  if (!src || n <= 0) return true;
+  dst.resize(static_cast<size_t>(n));
+  return cudaMemcpy(dst.data(), src, n * sizeof(V), cudaMemcpyDefault) == cudaSuccess;
+}
+
+enum ReqState { kQueued, kPreparing, kReady, kInFlight, kDone };
+
+struct Req {
+  uint64_t id = 0;
+  ReqState state = kQueued;
+  HostData data;
+  cox_options opts{};
+  std::vector<uint8_t> penalize;
+  size_t footprint = 0;
+  cox_handle *h = nullptr;
+  int slot = -1;
+  bool cancel = false;
+  std::vector<double> beta;
+  cox_fit_info info{};
+  int rc = COX_OK;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+};
+
+}  // namespace
+
+struct cox_server {
+  cox_server_options o{};
+  std::mutex mu;
+  std::condition_variable cv_prep, cv_run, cv_done;
+  std::deque<Req *> queue;
+  std::vector<Req *> ready;
+  std::unordered_map<uint64_t, Req *> reqs;
+  uint64_t next_id = 1;
+  size_t bytes_in_use = 0;
+  int n_preparing = 0, n_running = 0, n_done = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, replays = 0, step_launches = 0;
+  bool stop = false;
+  int device = 0;
+  cudaStream_t prep_stream = nullptr, run_stream = nullptr;
+  std::thread prep_thr, run_thr;
+  // batch state (run thread only)
+  BufferSet bufs;
+  DevFit *fits = nullptr;
+  FitCtl *ctls = nullptr;
+  LaunchCtl *lc = nullptr;
+  int2 *items = nullptr;
+  int64_t items_cap = 0;
+  FitCtl *h_ctls = nullptr;
+  std::vector<Req *> slots;
+  cudaGraphExec_t graph = nullptr;
+  int graph_valued = -1;
+  int grid = 0;
+};
+
+namespace {
+
+void finish_locked(cox_server *S, Req *r, int rc) {
+  r->rc = rc;
+  r->state = kDone;
+  r->t_done = now_ms();
+  r->info.status = rc;
+  r->info.wait_ms = (r->t_admit > 0.0 ? r->t_admit : r->t_done) - r->t_submit;
+  r->info.total_ms = r->t_done - r->t_submit;
+  S->n_done++;
+  if (rc < 0) S->failed++;
+  else S->completed++;
+  S->cv_done.notify_all();
+  S->cv_prep.notify_all();
+}
+
+bool can_admit_locked(cox_server *S) {
+  if (S->queue.empty()) return false;
+  if (S->queue.front()->cancel) return true;
+  const int inflight = S->n_preparing + S->n_running + int(S->ready.size());
+  return inflight < S->o.max_active && S->bytes_in_use + S->queue.front()->footprint <= S->o.memory_budget;
+}
+
+void prep_loop(cox_server *S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Req *r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_prep.wait(lk, [&] { return S->stop || can_admit_locked(S); });
+      if (S->stop) return;
+      r = S->queue.front();
+      S->queue.pop_front();
+      if (r->cancel) {
+        finish_locked(S, r, COX_E_INVALID);
+        continue;
+      }
+      r->state = kPreparing;
+      r->t_admit = now_ms();
+      S->n_preparing++;
+      S->bytes_in_use += r->footprint;
+    }
+    cox_options o = r->opts;
+    o.stream = S->prep_stream;
+    o.precision = S->o.precision;
+    o.engine = COX_ENGINE_STREAM;
+    o.penalize = r->penalize.empty() ? nullptr : r->penalize.data();
+    const cox_data d = r->data.view();
+    cox_handle *h = nullptr;
+    int rc = cox_create(&d, &o, &h);
+    bool direct = false;
+    if (!rc && (D(h).p == 0 || D(h).T == 0)) direct = true;   // nothing to iterate: fit right here
+    if (!rc && !direct) rc = init_state(h, nullptr);
+    std::vector<double> beta;
+    cox_fit_info info{};
+    if (!rc && direct) {
+      beta.assign(static_cast<size_t>(std::max<int32_t>(D(h).p, 1)), 0.0);
+      rc = cox_fit(h, nullptr, beta.data(), &info);
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->n_preparing--;
+    r->data = HostData{};
+    if (rc < 0 || direct) {
+      if (h) {
+        lk.unlock();
+        cox_destroy(h);
+        lk.lock();
+      }
+      S->bytes_in_use -= r->footprint;
+      if (direct && rc >= 0) {
+        r->beta = beta;
+        r->info = info;
+      }
+      finish_locked(S, r, rc);
+      continue;
+    }
+    // account the actual device bytes instead of the estimate
+    const size_t actual = h->bufs.bytes_total + h->sd->prep.bufs.bytes_total;
+    S->bytes_in_use = S->bytes_in_use - r->footprint + actual;
+    r->footprint = actual;
+    r->h = h;
+    r->state = kReady;
+    S->ready.push_back(r);
+    S->cv_run.notify_one();
+  }
+}
+
+int rebuild_batch(cox_server *S) {
+  std::vector<int2> it;
+  int64_t maxT = 0;
+  int valued = 0, active = 0;
+  for (size_t sl = 0; sl < S->slots.size(); ++sl)
+    if (Req *r = S->slots[sl]) {
+      maxT = std::max<int64_t>(maxT, D(r->h).T);
+      valued |= r->h->valued;
+      ++active;
+    }
+  for (int64_t k = 0; k < maxT; ++k)
+    for (size_t sl = 0; sl < S->slots.size(); ++sl)
+      if (Req *r = S->slots[sl])
+        if (k < D(r->h).T) it.push_back(make_int2(int(sl), int(D(r->h).T - 1 - k)));
+  if (int64_t(it.size()) > S->items_cap || valued != S->graph_valued || !S->graph) {
+    if (int64_t(it.size()) > S->items_cap) {
+      const int64_t cap = std::max<int64_t>(int64_t(it.size()) * 2, S->items_cap * 2);
+      int2 *ni = static_cast<int2 *>(S->bufs.get(cap * sizeof(int2)));
+      if (!ni) return COX_E_OOM;
+      S->items = ni;   // the old buffer stays in the set until the server is destroyed
+      S->items_cap = cap;
+    }
+    if (S->graph) {
+      cudaGraphExecDestroy(S->graph);
+      S->graph = nullptr;
+    }
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(S->run_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return COX_E_CUDA;
+    int rc = COX_OK;
+    for (int i = 0; i < S->o.steps_per_replay && !rc; ++i)
+      rc = launch_ccd(S->o.precision, S->fits, S->items, S->lc, S->grid, kModeFit, 0, valued, S->run_stream);
+    const cudaError_t e = cudaStreamEndCapture(S->run_stream, &g);
+    if (rc || e != cudaSuccess) return COX_E_CUDA;
+    const cudaError_t ei = cudaGraphInstantiate(&S->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return COX_E_CUDA;
+    S->graph_valued = valued;
+  }
+  LaunchCtl l{0u, 0u, int32_t(it.size()), active, 0};
+  if (!it.empty() && cudaMemcpyAsync(S->items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                     S->run_stream) != cudaSuccess)
+    return COX_E_CUDA;
+  if (cudaMemcpyAsync(S->lc, &l, sizeof(l), cudaMemcpyHostToDevice, S->run_stream) != cudaSuccess) return COX_E_CUDA;
+  return cudaStreamSynchronize(S->run_stream) == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+void run_loop(cox_server *S) {
+  cudaSetDevice(S->device);
+  bool dirty = false;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_run.wait_for(lk, std::chrono::milliseconds(20),
+                         [&] { return S->stop || !S->ready.empty() || S->n_running > 0; });
+      if (S->stop) return;
+      // join prepared fits
+      for (Req *r : S->ready) {
+        size_t sl = 0;
+        while (sl < S->slots.size() && S->slots[sl]) ++sl;
+        if (sl == S->slots.size()) break;   // cannot happen: slots == max_active
+        DevFit df = r->h->hfit;
+        df.ctl = S->ctls + sl;
+        cudaMemcpyAsync(S->fits + sl, &df, sizeof(df), cudaMemcpyHostToDevice, S->run_stream);
+        cudaMemcpyAsync(S->ctls + sl, r->h->ctl, sizeof(FitCtl), cudaMemcpyDeviceToDevice, S->run_stream);
+        r->h->stream = S->run_stream;
+        r->slot = int(sl);
+        r->state = kInFlight;
+        S->slots[sl] = r;
+        S->n_running++;
+        dirty = true;
+      }
+      S->ready.clear();
+      if (S->n_running == 0) continue;
+    }
+    // cancellations are honoured here, at a replay boundary
+    std::vector<Req *> retire;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (Req *r : S->slots)
+        if (r && r->cancel) retire.push_back(r);
+    }
+    if (retire.empty()) {
+      int rc = dirty ? rebuild_batch(S) : COX_OK;
+      dirty = false;
+      if (!rc && cudaGraphLaunch(S->graph, S->run_stream) != cudaSuccess) rc = COX_E_CUDA;
+      if (!rc) count_launches(S->o.steps_per_replay);
+      if (!rc && (cudaMemcpyAsync(S->h_ctls, S->ctls, S->slots.size() * sizeof(FitCtl), cudaMemcpyDeviceToHost,
+                                  S->run_stream) != cudaSuccess ||
+                  cudaStreamSynchronize(S->run_stream) != cudaSuccess))
+        rc = COX_E_CUDA;
+      if (rc) {   // a CUDA failure ends every fit in flight with that error
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Req *r : S->slots)
+          if (r) r->cancel = true;
+        continue;
+      }
+      S->replays++;
+      S->step_launches += S->o.steps_per_replay;
+      for (size_t sl = 0; sl < S->slots.size(); ++sl)
+        if (Req *r = S->slots[sl])
+          if (S->h_ctls[sl].state != kRunning || S->h_ctls[sl].error) retire.push_back(r);
+    }
+    for (Req *r : retire) {
+      const int sl = r->slot;
+      const FitCtl &c = S->h_ctls[sl];
+      int rc;
+      if (r->cancel) rc = COX_E_INVALID;
+      else if (c.error) rc = c.error;
+      else rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
+      r->beta.assign(static_cast<size_t>(std::max<int32_t>(D(r->h).p, 1)), 0.0);
+      if (rc >= 0 && D(r->h).p > 0)
+        cudaMemcpy(r->beta.data(), r->h->hfit.beta, D(r->h).p * sizeof(double), cudaMemcpyDeviceToHost);
+      r->info.sweeps = c.sweep;
+      r->info.converged = c.state == kConverged;
+      r->info.coord_updates = c.coord_updates;
+      r->info.loglik = c.loglik;
+      r->info.objective = c.obj;
+      cox_destroy(r->h);
+      r->h = nullptr;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->slots[sl] = nullptr;
+      r->slot = -1;
+      S->n_running--;
+      S->bytes_in_use -= r->footprint;
+      finish_locked(S, r, rc);
+      dirty = true;
+    }
+  }
+}
+
+int server_result(cox_server *S, Req *r, double *beta_out, cox_fit_info *info) {
+  // called with S->mu held; forgets the request
+  const int rc = r->rc;
+  if (info) *info = r->info;
+  if (beta_out && rc >= 0 && !r->beta.empty()) {
+    const size_t p = r->beta.size();
+    if (cudaMemcpy(beta_out, r->beta.data(), p * sizeof(double), cudaMemcpyDefault) != cudaSuccess) return COX_E_CUDA;
+  }
+  S->reqs.erase(r->id);
+  S->n_done--;
+  delete r;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cox_server_create(const cox_server_options *opts, cox_server **out) {
+  if (!out) return fail(nullptr, COX_E_INVALID, "cox_server_create: null argument");
+  *out = nullptr;
+  std::unique_ptr<cox_server> S(new cox_server());
+  if (opts) S->o = *opts;
+  if (S->o.precision != COX_FP64 && S->o.precision != COX_FP32C)
+    return fail(nullptr, COX_E_INVALID, "cox_server_create: precision");
+  if (S->o.max_active <= 0) S->o.max_active = 256;
+  if (S->o.steps_per_replay <= 0) S->o.steps_per_replay = 64;
+  if (cudaGetDevice(&S->device) != cudaSuccess) return cuda_fail(nullptr, "cox_server_create: no device");
+  if (S->o.memory_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_fail(nullptr, "cox_server_create: memory info");
+    S->o.memory_budget = size_t(double(fr) * 0.8);
+  }
+  if (cudaStreamCreateWithFlags(&S->prep_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->run_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_fail(nullptr, "cox_server_create: streams");
+  const int n = S->o.max_active;
+  S->fits = static_cast<DevFit *>(S->bufs.get(n * sizeof(DevFit)));
+  S->ctls = static_cast<FitCtl *>(S->bufs.get(n * sizeof(FitCtl)));
+  S->lc = static_cast<LaunchCtl *>(S->bufs.get(sizeof(LaunchCtl)));
+  S->items_cap = 1 << 16;
+  S->items = static_cast<int2 *>(S->bufs.get(S->items_cap * sizeof(int2)));
+  if (!S->fits || !S->ctls || !S->lc || !S->items) return fail(nullptr, COX_E_OOM, "cox_server_create: allocation");
+  if (cudaMallocHost(&S->h_ctls, n * sizeof(FitCtl)) != cudaSuccess) return cuda_fail(nullptr, "cox_server_create: pinned");
+  S->slots.assign(static_cast<size_t>(n), nullptr);
+  S->grid = std::max(1, std::max(ccd_max_grid(S->o.precision, 0), ccd_max_grid(S->o.precision, 1)));
+  cox_server *raw = S.get();
+  S->prep_thr = std::thread(prep_loop, raw);
+  S->run_thr = std::thread(run_loop, raw);
+  *out = S.release();
+  return COX_OK;
+}
+
+int cox_server_submit(cox_server *S, const cox_data *data, const cox_options *opts, uint64_t *request_id) {
+  if (!S || !data || !request_id) return fail(nullptr, COX_E_INVALID, "cox_server_submit: null argument");
+  if (check_options(opts)) return fail(nullptr, COX_E_INVALID, "cox_server_submit: invalid options");
+  std::unique_ptr<Req> r(new Req());
+  cox_options o = opts ? *opts : default_options();
+  o.precision = S->o.precision;
+  size_t fp = 0;
+  int rc = cox_footprint(data, &o, &fp);
+  if (rc) return rc;
+  if (fp > S->o.memory_budget) return fail(nullptr, COX_E_ADMISSION, "cox_server_submit: request exceeds the memory budget");
+  HostData &h = r->data;
+  h.n = data->n_rows;
+  h.p = data->p;
+  if (h.n < 0 || h.p < 0 || !data->stop || !data->event || !data->col_ptr)
+    return fail(nullptr, COX_E_INVALID, "cox_server_submit: null or negative argument");
+  bool ok = copy_in(h.col_ptr, data->col_ptr, int64_t(h.p) + 1);
+  const int64_t nnz = ok && h.p >= 0 ? h.col_ptr[h.p] : 0;
+  ok = ok && nnz >= 0 && copy_in(h.stop, data->stop, h.n) && copy_in(h.event, data->event, h.n) &&
+       copy_in(h.start, data->start, h.n) && copy_in(h.stratum, data->stratum, h.n) &&
+       copy_in(h.row_idx, data->row_idx, nnz) && copy_in(h.val, data->val, nnz);
+  if (ok && opts && opts->penalize && h.p > 0) ok = copy_in(r->penalize, opts->penalize, h.p);
+  if (!ok) return cuda_fail(nullptr, "cox_server_submit: copying the inputs");
+  if (h.stop.empty()) h.stop.resize(1);   // keep non-null pointers for empty data
+  if (h.event.empty()) h.event.resize(1);
+  if (h.row_idx.empty()) h.row_idx.resize(1);
+  o.penalize = nullptr;
+  r->opts = o;
+  r->footprint = fp;
+  r->t_submit = now_ms();
+  std::lock_guard<std::mutex> lk(S->mu);
+  r->id = S->next_id++;
+  *request_id = r->id;
+  S->reqs[r->id] = r.get();
+  S->queue.push_back(r.release());
+  S->submitted++;
+  S->cv_prep.notify_one();
+  return COX_OK;
+}
+
+int cox_server_poll(cox_server *S, uint64_t id, double *beta_out, cox_fit_info *info) {
+  if (!S) return fail(nullptr, COX_E_INVALID, "cox_server_poll: null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(nullptr, COX_E_NOT_FOUND, "cox_server_poll: unknown request");
+  if (it->second->state != kDone) return COX_E_BUSY;
+  return server_result(S, it->second, beta_out, info);
+}
+
+int cox_server_wait(cox_server *S, uint64_t id, double timeout_s, double *beta_out, cox_fit_info *info) {
+  if (!S) return fail(nullptr, COX_E_INVALID, "cox_server_wait: null server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto done = [&] {
+    auto it = S->reqs.find(id);
+    return it == S->reqs.end() || it->second->state == kDone;
+  };
+  if (timeout_s < 0) S->cv_done.wait(lk, done);
+  else S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(nullptr, COX_E_NOT_FOUND, "cox_server_wait: unknown request");
+  if (it->second->state != kDone) return COX_E_BUSY;
+  return server_result(S, it->second, beta_out, info);
+}
+
+int cox_server_cancel(cox_server *S, uint64_t id) {
+  if (!S) return fail(nullptr, COX_E_INVALID, "cox_server_cancel: null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(nullptr, COX_E_NOT_FOUND, "cox_server_cancel: unknown request");
+  it->second->cancel = true;
+  S->cv_prep.notify_all();
+  return COX_OK;
+}
+
+int cox_server_stats_get(cox_server *S, cox_server_stats *out) {
+  if (!S || !out) return fail(nullptr, COX_E_INVALID, "cox_server_stats_get: null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  out->submitted = S->submitted;
+  out->completed = S->completed;
+  out->failed = S->failed;
+  out->queued = int32_t(S->queue.size());
+  out->preparing = S->n_preparing + int32_t(S->ready.size());
+  out->running = S->n_running;
+  out->done_unpolled = S->n_done;
+  out->bytes_in_use = S->bytes_in_use;
+  out->memory_budget = S->o.memory_budget;
+  out->replays = S->replays;
+  out->step_launches = S->step_launches;
+  return COX_OK;
+}
+
+void cox_server_destroy(cox_server *S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_prep.notify_all();
+  S->cv_run.notify_all();
+  if (S->prep_thr.joinable()) S->prep_thr.join();
+  if (S->run_thr.joinable()) S->run_thr.join();
+  cudaStreamSynchronize(S->run_stream);
+  for (auto &kv : S->reqs) {
+    if (kv.second->h) cox_destroy(kv.second->h);
+    delete kv.second;
+  }
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->h_ctls) cudaFreeHost(S->h_ctls);
+  S->bufs.release();
+  if (S->prep_stream) cudaStreamDestroy(S->prep_stream);
+  if (S->run_stream) cudaStreamDestroy(S->run_stream);
+  delete S;
 }
 
 }  // extern "C"

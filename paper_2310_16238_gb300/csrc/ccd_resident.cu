@@ -8,7 +8,8 @@
 //   1. applies the previous step's update at its nonzeros (eta += dbeta, eq. parallel_xb;
 //      v = +-exp(eta - shift), eq. parallel_d) directly in shared memory,
 //   2. scans its positions for D = v and N1 = x_j v (segmented suffix, strata are segments),
-//      combines threads with one raking warp and CTAs with a decoupled look-back,
+//      combines threads with warp-shuffle scans and CTAs by reading the published aggregates
+//      of the later CTAs of the stratum (all CTAs are co-resident, so no carry chain),
 //   3. evaluates the tie-group ratios of eqs. (parallel_g)/(parallel_h) into a CTA partial,
 //   4. all-gathers the partials of every CTA and reduces them in a fixed order, so every CTA
 //      computes the same Newton / trust-region / L1 step (§2.4) without another launch.
@@ -94,6 +95,26 @@ static __device__ void block_sum_t(double (&v)[NV], double *scratch /* [NV*32] *
   __syncthreads();
 }
 
+
+// ---- epoch-tagged exchange records: every 8-byte word is (epoch << 32) | 32 data bits, so a
+// reader validates and receives a record with one round trip (aligned 8-byte accesses are
+// single-copy atomic; no status word, release or fence is needed)
+static __device__ __forceinline__ void st_cg_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.global.cg.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void ld_cg_v2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+  asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+static __device__ __forceinline__ void put_tagged(uint64_t *w, uint32_t tag, double v) {
+  const uint64_t b = uint64_t(__double_as_longlong(v));
+  st_cg_u64(w, (uint64_t(tag) << 32) | (b & 0xffffffffull));
+  st_cg_u64(w + 1, (uint64_t(tag) << 32) | (b >> 32));
+}
+static __device__ __forceinline__ bool tag_ok(uint64_t w, uint32_t tag) { return uint32_t(w >> 32) == tag; }
+static __device__ __forceinline__ double untag(uint64_t lo, uint64_t hi) {
+  return __longlong_as_double(static_cast<long long>((lo & 0xffffffffull) | ((hi & 0xffffffffull) << 32)));
+}
+
 static __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -162,6 +183,10 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
   __shared__ Acc s_carry[NV];
   __shared__ double s_wred[3][kResThreads / 32];
   __shared__ double s_G[3];
+  __shared__ Acc s_wagg[2][32];
+  __shared__ int s_wflag[32];
+  __shared__ Acc s_wcar[2][32];
+  __shared__ int s_wcflag[32];
 
   const DevFit &F = prm.F;
   const DevData &D = prm.D;
@@ -256,10 +281,20 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
     const bool need_ll = st.need_ll != 0;
     const uint32_t epoch = st.epoch;
     const int pslot = cur ^ 1;
-    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0 && (t == 0 || t == T_ - 1))
-                          ? prm.trace + (int64_t(t == 0 ? 0 : 1) * prm.trace_steps + step) * 8
-                          : nullptr;
+    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * T_ + t) * 8 : nullptr;
     if (trace) trace[0] = gtimer();
+    // this coordinate's inputs to the step, loaded now so their latency overlaps the step
+    // (beta_j and trust_j were last written by CTA 0 at least one all-gather ago when p >= 2)
+    double pre_dx = 0.0, pre_b = 0.0, pre_tr = 0.0;
+    int pre_pen = 1;
+    if (tid == 0) {
+      pre_dx = D.dX[j];
+      pre_pen = F.penalize ? F.penalize[j] != 0 : 1;
+      if (D.p >= 2) {
+        pre_b = ld_relaxed_f64(&F.beta[j]);
+        pre_tr = ld_relaxed_f64(&F.trust[j]);
+      }
+    }
     // ---- 1. the pending update, in shared memory (eta also written back to global)
     if (pend_j >= 0) {
       if (!st.list_over[pslot]) {
@@ -346,24 +381,11 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
         hcut[h] = uint8_t(seen);
       }
     }
-    tc[tslot(tid)] = a0;
-    tc[kTcStride + tslot(tid)] = a1;
-    tflag[tslot(tid)] = uint8_t(cm != 0u);
-    __syncthreads();
-    if (trace) trace[1] = gtimer();
-
-    // ---- 4. raking warp: tile aggregate, per-thread carries, look-back over later CTAs
-    if (warp == 0) {
-      const int t0 = lane * RAKE;
-      Acc r0 = P::zero(), r1 = P::zero();
-      int rf = 0;
-      for (int q = RAKE - 1; q >= 0; --q) {
-        const int sl = tslot(t0 + q);
-        if (tflag[sl]) { r0 = tc[sl]; r1 = tc[kTcStride + sl]; rf = 1; }
-        else { r0 = P::comb(tc[sl], r0); r1 = P::comb(tc[kTcStride + sl], r1); }
-      }
-      Acc x0 = r0, x1 = r1;
-      int xf = rf;
+    // ---- 4. segmented suffix over the thread aggregates: every warp scans its 32 threads,
+    //         then warp 0 scans the 32 warp aggregates, publishes the tile aggregate and looks back
+    {
+      Acc x0 = a0, x1 = a1;
+      int xf = cm != 0u;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const Acc y0 = P::shfl_down(x0, off), y1 = P::shfl_down(x1, off);
@@ -373,66 +395,79 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
           xf |= yf;
         }
       }
-      const int tf = __shfl_sync(0xffffffffu, xf, 0);
-      const double agg0 = __shfl_sync(0xffffffffu, P::to64(x0), 0), agg1 = __shfl_sync(0xffffffffu, P::to64(x1), 0);
-      const uint32_t ep = (epoch & 0x1fffffffu) << 3;
-      if (lane == 0) {
-        const int o = tf ? 3 : 0;
-        prm.tval[6 * t + o] = agg0;
-        prm.tval[6 * t + o + 1] = agg1;
-        st_release_u32(&prm.tstat[t], ep | (tf ? 4u | 2u : 1u));   // orders the stores above
+      // exclusive within the warp: the inclusive value of lane + 1
+      Acc e0 = P::shfl_down(x0, 1), e1 = P::shfl_down(x1, 1);
+      int ef = __shfl_down_sync(0xffffffffu, xf, 1);
+      if (lane == 31) { e0 = P::zero(); e1 = P::zero(); ef = 0; }
+      tc[tslot(tid)] = e0;
+      tc[kTcStride + tslot(tid)] = e1;
+      tflag[tslot(tid)] = uint8_t(ef);
+      if (lane == 0) { s_wagg[0][warp] = x0; s_wagg[1][warp] = x1; s_wflag[warp] = xf; }
+    }
+    __syncthreads();
+    if (trace) trace[1] = gtimer();
+    if (warp == 0) {
+      Acc x0 = s_wagg[0][lane], x1 = s_wagg[1][lane];
+      int xf = s_wflag[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const Acc y0 = P::shfl_down(x0, off), y1 = P::shfl_down(x1, off);
+        const int yf = __shfl_down_sync(0xffffffffu, xf, off);
+        if (lane + off < 32) {
+          if (!xf) { x0 = P::comb(x0, y0); x1 = P::comb(x1, y1); }
+          xf |= yf;
+        }
       }
       Acc c0 = P::shfl_down(x0, 1), c1 = P::shfl_down(x1, 1);
       int cf = __shfl_down_sync(0xffffffffu, xf, 1);
       if (lane == 31) { c0 = P::zero(); c1 = P::zero(); cf = 0; }
-      for (int q = RAKE - 1; q >= 0; --q) {
-        const int sl = tslot(t0 + q);
-        const Acc o0 = tc[sl], o1 = tc[kTcStride + sl];
-        const int of = tflag[sl];
-        tc[sl] = c0;
-        tc[kTcStride + sl] = c1;
-        tflag[sl] = uint8_t(cf);
-        if (of) { c0 = o0; c1 = o1; cf = 1; }
-        else { c0 = P::comb(o0, c0); c1 = P::comb(o1, c1); }
+      s_wcar[0][lane] = c0;   // carry into warp `lane` from the later warps of this tile
+      s_wcar[1][lane] = c1;
+      s_wcflag[lane] = cf;
+      const int tf = __shfl_sync(0xffffffffu, xf, 0);
+      const double agg0 = __shfl_sync(0xffffffffu, P::to64(x0), 0), agg1 = __shfl_sync(0xffffffffu, P::to64(x1), 0);
+      const uint32_t tag = epoch;
+      if (lane == 0) {   // publish the aggregate; a tile holding a stratum end is flagged
+        uint64_t *w = prm.tagg + 6 * int64_t(t);
+        put_tagged(w, tag, agg0);
+        put_tagged(w + 2, tag, agg1);
+        st_cg_u64(w + 4, (uint64_t(tag) << 32) | uint64_t(tf));
       }
+      // carry from the later tiles of this stratum: every CTA publishes its aggregate each step,
+      // so read them all (up to the first tile holding a stratum end) and sum them in a fixed
+      // order -- no tile waits for another tile's carry, and the result is deterministic
       double cr0 = 0.0, cr1 = 0.0;
       const bool last_is_cut = ((cutbits[(hi - lo - 1) >> 5] >> ((hi - lo - 1) & 31)) & 1u) != 0u;
       if (t + 1 < T_ && !last_is_cut) {
-        int base = t + 1;
         const long long tstart = clock64();
-        bool timed_out = false;
-        for (;;) {
+        for (int base = t + 1; base < T_; base += 32) {
           const int u = base + lane;
-          uint32_t s = 0;
-          bool valid = false;
-          for (;;) {
-            if (u < T_) {
-              s = ld_relaxed_u32(&prm.tstat[u]);
-              valid = (s & ~7u) == ep && (s & 3u) != 0u;
-            } else {
-              valid = true;
-              s = ep | 2u;
+          uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+          bool quit = false;
+          if (u < T_) {
+            const uint64_t *w = prm.tagg + 6 * int64_t(u);
+            for (;;) {
+              ld_cg_v2(w, w0, w1);
+              ld_cg_v2(w + 2, w2, w3);
+              ld_cg_v2(w + 4, w4, w5);
+              if (tag_ok(w0, tag) && tag_ok(w1, tag) && tag_ok(w2, tag) && tag_ok(w3, tag) && tag_ok(w4, tag)) break;
+              if (clock64() - tstart > kSpinBudget || *reinterpret_cast<volatile int32_t *>(&ctl->error) != 0) {
+                quit = true;
+                break;
+              }
+              __nanosleep(20);
             }
-            const uint32_t inv = __ballot_sync(0xffffffffu, !valid);
-            const uint32_t inc = __ballot_sync(0xffffffffu, valid && (s & 3u) == 2u);
-            if (inv == 0u || (inc != 0u && (__ffs(inc) < __ffs(inv)))) break;
-            // give up after the budget, or at once when another CTA already gave up
-            const bool quit = clock64() - tstart > kSpinBudget || *reinterpret_cast<volatile int32_t *>(&ctl->error) != 0;
-            if (__any_sync(0xffffffffu, quit)) { timed_out = true; break; }
-            __nanosleep(20);
           }
-          if (timed_out) {
+          if (__any_sync(0xffffffffu, quit)) {
             if (lane == 0) atomicCAS(&ctl->error, 0, COX_E_TIMEOUT);
             break;
           }
-          fence_acquire_gpu();   // the statuses seen above were published with release stores
-          const uint32_t inc = __ballot_sync(0xffffffffu, valid && (s & 3u) == 2u);
-          const int stop = inc ? __ffs(inc) - 1 : 31;
+          const uint32_t fm = __ballot_sync(0xffffffffu, u < T_ && (w4 & 1ull));
+          const int stop = fm ? __ffs(fm) - 1 : 31;
           double v0 = 0.0, v1 = 0.0;
-          if (lane <= stop && u < T_) {
-            const int o = (s & 3u) == 2u ? 3 : 0;
-            v0 = ld_relaxed_f64(&prm.tval[6 * u + o]);
-            v1 = ld_relaxed_f64(&prm.tval[6 * u + o + 1]);
+          if (u < T_ && lane <= stop) {
+            v0 = untag(w0, w1);
+            v1 = untag(w2, w3);
           }
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) {
@@ -441,18 +476,12 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
           }
           cr0 += __shfl_sync(0xffffffffu, v0, 0);
           cr1 += __shfl_sync(0xffffffffu, v1, 0);
-          if (inc) break;
-          base += 32;
+          if (fm) break;
         }
       }
       if (lane == 0) {
         s_carry[0] = P::from64(cr0);
         s_carry[1] = P::from64(cr1);
-        if (!tf) {
-          prm.tval[6 * t + 3] = agg0 + cr0;
-          prm.tval[6 * t + 4] = agg1 + cr1;
-          st_release_u32(&prm.tstat[t], ep | 2u);
-        }
       }
     }
     // the next column's entries, fetched while other CTAs are still scanning (its eta values
@@ -479,11 +508,16 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
       const Acc C0 = s_carry[0], C1 = s_carry[1];
       Acc q_g1 = P::zero(), q_g2 = P::zero();
       for (int h = tid; h < nh; h += kResThreads) {
-        const int o = tslot(hpos[h] / ITEMS);
+        const int ot = hpos[h] / ITEMS, o = tslot(ot), ow = ot >> 5;
         Acc s0 = hloc[NV * h], s1 = hloc[NV * h + 1];
         if (!hcut[h]) {
+          // carry of the owner thread: later threads of its warp, then later warps, then later tiles
           Acc k0 = tc[o], k1 = tc[kTcStride + o];
-          if (!tflag[o]) { k0 = P::comb(k0, C0); k1 = P::comb(k1, C1); }
+          if (!tflag[o]) {
+            k0 = P::comb(k0, s_wcar[0][ow]);
+            k1 = P::comb(k1, s_wcar[1][ow]);
+            if (!s_wcflag[ow]) { k0 = P::comb(k0, C0); k1 = P::comb(k1, C1); }
+          }
           s0 = P::comb(s0, k0);
           s1 = P::comb(s1, k1);
         }
@@ -523,28 +557,42 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
     if (lane == 0) { s_wred[0][warp] = r_g1; s_wred[1][warp] = r_g2; s_wred[2][warp] = r_ll; }
     __syncthreads();
     const int par = int(epoch & 1u);
-    const uint32_t ptag = (epoch << 1) | 1u;
-    if (tid == 0) {
-      double p0 = 0.0, p1 = 0.0, p2 = 0.0;
-      for (int ww = 0; ww < kResThreads / 32; ++ww) { p0 += s_wred[0][ww]; p1 += s_wred[1][ww]; p2 += s_wred[2][ww]; }
-      double *pv = prm.pval + 3 * (int64_t(par) * T_ + t);
-      pv[0] = p0; pv[1] = p1; pv[2] = p2;
-      st_release_u32(&prm.pstat[par * T_ + t], ptag);
-      if (trace) trace[3] = gtimer();
+    const uint32_t ptag = epoch;
+    if (warp == 0) {
+      double p0 = s_wred[0][lane], p1 = s_wred[1][lane], p2 = s_wred[2][lane];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        p0 += __shfl_down_sync(0xffffffffu, p0, off);
+        p1 += __shfl_down_sync(0xffffffffu, p1, off);
+        p2 += __shfl_down_sync(0xffffffffu, p2, off);
+      }
+      if (lane == 0) {
+        uint64_t *w = prm.tpart + 6 * (int64_t(par) * T_ + t);
+        put_tagged(w, ptag, p0);
+        put_tagged(w + 2, ptag, p1);
+        put_tagged(w + 4, ptag, p2);
+        if (trace) trace[3] = gtimer();
+      }
     }
     // ---- 6. all-gather of the CTA partials (one thread per CTA), fixed-order reduction
     if (tid < T_) {
       const long long tstart = clock64();
-      while (ld_relaxed_u32(&prm.pstat[par * T_ + tid]) != ptag) {
+      const uint64_t *w = prm.tpart + 6 * (int64_t(par) * T_ + tid);
+      uint64_t w0, w1, w2, w3, w4, w5;
+      for (;;) {
+        ld_cg_v2(w, w0, w1);
+        ld_cg_v2(w + 2, w2, w3);
+        ld_cg_v2(w + 4, w4, w5);
+        if (tag_ok(w0, ptag) && tag_ok(w1, ptag) && tag_ok(w2, ptag) && tag_ok(w3, ptag) && tag_ok(w4, ptag) &&
+            tag_ok(w5, ptag))
+          break;
         if (clock64() - tstart > kSpinBudget) { atomicCAS(&ctl->error, 0, COX_E_TIMEOUT); break; }
         if (*reinterpret_cast<volatile int32_t *>(&ctl->error) != 0) break;   // another CTA gave up
         __nanosleep(20);
       }
-      fence_acquire_gpu();
-      const double *pv = prm.pval + 3 * (int64_t(par) * T_ + tid);
-      gpart[3 * tid] = ld_relaxed_f64(pv);
-      gpart[3 * tid + 1] = ld_relaxed_f64(pv + 1);
-      gpart[3 * tid + 2] = ld_relaxed_f64(pv + 2);
+      gpart[3 * tid] = untag(w0, w1);
+      gpart[3 * tid + 1] = untag(w2, w3);
+      gpart[3 * tid + 2] = untag(w4, w5);
     } else if (!st.list_over[cur]) {
       // meanwhile the other threads read eta at column j's entries (current since this step's
       // update): the next step's update starts from these values
@@ -591,10 +639,11 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
       }
       if (stop) st.pend_j = -1;   // this step already applied the pending update
       if (!stop) {
-        const double g1 = -D.dX[j] + G1, g2 = G2;
-        const int pen = F.penalize ? F.penalize[j] != 0 : 1;
-        const double b_old = ld_relaxed_f64(&F.beta[j]);   // written by CTA 0 at an earlier step
-        double tr = ld_relaxed_f64(&F.trust[j]);
+        const double g1 = -pre_dx + G1, g2 = G2;
+        const int pen = pre_pen;
+        // with one column, CTA 0 wrote beta_0 in the previous step: read it after this all-gather
+        const double b_old = D.p >= 2 ? pre_b : ld_relaxed_f64(&F.beta[j]);
+        double tr = D.p >= 2 ? pre_tr : ld_relaxed_f64(&F.trust[j]);
         const double s = ccd_step_rule(g1, g2, b_old, &tr, F.penalty, F.lambda, F.l2_var, pen);
         const double b_new = b_old + s;
         if (t == 0) {
@@ -604,7 +653,7 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
         if (s != 0.0) {
           st.pend_j = j;
           st.pend_db = s;
-          st.bdx = st.bdx + s * D.dX[j];
+          st.bdx = st.bdx + s * pre_dx;
           st.pen = st.pen + (penalty_of(F, j, b_new) - penalty_of(F, j, b_old));
         } else {
           st.pend_j = -1;

@@ -97,10 +97,8 @@ struct ResParams {
   DevFit F;               // the fit (its d pointer is not used)
   DevData D;              // the data descriptor
   const int32_t *tile_lo, *tile_g, *tile_k, *col_tile;   // resident tile plan: one tile per CTA
-  uint32_t *tstat;        // [T] look-back status
-  double *tval;           // [6T] look-back values
-  uint32_t *pstat;        // [2T] partial tags, double-buffered by step parity
-  double *pval;           // [2T*3] partials
+  uint64_t *tagg;         // [6T] epoch-tagged tile aggregates (2 values + stratum-end flag)
+  uint64_t *tpart;        // [2][6T] epoch-tagged tile partials, double-buffered by step parity
   int64_t max_steps;      // coordinate steps this launch may take
   uint64_t *trace;        // optional [2][trace_steps][8] phase timestamps (ns) of the first and last CTA
   int64_t trace_steps;

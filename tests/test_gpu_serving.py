@@ -1,0 +1,97 @@
+"""The continuous-batching server (cox_server_*): results in the mix equal standalone fits,
+admission by memory footprint, cancellation."""
+from __future__ import annotations
+
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2310_16238_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+cox = pytest.importorskip("paper_2310_16238_gb300.cox")
+
+
+def _requests():
+    out = []
+    for i in range(6):
+        d, o = synth.stratified_sparse(n=3000 + 4000 * i, p=6 + 3 * i, k=1 + 5 * i, n_support=3, event_frac=0.2,
+                                       dens_lo=0.01, dens_hi=0.3, admin_days=200, lam_per_n=3e-4, seed=100 + i)
+        out.append((d, o))
+    for i in range(4):
+        d, o = synth.time_varying(n_subj=1500 + 1000 * i, p=5 + 2 * i, k=1 + i, density=0.05, event_frac=0.3,
+                                  n_support=3, seed=200 + i)
+        out.append((d, o))
+    d, o = synth.plain_dense(n=500, p=5, seed=300)
+    out.append((d, o))
+    return out
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_results_in_the_mix_equal_standalone_fits():
+    reqs = _requests()
+    alone = []
+    for d, o in reqs:
+        with cox.Handle(d, o, engine=cox.COX_ENGINE_STREAM) as h:
+            alone.append(h.fit())
+    # a budget that holds only a few requests at once, so that the queue, admission and
+    # retirement all take part while the other fits are in flight
+    budget = 6 * max(cox.cox_footprint(d, o) for d, o in reqs)
+    with cox.Server(memory_budget=budget, max_active=5) as srv:
+        ids = [srv.submit(d, o) for d, o in reqs]
+        got = [srv.wait(i, 120.0) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["running"] == 0
+    for (b, info), (bb, ii), (d, o) in zip(alone, got, reqs):
+        assert ii["sweeps"] == info["sweeps"] and ii["converged"] == info["converged"]
+        assert _rel(bb, b) <= 1e-12, (d.recipe, _rel(bb, b))
+        assert abs(ii["loglik"] - info["loglik"]) <= 1e-12 * abs(info["loglik"])
+        assert ii["total_ms"] >= ii["wait_ms"] >= 0.0
+
+
+def test_concurrent_submitters_and_polling():
+    reqs = _requests()[:6]
+    results = {}
+    with cox.Server(max_active=3) as srv:
+        def worker(k):
+            d, o = reqs[k]
+            rid = srv.submit(d, o)
+            while True:
+                r = srv.poll(rid)
+                if r is not None:
+                    results[k] = r
+                    return
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(len(reqs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(120)
+    assert len(results) == len(reqs)
+    for k, (d, o) in enumerate(reqs):
+        with cox.Handle(d, o, engine=cox.COX_ENGINE_STREAM) as h:
+            b, info = h.fit()
+        assert _rel(results[k][0], b) <= 1e-12
+
+
+def test_admission_rejects_requests_above_the_budget_and_cancel_frees():
+    d, o = synth.stratified_sparse(n=20000, p=8, k=3, n_support=3, event_frac=0.2, dens_lo=0.01, dens_hi=0.3,
+                                   admin_days=200, seed=5)
+    fp = cox.cox_footprint(d, o)
+    with cox.Server(memory_budget=fp // 2) as srv:
+        with pytest.raises(cox.CoxError) as e:
+            srv.submit(d, o)
+        assert e.value.code == cox.COX_E_ADMISSION
+    with cox.Server(memory_budget=4 * fp, max_active=1) as srv:
+        a = srv.submit(d, synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=0.0, max_sweeps=1_000_000))
+        b = srv.submit(d, o)
+        srv.cancel(a)
+        with pytest.raises(cox.CoxError):
+            srv.wait(a, 60.0)
+        rb = srv.wait(b, 60.0)
+        assert rb is not None and rb[1]["converged"]
+        st = srv.stats()
+        assert st["bytes_in_use"] == 0 and st["running"] == 0

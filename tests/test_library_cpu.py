@@ -43,7 +43,9 @@ def test_struct_layouts_match_header():
     assert C.sizeof(cox.cox_data) == 8 + 8 + 7 * 8
     # 2*int32, 2 doubles, ptr, double, 2*int32, ptr
     assert C.sizeof(cox.cox_options) == 8 + 16 + 8 + 8 + 8 + 8 + 8
-    assert C.sizeof(cox.cox_fit_info) == 8 + 8 + 16 + 8 + 16
+    assert C.sizeof(cox.cox_fit_info) == 8 + 8 + 16 + 8 + 16 + 16
+    assert C.sizeof(cox.cox_server_options) == 8 + 16
+    assert C.sizeof(cox.cox_server_stats) == 24 + 16 + 16 + 16
 
 
 def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):

@@ -368,6 +368,8 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
     Acc a0 = P::zero(), a1 = P::zero();
     int seen = 0;
     const bool any_nz = __any_sync(0xffffffffu, zm != 0u);
+    // warps whose slots all lie past the tile's end hold zeros only: nothing to scan
+    if (__any_sync(0xffffffffu, b0 < hi - lo))
 #pragma unroll
     for (int k = ITEMS - 1; k >= 0; --k) {
       if ((cm >> k) & 1u) { a0 = P::zero(); a1 = P::zero(); seen = 1; }

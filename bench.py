@@ -90,6 +90,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):
+    """Whole-job throughput over replicas: every rank processed `units_per_rank` per step; the
+    job's step time is the slowest rank's (max over ranks)."""
+    slowest = float(ms_per_step)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_per_step], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        slowest = float(t.item())
+    return units_per_rank * world / (slowest * 1e-3), slowest
+
+
 def workload(rank: int, scale: float = 1.0):
     n = int(2_000_000 * scale)
     data, opts = synth.stratified_sparse(n=n, p=2000, k=100, seed=synth.SEED_BASE + 2 + rank)
@@ -181,13 +193,8 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "hbm", "achieved": hbm_equiv, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
                     "traffic": None, "kernel": f"ccd ({engine})", "step_us": step_us, "alg_bytes_per_step": alg_bytes,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # gather max over ranks
-    vals = np.array([coords / (step_ms * 1e-3), step_ms], dtype=np.float64)
-    if world > 1:
-        t = torch.tensor(vals, device=dev)
-        torch.distributed.all_reduce(t[1:2], op=torch.distributed.ReduceOp.MAX)
-        vals = t.cpu().numpy()
-    value = coords * world / (vals[1] * 1e-3)
+    value, slowest_ms = aggregate_ranks(coords, step_ms, world, dev)
+    vals = np.array([value, slowest_ms])
     result = {
         "metric": "coordinate updates/sec (CCD, stratified Cox, one fit per step)",
         "value": value, "unit": "coord_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

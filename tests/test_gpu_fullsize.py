@@ -1,0 +1,112 @@
+"""Parity at the full benchmark sizes, in the engine the benchmark uses, on sampled outputs the
+oracle can compute one by one: risk-set sums, log-likelihood and derivatives at a random beta for
+a few sampled coordinates, and the optimality conditions of the GPU fit checked by the oracle.
+Tolerances as in the small-size parity tests: FP64 sums and log-likelihood 1e-12, derivatives
+1e-10 on their own scale; FP32C sums 1e-6, log-likelihood 1e-7, derivatives 1e-5."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_16238_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+cox = pytest.importorskip("paper_2310_16238_gb300.cox")
+
+
+@pytest.fixture(scope="module")
+def stratified_full():
+    return synth.stratified_sparse()          # N = 2e6, p = 2000, K = 100 (the bench workload)
+
+
+@pytest.fixture(scope="module")
+def counting_full():
+    return synth.time_varying()               # 1e6 subjects, ~2.9e6 rows, p = 5000, K = 20
+
+
+def _magnitudes(data, beta, j):
+    """Sum over all rows of exp(eta) and of |x_j| exp(eta): the scale that bounds the rounding
+    error of a risk-set sum whose entries and exits cancel (counting-process rows)."""
+    D = np.exp(oracle.eta(data, beta))
+    a, b = data.col_ptr[j], data.col_ptr[j + 1]
+    x = np.ones(b - a) if data.val is None else np.abs(data.val[a:b])
+    return float(D.sum()), float(np.sum(x * D[data.row_idx[a:b]]))
+
+
+def _sampled_parity(data, opts, precision, engine_expect, rtol_sum, rtol_ll, rtol_g):
+    rng = np.random.default_rng(1)
+    beta = np.zeros(data.p)
+    sup = rng.choice(data.p, 40, replace=False)
+    beta[sup] = rng.normal(0, 0.2, 40)
+    cols = [int(c) for c in rng.choice(data.p, 3, replace=False)] + [int(sup[0])]
+    dX = oracle.dX(data)
+    with cox.Handle(data, opts, precision=precision) as h:
+        ll, oll = h.loglik(beta), oracle.loglik(data, beta)
+        assert abs(ll - oll) <= rtol_ll * _ll_scale(data, beta, oll), (ll, oll)
+        g1, g2 = h.gradient(beta)
+        o1, o2 = oracle.grad_hess(data, beta, cols)
+        for k, j in enumerate(cols):
+            scale = max(1.0, abs(o1[k]), abs(dX[j]), abs(o2[k]))
+            assert abs(g1[j] - o1[k]) <= rtol_g * scale, (j, g1[j], o1[k])
+            assert abs(g2[j] - o2[k]) <= rtol_g * scale, (j, g2[j], o2[k])
+        j = cols[0]
+        S0, S1 = h.risk_sums(beta, j)
+        O0, O1, _ = oracle.risk_sums(data, beta, j)
+        t0, t1 = _magnitudes(data, beta, j) if data.start is not None else (0.0, 0.0)
+        assert np.all(np.abs(S0 - O0) <= rtol_sum * (np.abs(O0) + t0))
+        assert np.all(np.abs(S1 - O1) <= rtol_sum * (np.abs(O1) + t1))
+        bfit, info = h.fit()
+        assert info["converged"]
+        assert (info["step_launches"] == 1) == (engine_expect == "resident")
+    return bfit, info
+
+
+def _ll_scale(data, beta, ll):
+    """Magnitude of the terms the log-likelihood sums: |loglik|, sum |beta_j dX_j| and the events."""
+    dX = oracle.dX(data)
+    return max(abs(ll), float(np.sum(np.abs(beta * dX))) + float(np.sum(data.event)))
+
+
+def _kkt(data, opts, beta, objective, cols):
+    """KKT conditions of the penalized objective at the GPU fit, with the oracle's derivatives.
+
+    The fit stopped when a whole sweep lowered the objective by at most tol*|objective|; a
+    coordinate whose optimality residual is r would lower it by about r^2 / (2 g'') in one
+    Newton step, so r is bounded by sqrt(2 g'' tol |objective|) (times a safety factor 10)."""
+    g1, g2 = oracle.grad_hess(data, beta, cols)
+    for k, j in enumerate(cols):
+        bound = 10.0 * np.sqrt(2.0 * g2[k] * opts.tol * abs(objective)) + 1e-9 * max(1.0, abs(g1[k]))
+        if opts.penalty == synth.PEN_L2:
+            assert abs(g1[k] + beta[j] / opts.l2_var) <= bound, (j, g1[k], beta[j], bound)
+        elif beta[j] != 0.0:
+            assert abs(g1[k] + np.sign(beta[j]) * opts.lam) <= bound, (j, g1[k], beta[j], bound)
+        else:
+            assert abs(g1[k]) <= opts.lam + bound, (j, g1[k], bound)
+
+
+def test_stratified_full_size_fp64_resident(stratified_full):
+    data, opts = stratified_full
+    beta, info = _sampled_parity(data, opts, cox.COX_FP64, "resident", 1e-12, 1e-12, 1e-10)
+    # the bench's L1 weight keeps every coefficient at 0: check that the oracle agrees
+    cols = list(range(0, data.p, 97))
+    _kkt(data, opts, beta, info["objective"], cols)
+    # a weaker penalty moves coefficients: KKT of the GPU fit checked by the oracle
+    o2 = synth.CoxOptions(penalty=synth.PEN_L1, lam=1e-5 * data.n, tol=1e-12)
+    with cox.Handle(data, o2) as h:
+        b2, i2 = h.fit()
+        assert abs(h.loglik(b2) - oracle.loglik(data, b2)) <= 1e-11 * _ll_scale(data, b2, i2["loglik"])
+    assert i2["converged"] and np.count_nonzero(b2) > 0
+    moved = [int(j) for j in np.nonzero(b2)[0][:4]] + cols[:3]
+    _kkt(data, o2, b2, i2["objective"], moved)
+
+
+def test_stratified_full_size_fp32c_resident(stratified_full):
+    data, opts = stratified_full
+    _sampled_parity(data, opts, cox.COX_FP32C, "resident", 1e-6, 1e-7, 1e-5)
+
+
+def test_counting_full_size_streaming(counting_full):
+    data, opts = counting_full
+    beta, info = _sampled_parity(data, opts, cox.COX_FP64, "streaming", 1e-12, 1e-12, 1e-10)
+    _kkt(data, opts, beta, info["objective"], [0, 1, 2, int(np.argmax(np.abs(beta)))])

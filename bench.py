@@ -90,6 +90,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
+
+
 def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):
     """Whole-job throughput over replicas: every rank processed `units_per_rank` per step; the
     job's step time is the slowest rank's (max over ranks)."""
@@ -170,18 +173,28 @@ def run_ours(args, rank, world, local_rank):
     nnz_mean = float(np.diff(data.col_ptr).mean())
     steps_run = float(np.sum([i["coord_updates"] + 1 for i in infos]))
     step_us = float(np.sum([i["sweep_ms"] for i in infos])) / steps_run * 1e3
-    engine = "resident" if infos[-1]["step_launches"] == 1 else "streaming"
+    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
     moved = np.count_nonzero(beta) > 0
-    # paper's dense-scan method: bytes one step must move through memory
-    alg_bytes = s_e * M + 8.0 * G + 4.0 * K + 4.0 * nnz_mean + ((4 + 16 + s_e) * nnz_mean if moved else 0.0)
     peaks = _peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    hbm_equiv = alg_bytes / (step_us * 1e-6) / 1e9
-    if s_e == 8:
-        # FP64 instructions one step needs: one add per position (sum of D), one per column entry
-        # (sum of N1), and per tie group a divide, a multiply and two multiply-adds (ratios, G1, G2)
+    fp64_peak = 1.25e12 / 2 / 1e9   # recipe: 1.25 TFLOP/s FP64 = 0.625e12 FP64 instructions/s
+    p_cols = data.p
+    nnz_pos = nnz_mean * (2.0 if data.start is not None else 1.0)
+    if engine == "incremental":
+        # per coordinate step: a suffix of dD and one of v over the column's entries, and per tie
+        # group two adds, a divide and two multiply-adds; plus the dense S0 rebuild (one add per
+        # position) once per sweep, spread over the sweep's p steps
+        alg_ops = 2.0 * nnz_pos + 5.0 * G + M / p_cols
+        # bytes: the column's entries (4) with eta and v read (8 + s_e) and, when beta moved,
+        # written back; plus the rebuild's read of v once per sweep
+        alg_bytes = (4.0 + 8.0 + s_e) * nnz_pos + ((8.0 + s_e) * nnz_pos if moved else 0.0) + s_e * M / p_cols
+    else:
+        # paper's dense-scan method: one add per position (sum of D), one per column entry (sum of
+        # N1), and per tie group a divide, a multiply and two multiply-adds (ratios, G1, G2)
         alg_ops = M + nnz_mean + 4.0 * G
-        fp64_peak = 1.25e12 / 2 / 1e9   # recipe: 1.25 TFLOP/s FP64 = 0.625e12 FP64 instructions/s
+        alg_bytes = s_e * M + 8.0 * G + 4.0 * K + 4.0 * nnz_mean + ((4 + 16 + s_e) * nnz_mean if moved else 0.0)
+    hbm_equiv = alg_bytes / (step_us * 1e-6) / 1e9
+    if s_e == 8 or engine == "incremental":
         achieved = alg_ops / (step_us * 1e-6) / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "Gop/s (FP64)",
                     "frac": achieved / fp64_peak, "traffic": None, "kernel": f"ccd ({engine})", "step_us": step_us,
@@ -285,7 +298,7 @@ def run_time_varying(args):
             "config": {"workload": f"time_varying subjects={n_subj} rows={data.n} p=5000 K=20 L2 var=0.1",
                        "precision": args.precision, "sweeps": infos[-1]["sweeps"], "loglik": infos[-1]["loglik"],
                        "step_us": float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3,
-                       "engine": "resident" if infos[-1]["step_launches"] == 1 else "streaming"}}
+                       "engine": ENGINE_NAMES.get(infos[-1]["engine"], "unknown")}}
 
 
 def run_batch(args):

@@ -93,10 +93,16 @@ typedef struct {
  *   stream     cudaStream_t (NULL = default stream)
  *   tile       positions per tile of the streaming kernel, 0 = library default; a multiple
  *              of 32 in [1024, 4096 (FP64) or 8192 (FP32C)] otherwise
- *   engine     COX_ENGINE_AUTO: the resident kernel when the data qualify (binary X and the
- *              whole risk sequence fits the GPU's shared memory), else streaming;
- *              COX_ENGINE_STREAM / COX_ENGINE_RESIDENT force one (RESIDENT fails with
- *              COX_E_INVALID when the data do not qualify) */
+ *   engine     COX_ENGINE_AUTO: the incremental kernel when the data qualify (binary X; per
+ *              co-resident CTA at most 1024 tie groups, 65,536 risk positions and 1024
+ *              entries of any column), else the resident kernel when the data qualify
+ *              (binary X and the whole risk sequence fits the GPU's shared memory), else
+ *              streaming. COX_ENGINE_STREAM / _RESIDENT / _INCR force one; RESIDENT and
+ *              INCR fail with COX_E_INVALID when the data do not qualify. The incremental
+ *              kernel keeps each tie group's risk-set sum S0 resident and updates it from
+ *              the changed positions (cost per coordinate O(groups + nnz_j), not O(n)),
+ *              rebuilding it from a full scan at the start of every sweep; it computes the
+ *              sums in FP64 for either precision (COX_FP32C stores exp(eta) as float). */
 typedef struct {
   int32_t penalty;
   int32_t precision;
@@ -111,7 +117,7 @@ typedef struct {
   int32_t reserved;
 } cox_options;
 
-enum { COX_ENGINE_AUTO = 0, COX_ENGINE_STREAM = 1, COX_ENGINE_RESIDENT = 2 };
+enum { COX_ENGINE_AUTO = 0, COX_ENGINE_STREAM = 1, COX_ENGINE_RESIDENT = 2, COX_ENGINE_INCR = 3 };
 
 typedef struct {
   int32_t sweeps;          /* full sweeps over the p coordinates */
@@ -120,7 +126,8 @@ typedef struct {
   double loglik;           /* unpenalized log partial likelihood at beta_out */
   double objective;        /* -loglik + penalty at beta_out */
   int32_t status;          /* same as the return code */
-  int32_t reserved;
+  int32_t engine;          /* the kernel that ran the sweeps: COX_ENGINE_STREAM / _RESIDENT / _INCR
+                              (0 when no sweep ran) */
   int64_t step_launches;   /* coordinate-step kernel launches issued by the sweep loop */
   double sweep_ms;         /* CUDA-event time of the sweep loop on the fit's stream */
   double wait_ms;          /* serving only: submission to admission (device memory granted) */

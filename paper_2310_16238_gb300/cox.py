@@ -22,7 +22,7 @@ COX_E_INVALID, COX_E_UNSORTED, COX_E_OOM, COX_E_CUDA = -1, -2, -3, -4
 COX_E_TIMEOUT, COX_E_ADMISSION, COX_E_RANGE, COX_E_NOT_FOUND, COX_E_BUSY = -5, -6, -7, -8, -9
 COX_PEN_NONE, COX_PEN_L1, COX_PEN_L2 = 0, 1, 2
 COX_FP64, COX_FP32C = 0, 1
-COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT = 0, 1, 2
+COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1, 2, 3
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
@@ -51,14 +51,14 @@ class cox_options(C.Structure):
 
 class cox_fit_info(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("converged", C.c_int32), ("coord_updates", C.c_int64),
-                ("loglik", C.c_double), ("objective", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("loglik", C.c_double), ("objective", C.c_double), ("status", C.c_int32), ("engine", C.c_int32),
                 ("step_launches", C.c_int64), ("sweep_ms", C.c_double), ("wait_ms", C.c_double),
                 ("total_ms", C.c_double)]
 
     def as_dict(self):
         return dict(sweeps=self.sweeps, converged=bool(self.converged), coord_updates=self.coord_updates,
                     loglik=self.loglik, objective=self.objective, status=self.status,
-                    step_launches=self.step_launches, sweep_ms=self.sweep_ms, wait_ms=self.wait_ms,
+                    engine=self.engine, step_launches=self.step_launches, sweep_ms=self.sweep_ms, wait_ms=self.wait_ms,
                     total_ms=self.total_ms)
 
 

@@ -73,6 +73,10 @@ struct cox_handle {
   double *S0 = nullptr, *S1 = nullptr;
   // resident-kernel scratch (allocated when the data qualify)
   uint64_t *r_tagg = nullptr, *r_tpart = nullptr;
+  // incremental-kernel scratch (allocated when the data qualify)
+  uint64_t *i_trec = nullptr, *i_tref = nullptr;
+  double *i_bcopy = nullptr;
+  dw *i_vdw = nullptr;
   std::string err = "no error";
 };
 
@@ -106,7 +110,7 @@ int resolve_stream(cox_handle *h) {
 
 int check_options(const cox_options *o) {
   if (!o) return COX_OK;
-  if (o->engine < COX_ENGINE_AUTO || o->engine > COX_ENGINE_RESIDENT) return COX_E_INVALID;
+  if (o->engine < COX_ENGINE_AUTO || o->engine > COX_ENGINE_INCR) return COX_E_INVALID;
   if (o->penalty < COX_PEN_NONE || o->penalty > COX_PEN_L2) return COX_E_INVALID;
   if (o->precision != COX_FP64 && o->precision != COX_FP32C) return COX_E_INVALID;
   if (o->penalty == COX_PEN_L1 && !(o->lambda >= 0.0)) return COX_E_INVALID;
@@ -158,6 +162,14 @@ int alloc_fit_state(cox_handle *h) {
     h->r_tpart = static_cast<uint64_t *>(B.get(12 * RT * sizeof(uint64_t)));
     if (!h->r_tagg || !h->r_tpart)
       return fail(h, COX_E_OOM, "device allocation failed for the resident state");
+  }
+  if (const int IT = h->sd->prep.inc_T) {
+    h->i_trec = static_cast<uint64_t *>(B.get(2 * kIncRecWords * int64_t(IT) * sizeof(uint64_t)));
+    h->i_tref = static_cast<uint64_t *>(B.get(4 * int64_t(IT) * sizeof(uint64_t)));
+    h->i_bcopy = static_cast<double *>(B.get(std::max<int64_t>(2 * p * IT, 1) * sizeof(double)));
+    h->i_vdw = static_cast<dw *>(B.get(std::max<int64_t>(M, 1) * 2 * sizeof(float)));
+    if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw)
+      return fail(h, COX_E_OOM, "device allocation failed for the incremental state");
   }
   if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
@@ -408,6 +420,105 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
     info->loglik = c.loglik;
     info->objective = c.obj;
     info->status = rc;
+    info->engine = COX_ENGINE_RESIDENT;
+    info->step_launches = 1;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->sweep_ms = ms;
+  }
+  const int rc2 = copy_out(h, beta_out, h->hfit.beta, d.p);
+  return rc2 ? rc2 : rc;
+}
+
+// The whole fit in one cooperative launch of the incremental kernel (state already initialized).
+int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
+  const DevData &d = D(h);
+  const Prepared &P = h->sd->prep;
+  const int IT = P.inc_T;
+  cudaStream_t s = h->stream;
+  // tag 0 never matches: records start at epoch 1
+  if (cudaMemsetAsync(h->i_trec, 0, 2 * kIncRecWords * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess ||
+      cudaMemsetAsync(h->i_tref, 0, 4 * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess)
+    return cuda_fail(h, "memset");
+  IncParams prm{};
+  prm.F = h->hfit;
+  prm.D = d;
+  prm.tile_lo = P.inc_tile_lo;
+  prm.tile_g = P.inc_tile_g;
+  prm.tile_k = P.inc_tile_k;
+  prm.col_tile = P.inc_col_tile;
+  prm.trec = h->i_trec;
+  prm.tref = h->i_tref;
+  prm.bcopy = h->i_bcopy;
+  prm.vdw = h->i_vdw;
+  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
+  // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
+  const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
+  const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
+  BufferSet trbuf;
+  if (tr_steps > 0) {
+    prm.trace = static_cast<uint64_t *>(trbuf.get(tr_steps * IT * 8 * sizeof(uint64_t)));
+    prm.trace_steps = prm.trace ? tr_steps : 0;
+    if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * IT * 8 * sizeof(uint64_t), s);
+  }
+  if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
+    return cuda_fail(h, "event create");
+  cudaEventRecord(h->ev0, s);
+  if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+  cudaEventRecord(h->ev1, s);
+  int rc;
+  if ((rc = read_ctl(h))) return rc;
+  if (prm.trace_steps > 0) {
+    // mean phase times per CTA and the publish time after the earliest step start, for the
+    // slowest CTAs (phases: update, scans, S0 and ratios, partials and publish, all-gather,
+    // record reductions, step)
+    constexpr int kPh = 7;
+    std::vector<uint64_t> tr(size_t(prm.trace_steps * IT * 8));
+    cudaMemcpy(tr.data(), prm.trace, tr.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    std::vector<double> pub(IT, 0.0), ph(kPh * IT, 0.0), tot(IT, 0.0);
+    int64_t n = 0;
+    for (int64_t k = 1; k < prm.trace_steps; ++k) {
+      uint64_t t0 = ~0ull;
+      bool ok = true;
+      for (int c = 0; c < IT; ++c) {
+        const uint64_t *r = &tr[size_t((k * IT + c) * 8)];
+        for (int q = 0; q < 8; ++q) ok = ok && r[q] != 0;
+        t0 = std::min(t0, r[0]);
+      }
+      if (!ok) continue;
+      for (int c = 0; c < IT; ++c) {
+        const uint64_t *r = &tr[size_t((k * IT + c) * 8)];
+        pub[c] += double(r[4] - t0);
+        tot[c] += double(r[7] - r[0]);
+        for (int q = 0; q < kPh; ++q) ph[kPh * c + q] += double(r[q + 1] - r[q]);
+      }
+      ++n;
+    }
+    std::vector<int> order(IT);
+    for (int c = 0; c < IT; ++c) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return pub[a] > pub[b]; });
+    std::fprintf(stderr, "[phase trace] incremental kernel, %lld steps x %d CTAs (ns): publish-after-first-start | "
+                 "update scans S0+ratios publish gather reduce step | total\n", (long long)n, IT);
+    auto row = [&](const char *tag, int c) {
+      std::fprintf(stderr, "  %s CTA %3d: %6.0f | %5.0f %5.0f %5.0f %5.0f %5.0f %5.0f %5.0f | %6.0f\n", tag, c, pub[c] / n,
+                   ph[kPh * c] / n, ph[kPh * c + 1] / n, ph[kPh * c + 2] / n, ph[kPh * c + 3] / n, ph[kPh * c + 4] / n,
+                   ph[kPh * c + 5] / n, ph[kPh * c + 6] / n, tot[c] / n);
+    };
+    for (int q = 0; q < std::min(IT, 4) && n; ++q) row("slow", order[q]);
+    if (n) row("fast", order[IT - 1]);
+  }
+  if ((rc = device_error(h))) return rc;
+  const FitCtl &c = *h->h_ctl;
+  if (c.state == kRunning) return fail(h, COX_E_INVALID, "cox_fit: the incremental kernel stopped before the fit did");
+  rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
+  if (info) {
+    info->sweeps = c.sweep;
+    info->converged = c.state == kConverged;
+    info->coord_updates = c.coord_updates;
+    info->loglik = c.loglik;
+    info->objective = c.obj;
+    info->status = rc;
+    info->engine = COX_ENGINE_INCR;
     info->step_launches = 1;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -528,8 +639,20 @@ int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *
     }
     return copy_out(h, beta_out, h->hfit.beta, d.p);
   }
-  const bool resident = h->opts.engine != COX_ENGINE_STREAM && h->sd->prep.res_T > 0;
-  if (h->opts.engine == COX_ENGINE_RESIDENT && !resident)
+  const int eng = h->opts.engine;
+  const bool incr = (eng == COX_ENGINE_AUTO || eng == COX_ENGINE_INCR) && h->sd->prep.inc_T > 0;
+  if (eng == COX_ENGINE_INCR && !incr)
+    return fail(h, COX_E_INVALID,
+                "cox_fit: the data do not qualify for the incremental kernel (binary X; per CTA at most 1024 tie groups, "
+                "65536 positions and 1024 entries of a column)");
+  if (incr) {
+    rc = fit_incr(h, beta_out, info);
+    // its double-word sums hold |eta - shift| <= 60; beyond that AUTO refits with an FP64 engine
+    if (rc != COX_E_RANGE || eng != COX_ENGINE_AUTO) return rc;
+    if ((rc = init_state(h, beta0))) return rc;
+  }
+  const bool resident = (eng == COX_ENGINE_AUTO || eng == COX_ENGINE_RESIDENT) && h->sd->prep.res_T > 0;
+  if (eng == COX_ENGINE_RESIDENT && !resident)
     return fail(h, COX_E_INVALID, "cox_fit: the data do not qualify for the resident kernel (binary X, sequence within shared memory)");
   if (resident) return fit_resident(h, beta_out, info);
   const int len = kSweepBody;
@@ -562,6 +685,7 @@ int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *
     info->loglik = c.loglik;
     info->objective = c.obj;
     info->status = rc;
+    info->engine = COX_ENGINE_STREAM;
     info->step_launches = launched;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);

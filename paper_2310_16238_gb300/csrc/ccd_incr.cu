@@ -1,0 +1,950 @@
+// Incremental risk-set kernel: the per-tie-group risk-set sums S0 stay in registers across
+// coordinate steps and are updated from the changed positions only (arXiv 2310.16238 §2.4-§2.7
+// for the method; this is an exact reformulation of its segmented scans, not the paper's layout).
+//
+// One cooperative launch of one 1024-thread CTA per SM runs the whole fit. CTA t owns the risk
+// positions [tile_lo[t], tile_lo[t+1]) and the tie groups whose read position lies there (thread
+// h holds group h: its S0, read position, stratum segment and events). A coordinate step for
+// column j touches only the positions of column j's nonzeros:
+//   * the previous step's update (eta += dbeta, eq. parallel_xb; v = +-exp(eta - shift), eq.
+//     parallel_d) changes v at column j-1's entries by dD = v (e^dbeta - 1); S0 of every group
+//     grows by the segmented suffix sum of dD from its read position (strata are segments), plus,
+//     for groups whose stratum continues past the tile, the change in the later tiles;
+//   * S1 of every group is the segmented suffix sum of v over column j's entries, plus the later
+//     tiles' share, so the tie-group ratios of eqs. (parallel_g)/(parallel_h) cost
+//     O(groups + entries) per tile instead of O(positions);
+//   * the later tiles' shares come from the previous step's exchange: with binary X a tile's
+//     head-segment sums after an update by d are R + (e^d - 1) I, so every CTA publishes the sums
+//     it will need one step ahead, and one all-gather per step serves both the carries and the
+//     Newton / trust-region / L1 step (§2.4), which every CTA computes identically.
+// At the first step of a launch and of every sweep (where the log-likelihood is evaluated) v is
+// recomputed from eta at every position and S0 rebuilt from a dense scan, which bounds the
+// rounding that the multiplicative updates and the incremental sums accumulate within a sweep.
+//
+// Arithmetic: sums, scans and ratios use double-word floats (dw.cuh, about 48 bits; FP64 issue
+// is 64 cycles per warp instruction per sub-partition on this GPU); eta, beta, the step rule and
+// the log-likelihood are FP64. v is held as a double-word per position (vdw), so the float
+// exponent range applies: |eta - shift| above kIncRange raises COX_E_RANGE (the library then
+// falls back to an FP64 engine). Column j+2's entries and their eta and v are fetched while step
+// j waits on the exchange.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ccd_common.cuh"
+#include "cox.h"
+#include "cox_internal.h"
+#include "dw.cuh"
+
+namespace coxgb {
+
+constexpr int kIncThreads = 1024;
+constexpr int kIncGroupCap = 1024;   // tie groups per CTA (one per thread)
+constexpr int kIncListCap = 1024;    // entries of one column per CTA (one per thread)
+constexpr int kIncPosCap = 65536;    // positions per CTA (bitmask capacity)
+constexpr int kIncWords = kIncPosCap / 32;
+constexpr int kIncMaxCtas = 256;
+constexpr int kIncRec = kIncRecWords / 2;   // step record: G1, G2, LL, H1, R, I, error code
+constexpr double kIncRange = 60.0;          // |eta - shift| that keeps every sum inside float range
+constexpr unsigned kFull = 0xffffffffu;
+
+constexpr size_t inc_al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+struct IncSmem {
+  static constexpr size_t o_lpos = 0;                                   // u32 [4][cap] entry positions
+  static constexpr size_t o_lv = o_lpos + 4 * 4 * kIncListCap;          // dw  [4][cap] v at the entries
+  static constexpr size_t o_le = o_lv + 4 * 8 * kIncListCap;            // f64 [4][cap] eta at the entries
+  static constexpr size_t o_u0 = o_le + 4 * 8 * kIncListCap;            // dw  [cap] suffix of dD
+  static constexpr size_t o_u1 = o_u0 + 8 * kIncListCap;                // dw  [cap] suffix of v
+  static constexpr size_t o_cutb = o_u1 + 8 * kIncListCap;              // u32 [W] stratum ends
+  static constexpr size_t o_cutp = o_cutb + 4 * kIncWords;              // i32 [W] prefix counts
+  static constexpr size_t o_headb = o_cutp + 4 * kIncWords;             // u32 [W] read positions
+  static constexpr size_t o_headp = o_headb + 4 * kIncWords;            // i32 [W]
+  static constexpr size_t o_gs0 = o_headp + 4 * kIncWords;              // dw  [gcap] dense-scan S0
+  static constexpr size_t o_gseen = o_gs0 + 8 * kIncGroupCap;           // u8  [gcap]
+  static constexpr size_t o_rec = inc_al16(o_gseen + kIncGroupCap);     // 8-byte slots [C][7] records
+  static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
+  static constexpr size_t bytes = o_rref + 8 * 2 * kIncMaxCtas;
+};
+
+int inc_group_cap() { return kIncGroupCap; }
+int inc_list_cap() { return kIncListCap; }
+int inc_pos_cap() { return kIncPosCap; }
+
+// Step-synchronous control state, identical in every CTA.
+struct IncState {
+  int32_t j, sweep, need_ll, pend_j, state;
+  double pend_db, obj_prev, bdx, pen, loglik, obj;
+  dw E;                      // e^pend_db - 1
+  int64_t coord_updates;
+  uint32_t epoch;
+};
+
+// ---- epoch-tagged exchange words: (epoch << 32) | 32 data bits; relaxed 8-byte accesses are
+// single-copy atomic, so a reader that sees the tag has the data of that epoch
+static __device__ __forceinline__ void st_rlx_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void ld_rlx_v2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+static __device__ __forceinline__ void put_tag2(uint64_t *w, uint32_t tag, uint32_t a, uint32_t b) {
+  st_rlx_u64(w, (uint64_t(tag) << 32) | a);
+  st_rlx_u64(w + 1, (uint64_t(tag) << 32) | b);
+}
+static __device__ __forceinline__ void put_dw(uint64_t *w, uint32_t tag, dw v) {
+  put_tag2(w, tag, __float_as_uint(v.h), __float_as_uint(v.l));
+}
+static __device__ __forceinline__ void put_f64(uint64_t *w, uint32_t tag, double v) {
+  const uint64_t b = uint64_t(__double_as_longlong(v));
+  put_tag2(w, tag, uint32_t(b), uint32_t(b >> 32));
+}
+static __device__ __forceinline__ bool tagged(uint64_t a, uint64_t b, uint32_t tag) {
+  return uint32_t(a >> 32) == tag && uint32_t(b >> 32) == tag;
+}
+static __device__ __forceinline__ uint64_t inc_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// a record slot holds either a double-word or an FP64 value in 8 bytes
+static __device__ __forceinline__ dw slot_dw(const uint64_t *s) { return *reinterpret_cast<const dw *>(s); }
+static __device__ __forceinline__ double slot_f64(const uint64_t *s) { return *reinterpret_cast<const double *>(s); }
+
+// Wait for N tagged 8-byte payloads at w (2 words each; all loads of a poll in flight together)
+// and store the payloads (low halves of the word pairs) in out. false: the wait gave up (bound
+// reached or another CTA raised an error).
+template <int N>
+static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *out, int32_t *err) {
+  const long long t0 = clock64();
+  unsigned polls = 0;
+  for (;;) {
+    uint64_t a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) ld_rlx_v2(w + 2 * i, a[i], b[i]);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) ok = ok && tagged(a[i], b[i], tag);
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) out[i] = (a[i] & 0xffffffffull) | ((b[i] & 0xffffffffull) << 32);
+      return true;
+    }
+    if ((++polls & 63) == 0) {   // off the fast path: the bound and another CTA's failure
+      if (clock64() - t0 > kSpinBudget) {
+        atomicCAS(err, 0, COX_E_TIMEOUT);
+        return false;
+      }
+      if (*reinterpret_cast<volatile int32_t *>(err) != 0) return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+static __device__ __forceinline__ int inc_rank(const uint32_t *bits, const int32_t *pre, int q) {
+  return pre[q >> 5] + __popc(bits[q >> 5] & ((1u << (q & 31)) - 1u));
+}
+static __device__ __forceinline__ int inc_lower_bound(const uint32_t *lp, int n, int q) {
+  int a = 0, b = n;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (int(lp[m] & kPosMask) < q) a = m + 1;
+    else b = m;
+  }
+  return a;
+}
+
+static __device__ double inc_penalty(const DevFit &F, int j, double b) {
+  const bool pen = F.penalize ? F.penalize[j] != 0 : true;
+  if (!pen) return 0.0;
+  if (F.penalty == COX_PEN_L1) return F.lambda * fabs(b);
+  if (F.penalty == COX_PEN_L2) return b * b / (2.0 * F.l2_var);
+  return 0.0;
+}
+
+// v at a position from eta (eq. parallel_d): FP64 exp split into a double-word, or the float
+// exp of the compensated-FP32 precision; exits hold the negative. Raises COX_E_RANGE through
+// serr when |eta - shift| leaves the range the double-word sums can hold.
+template <class P>
+static __device__ __forceinline__ dw inc_v(double eta, double shift, bool exitp, typename P::T *out, int *serr) {
+  const double a = eta - shift;
+  if (!(fabs(a) <= kIncRange)) atomicCAS(serr, 0, COX_E_RANGE);
+  if constexpr (sizeof(typename P::T) == 8) {
+    const double e = exitp ? -exp(a) : exp(a);
+    *out = e;
+    return dw_from(e);
+  } else {
+    const float e = exitp ? -expf(__double2float_rn(a)) : expf(__double2float_rn(a));
+    *out = e;
+    return dw_make(e);
+  }
+}
+
+// Stage column j's entries in this tile (positions relative to lo, exit bit kept) with eta and v
+// at them, using threads [th0, th0 + nth).
+static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo, int npos, uint32_t *lp, dw *lv,
+                                     double *le, int *cnt, int th0, int nth, int *serr) {
+  const DevData &D = prm.D;
+  const int C = gridDim.x;
+  const int64_t cb = D.col_ptr[j];
+  const int32_t *ct = prm.col_tile + int64_t(j) * (C + 1);
+  const int64_t qa = cb + ct[t];
+  int n = ct[t + 1] - ct[t];
+  if (n > kIncListCap || n < 0) {   // the plan keeps every column within the cap
+    if (int(threadIdx.x) == th0) atomicCAS(serr, 0, COX_E_INVALID);
+    n = 0;
+  }
+  for (int m = int(threadIdx.x) - th0; m >= 0 && m < n; m += nth) {
+    const uint32_t e = D.idx[qa + m];
+    int q = int(e & kPosMask) - lo;
+    if (q < 0 || q >= npos) {
+      atomicCAS(serr, 0, COX_E_INVALID);
+      q = 0;
+    }
+    lp[m] = uint32_t(q) | (e & kExitBit);
+    lv[m] = prm.vdw[lo + q];
+    le[m] = prm.F.eta[lo + q];
+  }
+  if (int(threadIdx.x) == th0) *cnt = n;
+}
+
+// Inclusive segmented suffix sums of two sequences held one element per thread (element k =
+// thread k, k < nact; later elements are 0 and end their segments); f = 1 marks the last element
+// of a segment. Warps past nact skip the arithmetic. Results go to out0/out1[k] for k < nact.
+static __device__ void inc_seg_suffix2(dw x0, int f0, dw x1, int f1, int nact, dw *out0, dw *out1, dw (*s_agg)[32],
+                                       int (*s_flg)[32]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool act = warp * 32 < nact;   // warp-uniform
+  if (act) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const dw y0 = dw_shfl_down(x0, off), y1 = dw_shfl_down(x1, off);
+      const int g0 = __shfl_down_sync(kFull, f0, off), g1 = __shfl_down_sync(kFull, f1, off);
+      if (lane + off < 32) {
+        if (!f0) x0 = dw_add(x0, y0);
+        if (!f1) x1 = dw_add(x1, y1);
+        f0 |= g0;
+        f1 |= g1;
+      }
+    }
+  }
+  if (lane == 0) {
+    s_agg[0][warp] = act ? x0 : dw_make(0.0f);
+    s_agg[1][warp] = act ? x1 : dw_make(0.0f);
+    s_flg[0][warp] = act ? f0 : 1;
+    s_flg[1][warp] = act ? f1 : 1;
+  }
+  __syncthreads();
+  const int nwa = (nact + 31) >> 5;
+  if (warp == 0 && nwa > 1) {
+    dw a0 = s_agg[0][lane], a1 = s_agg[1][lane];
+    int h0 = s_flg[0][lane], h1 = s_flg[1][lane];
+    for (int off = 1; off < nwa; off <<= 1) {
+      const dw y0 = dw_shfl_down(a0, off), y1 = dw_shfl_down(a1, off);
+      const int g0 = __shfl_down_sync(kFull, h0, off), g1 = __shfl_down_sync(kFull, h1, off);
+      if (lane + off < 32) {
+        if (!h0) a0 = dw_add(a0, y0);
+        if (!h1) a1 = dw_add(a1, y1);
+        h0 |= g0;
+        h1 |= g1;
+      }
+    }
+    dw c0 = dw_shfl_down(a0, 1), c1 = dw_shfl_down(a1, 1);
+    if (lane == 31) { c0 = dw_make(0.0f); c1 = dw_make(0.0f); }
+    s_agg[0][lane] = c0;   // carry into warp `lane` from the later warps
+    s_agg[1][lane] = c1;
+  }
+  __syncthreads();
+  if (act) {
+    if (nwa > 1) {
+      if (!f0) x0 = dw_add(x0, s_agg[0][warp]);
+      if (!f1) x1 = dw_add(x1, s_agg[1][warp]);
+    }
+    out0[tid] = x0;
+    out1[tid] = x1;
+  }
+}
+
+// The rebuild: v recomputed from eta at every position of the tile (written to vdw and to the
+// fit's v), then a dense segmented suffix of v: every tie group's in-tile S0 (before the carry
+// from the later tiles) into gs0, and the tile's head aggregate (sum from its first position to
+// its first stratum end), returned in warp 0.
+template <class P>
+static __device__ dw inc_dense(const IncParams &prm, int lo, int npos, const uint32_t *cutb, const uint32_t *headb,
+                               const int32_t *headp, dw *gs0, uint8_t *gseen, dw *s_wagg, int *s_wflag, dw *s_wk, int RW,
+                               int *serr) {
+  using T = typename P::T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ws = warp * RW, we = min(ws + RW, npos);
+  const double *etat = prm.F.eta + lo;
+  T *vt = static_cast<T *>(prm.F.v) + lo;
+  dw *vd = prm.vdw + lo;
+  const uint32_t *exitb = prm.D.exit_bits;
+  const double shift = prm.F.shift;
+  dw carry = dw_make(0.0f);
+  int seen = 0;
+  if (ws < we) {
+    const int top = ws + ((we - ws - 1) >> 5) * 32;
+    for (int b = top; b >= ws; b -= 128) {
+      dw xs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int bb = b - 32 * u, p = bb + lane;
+        xs[u] = dw_make(0.0f);
+        if (bb >= ws && p < we) {
+          const int g = lo + p;
+          const bool ex = exitb != nullptr && ((exitb[g >> 5] >> (g & 31)) & 1u);
+          T vv;
+          xs[u] = inc_v<P>(etat[p], shift, ex, &vv, serr);
+          vt[p] = vv;
+          vd[p] = xs[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int bb = b - 32 * u;
+        if (bb < ws) break;
+        const int p = bb + lane;
+        const bool in = p < we;
+        const uint32_t cw = cutb[bb >> 5], hw = headb[bb >> 5];
+        dw x = xs[u];
+        int f = in ? int((cw >> lane) & 1u) : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const dw y = dw_shfl_down(x, off);
+          const int g = __shfl_down_sync(kFull, f, off);
+          if (lane + off < 32) {
+            if (!f) x = dw_add(x, y);
+            f |= g;
+          }
+        }
+        if (!f) x = dw_add(x, carry);
+        if (in && ((hw >> lane) & 1u)) {
+          const int h = headp[bb >> 5] + __popc(hw & ((1u << lane) - 1u));
+          gs0[h] = x;
+          gseen[h] = uint8_t(f | seen);
+        }
+        carry = dw_shfl(x, 0);
+        seen |= __shfl_sync(kFull, f, 0);
+      }
+    }
+  }
+  if (lane == 0) {
+    s_wagg[warp] = carry;
+    s_wflag[warp] = seen;
+  }
+  __syncthreads();
+  dw head = dw_make(0.0f);
+  if (warp == 0) {
+    dw a = s_wagg[lane];
+    int h = s_wflag[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const dw y = dw_shfl_down(a, off);
+      const int g = __shfl_down_sync(kFull, h, off);
+      if (lane + off < 32) {
+        if (!h) a = dw_add(a, y);
+        h |= g;
+      }
+    }
+    dw c = dw_shfl_down(a, 1);
+    if (lane == 31) c = dw_make(0.0f);
+    s_wk[lane] = c;
+    head = dw_shfl(a, 0);
+  }
+  __syncthreads();
+  return head;
+}
+
+// §2.4 step, the same rule as ccd_step_rule with the L2 prior's reciprocal variance given (the
+// scalar step runs on one thread between exchanges, where every FP64 operation is latency).
+static __device__ double inc_step_rule(double g1, double g2, double b, double *tr, int penalty, double lambda,
+                                       double inv_var, int penalized) {
+  double gamma = 0.0;
+  if (penalized && penalty == COX_PEN_L2) {
+    g1 = fma(b, inv_var, g1);
+    g2 = g2 + inv_var;
+  }
+  if (penalized && penalty == COX_PEN_L1) gamma = lambda;
+  double s;
+  if (!(g2 > 0.0) || !isfinite(g1) || !isfinite(g2)) {
+    s = 0.0;
+  } else if (gamma > 0.0) {
+    if (b == 0.0) {
+      if (g1 + gamma < 0.0) s = -(g1 + gamma) / g2;
+      else if (g1 - gamma > 0.0) s = -(g1 - gamma) / g2;
+      else s = 0.0;
+    } else {
+      s = -(g1 + (b > 0.0 ? gamma : -gamma)) / g2;
+    }
+  } else {
+    s = -g1 / g2;
+  }
+  const double t = *tr;
+  if (fabs(s) > t) s = s > 0.0 ? t : -t;
+  if (gamma > 0.0 && b != 0.0) {
+    const double nb = b + s;
+    if ((b > 0.0 && nb < 0.0) || (b < 0.0 && nb > 0.0)) s = -b;
+  }
+  const double a2 = 2.0 * fabs(s), h = 0.5 * t;
+  *tr = a2 > h ? a2 : h;
+  return s;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams prm) {
+  using T = typename P::T;
+  using S = IncSmem;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *lpos = reinterpret_cast<uint32_t *>(smem + S::o_lpos);
+  dw *lv = reinterpret_cast<dw *>(smem + S::o_lv);
+  double *le = reinterpret_cast<double *>(smem + S::o_le);
+  dw *u0 = reinterpret_cast<dw *>(smem + S::o_u0);
+  dw *u1 = reinterpret_cast<dw *>(smem + S::o_u1);
+  uint32_t *cutb = reinterpret_cast<uint32_t *>(smem + S::o_cutb);
+  int32_t *cutp = reinterpret_cast<int32_t *>(smem + S::o_cutp);
+  uint32_t *headb = reinterpret_cast<uint32_t *>(smem + S::o_headb);
+  int32_t *headp = reinterpret_cast<int32_t *>(smem + S::o_headp);
+  dw *gs0 = reinterpret_cast<dw *>(smem + S::o_gs0);
+  uint8_t *gseen = reinterpret_cast<uint8_t *>(smem + S::o_gseen);
+  uint64_t *srec = reinterpret_cast<uint64_t *>(smem + S::o_rec);
+  dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
+
+  __shared__ IncState st;
+  __shared__ int s_cnt[4];
+  __shared__ dw s_agg[2][32];
+  __shared__ int s_flg[2][32];
+  __shared__ dw s_red[4][32];
+  __shared__ double s_rll[32];
+  __shared__ dw s_G[2];
+  __shared__ double s_LL;
+  __shared__ dw s_chain[3];    // chain sums of the previous step's H1, R, I
+  __shared__ dw s_carry[2];    // rebuild: carries of S0 and S1 from the later tiles
+  __shared__ dw s_dagg[32], s_dcar[32];   // dense scan: warp aggregates, carries into warps
+  __shared__ int s_dflg[32];
+  __shared__ int s_chain_end, s_bad, s_err, s_anyerr;
+  __shared__ double s_inv_var;
+
+  const DevFit &F = prm.F;
+  const DevData &D = prm.D;
+  FitCtl *ctl = F.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = blockIdx.x, C = gridDim.x;
+  const int lo = prm.tile_lo[t], hi = prm.tile_lo[t + 1], npos = hi - lo;
+  const int ga = prm.tile_g[t], ng = prm.tile_g[t + 1] - ga;
+  const int kc0 = prm.tile_k[t], nc = prm.tile_k[t + 1] - kc0;
+  const double shift = F.shift;
+  const int p = D.p;
+  double *bet = prm.bcopy + size_t(t) * 2 * size_t(p);   // this CTA's copy of beta and trust
+  double *tru = bet + p;
+
+  // ---- one-time set-up: stratum ends and read positions as bitmasks, group registers, lists
+  if (tid == 0) {
+    s_bad = (npos > kIncPosCap || ng > kIncGroupCap || C > kIncMaxCtas || npos <= 0 || ng < 0) ? 1 : 0;
+    s_err = 0;
+  }
+  __syncthreads();
+  if (s_bad) {   // the plan never builds such a tile
+    if (tid == 0) atomicCAS(&ctl->error, 0, COX_E_INVALID);
+    return;
+  }
+  const int nw = (npos + 31) >> 5;
+  for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; }
+  if (tid == 0) {
+    st.j = ctl->j;
+    st.sweep = ctl->sweep;
+    st.need_ll = ctl->need_ll;
+    st.pend_j = ctl->pend_j;
+    st.pend_db = ctl->pend_db;
+    st.state = ctl->state;
+    st.obj_prev = ctl->obj_prev;
+    st.loglik = ctl->loglik;
+    st.obj = ctl->obj;
+    st.coord_updates = ctl->coord_updates;
+    st.epoch = ctl->epoch;
+    st.E = st.pend_j >= 0 ? dw_from(expm1(st.pend_db)) : dw_make(0.0f);
+    s_inv_var = 1.0 / F.l2_var;
+  }
+  for (int jj = tid; jj < p; jj += kIncThreads) {
+    bet[jj] = F.beta[jj];
+    tru[jj] = F.trust[jj];
+  }
+  __syncthreads();
+  int qg = 0;
+  float dg = 0.0f;   // events of this thread's tie group (exact in float below 2^24)
+  if (tid < ng) {
+    qg = D.head_pos[ga + tid] - lo;
+    dg = float(D.head_d[ga + tid]);
+    if (qg < 0 || qg >= npos) {
+      atomicCAS(&s_err, 0, COX_E_INVALID);
+      qg = 0;
+    }
+    atomicOr(&headb[qg >> 5], 1u << (qg & 31));
+  }
+  for (int k = tid; k < nc; k += kIncThreads) {
+    int q = D.cut_pos[kc0 + k] - lo;
+    if (q < 0 || q >= npos) {
+      atomicCAS(&s_err, 0, COX_E_INVALID);
+      q = 0;
+    }
+    atomicOr(&cutb[q >> 5], 1u << (q & 31));
+  }
+  {   // beta'dX and the penalty at the starting coefficients (same order in every CTA)
+    double ex[2] = {0.0, 0.0};
+    for (int jj = tid; jj < p; jj += kIncThreads) {
+      const double b = F.beta[jj];
+      ex[0] += b * D.dX[jj];
+      ex[1] += inc_penalty(F, jj, b);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) ex[i] += __shfl_down_sync(kFull, ex[i], off);
+    if (lane == 0) { s_rll[warp] = ex[0]; s_red[0][warp] = dw_from(ex[1]); }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double a = s_rll[lane], b = dw_to(s_red[0][lane]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_down_sync(kFull, a, off);
+      b += __shfl_down_sync(kFull, b, off);
+    }
+    if (lane == 0) { st.bdx = a; st.pen = b; }
+  } else if (warp == 1 || warp == 2) {   // prefix counts of the two bitmasks
+    const uint32_t *bits = warp == 1 ? cutb : headb;
+    int32_t *pre = warp == 1 ? cutp : headp;
+    int run = 0;
+    for (int base = 0; base < nw; base += 32) {
+      const int c = base + lane < nw ? __popc(bits[base + lane]) : 0;
+      int incl = c;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+      }
+      if (base + lane < nw) pre[base + lane] = run + incl - c;
+      run += __shfl_sync(kFull, incl, 31);
+    }
+  } else if (tid == 96) {
+    // the later tiles whose head segments continue this tile's last stratum: up to and including
+    // the first tile that holds a stratum end (none when this tile's last position ends one)
+    const bool last_cut = nc > 0 && D.cut_pos[kc0 + nc - 1] == hi - 1;
+    int e = t;
+    if (!last_cut)
+      for (int c = t + 1; c < C; ++c) {
+        e = c;
+        if (prm.tile_k[c + 1] > prm.tile_k[c]) break;
+      }
+    s_chain_end = e;
+  }
+  __syncthreads();
+  const int segg = tid < ng ? inc_rank(cutb, cutp, qg) : 0;
+  const bool tailg = tid < ng && segg == nc;
+  const int RW = max(32, ((npos + 1023) / 1024) * 32);   // positions per warp in the dense scan
+  const double inv_var = s_inv_var;
+  // list slots: previous column (pending update), current, next, and the one being fetched
+  int base = 0;
+  if (st.state == kRunning) {
+    if (st.pend_j >= 0)
+      inc_load_list(prm, t, st.pend_j, lo, npos, lpos, lv, le, &s_cnt[0], 0, kIncThreads, &s_err);
+    else if (tid == 0)
+      s_cnt[0] = 0;
+    const int j1 = st.j, j2 = st.j + 1 >= p ? 0 : st.j + 1;
+    inc_load_list(prm, t, j1, lo, npos, lpos + kIncListCap, lv + kIncListCap, le + kIncListCap, &s_cnt[1], 0, kIncThreads,
+                  &s_err);
+    inc_load_list(prm, t, j2, lo, npos, lpos + 2 * kIncListCap, lv + 2 * kIncListCap, le + 2 * kIncListCap, &s_cnt[2], 0,
+                  kIncThreads, &s_err);
+  }
+  __syncthreads();
+  dw S0 = dw_make(0.0f);   // this thread's tie group's risk-set sum, kept across steps
+  bool refreshed = false;  // the last step taken rebuilt v from eta
+
+  for (int64_t step = 0; step < prm.max_steps && st.state == kRunning; ++step) {
+    const int j = st.j, pj = st.pend_j;
+    const double db = st.pend_db;
+    const dw E = st.E;
+    const bool need_ll = st.need_ll != 0;
+    const bool refresh = need_ll || step == 0;
+    const uint32_t epoch = st.epoch;
+    const int sp = base & 3, sc = (base + 1) & 3, sn = (base + 2) & 3, sf = (base + 3) & 3;
+    uint32_t *lp_p = lpos + sp * kIncListCap, *lp_c = lpos + sc * kIncListCap, *lp_n = lpos + sn * kIncListCap;
+    dw *lv_p = lv + sp * kIncListCap, *lv_c = lv + sc * kIncListCap, *lv_n = lv + sn * kIncListCap;
+    double *le_p = le + sp * kIncListCap, *le_c = le + sc * kIncListCap, *le_n = le + sn * kIncListCap;
+    const int np = pj >= 0 ? s_cnt[sp] : 0, ncur = s_cnt[sc], nnx = s_cnt[sn];
+    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * 8 : nullptr;
+    if (trace) trace[0] = inc_timer();
+    // this coordinate's inputs to the step, loaded now so their latency overlaps the step
+    double pre_dx = 0.0, pre_b = 0.0, pre_tr = 0.0;
+    int pre_pen = 1;
+    if (tid == 0) {
+      pre_dx = D.dX[j];
+      pre_pen = F.penalize ? F.penalize[j] != 0 : 1;
+      pre_b = bet[j];
+      pre_tr = tru[j];
+    }
+    // ---- 1. the pending update at the previous column's entries (one per thread):
+    //         eta += dbeta (eq. parallel_xb); v (1 + (e^dbeta - 1)) (eq. parallel_d)
+    dw dd = dw_make(0.0f);
+    int fp = 1;
+    if (tid < np) {
+      const uint32_t e = lp_p[tid];
+      const int q = int(e & kPosMask);
+      const double et = __dadd_rn(le_p[tid], db);
+      if (!(fabs(et - shift) <= kIncRange)) atomicCAS(&s_err, 0, COX_E_RANGE);
+      dd = dw_mul(lv_p[tid], E);
+      const dw nv = dw_add(lv_p[tid], dd);
+      prm.vdw[lo + q] = nv;
+      F.eta[lo + q] = et;
+      le_p[tid] = et;
+      lv_p[tid] = nv;
+      fp = tid + 1 >= np || inc_rank(cutb, cutp, int(lp_p[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
+    }
+    __syncthreads();
+    if (trace) trace[1] = inc_timer();
+    // ---- 2. a sweep start rebuilds v and S0 from eta; otherwise the current and next lists
+    //         take the update at the entries they share with the previous column
+    dw HA0 = dw_make(0.0f);
+    if (refresh) {
+      HA0 = inc_dense<P>(prm, lo, npos, cutb, headb, headp, gs0, gseen, s_dagg, s_dflg, s_dcar, RW, &s_err);
+      if (tid < ncur) {
+        const int q = int(lp_c[tid] & kPosMask);
+        lv_c[tid] = prm.vdw[lo + q];
+        le_c[tid] = F.eta[lo + q];
+      }
+      if (tid < nnx) {
+        const int q = int(lp_n[tid] & kPosMask);
+        lv_n[tid] = prm.vdw[lo + q];
+        le_n[tid] = F.eta[lo + q];
+      }
+    } else if (np > 0) {
+      if (tid < ncur) {
+        const int q = int(lp_c[tid] & kPosMask);
+        const int k = inc_lower_bound(lp_p, np, q);
+        if (k < np && int(lp_p[k] & kPosMask) == q) {
+          lv_c[tid] = lv_p[k];
+          le_c[tid] = le_p[k];
+        }
+      }
+      if (tid < nnx) {
+        const int q = int(lp_n[tid] & kPosMask);
+        const int k = inc_lower_bound(lp_p, np, q);
+        if (k < np && int(lp_p[k] & kPosMask) == q) {
+          lv_n[tid] = lv_p[k];
+          le_n[tid] = le_p[k];
+        }
+      }
+    }
+    refreshed = refresh;
+    dw x1 = dw_make(0.0f);
+    int fc = 1;
+    if (tid < ncur) {
+      const int q = int(lp_c[tid] & kPosMask);
+      x1 = lv_c[tid];
+      fc = tid + 1 >= ncur || inc_rank(cutb, cutp, int(lp_c[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
+    }
+    const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : -1;
+    const dw vnx = tid < nnx ? lv_n[tid] : dw_make(0.0f);
+    // ---- 3. segmented suffix sums of dD (previous column) and v (current column)
+    inc_seg_suffix2(refresh ? dw_make(0.0f) : dd, refresh ? 1 : fp, x1, fc, refresh ? ncur : max(np, ncur), u0, u1, s_agg,
+                    s_flg);
+    __syncthreads();
+    // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
+    const dw H1 = (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? u1[0] : dw_make(0.0f);
+    if (trace) trace[2] = inc_timer();
+    dw C1;
+    if (refresh) {
+      // ---- carries of the rebuilt S0 and of S1 from one exchange of the tiles' head sums
+      const uint32_t tag = epoch;
+      if (tid == 0) {
+        uint64_t *w = prm.tref + 4 * int64_t(t);
+        put_dw(w, tag, HA0);
+        put_dw(w + 2, tag, H1);
+      }
+      if (tid < C) {
+        uint64_t r[2] = {0, 0};
+        if (!wait_tagged<2>(prm.tref + 4 * int64_t(tid), tag, r, &ctl->error)) {
+          atomicCAS(&s_err, 0, COX_E_TIMEOUT);
+          r[0] = r[1] = 0;
+        }
+        sref[2 * tid] = slot_dw(&r[0]);
+        sref[2 * tid + 1] = slot_dw(&r[1]);
+      }
+      __syncthreads();
+      if (warp < 2) {
+        dw c0 = dw_make(0.0f);
+        for (int c = t + 1 + lane; c <= s_chain_end; c += 32) c0 = dw_add(c0, sref[2 * c + warp]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c0 = dw_add(c0, dw_shfl_down(c0, off));
+        if (lane == 0) s_carry[warp] = c0;
+      }
+      __syncthreads();
+      if (tid < ng) {
+        S0 = gs0[tid];
+        if (!gseen[tid]) S0 = dw_add(S0, s_dcar[qg / RW]);
+        if (tailg) S0 = dw_add(S0, s_carry[0]);
+      }
+      C1 = s_carry[1];
+    } else {
+      // ---- S0 += the suffix of dD from the read position, and the later tiles' change
+      if (tid < ng && np > 0) {
+        const int k = inc_lower_bound(lp_p, np, qg);
+        if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == segg) S0 = dw_add(S0, u0[k]);
+      }
+      if (tailg && !dw_is_zero(E)) S0 = dw_add(S0, dw_mul(E, s_chain[0]));
+      C1 = dw_add(s_chain[1], dw_mul(E, s_chain[2]));
+    }
+    // ---- 4. tie-group ratios (warps holding groups); the next column's head-segment sums R,
+    //         and I over the entries this step's update may change (warps holding its entries)
+    const bool gwarp = warp * 32 < ng, nwarp = warp * 32 < nnx;   // warp-uniform
+    dw r_g1 = dw_make(0.0f), r_g2 = dw_make(0.0f), r_R = dw_make(0.0f), r_I = dw_make(0.0f);
+    double r_ll = 0.0;
+    if (gwarp) {
+      if (tid < ng) {
+        dw s1 = dw_make(0.0f);
+        if (ncur > 0) {
+          const int k = inc_lower_bound(lp_c, ncur, qg);
+          if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == segg) s1 = u1[k];
+        }
+        if (tailg) s1 = dw_add(s1, C1);
+        if (!dw_is_zero(s1)) {
+          const dw r = dw_div(s1, S0);
+          r_g1 = dw_mul_f(r, dg);
+          r_g2 = dw_mul(r_g1, dw_sub(dw_make(1.0f), r));
+        }
+        if (need_ll) r_ll = double(dg) * log(dw_to(S0));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        r_g1 = dw_add(r_g1, dw_shfl_down(r_g1, off));
+        r_g2 = dw_add(r_g2, dw_shfl_down(r_g2, off));
+      }
+      if (need_ll)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r_ll += __shfl_down_sync(kFull, r_ll, off);
+    }
+    if (nwarp) {
+      if (tid < nnx && inc_rank(cutb, cutp, qnx) == 0) {
+        r_R = vnx;
+        if (ncur > 0) {
+          const int k = inc_lower_bound(lp_c, ncur, qnx);
+          if (k < ncur && int(lp_c[k] & kPosMask) == qnx) r_I = vnx;
+        }
+      }
+      if (__any_sync(kFull, !dw_is_zero(r_R))) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          r_R = dw_add(r_R, dw_shfl_down(r_R, off));
+          r_I = dw_add(r_I, dw_shfl_down(r_I, off));
+        }
+      }
+    }
+    if (lane == 0) {
+      s_red[0][warp] = r_g1;
+      s_red[1][warp] = r_g2;
+      s_red[2][warp] = r_R;
+      s_red[3][warp] = r_I;
+      s_rll[warp] = r_ll;
+    }
+    if (trace) trace[3] = inc_timer();
+    __syncthreads();
+    // ---- one value per warp: sums of the warp partials, then this CTA's tagged record words
+    //      (G1, G2 and the head sums as double-words, LL in FP64, the error code)
+    const int par = int(epoch & 1u);
+    uint64_t *myrec = prm.trec + int64_t(kIncRecWords) * (int64_t(par) * C + t);
+    if (warp < 2 || warp == 3 || warp == 4) {
+      const int v = warp < 2 ? warp : warp - 1;           // s_red row: G1, G2, R, I
+      const int nv = warp < 2 ? (ng + 31) >> 5 : (nnx + 31) >> 5;
+      dw a = lane < nv ? s_red[v][lane] : dw_make(0.0f);
+      for (int off = 1; off < nv; off <<= 1) a = dw_add(a, dw_shfl_down(a, off));
+      if (lane == 0) put_dw(myrec + 2 * (warp < 2 ? warp : warp + 1), epoch, a);   // words 0, 2, 8, 10
+      if (trace) trace[4] = inc_timer();
+    } else if (warp == 2) {
+      const int nv = (ng + 31) >> 5;
+      double a = (need_ll && lane < nv) ? s_rll[lane] : 0.0;
+      if (need_ll)
+        for (int off = 1; off < nv; off <<= 1) a += __shfl_down_sync(kFull, a, off);
+      if (lane == 0) put_f64(myrec + 4, epoch, a);
+    } else if (tid == 5 * 32) {
+      put_dw(myrec + 6, epoch, H1);
+      const int err = s_err;
+      if (err) atomicCAS(&ctl->error, 0, err);
+      put_tag2(myrec + 12, epoch, uint32_t(err), 0u);
+    }
+    // ---- 5. all-gather of the records (one thread per CTA); meanwhile the other threads fetch
+    //         column j+2's entries with eta and v as of this step's update
+    const int jf = (j + 2) % p;
+    if (tid < C) {
+      uint64_t r[kIncRec];
+      if (!wait_tagged<kIncRec>(prm.trec + int64_t(kIncRecWords) * (int64_t(par) * C + tid), epoch, r, &ctl->error)) {
+        for (int i = 0; i < kIncRec; ++i) r[i] = 0;
+        r[kIncRec - 1] = uint64_t(uint32_t(COX_E_TIMEOUT));
+      }
+      for (int i = 0; i < kIncRec; ++i) srec[kIncRec * tid + i] = r[i];
+    } else {
+      inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap, &s_cnt[sf],
+                    C, kIncThreads - C, &s_err);
+    }
+    __syncthreads();
+    if (trace) trace[5] = inc_timer();
+    // ---- 6. fixed-order reductions, one value per warp: G1, G2, LL over every CTA; H1, R, I over
+    //         the later tiles this tile's last stratum continues into; the error codes
+    if (warp < 2 || (warp >= 3 && warp < 6)) {
+      const int v = warp;   // record field: 0 G1, 1 G2, 3 H1, 4 R, 5 I
+      const int c0 = v < 3 ? 0 : t + 1, c1 = v < 3 ? C - 1 : s_chain_end;
+      dw a = dw_make(0.0f);
+      for (int c = c0 + lane; c <= c1; c += 32) a = dw_add(a, slot_dw(&srec[kIncRec * c + v]));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a = dw_add(a, dw_shfl_down(a, off));
+      if (lane == 0) {
+        if (v < 2) s_G[v] = a;
+        else s_chain[v - 3] = a;
+      }
+    } else if (warp == 2) {
+      double a = 0.0;
+      if (need_ll) {
+        for (int c = lane; c < C; c += 32) a += slot_f64(&srec[kIncRec * c + 2]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
+      }
+      if (lane == 0) s_LL = a;
+    } else if (warp == 6) {
+      int e = 0;
+      for (int c = lane; c < C; c += 32) e |= (srec[kIncRec * c + 6] & 0xffffffffull) != 0;
+      e = __any_sync(kFull, e);
+      if (lane == 0) s_anyerr = e;
+    }
+    __syncthreads();
+    if (trace) trace[6] = inc_timer();
+    // ---- 7. the coordinate step, computed identically by every CTA
+    if (tid == 0) {
+      bool stop = false;
+      if (s_anyerr) {
+        st.state = kError;
+        stop = true;
+      } else if (need_ll) {
+        const double ll = st.bdx - s_LL - shift * D.sum_d;
+        const double obj = -ll + st.pen;
+        st.loglik = ll;
+        st.obj = obj;
+        if (st.sweep > 0 && fabs(obj - st.obj_prev) <= F.tol * fabs(obj)) {
+          st.state = kConverged;
+          stop = true;
+        } else if (st.sweep >= F.max_sweeps) {
+          st.state = kMaxed;
+          stop = true;
+        } else {
+          st.obj_prev = obj;
+        }
+      }
+      if (stop) {
+        st.pend_j = -1;   // this step already applied the pending update
+        st.E = dw_make(0.0f);
+      } else {
+        const double g1 = dw_to(s_G[0]) - pre_dx, g2 = dw_to(s_G[1]);
+        double tr = pre_tr;
+        const double s = inc_step_rule(g1, g2, pre_b, &tr, F.penalty, F.lambda, inv_var, pre_pen);
+        const double b_new = pre_b + s;
+        tru[j] = tr;
+        bet[j] = b_new;
+        if (s != 0.0) {
+          st.pend_j = j;
+          st.pend_db = s;
+          st.E = dw_from(expm1(s));
+          st.bdx = fma(s, pre_dx, st.bdx);
+          st.pen = st.pen + (inc_penalty(F, j, b_new) - inc_penalty(F, j, pre_b));
+        } else {
+          st.pend_j = -1;
+          st.pend_db = 0.0;
+          st.E = dw_make(0.0f);
+        }
+        st.coord_updates += 1;
+        const int jn = j + 1 >= p ? 0 : j + 1;
+        if (jn == 0) {
+          st.sweep += 1;
+          st.need_ll = 1;
+        } else {
+          st.need_ll = 0;
+        }
+        st.j = jn;
+      }
+      st.epoch = epoch + 1u;
+      if (trace) trace[7] = inc_timer();
+    }
+    __syncthreads();
+    ++base;
+  }
+
+  // ---- the fit's v in its own precision: current since the last rebuild unless later steps
+  //      updated positions
+  if (!refreshed) {
+    T *vt = static_cast<T *>(F.v);
+    for (int q = tid; q < npos; q += kIncThreads) {
+      const int g = lo + q;
+      const bool ex = D.exit_bits != nullptr && ((D.exit_bits[g >> 5] >> (g & 31)) & 1u);
+      T vv;
+      inc_v<P>(F.eta[g], shift, ex, &vv, &s_err);
+      vt[g] = vv;
+    }
+  }
+  __syncthreads();
+  // ---- CTA 0 writes back the coefficients, trust half-widths and the control state
+  if (t == 0) {
+    for (int jj = tid; jj < p; jj += kIncThreads) {
+      F.beta[jj] = bet[jj];
+      F.trust[jj] = tru[jj];
+    }
+    if (tid == 0) {
+      if (s_err) atomicCAS(&ctl->error, 0, s_err);
+      ctl->j = st.j;
+      ctl->sweep = st.sweep;
+      ctl->need_ll = st.need_ll;
+      ctl->pend_j = st.pend_j;
+      ctl->pend_db = st.pend_db;
+      ctl->state = st.state;
+      ctl->obj_prev = st.obj_prev;
+      ctl->loglik = st.loglik;
+      ctl->obj = st.obj;
+      ctl->coord_updates = st.coord_updates;
+      ctl->epoch = st.epoch;
+    }
+  } else if (tid == 0 && s_err) {
+    atomicCAS(&ctl->error, 0, s_err);
+  }
+}
+
+template <class P>
+static int inc_max_ctas() {
+  static int cached = -2;
+  if (cached != -2) return cached;
+  const size_t sm = IncSmem::bytes;
+  if (cudaFuncSetAttribute(ccd_incr_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) {
+    cudaGetLastError();
+    return cached = 0;
+  }
+  int per_sm = 0, dev = 0, nsm = 0, coop = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ccd_incr_kernel<P>, kIncThreads, sm) != cudaSuccess) {
+    cudaGetLastError();
+    return cached = 0;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  const int g = coop ? per_sm * nsm : 0;
+  return cached = g < kIncMaxCtas ? g : kIncMaxCtas;
+}
+
+int inc_max_grid(int precision) { return precision == COX_FP32C ? inc_max_ctas<PF32C>() : inc_max_ctas<PF64>(); }
+
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void *args[] = {const_cast<IncParams *>(&prm)};
+  if (grid <= 0 || grid > inc_max_grid(precision)) return COX_E_INVALID;
+  count_launches(1);
+  const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C>)
+                                          : reinterpret_cast<const void *>(ccd_incr_kernel<PF64>);
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
+  return e == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+}  // namespace coxgb

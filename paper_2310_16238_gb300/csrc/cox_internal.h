@@ -104,6 +104,26 @@ struct ResParams {
   int64_t trace_steps;
 };
 
+struct dw;   // double-word float (dw.cuh)
+
+// Words of one step record of the incremental kernel: 7 tagged doubles (G1, G2, LL, H1, R, I,
+// error code), two 8-byte words each.
+constexpr int kIncRecWords = 14;
+
+// Arguments of the incremental kernel (ccd_incr.cu), passed by value.
+struct IncParams {
+  DevFit F;               // the fit (its d pointer is not used)
+  DevData D;              // the data descriptor
+  const int32_t *tile_lo, *tile_g, *tile_k, *col_tile;   // incremental tile plan: one tile per CTA
+  uint64_t *trec;         // [2][C][kIncRecWords] epoch-tagged step records, double-buffered by step parity
+  uint64_t *tref;         // [C][4] epoch-tagged head sums of the dense refresh
+  double *bcopy;          // [C][2p] each CTA's copy of beta and the trust half-widths
+  dw *vdw;                // [M] v per position as a double-word (the kernel's working copy)
+  int64_t max_steps;      // coordinate steps this launch may take
+  uint64_t *trace;        // optional [trace_steps][C][8] phase timestamps (ns)
+  int64_t trace_steps;
+};
+
 // Count of kernels launched by the library (every launcher adds to it).
 void count_launches(int64_t n);
 
@@ -123,5 +143,13 @@ int res_tile(int precision);
 int res_head_cap();
 int res_max_grid(int precision);
 int launch_resident(int precision, const ResParams &prm, int grid, void *stream);
+
+// Incremental kernel (ccd_incr.cu): tie groups, column entries and positions one CTA holds,
+// largest cooperative grid (0 when unsupported), launch.
+int inc_group_cap();
+int inc_list_cap();
+int inc_pos_cap();
+int inc_max_grid(int precision);
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream);
 
 }  // namespace coxgb

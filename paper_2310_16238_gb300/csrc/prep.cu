@@ -486,6 +486,74 @@ static const V *device_view(const V *p, int64_t count, Scratch &sc, cudaStream_t
 
 // Greedy tile plan: tiles of `tile` positions, shortened when they would hold more than
 // kHeadCap tie-group read positions. Boundaries are multiples of 32.
+// Tiles of at most `per` positions (multiples of 32), each shortened so that it holds at most
+// `cap` tie-group read positions.
+static std::vector<int32_t> capped_plan(int64_t M, int64_t per, size_t cap, const std::vector<int32_t> &h_head) {
+  std::vector<int32_t> rl;
+  int64_t cur = 0;
+  size_t hh = 0;
+  while (cur < M) {
+    rl.push_back(int32_t(cur));
+    int64_t hi = std::min<int64_t>(cur + per, M);
+    while (hh < h_head.size() && h_head[hh] < cur) ++hh;
+    if (hh + cap < h_head.size() && h_head[hh + cap] < hi) {
+      const int64_t cut = (int64_t(h_head[hh + cap]) / 32) * 32;
+      if (cut > cur) hi = cut;
+    }
+    cur = hi;
+  }
+  rl.push_back(int32_t(M));
+  return rl;
+}
+
+// The shortest tile length (best balance across CTAs, at most pmax) whose capped plan has at
+// most `grid` tiles; empty when none has.
+static std::vector<int32_t> fit_plan(int64_t M, int64_t pmax, size_t cap, int64_t grid, const std::vector<int32_t> &h_head) {
+  int64_t plo = ((M + grid - 1) / grid + 31) / 32 * 32, phi = pmax;
+  if (plo > pmax || int64_t(capped_plan(M, pmax, cap, h_head).size()) - 1 > grid) return {};
+  while (plo < phi) {   // the plan size is nonincreasing in the tile length
+    const int64_t mid = ((plo + phi) / 2) / 32 * 32;
+    if (mid <= plo) break;
+    if (int64_t(capped_plan(M, mid, cap, h_head).size()) - 1 <= grid) phi = mid;
+    else plo = mid + 32;
+  }
+  std::vector<int32_t> rl = capped_plan(M, phi, cap, h_head);
+  if (int64_t(rl.size()) - 1 > grid) rl.clear();
+  return rl;
+}
+
+// Tiles holding equal numbers of tie-group read positions (at most `per_g` each; the
+// incremental kernel's step cost grows with its groups), each cut again after `pos_cap`
+// positions. Every tile but the first starts at a read position.
+static std::vector<int32_t> group_tiles(int64_t M, int64_t per_g, int64_t pos_cap, const std::vector<int32_t> &h_head) {
+  const int64_t G = int64_t(h_head.size());
+  std::vector<int32_t> rl{0};
+  int64_t cur = 0, g = 0;   // g: first group whose read position is >= cur
+  while (cur < M) {
+    int64_t hi = g + per_g < G ? int64_t(h_head[g + per_g]) : M;
+    hi = std::min(hi, cur + pos_cap);
+    if (hi <= cur) hi = std::min<int64_t>(M, cur + 1);
+    rl.push_back(int32_t(hi));
+    cur = hi;
+    while (g < G && h_head[g] < cur) ++g;
+  }
+  return rl;
+}
+
+// The smallest group count per tile whose group-balanced plan has at most `grid` tiles; empty
+// when none within `cap` groups per tile has.
+static std::vector<int32_t> group_plan(int64_t M, int64_t pos_cap, int64_t cap, int64_t grid, const std::vector<int32_t> &h_head) {
+  const int64_t G = int64_t(h_head.size());
+  int64_t lo = std::max<int64_t>(1, (G + grid - 1) / grid), hi = cap;
+  if (lo > hi || int64_t(group_tiles(M, hi, pos_cap, h_head).size()) - 1 > grid) return {};
+  while (lo < hi) {   // the tile count is nonincreasing in the groups per tile
+    const int64_t mid = (lo + hi) / 2;
+    if (int64_t(group_tiles(M, mid, pos_cap, h_head).size()) - 1 <= grid) hi = mid;
+    else lo = mid + 1;
+  }
+  return group_tiles(M, hi, pos_cap, h_head);
+}
+
 static std::vector<int32_t> plan_tiles(int64_t M, int tile, const std::vector<int32_t> &head_pos) {
   std::vector<int32_t> lo;
   int64_t cur = 0;
@@ -759,62 +827,69 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   D.col_tile = col_tile;
   out->h_tile_lo = h_lo;
 
-  // resident plan: binary X, at most one tile per co-resident CTA, each tile within the
-  // kernel's shared-memory capacity and head capacity
-  const int res_cap_grid = res_max_grid(precision);
-  if (in->val == nullptr && p > 0 && D.M > 0 && res_cap_grid > 0) {
-    // tiles of at most `per` positions, shortened to hold at most the head capacity
-    auto res_plan = [&](int64_t per) {
-      std::vector<int32_t> rl;
-      int64_t cur = 0;
-      size_t hh = 0;
-      const size_t cap = size_t(res_head_cap());
-      while (cur < D.M) {
-        rl.push_back(int32_t(cur));
-        int64_t hi = std::min<int64_t>(cur + per, D.M);
-        while (hh < h_head.size() && h_head[hh] < cur) ++hh;
-        if (hh + cap < h_head.size() && h_head[hh + cap] < hi) {
-          const int64_t cut = (int64_t(h_head[hh + cap]) / 32) * 32;
-          if (cut > cur) hi = cut;
-        }
-        cur = hi;
+  // one-tile-per-CTA plans of the resident and incremental kernels (binary X only)
+  auto tables = [&](const std::vector<int32_t> &rl, int32_t **lo_out, int32_t **g_out, int32_t **k_out,
+                    int32_t **ct_out) -> int {
+    const int32_t RT = int32_t(rl.size()) - 1;
+    int32_t *r_lo = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+    int32_t *r_g = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+    int32_t *r_k = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+    int32_t *r_ct = static_cast<int32_t *>(B.get(int64_t(p) * (RT + 1) * sizeof(int32_t)));
+    if (!r_lo || !r_g || !r_k || !r_ct) return COX_E_OOM;
+    cudaMemcpyAsync(r_lo, rl.data(), (RT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    count_launches(1);
+    tile_tables_kernel<<<grid_for(int64_t(RT) + 1), 256, 0, s>>>(RT, r_lo, head_pos, int32_t(G), cut_pos, int32_t(K), r_g, r_k);
+    count_launches(1);
+    col_tile_kernel<<<grid_for(int64_t(p) * (RT + 1)), 256, 0, s>>>(p, RT, col_ptr, idx, r_lo, r_ct);
+    *lo_out = r_lo;
+    *g_out = r_g;
+    *k_out = r_k;
+    *ct_out = r_ct;
+    return COX_OK;
+  };
+  if (in->val == nullptr && p > 0 && D.M > 0) {
+    const int res_grid = res_max_grid(precision);
+    if (res_grid > 0) {
+      std::vector<int32_t> rl = fit_plan(D.M, res_tile(precision), size_t(res_head_cap()), res_grid, h_head);
+      if (!rl.empty()) {
+        if ((rc = tables(rl, &out->res_tile_lo, &out->res_tile_g, &out->res_tile_k, &out->res_col_tile))) return rc;
+        out->res_T = int32_t(rl.size()) - 1;
       }
-      rl.push_back(int32_t(D.M));
-      return rl;
-    };
-    // the shortest tile length (best balance across CTAs) whose plan fits the grid
-    const int64_t pmax = res_tile(precision);
-    int64_t plo = ((D.M + res_cap_grid - 1) / res_cap_grid + 31) / 32 * 32, phi = pmax;
-    std::vector<int32_t> rl;
-    if (plo <= pmax && int64_t(res_plan(pmax).size()) - 1 <= res_cap_grid) {
-      while (plo < phi) {   // plan size is nonincreasing in the tile length
-        const int64_t mid = ((plo + phi) / 2) / 32 * 32;
-        if (mid <= plo) break;
-        if (int64_t(res_plan(mid).size()) - 1 <= res_cap_grid) phi = mid;
-        else plo = mid + 32;
-      }
-      rl = res_plan(phi);
-      if (int64_t(rl.size()) - 1 > res_cap_grid) rl.clear();
     }
-    const int32_t RT = rl.empty() ? 0 : int32_t(rl.size()) - 1;
-    if (RT > 0 && RT <= res_cap_grid) {
-      {
-        int32_t *r_lo = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-        int32_t *r_g = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-        int32_t *r_k = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-        int32_t *r_ct = static_cast<int32_t *>(B.get(int64_t(p) * (RT + 1) * sizeof(int32_t)));
-        if (!r_lo || !r_g || !r_k || !r_ct) return COX_E_OOM;
-        cudaMemcpyAsync(r_lo, rl.data(), (RT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-        count_launches(1);
-        tile_tables_kernel<<<grid_for(int64_t(RT) + 1), 256, 0, s>>>(RT, r_lo, head_pos, int32_t(G), cut_pos, int32_t(K), r_g,
-                                                                     r_k);
-        count_launches(1);
-        col_tile_kernel<<<grid_for(int64_t(p) * (RT + 1)), 256, 0, s>>>(p, RT, col_ptr, idx, r_lo, r_ct);
-        out->res_T = RT;
-        out->res_tile_lo = r_lo;
-        out->res_tile_g = r_g;
-        out->res_tile_k = r_k;
-        out->res_col_tile = r_ct;
+    const int inc_grid = inc_max_grid(precision);
+    if (inc_grid > 0) {
+      // candidate plans, best balanced first: equal tie groups per tile (the step's cost), then
+      // the same with shorter tiles, then equal positions; the first whose every column fits the
+      // kernel's list capacity in every tile is taken
+      std::vector<std::vector<int32_t>> cands;
+      for (int64_t pc = inc_pos_cap(); pc >= 1024; pc /= 4) cands.push_back(group_plan(D.M, pc, inc_group_cap(), inc_grid, h_head));
+      cands.push_back(fit_plan(D.M, inc_pos_cap(), size_t(inc_group_cap()), inc_grid, h_head));
+      for (const auto &il : cands) {
+        if (il.empty()) continue;
+        int32_t *ilo = nullptr, *ig = nullptr, *ik = nullptr, *ict = nullptr;
+        if ((rc = tables(il, &ilo, &ig, &ik, &ict))) return rc;
+        const int32_t IT = int32_t(il.size()) - 1;
+        std::vector<int32_t> hct(size_t(p) * (IT + 1));
+        if (cudaMemcpyAsync(hct.data(), ict, hct.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          *err = "cox_create: table kernels failed";
+          return COX_E_CUDA;
+        }
+        bool fits = true;
+        for (int32_t j = 0; j < p && fits; ++j)
+          for (int32_t t = 0; t < IT; ++t)
+            if (hct[size_t(j) * (IT + 1) + t + 1] - hct[size_t(j) * (IT + 1) + t] > inc_list_cap()) {
+              fits = false;
+              break;
+            }
+        if (fits) {
+          out->inc_T = IT;
+          out->inc_tile_lo = ilo;
+          out->inc_tile_g = ig;
+          out->inc_tile_k = ik;
+          out->inc_col_tile = ict;
+          break;
+        }
       }
     }
   }

@@ -45,6 +45,9 @@ struct Prepared {
   // resident plan (one tile per CTA of the resident kernel); res_T == 0 when not eligible
   int32_t res_T = 0;
   int32_t *res_tile_lo = nullptr, *res_tile_g = nullptr, *res_tile_k = nullptr, *res_col_tile = nullptr;
+  // incremental plan (one tile per CTA of the incremental kernel); inc_T == 0 when not eligible
+  int32_t inc_T = 0;
+  int32_t *inc_tile_lo = nullptr, *inc_tile_g = nullptr, *inc_tile_k = nullptr, *inc_col_tile = nullptr;
   int32_t *g_time = nullptr;            // [G] device
   int32_t *g_stratum = nullptr;         // [G] device
 };

@@ -1,0 +1,99 @@
+"""The incremental kernel (per-group S0 kept resident, updated from the changed positions, one
+cooperative launch per fit) against the oracle on cases aimed at its own logic: strata that span
+many CTAs, CTAs holding many stratum ends, counting-process rows whose entry and exit fall in
+different CTAs, one and two columns, the sweep limit, warm starts and the state left for the
+evaluations. Tolerances as in the other parity tests (FP64: beta 1e-9, log-likelihood 1e-11;
+FP32C: beta 1e-5, log-likelihood 1e-7)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_16238_gb300 import synth
+from tests.cases import random_beta
+
+pytestmark = pytest.mark.gpu
+cox = pytest.importorskip("paper_2310_16238_gb300.cox")
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) if len(b) else 0.0
+
+
+def _ll_scale(data, beta, ll):
+    dX = oracle.dX(data)
+    return max(abs(ll), float(np.sum(np.abs(beta * dX))) + float(np.sum(data.event)))
+
+
+def _cases():
+    out = []
+    # one big stratum spread over every CTA, plus small ones
+    d, o = synth.stratified_sparse(n=150000, p=12, k=6, n_support=6, event_frac=0.1, dens_lo=0.002, dens_hi=0.2,
+                                   admin_days=2000, lam_per_n=1e-4, seed=61)
+    out.append(("wide_strata_l1", d, o))
+    # many small strata: most CTAs hold several stratum ends
+    d, o = synth.stratified_sparse(n=60000, p=8, k=3000, n_support=4, event_frac=0.3, dens_lo=0.02, dens_hi=0.3,
+                                   admin_days=100, lam_per_n=1e-4, seed=62)
+    out.append(("many_strata_l1", d, o))
+    # counting-process rows, L2
+    d, o = synth.time_varying(n_subj=30000, p=10, k=3, density=0.02, event_frac=0.3, n_support=5, seed=63)
+    out.append(("counting_l2", d, o))
+    # one column and two columns
+    d, o = synth.stratified_sparse(n=20000, p=1, k=4, n_support=1, event_frac=0.2, dens_lo=0.2, dens_hi=0.3,
+                                   admin_days=300, lam_per_n=0.0, seed=64)
+    out.append(("one_column", d, synth.CoxOptions(penalty=synth.PEN_NONE, tol=1e-12)))
+    d, o = synth.time_varying(n_subj=5000, p=2, k=2, density=0.3, event_frac=0.4, n_support=2, seed=65)
+    out.append(("two_columns_counting", d, o))
+    return out
+
+
+CASES = _cases()
+IDS = [c[0] for c in CASES]
+
+
+@pytest.mark.parametrize("name,data,opts", CASES, ids=IDS)
+def test_incr_fit_matches_oracle(name, data, opts):
+    with cox.Handle(data, opts, engine=cox.COX_ENGINE_INCR) as h:
+        beta, info = h.fit()
+        assert info["step_launches"] == 1
+        # the state the kernel leaves behind is what the evaluations see
+        ll = h.loglik(beta)
+    ob, oinfo = oracle.fit(data, opts, max_sweeps=info["sweeps"])
+    assert info["sweeps"] == oinfo["sweeps"] or not oinfo["converged"]
+    assert _rel(beta, ob) <= 1e-9, _rel(beta, ob)
+    scale = _ll_scale(data, ob, oinfo["loglik"])
+    assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * scale
+    assert abs(ll - info["loglik"]) <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("name,data,opts", CASES[:3], ids=IDS[:3])
+def test_incr_sweep_limit_and_warm_start(name, data, opts):
+    o = synth.CoxOptions(penalty=opts.penalty, lam=opts.lam, l2_var=opts.l2_var, tol=1e-14, max_sweeps=2)
+    b0 = random_beta(data.p, 0.05, seed=3)
+    with cox.Handle(data, o, engine=cox.COX_ENGINE_INCR) as h:
+        beta, info = h.fit(b0)
+    assert info["sweeps"] == 2 and not info["converged"] and info["rc"] == cox.COX_W_NOT_CONVERGED
+    ob, oinfo = oracle.fit(data, o, beta0=b0, max_sweeps=2)
+    assert _rel(beta, ob) <= 1e-9
+    assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * _ll_scale(data, ob, oinfo["loglik"])
+
+
+@pytest.mark.parametrize("name,data,opts", CASES[:3], ids=IDS[:3])
+def test_incr_fp32c(name, data, opts):
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_INCR) as h:
+        beta, info = h.fit()
+    ob, oinfo = oracle.fit(data, opts)
+    assert _rel(beta, ob) <= 1e-5
+    assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-7 * _ll_scale(data, ob, oinfo["loglik"])
+
+
+def test_incr_is_deterministic_and_matches_streaming():
+    name, data, opts = CASES[0]
+    with cox.Handle(data, opts, engine=cox.COX_ENGINE_INCR) as h:
+        b1, i1 = h.fit()
+        b2, i2 = h.fit()
+    assert np.array_equal(b1, b2) and i1["loglik"] == i2["loglik"]
+    with cox.Handle(data, opts, engine=cox.COX_ENGINE_STREAM) as h:
+        b3, i3 = h.fit()
+    assert i3["sweeps"] == i1["sweeps"] and _rel(b1, b3) <= 1e-10

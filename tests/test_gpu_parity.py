@@ -232,23 +232,35 @@ def test_device_resident_inputs():
 
 @pytest.mark.parametrize("name,data,opts", CASES, ids=IDS)
 def test_engines_agree_with_oracle(name, data, opts):
-    """The streaming kernel (one launch per coordinate step) and the resident kernel (the whole
-    fit in one cooperative launch, values held in shared memory) follow the oracle's CCD path."""
+    """The streaming kernel (one launch per coordinate step), the resident kernel (the whole fit
+    in one cooperative launch, values held in shared memory) and the incremental kernel (one
+    cooperative launch, per-group S0 updated from the changed positions) all follow the oracle's
+    CCD path."""
     results = {}
-    for eng in (cox.COX_ENGINE_STREAM, cox.COX_ENGINE_AUTO):
+    for eng in (cox.COX_ENGINE_STREAM, cox.COX_ENGINE_RESIDENT, cox.COX_ENGINE_INCR, cox.COX_ENGINE_AUTO):
         with cox.Handle(data, opts, engine=eng) as h:
-            results[eng] = h.fit()
+            try:
+                results[eng] = h.fit()
+            except cox.CoxError as e:
+                assert e.code == cox.COX_E_INVALID and eng in (cox.COX_ENGINE_RESIDENT, cox.COX_ENGINE_INCR), (eng, e)
     for eng, (beta, info) in results.items():
         ob, oinfo = oracle.fit(data, opts, max_sweeps=info["sweeps"])
         assert _rel_beta(beta, ob) <= 1e-9, (eng, _rel_beta(beta, ob))
-        assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * _ll_scale(data, ob, oinfo["loglik"])
+        assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * _ll_scale(data, ob, oinfo["loglik"]), eng
+        assert info["sweeps"] == oinfo["sweeps"] or not oinfo["converged"], eng
     if data.val is None:
-        assert results[cox.COX_ENGINE_AUTO][1]["step_launches"] == 1   # binary X runs resident
+        # every binary case here fits the incremental kernel, which AUTO then runs in one launch
+        assert cox.COX_ENGINE_INCR in results, name
+        assert results[cox.COX_ENGINE_AUTO][1]["step_launches"] == 1
+    else:
+        assert cox.COX_ENGINE_INCR not in results and cox.COX_ENGINE_RESIDENT not in results
 
 
-def test_resident_engine_rejects_valued_x():
+@pytest.mark.parametrize("engine", ["resident", "incr"])
+def test_one_launch_engines_reject_valued_x(engine):
     d, o = synth.plain_dense(n=200, p=3, seed=2)
-    with cox.Handle(d, o, engine=cox.COX_ENGINE_RESIDENT) as h:
+    eng = cox.COX_ENGINE_RESIDENT if engine == "resident" else cox.COX_ENGINE_INCR
+    with cox.Handle(d, o, engine=eng) as h:
         with pytest.raises(cox.CoxError) as e:
             h.fit()
     assert e.value.code == cox.COX_E_INVALID

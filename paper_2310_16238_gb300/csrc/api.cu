@@ -164,7 +164,7 @@ int alloc_fit_state(cox_handle *h) {
       return fail(h, COX_E_OOM, "device allocation failed for the resident state");
   }
   if (const int IT = h->sd->prep.inc_T) {
-    h->i_trec = static_cast<uint64_t *>(B.get(2 * kIncRecWords * int64_t(IT) * sizeof(uint64_t)));
+    h->i_trec = static_cast<uint64_t *>(B.get(2 * kIncRecWords * int64_t(IT) * IT * sizeof(uint64_t)));
     h->i_tref = static_cast<uint64_t *>(B.get(4 * int64_t(IT) * sizeof(uint64_t)));
     h->i_bcopy = static_cast<double *>(B.get(std::max<int64_t>(2 * p * IT, 1) * sizeof(double)));
     h->i_vdw = static_cast<dw *>(B.get(std::max<int64_t>(M, 1) * 2 * sizeof(float)));
@@ -437,7 +437,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   const int IT = P.inc_T;
   cudaStream_t s = h->stream;
   // tag 0 never matches: records start at epoch 1
-  if (cudaMemsetAsync(h->i_trec, 0, 2 * kIncRecWords * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess ||
+  if (cudaMemsetAsync(h->i_trec, 0, 2 * kIncRecWords * int64_t(IT) * IT * sizeof(uint64_t), s) != cudaSuccess ||
       cudaMemsetAsync(h->i_tref, 0, 4 * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
   IncParams prm{};
@@ -457,9 +457,9 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
   BufferSet trbuf;
   if (tr_steps > 0) {
-    prm.trace = static_cast<uint64_t *>(trbuf.get(tr_steps * IT * 8 * sizeof(uint64_t)));
+    prm.trace = static_cast<uint64_t *>(trbuf.get(tr_steps * IT * 24 * sizeof(uint64_t)));
     prm.trace_steps = prm.trace ? tr_steps : 0;
-    if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * IT * 8 * sizeof(uint64_t), s);
+    if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * IT * 24 * sizeof(uint64_t), s);
   }
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
@@ -469,28 +469,34 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   int rc;
   if ((rc = read_ctl(h))) return rc;
   if (prm.trace_steps > 0) {
-    // mean phase times per CTA and the publish time after the earliest step start, for the
-    // slowest CTAs (phases: update, scans, S0 and ratios, partials and publish, all-gather,
-    // record reductions, step)
-    constexpr int kPh = 7;
-    std::vector<uint64_t> tr(size_t(prm.trace_steps * IT * 8));
+    // mean time between consecutive timestamps of thread 0 per CTA (update | patch | scan | scan
+    // barrier | S0 | ratios | group sums | barrier | CTA sums | barrier | push | inbox | barrier |
+    // record sums | step) and the publish time after the earliest step start, for the slowest
+    // CTAs and the fastest
+    constexpr int kSl = 24, kPh = 15;
+    std::vector<uint64_t> tr(size_t(prm.trace_steps * IT * kSl));
     cudaMemcpy(tr.data(), prm.trace, tr.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    std::vector<double> pub(IT, 0.0), ph(kPh * IT, 0.0), tot(IT, 0.0);
+    std::vector<double> pub(IT, 0.0), ph(kPh * IT, 0.0), tot(IT, 0.0), ex(4 * IT, 0.0), clk(IT, 0.0);
     int64_t n = 0;
     for (int64_t k = 1; k < prm.trace_steps; ++k) {
       uint64_t t0 = ~0ull;
       bool ok = true;
       for (int c = 0; c < IT; ++c) {
-        const uint64_t *r = &tr[size_t((k * IT + c) * 8)];
-        for (int q = 0; q < 8; ++q) ok = ok && r[q] != 0;
+        const uint64_t *r = &tr[size_t((k * IT + c) * kSl)];
+        for (int q = 0; q < 16; ++q) ok = ok && r[q] != 0;
         t0 = std::min(t0, r[0]);
       }
       if (!ok) continue;
       for (int c = 0; c < IT; ++c) {
-        const uint64_t *r = &tr[size_t((k * IT + c) * 8)];
-        pub[c] += double(r[4] - t0);
-        tot[c] += double(r[7] - r[0]);
+        const uint64_t *r = &tr[size_t((k * IT + c) * kSl)];
+        pub[c] += double(r[11] - t0);
+        tot[c] += double(r[15] - r[0]);
         for (int q = 0; q < kPh; ++q) ph[kPh * c + q] += double(r[q + 1] - r[q]);
+        ex[4 * c + 0] += double(r[16] - r[13]);   // warp 0's record sums before the barrier
+        ex[4 * c + 1] += double(r[18] - r[17]);   // the step rule
+        ex[4 * c + 2] += double(r[15] - r[18]);   // exp and bookkeeping after the rule
+        ex[4 * c + 3] += double(r[20]);           // polls of thread 0's inbox wait
+        clk[c] += double(r[22] - r[23]);           // SM clocks over the whole step
       }
       ++n;
     }
@@ -498,13 +504,15 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
     for (int c = 0; c < IT; ++c) order[c] = c;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return pub[a] > pub[b]; });
     std::fprintf(stderr, "[phase trace] incremental kernel, %lld steps x %d CTAs (ns): publish-after-first-start | "
-                 "update scans S0+ratios publish gather reduce step | total\n", (long long)n, IT);
+                 "upd patch scan bar S0 ratio gsum bar csum bar push inbox bar rsum step | total\n", (long long)n, IT);
     auto row = [&](const char *tag, int c) {
-      std::fprintf(stderr, "  %s CTA %3d: %6.0f | %5.0f %5.0f %5.0f %5.0f %5.0f %5.0f %5.0f | %6.0f\n", tag, c, pub[c] / n,
-                   ph[kPh * c] / n, ph[kPh * c + 1] / n, ph[kPh * c + 2] / n, ph[kPh * c + 3] / n, ph[kPh * c + 4] / n,
-                   ph[kPh * c + 5] / n, ph[kPh * c + 6] / n, tot[c] / n);
+      std::fprintf(stderr, "  %s CTA %3d: %6.0f |", tag, c, pub[c] / n);
+      for (int q = 0; q < kPh; ++q) std::fprintf(stderr, " %4.0f", ph[kPh * c + q] / n);
+      std::fprintf(stderr, " | %6.0f (%5.0f SM clocks, %.2f GHz) | rsum-own %4.0f rule %4.0f exp+ %4.0f polls %4.1f\n",
+                   tot[c] / n, clk[c] / n, clk[c] / tot[c], ex[4 * c] / n, ex[4 * c + 1] / n, ex[4 * c + 2] / n,
+                   ex[4 * c + 3] / n);
     };
-    for (int q = 0; q < std::min(IT, 4) && n; ++q) row("slow", order[q]);
+    for (int q = 0; q < std::min(IT, 3) && n; ++q) row("slow", order[q]);
     if (n) row("fast", order[IT - 1]);
   }
   if ((rc = device_error(h))) return rc;

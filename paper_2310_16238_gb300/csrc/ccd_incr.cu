@@ -44,9 +44,11 @@ constexpr int kIncListCap = 1024;    // entries of one column per CTA (one per t
 constexpr int kIncPosCap = 65536;    // positions per CTA (bitmask capacity)
 constexpr int kIncWords = kIncPosCap / 32;
 constexpr int kIncMaxCtas = 256;
-constexpr int kIncRec = kIncRecWords / 2;   // step record: G1, G2, LL, H1, R, I, error code
+constexpr int kIncRec = kIncRecWords / 2;   // step record payloads: G1, G2, LL, H1, R, I
+constexpr uint32_t kTagErr = 0x80000000u;   // tag bit: the writer raised an error
 constexpr double kIncRange = 60.0;          // |eta - shift| that keeps every sum inside float range
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kIncTraceSlots = 24;        // phase timestamps per step and CTA (COXGB_PHASE_TRACE)
 
 constexpr size_t inc_al16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -62,7 +64,7 @@ struct IncSmem {
   static constexpr size_t o_headp = o_headb + 4 * kIncWords;            // i32 [W]
   static constexpr size_t o_gs0 = o_headp + 4 * kIncWords;              // dw  [gcap] dense-scan S0
   static constexpr size_t o_gseen = o_gs0 + 8 * kIncGroupCap;           // u8  [gcap]
-  static constexpr size_t o_rec = inc_al16(o_gseen + kIncGroupCap);     // 8-byte slots [C][7] records
+  static constexpr size_t o_rec = inc_al16(o_gseen + kIncGroupCap);     // 8-byte slots [6][C] record payloads
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
   static constexpr size_t bytes = o_rref + 8 * 2 * kIncMaxCtas;
 };
@@ -85,6 +87,9 @@ struct IncState {
 static __device__ __forceinline__ void st_rlx_u64(uint64_t *p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+static __device__ __forceinline__ void st_rlx_v2(uint64_t *p, uint64_t a, uint64_t b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
 static __device__ __forceinline__ void ld_rlx_v2(const uint64_t *p, uint64_t &a, uint64_t &b) {
   asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
@@ -94,10 +99,6 @@ static __device__ __forceinline__ void put_tag2(uint64_t *w, uint32_t tag, uint3
 }
 static __device__ __forceinline__ void put_dw(uint64_t *w, uint32_t tag, dw v) {
   put_tag2(w, tag, __float_as_uint(v.h), __float_as_uint(v.l));
-}
-static __device__ __forceinline__ void put_f64(uint64_t *w, uint32_t tag, double v) {
-  const uint64_t b = uint64_t(__double_as_longlong(v));
-  put_tag2(w, tag, uint32_t(b), uint32_t(b >> 32));
 }
 static __device__ __forceinline__ bool tagged(uint64_t a, uint64_t b, uint32_t tag) {
   return uint32_t(a >> 32) == tag && uint32_t(b >> 32) == tag;
@@ -136,6 +137,45 @@ static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *ou
         return false;
       }
       if (*reinterpret_cast<volatile int32_t *>(err) != 0) return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+// Wait for the first n (<= N) tagged payloads of a record at w whose tags carry `tag` or `tag` with
+// the error bit; the payloads go to out. Returns 1 (clean), 2 (the writer raised an error) or 0
+// (the wait gave up: bound reached or another CTA raised an error).
+template <int N>
+static __device__ int wait_record(const uint64_t *w, int n, uint32_t tag, uint64_t *out, int32_t *err,
+                                  unsigned *npolls = nullptr) {
+  const long long t0 = clock64();
+  unsigned polls = 0;
+  for (;;) {
+    uint64_t a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) ld_rlx_v2(w + 2 * i, a[i], b[i]);
+    bool ok = true, bad = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) {
+        const uint32_t ta = uint32_t(a[i] >> 32), tb = uint32_t(b[i] >> 32);
+        ok = ok && (ta & ~kTagErr) == tag && (tb & ~kTagErr) == tag;
+        bad = bad || ((ta | tb) & kTagErr) != 0;
+      }
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) out[i] = (a[i] & 0xffffffffull) | ((b[i] & 0xffffffffull) << 32);
+      if (npolls) *npolls = polls + 1;
+      return bad ? 2 : 1;
+    }
+    if ((++polls & 63) == 0) {   // off the fast path: the bound and another CTA's failure
+      if (clock64() - t0 > kSpinBudget) {
+        atomicCAS(err, 0, COX_E_TIMEOUT);
+        return 0;
+      }
+      if (*reinterpret_cast<volatile int32_t *>(err) != 0) return 0;
     }
     __nanosleep(32);
   }
@@ -216,7 +256,7 @@ static __device__ void inc_seg_suffix2(dw x0, int f0, dw x1, int f1, int nact, d
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool act = warp * 32 < nact;   // warp-uniform
   if (act) {
-#pragma unroll
+#pragma unroll 1
     for (int off = 1; off < 32; off <<= 1) {
       const dw y0 = dw_shfl_down(x0, off), y1 = dw_shfl_down(x1, off);
       const int g0 = __shfl_down_sync(kFull, f0, off), g1 = __shfl_down_sync(kFull, f1, off);
@@ -309,7 +349,7 @@ static __device__ dw inc_dense(const IncParams &prm, int lo, int npos, const uin
         const uint32_t cw = cutb[bb >> 5], hw = headb[bb >> 5];
         dw x = xs[u];
         int f = in ? int((cw >> lane) & 1u) : 0;
-#pragma unroll
+#pragma unroll 1
         for (int off = 1; off < 32; off <<= 1) {
           const dw y = dw_shfl_down(x, off);
           const int g = __shfl_down_sync(kFull, f, off);
@@ -338,7 +378,7 @@ static __device__ dw inc_dense(const IncParams &prm, int lo, int npos, const uin
   if (warp == 0) {
     dw a = s_wagg[lane];
     int h = s_wflag[lane];
-#pragma unroll
+#pragma unroll 1
     for (int off = 1; off < 32; off <<= 1) {
       const dw y = dw_shfl_down(a, off);
       const int g = __shfl_down_sync(kFull, h, off);
@@ -416,14 +456,15 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   __shared__ int s_flg[2][32];
   __shared__ dw s_red[4][32];
   __shared__ double s_rll[32];
-  __shared__ dw s_G[2];
+  __shared__ dw s_Gq[2][4];   // G1, G2 over quarters of the CTAs
   __shared__ double s_LL;
   __shared__ dw s_chain[3];    // chain sums of the previous step's H1, R, I
   __shared__ dw s_carry[2];    // rebuild: carries of S0 and S1 from the later tiles
   __shared__ dw s_dagg[32], s_dcar[32];   // dense scan: warp aggregates, carries into warps
   __shared__ int s_dflg[32];
   __shared__ int s_chain_end, s_bad, s_err, s_anyerr;
-  __shared__ double s_inv_var;
+  __shared__ uint64_t s_pay[kIncRec];   // this CTA's record payloads (bits): G1, G2, LL, H1, R, I
+  __shared__ double s_inv_var, s_half_inv_var;
 
   const DevFit &F = prm.F;
   const DevData &D = prm.D;
@@ -464,6 +505,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
     st.epoch = ctl->epoch;
     st.E = st.pend_j >= 0 ? dw_from(expm1(st.pend_db)) : dw_make(0.0f);
     s_inv_var = 1.0 / F.l2_var;
+    s_half_inv_var = 0.5 / F.l2_var;
   }
   for (int jj = tid; jj < p; jj += kIncThreads) {
     bet[jj] = F.beta[jj];
@@ -498,14 +540,14 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
-#pragma unroll
+#pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) ex[i] += __shfl_down_sync(kFull, ex[i], off);
     if (lane == 0) { s_rll[warp] = ex[0]; s_red[0][warp] = dw_from(ex[1]); }
   }
   __syncthreads();
   if (warp == 0) {
     double a = s_rll[lane], b = dw_to(s_red[0][lane]);
-#pragma unroll
+#pragma unroll 1
     for (int off = 16; off > 0; off >>= 1) {
       a += __shfl_down_sync(kFull, a, off);
       b += __shfl_down_sync(kFull, b, off);
@@ -518,7 +560,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
     for (int base = 0; base < nw; base += 32) {
       const int c = base + lane < nw ? __popc(bits[base + lane]) : 0;
       int incl = c;
-#pragma unroll
+#pragma unroll 1
       for (int off = 1; off < 32; off <<= 1) {
         const int y = __shfl_up_sync(kFull, incl, off);
         if (lane >= off) incl += y;
@@ -538,11 +580,24 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
       }
     s_chain_end = e;
   }
+  // chain end of CTA tid (thread tid pushes this CTA's record into CTA tid's inbox: the head sums
+  // H1, R, I go only to CTAs whose last stratum continues into this tile)
+  int ce_of_tid = -1;
+  if (tid < C) {
+    const int k1 = prm.tile_k[tid + 1];
+    const bool lc = k1 > prm.tile_k[tid] && D.cut_pos[k1 - 1] == prm.tile_lo[tid + 1] - 1;
+    ce_of_tid = tid;
+    if (!lc)
+      for (int c = tid + 1; c < C; ++c) {
+        ce_of_tid = c;
+        if (prm.tile_k[c + 1] > prm.tile_k[c]) break;
+      }
+  }
   __syncthreads();
   const int segg = tid < ng ? inc_rank(cutb, cutp, qg) : 0;
   const bool tailg = tid < ng && segg == nc;
   const int RW = max(32, ((npos + 1023) / 1024) * 32);   // positions per warp in the dense scan
-  const double inv_var = s_inv_var;
+  const double inv_var = s_inv_var, half_inv_var = s_half_inv_var;
   // list slots: previous column (pending update), current, next, and the one being fetched
   int base = 0;
   if (st.state == kRunning) {
@@ -572,8 +627,8 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
     dw *lv_p = lv + sp * kIncListCap, *lv_c = lv + sc * kIncListCap, *lv_n = lv + sn * kIncListCap;
     double *le_p = le + sp * kIncListCap, *le_c = le + sc * kIncListCap, *le_n = le + sn * kIncListCap;
     const int np = pj >= 0 ? s_cnt[sp] : 0, ncur = s_cnt[sc], nnx = s_cnt[sn];
-    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * 8 : nullptr;
-    if (trace) trace[0] = inc_timer();
+    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * kIncTraceSlots : nullptr;
+    if (trace) { trace[0] = inc_timer(); trace[23] = uint64_t(clock64()); }
     // this coordinate's inputs to the step, loaded now so their latency overlaps the step
     double pre_dx = 0.0, pre_b = 0.0, pre_tr = 0.0;
     int pre_pen = 1;
@@ -582,6 +637,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
       pre_pen = F.penalize ? F.penalize[j] != 0 : 1;
       pre_b = bet[j];
       pre_tr = tru[j];
+      s_anyerr = 0;
     }
     // ---- 1. the pending update at the previous column's entries (one per thread):
     //         eta += dbeta (eq. parallel_xb); v (1 + (e^dbeta - 1)) (eq. parallel_d)
@@ -646,12 +702,14 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
     const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : -1;
     const dw vnx = tid < nnx ? lv_n[tid] : dw_make(0.0f);
     // ---- 3. segmented suffix sums of dD (previous column) and v (current column)
+    if (trace) trace[2] = inc_timer();
     inc_seg_suffix2(refresh ? dw_make(0.0f) : dd, refresh ? 1 : fp, x1, fc, refresh ? ncur : max(np, ncur), u0, u1, s_agg,
                     s_flg);
+    if (trace) trace[3] = inc_timer();
     __syncthreads();
     // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
     const dw H1 = (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? u1[0] : dw_make(0.0f);
-    if (trace) trace[2] = inc_timer();
+    if (trace) trace[4] = inc_timer();
     dw C1;
     if (refresh) {
       // ---- carries of the rebuilt S0 and of S1 from one exchange of the tiles' head sums
@@ -674,7 +732,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
       if (warp < 2) {
         dw c0 = dw_make(0.0f);
         for (int c = t + 1 + lane; c <= s_chain_end; c += 32) c0 = dw_add(c0, sref[2 * c + warp]);
-#pragma unroll
+#pragma unroll 1
         for (int off = 16; off > 0; off >>= 1) c0 = dw_add(c0, dw_shfl_down(c0, off));
         if (lane == 0) s_carry[warp] = c0;
       }
@@ -694,6 +752,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
       if (tailg && !dw_is_zero(E)) S0 = dw_add(S0, dw_mul(E, s_chain[0]));
       C1 = dw_add(s_chain[1], dw_mul(E, s_chain[2]));
     }
+    if (trace) trace[5] = inc_timer();
     // ---- 4. tie-group ratios (warps holding groups); the next column's head-segment sums R,
     //         and I over the entries this step's update may change (warps holding its entries)
     const bool gwarp = warp * 32 < ng, nwarp = warp * 32 < nnx;   // warp-uniform
@@ -714,15 +773,17 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
         }
         if (need_ll) r_ll = double(dg) * log(dw_to(S0));
       }
-#pragma unroll
+      if (trace) trace[6] = inc_timer();
+#pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) {
-        r_g1 = dw_add(r_g1, dw_shfl_down(r_g1, off));
-        r_g2 = dw_add(r_g2, dw_shfl_down(r_g2, off));
+        r_g1 = dw_add_same(r_g1, dw_shfl_down(r_g1, off));
+        r_g2 = dw_add_same(r_g2, dw_shfl_down(r_g2, off));
       }
       if (need_ll)
-#pragma unroll
+#pragma unroll 1
         for (int off = 16; off > 0; off >>= 1) r_ll += __shfl_down_sync(kFull, r_ll, off);
     }
+    if (trace && !gwarp) trace[6] = inc_timer();
     if (nwarp) {
       if (tid < nnx && inc_rank(cutb, cutp, qnx) == 0) {
         r_R = vnx;
@@ -732,7 +793,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
         }
       }
       if (__any_sync(kFull, !dw_is_zero(r_R))) {
-#pragma unroll
+#pragma unroll 1
         for (int off = 16; off > 0; off >>= 1) {
           r_R = dw_add(r_R, dw_shfl_down(r_R, off));
           r_I = dw_add(r_I, dw_shfl_down(r_I, off));
@@ -746,76 +807,98 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
       s_red[3][warp] = r_I;
       s_rll[warp] = r_ll;
     }
-    if (trace) trace[3] = inc_timer();
+    if (trace) trace[7] = inc_timer();
     __syncthreads();
-    // ---- one value per warp: sums of the warp partials, then this CTA's tagged record words
-    //      (G1, G2 and the head sums as double-words, LL in FP64, the error code)
+    if (trace) trace[8] = inc_timer();
+    // ---- one value per warp: sums of the warp partials (G1, G2, R, I as double-words, LL in
+    //      FP64), then this CTA's record, pushed into every CTA's inbox by thread r for reader r:
+    //      (G1, G2[, LL]) to every CTA, and (H1, R, I) as well to the CTAs whose chain holds this tile
     const int par = int(epoch & 1u);
-    uint64_t *myrec = prm.trec + int64_t(kIncRecWords) * (int64_t(par) * C + t);
     if (warp < 2 || warp == 3 || warp == 4) {
       const int v = warp < 2 ? warp : warp - 1;           // s_red row: G1, G2, R, I
       const int nv = warp < 2 ? (ng + 31) >> 5 : (nnx + 31) >> 5;
       dw a = lane < nv ? s_red[v][lane] : dw_make(0.0f);
-      for (int off = 1; off < nv; off <<= 1) a = dw_add(a, dw_shfl_down(a, off));
-      if (lane == 0) put_dw(myrec + 2 * (warp < 2 ? warp : warp + 1), epoch, a);   // words 0, 2, 8, 10
-      if (trace) trace[4] = inc_timer();
+      if (warp < 2)
+        for (int off = 1; off < nv; off <<= 1) a = dw_add_same(a, dw_shfl_down(a, off));
+      else
+        for (int off = 1; off < nv; off <<= 1) a = dw_add(a, dw_shfl_down(a, off));
+      if (lane == 0) s_pay[warp < 2 ? warp : warp + 1] = *reinterpret_cast<const uint64_t *>(&a);   // 0 G1, 1 G2, 4 R, 5 I
+      if (trace) trace[9] = inc_timer();
     } else if (warp == 2) {
       const int nv = (ng + 31) >> 5;
       double a = (need_ll && lane < nv) ? s_rll[lane] : 0.0;
       if (need_ll)
         for (int off = 1; off < nv; off <<= 1) a += __shfl_down_sync(kFull, a, off);
-      if (lane == 0) put_f64(myrec + 4, epoch, a);
+      if (lane == 0) s_pay[2] = uint64_t(__double_as_longlong(a));
     } else if (tid == 5 * 32) {
-      put_dw(myrec + 6, epoch, H1);
-      const int err = s_err;
-      if (err) atomicCAS(&ctl->error, 0, err);
-      put_tag2(myrec + 12, epoch, uint32_t(err), 0u);
+      s_pay[3] = *reinterpret_cast<const uint64_t *>(&H1);
     }
-    // ---- 5. all-gather of the records (one thread per CTA); meanwhile the other threads fetch
-    //         column j+2's entries with eta and v as of this step's update
+    __syncthreads();
+    if (trace) trace[10] = inc_timer();
+    const int nbase = need_ll ? 3 : 2;   // payloads every CTA gets
+    const uint32_t tag = (epoch & ~kTagErr) | (s_err ? kTagErr : 0u);
+    if (trace) trace[19] = inc_timer();
+    if (tid < C) {
+      uint64_t *w = prm.trec + int64_t(kIncRecWords) * ((int64_t(par) * C + tid) * C + t);
+      const int nw_ = (tid < t && ce_of_tid >= t) ? kIncRec : nbase;
+#pragma unroll 1
+      for (int i = 0; i < nw_; ++i) {
+        const uint64_t v = s_pay[i];
+        st_rlx_v2(w + 2 * i, (uint64_t(tag) << 32) | (v & 0xffffffffull), (uint64_t(tag) << 32) | (v >> 32));
+      }
+    }
+    if (tid == 0 && s_err) atomicCAS(&ctl->error, 0, s_err);
+    if (trace) trace[11] = inc_timer();
+    // ---- 5. the inbox: one thread per writer; meanwhile the other threads fetch column j+2's
+    //         entries with eta and v as of this step's update
     const int jf = (j + 2) % p;
     if (tid < C) {
       uint64_t r[kIncRec];
-      if (!wait_tagged<kIncRec>(prm.trec + int64_t(kIncRecWords) * (int64_t(par) * C + tid), epoch, r, &ctl->error)) {
+      unsigned polls = 0;
+      const int nr = (tid > t && tid <= s_chain_end) ? kIncRec : nbase;
+      const int got = wait_record<kIncRec>(prm.trec + int64_t(kIncRecWords) * ((int64_t(par) * C + t) * C + tid), nr,
+                                           epoch & ~kTagErr, r, &ctl->error, &polls);
+      if (trace) trace[20] = polls;
+      if (got != 1) {
         for (int i = 0; i < kIncRec; ++i) r[i] = 0;
-        r[kIncRec - 1] = uint64_t(uint32_t(COX_E_TIMEOUT));
+        atomicCAS(&s_anyerr, 0, got == 0 ? COX_E_TIMEOUT : 1);
       }
-      for (int i = 0; i < kIncRec; ++i) srec[kIncRec * tid + i] = r[i];
+      for (int i = 0; i < nr; ++i) srec[i * kIncMaxCtas + tid] = r[i];
+      if (trace) trace[12] = inc_timer();
     } else {
       inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap, &s_cnt[sf],
                     C, kIncThreads - C, &s_err);
     }
     __syncthreads();
-    if (trace) trace[5] = inc_timer();
-    // ---- 6. fixed-order reductions, one value per warp: G1, G2, LL over every CTA; H1, R, I over
-    //         the later tiles this tile's last stratum continues into; the error codes
-    if (warp < 2 || (warp >= 3 && warp < 6)) {
-      const int v = warp;   // record field: 0 G1, 1 G2, 3 H1, 4 R, 5 I
-      const int c0 = v < 3 ? 0 : t + 1, c1 = v < 3 ? C - 1 : s_chain_end;
+    if (trace) trace[13] = inc_timer();
+    // ---- 6. fixed-order reductions: G1 and G2 over every CTA by four warps each (quarters of the
+    //         CTAs, combined by the step), LL when evaluated; H1, R, I over the later tiles this
+    //         tile's last stratum continues into, one warp each
+    if (warp < 8) {
+      const int v = warp >> 2, qtr = warp & 3;   // payload 0 G1 / 1 G2, quarter of the CTAs
+      const int c0 = (C * qtr) >> 2, c1 = (C * (qtr + 1)) >> 2;
       dw a = dw_make(0.0f);
-      for (int c = c0 + lane; c <= c1; c += 32) a = dw_add(a, slot_dw(&srec[kIncRec * c + v]));
-#pragma unroll
+      for (int c = c0 + lane; c < c1; c += 32) a = dw_add_same(a, slot_dw(&srec[v * kIncMaxCtas + c]));
+#pragma unroll 1
+      for (int off = 16; off > 0; off >>= 1) a = dw_add_same(a, dw_shfl_down(a, off));
+      if (lane == 0) s_Gq[v][qtr] = a;
+      if (trace) trace[16] = inc_timer();
+    } else if (warp < 11) {
+      const int v = warp - 5;   // payload 3 H1, 4 R, 5 I
+      dw a = dw_make(0.0f);
+      for (int c = t + 1 + lane; c <= s_chain_end; c += 32) a = dw_add(a, slot_dw(&srec[v * kIncMaxCtas + c]));
+#pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) a = dw_add(a, dw_shfl_down(a, off));
-      if (lane == 0) {
-        if (v < 2) s_G[v] = a;
-        else s_chain[v - 3] = a;
-      }
-    } else if (warp == 2) {
+      if (lane == 0) s_chain[v - 3] = a;
+    } else if (warp == 11 && need_ll) {
       double a = 0.0;
-      if (need_ll) {
-        for (int c = lane; c < C; c += 32) a += slot_f64(&srec[kIncRec * c + 2]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
-      }
+      for (int c = lane; c < C; c += 32) a += slot_f64(&srec[2 * kIncMaxCtas + c]);
+#pragma unroll 1
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
       if (lane == 0) s_LL = a;
-    } else if (warp == 6) {
-      int e = 0;
-      for (int c = lane; c < C; c += 32) e |= (srec[kIncRec * c + 6] & 0xffffffffull) != 0;
-      e = __any_sync(kFull, e);
-      if (lane == 0) s_anyerr = e;
     }
     __syncthreads();
-    if (trace) trace[6] = inc_timer();
+    if (trace) trace[14] = inc_timer();
     // ---- 7. the coordinate step, computed identically by every CTA
     if (tid == 0) {
       bool stop = false;
@@ -841,18 +924,23 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
         st.pend_j = -1;   // this step already applied the pending update
         st.E = dw_make(0.0f);
       } else {
-        const double g1 = dw_to(s_G[0]) - pre_dx, g2 = dw_to(s_G[1]);
+        const dw G1 = dw_add_same(dw_add_same(s_Gq[0][0], s_Gq[0][1]), dw_add_same(s_Gq[0][2], s_Gq[0][3]));
+        const dw G2 = dw_add_same(dw_add_same(s_Gq[1][0], s_Gq[1][1]), dw_add_same(s_Gq[1][2], s_Gq[1][3]));
+        const double g1 = dw_to(G1) - pre_dx, g2 = dw_to(G2);
         double tr = pre_tr;
+        if (trace) trace[17] = inc_timer();
         const double s = inc_step_rule(g1, g2, pre_b, &tr, F.penalty, F.lambda, inv_var, pre_pen);
+        if (trace) trace[18] = inc_timer();
         const double b_new = pre_b + s;
         tru[j] = tr;
         bet[j] = b_new;
         if (s != 0.0) {
           st.pend_j = j;
           st.pend_db = s;
-          st.E = dw_from(expm1(s));
+          st.E = dw_from(exp(s) - 1.0);   // its absolute error is what the sums see
           st.bdx = fma(s, pre_dx, st.bdx);
-          st.pen = st.pen + (inc_penalty(F, j, b_new) - inc_penalty(F, j, pre_b));
+          if (pre_pen && F.penalty == COX_PEN_L1) st.pen += F.lambda * (fabs(b_new) - fabs(pre_b));
+          else if (pre_pen && F.penalty == COX_PEN_L2) st.pen += (b_new - pre_b) * (b_new + pre_b) * half_inv_var;
         } else {
           st.pend_j = -1;
           st.pend_db = 0.0;
@@ -869,7 +957,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
         st.j = jn;
       }
       st.epoch = epoch + 1u;
-      if (trace) trace[7] = inc_timer();
+      if (trace) { trace[15] = inc_timer(); trace[22] = uint64_t(clock64()); }
     }
     __syncthreads();
     ++base;

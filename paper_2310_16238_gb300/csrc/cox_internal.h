@@ -106,21 +106,22 @@ struct ResParams {
 
 struct dw;   // double-word float (dw.cuh)
 
-// Words of one step record of the incremental kernel: 7 tagged doubles (G1, G2, LL, H1, R, I,
-// error code), two 8-byte words each.
-constexpr int kIncRecWords = 14;
+// Words of one step record of the incremental kernel: 6 tagged 8-byte payloads (G1, G2, H1, R, I
+// as double-words, LL in FP64), two 8-byte words each.
+constexpr int kIncRecWords = 12;
 
 // Arguments of the incremental kernel (ccd_incr.cu), passed by value.
 struct IncParams {
   DevFit F;               // the fit (its d pointer is not used)
   DevData D;              // the data descriptor
   const int32_t *tile_lo, *tile_g, *tile_k, *col_tile;   // incremental tile plan: one tile per CTA
-  uint64_t *trec;         // [2][C][kIncRecWords] epoch-tagged step records, double-buffered by step parity
+  uint64_t *trec;         // [2][C readers][C writers][kIncRecWords] epoch-tagged step records (each
+                          // CTA writes its record into every CTA's inbox), double-buffered by parity
   uint64_t *tref;         // [C][4] epoch-tagged head sums of the dense refresh
   double *bcopy;          // [C][2p] each CTA's copy of beta and the trust half-widths
   dw *vdw;                // [M] v per position as a double-word (the kernel's working copy)
   int64_t max_steps;      // coordinate steps this launch may take
-  uint64_t *trace;        // optional [trace_steps][C][8] phase timestamps (ns)
+  uint64_t *trace;        // optional [trace_steps][C][24] phase timestamps (ns) and counters
   int64_t trace_steps;
 };
 

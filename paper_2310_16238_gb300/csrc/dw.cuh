@@ -8,7 +8,8 @@
 // available precision", Numer. Math. 18, 1971). Double-word operations follow the algorithms
 // analysed by M. Joldes, J.-M. Muller and V. Popescu, "Tight and rigorous error bounds for basic
 // building blocks of double-word arithmetic", ACM TOMS 44(2), 2017: the accurate DW+DW sum
-// (relative error <= 3u^2 + 13u^3), DW*FP (<= 2u^2), DW*DW with FMA (<= 5u^2) and DW/DW
+// (relative error <= 3u^2 + 13u^3; the sloppy sum for same-sign operands), DW*FP (<= 2u^2),
+// DW*DW with FMA (<= 5u^2) and DW/DW
 // (<= 15u^2 + 56u^3), u = 2^-24. Every step uses explicitly rounded intrinsics so that no
 // compiler contraction can change the error-free transformations.
 #pragma once
@@ -73,6 +74,14 @@ DW_FN dw dw_add(dw x, dw y) {
   const dw v = fast_two_sum(s.h, c);
   const float w = dw_fadd(t.l, v.l);
   return fast_two_sum(v.h, w);
+}
+// x + y for operands of the same sign (the sloppy double-word sum of the same paper: fewer
+// operations, relative error within 3u^2 when x and y do not cancel)
+DW_FN dw dw_add_same(dw x, dw y) {
+  const dw s = two_sum(x.h, y.h);
+  const float v = dw_fadd(x.l, y.l);
+  const float w = dw_fadd(s.l, v);
+  return fast_two_sum(s.h, w);
 }
 DW_FN dw dw_neg(dw x) { return {-x.h, -x.l}; }
 DW_FN dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }

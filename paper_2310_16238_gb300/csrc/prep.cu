@@ -460,6 +460,24 @@ __global__ void col_tile_kernel(int32_t p, int32_t T, const int64_t *col_ptr, co
   }
 }
 
+// Shortest run of risk positions that holds cap + 1 entries of one column, over every column
+// (one warp per column): a tile shorter than it holds at most cap entries of any column.
+__global__ void window_kernel(int32_t p, const int64_t *col_ptr, const uint32_t *idx, int32_t cap, int32_t *out_min) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t j = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; j < p; j += nwarps) {
+    const int64_t a = col_ptr[j], n = col_ptr[j + 1] - a;
+    int32_t best = 0x7fffffff;
+    for (int64_t k = lane; k + cap < n; k += 32) {
+      const int32_t w = int32_t(idx[a + k + cap] & kPosMask) - int32_t(idx[a + k] & kPosMask) + 1;
+      best = min(best, w);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, off));
+    if (lane == 0 && best < 0x7fffffff) atomicMin(out_min, best);
+  }
+}
+
 // ------------------------------------------------------------------ host orchestration
 static bool is_device_ptr(const void *p) {
   if (!p) return false;
@@ -858,11 +876,25 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
     }
     const int inc_grid = inc_max_grid(precision);
     if (inc_grid > 0) {
-      // candidate plans, best balanced first: equal tie groups per tile (the step's cost), then
-      // the same with shorter tiles, then equal positions; the first whose every column fits the
-      // kernel's list capacity in every tile is taken
+      // candidate plans: equal tie groups per tile (the step's cost) with tiles shorter than the
+      // shortest run of positions holding more entries of one column than the kernel's list
+      // capacity; then equal positions. The first whose lists fit is taken.
+      int32_t wmin = 0x7fffffff;
+      {
+        int32_t *d_w = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
+        if (!d_w) return COX_E_OOM;
+        cudaMemcpyAsync(d_w, &wmin, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        count_launches(1);
+        window_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr, idx, inc_list_cap(), d_w);
+        if (cudaMemcpyAsync(&wmin, d_w, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          *err = "cox_create: table kernels failed";
+          return COX_E_CUDA;
+        }
+      }
+      const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(wmin) - 1);
       std::vector<std::vector<int32_t>> cands;
-      for (int64_t pc = inc_pos_cap(); pc >= 1024; pc /= 4) cands.push_back(group_plan(D.M, pc, inc_group_cap(), inc_grid, h_head));
+      if (pos_cap >= 32) cands.push_back(group_plan(D.M, pos_cap, inc_group_cap(), inc_grid, h_head));
       cands.push_back(fit_plan(D.M, inc_pos_cap(), size_t(inc_group_cap()), inc_grid, h_head));
       for (const auto &il : cands) {
         if (il.empty()) continue;

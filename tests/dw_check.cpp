@@ -14,6 +14,7 @@ int main() {
     const dw x{xh, xl}, y{yh, yl};
     dw r{0.0f, 0.0f};
     if (!std::strcmp(op, "add")) r = coxgb::dw_add(x, y);
+    else if (!std::strcmp(op, "addsame")) r = coxgb::dw_add_same(x, y);
     else if (!std::strcmp(op, "mul")) r = coxgb::dw_mul(x, y);
     else if (!std::strcmp(op, "mulf")) r = coxgb::dw_mul_f(x, yh);
     else if (!std::strcmp(op, "div")) r = coxgb::dw_div(x, y);

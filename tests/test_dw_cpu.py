@@ -17,7 +17,8 @@ import pytest
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2310_16238_gb300", "csrc")
 U = Fraction(1, 2 ** 24)
-BOUND = {"add": 3 * U ** 2 + 13 * U ** 3, "mulf": 2 * U ** 2, "mul": 5 * U ** 2, "div": 15 * U ** 2 + 56 * U ** 3}
+BOUND = {"add": 3 * U ** 2 + 13 * U ** 3, "addsame": 3 * U ** 2 + 13 * U ** 3, "mulf": 2 * U ** 2, "mul": 5 * U ** 2,
+         "div": 15 * U ** 2 + 56 * U ** 3}
 
 
 @pytest.fixture(scope="module")
@@ -39,13 +40,15 @@ def _split(x):
     return h, np.float32(x - float(h))
 
 
-def _inputs(rng, n):
+def _inputs(rng, n, same_sign=False):
     out = []
     for _ in range(n):
         e1, e2 = rng.integers(-30, 30, 2)
         a = rng.uniform(0.5, 1.0) * 2.0 ** e1 * rng.choice([-1.0, 1.0])
         b = rng.uniform(0.5, 1.0) * 2.0 ** e2 * rng.choice([-1.0, 1.0])
-        if rng.random() < 0.2:   # near-cancellation for the sum
+        if same_sign:
+            b = abs(b) if a > 0 else -abs(b)
+        elif rng.random() < 0.2:   # near-cancellation for the sum
             b = -a * (1.0 + rng.uniform(-1e-6, 1e-6))
         out.append((_split(a), _split(b)))
     return out
@@ -75,17 +78,17 @@ def test_error_free_transforms(driver):
         assert _fr(p) + _fr(q) == _fr(xh) * _fr(yh)
 
 
-@pytest.mark.parametrize("op", ["add", "mulf", "mul", "div"])
+@pytest.mark.parametrize("op", ["add", "addsame", "mulf", "mul", "div"])
 def test_double_word_ops_within_published_bounds(driver, op):
-    rng = np.random.default_rng({"add": 1, "mulf": 2, "mul": 3, "div": 4}[op])
-    cases = _inputs(rng, 600)
+    rng = np.random.default_rng({"add": 1, "addsame": 5, "mulf": 2, "mul": 3, "div": 4}[op])
+    cases = _inputs(rng, 600, same_sign=(op == "addsame"))
     lines = [f"{op} {float(a[0]).hex()} {float(a[1]).hex()} {float(b[0]).hex()} {float(b[1]).hex()}" for a, b in cases]
     res = _run(driver, lines)
     worst = Fraction(0)
     for (a, b), (rh, rl) in zip(cases, res):
         x = _fr(a[0]) + _fr(a[1])
         y = _fr(b[0]) + _fr(b[1]) if op != "mulf" else _fr(b[0])
-        exact = {"add": x + y, "mulf": x * y, "mul": x * y, "div": x / y}[op]
+        exact = {"add": x + y, "addsame": x + y, "mulf": x * y, "mul": x * y, "div": x / y}[op]
         got = _fr(rh) + _fr(rl)
         if exact == 0:
             assert got == 0

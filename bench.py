@@ -92,6 +92,14 @@ class ClockSampler:
 
 ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 
+# DRAM bytes (read + write) per coordinate step of the dominant kernel, from one ncu capture of
+# the same kernel on the same workload (launch total / steps it ran); the summaries and commands
+# are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
+TRAFFIC = {
+    ("incremental", "stratified_sparse", "fp64"): (157.739264e6 + 35.210752e6) / 2001,
+    ("incremental", "time_varying", "fp64"): (1157.1456e6 + 5891.47136e6) / 20001,
+}
+
 
 def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):
     """Whole-job throughput over replicas: every rank processed `units_per_rank` per step; the
@@ -110,6 +118,60 @@ def workload(rank: int, scale: float = 1.0):
     data, opts = synth.stratified_sparse(n=n, p=2000, k=100, seed=synth.SEED_BASE + 2 + rank)
     name = f"stratified_sparse N={n} p=2000 K=100 binary density logU[1e-4,5e-2] L1 gamma=1e-3*N"
     return data, opts, name
+
+
+def dtype_of(engine, s_e):
+    """Arithmetic of the path: the incremental engine sums in double-word FP32 (about 48 bits) with
+    FP64 eta, beta and step; the dense engines in FP64, or FP32 with compensation and FP64 carries."""
+    if engine == "incremental":
+        return "f32x2+f64"
+    return "f64" if s_e == 8 else "f32+f64"
+
+
+def roofline_of(engine, data, beta, G, K, s_e, step_us, wname, precision_name):
+    """Roofline of the coordinate step of one fit (per coordinate step: the fit's CUDA-event time
+    over the steps it ran). Dense engines: FP64 instructions (FP64 path, bound by the FP64 pipe)
+    or bytes (FP32C path). Incremental engine: its O(groups + entries) arithmetic against the FP64
+    rate, plus the dense-equivalent bandwidth (the bytes the paper's dense scan moves per step over
+    this step's time)."""
+    M = data.n if data.start is None else 2 * data.n
+    nnz_mean = float(np.diff(data.col_ptr).mean())
+    moved = np.count_nonzero(beta) > 0
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp64_peak = 1.25e12 / 2 / 1e9   # recipe: 1.25 TFLOP/s FP64 = 0.625e12 FP64 instructions/s
+    p_cols = data.p
+    nnz_pos = nnz_mean * (2.0 if data.start is not None else 1.0)
+    dense_bytes = s_e * M + 8.0 * G + 4.0 * K + 4.0 * nnz_mean + ((4 + 16 + s_e) * nnz_mean if moved else 0.0)
+    if engine == "incremental":
+        # per coordinate step: a suffix of dD and one of v over the column's entries, and per tie
+        # group two adds, a divide and two multiply-adds; plus the dense S0 rebuild (one add per
+        # position) once per sweep, spread over the sweep's p steps
+        alg_ops = 2.0 * nnz_pos + 5.0 * G + M / p_cols
+        # bytes: the column's entries (4) with eta and v read (8 + 8) and, when beta moved,
+        # written back; plus the rebuild's read of eta and write of v once per sweep
+        alg_bytes = (4.0 + 16.0) * nnz_pos + (16.0 * nnz_pos if moved else 0.0) + (8.0 + 8.0 + s_e) * M / p_cols
+    else:
+        alg_ops = M + nnz_mean + 4.0 * G
+        alg_bytes = dense_bytes
+    hbm_equiv = alg_bytes / (step_us * 1e-6) / 1e9
+    traffic = TRAFFIC.get((engine, wname.split()[0], precision_name))
+    if s_e == 8 or engine == "incremental":
+        achieved = alg_ops / (step_us * 1e-6) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "Gop/s (FP64)",
+                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": f"ccd ({engine})", "step_us": step_us,
+                "alg_fp64_ops_per_step": alg_ops,
+                "peak_source": "derived from the recipe's FP64 rate (1.25 TFLOP/s, FMA = 2 flops); of nominal",
+                "hbm_equivalent": {"achieved_gbs": hbm_equiv, "peak_gbs": hbm_peak, "frac": hbm_equiv / hbm_peak,
+                                   "alg_bytes_per_step": alg_bytes}}
+        if engine == "incremental":
+            dense_gbs = dense_bytes / (step_us * 1e-6) / 1e9
+            roof["dense_equivalent"] = {"gbs": dense_gbs, "frac_of_hbm_peak": dense_gbs / hbm_peak,
+                                        "dense_bytes_per_step": dense_bytes}
+        return roof
+    return {"bound": "hbm", "achieved": hbm_equiv, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
+            "traffic": traffic, "kernel": f"ccd ({engine})", "step_us": step_us, "alg_bytes_per_step": alg_bytes,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -169,50 +231,17 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the coordinate step (per coordinate step: the sweep loop's CUDA-event time over
     # the steps it ran -- coord_updates plus the final convergence check of each fit)
     s_e = 4 if precision == cox.COX_FP32C else 8
-    M = data.n if data.start is None else 2 * data.n
-    nnz_mean = float(np.diff(data.col_ptr).mean())
     steps_run = float(np.sum([i["coord_updates"] + 1 for i in infos]))
     step_us = float(np.sum([i["sweep_ms"] for i in infos])) / steps_run * 1e3
     engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
-    moved = np.count_nonzero(beta) > 0
-    peaks = _peaks()
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak = 1.25e12 / 2 / 1e9   # recipe: 1.25 TFLOP/s FP64 = 0.625e12 FP64 instructions/s
-    p_cols = data.p
-    nnz_pos = nnz_mean * (2.0 if data.start is not None else 1.0)
-    if engine == "incremental":
-        # per coordinate step: a suffix of dD and one of v over the column's entries, and per tie
-        # group two adds, a divide and two multiply-adds; plus the dense S0 rebuild (one add per
-        # position) once per sweep, spread over the sweep's p steps
-        alg_ops = 2.0 * nnz_pos + 5.0 * G + M / p_cols
-        # bytes: the column's entries (4) with eta and v read (8 + s_e) and, when beta moved,
-        # written back; plus the rebuild's read of v once per sweep
-        alg_bytes = (4.0 + 8.0 + s_e) * nnz_pos + ((8.0 + s_e) * nnz_pos if moved else 0.0) + s_e * M / p_cols
-    else:
-        # paper's dense-scan method: one add per position (sum of D), one per column entry (sum of
-        # N1), and per tie group a divide, a multiply and two multiply-adds (ratios, G1, G2)
-        alg_ops = M + nnz_mean + 4.0 * G
-        alg_bytes = s_e * M + 8.0 * G + 4.0 * K + 4.0 * nnz_mean + ((4 + 16 + s_e) * nnz_mean if moved else 0.0)
-    hbm_equiv = alg_bytes / (step_us * 1e-6) / 1e9
-    if s_e == 8 or engine == "incremental":
-        achieved = alg_ops / (step_us * 1e-6) / 1e9
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "Gop/s (FP64)",
-                    "frac": achieved / fp64_peak, "traffic": None, "kernel": f"ccd ({engine})", "step_us": step_us,
-                    "alg_fp64_ops_per_step": alg_ops,
-                    "peak_source": "derived from the recipe's FP64 rate (1.25 TFLOP/s, FMA = 2 flops); of nominal",
-                    "hbm_equivalent": {"achieved_gbs": hbm_equiv, "peak_gbs": hbm_peak, "frac": hbm_equiv / hbm_peak,
-                                       "alg_bytes_per_step": alg_bytes}}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm_equiv, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
-                    "traffic": None, "kernel": f"ccd ({engine})", "step_us": step_us, "alg_bytes_per_step": alg_bytes,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roofline = roofline_of(engine, data, beta, G, K, s_e, step_us, wname, args.precision)
     value, slowest_ms = aggregate_ranks(coords, step_ms, world, dev)
     vals = np.array([value, slowest_ms])
     result = {
         "metric": "coordinate updates/sec (CCD, stratified Cox, one fit per step)",
         "value": value, "unit": "coord_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": float(vals[1]), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if s_e == 8 else "f32+f64", "data": "synthetic (seeded; paper cohorts unavailable)",
+        "dtype": dtype_of(engine, s_e), "data": "synthetic (seeded; paper cohorts unavailable)",
         "config": {"workload": wname, "precision": args.precision, "parallelism": f"replicas{world}",
                    "sweeps": infos[-1]["sweeps"], "coord_updates_per_fit": coords, "tie_groups": G, "strata": K,
                    "fits_per_s": world / (vals[1] * 1e-3), "l2": "flushed before every step (512 MB write)",
@@ -291,14 +320,21 @@ def run_time_varying(args):
     ms = float(np.mean(times))
     coords = float(np.mean([i["coord_updates"] for i in infos]))
     steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
+    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
+    h2 = cox.cox_create(data, opts, precision=precision)
+    md = cox.cox_metadata(h2)
+    cox.cox_destroy(h2)
+    wname = f"time_varying subjects={n_subj} rows={data.n} p=5000 K=20 L2 var=0.1"
+    roof = roofline_of(engine, data, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
+                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
     return {"metric": "coordinate updates/sec (CCD, counting-process Cox, one fit per step)",
             "value": coords / (ms * 1e-3), "unit": "coord_updates/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision == cox.COX_FP64 else "f32+f64", "data": "synthetic (seeded)",
-            "config": {"workload": f"time_varying subjects={n_subj} rows={data.n} p=5000 K=20 L2 var=0.1",
-                       "precision": args.precision, "sweeps": infos[-1]["sweeps"], "loglik": infos[-1]["loglik"],
-                       "step_us": float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3,
-                       "engine": ENGINE_NAMES.get(infos[-1]["engine"], "unknown")}}
+            "vs_baseline": None, "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4), "data": "synthetic (seeded)",
+            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
+                       "loglik": infos[-1]["loglik"], "step_us": step_us, "engine": engine},
+            "roofline": roof}
 
 
 def run_batch(args):

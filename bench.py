@@ -380,8 +380,32 @@ def run_batch(args):
                                   "coord_updates": int(sum(i["coord_updates"] for i in infos))}
         for h in handles:
             h.close()
-    out["value"] = out["batched_fp32c"]["fits_per_s"]
-    out["ms_per_step"] = 1e3 * out["batched_fp32c"]["seconds"]
+    # the incremental kernel: every fit on its compact plan, fits packed into waves of one CTA per
+    # SM (its per-data plan is built inside the timed call, on first use)
+    handles = []
+    for d, olist in sets:
+        base = cox.Handle(d, olist[0], precision=cox.COX_FP64)
+        handles.append(base)
+        handles.extend(base.clone(o) for o in olist[1:])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    betas, infos = cox.batch_fit(handles)
+    sec = time.perf_counter() - t0
+    err = 0.0
+    for (si, li), (b, info) in ref.items():
+        bb = betas[si * 16 + li]
+        err = max(err, float(np.max(np.abs(bb - b)) / max(np.max(np.abs(b)), 1e-12)) if np.any(b) else
+                  float(np.max(np.abs(bb))))
+    out["batched_incremental"] = {"fits": len(handles), "seconds": sec, "fits_per_s": len(handles) / sec,
+                                  "engine": ENGINE_NAMES.get(infos[0]["engine"], "unknown"),
+                                  "max_rel_beta_err_vs_fp64_single": err,
+                                  "coord_updates": int(sum(i["coord_updates"] for i in infos))}
+    for h in handles:
+        h.close()
+    best = max(("batched_fp32c", "batched_fp64", "batched_incremental"), key=lambda k: out[k]["fits_per_s"])
+    out["value"] = out[best]["fits_per_s"]
+    out["ms_per_step"] = 1e3 * out[best]["seconds"]
+    out["config"]["engine"] = best
     return out
 
 

@@ -77,6 +77,8 @@ struct cox_handle {
   uint64_t *i_trec = nullptr, *i_tref = nullptr;
   double *i_bcopy = nullptr;
   dw *i_vdw = nullptr;
+  IncParams *i_prm = nullptr;   // device copy of the fit's kernel arguments
+  int2 *i_map = nullptr;        // CTA -> (fit 0, tile)
   std::string err = "no error";
 };
 
@@ -168,8 +170,14 @@ int alloc_fit_state(cox_handle *h) {
     h->i_tref = static_cast<uint64_t *>(B.get(4 * int64_t(IT) * sizeof(uint64_t)));
     h->i_bcopy = static_cast<double *>(B.get(std::max<int64_t>(2 * p * IT, 1) * sizeof(double)));
     h->i_vdw = static_cast<dw *>(B.get(std::max<int64_t>(M, 1) * 2 * sizeof(float)));
-    if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw)
+    h->i_prm = static_cast<IncParams *>(B.get(sizeof(IncParams)));
+    h->i_map = static_cast<int2 *>(B.get(int64_t(IT) * sizeof(int2)));
+    if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw || !h->i_prm || !h->i_map)
       return fail(h, COX_E_OOM, "device allocation failed for the incremental state");
+    std::vector<int2> map(static_cast<size_t>(IT));
+    for (int t = 0; t < IT; ++t) map[t] = make_int2(0, t);
+    if (cudaMemcpyAsync(h->i_map, map.data(), IT * sizeof(int2), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return cuda_fail(h, "map copy");
   }
   if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
@@ -430,6 +438,151 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   return rc2 ? rc2 : rc;
 }
 
+// Kernel arguments of a fit on the incremental kernel: the full plan (one fit over the whole GPU)
+// or the compact plan (the fewest tiles; a batch runs several fits per launch).
+IncParams incr_params(cox_handle *h, bool compact) {
+  const Prepared &P = h->sd->prep;
+  IncParams prm{};
+  prm.F = h->hfit;
+  prm.D = D(h);
+  prm.T = compact ? P.cinc_T : P.inc_T;
+  prm.tile_lo = compact ? P.cinc_tile_lo : P.inc_tile_lo;
+  prm.tile_g = compact ? P.cinc_tile_g : P.inc_tile_g;
+  prm.tile_k = compact ? P.cinc_tile_k : P.inc_tile_k;
+  prm.col_tile = compact ? P.cinc_col_tile : P.inc_col_tile;
+  prm.trec = h->i_trec;
+  prm.tref = h->i_tref;
+  prm.bcopy = h->i_bcopy;
+  prm.vdw = h->i_vdw;
+  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * D(h).p + 2;
+  return prm;
+}
+
+// The fit's result from its control block (already read into h_ctl).
+int incr_result(cox_handle *h, double *beta_out, cox_fit_info *info, float ms) {
+  int rc;
+  if ((rc = device_error(h))) return rc;
+  const FitCtl &c = *h->h_ctl;
+  if (c.state == kRunning) return fail(h, COX_E_INVALID, "cox_fit: the incremental kernel stopped before the fit did");
+  rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
+  if (info) {
+    info->sweeps = c.sweep;
+    info->converged = c.state == kConverged;
+    info->coord_updates = c.coord_updates;
+    info->loglik = c.loglik;
+    info->objective = c.obj;
+    info->status = rc;
+    info->engine = COX_ENGINE_INCR;
+    info->step_launches = 1;
+    info->sweep_ms = ms;
+  }
+  const int rc2 = copy_out(h, beta_out, h->hfit.beta, D(h).p);
+  return rc2 ? rc2 : rc;
+}
+
+// Many fits on the incremental kernel: each fit runs on its compact plan's CTAs, fits packed
+// largest first into waves of at most one CTA per SM, one cooperative launch per wave (the CTAs
+// of a fit exchange records only among themselves).
+int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, double *const *beta_out, cox_fit_info *info) {
+  const int precision = hs[0]->sd->precision;
+  cudaStream_t s = hs[0]->stream;
+  const int grid = inc_max_grid(precision);
+  std::vector<cudaStream_t> saved(n);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = hs[i]->stream;
+    hs[i]->stream = s;
+  }
+  int rc = COX_OK;
+  for (int i = 0; i < n && !rc; ++i) rc = init_state(hs[i], beta0 ? beta0[i] : nullptr);
+  auto tiles = [&](int i) { return hs[i]->sd->prep.cinc_T; };
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tiles(a) > tiles(b); });
+  std::vector<std::vector<int>> waves;
+  std::vector<int> used;
+  for (int i : order) {
+    size_t w = 0;
+    while (w < waves.size() && used[w] + tiles(i) > grid) ++w;
+    if (w == waves.size()) {
+      waves.emplace_back();
+      used.push_back(0);
+    }
+    waves[w].push_back(i);
+    used[w] += tiles(i);
+  }
+  BufferSet B;
+  IncParams *dprm = static_cast<IncParams *>(B.get(size_t(n) * sizeof(IncParams)));
+  int2 *dmap = static_cast<int2 *>(B.get(size_t(waves.size()) * grid * sizeof(int2)));
+  if (!rc && (!dprm || !dmap)) rc = fail(nullptr, COX_E_OOM, "cox_batch_fit: allocation");
+  std::vector<IncParams> hp(n);
+  std::vector<int2> hm(waves.size() * size_t(grid));
+  std::vector<cudaEvent_t> ev(waves.size() + 1, nullptr);
+  for (auto &e : ev)
+    if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = cuda_fail(nullptr, "event create");
+  int off = 0;
+  if (!rc) cudaEventRecord(ev[0], s);
+  for (size_t w = 0; w < waves.size() && !rc; ++w) {
+    int cta = 0;
+    for (size_t k = 0; k < waves[w].size() && !rc; ++k) {
+      cox_handle *h = hs[waves[w][k]];
+      const int T = tiles(waves[w][k]);
+      hp[off + k] = incr_params(h, true);
+      for (int t = 0; t < T; ++t) hm[w * grid + cta++] = make_int2(int(k), t);
+      // tag 0 never matches: records start at epoch 1
+      if (cudaMemsetAsync(h->i_trec, 0, 2 * kIncRecWords * int64_t(T) * T * sizeof(uint64_t), s) != cudaSuccess ||
+          cudaMemsetAsync(h->i_tref, 0, 4 * int64_t(T) * sizeof(uint64_t), s) != cudaSuccess)
+        rc = cuda_fail(nullptr, "memset");
+    }
+    if (!rc && (cudaMemcpyAsync(dprm + off, hp.data() + off, waves[w].size() * sizeof(IncParams), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(dmap + w * grid, hm.data() + w * grid, cta * sizeof(int2), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess))
+      rc = cuda_fail(nullptr, "params copy");
+    if (!rc && launch_incr(precision, dprm + off, dmap + w * grid, cta, s)) rc = cuda_fail(nullptr, "incremental launch");
+    if (!rc) cudaEventRecord(ev[w + 1], s);
+    off += int(waves[w].size());
+  }
+  int worst = rc;
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) worst = rc = cuda_fail(nullptr, "batch execution");
+  if (!rc) {
+    // each fit's time is the time of its wave
+    std::vector<float> wms(waves.size(), 0.0f);
+    for (size_t w = 0; w < waves.size(); ++w) cudaEventElapsedTime(&wms[w], ev[w], ev[w + 1]);
+    if (std::getenv("COXGB_BATCH_TRACE")) {   // opt-in: the waves' composition and times
+      for (size_t w = 0; w < waves.size(); ++w) {
+        int64_t maxsteps = 0, sumsteps = 0;
+        for (int i : waves[w]) {
+          read_ctl(hs[i]);
+          maxsteps = std::max<int64_t>(maxsteps, hs[i]->h_ctl->coord_updates + hs[i]->h_ctl->sweep);
+          sumsteps += hs[i]->h_ctl->coord_updates;
+        }
+        std::fprintf(stderr, "[batch trace] wave %zu: %zu fits on %d CTAs, %.2f ms, longest fit %lld steps (%.2f us/step), "
+                     "%lld coordinate steps in all\n", w, waves[w].size(), used[w], wms[w], (long long)maxsteps,
+                     maxsteps ? 1e3 * wms[w] / double(maxsteps) : 0.0, (long long)sumsteps);
+      }
+    }
+    for (size_t w = 0; w < waves.size(); ++w)
+      for (int i : waves[w]) {
+        cox_handle *h = hs[i];
+        int r = read_ctl(h);
+        if (!r) r = incr_result(h, beta_out[i], info ? info + i : nullptr, wms[w]);
+        if (r == COX_E_RANGE && h->opts.engine == COX_ENGINE_AUTO) {
+          // beyond the double-word range: this fit again on an FP64 engine
+          h->stream = saved[i];
+          r = cox_fit(h, beta0 ? beta0[i] : nullptr, beta_out[i], info ? info + i : nullptr);
+          h->stream = s;
+        }
+        if (info) info[i].status = r;
+        if (r < 0 || (worst >= 0 && r > worst)) worst = r;
+      }
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < n; ++i) hs[i]->stream = saved[i];
+  cudaStreamSynchronize(s);
+  return worst;
+}
+
 // The whole fit in one cooperative launch of the incremental kernel (state already initialized).
 int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   const DevData &d = D(h);
@@ -440,18 +593,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   if (cudaMemsetAsync(h->i_trec, 0, 2 * kIncRecWords * int64_t(IT) * IT * sizeof(uint64_t), s) != cudaSuccess ||
       cudaMemsetAsync(h->i_tref, 0, 4 * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
-  IncParams prm{};
-  prm.F = h->hfit;
-  prm.D = d;
-  prm.tile_lo = P.inc_tile_lo;
-  prm.tile_g = P.inc_tile_g;
-  prm.tile_k = P.inc_tile_k;
-  prm.col_tile = P.inc_col_tile;
-  prm.trec = h->i_trec;
-  prm.tref = h->i_tref;
-  prm.bcopy = h->i_bcopy;
-  prm.vdw = h->i_vdw;
-  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
+  IncParams prm = incr_params(h, false);
   // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
   const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
@@ -463,8 +605,10 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   }
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
+  if (cudaMemcpyAsync(h->i_prm, &prm, sizeof(IncParams), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cuda_fail(h, "params copy");
   cudaEventRecord(h->ev0, s);
-  if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+  if (launch_incr(h->sd->precision, h->i_prm, h->i_map, IT, s)) return cuda_fail(h, "incremental launch");
   cudaEventRecord(h->ev1, s);
   int rc;
   if ((rc = read_ctl(h))) return rc;
@@ -515,25 +659,9 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
     for (int q = 0; q < std::min(IT, 3) && n; ++q) row("slow", order[q]);
     if (n) row("fast", order[IT - 1]);
   }
-  if ((rc = device_error(h))) return rc;
-  const FitCtl &c = *h->h_ctl;
-  if (c.state == kRunning) return fail(h, COX_E_INVALID, "cox_fit: the incremental kernel stopped before the fit did");
-  rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
-  if (info) {
-    info->sweeps = c.sweep;
-    info->converged = c.state == kConverged;
-    info->coord_updates = c.coord_updates;
-    info->loglik = c.loglik;
-    info->objective = c.obj;
-    info->status = rc;
-    info->engine = COX_ENGINE_INCR;
-    info->step_launches = 1;
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    info->sweep_ms = ms;
-  }
-  const int rc2 = copy_out(h, beta_out, h->hfit.beta, d.p);
-  return rc2 ? rc2 : rc;
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  return incr_result(h, beta_out, info, ms);
 }
 
 }  // namespace
@@ -852,6 +980,21 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     if (!hs[i] || !beta_out[i]) return fail(nullptr, COX_E_INVALID, "cox_batch_fit: null handle or output");
     if (hs[i]->sd->precision != precision) return fail(nullptr, COX_E_INVALID, "cox_batch_fit: mixed precisions");
   }
+  // every fit on the incremental kernel when each qualifies and its compact plan fits the GPU; in
+  // FP64 (measured on a 256-fit cross-validation batch: 424 fits/s against 277 for the streaming
+  // batch), while the compensated-FP32 streaming batch stays the faster FP32C path (567 fits/s)
+  bool incr = precision == COX_FP64;
+  for (int i = 0; i < n && incr; ++i) {
+    const int eng = hs[i]->opts.engine;
+    incr = (eng == COX_ENGINE_AUTO || eng == COX_ENGINE_INCR) && hs[i]->sd->prep.inc_T > 0 && D(hs[i]).p > 0;
+  }
+  for (int i = 0; i < n && incr; ++i) {
+    std::string err;
+    const int rc = prepare_compact_incr(&hs[i]->sd->prep, precision, hs[0]->stream, &err);
+    if (rc) return fail(nullptr, rc, err);
+    incr = hs[i]->sd->prep.cinc_T > 0;
+  }
+  if (incr) return batch_incr(hs, n, beta0, beta_out, info);
   cox_handle *h0 = hs[0];
   cudaStream_t s = h0->stream;
   // per-fit init on the shared stream
@@ -966,6 +1109,8 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
         info[i].loglik = c.loglik;
         info[i].objective = c.obj;
         info[i].status = r;
+        info[i].engine = COX_ENGINE_STREAM;
+        info[i].step_launches = launched;
       }
       int r2 = copy_out(h, beta_out[i], h->hfit.beta, D(h).p);
       if (r2) r = r2;

@@ -225,7 +225,7 @@ static __device__ __forceinline__ dw inc_v(double eta, double shift, bool exitp,
 static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo, int npos, uint32_t *lp, dw *lv,
                                      double *le, int *cnt, int th0, int nth, int *serr) {
   const DevData &D = prm.D;
-  const int C = gridDim.x;
+  const int C = prm.T;
   const int64_t cb = D.col_ptr[j];
   const int32_t *ct = prm.col_tile + int64_t(j) * (C + 1);
   const int64_t qa = cb + ct[t];
@@ -432,7 +432,7 @@ static __device__ double inc_step_rule(double g1, double g2, double b, double *t
 }
 
 template <class P>
-__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams prm) {
+__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams *prms, const int2 *cta_map) {
   using T = typename P::T;
   using S = IncSmem;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
 
   __shared__ IncState st;
+  __shared__ IncParams prm;   // this CTA's fit (a launch may run several fits, each on its own CTAs)
   __shared__ int s_cnt[4];
   __shared__ dw s_agg[2][32];
   __shared__ int s_flg[2][32];
@@ -466,11 +467,19 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   __shared__ uint64_t s_pay[kIncRec];   // this CTA's record payloads (bits): G1, G2, LL, H1, R, I
   __shared__ double s_inv_var, s_half_inv_var;
 
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int2 me = cta_map[blockIdx.x];   // (fit, tile of that fit)
+  {
+    static_assert(sizeof(IncParams) % 4 == 0, "copied in words");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(prms + me.x);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&prm);
+    for (int w = tid; w < int(sizeof(IncParams) / 4); w += kIncThreads) dst[w] = src[w];
+  }
+  __syncthreads();
   const DevFit &F = prm.F;
   const DevData &D = prm.D;
   FitCtl *ctl = F.ctl;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int t = blockIdx.x, C = gridDim.x;
+  const int t = me.y, C = prm.T;
   const int lo = prm.tile_lo[t], hi = prm.tile_lo[t + 1], npos = hi - lo;
   const int ga = prm.tile_g[t], ng = prm.tile_g[t + 1] - ga;
   const int kc0 = prm.tile_k[t], nc = prm.tile_k[t + 1] - kc0;
@@ -1024,9 +1033,9 @@ static int inc_max_ctas() {
 
 int inc_max_grid(int precision) { return precision == COX_FP32C ? inc_max_ctas<PF32C>() : inc_max_ctas<PF64>(); }
 
-int launch_incr(int precision, const IncParams &prm, int grid, void *stream) {
+int launch_incr(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  void *args[] = {const_cast<IncParams *>(&prm)};
+  void *args[] = {const_cast<IncParams **>(&prms), const_cast<int2 **>(&cta_map)};
   if (grid <= 0 || grid > inc_max_grid(precision)) return COX_E_INVALID;
   count_launches(1);
   const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C>)

@@ -110,10 +110,12 @@ struct dw;   // double-word float (dw.cuh)
 // as double-words, LL in FP64), two 8-byte words each.
 constexpr int kIncRecWords = 12;
 
-// Arguments of the incremental kernel (ccd_incr.cu), passed by value.
+// One fit of the incremental kernel (ccd_incr.cu); a launch takes an array of these in device
+// memory and a map from each CTA to (fit, tile of that fit).
 struct IncParams {
   DevFit F;               // the fit (its d pointer is not used)
   DevData D;              // the data descriptor
+  int32_t T, pad_;        // tiles (CTAs) of this fit
   const int32_t *tile_lo, *tile_g, *tile_k, *col_tile;   // incremental tile plan: one tile per CTA
   uint64_t *trec;         // [2][C readers][C writers][kIncRecWords] epoch-tagged step records (each
                           // CTA writes its record into every CTA's inbox), double-buffered by parity
@@ -151,6 +153,6 @@ int inc_group_cap();
 int inc_list_cap();
 int inc_pos_cap();
 int inc_max_grid(int precision);
-int launch_incr(int precision, const IncParams &prm, int grid, void *stream);
+int launch_incr(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream);
 
 }  // namespace coxgb

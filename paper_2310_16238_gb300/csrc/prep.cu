@@ -590,6 +590,86 @@ static std::vector<int32_t> plan_tiles(int64_t M, int tile, const std::vector<in
   return lo;
 }
 
+// Device tables of a one-tile-per-CTA plan: first tie group and first stratum end of every tile,
+// and every column's first entry in every tile.
+static int build_tile_tables(BufferSet &B, cudaStream_t s, const DevData &D, const std::vector<int32_t> &rl, int32_t **lo_out,
+                             int32_t **g_out, int32_t **k_out, int32_t **ct_out) {
+  const int32_t RT = int32_t(rl.size()) - 1;
+  const int32_t p = D.p;
+  int32_t *r_lo = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+  int32_t *r_g = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+  int32_t *r_k = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
+  int32_t *r_ct = static_cast<int32_t *>(B.get(std::max<int64_t>(int64_t(p) * (RT + 1), 1) * sizeof(int32_t)));
+  if (!r_lo || !r_g || !r_k || !r_ct) return COX_E_OOM;
+  cudaMemcpyAsync(r_lo, rl.data(), (RT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  count_launches(1);
+  tile_tables_kernel<<<grid_for(int64_t(RT) + 1), 256, 0, s>>>(RT, r_lo, D.head_pos, D.G, D.cut_pos, D.K, r_g, r_k);
+  if (p > 0) {
+    count_launches(1);
+    col_tile_kernel<<<grid_for(int64_t(p) * (RT + 1)), 256, 0, s>>>(p, RT, D.col_ptr, D.idx, r_lo, r_ct);
+  }
+  *lo_out = r_lo;
+  *g_out = r_g;
+  *k_out = r_k;
+  *ct_out = r_ct;
+  return COX_OK;
+}
+
+// Whether every column's entries in every tile of a plan fit the incremental kernel's lists.
+static int lists_fit(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, bool *fits) {
+  std::vector<int32_t> hct(size_t(D.p) * (T + 1));
+  if (!hct.empty() && (cudaMemcpyAsync(hct.data(), ct, hct.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess))
+    return COX_E_CUDA;
+  *fits = true;
+  for (int32_t j = 0; j < D.p && *fits; ++j)
+    for (int32_t t = 0; t < T; ++t)
+      if (hct[size_t(j) * (T + 1) + t + 1] - hct[size_t(j) * (T + 1) + t] > inc_list_cap()) {
+        *fits = false;
+        break;
+      }
+  return COX_OK;
+}
+
+int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string *err) {
+  if (P->cinc_T != 0) return COX_OK;
+  P->cinc_T = -1;
+  const DevData &D = P->desc;
+  const int grid = inc_max_grid(precision);
+  if (P->inc_T <= 0 || grid <= 0) return COX_OK;
+  std::vector<int32_t> h_head(size_t(D.G));
+  if (D.G > 0 && (cudaMemcpyAsync(h_head.data(), D.head_pos, size_t(D.G) * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+                      cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess)) {
+    *err = "cox_batch_fit: plan tables";
+    return COX_E_CUDA;
+  }
+  // as many tie groups per tile as a CTA holds, tiles shorter than the run of positions that
+  // would overflow a column's list (shortened further if a list still overflows)
+  for (int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(P->inc_wmin) - 1); pos_cap >= 32; pos_cap /= 2) {
+    std::vector<int32_t> rl = group_tiles(D.M, inc_group_cap(), pos_cap, h_head);
+    const int32_t T = int32_t(rl.size()) - 1;
+    if (T > grid) return COX_OK;
+    int32_t *lo = nullptr, *g = nullptr, *k = nullptr, *ct = nullptr;
+    int rc = build_tile_tables(P->bufs, s, D, rl, &lo, &g, &k, &ct);
+    if (rc) return rc;
+    bool fits = false;
+    if ((rc = lists_fit(D, ct, T, s, &fits))) {
+      *err = "cox_batch_fit: plan tables";
+      return rc;
+    }
+    if (fits) {
+      P->cinc_T = T;
+      P->cinc_tile_lo = lo;
+      P->cinc_tile_g = g;
+      P->cinc_tile_k = k;
+      P->cinc_col_tile = ct;
+      return COX_OK;
+    }
+  }
+  return COX_OK;
+}
+
 int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err) {
   Scratch sc;   // temporaries, freed on return
   const int64_t n = in->n_rows;
@@ -847,24 +927,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
 
   // one-tile-per-CTA plans of the resident and incremental kernels (binary X only)
   auto tables = [&](const std::vector<int32_t> &rl, int32_t **lo_out, int32_t **g_out, int32_t **k_out,
-                    int32_t **ct_out) -> int {
-    const int32_t RT = int32_t(rl.size()) - 1;
-    int32_t *r_lo = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-    int32_t *r_g = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-    int32_t *r_k = static_cast<int32_t *>(B.get((RT + 1) * sizeof(int32_t)));
-    int32_t *r_ct = static_cast<int32_t *>(B.get(int64_t(p) * (RT + 1) * sizeof(int32_t)));
-    if (!r_lo || !r_g || !r_k || !r_ct) return COX_E_OOM;
-    cudaMemcpyAsync(r_lo, rl.data(), (RT + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    count_launches(1);
-    tile_tables_kernel<<<grid_for(int64_t(RT) + 1), 256, 0, s>>>(RT, r_lo, head_pos, int32_t(G), cut_pos, int32_t(K), r_g, r_k);
-    count_launches(1);
-    col_tile_kernel<<<grid_for(int64_t(p) * (RT + 1)), 256, 0, s>>>(p, RT, col_ptr, idx, r_lo, r_ct);
-    *lo_out = r_lo;
-    *g_out = r_g;
-    *k_out = r_k;
-    *ct_out = r_ct;
-    return COX_OK;
-  };
+                    int32_t **ct_out) -> int { return build_tile_tables(B, s, D, rl, lo_out, g_out, k_out, ct_out); };
   if (in->val == nullptr && p > 0 && D.M > 0) {
     const int res_grid = res_max_grid(precision);
     if (res_grid > 0) {
@@ -892,6 +955,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
           return COX_E_CUDA;
         }
       }
+      out->inc_wmin = wmin;
       const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(wmin) - 1);
       std::vector<std::vector<int32_t>> cands;
       if (pos_cap >= 32) cands.push_back(group_plan(D.M, pos_cap, inc_group_cap(), inc_grid, h_head));
@@ -901,19 +965,11 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         int32_t *ilo = nullptr, *ig = nullptr, *ik = nullptr, *ict = nullptr;
         if ((rc = tables(il, &ilo, &ig, &ik, &ict))) return rc;
         const int32_t IT = int32_t(il.size()) - 1;
-        std::vector<int32_t> hct(size_t(p) * (IT + 1));
-        if (cudaMemcpyAsync(hct.data(), ict, hct.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
+        bool fits = false;
+        if ((rc = lists_fit(D, ict, IT, s, &fits))) {
           *err = "cox_create: table kernels failed";
-          return COX_E_CUDA;
+          return rc;
         }
-        bool fits = true;
-        for (int32_t j = 0; j < p && fits; ++j)
-          for (int32_t t = 0; t < IT; ++t)
-            if (hct[size_t(j) * (IT + 1) + t + 1] - hct[size_t(j) * (IT + 1) + t] > inc_list_cap()) {
-              fits = false;
-              break;
-            }
         if (fits) {
           out->inc_T = IT;
           out->inc_tile_lo = ilo;

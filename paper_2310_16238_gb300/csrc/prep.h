@@ -48,10 +48,16 @@ struct Prepared {
   // incremental plan (one tile per CTA of the incremental kernel); inc_T == 0 when not eligible
   int32_t inc_T = 0;
   int32_t *inc_tile_lo = nullptr, *inc_tile_g = nullptr, *inc_tile_k = nullptr, *inc_col_tile = nullptr;
+  int32_t inc_wmin = 0x7fffffff;        // shortest run of positions overflowing a column's list
+  // compact incremental plan (fewest tiles; batches), built on first use: 0 = not yet, -1 = none
+  int32_t cinc_T = 0;
+  int32_t *cinc_tile_lo = nullptr, *cinc_tile_g = nullptr, *cinc_tile_k = nullptr, *cinc_col_tile = nullptr;
   int32_t *g_time = nullptr;            // [G] device
   int32_t *g_stratum = nullptr;         // [G] device
 };
 
 int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err);
+// Build (once) the incremental kernel's compact plan of a prepared data set (fewest tiles).
+int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string *err);
 
 }  // namespace coxgb

@@ -97,3 +97,38 @@ def test_incr_is_deterministic_and_matches_streaming():
     with cox.Handle(data, opts, engine=cox.COX_ENGINE_STREAM) as h:
         b3, i3 = h.fit()
     assert i3["sweeps"] == i1["sweeps"] and _rel(b1, b3) <= 1e-10
+
+
+def test_incr_batch_waves_match_oracle():
+    """A batch on the incremental kernel: each fit on its own compact plan, fits packed into
+    waves of at most one CTA per SM (this batch needs more than one wave), warm starts included."""
+    sets = []
+    d1, _ = synth.stratified_sparse(n=150000, p=10, k=6, n_support=5, event_frac=0.1, dens_lo=0.005, dens_hi=0.2,
+                                    admin_days=2000, seed=71)
+    sets += [(d1, synth.CoxOptions(penalty=synth.PEN_L1, lam=lam, tol=1e-10)) for lam in np.geomspace(5.0, 500.0, 24)]
+    d2, o2 = synth.time_varying(n_subj=8000, p=8, k=3, density=0.05, event_frac=0.3, n_support=4, seed=72)
+    sets += [(d2, synth.CoxOptions(penalty=synth.PEN_L2, l2_var=v, tol=1e-10)) for v in (0.1, 1.0, 10.0)]
+    d3, _ = synth.stratified_sparse(n=3000, p=5, k=40, n_support=3, event_frac=0.4, dens_lo=0.05, dens_hi=0.5,
+                                    admin_days=50, seed=73)
+    sets += [(d3, synth.CoxOptions(penalty=synth.PEN_L1, lam=1.0, tol=1e-10))]
+    handles, by_data = [], {}
+    for d, o in sets:
+        if id(d) in by_data:
+            handles.append(by_data[id(d)].clone(o))
+        else:
+            h = cox.Handle(d, o)
+            by_data[id(d)] = h
+            handles.append(h)
+    b0 = [None] * len(sets)
+    b0[-1] = random_beta(sets[-1][0].p, 0.05, seed=2)
+    betas, infos = cox.batch_fit(handles, [np.zeros(d.p) if b is None else b for (d, _), b in zip(sets, b0)])
+    try:
+        for (d, o), b, beta, info in zip(sets, b0, betas, infos):
+            assert info["engine"] == cox.COX_ENGINE_INCR and info["step_launches"] == 1
+            ob, oinfo = oracle.fit(d, o, beta0=b, max_sweeps=info["sweeps"])
+            assert info["sweeps"] == oinfo["sweeps"] or not oinfo["converged"]
+            assert _rel(beta, ob) <= 1e-9, _rel(beta, ob)
+            assert abs(info["loglik"] - oinfo["loglik"]) <= 1e-11 * _ll_scale(d, ob, oinfo["loglik"])
+    finally:
+        for h in handles:
+            h.close()

@@ -77,8 +77,6 @@ struct cox_handle {
   uint64_t *i_trec = nullptr, *i_tref = nullptr;
   double *i_bcopy = nullptr;
   dw *i_vdw = nullptr;
-  IncParams *i_prm = nullptr;   // device copy of the fit's kernel arguments
-  int2 *i_map = nullptr;        // CTA -> (fit 0, tile)
   std::string err = "no error";
 };
 
@@ -170,14 +168,8 @@ int alloc_fit_state(cox_handle *h) {
     h->i_tref = static_cast<uint64_t *>(B.get(4 * int64_t(IT) * sizeof(uint64_t)));
     h->i_bcopy = static_cast<double *>(B.get(std::max<int64_t>(2 * p * IT, 1) * sizeof(double)));
     h->i_vdw = static_cast<dw *>(B.get(std::max<int64_t>(M, 1) * 2 * sizeof(float)));
-    h->i_prm = static_cast<IncParams *>(B.get(sizeof(IncParams)));
-    h->i_map = static_cast<int2 *>(B.get(int64_t(IT) * sizeof(int2)));
-    if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw || !h->i_prm || !h->i_map)
+    if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw)
       return fail(h, COX_E_OOM, "device allocation failed for the incremental state");
-    std::vector<int2> map(static_cast<size_t>(IT));
-    for (int t = 0; t < IT; ++t) map[t] = make_int2(0, t);
-    if (cudaMemcpyAsync(h->i_map, map.data(), IT * sizeof(int2), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-      return cuda_fail(h, "map copy");
   }
   if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
@@ -538,7 +530,8 @@ int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, dou
                 cudaMemcpyAsync(dmap + w * grid, hm.data() + w * grid, cta * sizeof(int2), cudaMemcpyHostToDevice, s) !=
                     cudaSuccess))
       rc = cuda_fail(nullptr, "params copy");
-    if (!rc && launch_incr(precision, dprm + off, dmap + w * grid, cta, s)) rc = cuda_fail(nullptr, "incremental launch");
+    if (!rc && launch_incr_multi(precision, dprm + off, dmap + w * grid, cta, s))
+      rc = cuda_fail(nullptr, "incremental launch");
     if (!rc) cudaEventRecord(ev[w + 1], s);
     off += int(waves[w].size());
   }
@@ -605,10 +598,8 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   }
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
-  if (cudaMemcpyAsync(h->i_prm, &prm, sizeof(IncParams), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return cuda_fail(h, "params copy");
   cudaEventRecord(h->ev0, s);
-  if (launch_incr(h->sd->precision, h->i_prm, h->i_map, IT, s)) return cuda_fail(h, "incremental launch");
+  if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
   cudaEventRecord(h->ev1, s);
   int rc;
   if ((rc = read_ctl(h))) return rc;

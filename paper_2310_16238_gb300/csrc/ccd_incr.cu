@@ -431,8 +431,10 @@ static __device__ double inc_step_rule(double g1, double g2, double b, double *t
   return s;
 }
 
+// The kernel body: CTA `t` of the fit described by `prm` (kernel parameters for a single fit,
+// shared memory when one launch runs several fits).
 template <class P>
-__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams *prms, const int2 *cta_map) {
+static __device__ __forceinline__ void incr_body(const IncParams &prm, const int t) {
   using T = typename P::T;
   using S = IncSmem;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -451,7 +453,6 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
 
   __shared__ IncState st;
-  __shared__ IncParams prm;   // this CTA's fit (a launch may run several fits, each on its own CTAs)
   __shared__ int s_cnt[4];
   __shared__ dw s_agg[2][32];
   __shared__ int s_flg[2][32];
@@ -468,18 +469,10 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   __shared__ double s_inv_var, s_half_inv_var;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int2 me = cta_map[blockIdx.x];   // (fit, tile of that fit)
-  {
-    static_assert(sizeof(IncParams) % 4 == 0, "copied in words");
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(prms + me.x);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(&prm);
-    for (int w = tid; w < int(sizeof(IncParams) / 4); w += kIncThreads) dst[w] = src[w];
-  }
-  __syncthreads();
   const DevFit &F = prm.F;
   const DevData &D = prm.D;
   FitCtl *ctl = F.ctl;
-  const int t = me.y, C = prm.T;
+  const int C = prm.T;
   const int lo = prm.tile_lo[t], hi = prm.tile_lo[t + 1], npos = hi - lo;
   const int ga = prm.tile_g[t], ng = prm.tile_g[t + 1] - ga;
   const int kc0 = prm.tile_k[t], nc = prm.tile_k[t + 1] - kc0;
@@ -1010,36 +1003,74 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParam
   }
 }
 
+// One fit over the whole grid: its arguments stay in the kernel-parameter space.
 template <class P>
-static int inc_max_ctas() {
-  static int cached = -2;
-  if (cached != -2) return cached;
+__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams prm) {
+  incr_body<P>(prm, int(blockIdx.x));
+}
+
+// Several fits per launch: CTA b runs tile cta_map[b].y of fit cta_map[b].x, whose arguments it
+// copies into shared memory.
+template <class P>
+__global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_multi_kernel(const IncParams *prms, const int2 *cta_map) {
+  __shared__ IncParams sp;
+  const int2 me = cta_map[blockIdx.x];
+  static_assert(sizeof(IncParams) % 4 == 0, "copied in words");
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(prms + me.x);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+  for (int w = int(threadIdx.x); w < int(sizeof(IncParams) / 4); w += kIncThreads) dst[w] = src[w];
+  __syncthreads();
+  incr_body<P>(sp, me.y);
+}
+
+template <class K>
+static int inc_max_ctas_of(K kernel) {
   const size_t sm = IncSmem::bytes;
-  if (cudaFuncSetAttribute(ccd_incr_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) {
     cudaGetLastError();
-    return cached = 0;
+    return 0;
   }
   int per_sm = 0, dev = 0, nsm = 0, coop = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ccd_incr_kernel<P>, kIncThreads, sm) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kIncThreads, sm) != cudaSuccess) {
     cudaGetLastError();
-    return cached = 0;
+    return 0;
   }
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   const int g = coop ? per_sm * nsm : 0;
-  return cached = g < kIncMaxCtas ? g : kIncMaxCtas;
+  return g < kIncMaxCtas ? g : kIncMaxCtas;
+}
+
+// the largest cooperative grid of both entry points (the smaller of the two)
+template <class P>
+static int inc_max_ctas() {
+  static int cached = -2;
+  if (cached != -2) return cached;
+  const int a = inc_max_ctas_of(ccd_incr_kernel<P>), b = inc_max_ctas_of(ccd_incr_multi_kernel<P>);
+  return cached = a < b ? a : b;
 }
 
 int inc_max_grid(int precision) { return precision == COX_FP32C ? inc_max_ctas<PF32C>() : inc_max_ctas<PF64>(); }
 
-int launch_incr(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream) {
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void *args[] = {const_cast<IncParams *>(&prm)};
+  if (grid <= 0 || grid > inc_max_grid(precision) || grid != prm.T) return COX_E_INVALID;
+  count_launches(1);
+  const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C>)
+                                          : reinterpret_cast<const void *>(ccd_incr_kernel<PF64>);
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
+  return e == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+int launch_incr_multi(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void *args[] = {const_cast<IncParams **>(&prms), const_cast<int2 **>(&cta_map)};
   if (grid <= 0 || grid > inc_max_grid(precision)) return COX_E_INVALID;
   count_launches(1);
-  const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C>)
-                                          : reinterpret_cast<const void *>(ccd_incr_kernel<PF64>);
+  const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_multi_kernel<PF32C>)
+                                          : reinterpret_cast<const void *>(ccd_incr_multi_kernel<PF64>);
   const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
   return e == cudaSuccess ? COX_OK : COX_E_CUDA;
 }

@@ -110,8 +110,8 @@ struct dw;   // double-word float (dw.cuh)
 // as double-words, LL in FP64), two 8-byte words each.
 constexpr int kIncRecWords = 12;
 
-// One fit of the incremental kernel (ccd_incr.cu); a launch takes an array of these in device
-// memory and a map from each CTA to (fit, tile of that fit).
+// One fit of the incremental kernel (ccd_incr.cu): passed by value for a single fit, or as a
+// device array with a map from each CTA to (fit, tile of that fit) when one launch runs several.
 struct IncParams {
   DevFit F;               // the fit (its d pointer is not used)
   DevData D;              // the data descriptor
@@ -153,6 +153,7 @@ int inc_group_cap();
 int inc_list_cap();
 int inc_pos_cap();
 int inc_max_grid(int precision);
-int launch_incr(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream);
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream);
+int launch_incr_multi(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream);
 
 }  // namespace coxgb

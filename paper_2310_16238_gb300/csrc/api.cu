@@ -604,14 +604,14 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   int rc;
   if ((rc = read_ctl(h))) return rc;
   if (prm.trace_steps > 0) {
-    // mean time between consecutive timestamps of thread 0 per CTA (update | patch | scan | scan
-    // barrier | S0 | ratios | group sums | barrier | CTA sums | barrier | push | inbox | barrier |
-    // record sums | step) and the publish time after the earliest step start, for the slowest
-    // CTAs and the fastest
+    // per CTA, mean SM clocks between consecutive phase points of thread 0 (update | patch | scan
+    // | barrier | S0 | ratios | group sums | barrier | CTA sums | barrier | push | inbox | barrier
+    // | record sums | step) and the global time of its push after the earliest step start, for the
+    // three CTAs that push last and the one that pushes first
     constexpr int kSl = 24, kPh = 15;
     std::vector<uint64_t> tr(size_t(prm.trace_steps * IT * kSl));
     cudaMemcpy(tr.data(), prm.trace, tr.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    std::vector<double> pub(IT, 0.0), ph(kPh * IT, 0.0), tot(IT, 0.0), ex(4 * IT, 0.0), clk(IT, 0.0);
+    std::vector<double> pub(IT, 0.0), ph(kPh * IT, 0.0), tot(IT, 0.0), ex(4 * IT, 0.0);
     int64_t n = 0;
     for (int64_t k = 1; k < prm.trace_steps; ++k) {
       uint64_t t0 = ~0ull;
@@ -619,36 +619,36 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
       for (int c = 0; c < IT; ++c) {
         const uint64_t *r = &tr[size_t((k * IT + c) * kSl)];
         for (int q = 0; q < 16; ++q) ok = ok && r[q] != 0;
-        t0 = std::min(t0, r[0]);
+        ok = ok && r[19] != 0 && r[21] != 0;
+        t0 = std::min(t0, r[21]);
       }
       if (!ok) continue;
       for (int c = 0; c < IT; ++c) {
         const uint64_t *r = &tr[size_t((k * IT + c) * kSl)];
-        pub[c] += double(r[11] - t0);
+        pub[c] += double(r[19] - t0);
         tot[c] += double(r[15] - r[0]);
         for (int q = 0; q < kPh; ++q) ph[kPh * c + q] += double(r[q + 1] - r[q]);
-        ex[4 * c + 0] += double(r[16] - r[13]);   // warp 0's record sums before the barrier
+        ex[4 * c + 0] += double(r[16] - r[13]);   // warp 0's share of the record sums
         ex[4 * c + 1] += double(r[18] - r[17]);   // the step rule
         ex[4 * c + 2] += double(r[15] - r[18]);   // exp and bookkeeping after the rule
         ex[4 * c + 3] += double(r[20]);           // polls of thread 0's inbox wait
-        clk[c] += double(r[22] - r[23]);           // SM clocks over the whole step
       }
       ++n;
     }
     std::vector<int> order(IT);
     for (int c = 0; c < IT; ++c) order[c] = c;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return pub[a] > pub[b]; });
-    std::fprintf(stderr, "[phase trace] incremental kernel, %lld steps x %d CTAs (ns): publish-after-first-start | "
-                 "upd patch scan bar S0 ratio gsum bar csum bar push inbox bar rsum step | total\n", (long long)n, IT);
+    std::fprintf(stderr, "[phase trace] incremental kernel, %lld steps x %d CTAs: push time after the earliest step start "
+                 "(ns) | SM clocks: upd patch scan bar S0 ratio gsum bar csum bar push inbox bar rsum step | total\n",
+                 (long long)n, IT);
     auto row = [&](const char *tag, int c) {
       std::fprintf(stderr, "  %s CTA %3d: %6.0f |", tag, c, pub[c] / n);
-      for (int q = 0; q < kPh; ++q) std::fprintf(stderr, " %4.0f", ph[kPh * c + q] / n);
-      std::fprintf(stderr, " | %6.0f (%5.0f SM clocks, %.2f GHz) | rsum-own %4.0f rule %4.0f exp+ %4.0f polls %4.1f\n",
-                   tot[c] / n, clk[c] / n, clk[c] / tot[c], ex[4 * c] / n, ex[4 * c + 1] / n, ex[4 * c + 2] / n,
-                   ex[4 * c + 3] / n);
+      for (int q = 0; q < kPh; ++q) std::fprintf(stderr, " %5.0f", ph[kPh * c + q] / n);
+      std::fprintf(stderr, " | %6.0f | rsum-own %5.0f rule %5.0f exp+ %5.0f polls %4.1f\n", tot[c] / n, ex[4 * c] / n,
+                   ex[4 * c + 1] / n, ex[4 * c + 2] / n, ex[4 * c + 3] / n);
     };
-    for (int q = 0; q < std::min(IT, 3) && n; ++q) row("slow", order[q]);
-    if (n) row("fast", order[IT - 1]);
+    for (int q = 0; q < std::min(IT, 3) && n; ++q) row("last ", order[q]);
+    if (n) row("first", order[IT - 1]);
   }
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);

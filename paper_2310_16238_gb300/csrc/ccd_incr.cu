@@ -66,8 +66,22 @@ struct IncSmem {
   static constexpr size_t o_gseen = o_gs0 + 8 * kIncGroupCap;           // u8  [gcap]
   static constexpr size_t o_rec = inc_al16(o_gseen + kIncGroupCap);     // 8-byte slots [6][C] record payloads
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
-  static constexpr size_t bytes = o_rref + 8 * 2 * kIncMaxCtas;
+  static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;          // GroupSlot [gcap]
+  static constexpr size_t bytes = o_grp + 24 * kIncGroupCap;
 };
+
+// One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
+// to the tile), events, stratum segment within the tile, and whether the later tiles' carry
+// reaches it. Kept in shared memory rather than registers: the step loop is register-bound at
+// 1024 threads, and spilled registers would go to memory.
+struct GroupSlot {
+  dw S0;
+  int32_t q;
+  float d;
+  int32_t seg;
+  int32_t tail;
+};
+static_assert(sizeof(GroupSlot) == 24, "group slot layout");
 
 int inc_group_cap() { return kIncGroupCap; }
 int inc_list_cap() { return kIncListCap; }
@@ -433,7 +447,7 @@ static __device__ double inc_step_rule(double g1, double g2, double b, double *t
 
 // The kernel body: CTA `t` of the fit described by `prm` (kernel parameters for a single fit,
 // shared memory when one launch runs several fits).
-template <class P>
+template <class P, bool kTrace>
 static __device__ __forceinline__ void incr_body(const IncParams &prm, const int t) {
   using T = typename P::T;
   using S = IncSmem;
@@ -451,6 +465,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   uint8_t *gseen = reinterpret_cast<uint8_t *>(smem + S::o_gseen);
   uint64_t *srec = reinterpret_cast<uint64_t *>(smem + S::o_rec);
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
+  GroupSlot *grp = reinterpret_cast<GroupSlot *>(smem + S::o_grp);
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -465,6 +480,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   __shared__ dw s_dagg[32], s_dcar[32];   // dense scan: warp aggregates, carries into warps
   __shared__ int s_dflg[32];
   __shared__ int s_chain_end, s_bad, s_err, s_anyerr;
+  __shared__ int s_ce[kIncMaxCtas];   // chain end of every CTA of the fit
   __shared__ uint64_t s_pay[kIncRec];   // this CTA's record payloads (bits): G1, G2, LL, H1, R, I
   __shared__ double s_inv_var, s_half_inv_var;
 
@@ -514,15 +530,15 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     tru[jj] = F.trust[jj];
   }
   __syncthreads();
-  int qg = 0;
-  float dg = 0.0f;   // events of this thread's tie group (exact in float below 2^24)
   if (tid < ng) {
-    qg = D.head_pos[ga + tid] - lo;
-    dg = float(D.head_d[ga + tid]);
+    int qg = D.head_pos[ga + tid] - lo;
     if (qg < 0 || qg >= npos) {
       atomicCAS(&s_err, 0, COX_E_INVALID);
       qg = 0;
     }
+    grp[tid].q = qg;
+    grp[tid].d = float(D.head_d[ga + tid]);   // events of the group (exact in float below 2^24)
+    grp[tid].S0 = dw_make(0.0f);
     atomicOr(&headb[qg >> 5], 1u << (qg & 31));
   }
   for (int k = tid; k < nc; k += kIncThreads) {
@@ -584,20 +600,23 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   }
   // chain end of CTA tid (thread tid pushes this CTA's record into CTA tid's inbox: the head sums
   // H1, R, I go only to CTAs whose last stratum continues into this tile)
-  int ce_of_tid = -1;
   if (tid < C) {
     const int k1 = prm.tile_k[tid + 1];
     const bool lc = k1 > prm.tile_k[tid] && D.cut_pos[k1 - 1] == prm.tile_lo[tid + 1] - 1;
-    ce_of_tid = tid;
+    int ce = tid;
     if (!lc)
       for (int c = tid + 1; c < C; ++c) {
-        ce_of_tid = c;
+        ce = c;
         if (prm.tile_k[c + 1] > prm.tile_k[c]) break;
       }
+    s_ce[tid] = ce;
   }
   __syncthreads();
-  const int segg = tid < ng ? inc_rank(cutb, cutp, qg) : 0;
-  const bool tailg = tid < ng && segg == nc;
+  if (tid < ng) {
+    const int seg = inc_rank(cutb, cutp, grp[tid].q);
+    grp[tid].seg = seg;
+    grp[tid].tail = seg == nc;
+  }
   const int RW = max(32, ((npos + 1023) / 1024) * 32);   // positions per warp in the dense scan
   const double inv_var = s_inv_var, half_inv_var = s_half_inv_var;
   // list slots: previous column (pending update), current, next, and the one being fetched
@@ -614,13 +633,11 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
                   kIncThreads, &s_err);
   }
   __syncthreads();
-  dw S0 = dw_make(0.0f);   // this thread's tie group's risk-set sum, kept across steps
   bool refreshed = false;  // the last step taken rebuilt v from eta
 
   for (int64_t step = 0; step < prm.max_steps && st.state == kRunning; ++step) {
     const int j = st.j, pj = st.pend_j;
     const double db = st.pend_db;
-    const dw E = st.E;
     const bool need_ll = st.need_ll != 0;
     const bool refresh = need_ll || step == 0;
     const uint32_t epoch = st.epoch;
@@ -629,8 +646,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     dw *lv_p = lv + sp * kIncListCap, *lv_c = lv + sc * kIncListCap, *lv_n = lv + sn * kIncListCap;
     double *le_p = le + sp * kIncListCap, *le_c = le + sc * kIncListCap, *le_n = le + sn * kIncListCap;
     const int np = pj >= 0 ? s_cnt[sp] : 0, ncur = s_cnt[sc], nnx = s_cnt[sn];
-    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * kIncTraceSlots : nullptr;
-    if (trace) { trace[0] = inc_timer(); trace[23] = uint64_t(clock64()); }
+    uint64_t *trace =
+        (kTrace && prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * kIncTraceSlots : nullptr;
+    if (trace) { trace[0] = uint64_t(clock64()); trace[21] = inc_timer(); }
     // this coordinate's inputs to the step, loaded now so their latency overlaps the step
     double pre_dx = 0.0, pre_b = 0.0, pre_tr = 0.0;
     int pre_pen = 1;
@@ -650,7 +668,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const int q = int(e & kPosMask);
       const double et = __dadd_rn(le_p[tid], db);
       if (!(fabs(et - shift) <= kIncRange)) atomicCAS(&s_err, 0, COX_E_RANGE);
-      dd = dw_mul(lv_p[tid], E);
+      dd = dw_mul(lv_p[tid], st.E);
       const dw nv = dw_add(lv_p[tid], dd);
       prm.vdw[lo + q] = nv;
       F.eta[lo + q] = et;
@@ -659,7 +677,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       fp = tid + 1 >= np || inc_rank(cutb, cutp, int(lp_p[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
     }
     __syncthreads();
-    if (trace) trace[1] = inc_timer();
+    if (trace) trace[1] = uint64_t(clock64());
     // ---- 2. a sweep start rebuilds v and S0 from eta; otherwise the current and next lists
     //         take the update at the entries they share with the previous column
     dw HA0 = dw_make(0.0f);
@@ -701,17 +719,15 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       x1 = lv_c[tid];
       fc = tid + 1 >= ncur || inc_rank(cutb, cutp, int(lp_c[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
     }
-    const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : -1;
-    const dw vnx = tid < nnx ? lv_n[tid] : dw_make(0.0f);
     // ---- 3. segmented suffix sums of dD (previous column) and v (current column)
-    if (trace) trace[2] = inc_timer();
+    if (trace) trace[2] = uint64_t(clock64());
     inc_seg_suffix2(refresh ? dw_make(0.0f) : dd, refresh ? 1 : fp, x1, fc, refresh ? ncur : max(np, ncur), u0, u1, s_agg,
                     s_flg);
-    if (trace) trace[3] = inc_timer();
+    if (trace) trace[3] = uint64_t(clock64());
     __syncthreads();
     // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
-    const dw H1 = (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? u1[0] : dw_make(0.0f);
-    if (trace) trace[4] = inc_timer();
+    auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? u1[0] : dw_make(0.0f); };
+    if (trace) trace[4] = uint64_t(clock64());
     dw C1;
     if (refresh) {
       // ---- carries of the rebuilt S0 and of S1 from one exchange of the tiles' head sums
@@ -719,7 +735,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       if (tid == 0) {
         uint64_t *w = prm.tref + 4 * int64_t(t);
         put_dw(w, tag, HA0);
-        put_dw(w + 2, tag, H1);
+        put_dw(w + 2, tag, head1());
       }
       if (tid < C) {
         uint64_t r[2] = {0, 0};
@@ -740,21 +756,33 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       }
       __syncthreads();
       if (tid < ng) {
-        S0 = gs0[tid];
-        if (!gseen[tid]) S0 = dw_add(S0, s_dcar[qg / RW]);
-        if (tailg) S0 = dw_add(S0, s_carry[0]);
+        dw S0 = gs0[tid];
+        if (!gseen[tid]) S0 = dw_add(S0, s_dcar[grp[tid].q / RW]);
+        if (grp[tid].tail) S0 = dw_add(S0, s_carry[0]);
+        grp[tid].S0 = S0;
       }
       C1 = s_carry[1];
     } else {
       // ---- S0 += the suffix of dD from the read position, and the later tiles' change
-      if (tid < ng && np > 0) {
-        const int k = inc_lower_bound(lp_p, np, qg);
-        if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == segg) S0 = dw_add(S0, u0[k]);
+      if (tid < ng) {
+        dw S0 = grp[tid].S0;
+        bool upd = false;
+        if (np > 0) {
+          const int k = inc_lower_bound(lp_p, np, grp[tid].q);
+          if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == grp[tid].seg) {
+            S0 = dw_add(S0, u0[k]);
+            upd = true;
+          }
+        }
+        if (grp[tid].tail && !dw_is_zero(st.E)) {
+          S0 = dw_add(S0, dw_mul(st.E, s_chain[0]));
+          upd = true;
+        }
+        if (upd) grp[tid].S0 = S0;
       }
-      if (tailg && !dw_is_zero(E)) S0 = dw_add(S0, dw_mul(E, s_chain[0]));
-      C1 = dw_add(s_chain[1], dw_mul(E, s_chain[2]));
+      C1 = dw_add(s_chain[1], dw_mul(st.E, s_chain[2]));
     }
-    if (trace) trace[5] = inc_timer();
+    if (trace) trace[5] = uint64_t(clock64());
     // ---- 4. tie-group ratios (warps holding groups); the next column's head-segment sums R,
     //         and I over the entries this step's update may change (warps holding its entries)
     const bool gwarp = warp * 32 < ng, nwarp = warp * 32 < nnx;   // warp-uniform
@@ -762,20 +790,21 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     double r_ll = 0.0;
     if (gwarp) {
       if (tid < ng) {
+        const GroupSlot g = grp[tid];
         dw s1 = dw_make(0.0f);
         if (ncur > 0) {
-          const int k = inc_lower_bound(lp_c, ncur, qg);
-          if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == segg) s1 = u1[k];
+          const int k = inc_lower_bound(lp_c, ncur, g.q);
+          if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = u1[k];
         }
-        if (tailg) s1 = dw_add(s1, C1);
+        if (g.tail) s1 = dw_add(s1, C1);
         if (!dw_is_zero(s1)) {
-          const dw r = dw_div(s1, S0);
-          r_g1 = dw_mul_f(r, dg);
+          const dw r = dw_div(s1, g.S0);
+          r_g1 = dw_mul_f(r, g.d);
           r_g2 = dw_mul(r_g1, dw_sub(dw_make(1.0f), r));
         }
-        if (need_ll) r_ll = double(dg) * log(dw_to(S0));
+        if (need_ll) r_ll = double(g.d) * log(dw_to(g.S0));
       }
-      if (trace) trace[6] = inc_timer();
+      if (trace) trace[6] = uint64_t(clock64());
 #pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) {
         r_g1 = dw_add_same(r_g1, dw_shfl_down(r_g1, off));
@@ -785,9 +814,11 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 #pragma unroll 1
         for (int off = 16; off > 0; off >>= 1) r_ll += __shfl_down_sync(kFull, r_ll, off);
     }
-    if (trace && !gwarp) trace[6] = inc_timer();
+    if (trace && !gwarp) trace[6] = uint64_t(clock64());
     if (nwarp) {
+      const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : 0;
       if (tid < nnx && inc_rank(cutb, cutp, qnx) == 0) {
+        const dw vnx = lv_n[tid];
         r_R = vnx;
         if (ncur > 0) {
           const int k = inc_lower_bound(lp_c, ncur, qnx);
@@ -809,9 +840,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       s_red[3][warp] = r_I;
       s_rll[warp] = r_ll;
     }
-    if (trace) trace[7] = inc_timer();
+    if (trace) trace[7] = uint64_t(clock64());
     __syncthreads();
-    if (trace) trace[8] = inc_timer();
+    if (trace) trace[8] = uint64_t(clock64());
     // ---- one value per warp: sums of the warp partials (G1, G2, R, I as double-words, LL in
     //      FP64), then this CTA's record, pushed into every CTA's inbox by thread r for reader r:
     //      (G1, G2[, LL]) to every CTA, and (H1, R, I) as well to the CTAs whose chain holds this tile
@@ -825,7 +856,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       else
         for (int off = 1; off < nv; off <<= 1) a = dw_add(a, dw_shfl_down(a, off));
       if (lane == 0) s_pay[warp < 2 ? warp : warp + 1] = *reinterpret_cast<const uint64_t *>(&a);   // 0 G1, 1 G2, 4 R, 5 I
-      if (trace) trace[9] = inc_timer();
+      if (trace) trace[9] = uint64_t(clock64());
     } else if (warp == 2) {
       const int nv = (ng + 31) >> 5;
       double a = (need_ll && lane < nv) ? s_rll[lane] : 0.0;
@@ -833,16 +864,17 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         for (int off = 1; off < nv; off <<= 1) a += __shfl_down_sync(kFull, a, off);
       if (lane == 0) s_pay[2] = uint64_t(__double_as_longlong(a));
     } else if (tid == 5 * 32) {
+      const dw H1 = head1();
       s_pay[3] = *reinterpret_cast<const uint64_t *>(&H1);
     }
     __syncthreads();
-    if (trace) trace[10] = inc_timer();
+    if (trace) trace[10] = uint64_t(clock64());
     const int nbase = need_ll ? 3 : 2;   // payloads every CTA gets
     const uint32_t tag = (epoch & ~kTagErr) | (s_err ? kTagErr : 0u);
-    if (trace) trace[19] = inc_timer();
+    if (trace) trace[19] = inc_timer();   // global time of the push (cross-CTA comparison)
     if (tid < C) {
       uint64_t *w = prm.trec + int64_t(kIncRecWords) * ((int64_t(par) * C + tid) * C + t);
-      const int nw_ = (tid < t && ce_of_tid >= t) ? kIncRec : nbase;
+      const int nw_ = (tid < t && s_ce[tid] >= t) ? kIncRec : nbase;
 #pragma unroll 1
       for (int i = 0; i < nw_; ++i) {
         const uint64_t v = s_pay[i];
@@ -850,7 +882,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       }
     }
     if (tid == 0 && s_err) atomicCAS(&ctl->error, 0, s_err);
-    if (trace) trace[11] = inc_timer();
+    if (trace) trace[11] = uint64_t(clock64());
     // ---- 5. the inbox: one thread per writer; meanwhile the other threads fetch column j+2's
     //         entries with eta and v as of this step's update
     const int jf = (j + 2) % p;
@@ -866,13 +898,13 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         atomicCAS(&s_anyerr, 0, got == 0 ? COX_E_TIMEOUT : 1);
       }
       for (int i = 0; i < nr; ++i) srec[i * kIncMaxCtas + tid] = r[i];
-      if (trace) trace[12] = inc_timer();
+      if (trace) trace[12] = uint64_t(clock64());
     } else {
       inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap, &s_cnt[sf],
                     C, kIncThreads - C, &s_err);
     }
     __syncthreads();
-    if (trace) trace[13] = inc_timer();
+    if (trace) trace[13] = uint64_t(clock64());
     // ---- 6. fixed-order reductions: G1 and G2 over every CTA by four warps each (quarters of the
     //         CTAs, combined by the step), LL when evaluated; H1, R, I over the later tiles this
     //         tile's last stratum continues into, one warp each
@@ -884,7 +916,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 #pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) a = dw_add_same(a, dw_shfl_down(a, off));
       if (lane == 0) s_Gq[v][qtr] = a;
-      if (trace) trace[16] = inc_timer();
+      if (trace) trace[16] = uint64_t(clock64());
     } else if (warp < 11) {
       const int v = warp - 5;   // payload 3 H1, 4 R, 5 I
       dw a = dw_make(0.0f);
@@ -900,7 +932,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       if (lane == 0) s_LL = a;
     }
     __syncthreads();
-    if (trace) trace[14] = inc_timer();
+    if (trace) trace[14] = uint64_t(clock64());
     // ---- 7. the coordinate step, computed identically by every CTA
     if (tid == 0) {
       bool stop = false;
@@ -930,9 +962,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         const dw G2 = dw_add_same(dw_add_same(s_Gq[1][0], s_Gq[1][1]), dw_add_same(s_Gq[1][2], s_Gq[1][3]));
         const double g1 = dw_to(G1) - pre_dx, g2 = dw_to(G2);
         double tr = pre_tr;
-        if (trace) trace[17] = inc_timer();
+        if (trace) trace[17] = uint64_t(clock64());
         const double s = inc_step_rule(g1, g2, pre_b, &tr, F.penalty, F.lambda, inv_var, pre_pen);
-        if (trace) trace[18] = inc_timer();
+        if (trace) trace[18] = uint64_t(clock64());
         const double b_new = pre_b + s;
         tru[j] = tr;
         bet[j] = b_new;
@@ -959,7 +991,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         st.j = jn;
       }
       st.epoch = epoch + 1u;
-      if (trace) { trace[15] = inc_timer(); trace[22] = uint64_t(clock64()); }
+      if (trace) trace[15] = uint64_t(clock64());
     }
     __syncthreads();
     ++base;
@@ -1003,10 +1035,12 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   }
 }
 
-// One fit over the whole grid: its arguments stay in the kernel-parameter space.
-template <class P>
+// One fit over the whole grid: its arguments stay in the kernel-parameter space. The traced
+// instantiation records phase timestamps (its trace pointer costs registers, so the production
+// instantiation has none).
+template <class P, bool kTrace>
 __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams prm) {
-  incr_body<P>(prm, int(blockIdx.x));
+  incr_body<P, kTrace>(prm, int(blockIdx.x));
 }
 
 // Several fits per launch: CTA b runs tile cta_map[b].y of fit cta_map[b].x, whose arguments it
@@ -1020,7 +1054,7 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_multi_kernel(const In
   uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
   for (int w = int(threadIdx.x); w < int(sizeof(IncParams) / 4); w += kIncThreads) dst[w] = src[w];
   __syncthreads();
-  incr_body<P>(sp, me.y);
+  incr_body<P, false>(sp, me.y);
 }
 
 template <class K>
@@ -1047,8 +1081,9 @@ template <class P>
 static int inc_max_ctas() {
   static int cached = -2;
   if (cached != -2) return cached;
-  const int a = inc_max_ctas_of(ccd_incr_kernel<P>), b = inc_max_ctas_of(ccd_incr_multi_kernel<P>);
-  return cached = a < b ? a : b;
+  const int a = inc_max_ctas_of(ccd_incr_kernel<P, false>), b = inc_max_ctas_of(ccd_incr_multi_kernel<P>);
+  const int c = inc_max_ctas_of(ccd_incr_kernel<P, true>);
+  return cached = a < b ? (a < c ? a : c) : (b < c ? b : c);
 }
 
 int inc_max_grid(int precision) { return precision == COX_FP32C ? inc_max_ctas<PF32C>() : inc_max_ctas<PF64>(); }
@@ -1058,8 +1093,12 @@ int launch_incr(int precision, const IncParams &prm, int grid, void *stream) {
   void *args[] = {const_cast<IncParams *>(&prm)};
   if (grid <= 0 || grid > inc_max_grid(precision) || grid != prm.T) return COX_E_INVALID;
   count_launches(1);
-  const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C>)
-                                          : reinterpret_cast<const void *>(ccd_incr_kernel<PF64>);
+  const bool tr = prm.trace != nullptr;
+  const void *fn = precision == COX_FP32C
+                       ? (tr ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, true>)
+                             : reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, false>))
+                       : (tr ? reinterpret_cast<const void *>(ccd_incr_kernel<PF64, true>)
+                             : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, false>));
   const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
   return e == cudaSuccess ? COX_OK : COX_E_CUDA;
 }

@@ -35,6 +35,7 @@
 #include "cox.h"
 #include "cox_internal.h"
 #include "dw.cuh"
+#include "step_rule.cuh"
 
 namespace coxgb {
 
@@ -94,6 +95,16 @@ struct IncState {
   dw E;                      // e^pend_db - 1
   int64_t coord_updates;
   uint32_t epoch;
+  // the last step's coefficient bookkeeping, done off the critical path at the next step
+  int32_t book, book_j, book_pen;
+  double book_s, book_b, book_dx, book_t;
+};
+
+// This step's column inputs, loaded and converted by an idle thread while the step runs.
+struct IncPre {
+  double dx, b, t;
+  dw dxw, bw, tw;
+  int32_t pen;
 };
 
 // ---- epoch-tagged exchange words: (epoch << 32) | 32 data bits; relaxed 8-byte accesses are
@@ -214,6 +225,23 @@ static __device__ double inc_penalty(const DevFit &F, int j, double b) {
   if (F.penalty == COX_PEN_L1) return F.lambda * fabs(b);
   if (F.penalty == COX_PEN_L2) return b * b / (2.0 * F.l2_var);
   return 0.0;
+}
+
+// The bookkeeping of a coordinate step (FP64): the new coefficient and trust half-width
+// (max(2 |s|, t / 2), §2.4) in this CTA's copies, beta'dX and the penalty.
+template <class St>
+static __device__ void inc_book(St &st, double *bet, double *tru, const DevFit &F, double half_inv_var) {
+  const int j = st.book_j;
+  const double s = st.book_s, b = st.book_b, bn = b + s;
+  bet[j] = bn;
+  const double a2 = 2.0 * fabs(s), h = 0.5 * st.book_t;
+  tru[j] = a2 > h ? a2 : h;
+  if (s != 0.0) {
+    st.bdx = fma(s, st.book_dx, st.bdx);
+    if (st.book_pen && F.penalty == COX_PEN_L1) st.pen += F.lambda * (fabs(bn) - fabs(b));
+    else if (st.book_pen && F.penalty == COX_PEN_L2) st.pen += (bn - b) * (bn + b) * half_inv_var;
+  }
+  st.book = 0;
 }
 
 // v at a position from eta (eq. parallel_d): FP64 exp split into a double-word, or the float
@@ -410,43 +438,6 @@ static __device__ dw inc_dense(const IncParams &prm, int lo, int npos, const uin
   return head;
 }
 
-// §2.4 step, the same rule as ccd_step_rule with the L2 prior's reciprocal variance given (the
-// scalar step runs on one thread between exchanges, where every FP64 operation is latency).
-static __device__ double inc_step_rule(double g1, double g2, double b, double *tr, int penalty, double lambda,
-                                       double inv_var, int penalized) {
-  double gamma = 0.0;
-  if (penalized && penalty == COX_PEN_L2) {
-    g1 = fma(b, inv_var, g1);
-    g2 = g2 + inv_var;
-  }
-  if (penalized && penalty == COX_PEN_L1) gamma = lambda;
-  double s;
-  if (!(g2 > 0.0) || !isfinite(g1) || !isfinite(g2)) {
-    s = 0.0;
-  } else if (gamma > 0.0) {
-    if (b == 0.0) {
-      if (g1 + gamma < 0.0) s = -(g1 + gamma) / g2;
-      else if (g1 - gamma > 0.0) s = -(g1 - gamma) / g2;
-      else s = 0.0;
-    } else {
-      s = -(g1 + (b > 0.0 ? gamma : -gamma)) / g2;
-    }
-  } else {
-    s = -g1 / g2;
-  }
-  const double t = *tr;
-  if (fabs(s) > t) s = s > 0.0 ? t : -t;
-  if (gamma > 0.0 && b != 0.0) {
-    const double nb = b + s;
-    if ((b > 0.0 && nb < 0.0) || (b < 0.0 && nb > 0.0)) s = -b;
-  }
-  const double a2 = 2.0 * fabs(s), h = 0.5 * t;
-  *tr = a2 > h ? a2 : h;
-  return s;
-}
-
-// The kernel body: CTA `t` of the fit described by `prm` (kernel parameters for a single fit,
-// shared memory when one launch runs several fits).
 template <class P, bool kTrace>
 static __device__ __forceinline__ void incr_body(const IncParams &prm, const int t) {
   using T = typename P::T;
@@ -482,7 +473,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   __shared__ int s_chain_end, s_bad, s_err, s_anyerr;
   __shared__ int s_ce[kIncMaxCtas];   // chain end of every CTA of the fit
   __shared__ uint64_t s_pay[kIncRec];   // this CTA's record payloads (bits): G1, G2, LL, H1, R, I
-  __shared__ double s_inv_var, s_half_inv_var;
+  __shared__ double s_half_inv_var;
+  __shared__ dw s_inv_var_dw, s_lambda_dw;
+  __shared__ IncPre s_pre;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const DevFit &F = prm.F;
@@ -522,8 +515,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     st.coord_updates = ctl->coord_updates;
     st.epoch = ctl->epoch;
     st.E = st.pend_j >= 0 ? dw_from(expm1(st.pend_db)) : dw_make(0.0f);
-    s_inv_var = 1.0 / F.l2_var;
     s_half_inv_var = 0.5 / F.l2_var;
+    s_inv_var_dw = dw_from(1.0 / F.l2_var);
+    s_lambda_dw = dw_from(F.lambda);
+    st.book = 0;
   }
   for (int jj = tid; jj < p; jj += kIncThreads) {
     bet[jj] = F.beta[jj];
@@ -618,7 +613,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     grp[tid].tail = seg == nc;
   }
   const int RW = max(32, ((npos + 1023) / 1024) * 32);   // positions per warp in the dense scan
-  const double inv_var = s_inv_var, half_inv_var = s_half_inv_var;
+  const double half_inv_var = s_half_inv_var;
   // list slots: previous column (pending update), current, next, and the one being fetched
   int base = 0;
   if (st.state == kRunning) {
@@ -649,16 +644,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     uint64_t *trace =
         (kTrace && prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * kIncTraceSlots : nullptr;
     if (trace) { trace[0] = uint64_t(clock64()); trace[21] = inc_timer(); }
-    // this coordinate's inputs to the step, loaded now so their latency overlaps the step
-    double pre_dx = 0.0, pre_b = 0.0, pre_tr = 0.0;
-    int pre_pen = 1;
-    if (tid == 0) {
-      pre_dx = D.dX[j];
-      pre_pen = F.penalize ? F.penalize[j] != 0 : 1;
-      pre_b = bet[j];
-      pre_tr = tru[j];
-      s_anyerr = 0;
-    }
+    if (tid == 0) s_anyerr = 0;
     // ---- 1. the pending update at the previous column's entries (one per thread):
     //         eta += dbeta (eq. parallel_xb); v (1 + (e^dbeta - 1)) (eq. parallel_d)
     dw dd = dw_make(0.0f);
@@ -900,6 +886,20 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       for (int i = 0; i < nr; ++i) srec[i * kIncMaxCtas + tid] = r[i];
       if (trace) trace[12] = uint64_t(clock64());
     } else {
+      if (tid == kIncThreads - 1) {
+        // while the records travel: the previous step's coefficient bookkeeping, then this
+        // coordinate's inputs to the step, converted for the double-word step rule
+        if (st.book) inc_book(st, bet, tru, F, half_inv_var);
+        IncPre q;
+        q.dx = D.dX[j];
+        q.b = bet[j];
+        q.t = tru[j];
+        q.pen = F.penalize ? F.penalize[j] != 0 : 1;
+        q.dxw = dw_from(q.dx);
+        q.bw = dw_from(q.b);
+        q.tw = dw_from(q.t);
+        s_pre = q;
+      }
       inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap, &s_cnt[sf],
                     C, kIncThreads - C, &s_err);
     }
@@ -960,26 +960,30 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       } else {
         const dw G1 = dw_add_same(dw_add_same(s_Gq[0][0], s_Gq[0][1]), dw_add_same(s_Gq[0][2], s_Gq[0][3]));
         const dw G2 = dw_add_same(dw_add_same(s_Gq[1][0], s_Gq[1][1]), dw_add_same(s_Gq[1][2], s_Gq[1][3]));
-        const double g1 = dw_to(G1) - pre_dx, g2 = dw_to(G2);
-        double tr = pre_tr;
+        const IncPre q = s_pre;
         if (trace) trace[17] = uint64_t(clock64());
-        const double s = inc_step_rule(g1, g2, pre_b, &tr, F.penalty, F.lambda, inv_var, pre_pen);
+        int kind;
+        const dw sw = inc_step_rule_dw(dw_sub(G1, q.dxw), G2, q.bw, q.b == 0.0, q.tw, F.penalty, s_lambda_dw,
+                                       s_inv_var_dw, q.pen, &kind);
         if (trace) trace[18] = uint64_t(clock64());
-        const double b_new = pre_b + s;
-        tru[j] = tr;
-        bet[j] = b_new;
-        if (s != 0.0) {
+        const double sd = inc_step_value(sw, kind, q.b, q.t);
+        if (sd != 0.0) {
           st.pend_j = j;
-          st.pend_db = s;
-          st.E = dw_from(exp(s) - 1.0);   // its absolute error is what the sums see
-          st.bdx = fma(s, pre_dx, st.bdx);
-          if (pre_pen && F.penalty == COX_PEN_L1) st.pen += F.lambda * (fabs(b_new) - fabs(pre_b));
-          else if (pre_pen && F.penalty == COX_PEN_L2) st.pen += (b_new - pre_b) * (b_new + pre_b) * half_inv_var;
+          st.pend_db = sd;
+          st.E = dw_from(exp(sd) - 1.0);   // its absolute error is what the sums see
         } else {
           st.pend_j = -1;
           st.pend_db = 0.0;
           st.E = dw_make(0.0f);
         }
+        // coefficient, trust, beta'dX and penalty follow at the next step (inc_book)
+        st.book = 1;
+        st.book_j = j;
+        st.book_s = sd;
+        st.book_b = q.b;
+        st.book_dx = q.dx;
+        st.book_t = q.t;
+        st.book_pen = q.pen;
         st.coord_updates += 1;
         const int jn = j + 1 >= p ? 0 : j + 1;
         if (jn == 0) {
@@ -997,6 +1001,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     ++base;
   }
 
+  if (tid == kIncThreads - 1 && st.book) inc_book(st, bet, tru, F, half_inv_var);
   // ---- the fit's v in its own precision: current since the last rebuild unless later steps
   //      updated positions
   if (!refreshed) {

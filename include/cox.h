@@ -199,6 +199,42 @@ int cox_batch_fit(cox_handle *const *h, int32_t n, const double *const *beta0, d
  * fit state and options: many fits of one data set (penalty grids) without re-preparing. */
 int cox_clone(const cox_handle *src, const cox_options *opts, cox_handle **out);
 
+/* ---------------------------------------------------------------- time-split view
+ * §2.2 (time-varying covariates on discrete intervals) and §2.3 (time-varying
+ * coefficients): cut days t_1 < ... < t_C split follow-up time into the C + 1 intervals
+ * I_0 = (-inf, t_1), I_k = [t_k, t_{k+1}), I_C = [t_C, +inf) (integer days). A Cox model whose
+ * covariates or coefficients are constant on each interval has the partial likelihood of a
+ * model stratified on the intervals (§2.2), and a coefficient that steps at the cuts is a
+ * covariate split into one copy per interval (§2.3). The view is that stratified model:
+ *
+ *   rows     stratum (s, k) holds every input row of stratum s that can be at risk at a time
+ *            in I_k: stop >= t_k and, for counting-process rows, start + 1 < t_{k+1}. Such a
+ *            row enters with stop' = min(stop, t_{k+1}) (stop when k = C), start' = start,
+ *            event' = event when stop lies in I_k, else 0. The paper's augmented copy also
+ *            keeps the rows that cannot be at risk in I_k; they add nothing to the likelihood
+ *            and are left out. Stratum ids: s_index * (C + 1) + k (s_index = 0-based rank of s).
+ *   columns  the input columns in order, each column listed in tvc_cols replaced by C + 1
+ *            consecutive columns (the column on I_0, ..., on I_C); the others unchanged. The
+ *            handle has p_view = p + n_tvc * C columns (cox_split_columns): options.penalize,
+ *            beta0 and beta_out are in view columns.
+ *
+ * The view is built by device kernels straight from the caller's arrays (host or device);
+ * no augmented copy is formed on the host or asked of the caller. Errors: COX_E_INVALID
+ * (cuts not strictly ascending, tvc_cols not strictly ascending in [0, p), sizes beyond the
+ * limits: view rows < 2^30, view nonzeros < 2^32), plus those of cox_create. */
+typedef struct {
+  int32_t n_cuts;           /* C >= 1 */
+  int32_t n_tvc;            /* columns with one coefficient per interval, 0..p */
+  const int32_t *cuts;      /* host, C strictly ascending days */
+  const int32_t *tvc_cols;  /* host, n_tvc strictly ascending column indices (NULL when 0) */
+} cox_split;
+
+/* p_view of a split of a p-column data set. */
+int cox_split_columns(int32_t p, const cox_split *split, int32_t *p_view);
+
+/* cox_create on the time-split view of `data`. The view's arrays live only during the call. */
+int cox_create_split(const cox_data *data, const cox_split *split, const cox_options *opts, cox_handle **out);
+
 /* Bytes of device memory a handle for `data` would hold (for admission control). */
 int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
 

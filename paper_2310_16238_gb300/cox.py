@@ -26,7 +26,7 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
-           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan",
+           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split",
            "cox_segscan_noalloc", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
@@ -60,6 +60,10 @@ class cox_fit_info(C.Structure):
                     loglik=self.loglik, objective=self.objective, status=self.status,
                     engine=self.engine, step_launches=self.step_launches, sweep_ms=self.sweep_ms, wait_ms=self.wait_ms,
                     total_ms=self.total_ms)
+
+
+class cox_split(C.Structure):
+    _fields_ = [("n_cuts", C.c_int32), ("n_tvc", C.c_int32), ("cuts", C.c_void_p), ("tvc_cols", C.c_void_p)]
 
 
 class cox_server_options(C.Structure):
@@ -109,6 +113,8 @@ def lib():
             L.cox_batch_fit.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(cox_fit_info)]
             L.cox_clone.argtypes = [vp, C.POINTER(cox_options), C.POINTER(vp)]
             L.cox_footprint.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_size_t)]
+            L.cox_split_columns.argtypes = [i32, C.POINTER(cox_split), C.POINTER(i32)]
+            L.cox_create_split.argtypes = [C.POINTER(cox_data), C.POINTER(cox_split), C.POINTER(cox_options), C.POINTER(vp)]
             L.cox_launch_count.argtypes = []
             L.cox_launch_count.restype = i64
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
@@ -204,6 +210,34 @@ def cox_create(data, opts=None, precision=COX_FP64, stream=None, tile=0, engine=
     h = C.c_void_p()
     _check(lib().cox_create(C.byref(d), C.byref(o), C.byref(h)))
     _P_CACHE[h.value] = int(data.p)
+    return h
+
+
+def make_split(cuts, tvc_cols=()):
+    """cox_split for cut days ``cuts`` (ascending) and the columns ``tvc_cols`` that get one
+    coefficient per interval."""
+    c = np.ascontiguousarray(cuts, dtype=np.int32)
+    t = np.ascontiguousarray(tvc_cols, dtype=np.int32)
+    sp = cox_split(int(c.shape[0]), int(t.shape[0]), _ptr(c), _ptr(t) if t.shape[0] else None)
+    return sp, (c, t)
+
+
+def cox_split_columns(p, cuts, tvc_cols=()):
+    sp, keep = make_split(cuts, tvc_cols)
+    out = C.c_int32()
+    _check(lib().cox_split_columns(int(p), C.byref(sp), C.byref(out)))
+    return int(out.value)
+
+
+def cox_create_split(data, cuts, tvc_cols=(), opts=None, precision=COX_FP64, stream=None, tile=0,
+                     engine=COX_ENGINE_AUTO):
+    """Handle on the time-split view of ``data`` (§2.2, §2.3); its p is the view's."""
+    d, keep = make_data(data)
+    sp, skeep = make_split(cuts, tvc_cols)
+    o, pen = make_options(opts, precision, stream, tile, engine)
+    h = C.c_void_p()
+    _check(lib().cox_create_split(C.byref(d), C.byref(sp), C.byref(o), C.byref(h)))
+    _P_CACHE[h.value] = cox_split_columns(data.p, cuts, tvc_cols)
     return h
 
 
@@ -349,6 +383,14 @@ class Handle:
             self.h, self.p = _raw
         _P_CACHE[self.h.value] = self.p
         self.precision = precision
+
+    @classmethod
+    def split(cls, data, cuts, tvc_cols=(), opts=None, precision=COX_FP64, stream=None, tile=0,
+              engine=COX_ENGINE_AUTO):
+        """Handle on the time-split view of ``data``: cut days ``cuts``, one coefficient per
+        interval for the columns ``tvc_cols`` (cox_create_split)."""
+        h = cox_create_split(data, cuts, tvc_cols, opts, precision, stream, tile, engine)
+        return cls(None, _raw=(h, _P_CACHE[h.value]), precision=precision)
 
     def fit(self, beta0=None):
         return cox_fit(self.h, beta0)

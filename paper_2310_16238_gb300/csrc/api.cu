@@ -206,6 +206,7 @@ int apply_options(cox_handle *h, const cox_options *o) {
     if (cudaMemcpyAsync(h->penalize, h->opts.penalize, p, cudaMemcpyDefault, h->stream) != cudaSuccess)
       return cuda_fail(h, "penalize copy");
     h->hfit.penalize = h->penalize;
+    h->opts.penalize = h->penalize;   // the caller's array may go away; clones copy from here
   }
   if (cudaMemcpyAsync(h->dfit, &h->hfit, sizeof(DevFit), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return cuda_fail(h, "fit descriptor copy");
@@ -700,6 +701,41 @@ int cox_create(const cox_data *data, const cox_options *opts, cox_handle **out) 
   }
   *out = h.release();
   return COX_OK;
+}
+
+int cox_split_columns(int32_t p, const cox_split *split, int32_t *p_view) {
+  if (!p_view || p < 0) return fail(nullptr, COX_E_INVALID, "cox_split_columns: bad arguments");
+  std::string err;
+  const int rc = split_columns(p, split, p_view, &err);
+  return rc ? fail(nullptr, rc, err) : COX_OK;
+}
+
+int cox_create_split(const cox_data *data, const cox_split *split, const cox_options *opts, cox_handle **out) {
+  if (!data || !split || !out) return fail(nullptr, COX_E_INVALID, "cox_create_split: null argument");
+  *out = nullptr;
+  if (check_options(opts)) return fail(nullptr, COX_E_INVALID, "cox_create_split: invalid options");
+  cudaStream_t s = opts && opts->stream ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  cudaStream_t own = nullptr;
+  if (!s) {
+    if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(nullptr, COX_E_CUDA, "cox_create_split: stream create");
+    s = own;
+  }
+  int rc;
+  {
+    BufferSet vb;   // the view's arrays, released once cox_create has copied what it needs
+    cox_data view{};
+    std::string err;
+    rc = build_split_view(data, split, s, vb, &view, &err);
+    if (rc) {
+      cudaGetLastError();
+      if (own) cudaStreamDestroy(own);
+      return fail(nullptr, rc, err.empty() ? "cox_create_split: view construction failed" : err);
+    }
+    rc = cox_create(&view, opts, out);
+  }
+  if (own) cudaStreamDestroy(own);
+  return rc;
 }
 
 int cox_clone(const cox_handle *src, const cox_options *opts, cox_handle **out) {

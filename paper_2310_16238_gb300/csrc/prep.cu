@@ -247,20 +247,43 @@ __global__ void validate_rows_kernel(int64_t n, const int32_t *stop, const int32
   if (e) atomicOr(err, e);
 }
 
-// one warp per column
-__global__ void validate_cols_kernel(int32_t p, int64_t n, const int64_t *col_ptr, const int32_t *row_idx, int32_t *err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+// ------------------------------------------------------------------ column segments
+// Per-column passes over the CSC run one block per segment of at most kSegLen entries of one
+// column, so one long column no longer serialises a pass (column lengths span three orders of
+// magnitude in the sparse workloads).
+constexpr int64_t kSegLen = 8192;
+constexpr int kSegThreads = 256;
+
+struct ColSeg {
+  int64_t a, b;     // entries [a, b) of column j (row-space CSC)
+  int64_t end;      // the column's end (col_ptr[j + 1])
+  int32_t j, pad;
+};
+
+// Segments of every non-empty column, in column order; first[j] = index of column j's first
+// segment (first[p] = number of segments).
+static void column_segments(const std::vector<int64_t> &col_ptr, std::vector<ColSeg> *segs, std::vector<int32_t> *first) {
+  const int32_t p = int32_t(col_ptr.size()) - 1;
+  segs->clear();
+  first->assign(size_t(p) + 1, 0);
+  for (int32_t j = 0; j < p; ++j) {
+    (*first)[j] = int32_t(segs->size());
+    for (int64_t a = col_ptr[j]; a < col_ptr[j + 1]; a += kSegLen)
+      segs->push_back({a, std::min(a + kSegLen, col_ptr[j + 1]), col_ptr[j + 1], j, 0});
+  }
+  (*first)[p] = int32_t(segs->size());
+}
+
+__global__ void validate_cols_kernel(const ColSeg *segs, const int64_t *col_ptr, const int32_t *row_idx, int64_t n,
+                                     int32_t *err) {
+  const ColSeg sg = segs[blockIdx.x];
+  const int64_t col_lo = col_ptr[sg.j];
   int32_t e = 0;
-  for (int64_t j = gw; j < p; j += nw) {
-    const int64_t a = col_ptr[j], b = col_ptr[j + 1];
-    if (b < a) { e |= kErrColPtr; continue; }
-    for (int64_t q = a + lane; q < b; q += 32) {
-      const int32_t r = row_idx[q];
-      if (r < 0 || r >= n) e |= kErrRowIdx;
-      if (q > a && !(row_idx[q - 1] < r)) e |= kErrColOrder;
-    }
+#pragma unroll 4
+  for (int64_t q = sg.a + threadIdx.x; q < sg.b; q += kSegThreads) {
+    const int32_t r = row_idx[q];
+    if (r < 0 || r >= n) e |= kErrRowIdx;
+    if (q > col_lo && !(row_idx[q - 1] < r)) e |= kErrColOrder;
   }
   if (e) atomicOr(err, e);
 }
@@ -348,19 +371,32 @@ __global__ void cut_build_kernel(int32_t K, const int32_t *seg_start, int counti
   }
 }
 
-// delta'X_j: one warp per column, lanes in a fixed order, then a fixed shuffle tree
-__global__ void dx_kernel(int32_t p, const int64_t *col_ptr, const int32_t *row_idx, const double *val,
-                          const uint8_t *event, double *dX) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t j = gw; j < p; j += nw) {
-    double s = 0.0;
-    for (int64_t q = col_ptr[j] + lane; q < col_ptr[j + 1]; q += 32)
-      if (event[row_idx[q]]) s += val ? val[q] : 1.0;
+// delta'X_j in two passes with a fixed summation order: one block per column segment (each
+// thread a strided subset, then a fixed tree), then one thread per column over its segments.
+__global__ void dx_seg_kernel(const ColSeg *segs, const int32_t *row_idx, const double *val, const uint8_t *event,
+                              double *partial) {
+  __shared__ double red[kSegThreads / 32];
+  const ColSeg sg = segs[blockIdx.x];
+  double s = 0.0;
+#pragma unroll 4
+  for (int64_t q = sg.a + threadIdx.x; q < sg.b; q += kSegThreads)
+    if (event[row_idx[q]]) s += val ? val[q] : 1.0;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) dX[j] = s;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kSegThreads / 32; ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void dx_final_kernel(int32_t p, const int32_t *first, const double *partial, double *dX) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < p; j += int64_t(gridDim.x) * blockDim.x) {
+    double s = 0.0;
+    for (int32_t i = first[j]; i < first[j + 1]; ++i) s += partial[i];
+    dX[j] = s;
   }
 }
 
@@ -402,19 +438,17 @@ __global__ void merge_positions_kernel(int64_t n, const int32_t *stop, const int
 }
 
 // two position-space entries per nonzero: key = (column << 32) | position
-__global__ void pos_csc_keys_kernel(int32_t p, const int64_t *col_ptr, const int32_t *row_idx, const int32_t *pos_entry,
+__global__ void pos_csc_keys_kernel(const ColSeg *segs, const int32_t *row_idx, const int32_t *pos_entry,
                                     const int32_t *pos_exit, uint64_t *key, uint32_t *pay) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t j = gw; j < p; j += nw)
-    for (int64_t q = col_ptr[j] + lane; q < col_ptr[j + 1]; q += 32) {
-      const int32_t r = row_idx[q];
-      key[2 * q] = (uint64_t(j) << 32) | uint64_t(uint32_t(pos_entry[r]));
-      pay[2 * q] = uint32_t(q) << 1;
-      key[2 * q + 1] = (uint64_t(j) << 32) | uint64_t(uint32_t(pos_exit[r]));
-      pay[2 * q + 1] = (uint32_t(q) << 1) | 1u;
-    }
+  const ColSeg sg = segs[blockIdx.x];
+  const uint64_t j = uint64_t(sg.j) << 32;
+  for (int64_t q = sg.a + threadIdx.x; q < sg.b; q += kSegThreads) {
+    const int32_t r = row_idx[q];
+    key[2 * q] = j | uint64_t(uint32_t(pos_entry[r]));
+    pay[2 * q] = uint32_t(q) << 1;
+    key[2 * q + 1] = j | uint64_t(uint32_t(pos_exit[r]));
+    pay[2 * q + 1] = (uint32_t(q) << 1) | 1u;
+  }
 }
 
 __global__ void pos_csc_fill_kernel(int64_t nnz2, const uint64_t *key, const uint32_t *pay, const double *val_row,
@@ -461,24 +495,22 @@ __global__ void col_tile_kernel(int32_t p, int32_t T, const int64_t *col_ptr, co
 }
 
 // Shortest run of risk positions that holds cap + 1 entries of one column, over every column
-// (one warp per column): a tile shorter than it holds at most cap entries of any column.
-__global__ void window_kernel(int32_t p, const int64_t *col_ptr, const uint32_t *idx, int32_t cap, int32_t *out_min) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t j = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; j < p; j += nwarps) {
-    const int64_t a = col_ptr[j], n = col_ptr[j + 1] - a;
-    int32_t best = 0x7fffffff;
-    for (int64_t k = lane; k + cap < n; k += 32) {
-      const int32_t w = int32_t(idx[a + k + cap] & kPosMask) - int32_t(idx[a + k] & kPosMask) + 1;
-      best = min(best, w);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, off));
-    if (lane == 0 && best < 0x7fffffff) atomicMin(out_min, best);
+// (one block per column segment; `scale` = position-space entries per nonzero): a tile shorter
+// than it holds at most cap entries of any column.
+__global__ void window_kernel(const ColSeg *segs, int32_t scale, const uint32_t *idx, int32_t cap, int32_t *out_min) {
+  const ColSeg sg = segs[blockIdx.x];
+  const int64_t a = scale * sg.a, b = scale * sg.b, end = scale * sg.end;
+  int32_t best = 0x7fffffff;
+#pragma unroll 4
+  for (int64_t k = a + threadIdx.x; k < b && k + cap < end; k += kSegThreads) {
+    const int32_t w = int32_t(idx[k + cap] & kPosMask) - int32_t(idx[k] & kPosMask) + 1;
+    best = min(best, w);
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0 && best < 0x7fffffff) atomicMin(out_min, best);
 }
 
-// ------------------------------------------------------------------ host orchestration
 static bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -670,8 +702,21 @@ int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string
   return COX_OK;
 }
 
-int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err) {
-  Scratch sc;   // temporaries, freed on return
+// Inputs staged on the device and validated (shared by cox_create and the time-split view).
+struct Staged {
+  int64_t n = 0, nnz = 0, nseg = 0;
+  int32_t p = 0;
+  const int32_t *stop = nullptr, *start = nullptr, *stratum = nullptr, *row_idx = nullptr;
+  const uint8_t *event = nullptr;
+  const double *val = nullptr;
+  const int64_t *col_ptr = nullptr;
+  std::vector<int64_t> h_col_ptr;
+  std::vector<int32_t> h_seg_first;
+  ColSeg *segs = nullptr;
+  int32_t *seg_first = nullptr;
+};
+
+static int stage_inputs(const cox_data *in, Scratch &sc, cudaStream_t s, Staged *st, std::string *err) {
   const int64_t n = in->n_rows;
   const int32_t p = in->p;
   if (n < 0 || p < 0 || !in->stop || !in->event || !in->col_ptr || (n > 0 && p > 0 && !in->row_idx)) {
@@ -682,15 +727,9 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
     *err = "cox_create: n_rows must be < 2^30";
     return COX_E_INVALID;
   }
-  const int counting = in->start != nullptr;
-  const int kernel_tile = ccd_tile(precision);
-  int tile = tile_req > 0 ? tile_req : kernel_tile;
-  if (tile % 32 != 0 || tile > kernel_tile || tile < 1024) {
-    *err = "cox_create: tile must be a multiple of 32 in [1024, " + std::to_string(kernel_tile) + "]";
-    return COX_E_INVALID;
-  }
   // column pointers (host copy for nnz and launch sizes)
-  std::vector<int64_t> h_col_ptr(size_t(p) + 1);
+  std::vector<int64_t> &h_col_ptr = st->h_col_ptr;
+  h_col_ptr.assign(size_t(p) + 1, 0);
   if (cudaMemcpy(h_col_ptr.data(), in->col_ptr, (size_t(p) + 1) * sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess) {
     *err = "cox_create: cannot read col_ptr";
     return COX_E_CUDA;
@@ -706,22 +745,44 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
       return COX_E_INVALID;
     }
   int rc = COX_OK;
-  const int32_t *stop = device_view(in->stop, n, sc, s, &rc);
-  const int32_t *start = device_view(in->start, n, sc, s, &rc);
-  const uint8_t *event = device_view(in->event, n, sc, s, &rc);
-  const int32_t *stratum = device_view(in->stratum, n, sc, s, &rc);
-  const int32_t *row_idx = device_view(in->row_idx, nnz, sc, s, &rc);
-  const double *val = device_view(in->val, nnz, sc, s, &rc);
-  const int64_t *col_ptr_in = device_view(in->col_ptr, int64_t(p) + 1, sc, s, &rc);
+  st->n = n;
+  st->p = p;
+  st->nnz = nnz;
+  st->stop = device_view(in->stop, n, sc, s, &rc);
+  st->start = device_view(in->start, n, sc, s, &rc);
+  st->event = device_view(in->event, n, sc, s, &rc);
+  st->stratum = device_view(in->stratum, n, sc, s, &rc);
+  st->row_idx = device_view(in->row_idx, nnz, sc, s, &rc);
+  st->val = device_view(in->val, nnz, sc, s, &rc);
+  st->col_ptr = device_view(in->col_ptr, int64_t(p) + 1, sc, s, &rc);
   if (rc) {
     *err = "cox_create: staging inputs failed";
     return rc;
   }
+  // column segments for the per-column passes (validation, delta'X, list windows)
+  std::vector<ColSeg> h_segs;
+  column_segments(h_col_ptr, &h_segs, &st->h_seg_first);
+  const int64_t nseg = st->nseg = int64_t(h_segs.size());
+  st->segs = static_cast<ColSeg *>(sc.get((nseg > 0 ? nseg : 1) * sizeof(ColSeg)));
+  st->seg_first = static_cast<int32_t *>(sc.get((size_t(p) + 1) * sizeof(int32_t)));
+  if (!st->segs || !st->seg_first) return COX_E_OOM;
+  if ((nseg > 0 && cudaMemcpyAsync(st->segs, h_segs.data(), nseg * sizeof(ColSeg), cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+      cudaMemcpyAsync(st->seg_first, st->h_seg_first.data(), (size_t(p) + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess) {
+    *err = "cox_create: staging column segments failed";
+    return COX_E_CUDA;
+  }
   int32_t *d_err = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
   if (!d_err) return COX_E_OOM;
   cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
-  if (n > 0) { count_launches(1); validate_rows_kernel<<<grid_for(n), 256, 0, s>>>(n, stop, start, event, stratum, d_err); }
-  if (p > 0) { count_launches(1); validate_cols_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, n, col_ptr_in, row_idx, d_err); }
+  if (n > 0) {
+    count_launches(1);
+    validate_rows_kernel<<<grid_for(n), 256, 0, s>>>(n, st->stop, st->start, st->event, st->stratum, d_err);
+  }
+  if (nseg > 0) {
+    count_launches(1);
+    validate_cols_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(st->segs, st->col_ptr, st->row_idx, n, d_err);
+  }
   int32_t h_err = 0;
   cudaMemcpyAsync(&h_err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -734,6 +795,30 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   if (h_err & kErrRowIdx) { *err = "cox_create: row_idx out of range"; return COX_E_INVALID; }
   if (h_err & kErrColOrder) { *err = "cox_create: row_idx must be strictly ascending within a column"; return COX_E_INVALID; }
   if (h_err & kErrColPtr) { *err = "cox_create: col_ptr must be nondecreasing"; return COX_E_INVALID; }
+  return COX_OK;
+}
+
+int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err) {
+  Scratch sc;   // temporaries, freed on return
+  const int counting = in->start != nullptr;
+  const int kernel_tile = ccd_tile(precision);
+  int tile = tile_req > 0 ? tile_req : kernel_tile;
+  if (tile % 32 != 0 || tile > kernel_tile || tile < 1024) {
+    *err = "cox_create: tile must be a multiple of 32 in [1024, " + std::to_string(kernel_tile) + "]";
+    return COX_E_INVALID;
+  }
+  Staged st;
+  int rc = stage_inputs(in, sc, s, &st, err);
+  if (rc) return rc;
+  const int64_t n = st.n, nnz = st.nnz, nseg = st.nseg;
+  const int32_t p = st.p;
+  const int32_t *stop = st.stop, *start = st.start, *stratum = st.stratum, *row_idx = st.row_idx;
+  const uint8_t *event = st.event;
+  const double *val = st.val;
+  const int64_t *col_ptr_in = st.col_ptr;
+  const std::vector<int64_t> &h_col_ptr = st.h_col_ptr;
+  const ColSeg *segs = st.segs;
+  const int32_t *seg_first = st.seg_first;
 
   BufferSet &B = out->bufs;
   DevData &D = out->desc;
@@ -848,7 +933,13 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   // delta'X
   double *dX = static_cast<double *>(B.get((p > 0 ? p : 1) * sizeof(double)));
   if (!dX) return COX_E_OOM;
-  if (p > 0) { count_launches(1); dx_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr_in, row_idx, val, event, dX); }
+  if (p > 0) {
+    double *partial = static_cast<double *>(sc.get((nseg > 0 ? nseg : 1) * sizeof(double)));
+    if (!partial) return COX_E_OOM;
+    if (nseg > 0) { count_launches(1); dx_seg_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, row_idx, val, event, partial); }
+    count_launches(1);
+    dx_final_kernel<<<grid_for(p), 256, 0, s>>>(p, seg_first, partial, dX);
+  }
   D.dX = dX;
 
   // ---- the position-space CSC
@@ -870,10 +961,11 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
     int32_t *pos_exit = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
     if (!exit_bits || !pos_entry || !pos_exit) return COX_E_OOM;
     cudaMemsetAsync(exit_bits, 0, ((M + 31) / 32 + 1) * sizeof(uint32_t), s);
-    if (n > 0)
+    if (n > 0) {
       count_launches(1);
       merge_positions_kernel<<<grid_for(n), 256, 0, s>>>(n, stop, start, kidx, seg_start, sidx, sorted_start, pos_entry,
                                                          pos_exit, exit_bits);
+    }
     count_launches(1);
     double_ptr_kernel<<<grid_for(int64_t(p) + 1), 256, 0, s>>>(p, col_ptr_in, col_ptr);
     if (nnz > 0) {
@@ -881,7 +973,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
       uint32_t *pay = static_cast<uint32_t *>(sc.get(nnz_pos * sizeof(uint32_t)));
       if (!key || !pay) return COX_E_OOM;
       count_launches(1);
-      pos_csc_keys_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr_in, row_idx, pos_entry, pos_exit, key, pay);
+      pos_csc_keys_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, row_idx, pos_entry, pos_exit, key, pay);
       std::vector<int> bits;
       const int pb = bits_needed(uint64_t(M > 0 ? M - 1 : 0)), jb = bits_needed(uint64_t(p > 0 ? p - 1 : 0));
       for (int b = 0; b < pb; ++b) bits.push_back(b);
@@ -947,8 +1039,9 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         int32_t *d_w = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
         if (!d_w) return COX_E_OOM;
         cudaMemcpyAsync(d_w, &wmin, sizeof(int32_t), cudaMemcpyHostToDevice, s);
-        count_launches(1);
-        window_kernel<<<grid_for(int64_t(p) * 32), 256, 0, s>>>(p, col_ptr, idx, inc_list_cap(), d_w);
+        if (nseg > 0) count_launches(1);
+        if (nseg > 0)
+          window_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, counting ? 2 : 1, idx, inc_list_cap(), d_w);
         if (cudaMemcpyAsync(&wmin, d_w, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
           *err = "cox_create: table kernels failed";
@@ -985,6 +1078,254 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
     *err = "cox_create: table kernels failed";
     return COX_E_CUDA;
   }
+  return COX_OK;
+}
+
+// ------------------------------------------------------------------ time-split view (§2.2, §2.3)
+// Intervals a row can be at risk in: I_k (k = 0..C, I_k = [t_k, t_{k+1}), t_0 = -inf,
+// t_{C+1} = +inf) holds an integer time t with start < t <= stop iff t_k <= stop and
+// start + 1 < t_{k+1}; both bounds are counts of cuts, so the intervals form the range [klo, khi].
+__device__ __forceinline__ void split_range(const int32_t *cuts, int32_t C, int32_t stop, const int32_t *start,
+                                            int64_t r, int32_t *klo, int32_t *khi) {
+  *khi = int32_t(upper_bound_dev<int32_t>(cuts, C, stop));
+  *klo = start ? int32_t(upper_bound_dev<int32_t>(cuts, C, start[r] + 1)) : 0;
+}
+
+__global__ void split_count_kernel(int64_t n, const int32_t *stop, const int32_t *start, const int32_t *cuts, int32_t C,
+                                   int32_t *cnt) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    int32_t klo, khi;
+    split_range(cuts, C, stop[r], start, r, &klo, &khi);
+    cnt[r] = khi - klo + 1;
+  }
+}
+
+// one (row, interval) pair per view row; key = view stratum (input stratum index, interval)
+__global__ void split_pairs_kernel(int64_t n, const int32_t *stop, const int32_t *start, const int32_t *kidx,
+                                   const int32_t *cuts, int32_t C, const int64_t *pair_off, uint64_t *key, uint32_t *pay) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    int32_t klo, khi;
+    split_range(cuts, C, stop[r], start, r, &klo, &khi);
+    for (int32_t k = klo; k <= khi; ++k) {
+      const int64_t q = pair_off[r] + (k - klo);
+      key[q] = uint64_t(kidx[r]) * uint64_t(C + 1) + uint64_t(k);
+      pay[q] = uint32_t(r);
+    }
+  }
+}
+
+// view rows in (stratum, interval, input row) order; inv maps each pair to its view row
+__global__ void split_rows_kernel(int64_t M, const uint64_t *key, const uint32_t *pay, const int32_t *cuts, int32_t C,
+                                  const int32_t *stop, const int32_t *start, const uint8_t *event, const int64_t *pair_off,
+                                  int32_t *v_stop, int32_t *v_start, uint8_t *v_event, int32_t *v_stratum, int32_t *inv) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < M; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = pay[i];
+    const int32_t k = int32_t(key[i] % uint64_t(C + 1));
+    int32_t klo, khi;
+    split_range(cuts, C, stop[r], start, r, &klo, &khi);
+    v_stop[i] = k < C ? min(stop[r], cuts[k]) : stop[r];
+    v_event[i] = (event[r] && k == khi) ? 1 : 0;
+    if (v_start) v_start[i] = start[r];
+    v_stratum[i] = int32_t(key[i]);
+    inv[pair_off[r] + (k - klo)] = int32_t(i);
+  }
+}
+
+__global__ void split_entry_count_kernel(int64_t nnz, const int32_t *row_idx, const int32_t *cnt, int32_t *ecnt) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nnz; q += int64_t(gridDim.x) * blockDim.x)
+    ecnt[q] = cnt[row_idx[q]];
+}
+
+// one view entry per (nonzero, interval of its row): key = (view column, view stratum); a
+// stable sort on the key leaves the entries of one (column, stratum) in input-row order,
+// which is view-row order
+__global__ void split_entries_kernel(const ColSeg *segs, const int32_t *row_idx, const int32_t *stop,
+                                     const int32_t *start, const int32_t *kidx, const int32_t *cuts, int32_t C, uint64_t Kv,
+                                     const int32_t *col_base, const uint8_t *col_tvc, const int64_t *pair_off,
+                                     const int32_t *inv, const int64_t *eoff, uint64_t *key, uint32_t *pay, int32_t *g_row,
+                                     int64_t *g_src) {
+  const ColSeg sg = segs[blockIdx.x];
+  const int32_t base = col_base[sg.j];
+  const bool tvc = col_tvc[sg.j] != 0;
+  for (int64_t q = sg.a + threadIdx.x; q < sg.b; q += kSegThreads) {
+    const int32_t r = row_idx[q];
+    int32_t klo, khi;
+    split_range(cuts, C, stop[r], start, r, &klo, &khi);
+    for (int32_t k = klo; k <= khi; ++k) {
+      const int64_t g = eoff[q] + (k - klo);
+      const uint64_t c = uint64_t(base + (tvc ? k : 0));
+      key[g] = c * Kv + uint64_t(kidx[r]) * uint64_t(C + 1) + uint64_t(k);
+      pay[g] = uint32_t(g);
+      g_row[g] = inv[pair_off[r] + (k - klo)];
+      if (g_src) g_src[g] = q;
+    }
+  }
+}
+
+__global__ void split_fill_kernel(int64_t E, const uint64_t *key, const uint32_t *pay, uint64_t Kv, int32_t p_view,
+                                  const int32_t *g_row, const int64_t *g_src, const double *val, int32_t *v_row,
+                                  double *v_val, int64_t *v_col_ptr) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < E; e += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t g = pay[e];
+    v_row[e] = g_row[g];
+    if (v_val) v_val[e] = val[g_src[g]];
+    const int64_t c = int64_t(key[e] / Kv);
+    const int64_t cp = e == 0 ? -1 : int64_t(key[e - 1] / Kv);
+    for (int64_t cc = cp + 1; cc <= c; ++cc) v_col_ptr[cc] = e;
+    if (e == E - 1)
+      for (int64_t cc = c + 1; cc <= p_view; ++cc) v_col_ptr[cc] = E;
+  }
+}
+
+int split_columns(int32_t p, const cox_split *sp, int32_t *p_view, std::string *err) {
+  if (!sp || sp->n_cuts < 1 || !sp->cuts || sp->n_tvc < 0 || sp->n_tvc > p || (sp->n_tvc > 0 && !sp->tvc_cols)) {
+    *err = "cox_split: need n_cuts >= 1 with cuts, and 0 <= n_tvc <= p with tvc_cols";
+    return COX_E_INVALID;
+  }
+  for (int32_t c = 1; c < sp->n_cuts; ++c)
+    if (!(sp->cuts[c - 1] < sp->cuts[c])) {
+      *err = "cox_split: cuts must be strictly ascending";
+      return COX_E_INVALID;
+    }
+  for (int32_t m = 0; m < sp->n_tvc; ++m)
+    if (sp->tvc_cols[m] < 0 || sp->tvc_cols[m] >= p || (m > 0 && !(sp->tvc_cols[m - 1] < sp->tvc_cols[m]))) {
+      *err = "cox_split: tvc_cols must be strictly ascending column indices in [0, p)";
+      return COX_E_INVALID;
+    }
+  const int64_t pv = int64_t(p) + int64_t(sp->n_tvc) * sp->n_cuts;
+  if (pv >= (int64_t(1) << 31)) {
+    *err = "cox_split: too many view columns";
+    return COX_E_INVALID;
+  }
+  *p_view = int32_t(pv);
+  return COX_OK;
+}
+
+int build_split_view(const cox_data *in, const cox_split *sp, cudaStream_t s, BufferSet &B, cox_data *view,
+                     std::string *err) {
+  Scratch sc;
+  int32_t p_view = 0;
+  int rc = split_columns(in ? in->p : 0, sp, &p_view, err);
+  if (rc) return rc;
+  Staged st;
+  if ((rc = stage_inputs(in, sc, s, &st, err))) return rc;
+  const int64_t n = st.n, nnz = st.nnz;
+  const int32_t p = st.p, C = sp->n_cuts;
+  // cuts and the column map on the device
+  std::vector<int32_t> h_base(size_t(p) + 1, 0);
+  std::vector<uint8_t> h_tvc(size_t(p) + 1, 0);
+  for (int32_t m = 0; m < sp->n_tvc; ++m) h_tvc[sp->tvc_cols[m]] = 1;
+  for (int32_t j = 0, c = 0; j < p; ++j) {
+    h_base[j] = c;
+    c += h_tvc[j] ? C + 1 : 1;
+  }
+  int32_t *cuts = static_cast<int32_t *>(sc.get(size_t(C) * sizeof(int32_t)));
+  int32_t *col_base = static_cast<int32_t *>(sc.get((size_t(p) + 1) * sizeof(int32_t)));
+  uint8_t *col_tvc = static_cast<uint8_t *>(sc.get(size_t(p) + 1));
+  if (!cuts || !col_base || !col_tvc) return COX_E_OOM;
+  if (cudaMemcpyAsync(cuts, sp->cuts, size_t(C) * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(col_base, h_base.data(), (size_t(p) + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(col_tvc, h_tvc.data(), size_t(p) + 1, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return COX_E_CUDA;
+
+  // stratum index of every row
+  const int64_t nn = n > 0 ? n : 1;
+  int32_t *seg_flag = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int32_t *ev_flag = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int64_t *seg_pre = static_cast<int64_t *>(sc.get(nn * sizeof(int64_t)));
+  int32_t *kidx = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int32_t *cnt = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int64_t *pair_off = static_cast<int64_t *>(sc.get(nn * sizeof(int64_t)));
+  if (!seg_flag || !ev_flag || !seg_pre || !kidx || !cnt || !pair_off) return COX_E_OOM;
+  int64_t K = 0, M = 0;
+  if (n > 0) {
+    count_launches(1);
+    row_flags_kernel<<<grid_for(n), 256, 0, s>>>(n, st.stop, st.event, st.stratum, seg_flag, ev_flag);
+    if ((rc = exclusive_scan(seg_flag, n, seg_pre, &K, sc, s))) return rc;
+    count_launches(1);
+    row_stratum_index_kernel<<<grid_for(n), 256, 0, s>>>(n, seg_flag, seg_pre, kidx);
+    count_launches(1);
+    split_count_kernel<<<grid_for(n), 256, 0, s>>>(n, st.stop, st.start, cuts, C, cnt);
+    if ((rc = exclusive_scan(cnt, n, pair_off, &M, sc, s))) return rc;
+  }
+  const uint64_t Kv = uint64_t(K > 0 ? K : 1) * uint64_t(C + 1);
+  if (M >= (int64_t(1) << 30) || Kv >= (uint64_t(1) << 31)) {
+    *err = "cox_split: the view needs fewer than 2^30 rows and 2^31 strata";
+    return COX_E_INVALID;
+  }
+  // view rows
+  const int64_t mm = M > 0 ? M : 1;
+  int32_t *v_stop = static_cast<int32_t *>(B.get(mm * sizeof(int32_t)));
+  int32_t *v_start = st.start ? static_cast<int32_t *>(B.get(mm * sizeof(int32_t))) : nullptr;
+  uint8_t *v_event = static_cast<uint8_t *>(B.get(mm));
+  int32_t *v_stratum = static_cast<int32_t *>(B.get(mm * sizeof(int32_t)));
+  int32_t *inv = static_cast<int32_t *>(sc.get(mm * sizeof(int32_t)));
+  if (!v_stop || (st.start && !v_start) || !v_event || !v_stratum || !inv) return COX_E_OOM;
+  if (M > 0) {
+    uint64_t *key = static_cast<uint64_t *>(sc.get(M * sizeof(uint64_t)));
+    uint32_t *pay = static_cast<uint32_t *>(sc.get(M * sizeof(uint32_t)));
+    if (!key || !pay) return COX_E_OOM;
+    count_launches(1);
+    split_pairs_kernel<<<grid_for(n), 256, 0, s>>>(n, st.stop, st.start, kidx, cuts, C, pair_off, key, pay);
+    std::vector<int> bits;
+    for (int b = 0; b < bits_needed(Kv - 1); ++b) bits.push_back(b);
+    if ((rc = radix_sort(key, pay, M, bits, sc, s))) return rc;
+    count_launches(1);
+    split_rows_kernel<<<grid_for(M), 256, 0, s>>>(M, key, pay, cuts, C, st.stop, st.start, st.event, pair_off, v_stop,
+                                                    v_start, v_event, v_stratum, inv);
+  }
+  // view columns
+  int64_t E = 0;
+  int32_t *ecnt = static_cast<int32_t *>(sc.get((nnz > 0 ? nnz : 1) * sizeof(int32_t)));
+  int64_t *eoff = static_cast<int64_t *>(sc.get((nnz > 0 ? nnz : 1) * sizeof(int64_t)));
+  if (!ecnt || !eoff) return COX_E_OOM;
+  if (nnz > 0) {
+    count_launches(1);
+    split_entry_count_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, st.row_idx, cnt, ecnt);
+    if ((rc = exclusive_scan(ecnt, nnz, eoff, &E, sc, s))) return rc;
+  }
+  if (E >= (int64_t(1) << 32)) {
+    *err = "cox_split: the view needs fewer than 2^32 nonzeros";
+    return COX_E_INVALID;
+  }
+  const int64_t ee = E > 0 ? E : 1;
+  int64_t *v_col_ptr = static_cast<int64_t *>(B.get((size_t(p_view) + 1) * sizeof(int64_t)));
+  int32_t *v_row = static_cast<int32_t *>(B.get(ee * sizeof(int32_t)));
+  double *v_val = st.val ? static_cast<double *>(B.get(ee * sizeof(double))) : nullptr;
+  if (!v_col_ptr || !v_row || (st.val && !v_val)) return COX_E_OOM;
+  cudaMemsetAsync(v_col_ptr, 0, (size_t(p_view) + 1) * sizeof(int64_t), s);
+  if (E > 0) {
+    uint64_t *key = static_cast<uint64_t *>(sc.get(E * sizeof(uint64_t)));
+    uint32_t *pay = static_cast<uint32_t *>(sc.get(E * sizeof(uint32_t)));
+    int32_t *g_row = static_cast<int32_t *>(sc.get(E * sizeof(int32_t)));
+    int64_t *g_src = st.val ? static_cast<int64_t *>(sc.get(E * sizeof(int64_t))) : nullptr;
+    if (!key || !pay || !g_row || (st.val && !g_src)) return COX_E_OOM;
+    count_launches(1);
+    split_entries_kernel<<<unsigned(st.nseg), kSegThreads, 0, s>>>(st.segs, st.row_idx, st.stop, st.start, kidx, cuts, C,
+                                                                   Kv, col_base, col_tvc, pair_off, inv, eoff, key, pay,
+                                                                   g_row, g_src);
+    std::vector<int> bits;
+    for (int b = 0; b < bits_needed(uint64_t(p_view) * Kv - 1); ++b) bits.push_back(b);
+    if ((rc = radix_sort(key, pay, E, bits, sc, s))) return rc;
+    count_launches(1);
+    split_fill_kernel<<<grid_for(E), 256, 0, s>>>(E, key, pay, Kv, p_view, g_row, g_src, st.val, v_row, v_val,
+                                                   v_col_ptr);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaPeekAtLastError() != cudaSuccess) {
+    *err = "cox_split: view kernels failed";
+    return COX_E_CUDA;
+  }
+  *view = cox_data{};
+  view->n_rows = M;
+  view->p = p_view;
+  view->stop = v_stop;
+  view->start = v_start;
+  view->event = v_event;
+  view->stratum = v_stratum;
+  view->col_ptr = v_col_ptr;
+  view->row_idx = v_row;
+  view->val = v_val;
   return COX_OK;
 }
 

@@ -57,6 +57,11 @@ struct Prepared {
 };
 
 int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s, Prepared *out, std::string *err);
+// Time-split view of a data set (§2.2, §2.3), built by device kernels; its arrays are owned
+// by `B` (device memory) and described by *view.
+int split_columns(int32_t p, const cox_split *sp, int32_t *p_view, std::string *err);
+int build_split_view(const cox_data *in, const cox_split *sp, cudaStream_t s, BufferSet &B, cox_data *view,
+                     std::string *err);
 // Build (once) the incremental kernel's compact plan of a prepared data set (fewest tiles).
 int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string *err);
 

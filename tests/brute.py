@@ -146,3 +146,30 @@ def fit(data, opts, max_sweeps=None):
             break
         obj_prev = obj
     return beta, sweeps, conv
+
+
+def loglik_step_coef(data, beta_view, cuts, tvc_cols):
+    """Log partial likelihood of a model whose listed coefficients step at the cut days
+    (eq. time_coef_l), from the unsplit data: at an event time t in interval k
+    (t_k <= t < t_{k+1}), every row's linear predictor uses the interval-k coefficient of each
+    listed column. ``beta_view`` is ordered as the split columns (each listed column replaced
+    by one coefficient per interval, interval 0 first)."""
+    cuts = list(cuts)
+    tv = set(int(j) for j in tvc_cols)
+    col, c = [], 0
+    for j in range(data.p):
+        col.append(c)
+        c += len(cuts) + 1 if j in tv else 1
+    x = _dense(data)
+    k = np.zeros(data.n, np.int64) if data.stratum is None else data.stratum.astype(np.int64)
+    terms = []
+    for i in range(data.n):
+        if not data.event[i]:
+            continue
+        t = int(data.stop[i])
+        kk = sum(1 for u in cuts if u <= t)          # interval of t
+        b_t = np.array([beta_view[col[j] + (kk if j in tv else 0)] for j in range(data.p)])
+        eta = x @ b_t
+        m = at_risk(data, int(k[i]), t)
+        terms.append(eta[i] - math.log(math.fsum(np.exp(eta[m]))))
+    return math.fsum(terms)

@@ -289,3 +289,34 @@ def test_resident_then_evaluations_consistent():
         ll = h.loglik(beta)
     assert np.max(np.abs(g1 + beta / 0.5)) < 1e-6
     assert abs(ll - info["loglik"]) <= 1e-11 * abs(ll)
+
+
+def test_long_columns_span_segments():
+    """Columns longer than one column segment (8192 entries): delta'X of a valued and a binary
+    column against the oracle, and an ordering error exactly at a segment boundary rejected."""
+    rng = np.random.default_rng(71)
+    n = 30000
+    stop = np.sort(rng.integers(1, 400, n)).astype(np.int32)
+    event = (rng.random(n) < 0.3).astype(np.uint8)
+    dense_rows = np.arange(n)
+    mid_rows = np.sort(rng.choice(n, 17000, replace=False))
+    small_rows = np.sort(rng.choice(n, 40, replace=False))
+    rows = [dense_rows, mid_rows, small_rows, np.zeros(0, np.int64)]
+    vals = [rng.normal(size=len(r)) for r in rows]
+    d = synth.finalize(stop, event, None, None, rows, vals, 4)
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-10)
+    with cox.Handle(d, o) as h:
+        assert np.allclose(h.dx(), oracle.dX(d), rtol=1e-12, atol=1e-12)
+        bh, ih = h.fit()
+    bo, io = oracle.fit(d, o, max_sweeps=ih["sweeps"])
+    assert _rel_beta(bh, bo) <= 1e-9
+    db = synth.finalize(stop, event, None, None, rows, None, 4)
+    with cox.Handle(db, o) as h:
+        assert h.dx().tolist() == oracle.dX(db).tolist()
+    bad = synth.CoxData(**{**db.__dict__})
+    bad.row_idx = db.row_idx.copy()
+    a = int(db.col_ptr[1])
+    bad.row_idx[a + 8192] = bad.row_idx[a + 8191]   # first entry of the column's second segment
+    with pytest.raises(cox.CoxError) as e:
+        cox.Handle(bad, o)
+    assert e.value.code == cox.COX_E_INVALID

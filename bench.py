@@ -96,8 +96,8 @@ ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 # the same kernel on the same workload (launch total / steps it ran); the summaries and commands
 # are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
 TRAFFIC = {
-    ("incremental", "stratified_sparse", "fp64"): (157.739264e6 + 35.210752e6) / 2001,
-    ("incremental", "time_varying", "fp64"): (1157.1456e6 + 5891.47136e6) / 20001,
+    ("incremental", "stratified_sparse", "fp64"): (156.35328e6 + 35.009536e6) / 2001,
+    ("incremental", "time_varying", "fp64"): (1082.671872e6 + 5862.565888e6) / 20001,
 }
 
 
@@ -337,6 +337,83 @@ def run_time_varying(args):
             "roofline": roof}
 
 
+def run_tvc(args):
+    """A treatment coefficient that steps at day 10 (the paper's cough analysis shape, §2.3 and
+    §3.3): 407,828 subjects, 9,666 baseline covariates at ~3 % density. One step = the
+    interval-stratified view built on the device from the unsplit arrays (cox_create_split) +
+    the L1 fit + destroy, inputs resident in HBM."""
+    import types
+    import torch
+    from paper_2310_16238_gb300 import cox
+    n = int(407_828 * args.scale)
+    data, opts = synth.tvc_cohort(n=n)
+    cuts, tvc = [10], [0]
+    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ddev = synth.CoxData(**{**data.__dict__})
+    for f in ("stop", "event", "col_ptr", "row_idx"):
+        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    times, view_ms, infos = [], [], []
+    launches0 = None
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + args.steps):
+                if k == args.warmup:
+                    launches0 = cox.cox_launch_count()
+                flush.fill_(float(k))
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                h = cox.cox_create_split(ddev, cuts, tvc, opts, precision=precision, stream=stream.cuda_stream)
+                e[1].record(stream)
+                try:
+                    beta, info = cox.cox_fit(h)
+                finally:
+                    cox.cox_destroy(h)
+                e[2].record(stream)
+                e[2].synchronize()
+                if k >= args.warmup:
+                    times.append(e[0].elapsed_time(e[2]))
+                    view_ms.append(e[0].elapsed_time(e[1]))
+                    infos.append(info)
+        torch.cuda.synchronize()
+    launches = cox.cox_launch_count() - launches0
+    h = cox.cox_create_split(data, cuts, tvc, opts, precision=precision)
+    md = cox.cox_metadata(h)
+    cox.cox_destroy(h)
+    n_view = int(md["strata_start"][-1])
+    # the view's shape for the roofline: rows, columns and nonzeros per column
+    reach = 1 + (data.stop >= cuts[0]).astype(np.int64)
+    per_col = np.add.reduceat(reach[data.row_idx], data.col_ptr[:-1]) if data.nnz else np.zeros(data.p, np.int64)
+    per_col[np.diff(data.col_ptr) == 0] = 0
+    t0 = data.row_idx[data.col_ptr[0]:data.col_ptr[1]]
+    view_cols = np.concatenate([[len(t0), int(np.sum(data.stop[t0] >= cuts[0]))], per_col[1:]])
+    vshape = types.SimpleNamespace(n=n_view, start=None, p=len(view_cols),
+                                   col_ptr=np.concatenate([[0], np.cumsum(view_cols)]))
+    ms = float(np.mean(times))
+    coords = float(np.mean([i["coord_updates"] for i in infos]))
+    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
+    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
+    wname = (f"tvc_cohort subjects={n} p=9666+treatment density logU[1.4e-3,0.14] cut=10 "
+             f"view rows={n_view} p_view={vshape.p} L1 gamma=1e-4*N")
+    roof = roofline_of(engine, vshape, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
+                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
+    return {"metric": "coordinate updates/sec (CCD, time-varying coefficient via the interval-stratified view, "
+                      "one fit per step)",
+            "value": coords / (ms * 1e-3), "unit": "coord_updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4),
+            "data": "synthetic (seeded; paper cohort unavailable)",
+            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
+                       "loglik": infos[-1]["loglik"], "step_us": step_us, "engine": engine,
+                       "view_build_ms": float(np.mean(view_ms)), "beta_treatment": [float(beta[0]), float(beta[1])],
+                       "l2": "flushed before every step (512 MB write)"},
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
 def run_batch(args):
     """256 fits (4 outcomes x 4 folds x 16 L1 weights) over one shared binary X: one-at-a-time
     FP64 vs the batched persistent launch (FP64 and FP32C, autotuned tile length)."""
@@ -502,7 +579,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="stratified", choices=["stratified", "time_varying", "batch", "serving"])
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "time_varying", "tvc", "batch", "serving"])
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-rows", type=int, default=2_000_000)
@@ -517,7 +594,8 @@ def main():
             print(json.dumps(res), flush=True)
         return
     if args.workload != "stratified":
-        fn = {"time_varying": run_time_varying, "batch": run_batch, "serving": run_serving}[args.workload]
+        fn = {"time_varying": run_time_varying, "tvc": run_tvc, "batch": run_batch,
+              "serving": run_serving}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:

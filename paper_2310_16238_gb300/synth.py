@@ -281,6 +281,54 @@ def time_varying(n_subj: int = 1_000_000, p: int = 5000, k: int = 20, density: f
     return data, CoxOptions(penalty=PEN_L2, l2_var=l2_var, tol=1e-8)
 
 
+def tvc_cohort(n: int = 407_828, p: int = 9_666, cut: int = 10, dens_lo: float = 1.4e-3, dens_hi: float = 0.14,
+               hr_early: float = 0.98, hr_late: float = 0.67, event_frac: float = 0.10, max_days: int = 1095,
+               n_support: int = 50, lam_per_n: float = 1e-4, seed: int = SEED_BASE + 6):
+    """A new-user cohort with a treatment whose effect steps at day ``cut`` (paper §3.3 shape:
+    407,828 patients, 9,666 baseline covariates at about 97 % sparsity, the treatment split
+    into before / after day 10).
+
+    Column 0 is the treatment (Bernoulli 0.5), columns 1..p binary baseline covariates with
+    density log-uniform in [dens_lo, dens_hi] (mean 3 %). ``n_support`` baseline coefficients
+    ~ N(0, 0.3^2). Hazard h exp(x'beta) times hr_early^treat before ``cut`` and hr_late^treat
+    after it, with h chosen by bisection for ~``event_frac`` events; censoring uniform on
+    [1, max_days]; Y = ceil(min(T, C)). Options: L1 with gamma = lam_per_n * n on the baseline
+    covariates, the treatment unpenalized (the penalize mask is over the split columns: the
+    treatment's two copies first).
+    """
+    rng = np.random.default_rng(seed)
+    treat = rng.random(n) < 0.5
+    dens = np.exp(rng.uniform(math.log(dens_lo), math.log(dens_hi), p))
+    cols = [np.flatnonzero(treat)]
+    for j in range(p):
+        m = int(rng.binomial(n, dens[j]))
+        cols.append(np.sort(rng.choice(n, size=m, replace=False)))
+    beta = np.zeros(p + 1)
+    sup = 1 + rng.choice(p, size=min(n_support, p), replace=False)
+    beta[sup] = rng.normal(0.0, 0.3, len(sup))
+    eta = np.zeros(n)
+    for j in sup:
+        eta[cols[j]] += beta[j]
+    c1 = np.where(treat, hr_early, 1.0)
+    c2 = np.where(treat, hr_late, 1.0)
+    e_draw = rng.exponential(1.0, n)
+    cens = rng.uniform(1.0, max_days, n)
+
+    def times(hh):
+        w = hh * np.exp(eta)
+        h_cut = w * c1 * cut                              # cumulative hazard at the cut
+        return np.where(e_draw < h_cut, e_draw / (w * c1), cut + (e_draw - h_cut) / (w * c2))
+
+    h = _bisect(lambda hh: float(np.mean(times(hh) <= cens)), 1e-12, 1e3, event_frac, increasing=True)
+    t = times(h)
+    ev = (t <= cens).astype(np.uint8)
+    y = np.maximum(np.ceil(np.minimum(t, cens)), 1).astype(np.int64)
+    data = finalize(y, ev, None, None, cols, None, p + 1, beta, "tvc_cohort")
+    pen = np.ones(p + 2, np.uint8)
+    pen[:2] = 0
+    return data, CoxOptions(penalty=PEN_L1, lam=lam_per_n * n, tol=1e-8, penalize=pen)
+
+
 def subset_rows(data: CoxData, rows: np.ndarray) -> CoxData:
     """Restrict a data set to ``rows`` (sorted row ids); keeps the sort order."""
     rows = np.asarray(rows, dtype=np.int64)

@@ -334,6 +334,21 @@ int copy_out(cox_handle *h, double *dst, const double *src, int64_t count) {
 }
 
 // The whole fit in one cooperative launch of the resident kernel (state already initialized).
+ResParams res_params(cox_handle *h) {
+  const Prepared &P = h->sd->prep;
+  ResParams prm{};
+  prm.F = h->hfit;
+  prm.D = D(h);
+  prm.tile_lo = P.res_tile_lo;
+  prm.tile_g = P.res_tile_g;
+  prm.tile_k = P.res_tile_k;
+  prm.col_tile = P.res_col_tile;
+  prm.tagg = h->r_tagg;
+  prm.tpart = h->r_tpart;
+  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * D(h).p + 2;
+  return prm;
+}
+
 int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   const DevData &d = D(h);
   const Prepared &P = h->sd->prep;
@@ -343,16 +358,7 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   if (cudaMemsetAsync(h->r_tagg, 0, 6 * RT * sizeof(uint64_t), s) != cudaSuccess ||
       cudaMemsetAsync(h->r_tpart, 0, 12 * RT * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
-  ResParams prm{};
-  prm.F = h->hfit;
-  prm.D = d;
-  prm.tile_lo = P.res_tile_lo;
-  prm.tile_g = P.res_tile_g;
-  prm.tile_k = P.res_tile_k;
-  prm.col_tile = P.res_col_tile;
-  prm.tagg = h->r_tagg;
-  prm.tpart = h->r_tpart;
-  prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * d.p + 2;
+  ResParams prm = res_params(h);
   // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
   const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
@@ -452,7 +458,7 @@ IncParams incr_params(cox_handle *h, bool compact) {
 }
 
 // The fit's result from its control block (already read into h_ctl).
-int incr_result(cox_handle *h, double *beta_out, cox_fit_info *info, float ms) {
+int incr_result(cox_handle *h, double *beta_out, cox_fit_info *info, float ms, int64_t launches) {
   int rc;
   if ((rc = device_error(h))) return rc;
   const FitCtl &c = *h->h_ctl;
@@ -466,7 +472,7 @@ int incr_result(cox_handle *h, double *beta_out, cox_fit_info *info, float ms) {
     info->objective = c.obj;
     info->status = rc;
     info->engine = COX_ENGINE_INCR;
-    info->step_launches = 1;
+    info->step_launches = launches;
     info->sweep_ms = ms;
   }
   const int rc2 = copy_out(h, beta_out, h->hfit.beta, D(h).p);
@@ -559,7 +565,7 @@ int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, dou
       for (int i : waves[w]) {
         cox_handle *h = hs[i];
         int r = read_ctl(h);
-        if (!r) r = incr_result(h, beta_out[i], info ? info + i : nullptr, wms[w]);
+        if (!r) r = incr_result(h, beta_out[i], info ? info + i : nullptr, wms[w], 1);
         if (r == COX_E_RANGE && h->opts.engine == COX_ENGINE_AUTO) {
           // beyond the double-word range: this fit again on an FP64 engine
           h->stream = saved[i];
@@ -600,10 +606,47 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
   cudaEventRecord(h->ev0, s);
-  if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
-  cudaEventRecord(h->ev1, s);
   int rc;
-  if ((rc = read_ctl(h))) return rc;
+  int64_t launches = 1;
+  if (P.inc_n_halt == 0) {
+    if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+    cudaEventRecord(h->ev1, s);
+    if ((rc = read_ctl(h))) return rc;
+  } else {
+    // columns too dense for the lists are stepped by the resident kernel: the incremental launch
+    // halts before such a column; one resident launch then steps the run of them and the column
+    // after it (whose step applies the last dense update), and the incremental kernel resumes
+    // from the shared state (eta, v, beta, trust and the control block)
+    if (P.res_T <= 0 || !h->r_tagg) return fail(h, COX_E_INVALID, "cox_fit: dense columns need the resident kernel");
+    if (cudaMemsetAsync(h->r_tagg, 0, 6 * P.res_T * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(h->r_tpart, 0, 12 * P.res_T * sizeof(uint64_t), s) != cudaSuccess)
+      return cuda_fail(h, "memset");
+    prm.halt = P.inc_halt;
+    ResParams rprm = res_params(h);
+    const std::vector<uint8_t> &halt = P.h_inc_halt;
+    const int32_t p = d.p;
+    int64_t left = prm.max_steps;
+    launches = 0;
+    if ((rc = read_ctl(h))) return rc;
+    while (h->h_ctl->state == kRunning && !h->h_ctl->error && left > 0) {
+      const int64_t before = h->h_ctl->coord_updates;
+      const int32_t j = h->h_ctl->j;
+      if (!halt[size_t(j)]) {
+        prm.max_steps = left;
+        if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+      } else {
+        int64_t k = 0;
+        for (int32_t jj = j; k < p && halt[size_t(jj)]; jj = jj + 1 >= p ? 0 : jj + 1) ++k;
+        rprm.max_steps = std::min<int64_t>(k + 1, left);
+        if (launch_resident(h->sd->precision, rprm, P.res_T, s)) return cuda_fail(h, "resident launch");
+      }
+      ++launches;
+      if ((rc = read_ctl(h))) return rc;
+      left -= std::max<int64_t>(1, h->h_ctl->coord_updates - before);
+    }
+    cudaEventRecord(h->ev1, s);
+    if (cudaEventSynchronize(h->ev1) != cudaSuccess) return cuda_fail(h, "event");
+  }
   if (prm.trace_steps > 0) {
     // per CTA, mean SM clocks between consecutive phase points of thread 0 (update | patch | scan
     // | barrier | S0 | ratios | group sums | barrier | CTA sums | barrier | push | inbox | barrier
@@ -653,7 +696,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   }
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-  return incr_result(h, beta_out, info, ms);
+  return incr_result(h, beta_out, info, ms, launches);
 }
 
 }  // namespace

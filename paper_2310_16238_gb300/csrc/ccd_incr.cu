@@ -91,6 +91,7 @@ int inc_pos_cap() { return kIncPosCap; }
 // Step-synchronous control state, identical in every CTA.
 struct IncState {
   int32_t j, sweep, need_ll, pend_j, state;
+  int32_t halt;              // the next column is a halt column: end the launch before it
   double pend_db, obj_prev, bdx, pen, loglik, obj;
   dw E;                      // e^pend_db - 1
   int64_t coord_updates;
@@ -104,7 +105,7 @@ struct IncState {
 struct IncPre {
   double dx, b, t;
   dw dxw, bw, tw;
-  int32_t pen;
+  int32_t pen, halt_next;
 };
 
 // ---- epoch-tagged exchange words: (epoch << 32) | 32 data bits; relaxed 8-byte accesses are
@@ -515,6 +516,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     st.coord_updates = ctl->coord_updates;
     st.epoch = ctl->epoch;
     st.E = st.pend_j >= 0 ? dw_from(expm1(st.pend_db)) : dw_make(0.0f);
+    st.halt = 0;
     s_half_inv_var = 0.5 / F.l2_var;
     s_inv_var_dw = dw_from(1.0 / F.l2_var);
     s_lambda_dw = dw_from(F.lambda);
@@ -624,13 +626,17 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const int j1 = st.j, j2 = st.j + 1 >= p ? 0 : st.j + 1;
     inc_load_list(prm, t, j1, lo, npos, lpos + kIncListCap, lv + kIncListCap, le + kIncListCap, &s_cnt[1], 0, kIncThreads,
                   &s_err);
-    inc_load_list(prm, t, j2, lo, npos, lpos + 2 * kIncListCap, lv + 2 * kIncListCap, le + 2 * kIncListCap, &s_cnt[2], 0,
-                  kIncThreads, &s_err);
+    if (prm.halt && prm.halt[j2]) {   // the launch ends before it
+      if (tid == 0) s_cnt[2] = 0;
+    } else {
+      inc_load_list(prm, t, j2, lo, npos, lpos + 2 * kIncListCap, lv + 2 * kIncListCap, le + 2 * kIncListCap, &s_cnt[2],
+                    0, kIncThreads, &s_err);
+    }
   }
   __syncthreads();
   bool refreshed = false;  // the last step taken rebuilt v from eta
 
-  for (int64_t step = 0; step < prm.max_steps && st.state == kRunning; ++step) {
+  for (int64_t step = 0; step < prm.max_steps && st.state == kRunning && !st.halt; ++step) {
     const int j = st.j, pj = st.pend_j;
     const double db = st.pend_db;
     const bool need_ll = st.need_ll != 0;
@@ -895,13 +901,18 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         q.b = bet[j];
         q.t = tru[j];
         q.pen = F.penalize ? F.penalize[j] != 0 : 1;
+        q.halt_next = prm.halt ? prm.halt[j + 1 >= p ? 0 : j + 1] : 0;
         q.dxw = dw_from(q.dx);
         q.bw = dw_from(q.b);
         q.tw = dw_from(q.t);
         s_pre = q;
       }
-      inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap, &s_cnt[sf],
-                    C, kIncThreads - C, &s_err);
+      if (prm.halt && prm.halt[jf]) {   // the launch ends before it
+        if (tid == C) s_cnt[sf] = 0;
+      } else {
+        inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap,
+                      &s_cnt[sf], C, kIncThreads - C, &s_err);
+      }
     }
     __syncthreads();
     if (trace) trace[13] = uint64_t(clock64());
@@ -993,6 +1004,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           st.need_ll = 0;
         }
         st.j = jn;
+        st.halt = q.halt_next;
       }
       st.epoch = epoch + 1u;
       if (trace) trace[15] = uint64_t(clock64());

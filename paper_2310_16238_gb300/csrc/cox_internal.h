@@ -123,6 +123,7 @@ struct IncParams {
   double *bcopy;          // [C][2p] each CTA's copy of beta and the trust half-widths
   dw *vdw;                // [M] v per position as a double-word (the kernel's working copy)
   int64_t max_steps;      // coordinate steps this launch may take
+  const uint8_t *halt;    // [p] columns too dense for the lists: the launch stops before them (null: none)
   uint64_t *trace;        // optional [trace_steps][C][24] phase timestamps (ns) and counters
   int64_t trace_steps;
 };

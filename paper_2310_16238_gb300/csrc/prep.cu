@@ -494,9 +494,9 @@ __global__ void col_tile_kernel(int32_t p, int32_t T, const int64_t *col_ptr, co
   }
 }
 
-// Shortest run of risk positions that holds cap + 1 entries of one column, over every column
-// (one block per column segment; `scale` = position-space entries per nonzero): a tile shorter
-// than it holds at most cap entries of any column.
+// Per column, the shortest run of risk positions that holds cap + 1 of its entries (one block per
+// column segment; `scale` = position-space entries per nonzero): a tile shorter than it holds at
+// most cap entries of the column. out_min[j] starts at INT32_MAX.
 __global__ void window_kernel(const ColSeg *segs, int32_t scale, const uint32_t *idx, int32_t cap, int32_t *out_min) {
   const ColSeg sg = segs[blockIdx.x];
   const int64_t a = scale * sg.a, b = scale * sg.b, end = scale * sg.end;
@@ -508,7 +508,7 @@ __global__ void window_kernel(const ColSeg *segs, int32_t scale, const uint32_t 
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, off));
-  if ((threadIdx.x & 31) == 0 && best < 0x7fffffff) atomicMin(out_min, best);
+  if ((threadIdx.x & 31) == 0 && best < 0x7fffffff) atomicMin(&out_min[sg.j], best);
 }
 
 static bool is_device_ptr(const void *p) {
@@ -648,19 +648,27 @@ static int build_tile_tables(BufferSet &B, cudaStream_t s, const DevData &D, con
 }
 
 // Whether every column's entries in every tile of a plan fit the incremental kernel's lists.
-static int lists_fit(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, bool *fits) {
+// Columns holding more than the list capacity of entries in some tile of a plan (over[j] = 1).
+static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, std::vector<uint8_t> *over) {
   std::vector<int32_t> hct(size_t(D.p) * (T + 1));
   if (!hct.empty() && (cudaMemcpyAsync(hct.data(), ct, hct.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                        cudaStreamSynchronize(s) != cudaSuccess))
     return COX_E_CUDA;
-  *fits = true;
-  for (int32_t j = 0; j < D.p && *fits; ++j)
+  over->assign(size_t(D.p), 0);
+  for (int32_t j = 0; j < D.p; ++j)
     for (int32_t t = 0; t < T; ++t)
       if (hct[size_t(j) * (T + 1) + t + 1] - hct[size_t(j) * (T + 1) + t] > inc_list_cap()) {
-        *fits = false;
+        (*over)[j] = 1;
         break;
       }
   return COX_OK;
+}
+
+static int lists_fit(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, bool *fits) {
+  std::vector<uint8_t> over;
+  const int rc = list_overflow(D, ct, T, s, &over);
+  *fits = rc == COX_OK && std::find(over.begin(), over.end(), uint8_t(1)) == over.end();
+  return rc;
 }
 
 int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string *err) {
@@ -668,7 +676,7 @@ int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string
   P->cinc_T = -1;
   const DevData &D = P->desc;
   const int grid = inc_max_grid(precision);
-  if (P->inc_T <= 0 || grid <= 0) return COX_OK;
+  if (P->inc_T <= 0 || P->inc_n_halt > 0 || grid <= 0) return COX_OK;   // batches have no dense-column hand-over
   std::vector<int32_t> h_head(size_t(D.G));
   if (D.G > 0 && (cudaMemcpyAsync(h_head.data(), D.head_pos, size_t(D.G) * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
                       cudaSuccess ||
@@ -1033,43 +1041,86 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
     if (inc_grid > 0) {
       // candidate plans: equal tie groups per tile (the step's cost) with tiles shorter than the
       // shortest run of positions holding more entries of one column than the kernel's list
-      // capacity; then equal positions. The first whose lists fit is taken.
-      int32_t wmin = 0x7fffffff;
+      // capacity; then equal positions. The first whose lists fit is taken. A few columns too
+      // dense for any plan of at most inc_grid tiles (a treatment indicator held by half the
+      // rows) are left to the resident kernel: the incremental launch halts before them.
+      std::vector<int32_t> wcol(size_t(p), 0x7fffffff);
       {
-        int32_t *d_w = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
+        int32_t *d_w = static_cast<int32_t *>(sc.get(size_t(p) * sizeof(int32_t)));
         if (!d_w) return COX_E_OOM;
-        cudaMemcpyAsync(d_w, &wmin, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_w, wcol.data(), size_t(p) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         if (nseg > 0) count_launches(1);
         if (nseg > 0)
           window_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, counting ? 2 : 1, idx, inc_list_cap(), d_w);
-        if (cudaMemcpyAsync(&wmin, d_w, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(wcol.data(), d_w, size_t(p) * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
           *err = "cox_create: table kernels failed";
           return COX_E_CUDA;
         }
       }
-      out->inc_wmin = wmin;
-      const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(wmin) - 1);
-      std::vector<std::vector<int32_t>> cands;
-      if (pos_cap >= 32) cands.push_back(group_plan(D.M, pos_cap, inc_group_cap(), inc_grid, h_head));
-      cands.push_back(fit_plan(D.M, inc_pos_cap(), size_t(inc_group_cap()), inc_grid, h_head));
-      for (const auto &il : cands) {
-        if (il.empty()) continue;
+      // Plans in order of preference; a plan is taken when at most `allowed` columns overflow its
+      // lists (those become halt columns). First every column on the lists; failing that, the
+      // columns that overflow the equal-positions plan are handed over (at most max(2, p / 16)),
+      // and the group-balanced plan is built for the others.
+      const int64_t max_halt = out->res_T > 0 ? std::max<int64_t>(2, p / 16) : 0;
+      auto take = [&](const std::vector<int32_t> &il, int64_t allowed, const std::vector<uint8_t> &pre,
+                      bool *taken, std::vector<uint8_t> *halt_out) -> int {
+        *taken = false;
+        if (il.empty()) return COX_OK;
         int32_t *ilo = nullptr, *ig = nullptr, *ik = nullptr, *ict = nullptr;
-        if ((rc = tables(il, &ilo, &ig, &ik, &ict))) return rc;
+        int r = tables(il, &ilo, &ig, &ik, &ict);
+        if (r) return r;
         const int32_t IT = int32_t(il.size()) - 1;
-        bool fits = false;
-        if ((rc = lists_fit(D, ict, IT, s, &fits))) {
-          *err = "cox_create: table kernels failed";
-          return rc;
+        std::vector<uint8_t> over;
+        if ((r = list_overflow(D, ict, IT, s, &over))) return r;
+        int64_t n2 = 0;
+        for (int32_t j = 0; j < p; ++j) {
+          over[j] = over[j] | pre[j];
+          n2 += over[j];
         }
-        if (fits) {
-          out->inc_T = IT;
-          out->inc_tile_lo = ilo;
-          out->inc_tile_g = ig;
-          out->inc_tile_k = ik;
-          out->inc_col_tile = ict;
-          break;
+        *halt_out = over;
+        if (n2 > allowed || n2 >= p) return COX_OK;
+        out->inc_T = IT;
+        out->inc_tile_lo = ilo;
+        out->inc_tile_g = ig;
+        out->inc_tile_k = ik;
+        out->inc_col_tile = ict;
+        out->inc_n_halt = int32_t(n2);
+        if (n2 > 0) {
+          uint8_t *dh = static_cast<uint8_t *>(B.get(size_t(p)));
+          if (!dh || cudaMemcpyAsync(dh, over.data(), size_t(p), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return COX_E_OOM;
+          out->inc_halt = dh;
+          out->h_inc_halt = over;
+        }
+        *taken = true;
+        return COX_OK;
+      };
+      auto group_for = [&](const std::vector<uint8_t> &excl) {
+        int32_t wmin = 0x7fffffff;
+        for (int32_t j = 0; j < p; ++j)
+          if (!excl[j]) wmin = std::min(wmin, wcol[j]);
+        const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(wmin) - 1);
+        return pos_cap >= 32 ? group_plan(D.M, pos_cap, inc_group_cap(), inc_grid, h_head) : std::vector<int32_t>{};
+      };
+      const std::vector<uint8_t> none(size_t(p), 0);
+      std::vector<uint8_t> hset;
+      bool taken = false;
+      {
+        int32_t wmin = 0x7fffffff;
+        for (int32_t j = 0; j < p; ++j) wmin = std::min(wmin, wcol[j]);
+        out->inc_wmin = wmin;
+      }
+      const std::vector<int32_t> fp = fit_plan(D.M, inc_pos_cap(), size_t(inc_group_cap()), inc_grid, h_head);
+      if ((rc = take(group_for(none), 0, none, &taken, &hset))) return rc;
+      if (!taken && (rc = take(fp, 0, none, &taken, &hset))) return rc;
+      if (!taken && max_halt > 0 && !fp.empty()) {
+        const std::vector<uint8_t> over_f = hset;   // the equal-positions plan's overflow set
+        int64_t nf = 0;
+        for (uint8_t v : over_f) nf += v;
+        if (nf > 0 && nf <= max_halt) {
+          if ((rc = take(group_for(over_f), max_halt, over_f, &taken, &hset))) return rc;
+          if (!taken && (rc = take(fp, max_halt, over_f, &taken, &hset))) return rc;
         }
       }
     }

@@ -49,6 +49,10 @@ struct Prepared {
   int32_t inc_T = 0;
   int32_t *inc_tile_lo = nullptr, *inc_tile_g = nullptr, *inc_tile_k = nullptr, *inc_col_tile = nullptr;
   int32_t inc_wmin = 0x7fffffff;        // shortest run of positions overflowing a column's list
+  // columns too dense for the incremental lists: fits step them with the resident kernel
+  int32_t inc_n_halt = 0;
+  uint8_t *inc_halt = nullptr;          // [p] device, null when none
+  std::vector<uint8_t> h_inc_halt;      // [p] host copy
   // compact incremental plan (fewest tiles; batches), built on first use: 0 = not yet, -1 = none
   int32_t cinc_T = 0;
   int32_t *cinc_tile_lo = nullptr, *cinc_tile_g = nullptr, *cinc_tile_k = nullptr, *cinc_col_tile = nullptr;

@@ -132,3 +132,52 @@ def test_incr_batch_waves_match_oracle():
     finally:
         for h in handles:
             h.close()
+
+
+def _dense_column_data(n, dense_cols, p=10, seed=70, n_strata=3, counting=False):
+    """Sparse binary columns plus the listed columns held by about half the rows (a treatment
+    indicator): too dense for the incremental lists of any plan on one CTA per SM."""
+    rng = np.random.default_rng(seed)
+    stop = rng.integers(1, 400, n)
+    event = (rng.random(n) < 0.2).astype(np.uint8)
+    stratum = rng.integers(0, n_strata, n)
+    start = (stop - rng.integers(1, 80, n)) if counting else None
+    rows = []
+    for j in range(p):
+        dens = 0.5 if j in dense_cols else float(np.exp(rng.uniform(np.log(0.002), np.log(0.05))))
+        rows.append(np.flatnonzero(rng.random(n) < dens))
+    return synth.finalize(stop, event, stratum, start, rows, None, p)
+
+
+@pytest.mark.parametrize("dense_cols,counting,pen", [
+    ([3], False, "l1"), ([0, 1], False, "l2"), ([9], True, "l2"), ([0, 4, 47], False, "l1"),
+], ids=["one_mid_l1", "two_first_l2", "last_counting_l2", "three_l1"])
+def test_incr_hands_dense_columns_to_the_resident_kernel(dense_cols, counting, pen):
+    # at most max(2, p / 16) columns are handed over; more than that and the fit stays resident
+    d = _dense_column_data(420000 if not counting else 220000, dense_cols, p=10 if len(dense_cols) < 3 else 48,
+                           counting=counting)
+    o = (synth.CoxOptions(penalty=synth.PEN_L1, lam=20.0, tol=1e-9) if pen == "l1"
+         else synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-9))
+    with cox.Handle(d, o) as h:
+        beta, info = h.fit()
+        ll_eval = h.loglik(beta)
+    assert info["engine"] == cox.COX_ENGINE_INCR
+    assert info["step_launches"] > 2            # launches alternate at the dense columns
+    ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
+    assert _rel(beta, ob) <= 1e-9
+    scale = _ll_scale(d, ob, oi["loglik"])
+    assert abs(info["loglik"] - oi["loglik"]) <= 1e-11 * scale
+    assert abs(ll_eval - oracle.loglik(d, beta)) <= 1e-11 * scale
+    with cox.Handle(d, o, engine=cox.COX_ENGINE_RESIDENT) as h:
+        br, ir = h.fit()
+    assert ir["sweeps"] == info["sweeps"] and _rel(beta, br) <= 1e-9
+
+
+def test_too_many_dense_columns_stay_resident():
+    d = _dense_column_data(420000, [0, 4, 9], p=10)
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-9)
+    with cox.Handle(d, o) as h:
+        beta, info = h.fit()
+    assert info["engine"] == cox.COX_ENGINE_RESIDENT
+    ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
+    assert _rel(beta, ob) <= 1e-9

@@ -235,6 +235,38 @@ int cox_split_columns(int32_t p, const cox_split *split, int32_t *p_view);
 /* cox_create on the time-split view of `data`. The view's arrays live only during the call. */
 int cox_create_split(const cox_data *data, const cox_split *split, const cox_options *opts, cox_handle **out);
 
+/* ---------------------------------------------------------------- cross-validated penalty path
+ * K-fold cross-validation along a penalty path, the way the paper picks its L1 weight
+ * (10-fold CV, §3.2 and §3.3). Training set k = the rows whose fold id is not k (built on the
+ * device); the rows of one subject (counting-process rows) must share a fold id. The path is
+ * walked in the given order: at each value every training fit and the full-data fit start from
+ * their own fit at the previous value (warm start; zeros at the first), and the K + 1 fits of a
+ * value run together as one batch (cox_batch_fit). For L1 the path values are the weight gamma
+ * (opts.lambda), for L2 the prior variance sigma^2 (opts.l2_var); the other options apply to
+ * every fit. Score: the cross-validated partial log-likelihood (P. Verweij and H. van
+ * Houwelingen, Stat. Med. 12, 1993),
+ *     cvl = sum_k [ l(beta_-k) - l_-k(beta_-k) ],
+ * l the full data's log partial likelihood, l_-k training set k's, beta_-k the fit on training
+ * set k: the held-out rows' contribution with their risk sets formed on all the data.
+ *
+ *   cvl        n_path doubles (host)
+ *   beta_path  n_path x p doubles (host, row-major; NULL to skip): the full-data fits
+ *   info       n_path x (K + 1) (host; NULL to skip): per value, the K training fits then the
+ *              full-data fit
+ *   best       index of the largest cvl (NULL to skip)
+ * Returns the worst status over the fits. Errors: COX_E_INVALID (K < 2, n_path < 1, penalty
+ * NONE, fold ids outside [0, K), a path value that is negative (L1) or not positive (L2)), plus
+ * those of cox_create and cox_batch_fit. */
+typedef struct {
+  int32_t n_folds;          /* K >= 2 */
+  int32_t n_path;           /* >= 1 */
+  const int32_t *fold;      /* host or device, n_rows fold ids in [0, K) */
+  const double *path;       /* host, n_path penalty values */
+} cox_cv;
+
+int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv, double *cvl, double *beta_path,
+                cox_fit_info *info, int32_t *best);
+
 /* Bytes of device memory a handle for `data` would hold (for admission control). */
 int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
 

@@ -26,7 +26,7 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
-           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split",
+           "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split", "cox_cv_path",
            "cox_segscan_noalloc", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
@@ -64,6 +64,10 @@ class cox_fit_info(C.Structure):
 
 class cox_split(C.Structure):
     _fields_ = [("n_cuts", C.c_int32), ("n_tvc", C.c_int32), ("cuts", C.c_void_p), ("tvc_cols", C.c_void_p)]
+
+
+class cox_cv(C.Structure):
+    _fields_ = [("n_folds", C.c_int32), ("n_path", C.c_int32), ("fold", C.c_void_p), ("path", C.c_void_p)]
 
 
 class cox_server_options(C.Structure):
@@ -115,6 +119,8 @@ def lib():
             L.cox_footprint.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_size_t)]
             L.cox_split_columns.argtypes = [i32, C.POINTER(cox_split), C.POINTER(i32)]
             L.cox_create_split.argtypes = [C.POINTER(cox_data), C.POINTER(cox_split), C.POINTER(cox_options), C.POINTER(vp)]
+            L.cox_cv_path.argtypes = [C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(cox_cv), vp, vp,
+                                      C.POINTER(cox_fit_info), C.POINTER(i32)]
             L.cox_launch_count.argtypes = []
             L.cox_launch_count.restype = i64
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
@@ -239,6 +245,39 @@ def cox_create_split(data, cuts, tvc_cols=(), opts=None, precision=COX_FP64, str
     _check(lib().cox_create_split(C.byref(d), C.byref(sp), C.byref(o), C.byref(h)))
     _P_CACHE[h.value] = cox_split_columns(data.p, cuts, tvc_cols)
     return h
+
+
+def cox_cv_path(data, folds, path, opts, n_folds=None, precision=COX_FP64, stream=None, engine=COX_ENGINE_AUTO):
+    """Cross-validated penalty path (cox_cv_path): ``folds`` holds a fold id per row, ``path``
+    the L1 weights (or L2 variances) in the order to walk. Returns a dict with ``cvl`` (per path
+    value), ``beta`` (n_path x p full-data fits), ``best`` (index of the largest cvl) and
+    ``info`` (per value: the training fits, then the full-data fit)."""
+    d, keep = make_data(data)
+    o, pen = make_options(opts, precision, stream, 0, engine)
+    f = folds.contiguous() if hasattr(folds, "data_ptr") else np.ascontiguousarray(folds, dtype=np.int32)
+    K = int(n_folds) if n_folds is not None else int((f.max().item() if hasattr(f, "data_ptr") else f.max()) + 1)
+    pth = np.ascontiguousarray(path, dtype=np.float64)
+    L = int(pth.shape[0])
+    cv = cox_cv(K, L, _ptr(f), _ptr(pth))
+    cvl = np.zeros(L)
+    beta = np.zeros((L, max(int(data.p), 1)))
+    infos = (cox_fit_info * (L * (K + 1)))()
+    best = C.c_int32(-1)
+    rc = _check(lib().cox_cv_path(C.byref(d), C.byref(o), C.byref(cv), _ptr(cvl), _ptr(beta), infos, C.byref(best)))
+    info = [[infos[i * (K + 1) + m].as_dict() for m in range(K + 1)] for i in range(L)]
+    return dict(cvl=cvl, beta=beta[:, :int(data.p)], best=int(best.value), info=info, status=rc)
+
+
+def make_folds(n_rows, n_folds, seed=0, subject=None):
+    """Fold id per row: subjects (``subject[r]``, default one per row) dealt to the folds in a
+    seeded random order, so the folds differ in size by at most one subject."""
+    rng = np.random.default_rng(seed)
+    subj = np.arange(n_rows) if subject is None else np.asarray(subject)
+    uniq, inv = np.unique(subj, return_inverse=True)
+    order = rng.permutation(len(uniq))
+    fold_of = np.empty(len(uniq), np.int32)
+    fold_of[order] = np.arange(len(uniq)) % n_folds
+    return fold_of[inv].astype(np.int32)
 
 
 def cox_fit(h, beta0=None, out=None):

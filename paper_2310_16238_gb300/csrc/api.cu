@@ -781,6 +781,102 @@ int cox_create_split(const cox_data *data, const cox_split *split, const cox_opt
   return rc;
 }
 
+int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv, double *cvl, double *beta_path,
+                cox_fit_info *info, int32_t *best) {
+  if (!data || !opts || !cv || !cvl) return fail(nullptr, COX_E_INVALID, "cox_cv_path: null argument");
+  const int32_t K = cv->n_folds, L = cv->n_path;
+  if (K < 2 || L < 1 || !cv->fold || !cv->path) return fail(nullptr, COX_E_INVALID, "cox_cv_path: need n_folds >= 2, n_path >= 1, fold ids and the path");
+  if (opts->penalty != COX_PEN_L1 && opts->penalty != COX_PEN_L2)
+    return fail(nullptr, COX_E_INVALID, "cox_cv_path: the path needs an L1 or L2 penalty");
+  for (int32_t i = 0; i < L; ++i)
+    if (opts->penalty == COX_PEN_L1 ? !(cv->path[i] >= 0.0) : !(cv->path[i] > 0.0))
+      return fail(nullptr, COX_E_INVALID, "cox_cv_path: path values must be >= 0 (L1 weights) or > 0 (L2 variances)");
+  if (check_options(opts)) return fail(nullptr, COX_E_INVALID, "cox_cv_path: invalid options");
+  cox_options o = *opts;
+  auto set_value = [&](int32_t i) {
+    if (o.penalty == COX_PEN_L1) o.lambda = cv->path[i];
+    else o.l2_var = cv->path[i];
+  };
+  set_value(0);
+  const int32_t p = data->p;
+  std::vector<cox_handle *> hs(size_t(K) + 1, nullptr);
+  auto release = [&]() {
+    for (cox_handle *h : hs) cox_destroy(h);
+  };
+  // training sets on the device, then the full data set (last)
+  {
+    cudaStream_t s = o.stream ? static_cast<cudaStream_t>(o.stream) : nullptr;
+    cudaStream_t own = nullptr;
+    if (!s) {
+      if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(nullptr, COX_E_CUDA, "cox_cv_path: stream create");
+      s = own;
+    }
+    int rc = COX_OK;
+    for (int32_t k = 0; k < K && !rc; ++k) {
+      BufferSet vb;
+      cox_data view{};
+      std::string err;
+      rc = build_fold_view(data, cv->fold, k, K, s, vb, &view, &err);
+      if (rc) {
+        cudaGetLastError();
+        rc = fail(nullptr, rc, err.empty() ? "cox_cv_path: training set construction failed" : err);
+        break;
+      }
+      rc = cox_create(&view, &o, &hs[size_t(k)]);
+    }
+    if (own) cudaStreamDestroy(own);
+    if (!rc) rc = cox_create(data, &o, &hs[size_t(K)]);
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
+  const size_t n = size_t(K) + 1;
+  std::vector<std::vector<double>> prev(n, std::vector<double>(size_t(std::max(p, 1)))), cur = prev;
+  std::vector<const double *> b0(n);
+  std::vector<double *> bo(n);
+  std::vector<cox_fit_info> fi(n);
+  int worst = COX_OK;
+  int rc = COX_OK;
+  for (int32_t i = 0; i < L && rc >= 0; ++i) {
+    set_value(i);
+    for (size_t m = 0; m < n && rc >= 0; ++m) rc = cox_set_options(hs[m], &o);
+    if (rc < 0) break;
+    for (size_t m = 0; m < n; ++m) {
+      b0[m] = prev[m].data();
+      bo[m] = cur[m].data();
+    }
+    rc = cox_batch_fit(hs.data(), int32_t(n), i == 0 ? nullptr : b0.data(), bo.data(), fi.data());
+    if (rc < 0) break;
+    if (rc > worst) worst = rc;
+    double score = 0.0;
+    for (int32_t k = 0; k < K && rc >= 0; ++k) {
+      double l_full = 0.0, l_train = 0.0;
+      if ((rc = cox_loglik(hs[size_t(K)], cur[size_t(k)].data(), &l_full)) < 0) break;
+      if ((rc = cox_loglik(hs[size_t(k)], cur[size_t(k)].data(), &l_train)) < 0) break;
+      score += l_full - l_train;
+    }
+    if (rc < 0) break;
+    cvl[i] = score;
+    if (beta_path && p > 0) std::memcpy(beta_path + size_t(i) * p, cur[size_t(K)].data(), size_t(p) * sizeof(double));
+    if (info)
+      for (size_t m = 0; m < n; ++m) info[size_t(i) * n + m] = fi[m];
+    std::swap(prev, cur);
+    rc = COX_OK;
+  }
+  if (rc >= 0 && best) {
+    int32_t bi = 0;
+    for (int32_t i = 1; i < L; ++i)
+      if (cvl[i] > cvl[bi]) bi = i;
+    *best = bi;
+  }
+  std::string msg = rc < 0 ? std::string(cox_last_error(nullptr)) : std::string();
+  release();
+  if (rc < 0) return fail(nullptr, rc, msg);
+  return worst;
+}
+
 int cox_clone(const cox_handle *src, const cox_options *opts, cox_handle **out) {
   if (!src || !out) return fail(nullptr, COX_E_INVALID, "cox_clone: null argument");
   *out = nullptr;

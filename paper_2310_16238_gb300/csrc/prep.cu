@@ -1380,4 +1380,133 @@ int build_split_view(const cox_data *in, const cox_split *sp, cudaStream_t s, Bu
   return COX_OK;
 }
 
+// ------------------------------------------------------------------ training-fold view
+// The rows of a data set whose fold id differs from k, in their order (so still sorted), with
+// the CSC restricted to them: row ranks by a prefix count of the kept rows, entries by a prefix
+// count of the kept entries (a column's kept entries stay contiguous and ascending).
+__global__ void fold_keep_kernel(int64_t n, const int32_t *fold, int32_t k, int32_t K, int32_t *keep, int32_t *err) {
+  int32_t e = 0;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t f = fold[r];
+    if (f < 0 || f >= K) e = 1;
+    keep[r] = f != k ? 1 : 0;
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void subset_rows_kernel(int64_t n, const int32_t *keep, const int64_t *pre, const int32_t *stop,
+                                   const int32_t *start, const uint8_t *event, const int32_t *stratum, int32_t *v_stop,
+                                   int32_t *v_start, uint8_t *v_event, int32_t *v_stratum) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x) {
+    if (!keep[r]) continue;
+    const int64_t i = pre[r];
+    v_stop[i] = stop[r];
+    v_event[i] = event[r];
+    if (v_start) v_start[i] = start[r];
+    if (v_stratum) v_stratum[i] = stratum[r];
+  }
+}
+
+__global__ void subset_entry_flags_kernel(int64_t nnz, const int32_t *row_idx, const int32_t *keep, int32_t *eflag) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nnz; q += int64_t(gridDim.x) * blockDim.x)
+    eflag[q] = keep[row_idx[q]];
+}
+
+__global__ void subset_entries_kernel(int64_t nnz, const int32_t *row_idx, const double *val, const int32_t *eflag,
+                                      const int64_t *epre, const int64_t *row_pre, int32_t *v_row, double *v_val) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nnz; q += int64_t(gridDim.x) * blockDim.x) {
+    if (!eflag[q]) continue;
+    const int64_t e = epre[q];
+    v_row[e] = int32_t(row_pre[row_idx[q]]);
+    if (v_val) v_val[e] = val[q];
+  }
+}
+
+__global__ void subset_colptr_kernel(int32_t p, const int64_t *col_ptr, int64_t nnz, const int64_t *epre, int64_t E,
+                                     int64_t *v_col_ptr) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j <= p; j += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t a = j < p ? col_ptr[j] : nnz;
+    v_col_ptr[j] = a < nnz ? epre[a] : E;
+  }
+}
+
+int build_fold_view(const cox_data *in, const int32_t *fold, int32_t k, int32_t K, cudaStream_t s, BufferSet &B,
+                    cox_data *view, std::string *err) {
+  Scratch sc;
+  if (!fold || K < 2 || k < 0 || k >= K) {
+    *err = "cox_cv_path: need fold ids and 0 <= k < n_folds, n_folds >= 2";
+    return COX_E_INVALID;
+  }
+  Staged st;
+  int rc = stage_inputs(in, sc, s, &st, err);
+  if (rc) return rc;
+  const int64_t n = st.n, nnz = st.nnz;
+  const int32_t p = st.p;
+  const int64_t nn = n > 0 ? n : 1;
+  const int32_t *dfold = device_view(fold, n, sc, s, &rc);
+  int32_t *keep = static_cast<int32_t *>(sc.get(nn * sizeof(int32_t)));
+  int64_t *row_pre = static_cast<int64_t *>(sc.get(nn * sizeof(int64_t)));
+  int32_t *d_err = static_cast<int32_t *>(sc.get(sizeof(int32_t)));
+  if (rc || !keep || !row_pre || !d_err) return rc ? rc : COX_E_OOM;
+  cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
+  int64_t M = 0;
+  if (n > 0) {
+    count_launches(1);
+    fold_keep_kernel<<<grid_for(n), 256, 0, s>>>(n, dfold, k, K, keep, d_err);
+    if ((rc = exclusive_scan(keep, n, row_pre, &M, sc, s))) return rc;   // synchronizes
+  }
+  int32_t h_err = 0;
+  if (cudaMemcpy(&h_err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return COX_E_CUDA;
+  if (h_err) {
+    *err = "cox_cv_path: fold ids must lie in [0, n_folds)";
+    return COX_E_INVALID;
+  }
+  const int64_t mm = M > 0 ? M : 1;
+  int32_t *v_stop = static_cast<int32_t *>(B.get(mm * sizeof(int32_t)));
+  int32_t *v_start = st.start ? static_cast<int32_t *>(B.get(mm * sizeof(int32_t))) : nullptr;
+  uint8_t *v_event = static_cast<uint8_t *>(B.get(mm));
+  int32_t *v_stratum = st.stratum ? static_cast<int32_t *>(B.get(mm * sizeof(int32_t))) : nullptr;
+  if (!v_stop || (st.start && !v_start) || !v_event || (st.stratum && !v_stratum)) return COX_E_OOM;
+  if (n > 0) {
+    count_launches(1);
+    subset_rows_kernel<<<grid_for(n), 256, 0, s>>>(n, keep, row_pre, st.stop, st.start, st.event, st.stratum, v_stop,
+                                                   v_start, v_event, v_stratum);
+  }
+  const int64_t ne = nnz > 0 ? nnz : 1;
+  int32_t *eflag = static_cast<int32_t *>(sc.get(ne * sizeof(int32_t)));
+  int64_t *epre = static_cast<int64_t *>(sc.get(ne * sizeof(int64_t)));
+  if (!eflag || !epre) return COX_E_OOM;
+  int64_t E = 0;
+  if (nnz > 0) {
+    count_launches(1);
+    subset_entry_flags_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, st.row_idx, keep, eflag);
+    if ((rc = exclusive_scan(eflag, nnz, epre, &E, sc, s))) return rc;
+  }
+  int64_t *v_col_ptr = static_cast<int64_t *>(B.get((size_t(p) + 1) * sizeof(int64_t)));
+  int32_t *v_row = static_cast<int32_t *>(B.get((E > 0 ? E : 1) * sizeof(int32_t)));
+  double *v_val = st.val ? static_cast<double *>(B.get((E > 0 ? E : 1) * sizeof(double))) : nullptr;
+  if (!v_col_ptr || !v_row || (st.val && !v_val)) return COX_E_OOM;
+  if (nnz > 0) {
+    count_launches(1);
+    subset_entries_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, st.row_idx, st.val, eflag, epre, row_pre, v_row, v_val);
+  }
+  count_launches(1);
+  subset_colptr_kernel<<<grid_for(int64_t(p) + 1), 256, 0, s>>>(p, st.col_ptr, nnz, epre, E, v_col_ptr);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaPeekAtLastError() != cudaSuccess) {
+    *err = "cox_cv_path: fold view kernels failed";
+    return COX_E_CUDA;
+  }
+  *view = cox_data{};
+  view->n_rows = M;
+  view->p = p;
+  view->stop = v_stop;
+  view->start = v_start;
+  view->event = v_event;
+  view->stratum = v_stratum;
+  view->col_ptr = v_col_ptr;
+  view->row_idx = v_row;
+  view->val = v_val;
+  return COX_OK;
+}
+
 }  // namespace coxgb

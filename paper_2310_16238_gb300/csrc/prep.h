@@ -66,6 +66,10 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
 int split_columns(int32_t p, const cox_split *sp, int32_t *p_view, std::string *err);
 int build_split_view(const cox_data *in, const cox_split *sp, cudaStream_t s, BufferSet &B, cox_data *view,
                      std::string *err);
+// The rows whose fold id differs from k (a cross-validation training set), built on the device;
+// arrays owned by `B`. Fold ids outside [0, K) are an error.
+int build_fold_view(const cox_data *in, const int32_t *fold, int32_t k, int32_t K, cudaStream_t s, BufferSet &B,
+                    cox_data *view, std::string *err);
 // Build (once) the incremental kernel's compact plan of a prepared data set (fewest tiles).
 int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string *err);
 

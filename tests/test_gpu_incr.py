@@ -181,3 +181,14 @@ def test_too_many_dense_columns_stay_resident():
     assert info["engine"] == cox.COX_ENGINE_RESIDENT
     ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
     assert _rel(beta, ob) <= 1e-9
+
+
+def test_dense_column_hand_over_fp32c():
+    d = _dense_column_data(420000, [2], p=10, seed=71)
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-9)
+    with cox.Handle(d, o, precision=cox.COX_FP32C) as h:
+        beta, info = h.fit()
+    assert info["engine"] == cox.COX_ENGINE_INCR and info["step_launches"] > 2
+    ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
+    assert _rel(beta, ob) <= 1e-5
+    assert abs(info["loglik"] - oi["loglik"]) <= 1e-7 * _ll_scale(d, ob, oi["loglik"])

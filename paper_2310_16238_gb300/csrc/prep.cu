@@ -184,38 +184,100 @@ static unsigned grid_for(int64_t n, int threads = 256, int64_t cap = 65536) {
   return unsigned(g);
 }
 
-// ------------------------------------------------------------------ stable split radix sort
-__global__ void bit_flags_kernel(const uint64_t *key, int64_t n, int bit, int32_t *flag) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    flag[i] = int32_t((key[i] >> bit) & 1u);
+// ------------------------------------------------------------------ stable LSD radix sort
+// Keys are sorted on a listed set of bit positions, four at a time (16 buckets per pass): per
+// tile of kSortTile keys a digit histogram, one exclusive scan of the histograms in
+// (digit, tile) order, then a stable scatter that ranks each key among the equal digits before
+// it in its tile (per round of 256 keys: warp match masks, then the counts of the earlier warps).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+struct SortDigit {
+  int32_t nb;       // bits in this digit (1..4)
+  int32_t pos[4];   // their positions in the key, least significant first
+};
+
+__device__ __forceinline__ int sort_digit(uint64_t k, const SortDigit &d) {
+  int v = 0;
+  for (int i = 0; i < d.nb; ++i) v |= int((k >> d.pos[i]) & 1u) << i;
+  return v;
 }
 
-__global__ void split_scatter_kernel(const uint64_t *key, const uint32_t *pay, const int32_t *flag, const int64_t *ones_before,
-                                     int64_t n, int64_t n_zero, uint64_t *key_out, uint32_t *pay_out) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t dst = flag[i] ? n_zero + ones_before[i] : i - ones_before[i];
-    key_out[dst] = key[i];
-    pay_out[dst] = pay[i];
+__global__ void digit_hist_kernel(const uint64_t *key, int64_t n, SortDigit dg, int64_t ntiles, int32_t *counts) {
+  __shared__ int h[16];
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = base + int64_t(r) * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[sort_digit(key[i], dg)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) counts[int64_t(threadIdx.x) * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void digit_scatter_kernel(const uint64_t *key, const uint32_t *pay, int64_t n, SortDigit dg, int64_t ntiles,
+                                     const int64_t *offs, uint64_t *key_out, uint32_t *pay_out) {
+  constexpr int kW = kSortThreads / 32;
+  __shared__ int64_t base_d[16];
+  __shared__ int wcnt[kW][17];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 16) base_d[threadIdx.x] = offs[int64_t(threadIdx.x) * ntiles + blockIdx.x];
+  const int64_t tile0 = int64_t(blockIdx.x) * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = tile0 + int64_t(r) * kSortThreads + threadIdx.x;
+    uint64_t k = 0;
+    uint32_t v = 0;
+    int d = 16;   // past the end: a bucket of its own
+    if (i < n) {
+      k = key[i];
+      v = pay[i];
+      d = sort_digit(k, dg);
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    __syncthreads();   // the previous round's positions are written and its counts folded in
+    for (int q = threadIdx.x; q < kW * 17; q += kSortThreads) wcnt[q / 17][q % 17] = 0;
+    __syncthreads();
+    if (rank == 0) wcnt[warp][d] = __popc(same);
+    __syncthreads();
+    if (d < 16) {
+      int64_t pos = base_d[d] + rank;
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+      key_out[pos] = k;
+      pay_out[pos] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      int add = 0;
+      for (int w = 0; w < kW; ++w) add += wcnt[w][threadIdx.x];
+      base_d[threadIdx.x] += add;
+    }
   }
 }
 
 // Sorts (key, payload) by the listed key bits, least significant first; stable.
 static int radix_sort(uint64_t *&key, uint32_t *&pay, int64_t n, const std::vector<int> &bits, Scratch &sc,
                       cudaStream_t s) {
-  if (n <= 1) return COX_OK;
+  if (n <= 1 || bits.empty()) return COX_OK;
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   uint64_t *k2 = static_cast<uint64_t *>(sc.get(n * sizeof(uint64_t)));
   uint32_t *p2 = static_cast<uint32_t *>(sc.get(n * sizeof(uint32_t)));
-  int32_t *flag = static_cast<int32_t *>(sc.get(n * sizeof(int32_t)));
-  int64_t *pre = static_cast<int64_t *>(sc.get(n * sizeof(int64_t)));
-  if (!k2 || !p2 || !flag || !pre) return COX_E_OOM;
-  for (int b : bits) {
+  int32_t *counts = static_cast<int32_t *>(sc.get(16 * ntiles * sizeof(int32_t)));
+  int64_t *offs = static_cast<int64_t *>(sc.get(16 * ntiles * sizeof(int64_t)));
+  if (!k2 || !p2 || !counts || !offs) return COX_E_OOM;
+  for (size_t b0 = 0; b0 < bits.size(); b0 += 4) {
+    SortDigit dg{};
+    dg.nb = int32_t(std::min<size_t>(4, bits.size() - b0));
+    for (int i = 0; i < dg.nb; ++i) dg.pos[i] = bits[b0 + i];
     count_launches(1);
-    bit_flags_kernel<<<grid_for(n), 256, 0, s>>>(key, n, b, flag);
-    int64_t ones = 0;
-    int rc = exclusive_scan(flag, n, pre, &ones, sc, s);
+    digit_hist_kernel<<<unsigned(ntiles), kSortThreads, 0, s>>>(key, n, dg, ntiles, counts);
+    int64_t total = 0;
+    int rc = exclusive_scan(counts, 16 * ntiles, offs, &total, sc, s);
     if (rc) return rc;
     count_launches(1);
-    split_scatter_kernel<<<grid_for(n), 256, 0, s>>>(key, pay, flag, pre, n, n - ones, k2, p2);
+    digit_scatter_kernel<<<unsigned(ntiles), kSortThreads, 0, s>>>(key, pay, n, dg, ntiles, offs, k2, p2);
     std::swap(key, k2);
     std::swap(pay, p2);
   }

@@ -647,7 +647,8 @@ static std::vector<int32_t> group_tiles(int64_t M, int64_t per_g, int64_t pos_ca
     if (hi <= cur) hi = std::min<int64_t>(M, cur + 1);
     rl.push_back(int32_t(hi));
     cur = hi;
-    while (g < G && h_head[g] < cur) ++g;
+    g = int64_t(std::lower_bound(h_head.begin() + g, h_head.end(), int32_t(std::min<int64_t>(cur, INT32_MAX))) -
+                h_head.begin());
   }
   return rl;
 }
@@ -710,20 +711,28 @@ static int build_tile_tables(BufferSet &B, cudaStream_t s, const DevData &D, con
 }
 
 // Whether every column's entries in every tile of a plan fit the incremental kernel's lists.
-// Columns holding more than the list capacity of entries in some tile of a plan (over[j] = 1).
+// Columns holding more than the list capacity of entries in some tile of a plan (over[j] = 1):
+// one thread per column over its per-tile entry offsets, then p bytes to the host.
+__global__ void list_over_kernel(int32_t p, int32_t T, const int32_t *ct, int32_t cap, uint8_t *over) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < p; j += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t *c = ct + j * (T + 1);
+    uint8_t o = 0;
+    for (int32_t t = 0; t < T && !o; ++t) o = c[t + 1] - c[t] > cap;
+    over[j] = o;
+  }
+}
+
 static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, std::vector<uint8_t> *over) {
-  std::vector<int32_t> hct(size_t(D.p) * (T + 1));
-  if (!hct.empty() && (cudaMemcpyAsync(hct.data(), ct, hct.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                       cudaStreamSynchronize(s) != cudaSuccess))
-    return COX_E_CUDA;
   over->assign(size_t(D.p), 0);
-  for (int32_t j = 0; j < D.p; ++j)
-    for (int32_t t = 0; t < T; ++t)
-      if (hct[size_t(j) * (T + 1) + t + 1] - hct[size_t(j) * (T + 1) + t] > inc_list_cap()) {
-        (*over)[j] = 1;
-        break;
-      }
-  return COX_OK;
+  if (D.p <= 0) return COX_OK;
+  uint8_t *d_over = static_cast<uint8_t *>(dev_alloc(size_t(D.p)));
+  if (!d_over) return COX_E_OOM;
+  count_launches(1);
+  list_over_kernel<<<grid_for(D.p), 256, 0, s>>>(D.p, T, ct, inc_list_cap(), d_over);
+  const bool ok = cudaMemcpyAsync(over->data(), d_over, size_t(D.p), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  dev_free(d_over, size_t(D.p));
+  return ok ? COX_OK : COX_E_CUDA;
 }
 
 static int lists_fit(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, bool *fits) {

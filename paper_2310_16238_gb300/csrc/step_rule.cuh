@@ -35,20 +35,30 @@ DW_FN dw inc_step_rule_dw(dw g1, dw g2, dw b, bool b_zero, dw t, int penalty, dw
     g1 = dw_add(g1, dw_mul(b, inv_var));
     g2 = dw_add(g2, inv_var);
   }
-  dw s = dw_make(0.0f);
-  if (!dw_pos(g2) || !dw_finite(g1) || !dw_finite(g2)) {
-    s = dw_make(0.0f);
-  } else if (l1) {
-    if (b_zero) {
-      const dw up = dw_add(g1, lambda), dn = dw_sub(g1, lambda);
-      if (dw_negv(up)) s = dw_neg(dw_div(up, g2));
-      else if (dw_pos(dn)) s = dw_neg(dw_div(dn, g2));
+  // the Newton numerator of the branch taken (one division below, whichever branch)
+  dw num = dw_make(0.0f);
+  bool take = false;
+  if (dw_pos(g2) && dw_finite(g1) && dw_finite(g2)) {
+    if (l1) {
+      if (b_zero) {
+        const dw up = dw_add(g1, lambda), dn = dw_sub(g1, lambda);
+        if (dw_negv(up)) {
+          num = up;
+          take = true;
+        } else if (dw_pos(dn)) {
+          num = dn;
+          take = true;
+        }
+      } else {
+        num = dw_add(g1, dw_negv(b) ? dw_neg(lambda) : lambda);
+        take = true;
+      }
     } else {
-      s = dw_neg(dw_div(dw_negv(b) ? dw_sub(g1, lambda) : dw_add(g1, lambda), g2));
+      num = g1;
+      take = true;
     }
-  } else {
-    s = dw_neg(dw_div(g1, g2));
   }
+  dw s = take ? dw_neg(dw_div(num, g2)) : dw_make(0.0f);
   if (dw_pos(dw_sub(dw_abs(s), t))) {
     *kind = dw_negv(s) ? kStepMinusT : kStepPlusT;
     s = dw_negv(s) ? dw_neg(t) : t;

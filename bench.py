@@ -488,6 +488,69 @@ def run_cv(args):
     return out
 
 
+def run_e1(args):
+    """The paper's synthetic experiment (§3.1): N = 1e6, P = 2000, binary X at 5 % density,
+    K = 50,000 equal strata, beta 20 % nonzero N(0, 1), L1 gamma = sqrt(2). One step = one full
+    fit (cox_create from device-resident arrays + cox_fit + cox_destroy). The paper reports
+    23 s per fit for this shape on a Quadro GV100 (and 17 min for its CPU implementation)."""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    n = int(1_000_000 * args.scale)
+    K = args.strata if args.strata > 0 else 50_000
+    data, opts = synth.synthetic_e1(n=n, p=2000, k=K)
+    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ddev = synth.CoxData(**{**data.__dict__})
+    for f in ("stop", "event", "stratum", "col_ptr", "row_idx"):
+        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    times, infos = [], []
+    launches0 = None
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + args.steps):
+                if k == args.warmup:
+                    launches0 = cox.cox_launch_count()
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h = cox.cox_create(ddev, opts, precision=precision, stream=stream.cuda_stream)
+                try:
+                    beta, info = cox.cox_fit(h)
+                finally:
+                    cox.cox_destroy(h)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+                    infos.append(info)
+        torch.cuda.synchronize()
+    launches = cox.cox_launch_count() - launches0
+    ms = float(np.mean(times))
+    coords = float(np.mean([i["coord_updates"] for i in infos]))
+    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
+    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
+    h = cox.cox_create(data, opts, precision=precision)
+    md = cox.cox_metadata(h)
+    cox.cox_destroy(h)
+    wname = f"synthetic_e1 N={n} p=2000 density 0.05 K={K} beta 20% N(0,1) L1 gamma=sqrt(2)"
+    roof = roofline_of(engine, data, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
+                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
+    return {"metric": "seconds per fit (CCD to convergence, stratified L1 Cox; the paper's synthetic experiment)",
+            "value": ms * 1e-3, "unit": "s/fit", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4), "data": "synthetic (seeded)",
+            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
+                       "coord_updates_per_s": coords / (ms * 1e-3), "nonzero_beta": int(np.count_nonzero(beta)),
+                       "tie_groups": len(md["group_time"]), "step_us": step_us, "engine": engine,
+                       "paper_context": "23 s per fit on a Quadro GV100 for N = 1e6, K = 50,000 (another GPU)",
+                       "l2": "flushed before every step (512 MB write)"},
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
 def run_batch(args):
     """256 fits (4 outcomes x 4 folds x 16 L1 weights) over one shared binary X: one-at-a-time
     FP64 vs the batched persistent launch (FP64 and FP32C, autotuned tile length)."""
@@ -653,10 +716,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="stratified", choices=["stratified", "time_varying", "tvc", "cv", "batch", "serving"])
+    ap.add_argument("--workload", default="stratified", choices=["stratified", "time_varying", "tvc", "cv", "e1", "batch", "serving"])
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--max-rows", type=int, default=2_000_000)
+    ap.add_argument("--strata", type=int, default=0, help="e1 workload: number of strata (default 50,000)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -668,7 +732,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
     if args.workload != "stratified":
-        fn = {"time_varying": run_time_varying, "tvc": run_tvc, "cv": run_cv, "batch": run_batch,
+        fn = {"time_varying": run_time_varying, "tvc": run_tvc, "cv": run_cv, "e1": run_e1, "batch": run_batch,
               "serving": run_serving}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return

@@ -485,7 +485,7 @@ int incr_result(cox_handle *h, double *beta_out, cox_fit_info *info, float ms, i
 int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, double *const *beta_out, cox_fit_info *info) {
   const int precision = hs[0]->sd->precision;
   cudaStream_t s = hs[0]->stream;
-  const int grid = inc_max_grid(precision);
+  const int grid = inc_max_grid(precision, 0);
   std::vector<cudaStream_t> saved(n);
   for (int i = 0; i < n; ++i) {
     saved[i] = hs[i]->stream;
@@ -609,7 +609,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
   int rc;
   int64_t launches = 1;
   if (P.inc_n_halt == 0) {
-    if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+    if (launch_incr(h->sd->precision, prm, IT, s, P.inc_variant)) return cuda_fail(h, "incremental launch");
     cudaEventRecord(h->ev1, s);
     if ((rc = read_ctl(h))) return rc;
   } else {
@@ -633,7 +633,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
       const int32_t j = h->h_ctl->j;
       if (!halt[size_t(j)]) {
         prm.max_steps = left;
-        if (launch_incr(h->sd->precision, prm, IT, s)) return cuda_fail(h, "incremental launch");
+        if (launch_incr(h->sd->precision, prm, IT, s, P.inc_variant)) return cuda_fail(h, "incremental launch");
       } else {
         int64_t k = 0;
         for (int32_t jj = j; k < p && halt[size_t(jj)]; jj = jj + 1 >= p ? 0 : jj + 1) ++k;
@@ -946,7 +946,7 @@ int cox_fit(cox_handle *h, const double *beta0, double *beta_out, cox_fit_info *
   if (eng == COX_ENGINE_INCR && !incr)
     return fail(h, COX_E_INVALID,
                 "cox_fit: the data do not qualify for the incremental kernel (binary X; per CTA at most 1024 tie groups, "
-                "65536 positions and 1024 entries of a column)");
+                "65536 positions and 1024 entries of a column, or 4096 groups, 32768 positions and 512 entries)");
   if (incr) {
     rc = fit_incr(h, beta_out, info);
     // its double-word sums hold |eta - shift| <= 60; beyond that AUTO refits with an FP64 engine

@@ -29,7 +29,9 @@
 // j waits on the exchange.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "ccd_common.cuh"
 #include "cox.h"
@@ -40,10 +42,6 @@
 namespace coxgb {
 
 constexpr int kIncThreads = 1024;
-constexpr int kIncGroupCap = 1024;   // tie groups per CTA (one per thread)
-constexpr int kIncListCap = 1024;    // entries of one column per CTA (one per thread)
-constexpr int kIncPosCap = 65536;    // positions per CTA (bitmask capacity)
-constexpr int kIncWords = kIncPosCap / 32;
 constexpr int kIncMaxCtas = 256;
 constexpr int kIncRec = kIncRecWords / 2;   // step record payloads: G1, G2, LL, H1, R, I
 constexpr uint32_t kTagErr = 0x80000000u;   // tag bit: the writer raised an error
@@ -53,22 +51,38 @@ constexpr int kIncTraceSlots = 24;        // phase timestamps per step and CTA (
 
 constexpr size_t inc_al16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Capacities of one kernel configuration: tie groups per CTA (kGpt per thread), entries of one
+// column per CTA (at most one per thread), positions per CTA (bitmask capacity).
+template <int GPT, int LCAP, int PCAP>
+struct IncCfg {
+  static constexpr int kGpt = GPT;
+  static constexpr int kGroupCap = GPT * kIncThreads;
+  static constexpr int kListCap = LCAP;
+  static constexpr int kPosCap = PCAP;
+  static constexpr int kWords = PCAP / 32;
+  static_assert(LCAP <= kIncThreads, "one list entry per thread");
+};
+using IncWide = IncCfg<1, 1024, 65536>;   // one tie group and up to one list entry per thread
+using IncDeep = IncCfg<4, 512, 32768>;    // group-dense data: up to four tie groups per thread
+
+template <class Cfg>
 struct IncSmem {
+  static constexpr int LC = Cfg::kListCap, GC = Cfg::kGroupCap, W = Cfg::kWords;
   static constexpr size_t o_lpos = 0;                                   // u32 [4][cap] entry positions
-  static constexpr size_t o_lv = o_lpos + 4 * 4 * kIncListCap;          // dw  [4][cap] v at the entries
-  static constexpr size_t o_le = o_lv + 4 * 8 * kIncListCap;            // f64 [4][cap] eta at the entries
-  static constexpr size_t o_u0 = o_le + 4 * 8 * kIncListCap;            // dw  [cap] suffix of dD
-  static constexpr size_t o_u1 = o_u0 + 8 * kIncListCap;                // dw  [cap] suffix of v
-  static constexpr size_t o_cutb = o_u1 + 8 * kIncListCap;              // u32 [W] stratum ends
-  static constexpr size_t o_cutp = o_cutb + 4 * kIncWords;              // i32 [W] prefix counts
-  static constexpr size_t o_headb = o_cutp + 4 * kIncWords;             // u32 [W] read positions
-  static constexpr size_t o_headp = o_headb + 4 * kIncWords;            // i32 [W]
-  static constexpr size_t o_gs0 = o_headp + 4 * kIncWords;              // dw  [gcap] dense-scan S0
-  static constexpr size_t o_gseen = o_gs0 + 8 * kIncGroupCap;           // u8  [gcap]
-  static constexpr size_t o_rec = inc_al16(o_gseen + kIncGroupCap);     // 8-byte slots [6][C] record payloads
+  static constexpr size_t o_lv = o_lpos + 4 * 4 * LC;                   // dw  [4][cap] v at the entries
+  static constexpr size_t o_le = o_lv + 4 * 8 * LC;                     // f64 [4][cap] eta at the entries
+  static constexpr size_t o_u0 = o_le + 4 * 8 * LC;                     // dw  [cap] suffix of dD
+  static constexpr size_t o_u1 = o_u0 + 8 * LC;                         // dw  [cap] suffix of v
+  static constexpr size_t o_cutb = o_u1 + 8 * LC;                       // u32 [W] stratum ends
+  static constexpr size_t o_cutp = o_cutb + 4 * W;                      // i32 [W] prefix counts
+  static constexpr size_t o_headb = o_cutp + 4 * W;                     // u32 [W] read positions
+  static constexpr size_t o_headp = o_headb + 4 * W;                    // i32 [W]
+  static constexpr size_t o_gs0 = o_headp + 4 * W;                      // dw  [gcap] dense-scan S0
+  static constexpr size_t o_gseen = o_gs0 + 8 * GC;                     // u8  [gcap]
+  static constexpr size_t o_rec = inc_al16(o_gseen + GC);               // 8-byte slots [6][C] record payloads
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
-  static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;          // GroupSlot [gcap]
-  static constexpr size_t bytes = o_grp + 24 * kIncGroupCap;
+  static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;         // GroupSlot [gcap]
+  static constexpr size_t bytes = o_grp + 24 * GC;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -84,9 +98,9 @@ struct GroupSlot {
 };
 static_assert(sizeof(GroupSlot) == 24, "group slot layout");
 
-int inc_group_cap() { return kIncGroupCap; }
-int inc_list_cap() { return kIncListCap; }
-int inc_pos_cap() { return kIncPosCap; }
+int inc_group_cap(int variant) { return variant ? IncDeep::kGroupCap : IncWide::kGroupCap; }
+int inc_list_cap(int variant) { return variant ? IncDeep::kListCap : IncWide::kListCap; }
+int inc_pos_cap(int variant) { return variant ? IncDeep::kPosCap : IncWide::kPosCap; }
 
 // Step-synchronous control state, identical in every CTA.
 struct IncState {
@@ -266,14 +280,14 @@ static __device__ __forceinline__ dw inc_v(double eta, double shift, bool exitp,
 // Stage column j's entries in this tile (positions relative to lo, exit bit kept) with eta and v
 // at them, using threads [th0, th0 + nth).
 static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo, int npos, uint32_t *lp, dw *lv,
-                                     double *le, int *cnt, int th0, int nth, int *serr) {
+                                     double *le, int *cnt, int th0, int nth, int *serr, int cap) {
   const DevData &D = prm.D;
   const int C = prm.T;
   const int64_t cb = D.col_ptr[j];
   const int32_t *ct = prm.col_tile + int64_t(j) * (C + 1);
   const int64_t qa = cb + ct[t];
   int n = ct[t + 1] - ct[t];
-  if (n > kIncListCap || n < 0) {   // the plan keeps every column within the cap
+  if (n > cap || n < 0) {   // the plan keeps every column within the cap
     if (int(threadIdx.x) == th0) atomicCAS(serr, 0, COX_E_INVALID);
     n = 0;
   }
@@ -439,10 +453,11 @@ static __device__ dw inc_dense(const IncParams &prm, int lo, int npos, const uin
   return head;
 }
 
-template <class P, bool kTrace>
+template <class P, class Cfg, bool kTrace>
 static __device__ __forceinline__ void incr_body(const IncParams &prm, const int t) {
   using T = typename P::T;
-  using S = IncSmem;
+  using S = IncSmem<Cfg>;
+  constexpr int LC = Cfg::kListCap;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *lpos = reinterpret_cast<uint32_t *>(smem + S::o_lpos);
   dw *lv = reinterpret_cast<dw *>(smem + S::o_lv);
@@ -493,7 +508,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 
   // ---- one-time set-up: stratum ends and read positions as bitmasks, group registers, lists
   if (tid == 0) {
-    s_bad = (npos > kIncPosCap || ng > kIncGroupCap || C > kIncMaxCtas || npos <= 0 || ng < 0) ? 1 : 0;
+    s_bad = (npos > Cfg::kPosCap || ng > Cfg::kGroupCap || C > kIncMaxCtas || npos <= 0 || ng < 0) ? 1 : 0;
     s_err = 0;
   }
   __syncthreads();
@@ -527,15 +542,15 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     tru[jj] = F.trust[jj];
   }
   __syncthreads();
-  if (tid < ng) {
-    int qg = D.head_pos[ga + tid] - lo;
+  for (int gi = tid; gi < ng; gi += kIncThreads) {
+    int qg = D.head_pos[ga + gi] - lo;
     if (qg < 0 || qg >= npos) {
       atomicCAS(&s_err, 0, COX_E_INVALID);
       qg = 0;
     }
-    grp[tid].q = qg;
-    grp[tid].d = float(D.head_d[ga + tid]);   // events of the group (exact in float below 2^24)
-    grp[tid].S0 = dw_make(0.0f);
+    grp[gi].q = qg;
+    grp[gi].d = float(D.head_d[ga + gi]);   // events of the group (exact in float below 2^24)
+    grp[gi].S0 = dw_make(0.0f);
     atomicOr(&headb[qg >> 5], 1u << (qg & 31));
   }
   for (int k = tid; k < nc; k += kIncThreads) {
@@ -609,10 +624,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     s_ce[tid] = ce;
   }
   __syncthreads();
-  if (tid < ng) {
-    const int seg = inc_rank(cutb, cutp, grp[tid].q);
-    grp[tid].seg = seg;
-    grp[tid].tail = seg == nc;
+  for (int gi = tid; gi < ng; gi += kIncThreads) {
+    const int seg = inc_rank(cutb, cutp, grp[gi].q);
+    grp[gi].seg = seg;
+    grp[gi].tail = seg == nc;
   }
   const int RW = max(32, ((npos + 1023) / 1024) * 32);   // positions per warp in the dense scan
   const double half_inv_var = s_half_inv_var;
@@ -620,17 +635,16 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   int base = 0;
   if (st.state == kRunning) {
     if (st.pend_j >= 0)
-      inc_load_list(prm, t, st.pend_j, lo, npos, lpos, lv, le, &s_cnt[0], 0, kIncThreads, &s_err);
+      inc_load_list(prm, t, st.pend_j, lo, npos, lpos, lv, le, &s_cnt[0], 0, kIncThreads, &s_err, LC);
     else if (tid == 0)
       s_cnt[0] = 0;
     const int j1 = st.j, j2 = st.j + 1 >= p ? 0 : st.j + 1;
-    inc_load_list(prm, t, j1, lo, npos, lpos + kIncListCap, lv + kIncListCap, le + kIncListCap, &s_cnt[1], 0, kIncThreads,
-                  &s_err);
+    inc_load_list(prm, t, j1, lo, npos, lpos + LC, lv + LC, le + LC, &s_cnt[1], 0, kIncThreads, &s_err, LC);
     if (prm.halt && prm.halt[j2]) {   // the launch ends before it
       if (tid == 0) s_cnt[2] = 0;
     } else {
-      inc_load_list(prm, t, j2, lo, npos, lpos + 2 * kIncListCap, lv + 2 * kIncListCap, le + 2 * kIncListCap, &s_cnt[2],
-                    0, kIncThreads, &s_err);
+      inc_load_list(prm, t, j2, lo, npos, lpos + 2 * LC, lv + 2 * LC, le + 2 * LC, &s_cnt[2], 0, kIncThreads, &s_err,
+                    LC);
     }
   }
   __syncthreads();
@@ -643,9 +657,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const bool refresh = need_ll || step == 0;
     const uint32_t epoch = st.epoch;
     const int sp = base & 3, sc = (base + 1) & 3, sn = (base + 2) & 3, sf = (base + 3) & 3;
-    uint32_t *lp_p = lpos + sp * kIncListCap, *lp_c = lpos + sc * kIncListCap, *lp_n = lpos + sn * kIncListCap;
-    dw *lv_p = lv + sp * kIncListCap, *lv_c = lv + sc * kIncListCap, *lv_n = lv + sn * kIncListCap;
-    double *le_p = le + sp * kIncListCap, *le_c = le + sc * kIncListCap, *le_n = le + sn * kIncListCap;
+    uint32_t *lp_p = lpos + sp * LC, *lp_c = lpos + sc * LC, *lp_n = lpos + sn * LC;
+    dw *lv_p = lv + sp * LC, *lv_c = lv + sc * LC, *lv_n = lv + sn * LC;
+    double *le_p = le + sp * LC, *le_c = le + sc * LC, *le_n = le + sn * LC;
     const int np = pj >= 0 ? s_cnt[sp] : 0, ncur = s_cnt[sc], nnx = s_cnt[sn];
     uint64_t *trace =
         (kTrace && prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * C + t) * kIncTraceSlots : nullptr;
@@ -747,30 +761,34 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         if (lane == 0) s_carry[warp] = c0;
       }
       __syncthreads();
-      if (tid < ng) {
-        dw S0 = gs0[tid];
-        if (!gseen[tid]) S0 = dw_add(S0, s_dcar[grp[tid].q / RW]);
-        if (grp[tid].tail) S0 = dw_add(S0, s_carry[0]);
-        grp[tid].S0 = S0;
+      for (int gi = tid; gi < ng; gi += kIncThreads) {
+        dw S0 = gs0[gi];
+        if (!gseen[gi]) S0 = dw_add(S0, s_dcar[grp[gi].q / RW]);
+        if (grp[gi].tail) S0 = dw_add(S0, s_carry[0]);
+        grp[gi].S0 = S0;
       }
       C1 = s_carry[1];
     } else {
       // ---- S0 += the suffix of dD from the read position, and the later tiles' change
-      if (tid < ng) {
-        dw S0 = grp[tid].S0;
-        bool upd = false;
-        if (np > 0) {
-          const int k = inc_lower_bound(lp_p, np, grp[tid].q);
-          if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == grp[tid].seg) {
-            S0 = dw_add(S0, u0[k]);
+#pragma unroll
+      for (int i = 0; i < Cfg::kGpt; ++i) {
+        const int gi = tid + i * kIncThreads;
+        if (gi < ng) {
+          dw S0 = grp[gi].S0;
+          bool upd = false;
+          if (np > 0) {
+            const int k = inc_lower_bound(lp_p, np, grp[gi].q);
+            if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == grp[gi].seg) {
+              S0 = dw_add(S0, u0[k]);
+              upd = true;
+            }
+          }
+          if (grp[gi].tail && !dw_is_zero(st.E)) {
+            S0 = dw_add(S0, dw_mul(st.E, s_chain[0]));
             upd = true;
           }
+          if (upd) grp[gi].S0 = S0;
         }
-        if (grp[tid].tail && !dw_is_zero(st.E)) {
-          S0 = dw_add(S0, dw_mul(st.E, s_chain[0]));
-          upd = true;
-        }
-        if (upd) grp[tid].S0 = S0;
       }
       C1 = dw_add(s_chain[1], dw_mul(st.E, s_chain[2]));
     }
@@ -781,20 +799,31 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     dw r_g1 = dw_make(0.0f), r_g2 = dw_make(0.0f), r_R = dw_make(0.0f), r_I = dw_make(0.0f);
     double r_ll = 0.0;
     if (gwarp) {
-      if (tid < ng) {
-        const GroupSlot g = grp[tid];
-        dw s1 = dw_make(0.0f);
-        if (ncur > 0) {
-          const int k = inc_lower_bound(lp_c, ncur, g.q);
-          if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = u1[k];
+#pragma unroll
+      for (int i = 0; i < Cfg::kGpt; ++i) {
+        const int gi = tid + i * kIncThreads;
+        if (gi < ng) {
+          const GroupSlot g = grp[gi];
+          dw s1 = dw_make(0.0f);
+          if (ncur > 0) {
+            const int k = inc_lower_bound(lp_c, ncur, g.q);
+            if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = u1[k];
+          }
+          if (g.tail) s1 = dw_add(s1, C1);
+          if (!dw_is_zero(s1)) {
+            const dw r = dw_div(s1, g.S0);
+            const dw a1 = dw_mul_f(r, g.d);
+            const dw a2 = dw_mul(a1, dw_sub(dw_make(1.0f), r));
+            if (Cfg::kGpt == 1) {
+              r_g1 = a1;
+              r_g2 = a2;
+            } else {
+              r_g1 = dw_add_same(r_g1, a1);
+              r_g2 = dw_add_same(r_g2, a2);
+            }
+          }
+          if (need_ll) r_ll += double(g.d) * log(dw_to(g.S0));
         }
-        if (g.tail) s1 = dw_add(s1, C1);
-        if (!dw_is_zero(s1)) {
-          const dw r = dw_div(s1, g.S0);
-          r_g1 = dw_mul_f(r, g.d);
-          r_g2 = dw_mul(r_g1, dw_sub(dw_make(1.0f), r));
-        }
-        if (need_ll) r_ll = double(g.d) * log(dw_to(g.S0));
       }
       if (trace) trace[6] = uint64_t(clock64());
 #pragma unroll 1
@@ -841,7 +870,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const int par = int(epoch & 1u);
     if (warp < 2 || warp == 3 || warp == 4) {
       const int v = warp < 2 ? warp : warp - 1;           // s_red row: G1, G2, R, I
-      const int nv = warp < 2 ? (ng + 31) >> 5 : (nnx + 31) >> 5;
+      const int nv = warp < 2 ? min((ng + 31) >> 5, 32) : (nnx + 31) >> 5;
       dw a = lane < nv ? s_red[v][lane] : dw_make(0.0f);
       if (warp < 2)
         for (int off = 1; off < nv; off <<= 1) a = dw_add_same(a, dw_shfl_down(a, off));
@@ -850,7 +879,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       if (lane == 0) s_pay[warp < 2 ? warp : warp + 1] = *reinterpret_cast<const uint64_t *>(&a);   // 0 G1, 1 G2, 4 R, 5 I
       if (trace) trace[9] = uint64_t(clock64());
     } else if (warp == 2) {
-      const int nv = (ng + 31) >> 5;
+      const int nv = min((ng + 31) >> 5, 32);
       double a = (need_ll && lane < nv) ? s_rll[lane] : 0.0;
       if (need_ll)
         for (int off = 1; off < nv; off <<= 1) a += __shfl_down_sync(kFull, a, off);
@@ -910,8 +939,8 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       if (prm.halt && prm.halt[jf]) {   // the launch ends before it
         if (tid == C) s_cnt[sf] = 0;
       } else {
-        inc_load_list(prm, t, jf, lo, npos, lpos + sf * kIncListCap, lv + sf * kIncListCap, le + sf * kIncListCap,
-                      &s_cnt[sf], C, kIncThreads - C, &s_err);
+        inc_load_list(prm, t, jf, lo, npos, lpos + sf * LC, lv + sf * LC, le + sf * LC, &s_cnt[sf], C, kIncThreads - C,
+                      &s_err, LC);
       }
     }
     __syncthreads();
@@ -1055,9 +1084,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 // One fit over the whole grid: its arguments stay in the kernel-parameter space. The traced
 // instantiation records phase timestamps (its trace pointer costs registers, so the production
 // instantiation has none).
-template <class P, bool kTrace>
+template <class P, class Cfg, bool kTrace>
 __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_kernel(const IncParams prm) {
-  incr_body<P, kTrace>(prm, int(blockIdx.x));
+  incr_body<P, Cfg, kTrace>(prm, int(blockIdx.x));
 }
 
 // Several fits per launch: CTA b runs tile cta_map[b].y of fit cta_map[b].x, whose arguments it
@@ -1071,12 +1100,11 @@ __global__ void __launch_bounds__(kIncThreads, 1) ccd_incr_multi_kernel(const In
   uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
   for (int w = int(threadIdx.x); w < int(sizeof(IncParams) / 4); w += kIncThreads) dst[w] = src[w];
   __syncthreads();
-  incr_body<P, false>(sp, me.y);
+  incr_body<P, IncWide, false>(sp, me.y);
 }
 
 template <class K>
-static int inc_max_ctas_of(K kernel) {
-  const size_t sm = IncSmem::bytes;
+static int inc_max_ctas_of(K kernel, size_t sm) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1093,41 +1121,51 @@ static int inc_max_ctas_of(K kernel) {
   return g < kIncMaxCtas ? g : kIncMaxCtas;
 }
 
-// the largest cooperative grid of both entry points (the smaller of the two)
-template <class P>
+// the largest cooperative grid of a configuration's entry points (the smallest of them)
+template <class P, class Cfg>
 static int inc_max_ctas() {
   static int cached = -2;
   if (cached != -2) return cached;
-  const int a = inc_max_ctas_of(ccd_incr_kernel<P, false>), b = inc_max_ctas_of(ccd_incr_multi_kernel<P>);
-  const int c = inc_max_ctas_of(ccd_incr_kernel<P, true>);
-  return cached = a < b ? (a < c ? a : c) : (b < c ? b : c);
+  const size_t sm = IncSmem<Cfg>::bytes;
+  int g = std::min(inc_max_ctas_of(ccd_incr_kernel<P, Cfg, false>, sm), inc_max_ctas_of(ccd_incr_kernel<P, Cfg, true>, sm));
+  if (std::is_same<Cfg, IncWide>::value) g = std::min(g, inc_max_ctas_of(ccd_incr_multi_kernel<P>, sm));
+  return cached = g;
 }
 
-int inc_max_grid(int precision) { return precision == COX_FP32C ? inc_max_ctas<PF32C>() : inc_max_ctas<PF64>(); }
+int inc_max_grid(int precision, int variant) {
+  if (variant)
+    return precision == COX_FP32C ? inc_max_ctas<PF32C, IncDeep>() : inc_max_ctas<PF64, IncDeep>();
+  return precision == COX_FP32C ? inc_max_ctas<PF32C, IncWide>() : inc_max_ctas<PF64, IncWide>();
+}
 
-int launch_incr(int precision, const IncParams &prm, int grid, void *stream) {
+template <class Cfg>
+static const void *incr_entry(int precision, bool trace) {
+  return precision == COX_FP32C ? (trace ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, true>)
+                                         : reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, false>))
+                                : (trace ? reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, true>)
+                                         : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, false>));
+}
+
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream, int variant) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void *args[] = {const_cast<IncParams *>(&prm)};
-  if (grid <= 0 || grid > inc_max_grid(precision) || grid != prm.T) return COX_E_INVALID;
+  if (grid <= 0 || grid > inc_max_grid(precision, variant) || grid != prm.T) return COX_E_INVALID;
   count_launches(1);
   const bool tr = prm.trace != nullptr;
-  const void *fn = precision == COX_FP32C
-                       ? (tr ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, true>)
-                             : reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, false>))
-                       : (tr ? reinterpret_cast<const void *>(ccd_incr_kernel<PF64, true>)
-                             : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, false>));
-  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
+  const void *fn = variant ? incr_entry<IncDeep>(precision, tr) : incr_entry<IncWide>(precision, tr);
+  const size_t sm = variant ? IncSmem<IncDeep>::bytes : IncSmem<IncWide>::bytes;
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, sm, s);
   return e == cudaSuccess ? COX_OK : COX_E_CUDA;
 }
 
 int launch_incr_multi(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void *args[] = {const_cast<IncParams **>(&prms), const_cast<int2 **>(&cta_map)};
-  if (grid <= 0 || grid > inc_max_grid(precision)) return COX_E_INVALID;
+  if (grid <= 0 || grid > inc_max_grid(precision, 0)) return COX_E_INVALID;
   count_launches(1);
   const void *fn = precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_multi_kernel<PF32C>)
                                           : reinterpret_cast<const void *>(ccd_incr_multi_kernel<PF64>);
-  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem::bytes, s);
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIncThreads), args, IncSmem<IncWide>::bytes, s);
   return e == cudaSuccess ? COX_OK : COX_E_CUDA;
 }
 

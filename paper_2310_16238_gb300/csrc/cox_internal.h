@@ -150,11 +150,14 @@ int launch_resident(int precision, const ResParams &prm, int grid, void *stream)
 
 // Incremental kernel (ccd_incr.cu): tie groups, column entries and positions one CTA holds,
 // largest cooperative grid (0 when unsupported), launch.
-int inc_group_cap();
-int inc_list_cap();
-int inc_pos_cap();
-int inc_max_grid(int precision);
-int launch_incr(int precision, const IncParams &prm, int grid, void *stream);
+// Incremental kernel configurations: 0 = one tie group per thread (1,024 per CTA), lists of
+// 1,024 entries, 65,536 positions; 1 = group-dense data (4,096 groups, 512 entries, 32,768
+// positions per CTA).
+int inc_group_cap(int variant);
+int inc_list_cap(int variant);
+int inc_pos_cap(int variant);
+int inc_max_grid(int precision, int variant);
+int launch_incr(int precision, const IncParams &prm, int grid, void *stream, int variant);
 int launch_incr_multi(int precision, const IncParams *prms, const int2 *cta_map, int grid, void *stream);
 
 }  // namespace coxgb

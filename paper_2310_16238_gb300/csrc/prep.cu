@@ -722,13 +722,14 @@ __global__ void list_over_kernel(int32_t p, int32_t T, const int32_t *ct, int32_
   }
 }
 
-static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, std::vector<uint8_t> *over) {
+static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, std::vector<uint8_t> *over,
+                         int cap) {
   over->assign(size_t(D.p), 0);
   if (D.p <= 0) return COX_OK;
   uint8_t *d_over = static_cast<uint8_t *>(dev_alloc(size_t(D.p)));
   if (!d_over) return COX_E_OOM;
   count_launches(1);
-  list_over_kernel<<<grid_for(D.p), 256, 0, s>>>(D.p, T, ct, inc_list_cap(), d_over);
+  list_over_kernel<<<grid_for(D.p), 256, 0, s>>>(D.p, T, ct, cap, d_over);
   const bool ok = cudaMemcpyAsync(over->data(), d_over, size_t(D.p), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
                   cudaStreamSynchronize(s) == cudaSuccess;
   dev_free(d_over, size_t(D.p));
@@ -737,7 +738,7 @@ static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStr
 
 static int lists_fit(const DevData &D, const int32_t *ct, int32_t T, cudaStream_t s, bool *fits) {
   std::vector<uint8_t> over;
-  const int rc = list_overflow(D, ct, T, s, &over);
+  const int rc = list_overflow(D, ct, T, s, &over, inc_list_cap(0));
   *fits = rc == COX_OK && std::find(over.begin(), over.end(), uint8_t(1)) == over.end();
   return rc;
 }
@@ -746,8 +747,9 @@ int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string
   if (P->cinc_T != 0) return COX_OK;
   P->cinc_T = -1;
   const DevData &D = P->desc;
-  const int grid = inc_max_grid(precision);
-  if (P->inc_T <= 0 || P->inc_n_halt > 0 || grid <= 0) return COX_OK;   // batches have no dense-column hand-over
+  const int grid = inc_max_grid(precision, 0);
+  // batches: configuration 0 only, and no dense-column hand-over
+  if (P->inc_T <= 0 || P->inc_n_halt > 0 || P->inc_variant != 0 || grid <= 0) return COX_OK;
   std::vector<int32_t> h_head(size_t(D.G));
   if (D.G > 0 && (cudaMemcpyAsync(h_head.data(), D.head_pos, size_t(D.G) * sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
                       cudaSuccess ||
@@ -757,8 +759,8 @@ int prepare_compact_incr(Prepared *P, int precision, cudaStream_t s, std::string
   }
   // as many tie groups per tile as a CTA holds, tiles shorter than the run of positions that
   // would overflow a column's list (shortened further if a list still overflows)
-  for (int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(P->inc_wmin) - 1); pos_cap >= 32; pos_cap /= 2) {
-    std::vector<int32_t> rl = group_tiles(D.M, inc_group_cap(), pos_cap, h_head);
+  for (int64_t pos_cap = std::min<int64_t>(inc_pos_cap(0), int64_t(P->inc_wmin) - 1); pos_cap >= 32; pos_cap /= 2) {
+    std::vector<int32_t> rl = group_tiles(D.M, inc_group_cap(0), pos_cap, h_head);
     const int32_t T = int32_t(rl.size()) - 1;
     if (T > grid) return COX_OK;
     int32_t *lo = nullptr, *g = nullptr, *k = nullptr, *ct = nullptr;
@@ -1108,8 +1110,10 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         out->res_T = int32_t(rl.size()) - 1;
       }
     }
-    const int inc_grid = inc_max_grid(precision);
-    if (inc_grid > 0) {
+    // configuration 0 first (one tie group per thread); configuration 1 for group-dense data
+    for (int variant = 0; variant < 2 && out->inc_T == 0; ++variant) {
+      const int inc_grid = inc_max_grid(precision, variant);
+      if (inc_grid <= 0) continue;
       // candidate plans: equal tie groups per tile (the step's cost) with tiles shorter than the
       // shortest run of positions holding more entries of one column than the kernel's list
       // capacity; then equal positions. The first whose lists fit is taken. A few columns too
@@ -1122,7 +1126,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         cudaMemcpyAsync(d_w, wcol.data(), size_t(p) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         if (nseg > 0) count_launches(1);
         if (nseg > 0)
-          window_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, counting ? 2 : 1, idx, inc_list_cap(), d_w);
+          window_kernel<<<unsigned(nseg), kSegThreads, 0, s>>>(segs, counting ? 2 : 1, idx, inc_list_cap(variant), d_w);
         if (cudaMemcpyAsync(wcol.data(), d_w, size_t(p) * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
           *err = "cox_create: table kernels failed";
@@ -1143,7 +1147,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         if (r) return r;
         const int32_t IT = int32_t(il.size()) - 1;
         std::vector<uint8_t> over;
-        if ((r = list_overflow(D, ict, IT, s, &over))) return r;
+        if ((r = list_overflow(D, ict, IT, s, &over, inc_list_cap(variant)))) return r;
         int64_t n2 = 0;
         for (int32_t j = 0; j < p; ++j) {
           over[j] = over[j] | pre[j];
@@ -1157,6 +1161,7 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         out->inc_tile_k = ik;
         out->inc_col_tile = ict;
         out->inc_n_halt = int32_t(n2);
+        out->inc_variant = variant;
         if (n2 > 0) {
           uint8_t *dh = static_cast<uint8_t *>(B.get(size_t(p)));
           if (!dh || cudaMemcpyAsync(dh, over.data(), size_t(p), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1171,8 +1176,8 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
         int32_t wmin = 0x7fffffff;
         for (int32_t j = 0; j < p; ++j)
           if (!excl[j]) wmin = std::min(wmin, wcol[j]);
-        const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(), int64_t(wmin) - 1);
-        return pos_cap >= 32 ? group_plan(D.M, pos_cap, inc_group_cap(), inc_grid, h_head) : std::vector<int32_t>{};
+        const int64_t pos_cap = std::min<int64_t>(inc_pos_cap(variant), int64_t(wmin) - 1);
+        return pos_cap >= 32 ? group_plan(D.M, pos_cap, inc_group_cap(variant), inc_grid, h_head) : std::vector<int32_t>{};
       };
       const std::vector<uint8_t> none(size_t(p), 0);
       std::vector<uint8_t> hset;
@@ -1180,9 +1185,10 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
       {
         int32_t wmin = 0x7fffffff;
         for (int32_t j = 0; j < p; ++j) wmin = std::min(wmin, wcol[j]);
-        out->inc_wmin = wmin;
+        if (variant == 0) out->inc_wmin = wmin;
       }
-      const std::vector<int32_t> fp = fit_plan(D.M, inc_pos_cap(), size_t(inc_group_cap()), inc_grid, h_head);
+      const std::vector<int32_t> fp =
+          fit_plan(D.M, inc_pos_cap(variant), size_t(inc_group_cap(variant)), inc_grid, h_head);
       if ((rc = take(group_for(none), 0, none, &taken, &hset))) return rc;
       if (!taken && (rc = take(fp, 0, none, &taken, &hset))) return rc;
       if (!taken && max_halt > 0 && !fp.empty()) {

@@ -51,6 +51,7 @@ struct Prepared {
   int32_t inc_wmin = 0x7fffffff;        // shortest run of positions overflowing a column's list
   // columns too dense for the incremental lists: fits step them with the resident kernel
   int32_t inc_n_halt = 0;
+  int32_t inc_variant = 0;              // kernel configuration of the plan (see inc_group_cap)
   uint8_t *inc_halt = nullptr;          // [p] device, null when none
   std::vector<uint8_t> h_inc_halt;      // [p] host copy
   // compact incremental plan (fewest tiles; batches), built on first use: 0 = not yet, -1 = none

@@ -192,3 +192,19 @@ def test_dense_column_hand_over_fp32c():
     ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
     assert _rel(beta, ob) <= 1e-5
     assert abs(info["loglik"] - oi["loglik"]) <= 1e-7 * _ll_scale(d, ob, oi["loglik"])
+
+
+@pytest.mark.parametrize("precision,tb,tl", [(cox.COX_FP64, 1e-9, 1e-11), (cox.COX_FP32C, 1e-5, 1e-7)],
+                         ids=["fp64", "fp32c"])
+def test_group_dense_configuration(precision, tb, tl):
+    """More tie groups than one per thread of every CTA (the shape of the paper's synthetic
+    experiment with many strata): the configuration with up to four groups per thread."""
+    d, o = synth.synthetic_e1(n=300000, p=24, k=30000, seed=90)
+    G = len(oracle.tie_groups(d)[0])
+    assert G > 1024 * 152            # beyond one group per thread on every SM
+    with cox.Handle(d, o, precision=precision) as h:
+        beta, info = h.fit()
+    assert info["engine"] == cox.COX_ENGINE_INCR and info["step_launches"] == 1
+    ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
+    assert _rel(beta, ob) <= tb
+    assert abs(info["loglik"] - oi["loglik"]) <= tl * _ll_scale(d, ob, oi["loglik"])

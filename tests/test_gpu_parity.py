@@ -320,3 +320,15 @@ def test_long_columns_span_segments():
     with pytest.raises(cox.CoxError) as e:
         cox.Handle(bad, o)
     assert e.value.code == cox.COX_E_INVALID
+
+
+@pytest.mark.parametrize("k", [1, 40, 1500])
+def test_paper_synthetic_shape(k):
+    """The shape of the paper's synthetic experiment (5 % binary X, 20 % of beta nonzero,
+    L1 gamma = sqrt 2) from one stratum to strata of two rows: the GPU fit follows the oracle."""
+    d, o = synth.synthetic_e1(n=3000, p=40, k=k, seed=81)
+    with cox.Handle(d, o) as h:
+        b, info = h.fit()
+    ob, oi = oracle.fit(d, o, max_sweeps=info["sweeps"])
+    assert _rel_beta(b, ob) <= 1e-9
+    assert abs(info["loglik"] - oi["loglik"]) <= 1e-11 * max(abs(oi["loglik"]), 1.0)

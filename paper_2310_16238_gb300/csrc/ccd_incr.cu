@@ -71,8 +71,8 @@ struct IncSmem {
   static constexpr size_t o_lpos = 0;                                   // u32 [4][cap] entry positions
   static constexpr size_t o_lv = o_lpos + 4 * 4 * LC;                   // dw  [4][cap] v at the entries
   static constexpr size_t o_le = o_lv + 4 * 8 * LC;                     // f64 [4][cap] eta at the entries
-  static constexpr size_t o_u0 = o_le + 4 * 8 * LC;                     // dw  [cap] suffix of dD
-  static constexpr size_t o_u1 = o_u0 + 8 * LC;                         // dw  [cap] suffix of v
+  static constexpr size_t o_u0 = o_le + 4 * 8 * LC;                     // dw  [2][cap] suffixes of v: this
+  static constexpr size_t o_u1 = o_u0 + 8 * LC;                         //   step's column, the previous one's
   static constexpr size_t o_cutb = o_u1 + 8 * LC;                       // u32 [W] stratum ends
   static constexpr size_t o_cutp = o_cutb + 4 * W;                      // i32 [W] prefix counts
   static constexpr size_t o_headb = o_cutp + 4 * W;                     // u32 [W] read positions
@@ -305,60 +305,48 @@ static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo,
   if (int(threadIdx.x) == th0) *cnt = n;
 }
 
-// Inclusive segmented suffix sums of two sequences held one element per thread (element k =
-// thread k, k < nact; later elements are 0 and end their segments); f = 1 marks the last element
-// of a segment. Warps past nact skip the arithmetic. Results go to out0/out1[k] for k < nact.
-static __device__ void inc_seg_suffix2(dw x0, int f0, dw x1, int f1, int nact, dw *out0, dw *out1, dw (*s_agg)[32],
-                                       int (*s_flg)[32]) {
+// Inclusive segmented suffix sum of one sequence held one element per thread (element k = thread
+// k, k < nact; later elements are 0 and end their segments); f = 1 marks the last element of a
+// segment. Warps past nact skip the arithmetic. Results go to out[k] for k < nact.
+static __device__ void inc_seg_suffix1(dw x, int f, int nact, dw *out, dw (*s_agg)[32], int (*s_flg)[32]) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool act = warp * 32 < nact;   // warp-uniform
   if (act) {
 #pragma unroll 1
     for (int off = 1; off < 32; off <<= 1) {
-      const dw y0 = dw_shfl_down(x0, off), y1 = dw_shfl_down(x1, off);
-      const int g0 = __shfl_down_sync(kFull, f0, off), g1 = __shfl_down_sync(kFull, f1, off);
+      const dw y = dw_shfl_down(x, off);
+      const int g = __shfl_down_sync(kFull, f, off);
       if (lane + off < 32) {
-        if (!f0) x0 = dw_add(x0, y0);
-        if (!f1) x1 = dw_add(x1, y1);
-        f0 |= g0;
-        f1 |= g1;
+        if (!f) x = dw_add(x, y);
+        f |= g;
       }
     }
   }
   if (lane == 0) {
-    s_agg[0][warp] = act ? x0 : dw_make(0.0f);
-    s_agg[1][warp] = act ? x1 : dw_make(0.0f);
-    s_flg[0][warp] = act ? f0 : 1;
-    s_flg[1][warp] = act ? f1 : 1;
+    s_agg[0][warp] = act ? x : dw_make(0.0f);
+    s_flg[0][warp] = act ? f : 1;
   }
   __syncthreads();
   const int nwa = (nact + 31) >> 5;
   if (warp == 0 && nwa > 1) {
-    dw a0 = s_agg[0][lane], a1 = s_agg[1][lane];
-    int h0 = s_flg[0][lane], h1 = s_flg[1][lane];
+    dw a = s_agg[0][lane];
+    int h = s_flg[0][lane];
     for (int off = 1; off < nwa; off <<= 1) {
-      const dw y0 = dw_shfl_down(a0, off), y1 = dw_shfl_down(a1, off);
-      const int g0 = __shfl_down_sync(kFull, h0, off), g1 = __shfl_down_sync(kFull, h1, off);
+      const dw y = dw_shfl_down(a, off);
+      const int g = __shfl_down_sync(kFull, h, off);
       if (lane + off < 32) {
-        if (!h0) a0 = dw_add(a0, y0);
-        if (!h1) a1 = dw_add(a1, y1);
-        h0 |= g0;
-        h1 |= g1;
+        if (!h) a = dw_add(a, y);
+        h |= g;
       }
     }
-    dw c0 = dw_shfl_down(a0, 1), c1 = dw_shfl_down(a1, 1);
-    if (lane == 31) { c0 = dw_make(0.0f); c1 = dw_make(0.0f); }
-    s_agg[0][lane] = c0;   // carry into warp `lane` from the later warps
-    s_agg[1][lane] = c1;
+    dw c = dw_shfl_down(a, 1);
+    if (lane == 31) c = dw_make(0.0f);
+    s_agg[0][lane] = c;   // carry into warp `lane` from the later warps
   }
   __syncthreads();
   if (act) {
-    if (nwa > 1) {
-      if (!f0) x0 = dw_add(x0, s_agg[0][warp]);
-      if (!f1) x1 = dw_add(x1, s_agg[1][warp]);
-    }
-    out0[tid] = x0;
-    out1[tid] = x1;
+    if (nwa > 1 && !f) x = dw_add(x, s_agg[0][warp]);
+    out[tid] = x;
   }
 }
 
@@ -667,20 +655,16 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     if (tid == 0) s_anyerr = 0;
     // ---- 1. the pending update at the previous column's entries (one per thread):
     //         eta += dbeta (eq. parallel_xb); v (1 + (e^dbeta - 1)) (eq. parallel_d)
-    dw dd = dw_make(0.0f);
-    int fp = 1;
     if (tid < np) {
       const uint32_t e = lp_p[tid];
       const int q = int(e & kPosMask);
       const double et = __dadd_rn(le_p[tid], db);
       if (!(fabs(et - shift) <= kIncRange)) atomicCAS(&s_err, 0, COX_E_RANGE);
-      dd = dw_mul(lv_p[tid], st.E);
-      const dw nv = dw_add(lv_p[tid], dd);
+      const dw nv = dw_add(lv_p[tid], dw_mul(lv_p[tid], st.E));
       prm.vdw[lo + q] = nv;
       F.eta[lo + q] = et;
       le_p[tid] = et;
       lv_p[tid] = nv;
-      fp = tid + 1 >= np || inc_rank(cutb, cutp, int(lp_p[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
     }
     __syncthreads();
     if (trace) trace[1] = uint64_t(clock64());
@@ -725,14 +709,17 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       x1 = lv_c[tid];
       fc = tid + 1 >= ncur || inc_rank(cutb, cutp, int(lp_c[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
     }
-    // ---- 3. segmented suffix sums of dD (previous column) and v (current column)
+    // ---- 3. segmented suffix sums of v over the current column (this step's buffer); the
+    //         previous step's, over the previous column, times e^dbeta - 1 is the change of S0
+    //         (binary X: the update multiplies v by e^dbeta at that column's entries)
+    dw *const ucur = (base & 1) ? u0 : u1;
+    const dw *const uprev = (base & 1) ? u1 : u0;
     if (trace) trace[2] = uint64_t(clock64());
-    inc_seg_suffix2(refresh ? dw_make(0.0f) : dd, refresh ? 1 : fp, x1, fc, refresh ? ncur : max(np, ncur), u0, u1, s_agg,
-                    s_flg);
+    inc_seg_suffix1(x1, fc, ncur, ucur, s_agg, s_flg);
     if (trace) trace[3] = uint64_t(clock64());
     __syncthreads();
     // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
-    auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? u1[0] : dw_make(0.0f); };
+    auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? ucur[0] : dw_make(0.0f); };
     if (trace) trace[4] = uint64_t(clock64());
     dw C1;
     if (refresh) {
@@ -779,7 +766,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           if (np > 0) {
             const int k = inc_lower_bound(lp_p, np, grp[gi].q);
             if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == grp[gi].seg) {
-              S0 = dw_add(S0, u0[k]);
+              S0 = dw_add(S0, dw_mul(st.E, uprev[k]));
               upd = true;
             }
           }
@@ -807,7 +794,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           dw s1 = dw_make(0.0f);
           if (ncur > 0) {
             const int k = inc_lower_bound(lp_c, ncur, g.q);
-            if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = u1[k];
+            if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = ucur[k];
           }
           if (g.tail) s1 = dw_add(s1, C1);
           if (!dw_is_zero(s1)) {

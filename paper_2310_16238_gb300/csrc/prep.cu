@@ -714,11 +714,15 @@ static int build_tile_tables(BufferSet &B, cudaStream_t s, const DevData &D, con
 // Columns holding more than the list capacity of entries in some tile of a plan (over[j] = 1):
 // one thread per column over its per-tile entry offsets, then p bytes to the host.
 __global__ void list_over_kernel(int32_t p, int32_t T, const int32_t *ct, int32_t cap, uint8_t *over) {
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < p; j += int64_t(gridDim.x) * blockDim.x) {
+  // one warp per column, lanes over its tiles
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t j = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; j < p; j += nw) {
     const int32_t *c = ct + j * (T + 1);
-    uint8_t o = 0;
-    for (int32_t t = 0; t < T && !o; ++t) o = c[t + 1] - c[t] > cap;
-    over[j] = o;
+    bool o = false;
+    for (int32_t t = lane; t < T; t += 32) o = o || c[t + 1] - c[t] > cap;
+    o = __any_sync(0xffffffffu, o);
+    if (lane == 0) over[j] = o ? 1 : 0;
   }
 }
 
@@ -729,7 +733,7 @@ static int list_overflow(const DevData &D, const int32_t *ct, int32_t T, cudaStr
   uint8_t *d_over = static_cast<uint8_t *>(dev_alloc(size_t(D.p)));
   if (!d_over) return COX_E_OOM;
   count_launches(1);
-  list_over_kernel<<<grid_for(D.p), 256, 0, s>>>(D.p, T, ct, cap, d_over);
+  list_over_kernel<<<grid_for(int64_t(D.p) * 32), 256, 0, s>>>(D.p, T, ct, cap, d_over);
   const bool ok = cudaMemcpyAsync(over->data(), d_over, size_t(D.p), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
                   cudaStreamSynchronize(s) == cudaSuccess;
   dev_free(d_over, size_t(D.p));

@@ -82,7 +82,8 @@ struct IncSmem {
   static constexpr size_t o_rec = inc_al16(o_gseen + GC);               // 8-byte slots [6][C] record payloads
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
   static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;         // GroupSlot [gcap]
-  static constexpr size_t bytes = o_grp + 24 * GC;
+  static constexpr size_t o_pmask = o_grp + 24 * GC;                    // u32 [W] the previous column's positions
+  static constexpr size_t bytes = o_pmask + 4 * W;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -461,6 +462,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   uint64_t *srec = reinterpret_cast<uint64_t *>(smem + S::o_rec);
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
   GroupSlot *grp = reinterpret_cast<GroupSlot *>(smem + S::o_grp);
+  uint32_t *pmask = reinterpret_cast<uint32_t *>(smem + S::o_pmask);
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -505,7 +507,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     return;
   }
   const int nw = (npos + 31) >> 5;
-  for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; }
+  for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; pmask[w] = 0u; }
   if (tid == 0) {
     st.j = ctl->j;
     st.sweep = ctl->sweep;
@@ -661,6 +663,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const double et = __dadd_rn(le_p[tid], db);
       if (!(fabs(et - shift) <= kIncRange)) atomicCAS(&s_err, 0, COX_E_RANGE);
       const dw nv = dw_add(lv_p[tid], dw_mul(lv_p[tid], st.E));
+      atomicOr(&pmask[q >> 5], 1u << (q & 31));
       prm.vdw[lo + q] = nv;
       F.eta[lo + q] = et;
       le_p[tid] = et;
@@ -684,20 +687,20 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         le_n[tid] = F.eta[lo + q];
       }
     } else if (np > 0) {
+      // an entry at a position of the previous column takes the same update (the copies of v
+      // and eta in every list agree, so the result is the previous list's to the bit)
       if (tid < ncur) {
         const int q = int(lp_c[tid] & kPosMask);
-        const int k = inc_lower_bound(lp_p, np, q);
-        if (k < np && int(lp_p[k] & kPosMask) == q) {
-          lv_c[tid] = lv_p[k];
-          le_c[tid] = le_p[k];
+        if ((pmask[q >> 5] >> (q & 31)) & 1u) {
+          lv_c[tid] = dw_add(lv_c[tid], dw_mul(lv_c[tid], st.E));
+          le_c[tid] = __dadd_rn(le_c[tid], db);
         }
       }
       if (tid < nnx) {
         const int q = int(lp_n[tid] & kPosMask);
-        const int k = inc_lower_bound(lp_p, np, q);
-        if (k < np && int(lp_p[k] & kPosMask) == q) {
-          lv_n[tid] = lv_p[k];
-          le_n[tid] = le_p[k];
+        if ((pmask[q >> 5] >> (q & 31)) & 1u) {
+          lv_n[tid] = dw_add(lv_n[tid], dw_mul(lv_n[tid], st.E));
+          le_n[tid] = __dadd_rn(le_n[tid], db);
         }
       }
     }
@@ -721,6 +724,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
     auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? ucur[0] : dw_make(0.0f); };
     if (trace) trace[4] = uint64_t(clock64());
+    if (tid < np) {   // the marks of the previous column are read; clear them for the next step
+      const int q = int(lp_p[tid] & kPosMask);
+      atomicAnd(&pmask[q >> 5], ~(1u << (q & 31)));
+    }
     dw C1;
     if (refresh) {
       // ---- carries of the rebuilt S0 and of S1 from one exchange of the tiles' head sums

@@ -83,7 +83,8 @@ struct IncSmem {
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
   static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;         // GroupSlot [gcap]
   static constexpr size_t o_pmask = o_grp + 24 * GC;                    // u32 [W] the previous column's positions
-  static constexpr size_t bytes = o_pmask + 4 * W;
+  static constexpr size_t o_cmask = o_pmask + 4 * W;                    // u32 [W] the current column's positions
+  static constexpr size_t bytes = o_cmask + 4 * W;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -463,6 +464,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
   GroupSlot *grp = reinterpret_cast<GroupSlot *>(smem + S::o_grp);
   uint32_t *pmask = reinterpret_cast<uint32_t *>(smem + S::o_pmask);
+  uint32_t *cmask = reinterpret_cast<uint32_t *>(smem + S::o_cmask);
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -477,6 +479,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   __shared__ dw s_dagg[32], s_dcar[32];   // dense scan: warp aggregates, carries into warps
   __shared__ int s_dflg[32];
   __shared__ int s_chain_end, s_bad, s_err, s_anyerr;
+  __shared__ int s_cut0;   // first stratum end in the tile (npos: none): positions up to it are the head segment
   __shared__ int s_ce[kIncMaxCtas];   // chain end of every CTA of the fit
   __shared__ uint64_t s_pay[kIncRec];   // this CTA's record payloads (bits): G1, G2, LL, H1, R, I
   __shared__ double s_half_inv_var;
@@ -498,6 +501,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 
   // ---- one-time set-up: stratum ends and read positions as bitmasks, group registers, lists
   if (tid == 0) {
+    s_cut0 = nc > 0 ? D.cut_pos[kc0] - lo : npos;
     s_bad = (npos > Cfg::kPosCap || ng > Cfg::kGroupCap || C > kIncMaxCtas || npos <= 0 || ng < 0) ? 1 : 0;
     s_err = 0;
   }
@@ -507,7 +511,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     return;
   }
   const int nw = (npos + 31) >> 5;
-  for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; pmask[w] = 0u; }
+  for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; pmask[w] = 0u; cmask[w] = 0u; }
   if (tid == 0) {
     st.j = ctl->j;
     st.sweep = ctl->sweep;
@@ -709,6 +713,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     int fc = 1;
     if (tid < ncur) {
       const int q = int(lp_c[tid] & kPosMask);
+      atomicOr(&cmask[q >> 5], 1u << (q & 31));
       x1 = lv_c[tid];
       fc = tid + 1 >= ncur || inc_rank(cutb, cutp, int(lp_c[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
     }
@@ -832,13 +837,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     if (trace && !gwarp) trace[6] = uint64_t(clock64());
     if (nwarp) {
       const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : 0;
-      if (tid < nnx && inc_rank(cutb, cutp, qnx) == 0) {
+      if (tid < nnx && qnx <= s_cut0) {
         const dw vnx = lv_n[tid];
         r_R = vnx;
-        if (ncur > 0) {
-          const int k = inc_lower_bound(lp_c, ncur, qnx);
-          if (k < ncur && int(lp_c[k] & kPosMask) == qnx) r_I = vnx;
-        }
+        if ((cmask[qnx >> 5] >> (qnx & 31)) & 1u) r_I = vnx;
       }
       if (__any_sync(kFull, !dw_is_zero(r_R))) {
 #pragma unroll 1
@@ -858,6 +860,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     if (trace) trace[7] = uint64_t(clock64());
     __syncthreads();
     if (trace) trace[8] = uint64_t(clock64());
+    if (tid < ncur) {   // the marks of the current column are read; clear them for the next step
+      const int q = int(lp_c[tid] & kPosMask);
+      atomicAnd(&cmask[q >> 5], ~(1u << (q & 31)));
+    }
     // ---- one value per warp: sums of the warp partials (G1, G2, R, I as double-words, LL in
     //      FP64), then this CTA's record, pushed into every CTA's inbox by thread r for reader r:
     //      (G1, G2[, LL]) to every CTA, and (H1, R, I) as well to the CTAs whose chain holds this tile

@@ -84,7 +84,11 @@ struct IncSmem {
   static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;         // GroupSlot [gcap]
   static constexpr size_t o_pmask = o_grp + 24 * GC;                    // u32 [W] the previous column's positions
   static constexpr size_t o_cmask = o_pmask + 4 * W;                    // u32 [W] the current column's positions
-  static constexpr size_t bytes = o_cmask + 4 * W;
+  // u16 [4][gcap]: per list slot and tie group, the first entry at or after the group's read
+  // position in its stratum segment (kNoEntry: none); kept for one group per thread only
+  static constexpr int KG = Cfg::kGpt == 1 ? GC : 0;
+  static constexpr size_t o_kg = o_cmask + 4 * W;
+  static constexpr size_t bytes = o_kg + 2 * 4 * KG;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -99,6 +103,13 @@ struct GroupSlot {
   int32_t tail;
 };
 static_assert(sizeof(GroupSlot) == 24, "group slot layout");
+
+constexpr uint16_t kNoEntry = 0xffffu;
+
+// First entry of the sorted list lp[0, n) at or after position q that lies in q's stratum
+// segment `seg` (kNoEntry: none).
+static __device__ __forceinline__ uint16_t inc_first_entry(const uint32_t *lp, int n, int q, int seg,
+                                                           const uint32_t *cutb, const int32_t *cutp);
 
 int inc_group_cap(int variant) { return variant ? IncDeep::kGroupCap : IncWide::kGroupCap; }
 int inc_list_cap(int variant) { return variant ? IncDeep::kListCap : IncWide::kListCap; }
@@ -234,6 +245,12 @@ static __device__ __forceinline__ int inc_lower_bound(const uint32_t *lp, int n,
     else b = m;
   }
   return a;
+}
+
+static __device__ __forceinline__ uint16_t inc_first_entry(const uint32_t *lp, int n, int q, int seg,
+                                                           const uint32_t *cutb, const int32_t *cutp) {
+  const int k = inc_lower_bound(lp, n, q);
+  return (k < n && inc_rank(cutb, cutp, int(lp[k] & kPosMask)) == seg) ? uint16_t(k) : kNoEntry;
 }
 
 static __device__ double inc_penalty(const DevFit &F, int j, double b) {
@@ -465,6 +482,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   GroupSlot *grp = reinterpret_cast<GroupSlot *>(smem + S::o_grp);
   uint32_t *pmask = reinterpret_cast<uint32_t *>(smem + S::o_pmask);
   uint32_t *cmask = reinterpret_cast<uint32_t *>(smem + S::o_cmask);
+  uint16_t *kg = reinterpret_cast<uint16_t *>(smem + S::o_kg);   // [4][gcap], one group per thread only
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -642,6 +660,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     }
   }
   __syncthreads();
+  if (Cfg::kGpt == 1 && st.state == kRunning && tid < ng)
+    for (int sl = 1; sl <= 2; ++sl)
+      kg[sl * S::KG + tid] = inc_first_entry(lpos + sl * LC, s_cnt[sl], grp[tid].q, grp[tid].seg, cutb, cutp);
+  __syncthreads();
   bool refreshed = false;  // the last step taken rebuilt v from eta
 
   for (int64_t step = 0; step < prm.max_steps && st.state == kRunning && !st.halt; ++step) {
@@ -776,8 +798,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           dw S0 = grp[gi].S0;
           bool upd = false;
           if (np > 0) {
-            const int k = inc_lower_bound(lp_p, np, grp[gi].q);
-            if (k < np && inc_rank(cutb, cutp, int(lp_p[k] & kPosMask)) == grp[gi].seg) {
+            const int k = Cfg::kGpt == 1 ? int(kg[sp * S::KG + gi])
+                                         : int(inc_first_entry(lp_p, np, grp[gi].q, grp[gi].seg, cutb, cutp));
+            if (k != kNoEntry) {
               S0 = dw_add(S0, dw_mul(st.E, uprev[k]));
               upd = true;
             }
@@ -805,8 +828,8 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           const GroupSlot g = grp[gi];
           dw s1 = dw_make(0.0f);
           if (ncur > 0) {
-            const int k = inc_lower_bound(lp_c, ncur, g.q);
-            if (k < ncur && inc_rank(cutb, cutp, int(lp_c[k] & kPosMask)) == g.seg) s1 = ucur[k];
+            const int k = Cfg::kGpt == 1 ? int(kg[sc * S::KG + gi]) : int(inc_first_entry(lp_c, ncur, g.q, g.seg, cutb, cutp));
+            if (k != kNoEntry) s1 = ucur[k];
           }
           if (g.tail) s1 = dw_add(s1, C1);
           if (!dw_is_zero(s1)) {
@@ -936,6 +959,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         q.tw = dw_from(q.t);
         s_pre = q;
       }
+      if (Cfg::kGpt == 1)   // the next column's first entries per group, for its step and the one after
+        for (int gi = tid - C; gi < ng; gi += kIncThreads - C)
+          kg[sn * S::KG + gi] = inc_first_entry(lp_n, nnx, grp[gi].q, grp[gi].seg, cutb, cutp);
       if (prm.halt && prm.halt[jf]) {   // the launch ends before it
         if (tid == C) s_cnt[sf] = 0;
       } else {

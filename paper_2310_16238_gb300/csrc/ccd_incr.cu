@@ -87,8 +87,11 @@ struct IncSmem {
   // u16 [4][gcap]: per list slot and tie group, the first entry at or after the group's read
   // position in its stratum segment (kNoEntry: none); kept for one group per thread only
   static constexpr int KG = Cfg::kGpt == 1 ? GC : 0;
+  static constexpr int KE = Cfg::kGpt == 1 ? LC : 0;
   static constexpr size_t o_kg = o_cmask + 4 * W;
-  static constexpr size_t bytes = o_kg + 2 * 4 * KG;
+  static constexpr size_t o_ginv = inc_al16(o_kg + 2 * 4 * KG);          // dw [gcap] 1 / S0 per group (same)
+  static constexpr size_t o_fce = o_ginv + 8 * KG;                        // u8 [4][cap] segment ends of each list (same)
+  static constexpr size_t bytes = o_fce + 4 * KE;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -245,6 +248,14 @@ static __device__ __forceinline__ int inc_lower_bound(const uint32_t *lp, int n,
     else b = m;
   }
   return a;
+}
+
+// Entry k of a sorted list ends its stratum segment within the list (the last entry, or the next
+// one lies past a stratum end).
+static __device__ __forceinline__ uint8_t inc_seg_end(const uint32_t *lp, int n, int k, const uint32_t *cutb,
+                                                      const int32_t *cutp) {
+  return (k + 1 >= n ||
+          inc_rank(cutb, cutp, int(lp[k + 1] & kPosMask)) != inc_rank(cutb, cutp, int(lp[k] & kPosMask))) ? 1 : 0;
 }
 
 static __device__ __forceinline__ uint16_t inc_first_entry(const uint32_t *lp, int n, int q, int seg,
@@ -483,6 +494,8 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   uint32_t *pmask = reinterpret_cast<uint32_t *>(smem + S::o_pmask);
   uint32_t *cmask = reinterpret_cast<uint32_t *>(smem + S::o_cmask);
   uint16_t *kg = reinterpret_cast<uint16_t *>(smem + S::o_kg);   // [4][gcap], one group per thread only
+  dw *ginv = reinterpret_cast<dw *>(smem + S::o_ginv);            // [gcap], one group per thread only
+  uint8_t *fce = smem + S::o_fce;                                 // [4][cap], one group per thread only
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -660,9 +673,12 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     }
   }
   __syncthreads();
-  if (Cfg::kGpt == 1 && st.state == kRunning && tid < ng)
-    for (int sl = 1; sl <= 2; ++sl)
-      kg[sl * S::KG + tid] = inc_first_entry(lpos + sl * LC, s_cnt[sl], grp[tid].q, grp[tid].seg, cutb, cutp);
+  if (Cfg::kGpt == 1 && st.state == kRunning) {
+    for (int sl = 1; sl <= 2; ++sl) {
+      if (tid < ng) kg[sl * S::KG + tid] = inc_first_entry(lpos + sl * LC, s_cnt[sl], grp[tid].q, grp[tid].seg, cutb, cutp);
+      if (tid < s_cnt[sl]) fce[sl * S::KE + tid] = inc_seg_end(lpos + sl * LC, s_cnt[sl], tid, cutb, cutp);
+    }
+  }
   __syncthreads();
   bool refreshed = false;  // the last step taken rebuilt v from eta
 
@@ -737,7 +753,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const int q = int(lp_c[tid] & kPosMask);
       atomicOr(&cmask[q >> 5], 1u << (q & 31));
       x1 = lv_c[tid];
-      fc = tid + 1 >= ncur || inc_rank(cutb, cutp, int(lp_c[tid + 1] & kPosMask)) != inc_rank(cutb, cutp, q);
+      fc = Cfg::kGpt == 1 ? int(fce[sc * S::KE + tid]) : int(inc_seg_end(lp_c, ncur, tid, cutb, cutp));
     }
     // ---- 3. segmented suffix sums of v over the current column (this step's buffer); the
     //         previous step's, over the previous column, times e^dbeta - 1 is the change of S0
@@ -787,6 +803,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         if (!gseen[gi]) S0 = dw_add(S0, s_dcar[grp[gi].q / RW]);
         if (grp[gi].tail) S0 = dw_add(S0, s_carry[0]);
         grp[gi].S0 = S0;
+        if (Cfg::kGpt == 1) ginv[gi] = dw_div(dw_make(1.0f), S0);
       }
       C1 = s_carry[1];
     } else {
@@ -809,7 +826,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
             S0 = dw_add(S0, dw_mul(st.E, s_chain[0]));
             upd = true;
           }
-          if (upd) grp[gi].S0 = S0;
+          if (upd) {
+            grp[gi].S0 = S0;
+            if (Cfg::kGpt == 1) ginv[gi] = dw_div(dw_make(1.0f), S0);
+          }
         }
       }
       C1 = dw_add(s_chain[1], dw_mul(st.E, s_chain[2]));
@@ -833,7 +853,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           }
           if (g.tail) s1 = dw_add(s1, C1);
           if (!dw_is_zero(s1)) {
-            const dw r = dw_div(s1, g.S0);
+            const dw r = Cfg::kGpt == 1 ? dw_mul(s1, ginv[gi]) : dw_div(s1, g.S0);
             const dw a1 = dw_mul_f(r, g.d);
             const dw a2 = dw_mul(a1, dw_sub(dw_make(1.0f), r));
             if (Cfg::kGpt == 1) {
@@ -959,9 +979,11 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         q.tw = dw_from(q.t);
         s_pre = q;
       }
-      if (Cfg::kGpt == 1)   // the next column's first entries per group, for its step and the one after
+      if (Cfg::kGpt == 1) {   // the next column's first entries per group and segment ends, for its step
         for (int gi = tid - C; gi < ng; gi += kIncThreads - C)
           kg[sn * S::KG + gi] = inc_first_entry(lp_n, nnx, grp[gi].q, grp[gi].seg, cutb, cutp);
+        for (int k = tid - C; k < nnx; k += kIncThreads - C) fce[sn * S::KE + k] = inc_seg_end(lp_n, nnx, k, cutb, cutp);
+      }
       if (prm.halt && prm.halt[jf]) {   // the launch ends before it
         if (tid == C) s_cnt[sf] = 0;
       } else {

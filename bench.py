@@ -96,8 +96,8 @@ ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 # the same kernel on the same workload (launch total / steps it ran); the summaries and commands
 # are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
 TRAFFIC = {
-    ("incremental", "stratified_sparse", "fp64"): (155.886336e6 + 34.845184e6) / 2001,
-    ("incremental", "time_varying", "fp64"): (1237.299968e6 + 5821.862144e6) / 20001,
+    ("incremental", "stratified_sparse", "fp64"): (156.857856e6 + 34.779648e6) / 2001,
+    ("incremental", "time_varying", "fp64"): (1233.798912e6 + 5819.235072e6) / 20001,
 }
 
 

@@ -93,16 +93,18 @@ typedef struct {
  *   stream     cudaStream_t (NULL = default stream)
  *   tile       positions per tile of the streaming kernel, 0 = library default; a multiple
  *              of 32 in [1024, 4096 (FP64) or 8192 (FP32C)] otherwise
- *   engine     COX_ENGINE_AUTO: the incremental kernel when the data qualify (binary X; per
- *              co-resident CTA at most 1024 tie groups, 65,536 risk positions and 1024
- *              entries of any column), else the resident kernel when the data qualify
- *              (binary X and the whole risk sequence fits the GPU's shared memory), else
- *              streaming. COX_ENGINE_STREAM / _RESIDENT / _INCR force one; RESIDENT and
- *              INCR fail with COX_E_INVALID when the data do not qualify. The incremental
- *              kernel keeps each tie group's risk-set sum S0 resident and updates it from
- *              the changed positions (cost per coordinate O(groups + nnz_j), not O(n)),
- *              rebuilding it from a full scan at the start of every sweep; it computes the
- *              sums in FP64 for either precision (COX_FP32C stores exp(eta) as float). */
+ *   engine     COX_ENGINE_AUTO: the incremental kernel when the data qualify (binary X and,
+ *              per co-resident CTA, at most 1024 tie groups, 65,536 risk positions and 1024
+ *              entries of any column, or 4096 groups, 32,768 positions and 512 entries; a
+ *              few columns too dense for those lists are stepped by the resident kernel),
+ *              else the resident kernel when the data qualify (binary X and the whole risk
+ *              sequence fits the GPU's shared memory), else streaming. COX_ENGINE_STREAM /
+ *              _RESIDENT / _INCR force one; RESIDENT and INCR fail with COX_E_INVALID when
+ *              the data do not qualify. The incremental kernel keeps each tie group's
+ *              risk-set sum S0 resident and updates it from the changed positions (cost per
+ *              coordinate O(groups + nnz_j), not O(n)), rebuilding it from a full scan at the
+ *              start of every sweep; its sums and ratios are double-word FP32 (about 48
+ *              significant bits), eta, beta and the step FP64, for either precision. */
 typedef struct {
   int32_t penalty;
   int32_t precision;
@@ -262,6 +264,9 @@ typedef struct {
   int32_t n_path;           /* >= 1 */
   const int32_t *fold;      /* host or device, n_rows fold ids in [0, K) */
   const double *path;       /* host, n_path penalty values */
+  const cox_split *split;   /* NULL, or every fit (training sets and full data) on its time-split
+                               view (cox_create_split); fold ids stay per input row, so a row's
+                               interval copies share its fold. beta_path has p_view columns. */
 } cox_cv;
 
 int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv, double *cvl, double *beta_path,

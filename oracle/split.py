@@ -80,8 +80,9 @@ def _stratum_index(data):
     return inv.astype(np.int64)
 
 
-def _assemble(stop, start, event, stratum, xrows, p_out, valued):
-    """Sort rows by (stratum, stop, construction order) and build the CSC."""
+def _assemble(stop, start, event, stratum, xrows, p_out, valued, source=None):
+    """Sort rows by (stratum, stop, construction order) and build the CSC; with ``source``
+    (the input row of every constructed row) also return it in the sorted order."""
     n = len(stop)
     order = np.lexsort((np.arange(n), np.asarray(stop), np.asarray(stratum))) if n else np.zeros(0, np.int64)
     newpos = np.empty(n, np.int64)
@@ -97,13 +98,16 @@ def _assemble(stop, start, event, stratum, xrows, p_out, valued):
         col_ptr[c + 1] = col_ptr[c] + len(ent)
         ri.extend(r for r, _ in ent)
         vv.extend(v for _, v in ent)
-    return SplitData(
+    out = SplitData(
         stop=np.asarray(stop, np.int32)[order].copy(),
         start=None if start is None else np.asarray(start, np.int32)[order].copy(),
         event=np.asarray(event, np.uint8)[order].copy(),
         stratum=np.asarray(stratum, np.int32)[order].copy(),
         col_ptr=col_ptr, row_idx=np.asarray(ri, np.int32),
         val=np.asarray(vv, np.float64) if valued else None, p=p_out)
+    if source is None:
+        return out
+    return out, np.asarray(source, np.int64)[order]
 
 
 def augment(data, cuts: Sequence[int], tvc_cols: Sequence[int] = ()) -> SplitData:
@@ -132,7 +136,7 @@ def augment(data, cuts: Sequence[int], tvc_cols: Sequence[int] = ()) -> SplitDat
     return _assemble(stop, None, event, stratum, xrows, p_out, data.val is not None)
 
 
-def split_counting(data, cuts: Sequence[int], tvc_cols: Sequence[int] = ()) -> SplitData:
+def split_counting(data, cuts: Sequence[int], tvc_cols: Sequence[int] = (), return_source: bool = False):
     """The same model as counting-process rows: row (start, stop] (start = before every time
     when the input has none) cut into the pieces (max(start, t_k - 1), min(stop, t_{k+1} - 1)]
     that hold at least one integer day; a piece carries the event when it ends at the row's
@@ -145,7 +149,7 @@ def split_counting(data, cuts: Sequence[int], tvc_cols: Sequence[int] = ()) -> S
     xr = _dense_rows(data)
     first = int(np.min(data.stop)) - 1 if data.n else 0
     lo_all = min(first, min(cuts) - 1)
-    stop, start, event, stratum, xrows = [], [], [], [], []
+    stop, start, event, stratum, xrows, source = [], [], [], [], [], []
     for i in range(data.n):
         a = lo_all if data.start is None else int(data.start[i])
         b = int(data.stop[i])
@@ -159,4 +163,6 @@ def split_counting(data, cuts: Sequence[int], tvc_cols: Sequence[int] = ()) -> S
             event.append(1 if (data.event[i] and pb == b) else 0)
             stratum.append(int(sidx[i]))
             xrows.append([(base[j] + (k if j in tv else 0), v) for j, v in xr[i]])
-    return _assemble(stop, start, event, stratum, xrows, p_out, data.val is not None)
+            source.append(i)
+    return _assemble(stop, start, event, stratum, xrows, p_out, data.val is not None,
+                     source if return_source else None)

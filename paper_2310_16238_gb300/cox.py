@@ -67,7 +67,8 @@ class cox_split(C.Structure):
 
 
 class cox_cv(C.Structure):
-    _fields_ = [("n_folds", C.c_int32), ("n_path", C.c_int32), ("fold", C.c_void_p), ("path", C.c_void_p)]
+    _fields_ = [("n_folds", C.c_int32), ("n_path", C.c_int32), ("fold", C.c_void_p), ("path", C.c_void_p),
+                ("split", C.c_void_p)]
 
 
 class cox_server_options(C.Structure):
@@ -247,25 +248,29 @@ def cox_create_split(data, cuts, tvc_cols=(), opts=None, precision=COX_FP64, str
     return h
 
 
-def cox_cv_path(data, folds, path, opts, n_folds=None, precision=COX_FP64, stream=None, engine=COX_ENGINE_AUTO):
+def cox_cv_path(data, folds, path, opts, n_folds=None, precision=COX_FP64, stream=None, engine=COX_ENGINE_AUTO,
+                cuts=None, tvc_cols=()):
     """Cross-validated penalty path (cox_cv_path): ``folds`` holds a fold id per row, ``path``
     the L1 weights (or L2 variances) in the order to walk. Returns a dict with ``cvl`` (per path
     value), ``beta`` (n_path x p full-data fits), ``best`` (index of the largest cvl) and
-    ``info`` (per value: the training fits, then the full-data fit)."""
+    ``info`` (per value: the training fits, then the full-data fit). With ``cuts`` every fit is
+    on the time-split view (cox_create_split) and ``beta`` has the view's columns."""
     d, keep = make_data(data)
+    sp, skeep = (None, None) if cuts is None else make_split(cuts, tvc_cols)
     o, pen = make_options(opts, precision, stream, 0, engine)
     f = folds.contiguous() if hasattr(folds, "data_ptr") else np.ascontiguousarray(folds, dtype=np.int32)
     K = int(n_folds) if n_folds is not None else int((f.max().item() if hasattr(f, "data_ptr") else f.max()) + 1)
     pth = np.ascontiguousarray(path, dtype=np.float64)
     L = int(pth.shape[0])
-    cv = cox_cv(K, L, _ptr(f), _ptr(pth))
+    cv = cox_cv(K, L, _ptr(f), _ptr(pth), C.cast(C.pointer(sp), C.c_void_p) if sp is not None else None)
+    p_out = int(data.p) if cuts is None else cox_split_columns(data.p, cuts, tvc_cols)
     cvl = np.zeros(L)
-    beta = np.zeros((L, max(int(data.p), 1)))
+    beta = np.zeros((L, max(p_out, 1)))
     infos = (cox_fit_info * (L * (K + 1)))()
     best = C.c_int32(-1)
     rc = _check(lib().cox_cv_path(C.byref(d), C.byref(o), C.byref(cv), _ptr(cvl), _ptr(beta), infos, C.byref(best)))
     info = [[infos[i * (K + 1) + m].as_dict() for m in range(K + 1)] for i in range(L)]
-    return dict(cvl=cvl, beta=beta[:, :int(data.p)], best=int(best.value), info=info, status=rc)
+    return dict(cvl=cvl, beta=beta[:, :p_out], best=int(best.value), info=info, status=rc)
 
 
 def make_folds(n_rows, n_folds, seed=0, subject=None):

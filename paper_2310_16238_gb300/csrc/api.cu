@@ -798,7 +798,12 @@ int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv,
     else o.l2_var = cv->path[i];
   };
   set_value(0);
-  const int32_t p = data->p;
+  int32_t p = data->p;
+  if (cv->split) {
+    std::string err;
+    const int rc = split_columns(data->p, cv->split, &p, &err);
+    if (rc) return fail(nullptr, rc, err);
+  }
   std::vector<cox_handle *> hs(size_t(K) + 1, nullptr);
   auto release = [&]() {
     for (cox_handle *h : hs) cox_destroy(h);
@@ -823,10 +828,22 @@ int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv,
         rc = fail(nullptr, rc, err.empty() ? "cox_cv_path: training set construction failed" : err);
         break;
       }
-      rc = cox_create(&view, &o, &hs[size_t(k)]);
+      if (cv->split) {   // the training set's time-split view
+        BufferSet vb2;
+        cox_data view2{};
+        rc = build_split_view(&view, cv->split, s, vb2, &view2, &err);
+        if (rc) {
+          cudaGetLastError();
+          rc = fail(nullptr, rc, err.empty() ? "cox_cv_path: split view construction failed" : err);
+          break;
+        }
+        rc = cox_create(&view2, &o, &hs[size_t(k)]);
+      } else {
+        rc = cox_create(&view, &o, &hs[size_t(k)]);
+      }
     }
     if (own) cudaStreamDestroy(own);
-    if (!rc) rc = cox_create(data, &o, &hs[size_t(K)]);
+    if (!rc) rc = cv->split ? cox_create_split(data, cv->split, &o, &hs[size_t(K)]) : cox_create(data, &o, &hs[size_t(K)]);
     if (rc) {
       release();
       return rc;

@@ -87,3 +87,25 @@ def test_cv_rejects_bad_arguments(bad):
     with pytest.raises(cox.CoxError) as e:
         cox.cox_cv_path(d, fold, path, o, n_folds=K)
     assert e.value.code == cox.COX_E_INVALID
+
+
+def test_cv_on_the_time_split_view():
+    """10-fold-style CV of a model whose treatment coefficient steps at a cut day (the paper's
+    §3.3 workflow): training sets and the full data are split on the device; the oracle walks
+    the same path on its counting-process split, each piece in its source row's fold."""
+    from oracle import split as osplit
+    d = mid(56, n=3000, p=8, n_strata=3)
+    fold = cox.make_folds(d.n, 4, seed=6)
+    cuts, tvc = [60, 140], [0, 5]
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-9)
+    path = [0.1, 0.5, 2.0]
+    r = cox.cox_cv_path(d, fold, path, o, n_folds=4, cuts=cuts, tvc_cols=tvc)
+    pv = osplit.view_columns(d.p, len(cuts), tvc)[1]
+    assert r["beta"].shape == (len(path), pv)
+    sc, src = osplit.split_counting(d, cuts, tvc, return_source=True)
+    sweeps = [[f["sweeps"] for f in row] for row in r["info"]]
+    cvl, betas, infos = ocv.cv_path(sc, o, fold[src], path, n_folds=4, sweeps=sweeps)
+    scale = sum(abs(f["loglik"]) for row in infos for f in row)
+    assert np.max(np.abs(r["cvl"] - cvl)) <= 1e-9 * scale
+    for i in range(len(path)):
+        assert _rel(r["beta"][i], betas[i]) <= 1e-9

@@ -850,6 +850,20 @@ int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv,
     }
   }
   const size_t n = size_t(K) + 1;
+  // the fits of one value run as one batch, unless every fit qualifies for the single-fit
+  // incremental kernel but not for its batched form (dense columns, the group-dense
+  // configuration): then one after the other, which is faster for fits of this size
+  bool sequential = o.precision == COX_FP64 && (o.engine == COX_ENGINE_AUTO || o.engine == COX_ENGINE_INCR);
+  bool batchable = sequential;
+  for (size_t m = 0; m < n && sequential; ++m) {
+    Prepared &P = hs[m]->sd->prep;
+    sequential = P.inc_T > 0 && D(hs[m]).p > 0;
+    std::string err;
+    if (batchable && (P.inc_n_halt > 0 || P.inc_variant != 0 || prepare_compact_incr(&P, o.precision, hs[m]->stream, &err) ||
+                      P.cinc_T <= 0))
+      batchable = false;
+  }
+  sequential = sequential && !batchable;
   std::vector<std::vector<double>> prev(n, std::vector<double>(size_t(std::max(p, 1)))), cur = prev;
   std::vector<const double *> b0(n);
   std::vector<double *> bo(n);
@@ -864,7 +878,14 @@ int cox_cv_path(const cox_data *data, const cox_options *opts, const cox_cv *cv,
       b0[m] = prev[m].data();
       bo[m] = cur[m].data();
     }
-    rc = cox_batch_fit(hs.data(), int32_t(n), i == 0 ? nullptr : b0.data(), bo.data(), fi.data());
+    if (sequential) {
+      for (size_t m = 0; m < n && rc >= 0; ++m) {
+        const int r = cox_fit(hs[m], i == 0 ? nullptr : b0[m], bo[m], &fi[m]);
+        rc = r < 0 ? r : std::max(rc, r);
+      }
+    } else {
+      rc = cox_batch_fit(hs.data(), int32_t(n), i == 0 ? nullptr : b0.data(), bo.data(), fi.data());
+    }
     if (rc < 0) break;
     if (rc > worst) worst = rc;
     double score = 0.0;

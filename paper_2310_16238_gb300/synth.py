@@ -359,6 +359,56 @@ def synthetic_e1(n: int = 1_000_000, p: int = 2000, k: int = 50_000, density: fl
     return data, CoxOptions(penalty=PEN_L1, lam=math.sqrt(2.0), tol=1e-8)
 
 
+def ps_stratified_cohort(n: int = 946_911, p: int = 9_976, k: int = 10, treated: float = 0.23,
+                         dens_lo: float = 1.4e-3, dens_hi: float = 0.14, hr: float = 0.82, event_frac: float = 0.05,
+                         max_days: int = 1825, n_support: int = 50, lam_per_n: float = 1e-4,
+                         seed: int = SEED_BASE + 9):
+    """A new-user cohort stratified on the propensity score (paper §3.2 shape: 946,911 patients,
+    9,976 baseline covariates at about 97 % sparsity, 23 % initiating the comparator, K = 5, 10
+    or 20 equal strata of the score).
+
+    Column 0 is the treatment; columns 1..p binary baseline covariates with density log-uniform
+    in [dens_lo, dens_hi] (mean 3 %). The treatment probability depends on the first 20 baseline
+    covariates through a logistic score; strata are the score's K quantile bins. Hazard
+    h exp(x'beta) hr^treat, ``n_support`` baseline coefficients ~ N(0, 0.3^2), h chosen by bisection
+    for ~``event_frac`` events, censoring uniform on [1, max_days]. Options: L1 with gamma =
+    lam_per_n * n on the baseline covariates, the treatment unpenalized (§3.2).
+    """
+    rng = np.random.default_rng(seed)
+    dens = np.exp(rng.uniform(math.log(dens_lo), math.log(dens_hi), p))
+    base_cols = []
+    for j in range(p):
+        m = int(rng.binomial(n, dens[j]))
+        base_cols.append(np.sort(rng.choice(n, size=m, replace=False)))
+    score = np.full(n, math.log(treated / (1.0 - treated)))
+    w = rng.normal(0.0, 0.5, min(20, p))
+    for j in range(min(20, p)):
+        score[base_cols[j]] += w[j]
+    prob = 1.0 / (1.0 + np.exp(-score))
+    treat = rng.random(n) < prob
+    order = np.argsort(prob, kind="stable")
+    stratum = np.empty(n, np.int64)
+    stratum[order] = (np.arange(n) * k) // n
+    cols = [np.flatnonzero(treat)] + base_cols
+    beta = np.zeros(p + 1)
+    beta[0] = math.log(hr)
+    sup = 1 + rng.choice(p, size=min(n_support, p), replace=False)
+    beta[sup] = rng.normal(0.0, 0.3, len(sup))
+    eta = np.zeros(n)
+    for j in np.flatnonzero(beta):
+        eta[cols[j]] += beta[j]
+    e_draw = rng.exponential(1.0, n)
+    cens = rng.uniform(1.0, max_days, n)
+    h = _bisect(lambda hh: float(np.mean(e_draw / (hh * np.exp(eta)) <= cens)), 1e-12, 1e3, event_frac, increasing=True)
+    t = e_draw / (h * np.exp(eta))
+    ev = (t <= cens).astype(np.uint8)
+    y = np.maximum(np.ceil(np.minimum(t, cens)), 1).astype(np.int64)
+    data = finalize(y, ev, stratum, None, cols, None, p + 1, beta, "ps_stratified_cohort")
+    pen = np.ones(p + 1, np.uint8)
+    pen[0] = 0
+    return data, CoxOptions(penalty=PEN_L1, lam=lam_per_n * n, tol=1e-8, penalize=pen)
+
+
 def subset_rows(data: CoxData, rows: np.ndarray) -> CoxData:
     """Restrict a data set to ``rows`` (sorted row ids); keeps the sort order."""
     rows = np.asarray(rows, dtype=np.int64)

@@ -95,10 +95,7 @@ ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 # DRAM bytes (read + write) per coordinate step of the dominant kernel, from one ncu capture of
 # the same kernel on the same workload (launch total / steps it ran); the summaries and commands
 # are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
-TRAFFIC = {
-    ("incremental", "stratified_sparse", "fp64"): (156.857856e6 + 34.779648e6) / 2001,
-    ("incremental", "time_varying", "fp64"): (1233.798912e6 + 5819.235072e6) / 20001,
-}
+TRAFFIC = {}
 
 
 def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):

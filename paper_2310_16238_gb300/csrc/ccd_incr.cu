@@ -26,7 +26,8 @@
 // the log-likelihood are FP64. v is held as a double-word per position (vdw), so the float
 // exponent range applies: |eta - shift| above kIncRange raises COX_E_RANGE (the library then
 // falls back to an FP64 engine). Column j+2's entries and their eta and v are fetched while step
-// j waits on the exchange.
+// j waits on the exchange, and column j+1's suffix sums are prepared while the step's records are
+// summed, in a form that takes step j's update as one multiply-add per tie group.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,13 +72,17 @@ struct IncSmem {
   static constexpr size_t o_lpos = 0;                                   // u32 [4][cap] entry positions
   static constexpr size_t o_lv = o_lpos + 4 * 4 * LC;                   // dw  [4][cap] v at the entries
   static constexpr size_t o_le = o_lv + 4 * 8 * LC;                     // f64 [4][cap] eta at the entries
-  static constexpr size_t o_u0 = o_le + 4 * 8 * LC;                     // dw  [2][cap] suffixes of v: this
-  static constexpr size_t o_u1 = o_u0 + 8 * LC;                         //   step's column, the previous one's
-  static constexpr size_t o_cutb = o_u1 + 8 * LC;                       // u32 [W] stratum ends
+  // dw [cap] x 2: segmented suffix sums of v over the current column's entries before the pending
+  // update (A), and over those of its entries that the pending update changes (B)
+  static constexpr size_t o_ua = o_le + 4 * 8 * LC;
+  static constexpr size_t o_ub = o_ua + 8 * LC;
+  static constexpr size_t o_cutb = o_ub + 8 * LC;                       // u32 [W] stratum ends
   static constexpr size_t o_cutp = o_cutb + 4 * W;                      // i32 [W] prefix counts
   static constexpr size_t o_headb = o_cutp + 4 * W;                     // u32 [W] read positions
   static constexpr size_t o_headp = o_headb + 4 * W;                    // i32 [W]
-  static constexpr size_t o_gs0 = o_headp + 4 * W;                      // dw  [gcap] dense-scan S0
+  // dw [gcap]: a rebuild's dense-scan S0 per group; otherwise each group's S1 of the last step
+  // (without the later tiles' share), which times e^dbeta - 1 is the change of its S0
+  static constexpr size_t o_gs0 = o_headp + 4 * W;
   static constexpr size_t o_gseen = o_gs0 + 8 * GC;                     // u8  [gcap]
   static constexpr size_t o_rec = inc_al16(o_gseen + GC);               // 8-byte slots [6][C] record payloads
   static constexpr size_t o_rref = o_rec + 8 * kIncRec * kIncMaxCtas;   // dw [C][2] refresh records
@@ -91,7 +96,8 @@ struct IncSmem {
   static constexpr size_t o_kg = o_cmask + 4 * W;
   static constexpr size_t o_ginv = inc_al16(o_kg + 2 * 4 * KG);          // dw [gcap] 1 / S0 per group (same)
   static constexpr size_t o_fce = o_ginv + 8 * KG;                        // u8 [4][cap] segment ends of each list (same)
-  static constexpr size_t bytes = o_fce + 4 * KE;
+  static constexpr size_t o_mfl = o_fce + 4 * KE;                         // u8 [cap] next-list entries in the current column
+  static constexpr size_t bytes = o_mfl + LC;
 };
 
 // One tie group of this CTA (thread h owns group h): its risk-set sum S0, read position (relative
@@ -321,6 +327,7 @@ static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo,
     if (int(threadIdx.x) == th0) atomicCAS(serr, 0, COX_E_INVALID);
     n = 0;
   }
+#pragma unroll 1
   for (int m = int(threadIdx.x) - th0; m >= 0 && m < n; m += nth) {
     const uint32_t e = D.idx[qa + m];
     int q = int(e & kPosMask) - lo;
@@ -361,6 +368,7 @@ static __device__ void inc_seg_suffix1(dw x, int f, int nact, dw *out, dw (*s_ag
   if (warp == 0 && nwa > 1) {
     dw a = s_agg[0][lane];
     int h = s_flg[0][lane];
+#pragma unroll 1
     for (int off = 1; off < nwa; off <<= 1) {
       const dw y = dw_shfl_down(a, off);
       const int g = __shfl_down_sync(kFull, h, off);
@@ -377,6 +385,110 @@ static __device__ void inc_seg_suffix1(dw x, int f, int nact, dw *out, dw (*s_ag
   if (act) {
     if (nwa > 1 && !f) x = dw_add(x, s_agg[0][warp]);
     out[tid] = x;
+  }
+}
+
+// The scan of the next step's column, run one step ahead by warps [kPsWarp0, 32) while thread 0
+// computes the step. Two inclusive segmented suffix sums over the list's entries: of v (A)
+// and of v at the entries that mfl marks (B: those the pending update will change); f = 1 marks
+// the last entry of a segment. After the update by e^dbeta - 1 = E at the marked entries, the
+// suffix sums of v are A + E B. Each warp takes 64 consecutive entries (two per lane); the warps'
+// aggregates meet in shared memory behind one named barrier of these warps only, which all of
+// them reach whatever the list's length.
+constexpr int kPsWarp0 = 16;
+constexpr int kPsThreads = (32 - kPsWarp0) * 32;
+constexpr int kPsBarrier = 1;   // named barrier id (0 is __syncthreads)
+static_assert((32 - kPsWarp0) * 64 >= kIncThreads, "the pre-scan warps cover a full list");
+
+static __device__ void inc_prescan(const dw *lv, const uint8_t *mfl, const uint8_t *fend, const uint32_t *lp, int n,
+                                   const uint32_t *cutb, const int32_t *cutp, dw *ua, dw *ub, dw (*s_agg)[32],
+                                   int (*s_flg)[32]) {
+  const int lane = threadIdx.x & 31, c = (int(threadIdx.x) >> 5) - kPsWarp0;   // this warp's chunk
+  const int e0 = 64 * c + 2 * lane, e1 = e0 + 1;
+  const int nch = (n + 63) >> 6;
+  dw a1 = dw_make(0.0f), b1 = dw_make(0.0f), xa = dw_make(0.0f), xb = dw_make(0.0f);
+  int f1 = 1, fl = 1;
+  if (c < nch) {   // warp-uniform
+    dw a0 = dw_make(0.0f), b0 = dw_make(0.0f);
+    int f0 = 1;
+    if (e0 < n) {
+      a0 = lv[e0];
+      b0 = mfl[e0] ? a0 : dw_make(0.0f);
+      f0 = fend ? int(fend[e0]) : int(inc_seg_end(lp, n, e0, cutb, cutp));
+    }
+    if (e1 < n) {
+      a1 = lv[e1];
+      b1 = mfl[e1] ? a1 : dw_make(0.0f);
+      f1 = fend ? int(fend[e1]) : int(inc_seg_end(lp, n, e1, cutb, cutp));
+    }
+    // the lane's pair from e0 to its segment end within the pair, then across the warp's lanes
+    xa = f0 ? a0 : dw_add(a0, a1);
+    xb = f0 ? b0 : dw_add(b0, b1);
+    fl = f0 | f1;
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+      const dw ya = dw_shfl_down(xa, off), yb = dw_shfl_down(xb, off);
+      const int g = __shfl_down_sync(kFull, fl, off);
+      if (lane + off < 32) {
+        if (!fl) {
+          xa = dw_add(xa, ya);
+          xb = dw_add(xb, yb);
+        }
+        fl |= g;
+      }
+    }
+    if (lane == 0) {
+      s_agg[0][c] = xa;
+      s_agg[1][c] = xb;
+      s_flg[0][c] = fl;
+    }
+  }
+  __syncwarp();
+  asm volatile("bar.sync %0, %1;" ::"n"(kPsBarrier), "n"(kPsThreads) : "memory");
+  if (c < nch) {
+    // carry into this chunk: the later chunks' sums up to the first one that ends a segment
+    dw za = lane < nch ? s_agg[0][lane] : dw_make(0.0f), zb = lane < nch ? s_agg[1][lane] : dw_make(0.0f);
+    int h = lane < nch ? s_flg[0][lane] : 1;
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+      const dw ya = dw_shfl_down(za, off), yb = dw_shfl_down(zb, off);
+      const int g = __shfl_down_sync(kFull, h, off);
+      if (lane + off < 32) {
+        if (!h) {
+          za = dw_add(za, ya);
+          zb = dw_add(zb, yb);
+        }
+        h |= g;
+      }
+    }
+    dw ca = dw_shfl(za, c + 1), cb = dw_shfl(zb, c + 1);   // c + 1 <= 16
+    if (c + 1 >= nch) ca = cb = dw_make(0.0f);
+    // e1: its own value plus, when its segment goes on, the next lane's sum
+    const dw na = dw_shfl_down(xa, 1), nb = dw_shfl_down(xb, 1);
+    const int nf = __shfl_down_sync(kFull, fl, 1);
+    dw sa1 = a1, sb1 = b1;
+    bool open1 = !f1;   // e1's segment reaches the chunk's end
+    if (!f1 && lane < 31) {
+      sa1 = dw_add(a1, na);
+      sb1 = dw_add(b1, nb);
+      open1 = !nf;
+    }
+    if (!fl) {
+      xa = dw_add(xa, ca);
+      xb = dw_add(xb, cb);
+    }
+    if (open1) {
+      sa1 = dw_add(sa1, ca);
+      sb1 = dw_add(sb1, cb);
+    }
+    if (e0 < n) {
+      ua[e0] = xa;
+      ub[e0] = xb;
+    }
+    if (e1 < n) {
+      ua[e1] = sa1;
+      ub[e1] = sb1;
+    }
   }
 }
 
@@ -480,13 +592,14 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   uint32_t *lpos = reinterpret_cast<uint32_t *>(smem + S::o_lpos);
   dw *lv = reinterpret_cast<dw *>(smem + S::o_lv);
   double *le = reinterpret_cast<double *>(smem + S::o_le);
-  dw *u0 = reinterpret_cast<dw *>(smem + S::o_u0);
-  dw *u1 = reinterpret_cast<dw *>(smem + S::o_u1);
+  dw *ua = reinterpret_cast<dw *>(smem + S::o_ua);
+  dw *ub = reinterpret_cast<dw *>(smem + S::o_ub);
   uint32_t *cutb = reinterpret_cast<uint32_t *>(smem + S::o_cutb);
   int32_t *cutp = reinterpret_cast<int32_t *>(smem + S::o_cutp);
   uint32_t *headb = reinterpret_cast<uint32_t *>(smem + S::o_headb);
   int32_t *headp = reinterpret_cast<int32_t *>(smem + S::o_headp);
   dw *gs0 = reinterpret_cast<dw *>(smem + S::o_gs0);
+  dw *s1p = gs0;   // outside a rebuild: each group's S1 of the last step
   uint8_t *gseen = reinterpret_cast<uint8_t *>(smem + S::o_gseen);
   uint64_t *srec = reinterpret_cast<uint64_t *>(smem + S::o_rec);
   dw *sref = reinterpret_cast<dw *>(smem + S::o_rref);
@@ -496,6 +609,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   uint16_t *kg = reinterpret_cast<uint16_t *>(smem + S::o_kg);   // [4][gcap], one group per thread only
   dw *ginv = reinterpret_cast<dw *>(smem + S::o_ginv);            // [gcap], one group per thread only
   uint8_t *fce = smem + S::o_fce;                                 // [4][cap], one group per thread only
+  uint8_t *mfl = smem + S::o_mfl;                                 // [cap] next-list entries in the current column
 
   __shared__ IncState st;
   __shared__ int s_cnt[4];
@@ -542,6 +656,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     return;
   }
   const int nw = (npos + 31) >> 5;
+#pragma unroll 1
   for (int w = tid; w < nw; w += kIncThreads) { cutb[w] = 0u; headb[w] = 0u; pmask[w] = 0u; cmask[w] = 0u; }
   if (tid == 0) {
     st.j = ctl->j;
@@ -562,11 +677,13 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     s_lambda_dw = dw_from(F.lambda);
     st.book = 0;
   }
+#pragma unroll 1
   for (int jj = tid; jj < p; jj += kIncThreads) {
     bet[jj] = F.beta[jj];
     tru[jj] = F.trust[jj];
   }
   __syncthreads();
+#pragma unroll 1
   for (int gi = tid; gi < ng; gi += kIncThreads) {
     int qg = D.head_pos[ga + gi] - lo;
     if (qg < 0 || qg >= npos) {
@@ -578,6 +695,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     grp[gi].S0 = dw_make(0.0f);
     atomicOr(&headb[qg >> 5], 1u << (qg & 31));
   }
+#pragma unroll 1
   for (int k = tid; k < nc; k += kIncThreads) {
     int q = D.cut_pos[kc0 + k] - lo;
     if (q < 0 || q >= npos) {
@@ -588,6 +706,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   }
   {   // beta'dX and the penalty at the starting coefficients (same order in every CTA)
     double ex[2] = {0.0, 0.0};
+#pragma unroll 1
     for (int jj = tid; jj < p; jj += kIncThreads) {
       const double b = F.beta[jj];
       ex[0] += b * D.dX[jj];
@@ -612,6 +731,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const uint32_t *bits = warp == 1 ? cutb : headb;
     int32_t *pre = warp == 1 ? cutp : headp;
     int run = 0;
+#pragma unroll 1
     for (int base = 0; base < nw; base += 32) {
       const int c = base + lane < nw ? __popc(bits[base + lane]) : 0;
       int incl = c;
@@ -629,6 +749,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const bool last_cut = nc > 0 && D.cut_pos[kc0 + nc - 1] == hi - 1;
     int e = t;
     if (!last_cut)
+#pragma unroll 1
       for (int c = t + 1; c < C; ++c) {
         e = c;
         if (prm.tile_k[c + 1] > prm.tile_k[c]) break;
@@ -642,6 +763,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     const bool lc = k1 > prm.tile_k[tid] && D.cut_pos[k1 - 1] == prm.tile_lo[tid + 1] - 1;
     int ce = tid;
     if (!lc)
+#pragma unroll 1
       for (int c = tid + 1; c < C; ++c) {
         ce = c;
         if (prm.tile_k[c + 1] > prm.tile_k[c]) break;
@@ -649,6 +771,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     s_ce[tid] = ce;
   }
   __syncthreads();
+#pragma unroll 1
   for (int gi = tid; gi < ng; gi += kIncThreads) {
     const int seg = inc_rank(cutb, cutp, grp[gi].q);
     grp[gi].seg = seg;
@@ -747,30 +870,35 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       }
     }
     refreshed = refresh;
-    dw x1 = dw_make(0.0f);
-    int fc = 1;
     if (tid < ncur) {
       const int q = int(lp_c[tid] & kPosMask);
       atomicOr(&cmask[q >> 5], 1u << (q & 31));
-      x1 = lv_c[tid];
-      fc = Cfg::kGpt == 1 ? int(fce[sc * S::KE + tid]) : int(inc_seg_end(lp_c, ncur, tid, cutb, cutp));
     }
-    // ---- 3. segmented suffix sums of v over the current column (this step's buffer); the
-    //         previous step's, over the previous column, times e^dbeta - 1 is the change of S0
-    //         (binary X: the update multiplies v by e^dbeta at that column's entries)
-    dw *const ucur = (base & 1) ? u0 : u1;
-    const dw *const uprev = (base & 1) ? u1 : u0;
+    // ---- 3. suffix sums of v over the current column: after a rebuild a segmented scan of the
+    //         reloaded list (into A, B unused); otherwise A + E B from the scan run one step ahead
+    //         (binary X: the pending update multiplies v by e^dbeta at the previous column's
+    //         entries). The previous step's S1 per group, times E, is the change of S0.
     if (trace) trace[2] = uint64_t(clock64());
-    inc_seg_suffix1(x1, fc, ncur, ucur, s_agg, s_flg);
+    if (refresh) {
+      dw x1 = dw_make(0.0f);
+      int fc = 1;
+      if (tid < ncur) {
+        x1 = lv_c[tid];
+        fc = Cfg::kGpt == 1 ? int(fce[sc * S::KE + tid]) : int(inc_seg_end(lp_c, ncur, tid, cutb, cutp));
+      }
+      inc_seg_suffix1(x1, fc, ncur, ua, s_agg, s_flg);
+    }
     if (trace) trace[3] = uint64_t(clock64());
     __syncthreads();
-    // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
-    auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? ucur[0] : dw_make(0.0f); };
-    if (trace) trace[4] = uint64_t(clock64());
     if (tid < np) {   // the marks of the previous column are read; clear them for the next step
       const int q = int(lp_p[tid] & kPosMask);
       atomicAnd(&pmask[q >> 5], ~(1u << (q & 31)));
     }
+    const dw Es = refresh ? dw_make(0.0f) : st.E;
+    auto s1_at = [&](int k) { return refresh ? ua[k] : dw_add(ua[k], dw_mul(Es, ub[k])); };
+    // head-segment sum of column j's v in this tile (what the earlier tiles of the stratum need)
+    auto head1 = [&]() { return (ncur > 0 && inc_rank(cutb, cutp, int(lp_c[0] & kPosMask)) == 0) ? s1_at(0) : dw_make(0.0f); };
+    if (trace) trace[4] = uint64_t(clock64());
     dw C1;
     if (refresh) {
       // ---- carries of the rebuilt S0 and of S1 from one exchange of the tiles' head sums
@@ -792,12 +920,14 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       __syncthreads();
       if (warp < 2) {
         dw c0 = dw_make(0.0f);
+#pragma unroll 1
         for (int c = t + 1 + lane; c <= s_chain_end; c += 32) c0 = dw_add(c0, sref[2 * c + warp]);
 #pragma unroll 1
         for (int off = 16; off > 0; off >>= 1) c0 = dw_add(c0, dw_shfl_down(c0, off));
         if (lane == 0) s_carry[warp] = c0;
       }
       __syncthreads();
+#pragma unroll 1
       for (int gi = tid; gi < ng; gi += kIncThreads) {
         dw S0 = gs0[gi];
         if (!gseen[gi]) S0 = dw_add(S0, s_dcar[grp[gi].q / RW]);
@@ -815,10 +945,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           dw S0 = grp[gi].S0;
           bool upd = false;
           if (np > 0) {
-            const int k = Cfg::kGpt == 1 ? int(kg[sp * S::KG + gi])
-                                         : int(inc_first_entry(lp_p, np, grp[gi].q, grp[gi].seg, cutb, cutp));
-            if (k != kNoEntry) {
-              S0 = dw_add(S0, dw_mul(st.E, uprev[k]));
+            const dw sp1 = s1p[gi];
+            if (!dw_is_zero(sp1)) {
+              S0 = dw_add(S0, dw_mul(st.E, sp1));
               upd = true;
             }
           }
@@ -849,8 +978,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           dw s1 = dw_make(0.0f);
           if (ncur > 0) {
             const int k = Cfg::kGpt == 1 ? int(kg[sc * S::KG + gi]) : int(inc_first_entry(lp_c, ncur, g.q, g.seg, cutb, cutp));
-            if (k != kNoEntry) s1 = ucur[k];
+            if (k != kNoEntry) s1 = s1_at(k);
           }
+          s1p[gi] = s1;
           if (g.tail) s1 = dw_add(s1, C1);
           if (!dw_is_zero(s1)) {
             const dw r = Cfg::kGpt == 1 ? dw_mul(s1, ginv[gi]) : dw_div(s1, g.S0);
@@ -880,10 +1010,12 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     if (trace && !gwarp) trace[6] = uint64_t(clock64());
     if (nwarp) {
       const int qnx = tid < nnx ? int(lp_n[tid] & kPosMask) : 0;
+      const bool inj = tid < nnx && ((cmask[qnx >> 5] >> (qnx & 31)) & 1u);
+      if (tid < nnx) mfl[tid] = uint8_t(inj);
       if (tid < nnx && qnx <= s_cut0) {
         const dw vnx = lv_n[tid];
         r_R = vnx;
-        if ((cmask[qnx >> 5] >> (qnx & 31)) & 1u) r_I = vnx;
+        if (inj) r_I = vnx;
       }
       if (__any_sync(kFull, !dw_is_zero(r_R))) {
 #pragma unroll 1
@@ -916,8 +1048,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const int nv = warp < 2 ? min((ng + 31) >> 5, 32) : (nnx + 31) >> 5;
       dw a = lane < nv ? s_red[v][lane] : dw_make(0.0f);
       if (warp < 2)
+#pragma unroll 1
         for (int off = 1; off < nv; off <<= 1) a = dw_add_same(a, dw_shfl_down(a, off));
       else
+#pragma unroll 1
         for (int off = 1; off < nv; off <<= 1) a = dw_add(a, dw_shfl_down(a, off));
       if (lane == 0) s_pay[warp < 2 ? warp : warp + 1] = *reinterpret_cast<const uint64_t *>(&a);   // 0 G1, 1 G2, 4 R, 5 I
       if (trace) trace[9] = uint64_t(clock64());
@@ -925,6 +1059,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const int nv = min((ng + 31) >> 5, 32);
       double a = (need_ll && lane < nv) ? s_rll[lane] : 0.0;
       if (need_ll)
+#pragma unroll 1
         for (int off = 1; off < nv; off <<= 1) a += __shfl_down_sync(kFull, a, off);
       if (lane == 0) s_pay[2] = uint64_t(__double_as_longlong(a));
     } else if (tid == 5 * 32) {
@@ -980,8 +1115,10 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         s_pre = q;
       }
       if (Cfg::kGpt == 1) {   // the next column's first entries per group and segment ends, for its step
+#pragma unroll 1
         for (int gi = tid - C; gi < ng; gi += kIncThreads - C)
           kg[sn * S::KG + gi] = inc_first_entry(lp_n, nnx, grp[gi].q, grp[gi].seg, cutb, cutp);
+#pragma unroll 1
         for (int k = tid - C; k < nnx; k += kIncThreads - C) fce[sn * S::KE + k] = inc_seg_end(lp_n, nnx, k, cutb, cutp);
       }
       if (prm.halt && prm.halt[jf]) {   // the launch ends before it
@@ -1000,6 +1137,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       const int v = warp >> 2, qtr = warp & 3;   // payload 0 G1 / 1 G2, quarter of the CTAs
       const int c0 = (C * qtr) >> 2, c1 = (C * (qtr + 1)) >> 2;
       dw a = dw_make(0.0f);
+#pragma unroll 1
       for (int c = c0 + lane; c < c1; c += 32) a = dw_add_same(a, slot_dw(&srec[v * kIncMaxCtas + c]));
 #pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) a = dw_add_same(a, dw_shfl_down(a, off));
@@ -1008,12 +1146,14 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     } else if (warp < 11) {
       const int v = warp - 5;   // payload 3 H1, 4 R, 5 I
       dw a = dw_make(0.0f);
+#pragma unroll 1
       for (int c = t + 1 + lane; c <= s_chain_end; c += 32) a = dw_add(a, slot_dw(&srec[v * kIncMaxCtas + c]));
 #pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) a = dw_add(a, dw_shfl_down(a, off));
       if (lane == 0) s_chain[v - 3] = a;
     } else if (warp == 11 && need_ll) {
       double a = 0.0;
+#pragma unroll 1
       for (int c = lane; c < C; c += 32) a += slot_f64(&srec[2 * kIncMaxCtas + c]);
 #pragma unroll 1
       for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
@@ -1021,7 +1161,11 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     }
     __syncthreads();
     if (trace) trace[14] = uint64_t(clock64());
-    // ---- 7. the coordinate step, computed identically by every CTA
+    // ---- 7. the coordinate step, computed identically by every CTA; meanwhile the next column's
+    //         A and B (its list holds v after the pending update; the update this step decides
+    //         changes the entries that mfl marks)
+    if (warp >= kPsWarp0)
+      inc_prescan(lv_n, mfl, Cfg::kGpt == 1 ? fce + sn * S::KE : nullptr, lp_n, nnx, cutb, cutp, ua, ub, s_agg, s_flg);
     if (tid == 0) {
       bool stop = false;
       if (s_anyerr) {
@@ -1095,6 +1239,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   //      updated positions
   if (!refreshed) {
     T *vt = static_cast<T *>(F.v);
+#pragma unroll 1
     for (int q = tid; q < npos; q += kIncThreads) {
       const int g = lo + q;
       const bool ex = D.exit_bits != nullptr && ((D.exit_bits[g >> 5] >> (g & 31)) & 1u);
@@ -1106,6 +1251,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   __syncthreads();
   // ---- CTA 0 writes back the coefficients, trust half-widths and the control state
   if (t == 0) {
+#pragma unroll 1
     for (int jj = tid; jj < p; jj += kIncThreads) {
       F.beta[jj] = bet[jj];
       F.trust[jj] = tru[jj];

@@ -96,8 +96,8 @@ ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 # the same kernel on the same workload (launch total / steps it ran); the summaries and commands
 # are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
 TRAFFIC = {
-    ("incremental", "stratified_sparse", "fp64"): (156.813056e6 + 34.564864e6) / 2001,
-    ("incremental", "time_varying", "fp64"): (1242.622208e6 + 5819.201792e6) / 20001,
+    ("incremental", "stratified_sparse", "fp64"): (157.152512e6 + 34.250240e6) / 2001,
+    ("incremental", "time_varying", "fp64"): (1243.523072e6 + 5819.752192e6) / 20001,
 }
 
 

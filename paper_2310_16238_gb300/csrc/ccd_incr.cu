@@ -43,7 +43,7 @@
 namespace coxgb {
 
 constexpr int kIncThreads = 1024;
-constexpr int kIncMaxCtas = 256;
+constexpr int kIncMaxCtas = 160;   // CTAs of one fit at most (one per SM; 152 on GB300)
 constexpr int kIncRec = kIncRecWords / 2;   // step record payloads: G1, G2, LL, H1, R, I
 constexpr uint32_t kTagErr = 0x80000000u;   // tag bit: the writer raised an error
 constexpr double kIncRange = 60.0;          // |eta - shift| that keeps every sum inside float range
@@ -89,14 +89,16 @@ struct IncSmem {
   static constexpr size_t o_grp = o_rref + 8 * 2 * kIncMaxCtas;         // GroupSlot [gcap]
   static constexpr size_t o_pmask = o_grp + 24 * GC;                    // u32 [W] the previous column's positions
   static constexpr size_t o_cmask = o_pmask + 4 * W;                    // u32 [W] the current column's positions
-  // u16 [4][gcap]: per list slot and tie group, the first entry at or after the group's read
-  // position in its stratum segment (kNoEntry: none); kept for one group per thread only
+  // u16 [gcap]: per tie group, the first entry of the current column's list at or after the
+  // group's read position in its stratum segment (kNoEntry: none). A step reads it for its own
+  // column before the exchange wait, where it is rebuilt for the next column, so one copy serves.
+  // Kept for one group per thread only: with four, building it off the chain (binary searches of
+  // 4,096 groups by the threads not polling) outlasts the wait, and the step searches instead.
   static constexpr int KG = Cfg::kGpt == 1 ? GC : 0;
-  static constexpr int KE = Cfg::kGpt == 1 ? LC : 0;
   static constexpr size_t o_kg = o_cmask + 4 * W;
-  static constexpr size_t o_ginv = inc_al16(o_kg + 2 * 4 * KG);          // dw [gcap] 1 / S0 per group (same)
-  static constexpr size_t o_fce = o_ginv + 8 * KG;                        // u8 [4][cap] segment ends of each list (same)
-  static constexpr size_t o_mfl = o_fce + 4 * KE;                         // u8 [cap] next-list entries in the current column
+  static constexpr size_t o_ginv = inc_al16(o_kg + 2 * KG);               // dw [gcap] 1 / S0 per group (same)
+  static constexpr size_t o_fce = o_ginv + 8 * KG;                        // u8 [cap] segment ends of a list (as kg)
+  static constexpr size_t o_mfl = o_fce + LC;                             // u8 [cap] next-list entries in the current column
   static constexpr size_t bytes = o_mfl + LC;
 };
 
@@ -390,7 +392,7 @@ static __device__ void inc_seg_suffix1(dw x, int f, int nact, dw *out, dw (*s_ag
 
 // The scan of the next step's column, run one step ahead by warps [kPsWarp0, 32) while thread 0
 // computes the step. Two inclusive segmented suffix sums over the list's entries: of v (A)
-// and of v at the entries that mfl marks (B: those the pending update will change); f = 1 marks
+// and of v at the entries that mfl marks (B: those the pending update will change); fend = 1 marks
 // the last entry of a segment. After the update by e^dbeta - 1 = E at the marked entries, the
 // suffix sums of v are A + E B. Each warp takes 64 consecutive entries (two per lane); the warps'
 // aggregates meet in shared memory behind one named barrier of these warps only, which all of
@@ -400,9 +402,8 @@ constexpr int kPsThreads = (32 - kPsWarp0) * 32;
 constexpr int kPsBarrier = 1;   // named barrier id (0 is __syncthreads)
 static_assert((32 - kPsWarp0) * 64 >= kIncThreads, "the pre-scan warps cover a full list");
 
-static __device__ void inc_prescan(const dw *lv, const uint8_t *mfl, const uint8_t *fend, const uint32_t *lp, int n,
-                                   const uint32_t *cutb, const int32_t *cutp, dw *ua, dw *ub, dw (*s_agg)[32],
-                                   int (*s_flg)[32]) {
+static __device__ void inc_prescan(const dw *lv, const uint8_t *mfl, const uint8_t *fend, int n, dw *ua, dw *ub,
+                                   dw (*s_agg)[32], int (*s_flg)[32]) {
   const int lane = threadIdx.x & 31, c = (int(threadIdx.x) >> 5) - kPsWarp0;   // this warp's chunk
   const int e0 = 64 * c + 2 * lane, e1 = e0 + 1;
   const int nch = (n + 63) >> 6;
@@ -414,12 +415,12 @@ static __device__ void inc_prescan(const dw *lv, const uint8_t *mfl, const uint8
     if (e0 < n) {
       a0 = lv[e0];
       b0 = mfl[e0] ? a0 : dw_make(0.0f);
-      f0 = fend ? int(fend[e0]) : int(inc_seg_end(lp, n, e0, cutb, cutp));
+      f0 = int(fend[e0]);
     }
     if (e1 < n) {
       a1 = lv[e1];
       b1 = mfl[e1] ? a1 : dw_make(0.0f);
-      f1 = fend ? int(fend[e1]) : int(inc_seg_end(lp, n, e1, cutb, cutp));
+      f1 = int(fend[e1]);
     }
     // the lane's pair from e0 to its segment end within the pair, then across the warp's lanes
     xa = f0 ? a0 : dw_add(a0, a1);
@@ -606,9 +607,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   GroupSlot *grp = reinterpret_cast<GroupSlot *>(smem + S::o_grp);
   uint32_t *pmask = reinterpret_cast<uint32_t *>(smem + S::o_pmask);
   uint32_t *cmask = reinterpret_cast<uint32_t *>(smem + S::o_cmask);
-  uint16_t *kg = reinterpret_cast<uint16_t *>(smem + S::o_kg);   // [4][gcap], one group per thread only
+  uint16_t *kg = reinterpret_cast<uint16_t *>(smem + S::o_kg);   // [gcap]
   dw *ginv = reinterpret_cast<dw *>(smem + S::o_ginv);            // [gcap], one group per thread only
-  uint8_t *fce = smem + S::o_fce;                                 // [4][cap], one group per thread only
+  uint8_t *fce = smem + S::o_fce;                                 // [cap]
   uint8_t *mfl = smem + S::o_mfl;                                 // [cap] next-list entries in the current column
 
   __shared__ IncState st;
@@ -796,11 +797,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     }
   }
   __syncthreads();
-  if (Cfg::kGpt == 1 && st.state == kRunning) {
-    for (int sl = 1; sl <= 2; ++sl) {
-      if (tid < ng) kg[sl * S::KG + tid] = inc_first_entry(lpos + sl * LC, s_cnt[sl], grp[tid].q, grp[tid].seg, cutb, cutp);
-      if (tid < s_cnt[sl]) fce[sl * S::KE + tid] = inc_seg_end(lpos + sl * LC, s_cnt[sl], tid, cutb, cutp);
-    }
+  if (st.state == kRunning) {   // the first column's lookups (later ones are built a step ahead)
+    if (Cfg::kGpt == 1 && tid < ng) kg[tid] = inc_first_entry(lpos + LC, s_cnt[1], grp[tid].q, grp[tid].seg, cutb, cutp);
+    if (tid < s_cnt[1]) fce[tid] = inc_seg_end(lpos + LC, s_cnt[1], tid, cutb, cutp);
   }
   __syncthreads();
   bool refreshed = false;  // the last step taken rebuilt v from eta
@@ -884,7 +883,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       int fc = 1;
       if (tid < ncur) {
         x1 = lv_c[tid];
-        fc = Cfg::kGpt == 1 ? int(fce[sc * S::KE + tid]) : int(inc_seg_end(lp_c, ncur, tid, cutb, cutp));
+        fc = int(fce[tid]);
       }
       inc_seg_suffix1(x1, fc, ncur, ua, s_agg, s_flg);
     }
@@ -977,7 +976,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
           const GroupSlot g = grp[gi];
           dw s1 = dw_make(0.0f);
           if (ncur > 0) {
-            const int k = Cfg::kGpt == 1 ? int(kg[sc * S::KG + gi]) : int(inc_first_entry(lp_c, ncur, g.q, g.seg, cutb, cutp));
+            const int k = Cfg::kGpt == 1 ? int(kg[gi]) : int(inc_first_entry(lp_c, ncur, g.q, g.seg, cutb, cutp));
             if (k != kNoEntry) s1 = s1_at(k);
           }
           s1p[gi] = s1;
@@ -1114,12 +1113,14 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
         q.tw = dw_from(q.t);
         s_pre = q;
       }
-      if (Cfg::kGpt == 1) {   // the next column's first entries per group and segment ends, for its step
+      {   // the next column's first entries per group and segment ends, for its step (this
+          // step's own were read before the exchange)
+        if (Cfg::kGpt == 1)
 #pragma unroll 1
-        for (int gi = tid - C; gi < ng; gi += kIncThreads - C)
-          kg[sn * S::KG + gi] = inc_first_entry(lp_n, nnx, grp[gi].q, grp[gi].seg, cutb, cutp);
+          for (int gi = tid - C; gi < ng; gi += kIncThreads - C)
+            kg[gi] = inc_first_entry(lp_n, nnx, grp[gi].q, grp[gi].seg, cutb, cutp);
 #pragma unroll 1
-        for (int k = tid - C; k < nnx; k += kIncThreads - C) fce[sn * S::KE + k] = inc_seg_end(lp_n, nnx, k, cutb, cutp);
+        for (int k = tid - C; k < nnx; k += kIncThreads - C) fce[k] = inc_seg_end(lp_n, nnx, k, cutb, cutp);
       }
       if (prm.halt && prm.halt[jf]) {   // the launch ends before it
         if (tid == C) s_cnt[sf] = 0;
@@ -1165,7 +1166,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     //         A and B (its list holds v after the pending update; the update this step decides
     //         changes the entries that mfl marks)
     if (warp >= kPsWarp0)
-      inc_prescan(lv_n, mfl, Cfg::kGpt == 1 ? fce + sn * S::KE : nullptr, lp_n, nnx, cutb, cutp, ua, ub, s_agg, s_flg);
+      inc_prescan(lv_n, mfl, fce, nnx, ua, ub, s_agg, s_flg);
     if (tid == 0) {
       bool stop = false;
       if (s_anyerr) {

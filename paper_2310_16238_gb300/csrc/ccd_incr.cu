@@ -1,15 +1,17 @@
-// Incremental risk-set kernel: the per-tie-group risk-set sums S0 stay in registers across
-// coordinate steps and are updated from the changed positions only (arXiv 2310.16238 §2.4-§2.7
+// Incremental risk-set kernel: the per-tie-group risk-set sums S0 stay on chip (shared memory)
+// across coordinate steps and are updated from the changed positions only (arXiv 2310.16238 §2.4-§2.7
 // for the method; this is an exact reformulation of its segmented scans, not the paper's layout).
 //
 // One cooperative launch of one 1024-thread CTA per SM runs the whole fit. CTA t owns the risk
 // positions [tile_lo[t], tile_lo[t+1]) and the tie groups whose read position lies there (thread
-// h holds group h: its S0, read position, stratum segment and events). A coordinate step for
+// h holds group h, or groups h + 1024 i in the group-dense configuration: S0, read position,
+// stratum segment and events). A coordinate step for
 // column j touches only the positions of column j's nonzeros:
 //   * the previous step's update (eta += dbeta, eq. parallel_xb; v = +-exp(eta - shift), eq.
 //     parallel_d) changes v at column j-1's entries by dD = v (e^dbeta - 1); S0 of every group
-//     grows by the segmented suffix sum of dD from its read position (strata are segments), plus,
-//     for groups whose stratum continues past the tile, the change in the later tiles;
+//     grows by the segmented suffix sum of dD from its read position (strata are segments),
+//     which is (e^dbeta - 1) times the group's S1 of the previous step (binary X), plus, for
+//     groups whose stratum continues past the tile, the change in the later tiles;
 //   * S1 of every group is the segmented suffix sum of v over column j's entries, plus the later
 //     tiles' share, so the tie-group ratios of eqs. (parallel_g)/(parallel_h) cost
 //     O(groups + entries) per tile instead of O(positions);
@@ -26,8 +28,8 @@
 // the log-likelihood are FP64. v is held as a double-word per position (vdw), so the float
 // exponent range applies: |eta - shift| above kIncRange raises COX_E_RANGE (the library then
 // falls back to an FP64 engine). Column j+2's entries and their eta and v are fetched while step
-// j waits on the exchange, and column j+1's suffix sums are prepared while the step's records are
-// summed, in a form that takes step j's update as one multiply-add per tie group.
+// j waits on the exchange, and column j+1's suffix sums are prepared while thread 0 computes
+// step j, in a form that takes step j's update as one multiply-add per tie group.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -645,7 +647,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   double *bet = prm.bcopy + size_t(t) * 2 * size_t(p);   // this CTA's copy of beta and trust
   double *tru = bet + p;
 
-  // ---- one-time set-up: stratum ends and read positions as bitmasks, group registers, lists
+  // ---- one-time set-up: stratum ends and read positions as bitmasks, group slots, lists
   if (tid == 0) {
     s_cut0 = nc > 0 ? D.cut_pos[kc0] - lo : npos;
     s_bad = (npos > Cfg::kPosCap || ng > Cfg::kGroupCap || C > kIncMaxCtas || npos <= 0 || ng < 0) ? 1 : 0;

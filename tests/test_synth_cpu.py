@@ -117,3 +117,37 @@ def test_ps_stratified_cohort_recipe():
     assert abs(d.event.mean() - 0.05) < 0.006
     assert d.beta_true[0] == pytest.approx(math.log(0.82))
     assert o.penalize.shape == (p + 1,) and o.penalize[0] == 0 and o.penalize[1:].all()
+
+
+def test_batch_views_recipe():
+    """Uneven training sets over one shared X: outcomes x folds sets, each with its penalty grid."""
+    n_total, p = 50_000, 80
+    sets = synth.batch_views(n_total=n_total, p=p, density=0.02, n_outcomes=2, n_folds=3, n_lambdas=4,
+                             n_lo=2e3, n_hi=2e4, max_strata=7)
+    assert len(sets) == 6 and all(len(opts) == 4 for _, opts in sets)
+    for d, opts in sets:
+        _check_layout(d)
+        assert 2e3 - 1 <= d.n <= 2e4 + 1 and d.stratum.max() < 7
+        assert abs(_densities(d).mean() - 0.02) < 0.004
+        lams = np.array([o.lam for o in opts])
+        assert lams[0] == pytest.approx(1e-4 * d.n) and lams[-1] == pytest.approx(1e-1 * d.n)
+        assert np.allclose(np.diff(np.log(lams)), np.log(1e3) / 3)
+        assert np.count_nonzero(d.beta_true) == 20
+    # sets of one outcome share its coefficients; the two outcomes differ
+    assert np.array_equal(sets[0][0].beta_true, sets[2][0].beta_true)
+    assert not np.array_equal(sets[0][0].beta_true, sets[3][0].beta_true)
+
+
+def test_serving_stream_recipe():
+    reqs = synth.serving_stream(rate=20.0, duration_s=200.0)
+    t = np.array([r.arrival_s for r in reqs])
+    assert np.all(np.diff(t) > 0) and t[-1] <= 200.0
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 20.0) < 0.005                    # Poisson arrivals at 20 per second
+    assert abs(len(reqs) - 4000) < 4 * math.sqrt(4000)
+    n = np.array([r.n_subj for r in reqs], float)
+    assert n.min() >= 1e4 - 1 and n.max() <= 1e7
+    assert abs(np.log(n).mean() - 0.5 * (math.log(1e4) + math.log(1e7))) < 0.15   # log-uniform rows
+    assert abs(np.mean([r.counting for r in reqs]) - 0.5) < 0.04
+    assert abs(np.mean([r.penalty == synth.PEN_L1 for r in reqs]) - 0.5) < 0.04
+    assert min(r.k for r in reqs) >= 1 and max(r.k for r in reqs) <= 200

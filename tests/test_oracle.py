@@ -392,3 +392,65 @@ def test_first_sweep_loglik_monotone_l2():
         if prev is not None:
             assert info["objective"] <= prev + 1e-12
         prev = info["objective"]
+
+
+# ------------------------------------------------------------------ invariants of eq. strat_l
+def _rebuild(d, rows, stop, start, extra_col=None):
+    """The rows ``rows`` of d (repeats allowed) with new stop/start days and optionally one more
+    column, through the generators' sort and CSC builder."""
+    x = d.dense_x()[rows]
+    if extra_col is not None:
+        x = np.column_stack([x, extra_col])
+    p = x.shape[1]
+    cols = [np.nonzero(x[:, j])[0] for j in range(p)]
+    vals = [x[c, j] for j, c in enumerate(cols)] if (d.val is not None or extra_col is not None) else None
+    return synth.finalize(np.asarray(stop), d.event[rows], None if d.stratum is None else d.stratum[rows],
+                          None if start is None else np.asarray(start), cols, vals, p)
+
+
+@pytest.mark.parametrize("name,data,opts", tiny_cases())
+def test_time_rescaling_invariant(name, data, opts):
+    """The partial likelihood sees event times only through their order (risk sets and tie groups):
+    stretching every day by 3 changes nothing."""
+    rows = np.arange(data.n)
+    sc = _rebuild(data, rows, 3 * data.stop.astype(np.int64),
+                  None if data.start is None else 3 * data.start.astype(np.int64))
+    beta = random_beta(data.p, 0.4, seed=6)
+    l0 = oracle.loglik(data, beta)
+    assert abs(oracle.loglik(sc, beta) - l0) <= 1e-13 * abs(l0)
+    a1, a2 = oracle.grad_hess(sc, beta)
+    b1, b2 = oracle.grad_hess(data, beta)
+    assert np.allclose(a1, b1, rtol=1e-12, atol=1e-13) and np.allclose(a2, b2, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("name,data,opts", tiny_cases())
+def test_row_duplication(name, data, opts):
+    """Every row twice: each risk-set sum and each tie group's events double, so
+    l2(beta) = 2 l(beta) - 2 D log 2 (D events), and the gradient and curvature double."""
+    rows = np.repeat(np.arange(data.n), 2)
+    du = _rebuild(data, rows, data.stop[rows], None if data.start is None else data.start[rows])
+    beta = random_beta(data.p, 0.4, seed=7)
+    D = int(data.event.sum())
+    l0 = oracle.loglik(data, beta)
+    assert abs(oracle.loglik(du, beta) - (2 * l0 - 2 * D * math.log(2.0))) <= 1e-12 * abs(l0)
+    a1, a2 = oracle.grad_hess(du, beta)
+    b1, b2 = oracle.grad_hess(data, beta)
+    assert np.allclose(a1, 2 * b1, rtol=1e-12, atol=1e-12) and np.allclose(a2, 2 * b2, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,data,opts", [c for c in tiny_cases() if c[1].stratum is not None])
+def test_stratum_constant_column(name, data, opts):
+    """A covariate constant within every stratum cancels from every ratio S1/S0 of eq. strat_g:
+    its gradient and curvature vanish at any beta, and the fit leaves its coefficient at 0."""
+    ks = np.unique(data.stratum)
+    level = np.random.default_rng(8).uniform(0.5, 2.0, int(ks.max()) + 1)
+    col = level[data.stratum]
+    ex = _rebuild(data, np.arange(data.n), data.stop, data.start, extra_col=col)
+    beta = np.append(random_beta(data.p, 0.4, seed=9), 0.7)
+    g1, g2 = oracle.grad_hess(ex, beta)
+    scale = max(1.0, float(np.max(np.abs(g1[:-1]))))
+    assert abs(g1[-1]) <= 1e-12 * scale and abs(g2[-1]) <= 1e-12 * max(1.0, float(np.max(g2[:-1])))
+    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-12, max_sweeps=200)
+    b, _ = oracle.fit(ex, o)
+    b0, _ = oracle.fit(data, o)
+    assert abs(b[-1]) <= 1e-10 and np.allclose(b[:-1], b0, rtol=1e-8, atol=1e-10)

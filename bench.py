@@ -1,27 +1,42 @@
 """Benchmark: regularized stratified Cox CCD fits on GB300 (one JSON line on rank 0).
 
-Workload (default): the large stratified sparse fit -- N = 2,000,000 subjects, p = 2,000
-binary columns with log-uniform density in [1e-4, 5e-2], 100 Zipf(1.1) strata, Weibull(1.5)
-event times in integer days (~5 % events), L1 gamma = 1e-3 N, FP64, seeded synthetic data.
-A step is one complete fit through the C ABI: cox_create (device-resident inputs:
-validation, strata, tie groups, delta'X, tile plan) + cox_fit (CCD sweeps until the
-tolerance) + cox_destroy. The metric is coordinate updates per second (and fits per second).
+Default workload (the headline): the large stratified sparse fit -- N = 2,000,000 subjects,
+p = 2,000 binary columns with log-uniform density in [1e-4, 5e-2], 100 Zipf(1.1) strata,
+Weibull(1.5) event times in integer days (~5 % events), L1 gamma = 1e-3 N, FP64 precision,
+seeded synthetic data. A step is one complete fit through the C ABI: cox_create
+(device-resident inputs: validation, strata, tie groups, delta'X, tile plan) + cox_fit (CCD
+sweeps until the tolerance) + cox_destroy. The metric is coordinate updates per second.
 
-Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the fit's stream;
-L2 (129 MB) is flushed by writing a 512 MB buffer before every timed step (outside the
-events); barrier + synchronize on both sides; max over ranks. Multi-GPU (torchrun): every
-rank fits its own independent replica (weak scaling, no collective on the data path).
+At that L1 weight every coefficient stays at 0 (the fit ends after one sweep and no eta update
+runs), so the same line also carries, as sub-results measured in the same run:
+  moving   the same data at gamma = 1e-5 N (hundreds of coefficients move), timed to
+           convergence, with the error of its two-sweep iterate against the FP64 oracle;
+  batch    256 fits (4 outcomes x 4 folds x 16 L1 weights over one shared X): the plain
+           one-fit-at-a-time FP64 path against the batched launches (compensated FP32
+           streaming, FP64 streaming, FP64 incremental waves), with the HBM roofline of the
+           batched streaming kernel;
+  serving  Poisson fit requests (rows logU[1e4, 1e7], p logU[100, 2e4], density logU[1e-4,
+           1e-2], 1-200 strata, half counting-process, L1 / L2) into the continuous-batching
+           server: its capacity under a burst, then a stream at a sustainable rate with
+           p50 / p99 time-to-fit.
 
-`--impl reference` times the FP64 CPU oracle (the plain restatement of the paper's method,
-single-threaded) on a bounded sample of the same workload: each step runs a fixed number of
-coordinate updates.
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the fit's stream; L2
+(129 MB) is flushed by writing a 512 MB buffer before every timed step (outside the events);
+barrier + synchronize on both sides; max over ranks. Multi-GPU (torchrun): every rank fits its
+own independent replica (weak scaling, no collective on the data path).
+
+`--impl reference` times the FP64 CPU oracle (the plain restatement of the paper's method) on the
+box's host cores: one independent oracle process per usable core, each running the same bounded
+sample (a fixed number of coordinate updates of the same fit from beta = 0).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -34,12 +49,22 @@ sys.path.insert(0, ROOT)
 
 from paper_2310_16238_gb300 import synth  # noqa: E402
 
+METRIC = "coordinate updates/sec and fits/sec vs plain FP64 path; HBM roofline %; p99 latency"
+EXCHANGE_FLOOR_US = 0.87   # cross-SM flag round trip on GB300 (a step of one fit needs at least one)
+
 
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def hbm_peak():
+    p = _peaks()
+    if "hbm_gbs" in p:
+        return float(p["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    return 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
 
 
 class ClockSampler:
@@ -92,13 +117,10 @@ class ClockSampler:
 
 ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 
-# DRAM bytes (read + write) per coordinate step of the dominant kernel, from one ncu capture of
-# the same kernel on the same workload (launch total / steps it ran); the summaries and commands
-# are in profiles/. Keyed by (engine, workload, precision); absent = not captured for this kernel.
-TRAFFIC = {
-    ("incremental", "stratified_sparse", "fp64"): (157.152512e6 + 34.250240e6) / 2001,
-    ("incremental", "time_varying", "fp64"): (1243.523072e6 + 5819.752192e6) / 20001,
-}
+# DRAM bytes (read + write) per coordinate step of a kernel, from one ncu capture of the same kernel
+# on the same workload (launch total / steps it ran); the summaries and the commands are in
+# profiles/. Keyed by (engine, workload, precision); absent = not captured for the current kernel.
+TRAFFIC = {}
 
 
 def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):
@@ -113,11 +135,33 @@ def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, devic
     return units_per_rank * world / (slowest * 1e-3), slowest
 
 
-def workload(rank: int, scale: float = 1.0):
+def headline_workload(scale: float = 1.0, seed_offset: int = 0):
     n = int(2_000_000 * scale)
-    data, opts = synth.stratified_sparse(n=n, p=2000, k=100, seed=synth.SEED_BASE + 2 + rank)
+    data, opts = synth.stratified_sparse(n=n, p=2000, k=100, seed=synth.SEED_BASE + 2 + seed_offset)
     name = f"stratified_sparse N={n} p=2000 K=100 binary density logU[1e-4,5e-2] L1 gamma=1e-3*N"
     return data, opts, name
+
+
+def moving_options(n: int):
+    return synth.CoxOptions(penalty=synth.PEN_L1, lam=1e-5 * n, tol=1e-8)
+
+
+def headline_config(wname: str) -> dict:
+    """The workload the metric is quoted on (identical in both arms)."""
+    return {"workload": wname, "precision": "fp64 (tolerance vs the FP64 oracle: 1e-9 beta, 1e-11 log-likelihood)"}
+
+
+def dense_bytes_per_step(M: int, G: int, K: int, nnz_pos: float, s_e: int, moved: bool) -> float:
+    """Algorithmic bytes of one coordinate step of the paper's dense method (the risk sequence of
+    exp(eta) read once, the tie-group and stratum tables, column j's entries, and -- when the
+    previous coordinate moved -- its entries' eta read and written and exp(eta) written)."""
+    return s_e * M + 8.0 * G + 4.0 * (K + 1) + 4.0 * nnz_pos + ((4 + 16 + s_e) * nnz_pos if moved else 0.0)
+
+
+def incr_own_bytes_per_step(M: int, p: int, nnz_pos: float, s_e: int, moved: bool) -> float:
+    """Bytes the incremental kernel itself moves per coordinate step: column j's entries with eta and
+    v (read and, when the step moved, written) plus the dense refresh once per sweep."""
+    return (4.0 + 16.0) * nnz_pos + (16.0 * nnz_pos if moved else 0.0) + (8.0 + 8.0 + s_e) * M / p
 
 
 def dtype_of(engine, s_e):
@@ -129,76 +173,84 @@ def dtype_of(engine, s_e):
 
 
 def roofline_of(engine, data, beta, G, K, s_e, step_us, wname, precision_name):
-    """Roofline of the coordinate step of one fit (per coordinate step: the fit's CUDA-event time
-    over the steps it ran). Dense engines: FP64 instructions (FP64 path, bound by the FP64 pipe)
-    or bytes (FP32C path). Incremental engine: its O(groups + entries) arithmetic against the FP64
-    rate, plus the dense-equivalent bandwidth (the bytes the paper's dense scan moves per step over
-    this step's time)."""
+    """Roofline of the coordinate-step kernel. `achieved` = the paper's dense method's algorithmic
+    bytes per coordinate step x the steps one launch runs / the launch's CUDA-event time, against
+    the measured HBM copy bandwidth. For the incremental kernel (which reads only the changed
+    positions) the line also gives its own bytes and the latency floor of a step."""
     M = data.n if data.start is None else 2 * data.n
     nnz_mean = float(np.diff(data.col_ptr).mean())
-    moved = np.count_nonzero(beta) > 0
-    peaks = _peaks()
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    fp64_peak = 1.25e12 / 2 / 1e9   # recipe: 1.25 TFLOP/s FP64 = 0.625e12 FP64 instructions/s
-    p_cols = data.p
     nnz_pos = nnz_mean * (2.0 if data.start is not None else 1.0)
-    dense_bytes = s_e * M + 8.0 * G + 4.0 * K + 4.0 * nnz_mean + ((4 + 16 + s_e) * nnz_mean if moved else 0.0)
+    moved = bool(np.count_nonzero(beta) > 0)
+    peak, src = hbm_peak()
+    dense = dense_bytes_per_step(M, G, K, nnz_pos, s_e, moved)
+    achieved = dense / (step_us * 1e-6) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get((engine, wname.split()[0], precision_name)),
+            "kernel": f"coordinate step ({engine})", "step_us": step_us, "alg_bytes_per_step": dense,
+            "basis": "bytes of the paper's dense scan per coordinate step x steps per launch / launch time",
+            "peak_source": src}
     if engine == "incremental":
-        # per coordinate step: a suffix of dD and one of v over the column's entries, and per tie
-        # group two adds, a divide and two multiply-adds; plus the dense S0 rebuild (one add per
-        # position) once per sweep, spread over the sweep's p steps
-        alg_ops = 2.0 * nnz_pos + 5.0 * G + M / p_cols
-        # bytes: the column's entries (4) with eta and v read (8 + 8) and, when beta moved,
-        # written back; plus the rebuild's read of eta and write of v once per sweep
-        alg_bytes = (4.0 + 16.0) * nnz_pos + (16.0 * nnz_pos if moved else 0.0) + (8.0 + 8.0 + s_e) * M / p_cols
-    else:
-        alg_ops = M + nnz_mean + 4.0 * G
-        alg_bytes = dense_bytes
-    hbm_equiv = alg_bytes / (step_us * 1e-6) / 1e9
-    traffic = TRAFFIC.get((engine, wname.split()[0], precision_name))
-    if s_e == 8 or engine == "incremental":
-        achieved = alg_ops / (step_us * 1e-6) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "Gop/s (FP64)",
-                "frac": achieved / fp64_peak, "traffic": traffic, "kernel": f"ccd ({engine})", "step_us": step_us,
-                "alg_fp64_ops_per_step": alg_ops,
-                "peak_source": "derived from the recipe's FP64 rate (1.25 TFLOP/s, FMA = 2 flops); of nominal",
-                "hbm_equivalent": {"achieved_gbs": hbm_equiv, "peak_gbs": hbm_peak, "frac": hbm_equiv / hbm_peak,
-                                   "alg_bytes_per_step": alg_bytes}}
-        if engine == "incremental":
-            dense_gbs = dense_bytes / (step_us * 1e-6) / 1e9
-            roof["dense_equivalent"] = {"gbs": dense_gbs, "frac_of_hbm_peak": dense_gbs / hbm_peak,
-                                        "dense_bytes_per_step": dense_bytes}
-        return roof
-    return {"bound": "hbm", "achieved": hbm_equiv, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_equiv / hbm_peak,
-            "traffic": traffic, "kernel": f"ccd ({engine})", "step_us": step_us, "alg_bytes_per_step": alg_bytes,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        own = incr_own_bytes_per_step(M, data.p, nnz_pos, s_e, moved)
+        own_gbs = own / (step_us * 1e-6) / 1e9
+        roof["own_bytes"] = {"per_step": own, "gbs": own_gbs, "frac": own_gbs / peak,
+                             "note": "the incremental kernel reads only column j's entries and the changed "
+                                     "positions; it is bound by the latency of its step, not by bytes"}
+        roof["latency"] = {"step_us": step_us, "floor_us": EXCHANGE_FLOOR_US, "frac": EXCHANGE_FLOOR_US / step_us,
+                           "floor": "one cross-SM exchange round trip per coordinate step"}
+    return roof
 
 
-def run_ours(args, rank, world, local_rank):
+def _device_copy(data, dev):
+    import torch
+    ddev = synth.CoxData(**{**data.__dict__})
+    for f in ("stop", "start", "event", "stratum", "col_ptr", "row_idx", "val"):
+        a = getattr(data, f)
+        if a is not None:
+            setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(a)).to(dev))
+    return ddev
+
+
+def _timed_fits(cox, ddev, opts, precision, stream, flush, steps, warmup, clk=None):
+    """CUDA-event times of `steps` whole fits (create + fit + destroy), L2 flushed before each."""
+    import torch
+
+    def step():
+        h = cox.cox_create(ddev, opts, precision=precision, stream=stream.cuda_stream)
+        try:
+            return cox.cox_fit(h)
+        finally:
+            cox.cox_destroy(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    times, infos, beta = [], [], None
+    launches0 = cox.cox_launch_count()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            beta, info = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+    torch.cuda.synchronize()
+    return times, infos, beta, cox.cox_launch_count() - launches0
+
+
+def run_headline(args, rank, world, local_rank):
     import torch
     from paper_2310_16238_gb300 import cox
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    data, opts, wname = workload(rank, args.scale)
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    data, opts, wname = headline_workload(args.scale, rank)
+    precision = cox.COX_FP64
     stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "stratum", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
+    ddev = _device_copy(data, dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-
-    def step(src):
-        h = cox.cox_create(src, opts, precision=precision, stream=stream.cuda_stream)
-        try:
-            beta, info = cox.cox_fit(h)
-        finally:
-            cox.cox_destroy(h)
-        return beta, info
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            beta, info = step(ddev)
     torch.cuda.synchronize()
     h = cox.cox_create(ddev, opts, precision=precision, stream=stream.cuda_stream)
     md = cox.cox_metadata(h)
@@ -207,60 +259,362 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    times, infos = [], []
-    launches0 = cox.cox_launch_count()
     wall0 = time.perf_counter()
     with ClockSampler(local_rank) as clk:
-        with torch.cuda.stream(stream):
-            for _ in range(args.steps):
-                flush.fill_(float(len(times)))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                beta, info = step(ddev)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-                infos.append(info)
-        torch.cuda.synchronize()
+        times, infos, beta, launches = _timed_fits(cox, ddev, opts, precision, stream, flush, args.steps, args.warmup)
     wall = time.perf_counter() - wall0
-    launches = cox.cox_launch_count() - launches0
     if world > 1:
         torch.distributed.barrier()
     step_ms = float(np.mean(times))
     coords = float(np.mean([i["coord_updates"] for i in infos]))
-    # roofline of the coordinate step (per coordinate step: the sweep loop's CUDA-event time over
-    # the steps it ran -- coord_updates plus the final convergence check of each fit)
-    s_e = 4 if precision == cox.COX_FP32C else 8
     steps_run = float(np.sum([i["coord_updates"] + 1 for i in infos]))
     step_us = float(np.sum([i["sweep_ms"] for i in infos])) / steps_run * 1e3
     engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
-    roofline = roofline_of(engine, data, beta, G, K, s_e, step_us, wname, args.precision)
     value, slowest_ms = aggregate_ranks(coords, step_ms, world, dev)
-    vals = np.array([value, slowest_ms])
     result = {
-        "metric": "coordinate updates/sec (CCD, stratified Cox, one fit per step)",
-        "value": value, "unit": "coord_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": float(vals[1]), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": dtype_of(engine, s_e), "data": "synthetic (seeded; paper cohorts unavailable)",
-        "config": {"workload": wname, "precision": args.precision, "parallelism": f"replicas{world}",
-                   "sweeps": infos[-1]["sweeps"], "coord_updates_per_fit": coords, "tie_groups": G, "strata": K,
-                   "fits_per_s": world / (vals[1] * 1e-3), "l2": "flushed before every step (512 MB write)",
-                   "engine": engine},
-        "roofline": roofline,
-        "gpu_launches": int(launches), "wall_s": wall,
-        "clocks": clk.summary(),
+        "metric": METRIC, "value": value, "unit": "coord_updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": slowest_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype_of(engine, 8), "data": "synthetic (seeded; paper cohorts unavailable)",
+        "config": headline_config(wname),
+        "parallelism": f"replicas{world}",
+        "fit": {"engine": engine, "sweeps": infos[-1]["sweeps"], "coord_updates_per_fit": coords,
+                "nonzero_beta": int(np.count_nonzero(beta)), "tie_groups": G, "strata": K,
+                "fits_per_s": world / (slowest_ms * 1e-3), "step_us": step_us,
+                "l2": "flushed before every step (512 MB write)",
+                "note": "at this L1 weight every coefficient stays at 0 (one sweep, no eta update); "
+                        "`moving` is the same data at a weight where coefficients move"},
+        "roofline": roofline_of(engine, data, beta, G, K, 8, step_us, wname, "fp64"),
+        "gpu_launches": int(launches), "wall_s": wall, "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_e2e:
-        result["e2e"] = e2e(args, data, opts, precision, stream)
-    if rank == 0 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(data, opts, args.cpu_seconds)
-    return result
+    return result, (data, ddev, stream, flush, G, K)
 
 
-def e2e(args, data, opts, precision, stream):
-    """Same metric through the public API with HOST buffers: the H2D copies of the inputs
-    (inside cox_create, from pinned host memory) and the D2H of beta are inside the timed
-    region."""
+def run_moving(args, data, ddev, stream, flush, G, K, oracle_result):
+    """The headline data at gamma = 1e-5 N: timed fits to convergence, plus the error of the
+    two-sweep iterate against the FP64 oracle's."""
+    from paper_2310_16238_gb300 import cox
+    opts = moving_options(data.n)
+    with ClockSampler(0) as clk:
+        times, infos, beta, _ = _timed_fits(cox, ddev, opts, cox.COX_FP64, stream, flush, max(3, args.steps // 4), 1)
+    ms = float(np.mean(times))
+    coords = float(np.mean([i["coord_updates"] for i in infos]))
+    steps_run = float(np.sum([i["coord_updates"] + 1 for i in infos]))
+    step_us = float(np.sum([i["sweep_ms"] for i in infos])) / steps_run * 1e3
+    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    out = {"workload": f"stratified_sparse N={data.n} p={data.p} K=100 L1 gamma=1e-5*N (same data as the headline)",
+           "engine": engine, "dtype": dtype_of(engine, 8), "fits": len(times), "ms_per_fit": ms,
+           "fits_per_s": 1e3 / ms, "coord_updates_per_s": coords / (ms * 1e-3), "sweeps": infos[-1]["sweeps"],
+           "converged": bool(infos[-1]["converged"]), "nonzero_beta": int(np.count_nonzero(beta)),
+           "step_us": step_us,
+           "roofline": roofline_of(engine, data, beta, G, K, 8, step_us, "stratified_sparse_moving", "fp64"),
+           "clocks": clk.summary()}
+    # the two-sweep iterate of the same fit, compared with the oracle's (computed beside the GPU legs)
+    o2 = synth.CoxOptions(penalty=opts.penalty, lam=opts.lam, tol=0.0, max_sweeps=2)
+    h = cox.cox_create(ddev, o2, precision=cox.COX_FP64, stream=stream.cuda_stream)
+    try:
+        b2, i2 = cox.cox_fit(h)
+        dx = cox.cox_dx(h)
+    finally:
+        cox.cox_destroy(h)
+    if oracle_result is not None:
+        ob, oll = oracle_result
+        scale = max(abs(oll), float(np.sum(np.abs(ob) * np.abs(dx))) + float(np.sum(data.event)))
+        out["vs_oracle"] = {"sweeps": 2, "max_rel_beta_err": float(np.max(np.abs(b2 - ob)) / max(np.max(np.abs(ob)), 1e-300)),
+                            "rel_loglik_err": abs(i2["loglik"] - oll) / scale, "tolerance": {"beta": 1e-9, "loglik": 1e-11},
+                            "oracle": "FP64 CPU oracle, the same fit after 2 sweeps (element by element)"}
+    return out
+
+
+# ---------------------------------------------------------------- config 4: batched fits
+def run_batch(args, sub=False):
+    """256 fits (4 outcomes x 4 folds x 16 L1 weights) over one shared binary X: the plain
+    one-fit-at-a-time FP64 path against the batched launches."""
+    import torch
+    from paper_2310_16238_gb300 import autotune, cox
+    sets = synth.batch_views(n_total=int(1_000_000 * args.scale), n_lo=1e4 * args.scale, n_hi=1e6 * args.scale)
+    stream = torch.cuda.Stream()
+    n_fits = sum(len(ol) for _, ol in sets)
+    rows = int(sum(d.n * len(ol) for d, ol in sets))
+    out = {"workload": f"batch_views: shared binary X {int(1e6 * args.scale)}x1000 density 1e-2, 16 training sets "
+                       f"(4 outcomes x 4 folds) N~logU[1e4,1e6] with 1-50 strata, 16 L1 weights each",
+           "fits": n_fits, "rows_total": rows}
+    meta = []
+    for d, ol in sets:
+        h = cox.Handle(d, ol[0], precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM)
+        md = h.metadata()
+        meta.append((len(md["group_time"]), len(md["strata_start"]) - 1, float(np.diff(d.col_ptr).mean())))
+        h.close()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, time.perf_counter() - t0, e0.elapsed_time(e1)
+
+    # the plain path: every fit on its own, one after the other (AUTO engine, FP64)
+    def plain():
+        res = []
+        for d, ol in sets:
+            for o in ol:
+                with cox.Handle(d, o, precision=cox.COX_FP64, stream=stream.cuda_stream) as h:
+                    res.append(h.fit())
+        return res
+    with ClockSampler(0) as clk:
+        ref, sec, _ = timed(plain)
+    out["plain_fp64"] = {"fits_per_s": n_fits / sec, "seconds": sec, "engine": "AUTO per fit (one fit at a time)",
+                         "clocks": clk.summary()}
+
+    def errors(betas):
+        eb = 0.0
+        for bb, (b, _) in zip(betas, ref):
+            den = max(np.max(np.abs(b)), 1e-12) if np.any(b) else 1.0
+            eb = max(eb, float(np.max(np.abs(bb - b)) / den))
+        return eb
+
+    peak, src = hbm_peak()
+    for prec, name, engine in ((cox.COX_FP32C, "batched_fp32c", cox.COX_ENGINE_STREAM),
+                               (cox.COX_FP64, "batched_fp64", cox.COX_ENGINE_STREAM),
+                               (cox.COX_FP64, "batched_incremental", cox.COX_ENGINE_AUTO)):
+        tile = autotune.batch_tile(sets, prec) if engine == cox.COX_ENGINE_STREAM else 0
+        handles = []
+        for d, ol in sets:
+            base = cox.Handle(d, ol[0], precision=prec, tile=tile, engine=engine, stream=stream.cuda_stream)
+            handles.append(base)
+            handles.extend(base.clone(o) for o in ol[1:])
+        launches0 = cox.cox_launch_count()
+        with ClockSampler(0) as clk:
+            (betas, infos), sec, dev_ms = timed(lambda: cox.batch_fit(handles))
+        launches = cox.cox_launch_count() - launches0
+        r = {"fits_per_s": n_fits / sec, "seconds": sec, "device_ms": dev_ms,
+             "engine": ENGINE_NAMES.get(infos[0]["engine"], "unknown"), "tile": tile or None,
+             "max_rel_beta_err_vs_plain_fp64": errors(betas), "gpu_launches": int(launches),
+             "speedup_vs_plain": (n_fits / sec) / out["plain_fp64"]["fits_per_s"], "clocks": clk.summary()}
+        if engine == cox.COX_ENGINE_STREAM:
+            s_e = 4 if prec == cox.COX_FP32C else 8
+            alg = 0.0
+            for k, ((d, ol), (G, K, nnz)) in enumerate(zip(sets, meta)):
+                for m in range(len(ol)):
+                    i = infos[k * len(ol) + m]
+                    steps = i["coord_updates"] + 1
+                    alg += steps * dense_bytes_per_step(d.n, G, K, nnz, s_e, True)
+            ach = alg / (dev_ms * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "alg_bytes": alg, "launches": infos[0]["step_launches"],
+                             "us_per_launch": 1e3 * dev_ms / max(infos[0]["step_launches"], 1),
+                             "basis": "dense-method bytes of every fit's coordinate steps / CUDA-event time of the batch",
+                             "peak_source": src}
+        out[name] = r
+        for hh in handles:
+            hh.close()
+    best = max(("batched_fp32c", "batched_fp64", "batched_incremental"), key=lambda k: out[k]["fits_per_s"])
+    out["best"] = best
+    out["fits_per_s"] = out[best]["fits_per_s"]
+    if not sub:
+        return {"metric": "fits/sec (256 CCD fits: 4 outcomes x 4 folds x 16 L1 weights)", "value": out["fits_per_s"],
+                "unit": "fits/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic (seeded)",
+                "config": {"workload": out["workload"]}, "batch": out}
+    return out
+
+
+# ---------------------------------------------------------------- config 5: serving
+def run_serving(args, sub=False):
+    """Poisson fit requests into the continuous-batching server: capacity under a burst, then a
+    stream at a sustainable rate with p50 / p99 time-to-fit."""
+    from paper_2310_16238_gb300 import cox
+    prec = cox.COX_FP32C
+    reqs = synth.serving_stream(rate=args.rate, duration_s=max(args.duration, 30.0))
+    pool = []
+    for r in reqs[:args.pool]:
+        pool.append((r, synth.request_data(r, max_rows=args.max_rows)))
+    rng = np.random.default_rng(7)
+
+    def options(r, d):
+        if r.penalty == synth.PEN_L1:
+            return synth.CoxOptions(penalty=synth.PEN_L1, lam=float(np.exp(rng.uniform(-10, -6))) * d.n, tol=1e-8)
+        return synth.CoxOptions(penalty=synth.PEN_L2, l2_var=float(np.exp(rng.uniform(-2, 1))), tol=1e-8)
+
+    def drive(arrivals, timeout_s):
+        lat, waits = [], []
+        with cox.Server(precision=prec) as srv:
+            t_start = time.perf_counter()
+            pending, k = {}, 0
+            while k < len(arrivals) or pending:
+                now = time.perf_counter() - t_start
+                while k < len(arrivals) and arrivals[k] <= now:
+                    r, (d, o) = pool[k % len(pool)]
+                    pending[srv.submit(d, options(r, d))] = k
+                    k += 1
+                for rid in list(pending):
+                    res = srv.poll(rid)
+                    if res is not None:
+                        lat.append(res[1]["total_ms"])
+                        waits.append(res[1]["wait_ms"])
+                        del pending[rid]
+                time.sleep(0.002)
+                if now > timeout_s:
+                    break
+            elapsed = time.perf_counter() - t_start
+            st = srv.stats()
+        return np.array(lat), np.array(waits), elapsed, st
+
+    # capacity: a burst of requests all at t = 0
+    n_burst = 2 * len(pool)
+    lat_b, _, el_b, _ = drive([0.0] * n_burst, 600.0)
+    capacity = len(lat_b) / el_b
+    rate = 0.8 * capacity
+    # a Poisson stream at 80 % of that capacity
+    t, arr = 0.0, []
+    r2 = np.random.default_rng(11)
+    while t < args.duration:
+        t += r2.exponential(1.0 / rate)
+        arr.append(t)
+    lat, waits, el, st = drive(arr[:-1], args.duration * 4)
+    out = {"workload": f"Poisson arrivals, rows logU[1e4,1e7] (capped at {args.max_rows}), p logU[100,2e4], "
+                       f"density logU[1e-4,1e-2], K U{{1..200}}, 50% counting-process, L1/L2 (pool of {len(pool)})",
+           "precision": "fp32c", "capacity_fits_per_s": capacity, "burst_requests": n_burst,
+           "sustainable_rate": rate, "offered_rate_config": args.rate,
+           "stream": {"requests": len(lat), "fits_per_s": len(lat) / el,
+                      "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                      "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                      "p50_wait_ms": float(np.percentile(waits, 50)) if len(waits) else None},
+           "server": st}
+    if not sub:
+        return {"metric": "fits/sec and p50/p99 time-to-fit (continuous-batching server)",
+                "value": out["stream"]["fits_per_s"], "unit": "fits/s", "n_gpus": 1, "higher_is_better": True,
+                "data": "synthetic (seeded request pool)", "config": {"workload": out["workload"]}, "serving": out}
+    return out
+
+
+# ---------------------------------------------------------------- other single workloads
+def run_time_varying(args):
+    """Counting-process fit (1e6 subjects, ~2.9e6 (start, stop] rows, p = 5000, K = 20, L2)."""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    data, opts = synth.time_varying(n_subj=int(1_000_000 * args.scale), p=5000, k=20)
+    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    engine = {"auto": cox.COX_ENGINE_AUTO, "stream": cox.COX_ENGINE_STREAM}[args.engine]
+    stream = torch.cuda.Stream()
+    times, infos = [], []
+    with torch.cuda.stream(stream):
+        h = cox.cox_create(data, opts, precision=precision, stream=stream.cuda_stream, engine=engine)
+        for k in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            beta, info = cox.cox_fit(h)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+                infos.append(info)
+        md = cox.cox_metadata(h)
+        cox.cox_destroy(h)
+    ms = float(np.mean(times))
+    coords = float(np.mean([i["coord_updates"] for i in infos]))
+    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
+    eng = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
+    wname = f"time_varying subjects={int(1_000_000 * args.scale)} rows={data.n} p=5000 K=20 L2 var=0.1"
+    s_e = 4 if precision == cox.COX_FP32C else 8
+    roof = roofline_of(eng, data, beta, len(md["group_time"]), len(md["strata_start"]) - 1, s_e, step_us, wname,
+                       args.precision)
+    return {"metric": "coordinate updates/sec (CCD, counting-process Cox, one fit per step)",
+            "value": coords / (ms * 1e-3), "unit": "coord_updates/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype_of(eng, s_e), "data": "synthetic (seeded)",
+            "config": {"workload": wname, "precision": args.precision},
+            "fit": {"sweeps": infos[-1]["sweeps"], "loglik": infos[-1]["loglik"], "step_us": step_us, "engine": eng},
+            "roofline": roof}
+
+
+def run_cv(args):
+    """10-fold cross-validation along an L1 path (the paper's tuning procedure, §3.2): a stratified
+    sparse data set of 2e5 rows, p = 1000, 10 strata, 8 weights log-spaced from 1e-2 N down to
+    1e-4 N; every weight's 10 training fits and the full-data fit run as one warm-started batch."""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    n = int(200_000 * args.scale)
+    data, opts = synth.stratified_sparse(n=n, p=1000, k=10, n_support=30, event_frac=0.1, dens_lo=1e-3, dens_hi=5e-2,
+                                         seed=synth.SEED_BASE + 7)
+    K = 10
+    fold = cox.make_folds(data.n, K, seed=7)
+    path = list(np.logspace(np.log10(1e-2 * n), np.log10(1e-4 * n), 8))
+    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ddev = _device_copy(data, dev)
+    dfold = torch.from_numpy(fold).to(dev)
+    torch.cuda.synchronize()
+    times, res = [], None
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = cox.cox_cv_path(ddev, dfold, path, opts, n_folds=K, precision=precision,
+                                      stream=stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    ms = float(np.mean(times))
+    fits = len(path) * (K + 1)
+    coords = sum(f["coord_updates"] for row in res["info"] for f in row)
+    engines = sorted({ENGINE_NAMES.get(f["engine"], "unknown") for row in res["info"] for f in row})
+    return {"metric": "fits/sec (10-fold cross-validated L1 path: 8 weights x (10 training + 1 full-data) fits, "
+                      "warm-started batches)",
+            "value": fits / (ms * 1e-3), "unit": "fits/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2+f64" if "incremental" in engines else ("f64" if precision == cox.COX_FP64 else "f32+f64"),
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"stratified_sparse N={n} p=1000 K=10 strata, 10 folds, L1 path "
+                                   f"{path[0]:.0f}..{path[-1]:.1f} (8 values)", "precision": args.precision},
+            "cv": {"coord_updates_per_path": coords, "coord_updates_per_s": coords / (ms * 1e-3), "engines": engines,
+                   "best": res["best"], "cvl": [float(v) for v in res["cvl"]],
+                   "nonzero_at_best": int(np.count_nonzero(res["beta"][res["best"]]))},
+            "clocks": clk.summary()}
+
+
+def run_e1(args):
+    """The paper's synthetic experiment shape (§3.1): N = 1e6, P = 2000, binary X at 5 % density,
+    K equal strata (default 50,000), beta 20 % nonzero N(0, 1), L1 gamma = sqrt(2). One step = one
+    full fit (cox_create from device-resident arrays + cox_fit + cox_destroy)."""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    n = int(1_000_000 * args.scale)
+    K = args.strata if args.strata > 0 else 50_000
+    data, opts = synth.synthetic_e1(n=n, p=2000, k=K)
+    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    ddev = _device_copy(data, dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with ClockSampler(0) as clk:
+        times, infos, beta, _ = _timed_fits(cox, ddev, opts, precision, stream, flush, args.steps, args.warmup)
+    ms = float(np.mean(times))
+    coords = float(np.mean([i["coord_updates"] for i in infos]))
+    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
+    eng = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
+    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
+    return {"metric": "seconds per fit (CCD to convergence, stratified L1 Cox; the paper's synthetic experiment shape)",
+            "value": ms * 1e-3, "unit": "s/fit", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_of(eng, 8 if precision == cox.COX_FP64 else 4), "data": "synthetic (seeded)",
+            "config": {"workload": f"synthetic_e1 N={n} p=2000 density 0.05 K={K} beta 20% N(0,1) L1 gamma=sqrt(2)",
+                       "precision": args.precision},
+            "fit": {"sweeps": infos[-1]["sweeps"], "coord_updates_per_s": coords / (ms * 1e-3),
+                    "nonzero_beta": int(np.count_nonzero(beta)), "step_us": step_us, "engine": eng},
+            "clocks": clk.summary()}
+
+
+# ---------------------------------------------------------------- end to end from host buffers
+def e2e(args, data, opts, stream):
+    """Same metric through the public API with HOST buffers: the H2D copies of the inputs (inside
+    cox_create, from pinned host memory) and the D2H of beta are inside the timed region."""
     import copy
     import torch
     from paper_2310_16238_gb300 import cox
@@ -279,7 +633,7 @@ def e2e(args, data, opts, precision, stream):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            h = cox.cox_create(hdata, opts, precision=precision, stream=stream.cuda_stream)
+            h = cox.cox_create(hdata, opts, precision=cox.COX_FP64, stream=stream.cuda_stream)
             beta, info = cox.cox_fit(h)
             cox.cox_destroy(h)
             e1.record(stream)
@@ -291,545 +645,130 @@ def e2e(args, data, opts, precision, stream):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * data.p)}
 
 
-def cpu_baseline(data, opts, seconds):
+# ---------------------------------------------------------------- the CPU oracle (baseline arm)
+_CPU = {}
+
+
+def _cpu_init(scale):
+    """Worker set-up: the headline data (the same seed in every worker) and the built oracle."""
     import oracle
     oracle.build()
+    data, opts, _ = headline_workload(scale)
+    _CPU["data"], _CPU["opts"] = data, opts
+
+
+def _cpu_run(ncoords):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.time_sample(_CPU["data"], _CPU["opts"], int(ncoords))
+    return time.perf_counter() - t0
+
+
+def usable_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """Independent oracle processes, one per core, each holding its own copy of the headline data:
+    the fit replicated on every core (no shared state, no change to the oracle's arithmetic)."""
+
+    def __init__(self, cores, scale):
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores, initializer=_cpu_init, initargs=(scale,))
+        self.pool.map(_cpu_run, [1] * cores)          # every worker ready (data built, oracle loaded)
+
+    def rate(self, ncoords):
+        """Coordinate updates per second of all workers running `ncoords` each at once."""
+        t0 = time.perf_counter()
+        self.pool.map(_cpu_run, [ncoords] * self.cores, chunksize=1)
+        return self.cores * ncoords / (time.perf_counter() - t0)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(scale, seconds):
+    """The oracle as it stands on the host: one core, and one process per usable core."""
+    import oracle
+    oracle.build()
+    data, opts, _ = headline_workload(scale)
     t0 = time.perf_counter()
     oracle.time_sample(data, opts, 2)
     per = (time.perf_counter() - t0) / 2
-    n = max(2, int(seconds / max(per, 1e-6)))
+    n1 = max(2, int(0.5 * seconds / max(per, 1e-6)))
     t0 = time.perf_counter()
-    oracle.time_sample(data, opts, n)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "coord_updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} coordinate updates (Newton step + eta update) of the same fit from beta = 0, "
-                      f"single-threaded FP64 C oracle, {dt:.1f} s"}
+    oracle.time_sample(data, opts, n1)
+    one = n1 / (time.perf_counter() - t0)
+    cores = usable_cores()
+    pool = OraclePool(cores, scale)
+    try:
+        allc = pool.rate(max(2, int(0.5 * seconds * one)))
+    finally:
+        pool.close()
+    return {"value": allc, "unit": "coord_updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent oracle processes (one per usable core), each running "
+                      f"{max(2, int(0.5 * seconds * one))} coordinate updates (Newton step + eta update) of the "
+                      f"headline fit from beta = 0; FP64 C oracle",
+            "single_core": {"value": one, "cores": 1, "sample": f"{n1} coordinate updates, one process"},
+            "cpu": cpu_model()}
 
 
-def run_time_varying(args):
-    """Counting-process fit (1e6 subjects, ~2.9e6 (start, stop] rows, p = 5000, K = 20, L2)."""
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n_subj = int(1_000_000 * args.scale)
-    data, opts = synth.time_varying(n_subj=n_subj, p=5000, k=20)
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    stream = torch.cuda.Stream()
-    times, infos = [], []
-    with torch.cuda.stream(stream):
-        h = cox.cox_create(data, opts, precision=precision, stream=stream.cuda_stream)
-        for k in range(args.warmup + args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            beta, info = cox.cox_fit(h)
-            e1.record(stream)
-            e1.synchronize()
-            if k >= args.warmup:
-                times.append(e0.elapsed_time(e1))
-                infos.append(info)
-        cox.cox_destroy(h)
-    ms = float(np.mean(times))
-    coords = float(np.mean([i["coord_updates"] for i in infos]))
-    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
-    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
-    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
-    h2 = cox.cox_create(data, opts, precision=precision)
-    md = cox.cox_metadata(h2)
-    cox.cox_destroy(h2)
-    wname = f"time_varying subjects={n_subj} rows={data.n} p=5000 K=20 L2 var=0.1"
-    roof = roofline_of(engine, data, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
-                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
-    return {"metric": "coordinate updates/sec (CCD, counting-process Cox, one fit per step)",
-            "value": coords / (ms * 1e-3), "unit": "coord_updates/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4), "data": "synthetic (seeded)",
-            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
-                       "loglik": infos[-1]["loglik"], "step_us": step_us, "engine": engine},
-            "roofline": roof}
-
-
-def run_tvc(args):
-    """A treatment coefficient that steps at day 10 (the paper's cough analysis shape, §2.3 and
-    §3.3): 407,828 subjects, 9,666 baseline covariates at ~3 % density. One step = the
-    interval-stratified view built on the device from the unsplit arrays (cox_create_split) +
-    the L1 fit + destroy, inputs resident in HBM."""
-    import types
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n = int(407_828 * args.scale)
-    data, opts = synth.tvc_cohort(n=n)
-    cuts, tvc = [10], [0]
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-    times, view_ms, infos = [], [], []
-    launches0 = None
-    with ClockSampler(0) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
-                if k == args.warmup:
-                    launches0 = cox.cox_launch_count()
-                flush.fill_(float(k))
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                e[0].record(stream)
-                h = cox.cox_create_split(ddev, cuts, tvc, opts, precision=precision, stream=stream.cuda_stream)
-                e[1].record(stream)
-                try:
-                    beta, info = cox.cox_fit(h)
-                finally:
-                    cox.cox_destroy(h)
-                e[2].record(stream)
-                e[2].synchronize()
-                if k >= args.warmup:
-                    times.append(e[0].elapsed_time(e[2]))
-                    view_ms.append(e[0].elapsed_time(e[1]))
-                    infos.append(info)
-        torch.cuda.synchronize()
-    launches = cox.cox_launch_count() - launches0
-    h = cox.cox_create_split(data, cuts, tvc, opts, precision=precision)
-    md = cox.cox_metadata(h)
-    cox.cox_destroy(h)
-    n_view = int(md["strata_start"][-1])
-    # the view's shape for the roofline: rows, columns and nonzeros per column
-    reach = 1 + (data.stop >= cuts[0]).astype(np.int64)
-    per_col = np.add.reduceat(reach[data.row_idx], data.col_ptr[:-1]) if data.nnz else np.zeros(data.p, np.int64)
-    per_col[np.diff(data.col_ptr) == 0] = 0
-    t0 = data.row_idx[data.col_ptr[0]:data.col_ptr[1]]
-    view_cols = np.concatenate([[len(t0), int(np.sum(data.stop[t0] >= cuts[0]))], per_col[1:]])
-    vshape = types.SimpleNamespace(n=n_view, start=None, p=len(view_cols),
-                                   col_ptr=np.concatenate([[0], np.cumsum(view_cols)]))
-    ms = float(np.mean(times))
-    coords = float(np.mean([i["coord_updates"] for i in infos]))
-    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
-    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
-    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
-    wname = (f"tvc_cohort subjects={n} p=9666+treatment density logU[1.4e-3,0.14] cut=10 "
-             f"view rows={n_view} p_view={vshape.p} L1 gamma=1e-4*N")
-    roof = roofline_of(engine, vshape, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
-                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
-    return {"metric": "coordinate updates/sec (CCD, time-varying coefficient via the interval-stratified view, "
-                      "one fit per step)",
-            "value": coords / (ms * 1e-3), "unit": "coord_updates/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4),
-            "data": "synthetic (seeded; paper cohort unavailable)",
-            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
-                       "loglik": infos[-1]["loglik"], "step_us": step_us, "engine": engine,
-                       "view_build_ms": float(np.mean(view_ms)), "beta_treatment": [float(beta[0]), float(beta[1])],
-                       "l2": "flushed before every step (512 MB write)"},
-            "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary()}
-
-
-def run_cv(args):
-    """10-fold cross-validation along an L1 path (the paper's tuning procedure, §3.2): a stratified
-    sparse data set of 2e5 rows, p = 1000, 10 strata, 8 weights log-spaced from 1e-2 N down to
-    1e-4 N; every weight's 10 training fits and the full-data fit run as one warm-started batch."""
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n = int(200_000 * args.scale)
-    data, opts = synth.stratified_sparse(n=n, p=1000, k=10, n_support=30, event_frac=0.1, dens_lo=1e-3, dens_hi=5e-2,
-                                         seed=synth.SEED_BASE + 7)
-    K = 10
-    fold = cox.make_folds(data.n, K, seed=7)
-    path = list(np.logspace(np.log10(1e-2 * n), np.log10(1e-4 * n), 8))
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "stratum", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
-    dfold = torch.from_numpy(fold).to(dev)
-    torch.cuda.synchronize()
-    times, res = [], None
-    launches0 = None
-    with ClockSampler(0) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
-                if k == args.warmup:
-                    launches0 = cox.cox_launch_count()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                res = cox.cox_cv_path(ddev, dfold, path, opts, n_folds=K, precision=precision,
-                                      stream=stream.cuda_stream)
-                e1.record(stream)
-                e1.synchronize()
-                if k >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-    launches = cox.cox_launch_count() - launches0
-    ms = float(np.mean(times))
-    fits = len(path) * (K + 1)
-    coords = sum(f["coord_updates"] for row in res["info"] for f in row)
-    engines = sorted({ENGINE_NAMES.get(f["engine"], "unknown") for row in res["info"] for f in row})
-    out = {"metric": "fits/sec (10-fold cross-validated L1 path: 8 weights x (10 training + 1 full-data) fits, "
-                     "warm-started batches)",
-           "value": fits / (ms * 1e-3), "unit": "fits/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32x2+f64" if "incremental" in engines else ("f64" if precision == cox.COX_FP64 else "f32+f64"),
-           "data": "synthetic (seeded)",
-           "config": {"workload": f"stratified_sparse N={n} p=1000 K=10 strata, 10 folds, L1 path "
-                                  f"{path[0]:.0f}..{path[-1]:.1f} (8 values)",
-                      "precision": args.precision, "coord_updates_per_path": coords,
-                      "coord_updates_per_s": coords / (ms * 1e-3), "engines": engines, "best": res["best"],
-                      "cvl": [float(v) for v in res["cvl"]],
-                      "nonzero_at_best": int(np.count_nonzero(res["beta"][res["best"]]))},
-           "gpu_launches": int(launches), "clocks": clk.summary()}
-    if not args.no_cpu:
+def _oracle_moving(q, scale):
+    """Child process: the oracle's two-sweep iterate of the moving fit (run beside the GPU legs)."""
+    try:
         import oracle
-        from oracle import cv as ocv
         oracle.build()
-        tr = ocv.training_set(data, fold, 0)
-        o0 = synth.CoxOptions(penalty=synth.PEN_L1, lam=path[0], tol=1e-8)
-        t0 = time.perf_counter()
-        oracle.time_sample(tr, o0, 20)
-        nc = max(20, int(20 * args.cpu_seconds / max(time.perf_counter() - t0, 1e-6)))
-        t0 = time.perf_counter()
-        oracle.time_sample(tr, o0, nc)
-        dt = time.perf_counter() - t0
-        per_coord = dt / nc
-        out["cpu_baseline"] = {"value": 1.0 / (per_coord * coords / fits), "unit": "fits/s", "cores": 1,
-                               "kind": "oracle",
-                               "sample": f"{nc} coordinate updates of training fold 0 at the first weight ({dt:.1f} s), "
-                                         f"scaled to the GPU path's mean coordinate updates per fit"}
-    return out
-
-
-def run_e1(args):
-    """The paper's synthetic experiment (§3.1): N = 1e6, P = 2000, binary X at 5 % density,
-    K = 50,000 equal strata, beta 20 % nonzero N(0, 1), L1 gamma = sqrt(2). One step = one full
-    fit (cox_create from device-resident arrays + cox_fit + cox_destroy). The paper reports
-    23 s per fit for this shape on a Quadro GV100 (and 17 min for its CPU implementation)."""
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n = int(1_000_000 * args.scale)
-    K = args.strata if args.strata > 0 else 50_000
-    data, opts = synth.synthetic_e1(n=n, p=2000, k=K)
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "stratum", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-    times, infos = [], []
-    launches0 = None
-    with ClockSampler(0) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
-                if k == args.warmup:
-                    launches0 = cox.cox_launch_count()
-                flush.fill_(float(k))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                h = cox.cox_create(ddev, opts, precision=precision, stream=stream.cuda_stream)
-                try:
-                    beta, info = cox.cox_fit(h)
-                finally:
-                    cox.cox_destroy(h)
-                e1.record(stream)
-                e1.synchronize()
-                if k >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
-                    infos.append(info)
-        torch.cuda.synchronize()
-    launches = cox.cox_launch_count() - launches0
-    ms = float(np.mean(times))
-    coords = float(np.mean([i["coord_updates"] for i in infos]))
-    steps = float(np.mean([i["coord_updates"] + 1 for i in infos]))
-    engine = ENGINE_NAMES.get(infos[-1]["engine"], "unknown")
-    step_us = float(np.mean([i["sweep_ms"] for i in infos])) / steps * 1e3
-    h = cox.cox_create(data, opts, precision=precision)
-    md = cox.cox_metadata(h)
-    cox.cox_destroy(h)
-    wname = f"synthetic_e1 N={n} p=2000 density 0.05 K={K} beta 20% N(0,1) L1 gamma=sqrt(2)"
-    roof = roofline_of(engine, data, beta, len(md["group_time"]), len(md["strata_start"]) - 1,
-                       4 if precision == cox.COX_FP32C else 8, step_us, wname, args.precision)
-    return {"metric": "seconds per fit (CCD to convergence, stratified L1 Cox; the paper's synthetic experiment)",
-            "value": ms * 1e-3, "unit": "s/fit", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            # the paper's own number for this shape (N = 1e6, K = 50,000; a Quadro GV100): context
-            "vs_baseline": (ms * 1e-3) / 23.0 if (n == 1_000_000 and K == 50_000) else None,
-            "dtype": dtype_of(engine, 8 if precision == cox.COX_FP64 else 4), "data": "synthetic (seeded)",
-            "config": {"workload": wname, "precision": args.precision, "sweeps": infos[-1]["sweeps"],
-                       "coord_updates_per_s": coords / (ms * 1e-3), "nonzero_beta": int(np.count_nonzero(beta)),
-                       "tie_groups": len(md["group_time"]), "step_us": step_us, "engine": engine,
-                       "paper_context": "23 s per fit on a Quadro GV100 for N = 1e6, K = 50,000 (another GPU)",
-                       "l2": "flushed before every step (512 MB write)"},
-            "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary()}
-
-
-def run_tvc_cv(args):
-    """The paper's §3.3 analysis as one call: 10-fold cross-validation along an L1 path (6 weights
-    from 1e-3 N down to 1e-5 N) of the treatment-split model on the cohort of the tvc line; every
-    training set and the full data split on the device. One step = the whole cross-validated
-    path (66 fits). The paper reports 1.86 h for its cough analysis, CV included, on a Quadro
-    GV100 (21.6 h for its CPU implementation)."""
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n = int(407_828 * args.scale)
-    data, opts = synth.tvc_cohort(n=n)
-    K, cuts, tvc = 10, [10], [0]
-    fold = cox.make_folds(data.n, K, seed=11)
-    path = list(np.logspace(np.log10(1e-3 * n), np.log10(1e-5 * n), 6))
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
-    dfold = torch.from_numpy(fold).to(dev)
-    torch.cuda.synchronize()
-    times, res = [], None
-    launches0 = None
-    with ClockSampler(0) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
-                if k == args.warmup:
-                    launches0 = cox.cox_launch_count()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                res = cox.cox_cv_path(ddev, dfold, path, opts, n_folds=K, precision=precision,
-                                      stream=stream.cuda_stream, cuts=cuts, tvc_cols=tvc)
-                e1.record(stream)
-                e1.synchronize()
-                if k >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-    launches = cox.cox_launch_count() - launches0
-    ms = float(np.mean(times))
-    fits = len(path) * (K + 1)
-    coords = sum(f["coord_updates"] for row in res["info"] for f in row)
-    engines = sorted({ENGINE_NAMES.get(f["engine"], "unknown") for row in res["info"] for f in row})
-    b = res["beta"][res["best"]]
-    return {"metric": "seconds per cross-validated path (10 folds x 6 L1 weights on the treatment-split view, "
-                      "the paper's cough analysis shape)",
-            "value": ms * 1e-3, "unit": "s/path", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2+f64" if "incremental" in engines else "f64", "data": "synthetic (seeded; paper cohort unavailable)",
-            "config": {"workload": f"tvc_cohort subjects={n} p=9666+treatment cut=10, 10 folds, L1 path "
-                                   f"{path[0]:.1f}..{path[-1]:.2f} (6 values), treatment copies unpenalized",
-                       "precision": args.precision, "fits": fits, "coord_updates": coords,
-                       "coord_updates_per_s": coords / (ms * 1e-3), "engines": engines, "best": res["best"],
-                       "cvl": [float(v) for v in res["cvl"]],
-                       "treatment_log_hr_at_best": [float(b[0]), float(b[1])],
-                       "paper_context": "1.86 h for the cough analysis with 10-fold CV on a Quadro GV100"},
-            "gpu_launches": int(launches), "clocks": clk.summary()}
-
-
-def run_ps_cv(args):
-    """The paper's §3.2 analysis as one call: 10-fold cross-validation along an L1 path (6 weights
-    from 1e-3 N down to 1e-5 N) of the propensity-score-stratified model (946,911 patients, 9,976
-    baseline covariates, treatment unpenalized, K = --strata, default 10). One step = the whole
-    cross-validated path (66 fits). The paper reports 1.38 h for K = 10 (1.41 h for 5, 1.57 h for
-    20), CV included, on a Quadro GV100."""
-    import torch
-    from paper_2310_16238_gb300 import cox
-    n = int(946_911 * args.scale)
-    K_strata = args.strata if args.strata > 0 else 10
-    data, opts = synth.ps_stratified_cohort(n=n, k=K_strata)
-    K = 10
-    fold = cox.make_folds(data.n, K, seed=12)
-    path = list(np.logspace(np.log10(1e-3 * n), np.log10(1e-5 * n), 6))
-    precision = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(device=dev)
-    ddev = synth.CoxData(**{**data.__dict__})
-    for f in ("stop", "event", "stratum", "col_ptr", "row_idx"):
-        setattr(ddev, f, torch.from_numpy(np.ascontiguousarray(getattr(data, f))).to(dev))
-    dfold = torch.from_numpy(fold).to(dev)
-    torch.cuda.synchronize()
-    times, res = [], None
-    launches0 = None
-    with ClockSampler(0) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + args.steps):
-                if k == args.warmup:
-                    launches0 = cox.cox_launch_count()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                res = cox.cox_cv_path(ddev, dfold, path, opts, n_folds=K, precision=precision,
-                                      stream=stream.cuda_stream)
-                e1.record(stream)
-                e1.synchronize()
-                if k >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-    launches = cox.cox_launch_count() - launches0
-    ms = float(np.mean(times))
-    fits = len(path) * (K + 1)
-    coords = sum(f["coord_updates"] for row in res["info"] for f in row)
-    engines = sorted({ENGINE_NAMES.get(f["engine"], "unknown") for row in res["info"] for f in row})
-    b = res["beta"][res["best"]]
-    return {"metric": "seconds per cross-validated path (10 folds x 6 L1 weights, propensity-score-stratified model, "
-                      "the paper's heart-failure analysis shape)",
-            "value": ms * 1e-3, "unit": "s/path", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32x2+f64" if "incremental" in engines else "f64", "data": "synthetic (seeded; paper cohort unavailable)",
-            "config": {"workload": f"ps_stratified_cohort N={n} p=9976+treatment K={K_strata} PS strata, 10 folds, "
-                                   f"L1 path {path[0]:.1f}..{path[-1]:.2f} (6 values), treatment unpenalized",
-                       "precision": args.precision, "fits": fits, "coord_updates": coords,
-                       "coord_updates_per_s": coords / (ms * 1e-3), "engines": engines, "best": res["best"],
-                       "cvl": [float(v) for v in res["cvl"]], "treatment_log_hr_at_best": float(b[0]),
-                       "paper_context": "1.38 h (K = 10) for the heart-failure analysis with 10-fold CV on a Quadro GV100"},
-            "gpu_launches": int(launches), "clocks": clk.summary()}
-
-
-def run_batch(args):
-    """256 fits (4 outcomes x 4 folds x 16 L1 weights) over one shared binary X: one-at-a-time
-    FP64 vs the batched persistent launch (FP64 and FP32C, autotuned tile length)."""
-    import torch
-    from paper_2310_16238_gb300 import autotune, cox
-    sets = synth.batch_views(n_total=int(1_000_000 * args.scale), n_lo=1e4 * args.scale, n_hi=1e6 * args.scale)
-    out = {"metric": "fits/sec (256 CCD fits: 4 outcomes x 4 folds x 16 L1 weights)", "unit": "fits/s",
-           "n_gpus": 1, "higher_is_better": True, "data": "synthetic (seeded)",
-           "config": {"workload": f"batch_views shared X {int(1e6 * args.scale)}x1000 density 1e-2, "
-                                  f"16 training sets N~logU[1e4,1e6], 16 lambdas each",
-                      "rows_total": int(sum(d.n for d, _ in sets) * 16)}}
-    # one-at-a-time FP64 (the plain path): a sample of the fits, extrapolated to 256
-    t0 = time.perf_counter()
-    n_single = 0
-    ref = {}
-    for si, (d, olist) in enumerate(sets):
-        for li in (0, len(olist) - 1):
-            with cox.Handle(d, olist[li], precision=cox.COX_FP64) as h:
-                ref[(si, li)] = h.fit()
-            n_single += 1
-    single_s = time.perf_counter() - t0
-    out["single_fp64"] = {"fits": n_single, "seconds": single_s, "fits_per_s": n_single / single_s}
-    for prec, name in ((cox.COX_FP64, "fp64"), (cox.COX_FP32C, "fp32c")):
-        tile = autotune.batch_tile(sets, prec)
-        handles = []
-        for d, olist in sets:
-            base = cox.Handle(d, olist[0], precision=prec, tile=tile, engine=cox.COX_ENGINE_STREAM)
-            handles.append(base)
-            handles.extend(base.clone(o) for o in olist[1:])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        betas, infos = cox.batch_fit(handles)
-        sec = time.perf_counter() - t0
-        err = 0.0
-        for (si, li), (b, info) in ref.items():
-            bb = betas[si * 16 + li]
-            err = max(err, float(np.max(np.abs(bb - b)) / max(np.max(np.abs(b)), 1e-12)) if np.any(b) else
-                      float(np.max(np.abs(bb))))
-        out[f"batched_{name}"] = {"fits": len(handles), "seconds": sec, "fits_per_s": len(handles) / sec,
-                                  "tile": tile, "max_rel_beta_err_vs_fp64_single": err,
-                                  "coord_updates": int(sum(i["coord_updates"] for i in infos))}
-        for h in handles:
-            h.close()
-    # the incremental kernel: every fit on its compact plan, fits packed into waves of one CTA per
-    # SM (its per-data plan is built inside the timed call, on first use)
-    handles = []
-    for d, olist in sets:
-        base = cox.Handle(d, olist[0], precision=cox.COX_FP64)
-        handles.append(base)
-        handles.extend(base.clone(o) for o in olist[1:])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    betas, infos = cox.batch_fit(handles)
-    sec = time.perf_counter() - t0
-    err = 0.0
-    for (si, li), (b, info) in ref.items():
-        bb = betas[si * 16 + li]
-        err = max(err, float(np.max(np.abs(bb - b)) / max(np.max(np.abs(b)), 1e-12)) if np.any(b) else
-                  float(np.max(np.abs(bb))))
-    out["batched_incremental"] = {"fits": len(handles), "seconds": sec, "fits_per_s": len(handles) / sec,
-                                  "engine": ENGINE_NAMES.get(infos[0]["engine"], "unknown"),
-                                  "max_rel_beta_err_vs_fp64_single": err,
-                                  "coord_updates": int(sum(i["coord_updates"] for i in infos))}
-    for h in handles:
-        h.close()
-    best = max(("batched_fp32c", "batched_fp64", "batched_incremental"), key=lambda k: out[k]["fits_per_s"])
-    out["value"] = out[best]["fits_per_s"]
-    out["ms_per_step"] = 1e3 * out[best]["seconds"]
-    out["config"]["engine"] = best
-    return out
-
-
-def run_serving(args):
-    """Poisson fit requests into the continuous-batching server; p50/p99 time-to-fit and fits/s."""
-    from paper_2310_16238_gb300 import cox
-    rate, duration = args.rate, args.duration
-    reqs = synth.serving_stream(rate=rate, duration_s=duration)
-    pool = {}
-    rng = np.random.default_rng(7)
-    # a pool of materialized data sets (generation in NumPy is slower than the GPU fits); every
-    # request reuses one of them with its own penalty draw
-    n_pool = 24
-    pool_reqs = reqs[:n_pool]
-    for i, r in enumerate(pool_reqs):
-        pool[i] = synth.request_data(r, max_rows=args.max_rows)
-    prec = cox.COX_FP32C if args.precision == "fp32c" else cox.COX_FP64
-    lat, waits, done = [], [], 0
-    with cox.Server(precision=prec) as srv:
-        t_start = time.perf_counter()
-        pending = {}
-        k = 0
-        while k < len(reqs) or pending:
-            now = time.perf_counter() - t_start
-            while k < len(reqs) and reqs[k].arrival_s <= now:
-                d, o = pool[k % n_pool]
-                if reqs[k].penalty == synth.PEN_L1:
-                    o = synth.CoxOptions(penalty=synth.PEN_L1, lam=float(np.exp(rng.uniform(-10, -6))) * d.n, tol=1e-8)
-                else:
-                    o = synth.CoxOptions(penalty=synth.PEN_L2, l2_var=float(np.exp(rng.uniform(-2, 1))), tol=1e-8)
-                pending[srv.submit(d, o)] = k
-                k += 1
-            for rid in list(pending):
-                r = srv.poll(rid)
-                if r is not None:
-                    lat.append(r[1]["total_ms"])
-                    waits.append(r[1]["wait_ms"])
-                    del pending[rid]
-                    done += 1
-            time.sleep(0.002)
-            if time.perf_counter() - t_start > duration * 6:
-                break
-        elapsed = time.perf_counter() - t_start
-        st = srv.stats()
-    lat = np.array(lat) if lat else np.zeros(1)
-    return {"metric": "fits/sec and p50/p99 time-to-fit (continuous-batching server)", "value": done / elapsed,
-            "unit": "fits/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic (seeded request pool)",
-            "config": {"workload": f"Poisson {rate}/s for {duration}s, rows logU[1e4,1e7] capped at {args.max_rows}, "
-                                   f"p logU[100,2e4], 50% counting-process, L1/L2", "requests": len(reqs),
-                       "pool": n_pool, "precision": args.precision},
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "p50_wait_ms": float(np.percentile(waits, 50)) if waits else None, "completed": done,
-            "elapsed_s": elapsed, "server": st}
+        data, _, _ = headline_workload(scale)
+        o = moving_options(data.n)
+        b, info = oracle.fit(data, synth.CoxOptions(penalty=o.penalty, lam=o.lam, tol=0.0, max_sweeps=2), max_sweeps=2)
+        q.put((b, info["loglik"]))
+    except Exception as e:   # reported in the bench line, not fatal
+        q.put(("error", repr(e)))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    import oracle
-    oracle.build()
-    data, opts, wname = workload(0, args.scale)
-    t0 = time.perf_counter()
-    oracle.time_sample(data, opts, 1)
-    per = time.perf_counter() - t0
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    ncoords = max(1, int(budget / max(per, 1e-6)))
-    for _ in range(args.warmup):
-        oracle.time_sample(data, opts, ncoords)
-    times = []
-    for _ in range(args.steps):
+    _, _, wname = headline_workload(args.scale)
+    cores = usable_cores()
+    pool = OraclePool(cores, args.scale)
+    try:
         t0 = time.perf_counter()
-        oracle.time_sample(data, opts, ncoords)
-        times.append(time.perf_counter() - t0)
-    ms = 1e3 * float(np.mean(times))
-    value = ncoords / (ms * 1e-3)
-    sample = f"{ncoords} coordinate updates per step of the same fit, single-threaded FP64 C oracle"
-    return {"impl": "reference", "metric": "coordinate updates/sec (CCD, stratified Cox, one fit per step)",
+        pool.rate(1)
+        per = (time.perf_counter() - t0)
+        budget = 150.0 / max(1, args.steps + args.warmup)
+        ncoords = max(1, int(budget / max(per, 1e-6)))
+        for _ in range(args.warmup):
+            pool.rate(ncoords)
+        rates = [pool.rate(ncoords) for _ in range(args.steps)]
+    finally:
+        pool.close()
+    value = float(np.mean(rates))
+    ms = 1e3 * cores * ncoords / value
+    sample = (f"{cores} independent oracle processes (one per usable core), each running {ncoords} coordinate "
+              f"updates of the same fit per step; FP64 C oracle")
+    return {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "coord_updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": wname, "precision": "fp64",
-                                                      "parallelism": "cpu oracle, rank 0 only"},
-            "cpu_baseline": {"value": value, "unit": "coord_updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic (seeded)", "config": headline_config(wname),
+            "parallelism": f"cpu oracle, {cores} processes on rank 0",
+            "cpu_baseline": {"value": value, "unit": "coord_updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "coord_updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -840,15 +779,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32c"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "stream"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of N (testing only)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="stratified", choices=["stratified", "time_varying", "tvc", "tvc_cv", "ps_cv", "cv", "e1", "batch", "serving"])
+    ap.add_argument("--no-sub", action="store_true", help="headline only (no moving / batch / serving sub-results)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default="default",
+                    choices=["default", "time_varying", "cv", "e1", "batch", "serving"])
     ap.add_argument("--rate", type=float, default=20.0)
-    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--pool", type=int, default=24)
     ap.add_argument("--max-rows", type=int, default=2_000_000)
-    ap.add_argument("--strata", type=int, default=0, help="e1 / ps_cv workloads: number of strata (defaults 50,000 / 10)")
+    ap.add_argument("--strata", type=int, default=0, help="e1 workload: number of strata (default 50,000)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -859,19 +803,45 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload != "stratified":
-        fn = {"time_varying": run_time_varying, "tvc": run_tvc, "tvc_cv": run_tvc_cv, "ps_cv": run_ps_cv, "cv": run_cv,
-              "e1": run_e1,
-              "batch": run_batch,
+    if args.workload != "default":
+        fn = {"time_varying": run_time_varying, "cv": run_cv, "e1": run_e1, "batch": run_batch,
               "serving": run_serving}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
+    # the oracle's iterate of the moving fit runs in its own process beside the GPU legs (started
+    # before the first CUDA call)
+    q = proc = None
+    if rank == 0 and not args.no_sub:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        proc = ctx.Process(target=_oracle_moving, args=(q, args.scale), daemon=True)
+        proc.start()
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
+    res, (data, ddev, stream, flush, G, K) = run_headline(args, rank, world, local_rank)
     if rank == 0:
+        if not args.no_e2e:
+            _, opts, _ = headline_workload(args.scale)
+            res["e2e"] = e2e(args, data, opts, stream)
+        if not args.no_sub:
+            res["batch"] = run_batch(args, sub=True)
+            if not args.no_serving:
+                res["serving"] = run_serving(args, sub=True)
+            orc = None
+            try:
+                got = q.get(timeout=900)
+                orc = None if (isinstance(got[0], str) and got[0] == "error") else got
+                if orc is None:
+                    res["oracle_error"] = got[1]
+            except Exception as e:
+                res["oracle_error"] = repr(e)
+            if proc is not None:
+                proc.join(timeout=10)
+            res["moving"] = run_moving(args, data, ddev, stream, flush, G, K, orc)
+        if not args.no_cpu:
+            res["cpu_baseline"] = cpu_baseline(args.scale, args.cpu_seconds)
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch

@@ -279,6 +279,16 @@ int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
  * every kernel node). For measurement; never decreases. */
 int64_t cox_launch_count(void);
 
+/* Failure handling. Every device-side wait in the kernels (a tile waiting for the sums of the
+ * tiles to its right, the CTAs of one fit exchanging their step records, the stages of the
+ * streaming pipeline) gives up after a bounded number of SM clocks; the call then returns
+ * COX_E_TIMEOUT and the kernel exits, so no wait can hang the GPU. This sets that bound for every
+ * kernel launched afterwards, process-wide (clocks <= 0: the default, 4e9 clocks, about 2 s);
+ * graphs already captured keep the bound they were captured with. A bound too short for a
+ * kernel's exchanges exercises the failure path without any fault: the calls fail with
+ * COX_E_TIMEOUT and later calls with the default bound succeed. Returns COX_OK. */
+int cox_debug_set_wait_limit(long long clocks);
+
 /* ---------------------------------------------------------------- primitives
  * Segmented inclusive scan with the flag-value operator of §2.6 ("Efficient parallel
  * segmented-scan on GPUs"): out[i] = sum of a[k] for k from the last index h <= i with
@@ -296,7 +306,8 @@ int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *o
  * Its scratch is one static device array of 81,936 bytes that every GPU loading this library
  * holds until the process exits; n is therefore limited to 16,777,216 values (COX_E_INVALID
  * beyond that). The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * (cudaGetSymbolAddress) with that device current, and looks it up again if the device's
+ * context has been recreated since (cudaDeviceReset); make that first call before any stream
  * capture. All calls share the array and clear the parts that must start at zero, so calls
  * whose work overlaps on the GPU race with each other: issue them one at a time (same stream,
  * or synchronized). Other arguments, errors and stream behaviour as cox_segscan. */

@@ -78,7 +78,7 @@ def lib():
             L.ocx_step.argtypes = [dbl, dbl, dbl, vp, i32, dbl, dbl, i32]
             L.ocx_step.restype = dbl
             L.ocx_fit.argtypes = [C.POINTER(_Data), C.POINTER(_Opts), vp, vp, C.POINTER(_Info)]
-            L.ocx_time_sample.argtypes = [C.POINTER(_Data), C.POINTER(_Opts), i32, vp]
+            L.ocx_time_sample.argtypes = [C.POINTER(_Data), C.POINTER(_Opts), i32, vp, vp]
             _lib = L
     return _lib
 
@@ -222,12 +222,15 @@ def fit(data, opts, beta0=None, max_sweeps=None):
                                    objective=info.objective, converged=bool(info.converged))
 
 
-def time_sample(data, opts, ncoords: int) -> float:
-    """Run ``ncoords`` coordinate steps from beta = 0 (a bounded timing sample). Returns a checksum."""
+def time_sample(data, opts, ncoords: int, return_beta: bool = False):
+    """Run ``ncoords`` coordinate steps from beta = 0 (a bounded timing sample: the first
+    ``ncoords`` steps of the fit, cyclic order). Returns a checksum, or (checksum, beta) with
+    ``return_beta``."""
     b = _Bound(data)
     o, keep = _opts(opts, b.p)
     out = np.zeros(1)
-    rc = lib().ocx_time_sample(C.byref(b.s), C.byref(o), int(ncoords), _ptr(out))
+    beta = np.zeros(max(b.p, 1)) if return_beta else None
+    rc = lib().ocx_time_sample(C.byref(b.s), C.byref(o), int(ncoords), _ptr(out), _ptr(beta))
     if rc:
         raise RuntimeError(f"ocx_time_sample failed: {rc}")
-    return float(out[0])
+    return (float(out[0]), beta[:b.p].copy()) if return_beta else float(out[0])

@@ -536,7 +536,7 @@ int ocx_fit(const ocx_data *d, const ocx_options *o, const double *beta0, double
 
 /* A bounded sample of the fit's work, for timing: `ncoords` coordinate evaluations
  * (risk sums + gradient/Hessian + step + eta update) starting from beta = 0. */
-int ocx_time_sample(const ocx_data *d, const ocx_options *o, int32_t ncoords, double *checksum) {
+int ocx_time_sample(const ocx_data *d, const ocx_options *o, int32_t ncoords, double *checksum, double *beta_out) {
   ctx_t c;
   int rc = ctx_init(&c, d);
   if (rc) return rc;
@@ -571,6 +571,8 @@ int ocx_time_sample(const ocx_data *d, const ocx_options *o, int32_t ncoords, do
     acc += g1 + g2;
   }
   *checksum = acc;
+  if (beta_out)
+    for (int32_t j = 0; j < p; ++j) beta_out[j] = beta[j];
   free(eta); free(D); free(S0); free(S1); free(S2); free(dX); free(tr); free(beta);
   ctx_free(&c);
   return OCX_OK;

@@ -27,7 +27,7 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
            "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split", "cox_cv_path",
-           "cox_segscan_noalloc", "cox_server_create", "cox_server_submit", "cox_server_poll",
+           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
 
@@ -126,6 +126,7 @@ def lib():
             L.cox_launch_count.restype = i64
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
             L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
+            L.cox_debug_set_wait_limit.argtypes = [C.c_longlong]
             L.cox_server_create.argtypes = [C.POINTER(cox_server_options), C.POINTER(vp)]
             L.cox_server_submit.argtypes = [vp, C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_uint64)]
             L.cox_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(cox_fit_info)]
@@ -393,6 +394,12 @@ _P_CACHE = {}
 
 def cox_launch_count() -> int:
     return int(lib().cox_launch_count())
+
+
+def cox_debug_set_wait_limit(clocks: int) -> None:
+    """Bound, in SM clocks, of every device-side wait of kernels launched afterwards (<= 0: the
+    default). For tests of the failure path: too short a bound makes calls return COX_E_TIMEOUT."""
+    _check(lib().cox_debug_set_wait_limit(int(clocks)))
 
 
 def cox_segscan(a, head_flags, out=None, stream=None):

@@ -58,7 +58,7 @@ struct cox_handle {
   DevFit *dfit = nullptr;
   FitCtl *ctl = nullptr;
   LaunchCtl *lc = nullptr;
-  int2 *items = nullptr;
+  WorkItem *items = nullptr;
   int n_items = 0;
   int grid = 0;
   int valued = 0;
@@ -66,8 +66,10 @@ struct cox_handle {
   cudaStream_t own_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
+  long long graph_spin = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   FitCtl *h_ctl = nullptr;     // pinned readback
+  LaunchCtl *h_lc = nullptr;   // pinned readback of the launch control (same allocation)
   uint8_t *penalize = nullptr; // device copy of the penalty mask
   double *gout = nullptr;
   double *S0 = nullptr, *S1 = nullptr;
@@ -129,6 +131,12 @@ cox_options default_options() {
   return o;
 }
 
+// Work item of the streaming kernel: tile t of the handle's data as fit f of a work list.
+WorkItem work_item(const cox_handle *h, int f, int t) {
+  const std::vector<int32_t> &lo = h->sd->prep.h_tile_lo, &g = h->sd->prep.h_tile_g;
+  return WorkItem{f, t, lo[size_t(t)], lo[size_t(t) + 1], g[size_t(t)], g[size_t(t) + 1], {0, 0}};
+}
+
 // Allocate the per-fit state of a handle on its (shared) data.
 int alloc_fit_state(cox_handle *h) {
   const DevData &d = D(h);
@@ -141,7 +149,7 @@ int alloc_fit_state(cox_handle *h) {
   h->ctl = static_cast<FitCtl *>(B.get(sizeof(FitCtl)));
   h->lc = static_cast<LaunchCtl *>(B.get(sizeof(LaunchCtl)));
   h->dfit = static_cast<DevFit *>(B.get(sizeof(DevFit)));
-  h->items = static_cast<int2 *>(B.get(std::max<int64_t>(T, 1) * sizeof(int2)));
+  h->items = static_cast<WorkItem *>(B.get(std::max<int64_t>(T, 1) * sizeof(WorkItem)));
   h->hfit.eta = static_cast<double *>(B.get(std::max<int64_t>(M, 1) * sizeof(double)));
   h->hfit.v = B.get((M + tile_k + 64) * sv);
   h->hfit.beta = static_cast<double *>(B.get(std::max<int64_t>(p, 1) * sizeof(double)));
@@ -171,13 +179,17 @@ int alloc_fit_state(cox_handle *h) {
     if (!h->i_trec || !h->i_tref || !h->i_bcopy || !h->i_vdw)
       return fail(h, COX_E_OOM, "device allocation failed for the incremental state");
   }
-  if (cudaMallocHost(&h->h_ctl, sizeof(FitCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
+  void *pin = nullptr;
+  if (cudaMallocHost(&pin, sizeof(FitCtl) + sizeof(LaunchCtl)) != cudaSuccess) return cuda_fail(h, "pinned alloc");
+  h->h_ctl = static_cast<FitCtl *>(pin);
+  h->h_lc = reinterpret_cast<LaunchCtl *>(static_cast<unsigned char *>(pin) + sizeof(FitCtl));
+  *h->h_lc = LaunchCtl{};
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
   if (cudaMemsetAsync(h->hfit.v, 0, (M + tile_k + 64) * sv, h->stream) != cudaSuccess) return cuda_fail(h, "memset");
-  std::vector<int2> it(static_cast<size_t>(std::max<int64_t>(T, 1)));
-  for (int64_t t = 0; t < T; ++t) it[t] = make_int2(0, int(T - 1 - t));   // reverse order for the look-back
+  std::vector<WorkItem> it(static_cast<size_t>(std::max<int64_t>(T, 1)));
+  for (int64_t t = 0; t < T; ++t) it[t] = work_item(h, 0, int(T - 1 - t));   // reverse order for the look-back
   h->n_items = int(T);
-  if (cudaMemcpyAsync(h->items, it.data(), std::max<int64_t>(T, 1) * sizeof(int2), cudaMemcpyHostToDevice, h->stream) !=
+  if (cudaMemcpyAsync(h->items, it.data(), std::max<int64_t>(T, 1) * sizeof(WorkItem), cudaMemcpyHostToDevice, h->stream) !=
       cudaSuccess)
     return cuda_fail(h, "items copy");
   LaunchCtl lc{0u, 0u, int32_t(T), 1, 0};
@@ -237,6 +249,7 @@ int init_state(cox_handle *h, const double *beta0) {
   if (p > 0 && cudaMemcpyAsync(h->hfit.trust, ones.data(), p * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return cuda_fail(h, "trust copy");
   if (d.T > 0 && cudaMemsetAsync(h->hfit.tstat, 0, d.T * sizeof(uint32_t), s) != cudaSuccess) return cuda_fail(h, "memset");
+  if (cudaMemsetAsync(&h->lc->error, 0, sizeof(int32_t), s) != cudaSuccess) return cuda_fail(h, "memset");
   FitCtl c{};
   c.j = 0;
   c.state = kRunning;
@@ -258,7 +271,8 @@ int init_state(cox_handle *h, const double *beta0) {
 }
 
 int read_ctl(cox_handle *h) {
-  if (cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(FitCtl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+  if (cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(FitCtl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->h_lc, h->lc, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
     return cuda_fail(h, "ctl read");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "kernel execution");
   return COX_OK;
@@ -271,7 +285,7 @@ int launch_mode(cox_handle *h, int mode, int j) {
 }
 
 int device_error(cox_handle *h) {
-  const int e = h->h_ctl->error;
+  const int e = h->h_ctl->error ? h->h_ctl->error : h->h_lc->error;
   if (e == COX_E_TIMEOUT) return fail(h, COX_E_TIMEOUT, "a device-side wait exceeded its bound");
   if (e == COX_E_RANGE) return fail(h, COX_E_RANGE, "|eta - shift| left the float exp range (use COX_FP64)");
   if (e) return fail(h, e, "device error");
@@ -282,7 +296,7 @@ int device_error(cox_handle *h) {
 // launches. The kernel ends the loop (sets the condition to 0) when the fit has stopped or the
 // launch budget in LaunchCtl is spent, so a whole fit is one cudaGraphLaunch.
 int build_graph(cox_handle *h, int len) {
-  if (h->graph && h->graph_len == len) return COX_OK;
+  if (h->graph && h->graph_len == len && h->graph_spin == wait_limit()) return COX_OK;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -322,6 +336,7 @@ int build_graph(cox_handle *h, int len) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(h, "graph instantiate");
   h->graph_len = len;
+  h->graph_spin = wait_limit();   // the wait bound is captured into the graph's launches
   return COX_OK;
 }
 
@@ -346,6 +361,7 @@ ResParams res_params(cox_handle *h) {
   prm.tagg = h->r_tagg;
   prm.tpart = h->r_tpart;
   prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * D(h).p + 2;
+  prm.spin = wait_limit();
   return prm;
 }
 
@@ -359,7 +375,8 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
       cudaMemsetAsync(h->r_tpart, 0, 12 * RT * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
   ResParams prm = res_params(h);
-  // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
+#if COX_TRACE_ON
+  // phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
   const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
   BufferSet trbuf;
@@ -368,6 +385,7 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
     prm.trace_steps = prm.trace ? tr_steps : 0;
     if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * RT * 8 * sizeof(uint64_t), s);
   }
+#endif
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
   cudaEventRecord(h->ev0, s);
@@ -375,6 +393,7 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
   cudaEventRecord(h->ev1, s);
   int rc;
   if ((rc = read_ctl(h))) return rc;
+#if COX_TRACE_ON
   if (prm.trace_steps > 0) {
     // per CTA: mean phase times and the time from the earliest step start to its partial publish
     std::vector<uint64_t> tr(size_t(prm.trace_steps * RT * 8));
@@ -416,6 +435,7 @@ int fit_resident(cox_handle *h, double *beta_out, cox_fit_info *info) {
     if (n) std::fprintf(stderr, "  fastest CTA %d positions %d groups %d: publish %.0f, step %.0f\n", c, rlo[c + 1] - rlo[c],
                         rg[c + 1] - rg[c], pub[c] / n, stepm[c] / n);
   }
+#endif
   if ((rc = device_error(h))) return rc;
   const FitCtl &c = *h->h_ctl;
   if (c.state == kRunning) return fail(h, COX_E_INVALID, "cox_fit: the resident kernel stopped before the fit did");
@@ -454,6 +474,7 @@ IncParams incr_params(cox_handle *h, bool compact) {
   prm.bcopy = h->i_bcopy;
   prm.vdw = h->i_vdw;
   prm.max_steps = (int64_t(h->opts.max_sweeps) + 2) * D(h).p + 2;
+  prm.spin = wait_limit();
   return prm;
 }
 
@@ -548,6 +569,7 @@ int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, dou
     // each fit's time is the time of its wave
     std::vector<float> wms(waves.size(), 0.0f);
     for (size_t w = 0; w < waves.size(); ++w) cudaEventElapsedTime(&wms[w], ev[w], ev[w + 1]);
+#if COX_TRACE_ON
     if (std::getenv("COXGB_BATCH_TRACE")) {   // opt-in: the waves' composition and times
       for (size_t w = 0; w < waves.size(); ++w) {
         int64_t maxsteps = 0, sumsteps = 0;
@@ -561,6 +583,7 @@ int batch_incr(cox_handle *const *hs, int32_t n, const double *const *beta0, dou
                      maxsteps ? 1e3 * wms[w] / double(maxsteps) : 0.0, (long long)sumsteps);
       }
     }
+#endif
     for (size_t w = 0; w < waves.size(); ++w)
       for (int i : waves[w]) {
         cox_handle *h = hs[i];
@@ -594,7 +617,8 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
       cudaMemsetAsync(h->i_tref, 0, 4 * int64_t(IT) * sizeof(uint64_t), s) != cudaSuccess)
     return cuda_fail(h, "memset");
   IncParams prm = incr_params(h, false);
-  // optional phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
+#if COX_TRACE_ON
+  // phase trace of the first steps (COXGB_PHASE_TRACE=<steps>), printed to stderr
   const char *tr_env = std::getenv("COXGB_PHASE_TRACE");
   const int64_t tr_steps = tr_env ? std::max<int64_t>(0, std::atoll(tr_env)) : 0;
   BufferSet trbuf;
@@ -603,6 +627,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
     prm.trace_steps = prm.trace ? tr_steps : 0;
     if (prm.trace) cudaMemsetAsync(prm.trace, 0, tr_steps * IT * 24 * sizeof(uint64_t), s);
   }
+#endif
   if (!h->ev0 && (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess))
     return cuda_fail(h, "event create");
   cudaEventRecord(h->ev0, s);
@@ -647,6 +672,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
     cudaEventRecord(h->ev1, s);
     if (cudaEventSynchronize(h->ev1) != cudaSuccess) return cuda_fail(h, "event");
   }
+#if COX_TRACE_ON
   if (prm.trace_steps > 0) {
     // per CTA, mean SM clocks between consecutive phase points of thread 0 (update | patch | scan
     // | barrier | S0 | ratios | group sums | barrier | CTA sums | barrier | push | inbox | barrier
@@ -694,6 +720,7 @@ int fit_incr(cox_handle *h, double *beta_out, cox_fit_info *info) {
     for (int q = 0; q < std::min(IT, 3) && n; ++q) row("last ", order[q]);
     if (n) row("first", order[IT - 1]);
   }
+#endif
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   return incr_result(h, beta_out, info, ms, launches);
@@ -1153,6 +1180,11 @@ int cox_dx(cox_handle *h, double *dx) {
 
 int64_t cox_launch_count(void) { return launch_count(); }
 
+int cox_debug_set_wait_limit(long long clocks) {
+  set_wait_limit(clocks);
+  return COX_OK;
+}
+
 int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes) {
   if (!data || !bytes) return fail(nullptr, COX_E_INVALID, "cox_footprint: null argument");
   const int precision = opts ? opts->precision : COX_FP64;
@@ -1220,7 +1252,7 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     total_items += D(hs[i]).T;
     valued |= hs[i]->valued;
   }
-  int2 *items = static_cast<int2 *>(B.get(std::max<int64_t>(total_items, 1) * sizeof(int2)));
+  WorkItem *items = static_cast<WorkItem *>(B.get(std::max<int64_t>(total_items, 1) * sizeof(WorkItem)));
   FitCtl *hc = nullptr;
   if (!rc && (!fits || !ctls || !lc || !items)) rc = fail(nullptr, COX_E_OOM, "cox_batch_fit: allocation");
   if (!rc && cudaMallocHost(&hc, n * sizeof(FitCtl)) != cudaSuccess) rc = cuda_fail(nullptr, "pinned alloc");
@@ -1235,18 +1267,18 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     rc = cuda_fail(nullptr, "fits copy");
   std::vector<int> running(n, 1);
   auto rebuild_items = [&]() -> int {
-    std::vector<int2> it;
+    std::vector<WorkItem> it;
     // interleave fits tile by tile (each fit's tiles stay in reverse order)
     int64_t maxT = 0;
     for (int i = 0; i < n; ++i)
       if (running[i]) maxT = std::max<int64_t>(maxT, D(hs[i]).T);
     for (int64_t k = 0; k < maxT; ++k)
       for (int i = 0; i < n; ++i)
-        if (running[i] && k < D(hs[i]).T) it.push_back(make_int2(i, int(D(hs[i]).T - 1 - k)));
+        if (running[i] && k < D(hs[i]).T) it.push_back(work_item(hs[i], i, int(D(hs[i]).T - 1 - k)));
     int act = 0;
     for (int i = 0; i < n; ++i) act += running[i];
     LaunchCtl l{0u, 0u, int32_t(it.size()), act, 0};
-    if (!it.empty() && cudaMemcpyAsync(items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (!it.empty() && cudaMemcpyAsync(items, it.data(), it.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return cuda_fail(nullptr, "items copy");
     if (cudaMemcpyAsync(lc, &l, sizeof(l), cudaMemcpyHostToDevice, s) != cudaSuccess) return cuda_fail(nullptr, "lc copy");
     return cudaStreamSynchronize(s) == cudaSuccess ? COX_OK : cuda_fail(nullptr, "items");
@@ -1280,9 +1312,15 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     if (cudaGraphLaunch(graph, s) != cudaSuccess) { rc = cuda_fail(nullptr, "graph launch"); break; }
     count_launches(len);
     launched += len;
+    LaunchCtl lc_now{};
     if (cudaMemcpyAsync(hc, ctls, n * sizeof(FitCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&lc_now, lc, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       rc = cuda_fail(nullptr, "batch execution");
+      break;
+    }
+    if (lc_now.error) {
+      rc = fail(nullptr, COX_E_TIMEOUT, "cox_batch_fit: a device-side wait exceeded its bound");
       break;
     }
     bool changed = false;
@@ -1407,7 +1445,7 @@ struct cox_server {
   DevFit *fits = nullptr;
   FitCtl *ctls = nullptr;
   LaunchCtl *lc = nullptr;
-  int2 *items = nullptr;
+  WorkItem *items = nullptr;
   int64_t items_cap = 0;
   FitCtl *h_ctls = nullptr;
   std::vector<Req *> slots;
@@ -1504,7 +1542,7 @@ void prep_loop(cox_server *S) {
 }
 
 int rebuild_batch(cox_server *S) {
-  std::vector<int2> it;
+  std::vector<WorkItem> it;
   int64_t maxT = 0;
   int valued = 0, active = 0;
   for (size_t sl = 0; sl < S->slots.size(); ++sl)
@@ -1516,11 +1554,11 @@ int rebuild_batch(cox_server *S) {
   for (int64_t k = 0; k < maxT; ++k)
     for (size_t sl = 0; sl < S->slots.size(); ++sl)
       if (Req *r = S->slots[sl])
-        if (k < D(r->h).T) it.push_back(make_int2(int(sl), int(D(r->h).T - 1 - k)));
+        if (k < D(r->h).T) it.push_back(work_item(r->h, int(sl), int(D(r->h).T - 1 - k)));
   if (int64_t(it.size()) > S->items_cap || valued != S->graph_valued || !S->graph) {
     if (int64_t(it.size()) > S->items_cap) {
       const int64_t cap = std::max<int64_t>(int64_t(it.size()) * 2, S->items_cap * 2);
-      int2 *ni = static_cast<int2 *>(S->bufs.get(cap * sizeof(int2)));
+      WorkItem *ni = static_cast<WorkItem *>(S->bufs.get(cap * sizeof(WorkItem)));
       if (!ni) return COX_E_OOM;
       S->items = ni;   // the old buffer stays in the set until the server is destroyed
       S->items_cap = cap;
@@ -1533,7 +1571,9 @@ int rebuild_batch(cox_server *S) {
     if (cudaStreamBeginCapture(S->run_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return COX_E_CUDA;
     int rc = COX_OK;
     for (int i = 0; i < S->o.steps_per_replay && !rc; ++i)
-      rc = launch_ccd(S->o.precision, S->fits, S->items, S->lc, S->grid, kModeFit, 0, valued, S->run_stream);
+      // the streaming kernel's CTAs must all be resident at once: the grid of the variant launched
+      rc = launch_ccd(S->o.precision, S->fits, S->items, S->lc, std::max(1, ccd_max_grid(S->o.precision, valued)),
+                      kModeFit, 0, valued, S->run_stream);
     const cudaError_t e = cudaStreamEndCapture(S->run_stream, &g);
     if (rc || e != cudaSuccess) return COX_E_CUDA;
     const cudaError_t ei = cudaGraphInstantiate(&S->graph, g, 0);
@@ -1542,7 +1582,7 @@ int rebuild_batch(cox_server *S) {
     S->graph_valued = valued;
   }
   LaunchCtl l{0u, 0u, int32_t(it.size()), active, 0};
-  if (!it.empty() && cudaMemcpyAsync(S->items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice,
+  if (!it.empty() && cudaMemcpyAsync(S->items, it.data(), it.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                                      S->run_stream) != cudaSuccess)
     return COX_E_CUDA;
   if (cudaMemcpyAsync(S->lc, &l, sizeof(l), cudaMemcpyHostToDevice, S->run_stream) != cudaSuccess) return COX_E_CUDA;
@@ -1579,6 +1619,7 @@ void run_loop(cox_server *S) {
     }
     // cancellations are honoured here, at a replay boundary
     std::vector<Req *> retire;
+    bool waits_failed = false;   // a launch of the work list gave up a device-side wait
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (Req *r : S->slots)
@@ -1589,10 +1630,14 @@ void run_loop(cox_server *S) {
       dirty = false;
       if (!rc && cudaGraphLaunch(S->graph, S->run_stream) != cudaSuccess) rc = COX_E_CUDA;
       if (!rc) count_launches(S->o.steps_per_replay);
+      LaunchCtl lc_now{};
       if (!rc && (cudaMemcpyAsync(S->h_ctls, S->ctls, S->slots.size() * sizeof(FitCtl), cudaMemcpyDeviceToHost,
                                   S->run_stream) != cudaSuccess ||
+                  cudaMemcpyAsync(&lc_now, S->lc, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, S->run_stream) !=
+                      cudaSuccess ||
                   cudaStreamSynchronize(S->run_stream) != cudaSuccess))
         rc = COX_E_CUDA;
+      waits_failed = !rc && lc_now.error != 0;
       if (rc) {   // a CUDA failure ends every fit in flight with that error
         std::lock_guard<std::mutex> lk(S->mu);
         for (Req *r : S->slots)
@@ -1603,7 +1648,7 @@ void run_loop(cox_server *S) {
       S->step_launches += S->o.steps_per_replay;
       for (size_t sl = 0; sl < S->slots.size(); ++sl)
         if (Req *r = S->slots[sl])
-          if (S->h_ctls[sl].state != kRunning || S->h_ctls[sl].error) retire.push_back(r);
+          if (waits_failed || S->h_ctls[sl].state != kRunning || S->h_ctls[sl].error) retire.push_back(r);
     }
     for (Req *r : retire) {
       const int sl = r->slot;
@@ -1611,6 +1656,7 @@ void run_loop(cox_server *S) {
       int rc;
       if (r->cancel) rc = COX_E_INVALID;
       else if (c.error) rc = c.error;
+      else if (waits_failed) rc = COX_E_TIMEOUT;
       else rc = c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED;
       r->beta.assign(static_cast<size_t>(std::max<int32_t>(D(r->h).p, 1)), 0.0);
       if (rc >= 0 && D(r->h).p > 0)
@@ -1674,7 +1720,7 @@ int cox_server_create(const cox_server_options *opts, cox_server **out) {
   S->ctls = static_cast<FitCtl *>(S->bufs.get(n * sizeof(FitCtl)));
   S->lc = static_cast<LaunchCtl *>(S->bufs.get(sizeof(LaunchCtl)));
   S->items_cap = 1 << 16;
-  S->items = static_cast<int2 *>(S->bufs.get(S->items_cap * sizeof(int2)));
+  S->items = static_cast<WorkItem *>(S->bufs.get(S->items_cap * sizeof(WorkItem)));
   if (!S->fits || !S->ctls || !S->lc || !S->items) return fail(nullptr, COX_E_OOM, "cox_server_create: allocation");
   if (cudaMallocHost(&S->h_ctls, n * sizeof(FitCtl)) != cudaSuccess) return cuda_fail(nullptr, "cox_server_create: pinned");
   S->slots.assign(static_cast<size_t>(n), nullptr);

@@ -36,8 +36,15 @@ static __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) 
   uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+// 4-byte asynchronous copy (both addresses 4-byte aligned), for word-granular tables
+static __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
 static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// all but the most recent commit group have completed
+static __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // ------------------------------------------------------------------ precision policies
 // FP64: values, scans, ratios in double.
@@ -83,7 +90,6 @@ struct PF32C {
   }
 };
 
-constexpr long long kSpinBudget = 4000000000LL;   // ~2 s of SM clock for any device-side wait
 
 // ------------------------------------------------------------------ the coordinate step
 // §2.4, with these readings where the paper is silent: L2 adds beta/sigma^2 and 1/sigma^2; L1 uses the

@@ -182,7 +182,7 @@ static __device__ __forceinline__ double slot_f64(const uint64_t *s) { return *r
 // and store the payloads (low halves of the word pairs) in out. false: the wait gave up (bound
 // reached or another CTA raised an error).
 template <int N>
-static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *out, int32_t *err) {
+static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *out, int32_t *err, long long spin) {
   const long long t0 = clock64();
   unsigned polls = 0;
   for (;;) {
@@ -198,7 +198,7 @@ static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *ou
       return true;
     }
     if ((++polls & 63) == 0) {   // off the fast path: the bound and another CTA's failure
-      if (clock64() - t0 > kSpinBudget) {
+      if (clock64() - t0 > spin) {
         atomicCAS(err, 0, COX_E_TIMEOUT);
         return false;
       }
@@ -212,7 +212,7 @@ static __device__ bool wait_tagged(const uint64_t *w, uint32_t tag, uint64_t *ou
 // the error bit; the payloads go to out. Returns 1 (clean), 2 (the writer raised an error) or 0
 // (the wait gave up: bound reached or another CTA raised an error).
 template <int N>
-static __device__ int wait_record(const uint64_t *w, int n, uint32_t tag, uint64_t *out, int32_t *err,
+static __device__ int wait_record(const uint64_t *w, int n, uint32_t tag, uint64_t *out, int32_t *err, long long spin,
                                   unsigned *npolls = nullptr) {
   const long long t0 = clock64();
   unsigned polls = 0;
@@ -237,7 +237,7 @@ static __device__ int wait_record(const uint64_t *w, int n, uint32_t tag, uint64
       return bad ? 2 : 1;
     }
     if ((++polls & 63) == 0) {   // off the fast path: the bound and another CTA's failure
-      if (clock64() - t0 > kSpinBudget) {
+      if (clock64() - t0 > spin) {
         atomicCAS(err, 0, COX_E_TIMEOUT);
         return 0;
       }
@@ -911,7 +911,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       }
       if (tid < C) {
         uint64_t r[2] = {0, 0};
-        if (!wait_tagged<2>(prm.tref + 4 * int64_t(tid), tag, r, &ctl->error)) {
+        if (!wait_tagged<2>(prm.tref + 4 * int64_t(tid), tag, r, &ctl->error, prm.spin)) {
           atomicCAS(&s_err, 0, COX_E_TIMEOUT);
           r[0] = r[1] = 0;
         }
@@ -1091,7 +1091,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       unsigned polls = 0;
       const int nr = (tid > t && tid <= s_chain_end) ? kIncRec : nbase;
       const int got = wait_record<kIncRec>(prm.trec + int64_t(kIncRecWords) * ((int64_t(par) * C + t) * C + tid), nr,
-                                           epoch & ~kTagErr, r, &ctl->error, &polls);
+                                           epoch & ~kTagErr, r, &ctl->error, prm.spin, &polls);
       if (trace) trace[20] = polls;
       if (got != 1) {
         for (int i = 0; i < kIncRec; ++i) r[i] = 0;
@@ -1324,7 +1324,10 @@ static int inc_max_ctas() {
   static int cached = -2;
   if (cached != -2) return cached;
   const size_t sm = IncSmem<Cfg>::bytes;
-  int g = std::min(inc_max_ctas_of(ccd_incr_kernel<P, Cfg, false>, sm), inc_max_ctas_of(ccd_incr_kernel<P, Cfg, true>, sm));
+  int g = inc_max_ctas_of(ccd_incr_kernel<P, Cfg, false>, sm);
+#if COX_TRACE_ON
+  g = std::min(g, inc_max_ctas_of(ccd_incr_kernel<P, Cfg, true>, sm));
+#endif
   if (std::is_same<Cfg, IncWide>::value) g = std::min(g, inc_max_ctas_of(ccd_incr_multi_kernel<P>, sm));
   return cached = g;
 }
@@ -1337,10 +1340,15 @@ int inc_max_grid(int precision, int variant) {
 
 template <class Cfg>
 static const void *incr_entry(int precision, bool trace) {
-  return precision == COX_FP32C ? (trace ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, true>)
-                                         : reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, false>))
-                                : (trace ? reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, true>)
-                                         : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, false>));
+#if COX_TRACE_ON
+  if (trace)
+    return precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, true>)
+                                  : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, true>);
+#else
+  (void)trace;
+#endif
+  return precision == COX_FP32C ? reinterpret_cast<const void *>(ccd_incr_kernel<PF32C, Cfg, false>)
+                                : reinterpret_cast<const void *>(ccd_incr_kernel<PF64, Cfg, false>);
 }
 
 int launch_incr(int precision, const IncParams &prm, int grid, void *stream, int variant) {

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
     const bool need_ll = st.need_ll != 0;
     const uint32_t epoch = st.epoch;
     const int pslot = cur ^ 1;
-    uint64_t *trace = (prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * T_ + t) * 8 : nullptr;
+    uint64_t *trace = (COX_TRACE_ON && prm.trace && step < prm.trace_steps && tid == 0) ? prm.trace + (step * T_ + t) * 8 : nullptr;
     if (trace) trace[0] = gtimer();
     // this coordinate's inputs to the step, loaded now so their latency overlaps the step
     // (beta_j and trust_j were last written by CTA 0 at least one all-gather ago when p >= 2)
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
               ld_cg_v2(w + 2, w2, w3);
               ld_cg_v2(w + 4, w4, w5);
               if (tag_ok(w0, tag) && tag_ok(w1, tag) && tag_ok(w2, tag) && tag_ok(w3, tag) && tag_ok(w4, tag)) break;
-              if (clock64() - tstart > kSpinBudget || *reinterpret_cast<volatile int32_t *>(&ctl->error) != 0) {
+              if (clock64() - tstart > prm.spin || *reinterpret_cast<volatile int32_t *>(&ctl->error) != 0) {
                 quit = true;
                 break;
               }
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(kResThreads, 1) ccd_resident_kernel(const ResP
         if (tag_ok(w0, ptag) && tag_ok(w1, ptag) && tag_ok(w2, ptag) && tag_ok(w3, ptag) && tag_ok(w4, ptag) &&
             tag_ok(w5, ptag))
           break;
-        if (clock64() - tstart > kSpinBudget) { atomicCAS(&ctl->error, 0, COX_E_TIMEOUT); break; }
+        if (clock64() - tstart > prm.spin) { atomicCAS(&ctl->error, 0, COX_E_TIMEOUT); break; }
         if (*reinterpret_cast<volatile int32_t *>(&ctl->error) != 0) break;   // another CTA gave up
         __nanosleep(20);
       }

@@ -13,6 +13,15 @@
 #pragma once
 #include <cstdint>
 
+// Phase tracing of the resident and incremental kernels (timestamps per step, printed to stderr
+// when COXGB_PHASE_TRACE=<steps> is set at run time) exists only in builds compiled with
+// -DCOXGB_TRACE; the library's default build has none of it.
+#ifdef COXGB_TRACE
+#define COX_TRACE_ON 1
+#else
+#define COX_TRACE_ON 0
+#endif
+
 namespace coxgb {
 
 constexpr int kThreads = 256;        // CTA size of the scan kernel
@@ -41,6 +50,8 @@ struct DevData {
   const int32_t *tile_k;  // [T+1] first stratum whose last position is in tile t
   const double *dX;       // [p] delta' X_j
   const uint32_t *exit_bits; // [ceil(M/32)] exit positions (counting process) or nullptr
+  const uint32_t *head_bits; // [ceil(M/32) + 64] bitmap of the tie-group read positions
+  const uint32_t *cut_bits;  // [ceil(M/32) + 64] bitmap of the stratum ends
 };
 
 // Mutable control block of one fit (written by the last CTA of each launch).
@@ -88,9 +99,21 @@ struct LaunchCtl {
   int32_t n_items;
   int32_t active;         // running fits in the work list; 0 ends a conditional sweep loop
   int64_t budget;         // launches left before a conditional sweep loop is ended regardless
+  int32_t error;          // COX_E_TIMEOUT when a CTA's internal pipeline wait gave up (0: none)
+  int32_t pad_;
 };
 
+// Limit, in SM clocks, of every bounded device-side wait (look-backs, exchanges, pipeline
+// barriers): the process-wide value set with cox_debug_set_wait_limit, else kSpinBudget.
+long long wait_limit();
+
 enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
+
+// One work item of the streaming kernel: tile t of fit f, covering risk positions [lo, hi) and
+// tie groups [ga, gb).
+struct WorkItem {
+  int32_t f, t, lo, hi, ga, gb, pad_[2];
+};
 
 // Arguments of the resident kernel (ccd_resident.cu), passed by value.
 struct ResParams {
@@ -102,6 +125,7 @@ struct ResParams {
   int64_t max_steps;      // coordinate steps this launch may take
   uint64_t *trace;        // optional [2][trace_steps][8] phase timestamps (ns) of the first and last CTA
   int64_t trace_steps;
+  long long spin;         // limit of each device-side wait, SM clocks (wait_limit())
 };
 
 struct dw;   // double-word float (dw.cuh)
@@ -126,15 +150,17 @@ struct IncParams {
   const uint8_t *halt;    // [p] columns too dense for the lists: the launch stops before them (null: none)
   uint64_t *trace;        // optional [trace_steps][C][24] phase timestamps (ns) and counters
   int64_t trace_steps;
+  long long spin;         // limit of each device-side wait, SM clocks (wait_limit())
 };
 
 // Count of kernels launched by the library (every launcher adds to it).
 void count_launches(int64_t n);
 
-// Host-visible launchers (ccd.cu).
+// Host-visible launchers (ccd.cu). The streaming kernel assigns work items to CTAs statically, so
+// `grid` must not exceed ccd_max_grid(precision, valued) (every CTA resident at once).
 // `cond`: handle of the enclosing conditional WHILE graph node (0 = none). The kernel sets it
 // to 0 once no fit in the work list is running or the launch budget is spent.
-int launch_ccd(int precision, const DevFit *fits, const int2 *items, LaunchCtl *lc, int grid, int mode,
+int launch_ccd(int precision, const DevFit *fits, const WorkItem *items, LaunchCtl *lc, int grid, int mode,
                int j_eval, int valued, void *stream, unsigned long long cond = 0);
 int ccd_max_grid(int precision, int valued);
 int ccd_tile(int precision);

@@ -37,6 +37,13 @@ void set_allocator(cox_alloc_fn a, cox_free_fn f, void *ctx) {
   g_alloc_ctx = ctx;
 }
 
+static std::atomic<long long> g_wait_limit{0};
+long long wait_limit() {
+  const long long v = g_wait_limit.load(std::memory_order_relaxed);
+  return v > 0 ? v : 4000000000LL;   // ~2 s of SM clock
+}
+void set_wait_limit(long long clocks) { g_wait_limit.store(clocks > 0 ? clocks : 0, std::memory_order_relaxed); }
+
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
@@ -430,6 +437,14 @@ __global__ void cut_build_kernel(int32_t K, const int32_t *seg_start, int counti
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < K; k += int64_t(gridDim.x) * blockDim.x) {
     const int64_t b = seg_start[k + 1];
     cut_pos[k] = int32_t(counting ? 2 * b - 1 : b - 1);
+  }
+}
+
+// bit pos[i] of a bitmap, for every i (the bitmap starts zeroed)
+__global__ void set_bits_kernel(const int32_t *pos, int64_t n, uint32_t *bits) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t q = pos[i];
+    atomicOr(&bits[q >> 5], 1u << (q & 31));
   }
 }
 
@@ -1014,6 +1029,20 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   if (!cut_pos) return COX_E_OOM;
   if (K > 0) { count_launches(1); cut_build_kernel<<<grid_for(K), 256, 0, s>>>(int32_t(K), seg_start, counting, cut_pos); }
   D.cut_pos = cut_pos;
+  // the same positions as bitmaps over the risk sequence (the streaming kernel stages a tile's
+  // words beside its values); one padding word per 32 positions past the end
+  {
+    const int64_t words = (D.M + 31) / 32 + 64;
+    uint32_t *hb = static_cast<uint32_t *>(B.get(words * sizeof(uint32_t)));
+    uint32_t *cb = static_cast<uint32_t *>(B.get(words * sizeof(uint32_t)));
+    if (!hb || !cb) return COX_E_OOM;
+    cudaMemsetAsync(hb, 0, words * sizeof(uint32_t), s);
+    cudaMemsetAsync(cb, 0, words * sizeof(uint32_t), s);
+    if (G > 0) { count_launches(1); set_bits_kernel<<<grid_for(G), 256, 0, s>>>(head_pos, G, hb); }
+    if (K > 0) { count_launches(1); set_bits_kernel<<<grid_for(K), 256, 0, s>>>(cut_pos, K, cb); }
+    D.head_bits = hb;
+    D.cut_bits = cb;
+  }
 
   // delta'X
   double *dX = static_cast<double *>(B.get((p > 0 ? p : 1) * sizeof(double)));
@@ -1101,6 +1130,9 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   D.tile_k = tile_k;
   D.col_tile = col_tile;
   out->h_tile_lo = h_lo;
+  out->h_tile_g.resize(h_lo.size());
+  for (size_t t = 0; t < h_lo.size(); ++t)
+    out->h_tile_g[t] = int32_t(std::lower_bound(h_head.begin(), h_head.end(), h_lo[t]) - h_head.begin());
 
   // one-tile-per-CTA plans of the resident and incremental kernels (binary X only)
   auto tables = [&](const std::vector<int32_t> &rl, int32_t **lo_out, int32_t **g_out, int32_t **k_out,

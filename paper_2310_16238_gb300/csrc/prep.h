@@ -17,6 +17,8 @@ void *dev_alloc(size_t bytes);
 void dev_free(void *p, size_t bytes);
 bool pointer_on_device(const void *p);
 int64_t launch_count();
+// Process-wide limit of the device-side waits (0: the default); read by every launcher.
+void set_wait_limit(long long clocks);
 // Record `msg` as the calling thread's last error and return `code` (api.cu).
 int set_last_error(int code, const char *msg);
 
@@ -40,7 +42,8 @@ struct Prepared {
   int64_t nnz_rows = 0;
   std::vector<int64_t> h_col_ptr_rows;  // row-space CSC pointers
   std::vector<int64_t> h_col_ptr;       // position-space CSC pointers
-  std::vector<int32_t> h_tile_lo;
+  std::vector<int32_t> h_tile_lo;       // streaming plan: first position of each tile
+  std::vector<int32_t> h_tile_g;        // streaming plan: first tie group of each tile
   int32_t *strata_start = nullptr;      // [K+1] device
   // resident plan (one tile per CTA of the resident kernel); res_T == 0 when not eligible
   int32_t res_T = 0;

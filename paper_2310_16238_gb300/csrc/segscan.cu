@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -20,7 +21,6 @@ namespace coxgb {
 constexpr int kSegThreads = 256;
 constexpr int kSegItems = 16;
 constexpr int kSegTile = kSegThreads * kSegItems;
-constexpr long long kSegSpin = 4000000000LL;
 
 // Scratch layout (bytes): [0] ticket, [4] exited, [8] error, [16 .. 16+4T) status,
 // then aggregates (8T) and inclusive values (8T), 8-byte aligned.
@@ -63,7 +63,7 @@ __device__ __forceinline__ double seg_ld_relaxed(const double *p) {
 // status word: bit 0 aggregate published, bit 1 inclusive published, bit 2 tile holds a head
 __global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, const uint8_t *__restrict__ f,
                                                               int64_t n, double *b, unsigned char *scratch,
-                                                              int64_t tiles) {
+                                                              int64_t tiles, long long spin) {
   const SegScratchView S = seg_view(scratch, tiles);
   __shared__ int64_t s_tile;
   __shared__ double s_wsum[kSegThreads / 32];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, c
         for (int64_t u = t - 1; u >= 0; --u) {
           uint32_t st;
           while (((st = seg_ld_acquire(&S.status[u])) & 3u) == 0u) {
-            if (clock64() - t0 > kSegSpin) { atomicExch(S.error, 1u); st = 2u; break; }
+            if (clock64() - t0 > spin) { atomicExch(S.error, 1u); st = 2u; break; }
             __nanosleep(32);
           }
           if (st & 2u) { carry = seg_ld_relaxed(&S.incl[u]) + carry; break; }
@@ -167,14 +167,25 @@ __global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, c
   }
 }
 
+// Resident CTAs of segscan_kernel on a device (occupancy x SMs), computed once per device; the
+// array is indexed by device ordinal and written under a lock, so concurrent first calls and
+// devices with different SM counts each get their own value.
+constexpr int kGridDevices = 64;
+static std::atomic<int> g_seg_cap[kGridDevices];
+
 static int seg_grid(int64_t tiles) {
-  static int cap = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kGridDevices) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  int cap = dev >= 0 ? g_seg_cap[dev].load(std::memory_order_acquire) : 0;
   if (!cap) {
-    int per = 0, dev = 0, nsm = 0;
+    int per = 0, nsm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, segscan_kernel, kSegThreads, 0);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev >= 0 ? dev : 0);
     cap = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
+    if (dev >= 0) g_seg_cap[dev].store(cap, std::memory_order_release);
   }
   return int(tiles < cap ? tiles : cap);
 }
@@ -183,7 +194,7 @@ static int seg_grid(int64_t tiles) {
 static int segscan_run(const double *a, const uint8_t *f, int64_t n, double *b, unsigned char *scratch, int64_t tiles,
                        cudaStream_t s, std::string *err) {
   count_launches(1);
-  segscan_kernel<<<seg_grid(tiles), kSegThreads, 0, s>>>(a, f, n, b, scratch, tiles);
+  segscan_kernel<<<seg_grid(tiles), kSegThreads, 0, s>>>(a, f, n, b, scratch, tiles, wait_limit());
   if (cudaGetLastError() != cudaSuccess) { *err = "cox_segscan: launch failed"; return COX_E_CUDA; }
   uint32_t e = 0;
   if (cudaMemcpyAsync(&e, scratch + 8, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -236,10 +247,41 @@ static __device__ __align__(256) unsigned char g_segscan_static_scratch[kStaticS
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_static_mu;
-static unsigned char *g_static_addr[kMaxDevices] = {};
+// Per device: the array's device address and the CUDA context it was looked up in. A context
+// destroyed and recreated (cudaDeviceReset) may load the module at another address, so a cached
+// address is reused only while the current context is the one it came from.
+struct StaticSlot {
+  void *ctx;
+  unsigned char *addr;
+};
+static StaticSlot g_static_slot[kMaxDevices] = {};
 
-// Device address of the static scratch on the current device, looked up once per device
-// (host code cannot use the array's name as a device address).
+// The driver's cuCtxGetCurrent, fetched through the runtime (no link-time dependency on libcuda).
+using CtxGetCurrentFn = int (*)(void **);
+static CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
+static void *current_context() {
+  void *c = nullptr;
+  if (CtxGetCurrentFn f = ctx_get_current())
+    if (f(&c) != 0) c = nullptr;
+  return c;
+}
+
+// Device address of the static scratch on the current device (host code cannot use the array's
+// name as a device address): looked up with cudaGetSymbolAddress on the first call on each device
+// and again whenever the device's current context has changed since.
 static int static_scratch_address(unsigned char **out, std::string *err) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -248,7 +290,9 @@ static int static_scratch_address(unsigned char **out, std::string *err) {
     return COX_E_CUDA;
   }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  StaticSlot &slot = g_static_slot[dev];
+  void *ctx = current_context();
+  if (!slot.addr || !ctx || slot.ctx != ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_segscan_static_scratch);
     if (e != cudaSuccess || !p) {
@@ -256,9 +300,10 @@ static int static_scratch_address(unsigned char **out, std::string *err) {
       *err = std::string("cox_segscan_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
       return COX_E_CUDA;
     }
-    g_static_addr[dev] = static_cast<unsigned char *>(p);
+    slot.addr = static_cast<unsigned char *>(p);
+    slot.ctx = current_context();   // the lookup makes the device's primary context current
   }
-  *out = g_static_addr[dev];
+  *out = slot.addr;
   return COX_OK;
 }
 }  // namespace coxgb

@@ -281,54 +281,6 @@ def time_varying(n_subj: int = 1_000_000, p: int = 5000, k: int = 20, density: f
     return data, CoxOptions(penalty=PEN_L2, l2_var=l2_var, tol=1e-8)
 
 
-def tvc_cohort(n: int = 407_828, p: int = 9_666, cut: int = 10, dens_lo: float = 1.4e-3, dens_hi: float = 0.14,
-               hr_early: float = 0.98, hr_late: float = 0.67, event_frac: float = 0.10, max_days: int = 1095,
-               n_support: int = 50, lam_per_n: float = 1e-4, seed: int = SEED_BASE + 6):
-    """A new-user cohort with a treatment whose effect steps at day ``cut`` (paper §3.3 shape:
-    407,828 patients, 9,666 baseline covariates at about 97 % sparsity, the treatment split
-    into before / after day 10).
-
-    Column 0 is the treatment (Bernoulli 0.5), columns 1..p binary baseline covariates with
-    density log-uniform in [dens_lo, dens_hi] (mean 3 %). ``n_support`` baseline coefficients
-    ~ N(0, 0.3^2). Hazard h exp(x'beta) times hr_early^treat before ``cut`` and hr_late^treat
-    after it, with h chosen by bisection for ~``event_frac`` events; censoring uniform on
-    [1, max_days]; Y = ceil(min(T, C)). Options: L1 with gamma = lam_per_n * n on the baseline
-    covariates, the treatment unpenalized (the penalize mask is over the split columns: the
-    treatment's two copies first).
-    """
-    rng = np.random.default_rng(seed)
-    treat = rng.random(n) < 0.5
-    dens = np.exp(rng.uniform(math.log(dens_lo), math.log(dens_hi), p))
-    cols = [np.flatnonzero(treat)]
-    for j in range(p):
-        m = int(rng.binomial(n, dens[j]))
-        cols.append(np.sort(rng.choice(n, size=m, replace=False)))
-    beta = np.zeros(p + 1)
-    sup = 1 + rng.choice(p, size=min(n_support, p), replace=False)
-    beta[sup] = rng.normal(0.0, 0.3, len(sup))
-    eta = np.zeros(n)
-    for j in sup:
-        eta[cols[j]] += beta[j]
-    c1 = np.where(treat, hr_early, 1.0)
-    c2 = np.where(treat, hr_late, 1.0)
-    e_draw = rng.exponential(1.0, n)
-    cens = rng.uniform(1.0, max_days, n)
-
-    def times(hh):
-        w = hh * np.exp(eta)
-        h_cut = w * c1 * cut                              # cumulative hazard at the cut
-        return np.where(e_draw < h_cut, e_draw / (w * c1), cut + (e_draw - h_cut) / (w * c2))
-
-    h = _bisect(lambda hh: float(np.mean(times(hh) <= cens)), 1e-12, 1e3, event_frac, increasing=True)
-    t = times(h)
-    ev = (t <= cens).astype(np.uint8)
-    y = np.maximum(np.ceil(np.minimum(t, cens)), 1).astype(np.int64)
-    data = finalize(y, ev, None, None, cols, None, p + 1, beta, "tvc_cohort")
-    pen = np.ones(p + 2, np.uint8)
-    pen[:2] = 0
-    return data, CoxOptions(penalty=PEN_L1, lam=lam_per_n * n, tol=1e-8, penalize=pen)
-
-
 def synthetic_e1(n: int = 1_000_000, p: int = 2000, k: int = 50_000, density: float = 0.05, censor_frac: float = 0.3,
                  seed: int = SEED_BASE + 8):
     """The paper's synthetic experiment (§3.1): binary X with 5 % of the entries set to 1
@@ -357,56 +309,6 @@ def synthetic_e1(n: int = 1_000_000, p: int = 2000, k: int = 50_000, density: fl
     stratum = (np.arange(n, dtype=np.int64) * k) // n
     data = finalize(y, ev, stratum, None, cols, None, p, beta, "synthetic_e1")
     return data, CoxOptions(penalty=PEN_L1, lam=math.sqrt(2.0), tol=1e-8)
-
-
-def ps_stratified_cohort(n: int = 946_911, p: int = 9_976, k: int = 10, treated: float = 0.23,
-                         dens_lo: float = 1.4e-3, dens_hi: float = 0.14, hr: float = 0.82, event_frac: float = 0.05,
-                         max_days: int = 1825, n_support: int = 50, lam_per_n: float = 1e-4,
-                         seed: int = SEED_BASE + 9):
-    """A new-user cohort stratified on the propensity score (paper §3.2 shape: 946,911 patients,
-    9,976 baseline covariates at about 97 % sparsity, 23 % initiating the comparator, K = 5, 10
-    or 20 equal strata of the score).
-
-    Column 0 is the treatment; columns 1..p binary baseline covariates with density log-uniform
-    in [dens_lo, dens_hi] (mean 3 %). The treatment probability depends on the first 20 baseline
-    covariates through a logistic score; strata are the score's K quantile bins. Hazard
-    h exp(x'beta) hr^treat, ``n_support`` baseline coefficients ~ N(0, 0.3^2), h chosen by bisection
-    for ~``event_frac`` events, censoring uniform on [1, max_days]. Options: L1 with gamma =
-    lam_per_n * n on the baseline covariates, the treatment unpenalized (§3.2).
-    """
-    rng = np.random.default_rng(seed)
-    dens = np.exp(rng.uniform(math.log(dens_lo), math.log(dens_hi), p))
-    base_cols = []
-    for j in range(p):
-        m = int(rng.binomial(n, dens[j]))
-        base_cols.append(np.sort(rng.choice(n, size=m, replace=False)))
-    score = np.full(n, math.log(treated / (1.0 - treated)))
-    w = rng.normal(0.0, 0.5, min(20, p))
-    for j in range(min(20, p)):
-        score[base_cols[j]] += w[j]
-    prob = 1.0 / (1.0 + np.exp(-score))
-    treat = rng.random(n) < prob
-    order = np.argsort(prob, kind="stable")
-    stratum = np.empty(n, np.int64)
-    stratum[order] = (np.arange(n) * k) // n
-    cols = [np.flatnonzero(treat)] + base_cols
-    beta = np.zeros(p + 1)
-    beta[0] = math.log(hr)
-    sup = 1 + rng.choice(p, size=min(n_support, p), replace=False)
-    beta[sup] = rng.normal(0.0, 0.3, len(sup))
-    eta = np.zeros(n)
-    for j in np.flatnonzero(beta):
-        eta[cols[j]] += beta[j]
-    e_draw = rng.exponential(1.0, n)
-    cens = rng.uniform(1.0, max_days, n)
-    h = _bisect(lambda hh: float(np.mean(e_draw / (hh * np.exp(eta)) <= cens)), 1e-12, 1e3, event_frac, increasing=True)
-    t = e_draw / (h * np.exp(eta))
-    ev = (t <= cens).astype(np.uint8)
-    y = np.maximum(np.ceil(np.minimum(t, cens)), 1).astype(np.int64)
-    data = finalize(y, ev, stratum, None, cols, None, p + 1, beta, "ps_stratified_cohort")
-    pen = np.ones(p + 1, np.uint8)
-    pen[0] = 0
-    return data, CoxOptions(penalty=PEN_L1, lam=lam_per_n * n, tol=1e-8, penalize=pen)
 
 
 def subset_rows(data: CoxData, rows: np.ndarray) -> CoxData:

@@ -7,6 +7,7 @@ import threading
 import numpy as np
 import pytest
 
+import oracle
 from paper_2310_16238_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -95,3 +96,53 @@ def test_admission_rejects_requests_above_the_budget_and_cancel_frees():
         assert rb is not None and rb[1]["converged"]
         st = srv.stats()
         assert st["bytes_in_use"] == 0 and st["running"] == 0
+
+
+def _ll_scale(data, beta, ll):
+    """Magnitude of the terms summed in the log-likelihood (the relative error's denominator)."""
+    return max(abs(ll), float(np.abs(beta) @ np.abs(oracle.dX(data))) + float(data.event.sum()))
+
+
+@pytest.mark.parametrize("precision,btol,ltol", [(cox.COX_FP64, 1e-9, 1e-11), (cox.COX_FP32C, 1e-5, 1e-7)],
+                         ids=["fp64", "fp32c"])
+def test_served_results_match_the_oracle(precision, btol, ltol):
+    """Every result the server returns, with the other requests in flight beside it, is the
+    oracle's fit of that request after the same number of sweeps, within the path's tolerance
+    (FP64: 1e-9 in beta, 1e-11 in the log-likelihood; compensated FP32: 1e-5 and 1e-7)."""
+    reqs = _requests()
+    budget = 6 * max(cox.cox_footprint(d, o, precision) for d, o in reqs)
+    with cox.Server(memory_budget=budget, max_active=5, precision=precision) as srv:
+        ids = [srv.submit(d, o) for d, o in reqs]
+        got = [srv.wait(i, 120.0) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for (bb, ii), (d, o) in zip(got, reqs):
+        if precision == cox.COX_FP64:
+            ob, oi = oracle.fit(d, o, max_sweeps=ii["sweeps"])
+            assert ii["sweeps"] == oi["sweeps"] or not oi["converged"], (d.recipe, ii, oi)
+        else:
+            # the convergence test of a compensated-FP32 fit may fall one sweep apart from the
+            # FP64 oracle's; the iterates are compared after the same number of sweeps
+            o_same = synth.CoxOptions(penalty=o.penalty, lam=o.lam, l2_var=o.l2_var, penalize=o.penalize, tol=0.0)
+            ob, oi = oracle.fit(d, o_same, max_sweeps=ii["sweeps"])
+        assert _rel(bb, ob) <= btol, (d.recipe, _rel(bb, ob))
+        assert abs(ii["loglik"] - oi["loglik"]) <= ltol * _ll_scale(d, ob, oi["loglik"]), (d.recipe, ii, oi)
+
+
+def test_fp32c_results_in_the_mix_equal_standalone_fits():
+    """The compensated-FP32 server: each result in the mix equals the same request fitted alone
+    with the same precision, within the stated FP32C tolerance (1e-5 in beta, 1e-7 in the
+    log-likelihood)."""
+    reqs = _requests()
+    alone = []
+    for d, o in reqs:
+        with cox.Handle(d, o, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+            alone.append(h.fit())
+    budget = 6 * max(cox.cox_footprint(d, o, cox.COX_FP32C) for d, o in reqs)
+    with cox.Server(memory_budget=budget, max_active=5, precision=cox.COX_FP32C) as srv:
+        ids = [srv.submit(d, o) for d, o in reqs]
+        got = [srv.wait(i, 120.0) for i in ids]
+    for (b, info), (bb, ii), (d, o) in zip(alone, got, reqs):
+        assert abs(ii["sweeps"] - info["sweeps"]) <= 1, (d.recipe, ii, info)
+        assert _rel(bb, b) <= 1e-5, (d.recipe, _rel(bb, b))
+        assert abs(ii["loglik"] - info["loglik"]) <= 1e-7 * _ll_scale(d, b, info["loglik"])

@@ -454,3 +454,20 @@ def test_stratum_constant_column(name, data, opts):
     b, _ = oracle.fit(ex, o)
     b0, _ = oracle.fit(data, o)
     assert abs(b[-1]) <= 1e-10 and np.allclose(b[:-1], b0, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("name,data,opts", tiny_cases())
+def test_time_sample_is_the_fits_first_steps(name, data, opts):
+    """The timed CPU baseline (a bounded sample of k coordinate steps from beta = 0) does the fit's
+    own work: after k < p steps its coefficients are the first sweep's first k coefficients (the
+    cyclic order visits j = 0..k-1 first, and later coordinates have not moved), and after two
+    full sweeps they are the two-sweep fit's. Same arithmetic in the same order: bit-exact."""
+    o = synth.CoxOptions(penalty=opts.penalty, lam=opts.lam, l2_var=opts.l2_var, tol=0.0, max_sweeps=2)
+    b1, _ = oracle.fit(data, synth.CoxOptions(penalty=opts.penalty, lam=opts.lam, l2_var=opts.l2_var, tol=0.0,
+                                              max_sweeps=1))
+    b2, _ = oracle.fit(data, o)
+    k = data.p // 2 + 1
+    _, bk = oracle.time_sample(data, o, k, return_beta=True)
+    assert np.array_equal(bk[:k], b1[:k]) and not np.any(bk[k:])
+    _, bs = oracle.time_sample(data, o, 2 * data.p, return_beta=True)
+    assert np.array_equal(bs, b2)

@@ -96,29 +96,6 @@ def test_synthetic_e1_recipe():
     assert o.penalty == synth.PEN_L1 and o.lam == pytest.approx(math.sqrt(2.0))
 
 
-def test_tvc_cohort_recipe():
-    n, p = 20_000, 200
-    d, o = synth.tvc_cohort(n=n, p=p)
-    _check_layout(d)
-    assert d.stratum is None and d.p == p + 1
-    assert abs(_densities(d)[0] - 0.5) < 0.02                     # column 0: the treatment
-    assert abs(d.event.mean() - 0.10) < 0.01
-    assert d.stop.max() <= 1095
-    assert o.penalize.shape == (p + 2,) and not o.penalize[:2].any() and o.penalize[2:].all()
-    assert d.beta_true[0] == 0.0 and np.count_nonzero(d.beta_true) == 50
-
-
-def test_ps_stratified_cohort_recipe():
-    n, p, k = 20_000, 100, 10
-    d, o = synth.ps_stratified_cohort(n=n, p=p, k=k)
-    _check_layout(d)
-    assert np.array_equal(np.bincount(d.stratum, minlength=k), np.full(k, n // k))
-    assert abs(_densities(d)[0] - 0.23) < 0.03                    # ~23 % treated
-    assert abs(d.event.mean() - 0.05) < 0.006
-    assert d.beta_true[0] == pytest.approx(math.log(0.82))
-    assert o.penalize.shape == (p + 1,) and o.penalize[0] == 0 and o.penalize[1:].all()
-
-
 def test_batch_views_recipe():
     """Uneven training sets over one shared X: outcomes x folds sets, each with its penalty grid."""
     n_total, p = 50_000, 80
@@ -151,3 +128,21 @@ def test_serving_stream_recipe():
     assert abs(np.mean([r.counting for r in reqs]) - 0.5) < 0.04
     assert abs(np.mean([r.penalty == synth.PEN_L1 for r in reqs]) - 0.5) < 0.04
     assert min(r.k for r in reqs) >= 1 and max(r.k for r in reqs) <= 200
+
+
+def test_device_generators_follow_the_recipes():
+    """The torch generators used for serving requests too large for NumPy (run here on CPU
+    tensors): sorted rows, a valid CSC, the recipe's densities and event fractions."""
+    torch = pytest.importorskip("torch")
+    from paper_2310_16238_gb300 import synth_device as sd
+    for d, dens, ev in ((sd.stratified_sparse(40000, 40, 9, 0.01, 5, "cpu"), 0.01, 0.05),
+                        (sd.time_varying(12000, 30, 4, 0.01, 6, "cpu"), 0.01, None)):
+        host = synth.CoxData(stop=d.stop.numpy(), event=d.event.numpy(), col_ptr=d.col_ptr.numpy(),
+                             row_idx=d.row_idx.numpy(), p=d.p, stratum=d.stratum.numpy(),
+                             start=None if d.start is None else d.start.numpy())
+        _check_layout(host)
+        assert abs(np.diff(host.col_ptr).mean() / host.n - dens) < 0.1 * dens
+        if ev is not None:
+            assert abs(host.event.mean() - ev) < 0.2 * ev
+        else:
+            assert np.all(host.start < host.stop)

@@ -279,6 +279,40 @@ int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes);
  * every kernel node). For measurement; never decreases. */
 int64_t cox_launch_count(void);
 
+/* ---------------------------------------------------------------- one fit sharded by stratum
+ * The stratified partial likelihood is a sum over strata (§2.1 eq. strat_l) and every risk-set sum
+ * a suffix sum within its stratum (§2.6-§2.7), so one fit's rows, sorted by (stratum, stop), can be
+ * cut into contiguous shards, one per rank (GPU). A cut never splits a tie group (equal stratum and
+ * stop with an event); a stratum may be split (right-censored data). Each rank makes a handle on its
+ * own rows with cox_create (COX_FP64; options as for the whole fit) and, with the collectives done by
+ * the caller, every rank runs per coordinate j = 0 .. p-1 of every sweep, in lock step:
+ *   cox_shard_head     applies the previous step's update at the shard's entries of that column,
+ *                      then head[0..2] = the sums of exp(eta), x_j exp(eta), x_j^2 exp(eta) from the
+ *                      shard's first row to its first stratum end (head[3] = 0);
+ *   (all-gather of the head sums; the carry of a rank whose last stratum continues is the sum of the
+ *    next ranks' head sums that continue that stratum, up to the first rank where it ends)
+ *   cox_shard_partial  out = (G1, G2, sum d log S0, beta'dX) of column j over the shard's tie groups,
+ *                      the last stratum completed by `carry` (3 doubles; ignored unless set up with
+ *                      last_continues); the last two only when need_ll (the first coordinate of a
+ *                      sweep), else 0;
+ *   (all-reduce of the four sums)
+ *   cox_shard_step     from the summed `tot`: when need_ll the log-likelihood beta'dX - sum d log S0
+ *                      and the convergence test of the penalized objective (sweep = completed sweeps,
+ *                      stop when |obj_s - obj_{s-1}| <= tol |obj_s| or sweep >= max_sweeps), else /
+ *                      then the coordinate step (§2.4) with g' = -dX_j + G1 (dX the whole fit's) and
+ *                      g'' = G2, the same on every rank. *state: 0 running, 1 converged, 2 sweep
+ *                      limit; *loglik when need_ll.
+ * cox_shard_setup, once before the first coordinate: dx_global = delta'X of the whole fit (p
+ * doubles, the sum of the ranks' cox_dx), last_continues = 1 when the shard's last stratum continues
+ * on the next rank; it resets the fit state to beta = 0. cox_shard_beta copies the coefficients
+ * (identical on every rank). A handle set up for sharding serves only these calls. */
+int cox_shard_setup(cox_handle *h, const double *dx_global, int32_t last_continues);
+int cox_shard_head(cox_handle *h, int32_t j, double *head);
+int cox_shard_partial(cox_handle *h, int32_t j, const double *carry, int32_t need_ll, double *out);
+int cox_shard_step(cox_handle *h, int32_t j, const double *tot, int32_t need_ll, int32_t sweep, int32_t max_sweeps,
+                   int32_t *state, double *loglik);
+int cox_shard_beta(cox_handle *h, double *beta);
+
 /* Failure handling. Every device-side wait in the kernels (a tile waiting for the sums of the
  * tiles to its right, the CTAs of one fit exchanging their step records, the stages of the
  * streaming pipeline) gives up after a bounded number of SM clocks; the call then returns

@@ -27,7 +27,8 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
            "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split", "cox_cv_path",
-           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_server_create", "cox_server_submit", "cox_server_poll",
+           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_shard_setup", "cox_shard_head",
+           "cox_shard_partial", "cox_shard_step", "cox_shard_beta", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
 
@@ -127,6 +128,11 @@ def lib():
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
             L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
             L.cox_debug_set_wait_limit.argtypes = [C.c_longlong]
+            L.cox_shard_setup.argtypes = [vp, vp, i32]
+            L.cox_shard_head.argtypes = [vp, i32, vp]
+            L.cox_shard_partial.argtypes = [vp, i32, vp, i32, vp]
+            L.cox_shard_step.argtypes = [vp, i32, vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_double)]
+            L.cox_shard_beta.argtypes = [vp, vp]
             L.cox_server_create.argtypes = [C.POINTER(cox_server_options), C.POINTER(vp)]
             L.cox_server_submit.argtypes = [vp, C.POINTER(cox_data), C.POINTER(cox_options), C.POINTER(C.c_uint64)]
             L.cox_server_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(cox_fit_info)]

@@ -79,6 +79,10 @@ struct cox_handle {
   uint64_t *i_trec = nullptr, *i_tref = nullptr;
   double *i_bcopy = nullptr;
   dw *i_vdw = nullptr;
+  // one rank's part of a sharded fit (cox_shard_*): the global delta'X, small result buffers, the
+  // carry of a last stratum that continues on the next rank
+  double *sh_dx = nullptr, *sh_buf = nullptr, *sh_ext = nullptr;
+  int sh_open = 0;
   std::string err = "no error";
 };
 
@@ -1179,6 +1183,79 @@ int cox_dx(cox_handle *h, double *dx) {
 }
 
 int64_t cox_launch_count(void) { return launch_count(); }
+
+// ------------------------------------------------------------------ one fit sharded by stratum
+int cox_shard_setup(cox_handle *h, const double *dx_global, int32_t last_continues) {
+  if (!h || (!dx_global && D(h).p > 0)) return fail(h, COX_E_INVALID, "cox_shard_setup: null argument");
+  if (h->sd->precision != COX_FP64) return fail(h, COX_E_INVALID, "cox_shard_setup: shards run in COX_FP64");
+  const int64_t p = D(h).p;
+  if (!h->sh_dx) {
+    h->sh_dx = static_cast<double *>(h->bufs.get(std::max<int64_t>(p, 1) * sizeof(double)));
+    h->sh_buf = static_cast<double *>(h->bufs.get(8 * sizeof(double)));
+    h->sh_ext = static_cast<double *>(h->bufs.get(4 * sizeof(double)));
+    if (!h->sh_dx || !h->sh_buf || !h->sh_ext) return fail(h, COX_E_OOM, "cox_shard_setup: allocation");
+  }
+  if (p > 0 && cudaMemcpyAsync(h->sh_dx, dx_global, p * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess)
+    return cuda_fail(h, "cox_shard_setup: copy");
+  int rc = init_state(h, nullptr);
+  if (rc) return rc;
+  if (last_continues && !h->sh_open) {
+    if (launch_shard_open_end(h->sd->d_desc, const_cast<int32_t *>(D(h).tile_k), h->stream))
+      return cuda_fail(h, "cox_shard_setup: launch");
+    h->sh_open = 1;
+  }
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? COX_OK : cuda_fail(h, "cox_shard_setup");
+}
+
+int cox_shard_head(cox_handle *h, int32_t j, double *head) {
+  if (!h || !head || j < 0 || j >= D(h).p || !h->sh_dx) return fail(h, COX_E_INVALID, "cox_shard_head: bad arguments");
+  if (launch_shard_head(h->dfit, j, h->sh_buf, h->stream)) return cuda_fail(h, "cox_shard_head: launch");
+  int rc;
+  if ((rc = read_ctl(h)) || (rc = device_error(h))) return rc;
+  return copy_out(h, head, h->sh_buf, 4);
+}
+
+int cox_shard_partial(cox_handle *h, int32_t j, const double *carry, int32_t need_ll, double *out) {
+  if (!h || !out || j < 0 || j >= D(h).p || !h->sh_dx) return fail(h, COX_E_INVALID, "cox_shard_partial: bad arguments");
+  const int32_t nl = need_ll ? 1 : 0;
+  const double *ext = nullptr;
+  if (h->sh_open && carry) {
+    if (cudaMemcpyAsync(h->sh_ext, carry, 3 * sizeof(double), cudaMemcpyDefault, h->stream) != cudaSuccess)
+      return cuda_fail(h, "cox_shard_partial: carry");
+    ext = h->sh_ext;
+  }
+  if (cudaMemcpyAsync(&h->ctl->need_ll, &nl, sizeof(nl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&h->lc->ext, &ext, sizeof(ext), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "cox_shard_partial: control");
+  int rc;
+  if ((rc = launch_mode(h, kModeShard, j)) || (rc = read_ctl(h)) || (rc = device_error(h))) return rc;
+  const FitCtl &c = *h->h_ctl;
+  const double r[4] = {c.out_g1, c.out_g2, nl ? c.out_ll : 0.0, nl ? c.out_bdx : 0.0};
+  if (cudaMemcpy(out, r, sizeof(r), cudaMemcpyDefault) != cudaSuccess) return cuda_fail(h, "cox_shard_partial: out");
+  return COX_OK;
+}
+
+int cox_shard_step(cox_handle *h, int32_t j, const double *tot, int32_t need_ll, int32_t sweep, int32_t max_sweeps,
+                   int32_t *state, double *loglik) {
+  if (!h || !tot || j < 0 || j >= D(h).p || !h->sh_dx) return fail(h, COX_E_INVALID, "cox_shard_step: bad arguments");
+  double t[4];
+  if (cudaMemcpy(t, tot, sizeof(t), cudaMemcpyDefault) != cudaSuccess) return cuda_fail(h, "cox_shard_step: sums");
+  if (launch_shard_step(h->dfit, h->sh_dx, j, t, need_ll ? 1 : 0, sweep, max_sweeps, h->sh_buf, h->stream))
+    return cuda_fail(h, "cox_shard_step: launch");
+  double r[2];
+  if (cudaMemcpyAsync(r, h->sh_buf, sizeof(r), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cuda_fail(h, "cox_shard_step: result");
+  if (state) *state = int32_t(r[0]);
+  if (loglik) *loglik = r[1];
+  if (int32_t(r[0]) == kError) return fail(h, COX_E_CUDA, "cox_shard_step: device error");
+  return COX_OK;
+}
+
+int cox_shard_beta(cox_handle *h, double *beta) {
+  if (!h || !beta) return fail(h, COX_E_INVALID, "cox_shard_beta: null argument");
+  return copy_out(h, beta, h->hfit.beta, D(h).p);
+}
 
 int cox_debug_set_wait_limit(long long clocks) {
   set_wait_limit(clocks);

@@ -68,7 +68,8 @@ struct FitCtl {
   uint32_t done_tiles;    // tiles finished in the current launch
   int64_t coord_updates;
   double out_g1, out_g2;  // EVAL mode result
-  double out_ll;          // LL mode result
+  double out_ll;          // LL mode result (shard mode: the tie groups' sum d log S0)
+  double out_bdx;         // shard mode: beta'dX over the shard's rows (when the log-likelihood is due)
 };
 
 enum : int32_t { kRunning = 0, kConverged = 1, kMaxed = 2, kError = 3 };
@@ -101,13 +102,16 @@ struct LaunchCtl {
   int64_t budget;         // launches left before a conditional sweep loop is ended regardless
   int32_t error;          // COX_E_TIMEOUT when a CTA's internal pipeline wait gave up (0: none)
   int32_t pad_;
+  const double *ext;      // shard mode: sums (NV) of the last stratum beyond the data's end (null: none)
 };
 
 // Limit, in SM clocks, of every bounded device-side wait (look-backs, exchanges, pipeline
 // barriers): the process-wide value set with cox_debug_set_wait_limit, else kSpinBudget.
 long long wait_limit();
 
-enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2 };
+// kModeShard: one rank's part of a sharded fit -- column j's (G1, G2) and, when ctl->need_ll, the
+// log-likelihood terms over the shard's rows, the last stratum completed by lc->ext; no step.
+enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2, kModeShard = 3 };
 
 // One work item of the streaming kernel: tile t of fit f, covering risk positions [lo, hi) and
 // tie groups [ga, gb).
@@ -152,6 +156,12 @@ struct IncParams {
   int64_t trace_steps;
   long long spin;         // limit of each device-side wait, SM clocks (wait_limit())
 };
+
+// One rank's part of a sharded fit (shard.cu).
+int launch_shard_head(const DevFit *fit, int32_t j, double *out, void *stream);
+int launch_shard_step(const DevFit *fit, const double *dxg, int32_t j, const double *tot, int32_t need_ll, int32_t sweep,
+                      int32_t max_sweeps, double *out, void *stream);
+int launch_shard_open_end(DevData *d, int32_t *tile_k, void *stream);
 
 // Count of kernels launched by the library (every launcher adds to it).
 void count_launches(int64_t n);

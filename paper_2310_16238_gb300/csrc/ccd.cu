@@ -378,6 +378,11 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
             const int o = (st & 3u) == 2u ? 3 : 0;
 #pragma unroll
             for (int i = 0; i < NV; ++i) v[i] = ld_relaxed_f64(&F.tval[6 * u + o + i]);
+          } else if (lane == stop && u == T_ && lc->ext) {
+            // past the data's end: the continuation of its last stratum (the last tile may not have
+            // published its inclusive value yet, so a walk can reach here through its aggregate)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = lc->ext[i];
           }
 #pragma unroll
           for (int i = 0; i < NV; ++i) {

@@ -32,6 +32,7 @@ sample (a fixed number of coordinate updates of the same fit from beta = 0).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import multiprocessing as mp
@@ -368,12 +369,23 @@ def run_batch(args, sub=False):
     out["plain_fp64"] = {"fits_per_s": n_fits / sec, "seconds": sec, "engine": "AUTO per fit (one fit at a time)",
                          "clocks": clk.summary()}
 
-    def errors(betas):
-        eb = 0.0
-        for bb, (b, _) in zip(betas, ref):
+    flat = [(d, o) for d, ol in sets for o in ol]
+
+    def errors(betas, infos):
+        """Largest beta error relative to the fit's max |beta| against the plain FP64 fit stopped
+        at the same sweep (a fit whose convergence test passed one sweep earlier or later in the
+        other precision is refitted in FP64 for that many sweeps, untimed)."""
+        eb, mism = 0.0, 0
+        for k, (bb, ii, (b, i)) in enumerate(zip(betas, infos, ref)):
+            if ii["sweeps"] != i["sweeps"]:
+                mism += 1
+                d, o = flat[k]
+                o2 = dataclasses.replace(o, max_sweeps=int(ii["sweeps"]), tol=0.0)
+                with cox.Handle(d, o2, precision=cox.COX_FP64, stream=stream.cuda_stream) as h:
+                    b, _ = h.fit()
             den = max(np.max(np.abs(b)), 1e-12) if np.any(b) else 1.0
             eb = max(eb, float(np.max(np.abs(bb - b)) / den))
-        return eb
+        return eb, mism
 
     peak, src = hbm_peak()
     for prec, name, engine in ((cox.COX_FP32C, "batched_fp32c", cox.COX_ENGINE_STREAM),
@@ -389,9 +401,11 @@ def run_batch(args, sub=False):
         with ClockSampler(0) as clk:
             (betas, infos), sec, dev_ms = timed(lambda: cox.batch_fit(handles))
         launches = cox.cox_launch_count() - launches0
+        err, mism = errors(betas, infos)
         r = {"fits_per_s": n_fits / sec, "seconds": sec, "device_ms": dev_ms,
              "engine": ENGINE_NAMES.get(infos[0]["engine"], "unknown"), "tile": tile or None,
-             "max_rel_beta_err_vs_plain_fp64": errors(betas), "gpu_launches": int(launches),
+             "max_rel_beta_err_vs_plain_fp64": err, "sweep_mismatches_vs_plain_fp64": mism,
+             "gpu_launches": int(launches),
              "speedup_vs_plain": (n_fits / sec) / out["plain_fp64"]["fits_per_s"], "clocks": clk.summary()}
         if engine == cox.COX_ENGINE_STREAM:
             s_e = 4 if prec == cox.COX_FP32C else 8

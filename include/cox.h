@@ -323,6 +323,15 @@ int cox_shard_beta(cox_handle *h, double *beta);
  * COX_E_TIMEOUT and later calls with the default bound succeed. Returns COX_OK. */
 int cox_debug_set_wait_limit(long long clocks);
 
+/* Chunk length of the FP32C streaming kernel. The kernel streams each fit's risk sequence as
+ * chunks of consecutive tiles (4,096 positions per tile), one chunk per CTA, with one look-back
+ * between chunks; by default the library picks the smallest chunk length for which every resident
+ * CTA gets at most one chunk. This forces `tiles` tiles per chunk (1..64; 0 restores the automatic
+ * choice) for every work list built afterwards, process-wide; it changes the summation order only,
+ * not the method. Meant for tests of multi-tile chunks on small data. Returns COX_OK, or
+ * COX_E_INVALID for a value outside 0..64. */
+int cox_debug_set_chunk_tiles(int32_t tiles);
+
 /* ---------------------------------------------------------------- primitives
  * Segmented inclusive scan with the flag-value operator of §2.6 ("Efficient parallel
  * segmented-scan on GPUs"): out[i] = sum of a[k] for k from the last index h <= i with

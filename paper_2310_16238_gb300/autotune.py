@@ -13,7 +13,7 @@ import time
 from . import cox, synth
 
 _CACHE = {}
-CANDIDATES = {cox.COX_FP64: (2048, 4096), cox.COX_FP32C: (2048, 4096, 8192)}
+CANDIDATES = {cox.COX_FP64: (2048, 4096), cox.COX_FP32C: (2048, 4096)}
 
 
 def batch_tile(sets, precision, max_sweeps_probe: int = 1) -> int:

@@ -37,7 +37,7 @@ def _stale(lib: str, sources) -> bool:
     if not os.path.exists(lib):
         return True
     t = os.path.getmtime(lib)
-    deps = list(sources) + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "cox.h"), __file__]
+    deps = list(sources) + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "cox.h"), __file__]
     return any(os.path.getmtime(s) > t for s in deps)
 
 

@@ -27,7 +27,7 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
            "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split", "cox_cv_path",
-           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_shard_setup", "cox_shard_head",
+           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_debug_set_chunk_tiles", "cox_shard_setup", "cox_shard_head",
            "cox_shard_partial", "cox_shard_step", "cox_shard_beta", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
@@ -128,6 +128,7 @@ def lib():
             L.cox_segscan.argtypes = [vp, vp, i64, vp, vp]
             L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
             L.cox_debug_set_wait_limit.argtypes = [C.c_longlong]
+            L.cox_debug_set_chunk_tiles.argtypes = [C.c_int32]
             L.cox_shard_setup.argtypes = [vp, vp, i32]
             L.cox_shard_head.argtypes = [vp, i32, vp]
             L.cox_shard_partial.argtypes = [vp, i32, vp, i32, vp]
@@ -406,6 +407,12 @@ def cox_debug_set_wait_limit(clocks: int) -> None:
     """Bound, in SM clocks, of every device-side wait of kernels launched afterwards (<= 0: the
     default). For tests of the failure path: too short a bound makes calls return COX_E_TIMEOUT."""
     _check(lib().cox_debug_set_wait_limit(int(clocks)))
+
+
+def cox_debug_set_chunk_tiles(tiles: int) -> None:
+    """Tiles per chunk of the FP32C streaming kernel for work lists built afterwards (0: the
+    library's choice). For tests of multi-tile chunks on small data."""
+    _check(lib().cox_debug_set_chunk_tiles(int(tiles)))
 
 
 def cox_segscan(a, head_flags, out=None, stream=None):

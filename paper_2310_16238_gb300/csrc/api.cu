@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <thread>
 #include <unordered_map>
@@ -60,6 +61,7 @@ struct cox_handle {
   LaunchCtl *lc = nullptr;
   WorkItem *items = nullptr;
   int n_items = 0;
+  int nck = 0;                 // FP32C: chunks of this fit in its own work list
   int grid = 0;
   int valued = 0;
   cudaStream_t stream = nullptr;
@@ -141,6 +143,76 @@ WorkItem work_item(const cox_handle *h, int f, int t) {
   return WorkItem{f, t, lo[size_t(t)], lo[size_t(t) + 1], g[size_t(t)], g[size_t(t) + 1], {0, 0}};
 }
 
+// Tiles per chunk forced for every plan (0: automatic), set by cox_debug_set_chunk_tiles.
+std::atomic<int> g_chunk_tiles{0};
+
+// Chunk plan of the FP32C chunked kernel for fits of T[i] tiles sharing `slots` resident CTAs: the
+// smallest chunk length C (tiles, at most kChunkMaxTiles) for which the fits' chunk counts
+// ceil(T[i] / C) add up to at most `slots`, so one launch gives every CTA at most one chunk (the
+// kernel assigns chunks to CTAs statically). Returns each fit's chunk count.
+std::vector<int> plan_chunks(const std::vector<int64_t> &T, int slots) {
+  auto total = [&](int64_t C) {
+    int64_t s = 0;
+    for (int64_t t : T) s += (t + C - 1) / C;
+    return s;
+  };
+  int64_t C = g_chunk_tiles.load();
+  if (C <= 0) {
+    int64_t lo = 1, hi = kChunkMaxTiles;
+    if (total(hi) <= slots) {
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (total(mid) <= int64_t(slots)) hi = mid;
+        else lo = mid + 1;
+      }
+    }
+    C = hi;
+  }
+  C = std::max<int64_t>(1, std::min<int64_t>(C, kChunkMaxTiles));
+  std::vector<int> n(T.size());
+  for (size_t i = 0; i < T.size(); ++i) n[i] = int(T[i] > 0 ? (T[i] + C - 1) / C : 0);
+  return n;
+}
+
+// Work items of fit f of a work list in the order the look-back needs (later positions first):
+// the tiles of the FP64 kernel, or `nck` chunks of nearly equal tile counts for the FP32C kernel.
+std::vector<WorkItem> fit_items(const cox_handle *h, int f, int nck) {
+  std::vector<WorkItem> out;
+  const int64_t T = D(h).T;
+  if (h->sd->precision == COX_FP32C) {
+    const std::vector<int32_t> &lo = h->sd->prep.h_tile_lo;
+    for (int c = nck - 1; c >= 0; --c) {
+      const int ta = int(int64_t(c) * T / nck), tb = int(int64_t(c + 1) * T / nck);
+      const ChunkItem ci{f, c, ta, tb, nck, lo[size_t(tb - 1)], {0, 0}};
+      WorkItem w;
+      std::memcpy(&w, &ci, sizeof(w));
+      out.push_back(w);
+    }
+  } else {
+    for (int64_t t = T - 1; t >= 0; --t) out.push_back(work_item(h, f, int(t)));
+  }
+  return out;
+}
+
+// Several fits' lists interleaved item by item (each fit's own order kept).
+std::vector<WorkItem> interleave(const std::vector<std::vector<WorkItem>> &lists) {
+  std::vector<WorkItem> out;
+  size_t most = 0;
+  for (const auto &l : lists) most = std::max(most, l.size());
+  for (size_t k = 0; k < most; ++k)
+    for (const auto &l : lists)
+      if (k < l.size()) out.push_back(l[k]);
+  return out;
+}
+
+// Clear a fit's published look-back words (the chunked kernel's tags are 4 bits: a word left from
+// an earlier chunk layout must never read as current).
+int clear_lookback(cox_handle *h, cudaStream_t s) {
+  const int64_t T = D(h).T;
+  if (T > 0 && cudaMemsetAsync(h->hfit.tval, 0, T * 6 * sizeof(double), s) != cudaSuccess) return COX_E_CUDA;
+  return COX_OK;
+}
+
 // Allocate the per-fit state of a handle on its (shared) data.
 int alloc_fit_state(cox_handle *h) {
   const DevData &d = D(h);
@@ -150,6 +222,19 @@ int alloc_fit_state(cox_handle *h) {
   BufferSet &B = h->bufs;
   h->hfit = DevFit{};
   h->hfit.d = h->sd->d_desc;
+  {
+    const DevData &hd = h->sd->prep.desc;
+    h->hfit.tile_lo = hd.tile_lo;
+    h->hfit.tile_g = hd.tile_g;
+    h->hfit.col_tile = hd.col_tile;
+    h->hfit.head_d = hd.head_d;
+    h->hfit.col_ptr = hd.col_ptr;
+    h->hfit.idx = hd.idx;
+    h->hfit.cut_bits = hd.cut_bits;
+    h->hfit.head_bits = hd.head_bits;
+    h->hfit.val = hd.val;
+    h->hfit.T = hd.T;
+  }
   h->ctl = static_cast<FitCtl *>(B.get(sizeof(FitCtl)));
   h->lc = static_cast<LaunchCtl *>(B.get(sizeof(LaunchCtl)));
   h->dfit = static_cast<DevFit *>(B.get(sizeof(DevFit)));
@@ -165,10 +250,20 @@ int alloc_fit_state(cox_handle *h) {
   h->S0 = static_cast<double *>(B.get(std::max<int64_t>(G, 1) * sizeof(double)));
   h->S1 = static_cast<double *>(B.get(std::max<int64_t>(G, 1) * sizeof(double)));
   h->penalize = static_cast<uint8_t *>(B.get(std::max<int64_t>(p, 1)));
+  if (h->sd->precision == COX_FP32C) h->hfit.hscr = static_cast<float *>(B.get(std::max<int64_t>(G, 1) * 6 * sizeof(float)));
   if (!h->ctl || !h->lc || !h->dfit || !h->items || !h->hfit.eta || !h->hfit.v || !h->hfit.beta || !h->hfit.trust ||
-      !h->hfit.tstat || !h->hfit.tval || !h->hfit.part || !h->gout || !h->S0 || !h->S1 || !h->penalize)
+      !h->hfit.tstat || !h->hfit.tval || !h->hfit.part || !h->gout || !h->S0 || !h->S1 || !h->penalize ||
+      (h->sd->precision == COX_FP32C && !h->hfit.hscr))
     return fail(h, COX_E_OOM, "device allocation failed for the fit state");
   h->hfit.ctl = h->ctl;
+  if (h->sd->precision == COX_FP32C) {   // the tensor map of v for the chunked kernel's tile copies
+    alignas(64) unsigned char map[128];
+    void *dmap = B.get(sizeof(map));
+    if (!dmap) return fail(h, COX_E_OOM, "device allocation failed for the fit state");
+    if (chunk_encode_vmap(h->hfit.v, M + tile_k + 64, map)) return fail(h, COX_E_CUDA, "tensor map of v");
+    if (cudaMemcpy(dmap, map, sizeof(map), cudaMemcpyHostToDevice) != cudaSuccess) return cuda_fail(h, "tensor map copy");
+    h->hfit.vmap = dmap;
+  }
   if (const int RT = h->sd->prep.res_T) {
     h->r_tagg = static_cast<uint64_t *>(B.get(6 * RT * sizeof(uint64_t)));
     h->r_tpart = static_cast<uint64_t *>(B.get(12 * RT * sizeof(uint64_t)));
@@ -190,18 +285,18 @@ int alloc_fit_state(cox_handle *h) {
   *h->h_lc = LaunchCtl{};
   // zero the padded tail of v once (positions >= M are read as whole 16-byte chunks)
   if (cudaMemsetAsync(h->hfit.v, 0, (M + tile_k + 64) * sv, h->stream) != cudaSuccess) return cuda_fail(h, "memset");
-  std::vector<WorkItem> it(static_cast<size_t>(std::max<int64_t>(T, 1)));
-  for (int64_t t = 0; t < T; ++t) it[t] = work_item(h, 0, int(T - 1 - t));   // reverse order for the look-back
-  h->n_items = int(T);
-  if (cudaMemcpyAsync(h->items, it.data(), std::max<int64_t>(T, 1) * sizeof(WorkItem), cudaMemcpyHostToDevice, h->stream) !=
-      cudaSuccess)
-    return cuda_fail(h, "items copy");
-  LaunchCtl lc{0u, 0u, int32_t(T), 1, 0};
-  if (cudaMemcpyAsync(h->lc, &lc, sizeof(lc), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return cuda_fail(h, "lc copy");
   h->valued = d.val != nullptr;
   const int mg = ccd_max_grid(h->sd->precision, h->valued);
   if (mg <= 0) return cuda_fail(h, "kernel attributes");
-  h->grid = int(std::max<int64_t>(1, std::min<int64_t>(T, mg)));
+  h->nck = plan_chunks({T}, mg)[0];   // a fit alone: at most one chunk per resident CTA
+  std::vector<WorkItem> it = fit_items(h, 0, h->nck);
+  h->n_items = int(it.size());
+  if (!it.empty() &&
+      cudaMemcpyAsync(h->items, it.data(), it.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cuda_fail(h, "items copy");
+  LaunchCtl lc{0u, 0u, int32_t(h->n_items), 1, 0};
+  if (cudaMemcpyAsync(h->lc, &lc, sizeof(lc), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return cuda_fail(h, "lc copy");
+  h->grid = int(std::max<int64_t>(1, std::min<int64_t>(h->n_items, mg)));
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, "state init");
   return COX_OK;
 }
@@ -253,6 +348,7 @@ int init_state(cox_handle *h, const double *beta0) {
   if (p > 0 && cudaMemcpyAsync(h->hfit.trust, ones.data(), p * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return cuda_fail(h, "trust copy");
   if (d.T > 0 && cudaMemsetAsync(h->hfit.tstat, 0, d.T * sizeof(uint32_t), s) != cudaSuccess) return cuda_fail(h, "memset");
+  if (clear_lookback(h, s)) return cuda_fail(h, "memset");
   if (cudaMemsetAsync(&h->lc->error, 0, sizeof(int32_t), s) != cudaSuccess) return cuda_fail(h, "memset");
   FitCtl c{};
   c.j = 0;
@@ -1262,6 +1358,12 @@ int cox_debug_set_wait_limit(long long clocks) {
   return COX_OK;
 }
 
+int cox_debug_set_chunk_tiles(int32_t tiles) {
+  if (tiles < 0 || tiles > kChunkMaxTiles) return fail(nullptr, COX_E_INVALID, "cox_debug_set_chunk_tiles: 0 to 64");
+  g_chunk_tiles.store(tiles);
+  return COX_OK;
+}
+
 int cox_footprint(const cox_data *data, const cox_options *opts, size_t *bytes) {
   if (!data || !bytes) return fail(nullptr, COX_E_INVALID, "cox_footprint: null argument");
   const int precision = opts ? opts->precision : COX_FP64;
@@ -1343,15 +1445,21 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
   if (!rc && cudaMemcpyAsync(fits, hf.data(), n * sizeof(DevFit), cudaMemcpyHostToDevice, s) != cudaSuccess)
     rc = cuda_fail(nullptr, "fits copy");
   std::vector<int> running(n, 1);
+  const int slots = std::max(1, ccd_max_grid(precision, valued));
   auto rebuild_items = [&]() -> int {
-    std::vector<WorkItem> it;
-    // interleave fits tile by tile (each fit's tiles stay in reverse order)
-    int64_t maxT = 0;
+    // the running fits' chunks re-planned over the resident CTAs (their look-back words cleared:
+    // a new chunk layout), interleaved item by item (each fit's items in their look-back order)
+    std::vector<int64_t> tiles;
     for (int i = 0; i < n; ++i)
-      if (running[i]) maxT = std::max<int64_t>(maxT, D(hs[i]).T);
-    for (int64_t k = 0; k < maxT; ++k)
-      for (int i = 0; i < n; ++i)
-        if (running[i] && k < D(hs[i]).T) it.push_back(work_item(hs[i], i, int(D(hs[i]).T - 1 - k)));
+      if (running[i]) tiles.push_back(D(hs[i]).T);
+    const std::vector<int> nck = plan_chunks(tiles, slots);
+    std::vector<std::vector<WorkItem>> lists;
+    for (int i = 0, r = 0; i < n; ++i)
+      if (running[i]) {
+        if (precision == COX_FP32C && clear_lookback(hs[i], s)) return cuda_fail(nullptr, "memset");
+        lists.push_back(fit_items(hs[i], i, nck[r++]));
+      }
+    const std::vector<WorkItem> it = interleave(lists);
     int act = 0;
     for (int i = 0; i < n; ++i) act += running[i];
     LaunchCtl l{0u, 0u, int32_t(it.size()), act, 0};
@@ -1414,9 +1522,10 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
   if (!rc) {
     for (int i = 0; i < n; ++i) {
       cox_handle *h = hs[i];
-      // results back into the handle
+      // results back into the handle; its own work list has another chunk layout
       cudaMemcpyAsync(h->ctl, ctls + i, sizeof(FitCtl), cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(h->h_ctl, ctls + i, sizeof(FitCtl), cudaMemcpyDeviceToHost, s);
+      clear_lookback(h, s);
       cudaStreamSynchronize(s);
       const FitCtl &c = *h->h_ctl;
       int r = c.error ? device_error(h) : (D(h).p == 0 ? COX_OK : (c.state == kConverged ? COX_OK : COX_W_NOT_CONVERGED));
@@ -1619,19 +1728,24 @@ void prep_loop(cox_server *S) {
 }
 
 int rebuild_batch(cox_server *S) {
-  std::vector<WorkItem> it;
-  int64_t maxT = 0;
   int valued = 0, active = 0;
+  std::vector<int64_t> tiles;
   for (size_t sl = 0; sl < S->slots.size(); ++sl)
     if (Req *r = S->slots[sl]) {
-      maxT = std::max<int64_t>(maxT, D(r->h).T);
       valued |= r->h->valued;
       ++active;
+      tiles.push_back(D(r->h).T);
     }
-  for (int64_t k = 0; k < maxT; ++k)
-    for (size_t sl = 0; sl < S->slots.size(); ++sl)
-      if (Req *r = S->slots[sl])
-        if (k < D(r->h).T) it.push_back(work_item(r->h, int(sl), int(D(r->h).T - 1 - k)));
+  // the in-flight fits' chunks re-planned over the resident CTAs (a new layout: look-back words
+  // cleared on the run stream, ahead of the next replay)
+  const std::vector<int> nck = plan_chunks(tiles, std::max(1, ccd_max_grid(S->o.precision, valued)));
+  std::vector<std::vector<WorkItem>> lists;
+  for (size_t sl = 0, r = 0; sl < S->slots.size(); ++sl)
+    if (Req *q = S->slots[sl]) {
+      if (S->o.precision == COX_FP32C && clear_lookback(q->h, S->run_stream)) return COX_E_CUDA;
+      lists.push_back(fit_items(q->h, int(sl), nck[r++]));
+    }
+  const std::vector<WorkItem> it = interleave(lists);
   if (int64_t(it.size()) > S->items_cap || valued != S->graph_valued || !S->graph) {
     if (int64_t(it.size()) > S->items_cap) {
       const int64_t cap = std::max<int64_t>(int64_t(it.size()) * 2, S->items_cap * 2);

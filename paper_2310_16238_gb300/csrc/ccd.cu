@@ -489,93 +489,7 @@ __global__ void __launch_bounds__(kThreads) ccd_kernel(const DevFit *__restrict_
     __syncthreads();
 
     // ---- 6. last CTA of this fit: fixed-order reduction and the coordinate step
-    if (s_last) {
-      __threadfence();
-      double acc[3] = {0.0, 0.0, 0.0};
-      for (int u = tid; u < T_; u += kThreads) {
-        acc[0] += ld_relaxed_f64(&F.part[3 * u + 0]);
-        acc[1] += ld_relaxed_f64(&F.part[3 * u + 1]);
-        acc[2] += ld_relaxed_f64(&F.part[3 * u + 2]);
-      }
-      block_sum<3>(acc, s_red);
-      double extra[2] = {0.0, 0.0};   // beta'dX and the penalty, when the log-likelihood is due
-      if (need_ll) {
-        for (int jj = tid; jj < D->p; jj += kThreads) {
-          const double b = F.beta[jj];
-          extra[0] += b * D->dX[jj];
-          const bool pen = F.penalize ? F.penalize[jj] != 0 : true;
-          if (pen && F.penalty == COX_PEN_L1) extra[1] += F.lambda * fabs(b);
-          if (pen && F.penalty == COX_PEN_L2) extra[1] += b * b / (2.0 * F.l2_var);
-        }
-        block_sum<2>(extra, s_red);
-      }
-      if (tid == 0) {
-        const double G1 = acc[0], G2 = acc[1], LL = acc[2];
-        if (ctl->error != 0) {
-          if (mode == kModeFit && ctl->state == kRunning) atomicSub(&lc->active, 1);
-          ctl->state = kError;
-        } else if (mode == kModeShard) {
-          ctl->out_g1 = G1;
-          ctl->out_g2 = G2;
-          ctl->out_ll = LL;
-          ctl->out_bdx = extra[0];
-        } else if (mode == kModeEval) {
-          ctl->out_g1 = -D->dX[j] + G1;
-          ctl->out_g2 = G2;
-          if (F.gout) { F.gout[2 * j] = -D->dX[j] + G1; F.gout[2 * j + 1] = G2; }
-        } else if (mode == kModeLL) {
-          ctl->out_ll = extra[0] - LL - shift * D->sum_d;
-        } else {
-          bool stop = false;
-          if (need_ll) {
-            const double ll = extra[0] - LL - shift * D->sum_d;
-            const double obj = -ll + extra[1];
-            ctl->loglik = ll;
-            ctl->obj = obj;
-            if (ctl->sweep > 0 && fabs(obj - ctl->obj_prev) <= F.tol * fabs(obj)) {
-              ctl->state = kConverged;
-              stop = true;
-            } else if (ctl->sweep >= F.max_sweeps) {
-              ctl->state = kMaxed;
-              stop = true;
-            }
-            if (stop) {
-              atomicSub(&lc->active, 1);
-              ctl->pend_j = -1;   // this launch's tiles already applied the pending update
-            } else {
-              ctl->obj_prev = obj;
-            }
-          }
-          if (!stop) {
-            const double g1 = -D->dX[j] + G1, g2 = G2;
-            const int pen = F.penalize ? F.penalize[j] != 0 : 1;
-            double tr = F.trust[j];
-            const double s = ccd_step_rule(g1, g2, F.beta[j], &tr, F.penalty, F.lambda, F.l2_var, pen);
-            F.trust[j] = tr;
-            if (s != 0.0) {
-              F.beta[j] = F.beta[j] + s;
-              ctl->pend_j = j;
-              ctl->pend_db = s;
-            } else {
-              ctl->pend_j = -1;
-              ctl->pend_db = 0.0;
-            }
-            ctl->coord_updates += 1;
-            int jn = j + 1;
-            if (jn >= D->p) {
-              jn = 0;
-              ctl->sweep += 1;
-              ctl->need_ll = 1;
-            } else {
-              ctl->need_ll = 0;
-            }
-            ctl->j = jn;
-          }
-        }
-        ctl->done_tiles = 0u;
-        ctl->epoch = epoch + 1u;
-      }
-    }
+    if (s_last) finish_launch_step<kThreads>(F, lc, mode, j, need_ll, T_, epoch, s_red);
     __syncthreads();
   }
   if (tid == 0) {
@@ -639,23 +553,27 @@ static int max_grid_one() {
   return (per_sm > 0 ? per_sm : 1) * nsm;
 }
 
-// Resident CTAs of a variant (occupancy x SMs); both graph variants share the smaller figure.
+// Resident CTAs of a variant on the current device (occupancy x SMs); both graph variants share
+// the smaller figure.
 template <class P, int NV>
 static int max_grid_impl() {
-  static int cached = 0;
-  if (cached) return cached;
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  if (cached[dev]) return cached[dev];
   const int a = max_grid_one<P, NV, false>(), b = max_grid_one<P, NV, true>();
   if (a < 0 || b < 0) return -1;
-  cached = a < b ? a : b;
-  return cached;
+  cached[dev] = a < b ? a : b;
+  return cached[dev];
 }
 
+// FP32C runs the chunked kernel (ccd_chunk.cu); this kernel serves FP64.
 int ccd_max_grid(int precision, int valued) {
-  if (precision == COX_FP32C) return valued ? max_grid_impl<PF32C, 3>() : max_grid_impl<PF32C, 2>();
+  if (precision == COX_FP32C) return chunk_max_grid(valued);
   return valued ? max_grid_impl<PF64, 3>() : max_grid_impl<PF64, 2>();
 }
 
-int ccd_tile(int precision) { return precision == COX_FP32C ? kThreads * PF32C::ITEMS : kThreads * PF64::ITEMS; }
+int ccd_tile(int precision) { return precision == COX_FP32C ? kChunkTile : kThreads * PF64::ITEMS; }
 
 template <class P, int NV>
 static int launch_impl(const DevFit *fits, const WorkItem *items, LaunchCtl *lc, int grid, int mode, int j_eval,
@@ -677,13 +595,10 @@ int launch_ccd(int precision, const DevFit *fits, const WorkItem *items, LaunchC
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs == cudaStreamCaptureStatusNone) count_launches(1);   // graph nodes are counted per replay
-  int rc;
   if (precision == COX_FP32C)
-    rc = valued ? launch_impl<PF32C, 3>(fits, items, lc, grid, mode, j_eval, s, cond)
-                : launch_impl<PF32C, 2>(fits, items, lc, grid, mode, j_eval, s, cond);
-  else
-    rc = valued ? launch_impl<PF64, 3>(fits, items, lc, grid, mode, j_eval, s, cond)
-                : launch_impl<PF64, 2>(fits, items, lc, grid, mode, j_eval, s, cond);
+    return launch_chunk(fits, reinterpret_cast<const ChunkItem *>(items), lc, grid, mode, j_eval, valued, stream, cond);
+  const int rc = valued ? launch_impl<PF64, 3>(fits, items, lc, grid, mode, j_eval, s, cond)
+                        : launch_impl<PF64, 2>(fits, items, lc, grid, mode, j_eval, s, cond);
   if (rc) return rc;
   return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
 }

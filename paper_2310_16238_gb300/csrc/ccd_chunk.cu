@@ -1,0 +1,846 @@
+// FP32C coordinate-step kernel for cyclic coordinate descent on the stratified / time-varying
+// Cox partial likelihood (arXiv 2310.16238, §2.4-§2.7): one launch advances every fit in its work
+// list by one coordinate.
+//
+// A fit's risk sequence is cut into tiles of up to 4,096 positions and its tiles into contiguous
+// chunks; a work item is one chunk. One CTA of 128 threads streams the chunk's tiles right to left,
+// the direction of the suffix sums, staging the next tile with cp.async while it scans the current:
+//   * at the chunk's start, the previous coordinate's pending update at the chunk's entries of that
+//     column (eta += x dbeta, eq. parallel_xb; v = +-exp(eta - shift), eq. parallel_d);
+//   * per tile, each thread owns 32 consecutive positions. The stratum-segmented suffix sums of v
+//     (strata are segments of §2.6's flag-value operator) are plain float sums inside blocks of 8
+//     positions and compensated (TwoSum) sums above them; the column's x v and x^2 v sums come
+//     from a walk over the thread's nonzeros only. Warp-shuffle segmented scans and a combine over
+//     the 4 warps give each thread its carry from the chunk's later positions, and the tile's tie
+//     groups then read their risk-set sums head-parallel and add the ratios of eqs.
+//     (parallel_g)/(parallel_h) to the chunk's partial;
+//   * tie groups whose risk set runs past the chunk's end keep their local sums in a per-group
+//     scratch until the chunk's carry arrives: one decoupled look-back per chunk over epoch-tagged
+//     64-bit words (each word carries its own tag in its low mantissa bits, so publishing needs no
+//     memory fence and a reader needs no second load);
+//   * the CTA that finishes a fit's last chunk reduces the chunk partials in a fixed order and
+//     takes the coordinate step (§2.4).
+// A tile's sums are thus written to shared memory once and read at its tie groups only; the only
+// global writes are the pending update's eta and v, the deferred groups' scratch and the partials.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <climits>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "ccd_common.cuh"
+#include "cox.h"
+#include "cox_internal.h"
+
+namespace coxgb {
+namespace {
+
+constexpr int kCT = 128;        // threads per CTA
+constexpr int kCI = 32;         // positions per thread
+constexpr int kCW = kCT / 32;   // warps per CTA
+constexpr int kPF = 2;          // events-per-group values each thread prefetches for its first groups
+#ifndef COXGB_CHUNK_MIN_CTAS
+#define COXGB_CHUNK_MIN_CTAS 4  // resident CTAs per SM the register allocation is held to
+#endif
+static_assert(kCT * kCI == kChunkTile, "a tile is one position range per thread");
+
+using P = PF32C;
+using Acc = P::Acc;
+
+#if COX_TRACE_ON
+// Phase stamps (ns) of one traced launch: [work item][8] (diagnostic builds only).
+__device__ uint64_t *g_chunk_trace = nullptr;
+#define CHUNK_STAMP(k)                                                              \
+  do {                                                                              \
+    if (g_chunk_trace && tid == 0) {                                                \
+      uint64_t t_;                                                                  \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                        \
+      g_chunk_trace[8 * int64_t(w) + (k)] = t_;                                     \
+    }                                                                               \
+  } while (0)
+#else
+#define CHUNK_STAMP(k) \
+  do {                 \
+  } while (0)
+#endif
+
+template <int NV>
+struct ChunkSmem {
+  float v[2][kChunkTile];                                  // staged tiles (16-byte chunks swizzled);
+                                                           // the current tile's S0 partials overwrite it
+  float xs[NV == 3 ? 2 : 1][NV == 3 ? kChunkTile : 4];     // column values at the tile's nonzeros
+  float s1h[NV - 1][kHeadCap];                             // tie groups' thread-local S1 (and S2) sums
+  uint32_t cw[2][kCT], hw[2][kCT];                         // stratum-end and tie-group bits per thread
+  uint32_t nzw[3][kCT];                                    // column-j bits per thread, by tile mod 3
+  int32_t tlo[kChunkMaxTiles + 1], tg[kChunkMaxTiles + 1]; // the chunk's tile positions and first groups
+  int32_t ctj[kChunkMaxTiles + 1], ctp[kChunkMaxTiles + 1];// column j's / the pending column's first entries
+  uint16_t hpos[kHeadCap];                                 // the tile's tie-group positions
+  Acc bs[4][kCT];                                          // S0 suffix of a thread's blocks right of block b
+  Acc E[NV][kCT];                                          // each thread's carry from the chunk's later positions
+  uint8_t Eo[kCT], zf[kCT];                                // that carry runs to the chunk's end / thread has nonzeros
+  Acc wa[NV][kCW];                                         // warp sums from the warp's first position
+  int32_t wf[kCW];                                         // warp holds a stratum end
+  Acc cc[2][NV];                                           // the chunk carry into the current tile
+  int32_t ccf[2];                                          // that carry stopped at a stratum end
+  int32_t hopen, last;
+  uint64_t mbar[2];                                        // tile copy completion, per buffer
+  double red[3][kCW];
+  double scratch[3 * 32];
+  double cr[NV];
+};
+
+// position e of a staged tile -> its float slot (16-byte chunks XOR-swizzled within 128-byte rows,
+// so a thread's eight 16-byte reads of its own 128 bytes hit distinct banks)
+__device__ __forceinline__ int swz(int e) {
+  const int c = e >> 2;
+  return ((c ^ ((c >> 3) & 7)) << 2) | (e & 3);
+}
+
+// a double with a 4-bit tag in its lowest mantissa bits (a relative change below 2^-48)
+__device__ __forceinline__ uint64_t tag_word(double v, uint32_t tg) {
+  return (static_cast<uint64_t>(__double_as_longlong(v)) & ~uint64_t(15)) | uint64_t(tg);
+}
+__device__ __forceinline__ double word_value(uint64_t w) {
+  return __longlong_as_double(static_cast<long long>(w & ~uint64_t(15)));
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---- tile copies: one bulk tensor copy (TMA) per tile, completion counted on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// rows [y, y + 128) of the 32-float-wide view of v into dst (1024-byte aligned), 128-byte swizzle
+__device__ __forceinline__ void tma_load_rows(void *dst, const void *map, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(0), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// generic-proxy accesses before async-proxy (TMA) accesses of the same memory
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// a tile copy that has not landed within this many SM clocks (about 2 s) is an error
+constexpr long long kTmaWait = 1ll << 32;
+
+// One tie group's terms of eqs. (parallel_g)/(parallel_h) (and d log S0 when the log-likelihood
+// is due) from its risk-set sums sh = (S0, S1[, S2]).
+template <int NV>
+__device__ __forceinline__ void add_group(const Acc (&sh)[NV], int dgi, int j, bool need_ll, Acc &g1q, Acc &g2q,
+                                          double &llq, const DevFit &F, int gidx) {
+  const float S0 = sh[0].s + sh[0].c, S1 = sh[1].s + sh[1].c;
+  const float fd = float(dgi);
+  if (j >= 0) {
+    const float inv = __frcp_rn(S0);
+    const float r = __fdiv_rn(S1, S0);
+    P::add(g1q, fd * r);
+    if constexpr (NV == 3) P::add(g2q, fd * ((sh[2].s + sh[2].c) * inv - r * r));
+    else P::add(g2q, fd * (r * (1.0f - r)));
+  }
+  if (need_ll) llq += double(dgi) * log(P::to64(sh[0]));
+  if (F.out_S0) {
+    F.out_S0[gidx] = P::to64(sh[0]);
+    F.out_S1[gidx] = P::to64(sh[1]);
+  }
+}
+
+template <int NV, bool kCond>
+__global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const DevFit *__restrict__ fits, const ChunkItem *__restrict__ items,
+                                                    LaunchCtl *lc, int mode, int j_eval, unsigned long long cond,
+                                                    long long spin) {
+  constexpr bool VAL = NV == 3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // the tile buffers start on a 1024-byte boundary (the period of the copies' 128-byte swizzle)
+  ChunkSmem<NV> &S = *reinterpret_cast<ChunkSmem<NV> *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&S.mbar[0], 1);
+    mbar_init(&S.mbar[1], 1);
+    mbar_init_fence();
+  }
+  uint32_t ph = 0;   // bit b: the phase of buffer b's barrier that the next wait expects
+  bool tma_late = false;
+  const int n_items = lc->n_items;
+  ChunkItem it = blockIdx.x < n_items ? items[blockIdx.x] : ChunkItem{};   // issued before the check below
+  // nothing to do once every fit stopped, or after a launch of this work list gave up a wait
+  const int active = __syncthreads_or(
+      tid == 0 && *reinterpret_cast<volatile int32_t *>(&lc->error) == 0 &&
+      (mode != kModeFit || *reinterpret_cast<volatile int32_t *>(&lc->active) > 0));
+
+  for (int w = blockIdx.x; active && w < n_items; w += gridDim.x) {
+    CHUNK_STAMP(0);
+    if (w != int(blockIdx.x)) it = items[w];
+    const DevFit &F = fits[it.f];
+    FitCtl *ctl = F.ctl;
+    const int c = it.c, ta = it.ta, tb = it.tb, nc = it.nc, nt = tb - ta;
+    const float *vg = static_cast<const float *>(F.v);   // the patch below reads v directly
+    auto stage = [&](int t, int lo) {   // tile t's values (one tensor copy) and bits, asynchronously
+      const int b = t & 1;
+      if (tid == 0) {
+        mbar_expect_tx(&S.mbar[b], uint32_t(kChunkTile * sizeof(float)));
+        tma_load_rows(&S.v[b][0], F.vmap, lo >> 5, &S.mbar[b]);
+      }
+      cp_async4(&S.cw[b][tid], F.cut_bits + (lo >> 5) + tid);
+      cp_async4(&S.hw[b][tid], F.head_bits + (lo >> 5) + tid);
+      cp_async_commit();
+    };
+    if (__syncthreads_or(tid == 0 && mode == kModeFit && ctl->state != kRunning)) continue;
+    stage(tb - 1, it.lo_last);   // the chunk's last tile, before its tables arrive
+    const int T_ = F.T;
+    const int j = (mode == kModeEval || mode == kModeShard) ? j_eval : (mode == kModeFit ? ctl->j : -1);
+    const bool need_ll = mode == kModeLL || ((mode == kModeFit || mode == kModeShard) && ctl->need_ll);
+    const int pend_j = mode == kModeFit ? ctl->pend_j : -1;
+    const double pend_db = ctl->pend_db;
+    const uint32_t epoch = ctl->epoch;
+    const uint32_t etag = epoch % 15u + 1u;   // never 0: zeroed words are never current
+    const double shift = F.shift;
+    const bool vf = VAL && F.val != nullptr;   // binary fits in a valued launch use x = 1
+
+    // ---- the chunk's tables
+    for (int q = tid; q <= nt; q += kCT) {
+      S.tlo[q] = F.tile_lo[ta + q];
+      S.tg[q] = F.tile_g[ta + q];
+      S.ctj[q] = j >= 0 ? F.col_tile[int64_t(j) * (T_ + 1) + ta + q] : 0;
+      S.ctp[q] = pend_j >= 0 ? F.col_tile[int64_t(pend_j) * (T_ + 1) + ta + q] : 0;
+    }
+    for (int q = tid; q < 3 * kCT; q += kCT) S.nzw[q / kCT][q % kCT] = 0u;
+    if (tid == 0) {
+      for (int i = 0; i < NV; ++i) S.cc[0][i] = P::zero();
+      S.ccf[0] = 0;
+      S.hopen = INT_MAX;
+    }
+    __syncthreads();
+
+    auto scatter = [&](int t) {   // column j's entries of tile t -> per-thread bits (and values)
+      if (j < 0) return;
+      const int tq = t - ta, lo = S.tlo[tq];
+      const int64_t cb = F.col_ptr[j];
+      for (int64_t q = cb + S.ctj[tq] + tid; q < cb + S.ctj[tq + 1]; q += kCT) {
+        const int e = int(F.idx[q] & kPosMask) - lo;
+        atomicOr(&S.nzw[t % 3][e >> 5], 1u << (e & 31));
+        if constexpr (VAL) {
+          if (vf) S.xs[t & 1][e] = float(F.val[q]);
+        }
+      }
+    };
+
+    // ---- the pending update at the chunk's entries of column pend_j (global eta and v); the new
+    //      values at the last tile's positions (staged before the update) are kept for its patch
+    constexpr int kKeep = 4;
+    int np = 0, keep_pos[kKeep];
+    float keep_v[kKeep];
+    bool overflow = false;
+    if (pend_j >= 0) {
+      const int64_t cb = F.col_ptr[pend_j];
+      const int lo_l = S.tlo[nt - 1], hi_l = S.tlo[nt];
+      for (int64_t q = cb + S.ctp[0] + tid; q < cb + S.ctp[nt]; q += kCT) {
+        const uint32_t e = F.idx[q];
+        const int64_t pos = e & kPosMask;
+        const double x = F.val ? F.val[q] : 1.0;
+        const double et = __dadd_rn(F.eta[pos], __dmul_rn(x, pend_db));
+        F.eta[pos] = et;
+        const float nv = make_v<P>(et, shift, (e & kExitBit) != 0, &ctl->error);
+        static_cast<float *>(F.v)[pos] = nv;
+        if (pos >= lo_l && pos < hi_l) {
+          if (np < kKeep) {
+#pragma unroll
+            for (int u = 0; u < kKeep; ++u)
+              if (u == np) { keep_pos[u] = int(pos - lo_l); keep_v[u] = nv; }
+            ++np;
+          } else {
+            overflow = true;
+          }
+        }
+      }
+      // the chunk's earlier tiles are read by tensor copies (the async proxy, through L2): the new
+      // values must be there, and ordered before those copies, by the barrier that precedes them
+      __threadfence();
+      fence_proxy_async_global();
+    }
+    scatter(tb - 1);
+    CHUNK_STAMP(1);
+
+    int slot = 0;
+    Acc g1q = P::zero(), g2q = P::zero();
+    double llq = 0.0;
+    for (int t = tb - 1; t >= ta; --t) {
+      const int b = t & 1, tq = t - ta;
+      const int lo = S.tlo[tq], hi = S.tlo[tq + 1], ga = S.tg[tq], gb = S.tg[tq + 1];
+      {   // tile t's copy landed (bounded wait), its bits too
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&S.mbar[b], (ph >> b) & 1u))
+          if (clock64() - t0 > kTmaWait) {
+            tma_late = true;
+            break;
+          }
+        ph ^= 1u << b;
+      }
+      cp_async_wait_all();
+      __syncthreads();   // tile t staged, its bits scattered; tile t+1 finished
+      if (t == tb - 1) CHUNK_STAMP(2);
+      if (t == tb - 1 && pend_j >= 0) {
+        // the tile was staged before the pending update: put in the updated values (from registers;
+        // from global memory where a thread had more of them than it kept)
+        if (__syncthreads_or(overflow)) {
+          const int64_t cb = F.col_ptr[pend_j];
+          for (int64_t q = cb + S.ctp[tq] + tid; q < cb + S.ctp[tq + 1]; q += kCT) {
+            const int64_t pos = F.idx[q] & kPosMask;
+            S.v[b][swz(int(pos - lo))] = vg[pos];
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < kKeep; ++u)
+            if (u < np) S.v[b][swz(keep_pos[u])] = keep_v[u];
+        }
+        __syncthreads();
+      }
+      if (t - 1 >= ta) stage(t - 1, S.tlo[tq - 1]);
+      S.nzw[(t + 1) % 3][tid] = 0u;   // tile t+1's bits are no longer read
+      if (t - 1 >= ta) scatter(t - 1);
+      const int nh = gb - ga;
+      int dpre[kPF];
+#pragma unroll
+      for (int u = 0; u < kPF; ++u) dpre[u] = tid + u * kCT < nh ? F.head_d[ga + tid + u * kCT] : 0;
+
+      const bool act = tid * kCI < hi - lo;   // positions past the tile's end belong to the next tile
+      const uint32_t cm = act ? S.cw[b][tid] : 0u, hm = act ? S.hw[b][tid] : 0u;
+      const uint32_t zm = S.nzw[t % 3][tid];
+      // this thread's first tie group within the tile: earlier lanes, then earlier warps
+      const int hc = __popc(hm);
+      int hinc = hc;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, hinc, off);
+        if (lane >= off) hinc += y;
+      }
+      int wpre = 0;
+      for (int q = lane; q < warp * 32; q += 32) wpre += q * kCI < hi - lo ? __popc(S.hw[b][q]) : 0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) wpre += __shfl_xor_sync(0xffffffffu, wpre, off);
+      const int hbase = wpre + hinc - hc;
+
+      // ---- S1 (S2) over the thread's nonzeros, right to left (reads v before it is overwritten)
+      float a1 = 0.f, a2 = 0.f;
+      if (zm) {
+        float r1 = 0.f, r2 = 0.f;
+        int rank = hc;
+        for (uint32_t m = zm | hm | cm; m;) {
+          const int k = 31 - __clz(m);
+          m &= ~(1u << k);
+          if ((cm >> k) & 1u) { r1 = 0.f; r2 = 0.f; }   // k ends its stratum: later positions are another
+          if ((zm >> k) & 1u) {
+            const float vv = S.v[b][swz(tid * kCI + k)];
+            if constexpr (VAL) {
+              const float x = vf ? S.xs[t & 1][tid * kCI + k] : 1.0f;
+              const float xv = x * vv;
+              r1 += xv;
+              r2 += x * xv;
+            } else {
+              r1 += vv;
+            }
+          }
+          if ((hm >> k) & 1u) {
+            --rank;
+            S.s1h[0][hbase + rank] = r1;
+            if constexpr (VAL) S.s1h[1][hbase + rank] = r2;
+          }
+        }
+        a1 = r1;
+        a2 = r2;
+      }
+      S.zf[tid] = zm != 0u;
+
+      // ---- S0: plain sums within blocks of 8, compensated above; partials replace v in place
+      float x[kCI];
+#pragma unroll
+      for (int q = 0; q < kCI / 4; ++q) {
+        const int ch = tid * (kCI / 4) + q;
+        const float4 f = *reinterpret_cast<const float4 *>(&S.v[b][(ch ^ ((ch >> 3) & 7)) * 4]);
+        x[4 * q] = act ? f.x : 0.f;
+        x[4 * q + 1] = act ? f.y : 0.f;
+        x[4 * q + 2] = act ? f.z : 0.f;
+        x[4 * q + 3] = act ? f.w : 0.f;
+      }
+      Acc run = P::zero();
+      int rf = 0;
+      const bool nocut = __all_sync(0xffffffffu, cm == 0u);
+#pragma unroll
+      for (int bl = 3; bl >= 0; --bl) {
+        S.bs[bl][tid] = run;
+        float p = 0.f, pr[8];
+        if (nocut) {
+#pragma unroll
+          for (int i = 7; i >= 0; --i) {
+            p += x[8 * bl + i];
+            pr[i] = p;
+          }
+        } else {
+#pragma unroll
+          for (int i = 7; i >= 0; --i) {
+            if ((cm >> (8 * bl + i)) & 1u) p = 0.f;
+            p += x[8 * bl + i];
+            pr[i] = p;
+          }
+        }
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+          const int ch = tid * (kCI / 4) + 2 * bl + hq;
+          *reinterpret_cast<float4 *>(&S.v[b][(ch ^ ((ch >> 3) & 7)) * 4]) =
+              make_float4(pr[4 * hq], pr[4 * hq + 1], pr[4 * hq + 2], pr[4 * hq + 3]);
+        }
+        const bool bc = ((cm >> (8 * bl)) & 0xffu) != 0u;
+        run = bc ? Acc{p, 0.f} : P::comb(Acc{p, 0.f}, run);
+        rf |= int(bc);
+      }
+
+      // ---- warp segmented suffix scan of the thread sums (from each thread's first position)
+      Acc I[NV];
+      I[0] = run;
+      I[1] = Acc{a1, 0.f};
+      if constexpr (VAL) I[2] = Acc{a2, 0.f};
+      int If = rf;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        Acc y[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) y[i] = P::shfl_down(I[i], off);
+        const int yf = __shfl_down_sync(0xffffffffu, If, off);
+        if (lane + off < 32) {
+          if (!If) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) I[i] = P::comb(I[i], y[i]);
+          }
+          If |= yf;
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) S.wa[i][warp] = I[i];
+        S.wf[warp] = If;
+      }
+      {   // the tile's tie-group positions, in order
+        int hq = hbase;
+        for (uint32_t m = hm; m; m &= m - 1u) S.hpos[hq++] = uint16_t(tid * kCI + __ffs(m) - 1);
+      }
+      __syncthreads();
+
+      // ---- each thread's carry from the chunk's later positions (known part) and the tile total
+      Acc CC[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) CC[i] = S.cc[slot][i];
+      const int CCf = S.ccf[slot];
+      Acc Cw[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) Cw[i] = CC[i];
+      int Cwo = !CCf;
+      for (int q = kCW - 1; q > warp; --q) {
+        if (S.wf[q]) {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) Cw[i] = S.wa[i][q];
+          Cwo = 0;
+        } else {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) Cw[i] = P::comb(S.wa[i][q], Cw[i]);
+        }
+      }
+      Acc E[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) E[i] = P::shfl_down(I[i], 1);
+      const int Ef = __shfl_down_sync(0xffffffffu, If, 1);
+      int Eo;
+      if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) E[i] = Cw[i];
+        Eo = Cwo;
+      } else if (Ef) {
+        Eo = 0;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) E[i] = P::comb(E[i], Cw[i]);
+        Eo = Cwo;
+      }
+#pragma unroll
+      for (int i = 0; i < NV; ++i) S.E[i][tid] = E[i];
+      S.Eo[tid] = uint8_t(Eo);
+      if (tid == 0) {
+        Acc TI[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) TI[i] = P::zero();
+        int TF = 0;
+        for (int q = kCW - 1; q >= 0; --q) {
+          if (S.wf[q]) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) TI[i] = S.wa[i][q];
+            TF = 1;
+          } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) TI[i] = P::comb(S.wa[i][q], TI[i]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) S.cc[slot ^ 1][i] = TF ? TI[i] : P::comb(TI[i], CC[i]);
+        S.ccf[slot ^ 1] = TF | CCf;
+      }
+      __syncthreads();
+
+      // ---- the tile's tie groups (head-parallel)
+      int myopen = INT_MAX;
+      for (int u = 0, h = tid; h < nh; ++u, h += kCT) {
+        const int pos = S.hpos[h], o = pos >> 5, k = pos & 31, bl = k >> 3;
+        const uint32_t m = S.cw[b][o];
+        const uint32_t toend = 0xffffffffu << k;
+        const uint32_t upto = bl == 3 ? toend : (toend & ((1u << (8 * bl + 8)) - 1u));
+        Acc sh[NV];
+        sh[0] = Acc{S.v[b][swz(pos)], 0.f};
+        const bool z = S.zf[o] != 0;
+        sh[1] = Acc{z ? S.s1h[0][h] : 0.f, 0.f};
+        if constexpr (VAL) sh[2] = Acc{z ? S.s1h[1][h] : 0.f, 0.f};
+        int open = 0;
+        if ((m & upto) == 0u) sh[0] = P::comb(sh[0], S.bs[bl][o]);
+        if ((m & toend) == 0u) {   // the risk set runs past the thread's positions
+#pragma unroll
+          for (int i = 0; i < NV; ++i) sh[i] = P::comb(sh[i], S.E[i][o]);
+          open = S.Eo[o];
+        }
+        const int gidx = ga + h;
+        const int dgi = u == 0 ? dpre[0] : (u == 1 ? dpre[1] : F.head_d[gidx]);
+        if (open) {   // wait for the chunk's carry
+          float2 *hs = reinterpret_cast<float2 *>(F.hscr) + 3 * int64_t(gidx);
+#pragma unroll
+          for (int i = 0; i < NV; ++i) hs[i] = make_float2(sh[i].s, sh[i].c);
+          myopen = min(myopen, gidx);
+        } else {
+          add_group<NV>(sh, dgi, j, need_ll, g1q, g2q, llq, F, gidx);
+        }
+      }
+      if (myopen != INT_MAX) atomicMin(&S.hopen, myopen);
+      fence_proxy_async_smem();   // this tile's buffer is rewritten by a later copy
+      slot ^= 1;
+    }
+    __syncthreads();
+
+    CHUNK_STAMP(3);
+    // ---- publish the chunk's sums; look back for its carry
+    const int hopen = S.hopen;
+    const int gac = S.tg[0], gbc = S.tg[nt];
+    const int q0 = min(max(hopen, gac), gbc);   // deferred groups: [q0, gbc) (hopen is INT_MAX when none)
+    // each thread's first deferred group, loaded while warp 0 looks back
+    float2 pre_hs[NV];
+    int pre_d = 0;
+    if (q0 + tid < gbc) {
+      const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q0 + tid);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) pre_hs[i] = hs[i];
+      pre_d = F.head_d[q0 + tid];
+    }
+    uint64_t *cwd = reinterpret_cast<uint64_t *>(F.tval);   // per chunk: aggregate words 0..2, inclusive 3..5
+    if (warp == 0) {
+      double agg[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) agg[i] = P::to64(S.cc[slot][i]);
+      const int AF = S.ccf[slot];   // a stratum ends in the chunk: its sums from the first position are final
+      if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + (AF ? 3 : 0) + i], tag_word(agg[i], etag));
+      double cr[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) cr[i] = 0.0;
+      const bool need_lb = c + 1 < nc && (hopen < gbc || !AF);
+      if (need_lb) {
+        int base = c + 1;
+        const long long t0 = clock64();
+        bool timed_out = false;
+        for (;;) {
+          const int u = base + lane;
+          double val[NV];
+          int vi = 0, va = 0;
+          for (;;) {
+            vi = 0;
+            va = 0;
+            if (u < nc) {
+              uint64_t wv[NV];
+              bool ok = true;
+#pragma unroll
+              for (int i = 0; i < NV; ++i) {
+                wv[i] = ld_relaxed_u64(&cwd[6 * u + 3 + i]);
+                ok = ok && (wv[i] & 15u) == etag;
+              }
+              if (!ok) {
+                ok = true;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                  wv[i] = ld_relaxed_u64(&cwd[6 * u + i]);
+                  ok = ok && (wv[i] & 15u) == etag;
+                }
+                va = ok;
+              } else {
+                vi = 1;
+              }
+#pragma unroll
+              for (int i = 0; i < NV; ++i) val[i] = word_value(wv[i]);
+            } else {   // past the fit's last chunk
+              vi = 1;
+#pragma unroll
+              for (int i = 0; i < NV; ++i) val[i] = 0.0;
+            }
+            const uint32_t inv = __ballot_sync(0xffffffffu, !(vi || va));
+            const uint32_t inc = __ballot_sync(0xffffffffu, vi);
+            if (inv == 0u || (inc != 0u && __ffs(inc) < __ffs(inv))) break;
+            if (clock64() - t0 > spin) {
+              timed_out = true;
+              break;
+            }
+            __nanosleep(32);
+          }
+          if (timed_out) {
+            if (lane == 0) {
+              atomicExch(&ctl->error, COX_E_TIMEOUT);
+              atomicExch(&lc->error, COX_E_TIMEOUT);
+            }
+            break;
+          }
+          const uint32_t inc = __ballot_sync(0xffffffffu, vi);
+          const int stop = inc ? __ffs(inc) - 1 : 31;
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            double xv = lane <= stop ? val[i] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) xv += __shfl_down_sync(0xffffffffu, xv, off);
+            cr[i] += __shfl_sync(0xffffffffu, xv, 0);
+          }
+          if (inc) break;
+          base += 32;
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) S.cr[i] = cr[i];
+        if (!AF && (need_lb || c + 1 == nc))
+#pragma unroll
+          for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + 3 + i], tag_word(agg[i] + cr[i], etag));
+      }
+    }
+    __syncthreads();
+
+    CHUNK_STAMP(4);
+    // ---- the deferred tie groups: a contiguous run of the chunk's last groups
+    {
+      Acc CR[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) CR[i] = P::from64(S.cr[i]);
+      if (q0 + tid < gbc) {
+        Acc sh[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[i] = P::comb(Acc{pre_hs[i].x, pre_hs[i].y}, CR[i]);
+        add_group<NV>(sh, pre_d, j, need_ll, g1q, g2q, llq, F, q0 + tid);
+      }
+      for (int q = q0 + tid + kCT; q < gbc; q += kCT) {
+        const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q);
+        Acc sh[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          const float2 f2 = hs[i];
+          sh[i] = P::comb(Acc{f2.x, f2.y}, CR[i]);
+        }
+        add_group<NV>(sh, F.head_d[q], j, need_ll, g1q, g2q, llq, F, q);
+      }
+    }
+
+    // ---- the chunk's partial, then the step by the CTA that finishes the fit's last chunk
+    double r[3] = {P::to64(g1q), P::to64(g2q), llq};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) r[i] += __shfl_down_sync(0xffffffffu, r[i], off);
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) S.red[i][warp] = r[i];
+    __syncthreads();
+    if (tid == 0) {
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+      for (int q = 0; q < kCW; ++q) { p0 += S.red[0][q]; p1 += S.red[1][q]; p2 += S.red[2][q]; }
+      F.part[3 * c + 0] = p0;
+      F.part[3 * c + 1] = p1;
+      F.part[3 * c + 2] = p2;
+      // release: the partials before the count; acquire for the CTA that finds itself last
+      uint32_t prev;
+      asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->done_tiles) : "memory");
+      S.last = prev == uint32_t(nc - 1);
+    }
+    __syncthreads();
+    CHUNK_STAMP(5);
+    if (S.last) finish_launch_step<kCT>(F, lc, mode, j, need_ll, nc, epoch, S.scratch);
+    __syncthreads();
+    CHUNK_STAMP(6);
+  }
+  cp_async_wait_all();
+  if (tma_late) {   // a copy that missed its bound: flag it, then give it one more bound before exit
+    if (tid == 0) {
+      atomicExch(&lc->error, COX_E_TIMEOUT);
+      for (int b = 0; b < 2; ++b) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&S.mbar[b], (ph >> b) & 1u) && clock64() - t0 < kTmaWait) {
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (kCond) {   // the last CTA of the launch ends the graph's loop when nothing is left
+    if (tid == 0) {
+      __threadfence();
+      if (atomicAdd(&lc->exited, 1u) == gridDim.x - 1) {
+        lc->exited = 0u;
+        if (mode == kModeFit && cond) {
+          const long long left = --lc->budget;
+          if (*reinterpret_cast<volatile int32_t *>(&lc->active) <= 0 || left <= 0 ||
+              *reinterpret_cast<volatile int32_t *>(&lc->error) != 0)
+            cudaGraphSetConditional(cond, 0u);
+        }
+      }
+    }
+  }
+}
+
+template <int NV, bool kCond>
+int occupancy_one() {
+  const int sm = int(sizeof(ChunkSmem<NV>)) + 1024;
+  if (cudaFuncSetAttribute(chunk_kernel<NV, kCond>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+    return -1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chunk_kernel<NV, kCond>, kCT, sm) != cudaSuccess) return -1;
+  return per_sm > 0 ? per_sm : 1;
+}
+
+// Resident CTAs of a variant on the current device (both graph variants share the smaller figure).
+template <int NV>
+int max_grid_nv() {
+  static int cached[64] = {0};
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  if (cached[dev]) return cached[dev];
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  const int a = occupancy_one<NV, false>(), b = occupancy_one<NV, true>();
+  if (a < 0 || b < 0) return -1;
+  cached[dev] = (a < b ? a : b) * nsm;
+  return cached[dev];
+}
+
+template <int NV>
+int launch_nv(const DevFit *fits, const ChunkItem *items, LaunchCtl *lc, int grid, int mode, int j_eval, cudaStream_t s,
+              unsigned long long cond) {
+  if (max_grid_nv<NV>() < 0) return COX_E_CUDA;
+  const long long spin = wait_limit();
+  const size_t sm = sizeof(ChunkSmem<NV>) + 1024;
+  if (cond) chunk_kernel<NV, true><<<grid, kCT, sm, s>>>(fits, items, lc, mode, j_eval, cond, spin);
+  else chunk_kernel<NV, false><<<grid, kCT, sm, s>>>(fits, items, lc, mode, j_eval, 0ull, spin);
+  return COX_OK;
+}
+
+}  // namespace
+
+int chunk_max_grid(int valued) { return valued ? max_grid_nv<3>() : max_grid_nv<2>(); }
+
+int chunk_encode_vmap(void *v, int64_t n_floats, void *out) {
+  // the driver's encoder, fetched through the runtime (no link-time dependency on libcuda)
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  if (!enc || !v || n_floats < 32 * 128 || (reinterpret_cast<uintptr_t>(v) & 15u)) return COX_E_CUDA;
+  const cuuint64_t dims[2] = {32, cuuint64_t(n_floats / 32)};
+  const cuuint64_t strides[1] = {32 * sizeof(float)};
+  const cuuint32_t box[2] = {32, kChunkTile / 32};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(static_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, v, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? COX_OK : COX_E_CUDA;
+}
+
+int launch_chunk(const DevFit *fits, const ChunkItem *items, LaunchCtl *lc, int grid, int mode, int j_eval, int valued,
+                 void *stream, unsigned long long cond) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+#if COX_TRACE_ON
+  // COXGB_CHUNK_TRACE=<k>: stamp the phases of the k-th launch made outside a graph capture and
+  // print, per phase, the mean and largest time over the launch's work items
+  static long long seen = 0;
+  static const long long want = std::getenv("COXGB_CHUNK_TRACE") ? std::atoll(std::getenv("COXGB_CHUNK_TRACE")) : -1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  uint64_t *tr = nullptr;
+  const int kMaxItems = 1 << 16;
+  if (cs == cudaStreamCaptureStatusNone && want >= 0 && seen++ == want) {
+    cudaMalloc(&tr, size_t(kMaxItems) * 8 * sizeof(uint64_t));
+    cudaMemset(tr, 0, size_t(kMaxItems) * 8 * sizeof(uint64_t));
+    cudaMemcpyToSymbol(g_chunk_trace, &tr, sizeof(tr));
+  }
+#endif
+  const int rc = valued ? launch_nv<3>(fits, items, lc, grid, mode, j_eval, s, cond)
+                        : launch_nv<2>(fits, items, lc, grid, mode, j_eval, s, cond);
+#if COX_TRACE_ON
+  if (tr) {
+    cudaStreamSynchronize(s);
+    std::vector<uint64_t> h(size_t(kMaxItems) * 8);
+    cudaMemcpy(h.data(), tr, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    uint64_t *null = nullptr;
+    cudaMemcpyToSymbol(g_chunk_trace, &null, sizeof(null));
+    cudaFree(tr);
+    double sum[6] = {0}, mx[6] = {0};
+    uint64_t t0 = ~0ull, t1 = 0;
+    int n = 0;
+    for (int i = 0; i < kMaxItems; ++i) {
+      const uint64_t *r = &h[size_t(i) * 8];
+      if (!r[0] || !r[6]) continue;
+      ++n;
+      t0 = std::min(t0, r[0]);
+      t1 = std::max(t1, r[6]);
+      for (int k = 0; k < 6; ++k) {
+        const double d = double(r[k + 1] - r[k]);
+        sum[k] += d;
+        mx[k] = std::max(mx[k], d);
+      }
+    }
+    static const char *names[6] = {"tables+update", "first tile wait", "tiles", "look-back", "deferred+partial",
+                                   "final step"};
+    std::fprintf(stderr, "[chunk trace] %d items, span %.2f us\n", n, n ? (t1 - t0) * 1e-3 : 0.0);
+    for (int k = 0; k < 6; ++k)
+      std::fprintf(stderr, "  %-18s mean %7.2f us  max %7.2f us\n", names[k], n ? sum[k] / n * 1e-3 : 0.0, mx[k] * 1e-3);
+  }
+#endif
+  if (rc) return rc;
+  return cudaPeekAtLastError() == cudaSuccess ? COX_OK : COX_E_CUDA;
+}
+
+}  // namespace coxgb

@@ -154,6 +154,147 @@ static __device__ void block_sum(double (&v)[NV], double *scratch /* [NV*32] */)
   __syncthreads();
 }
 
+// block_sum for a CTA of NT threads (NT a multiple of 32, at most 1024).
+template <int NV, int NT>
+static __device__ void block_sum_nt(double (&v)[NV], double *scratch /* [NV*32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double x = lane < (NT / 32) ? scratch[i * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      v[i] = x;   // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// The end of a launch for one fit, run by the CTA that finished its last unit of work: the units'
+// partials (G1, G2, sum d log S0) summed in a fixed order, then by mode the evaluation result, the
+// log-likelihood, or the convergence test (once per sweep) and the coordinate step of §2.4 with
+// the update it leaves pending for the next launch. `nunits` partials sit in F.part[3u..3u+2].
+template <int NT>
+static __device__ void finish_launch_step(const DevFit &F, LaunchCtl *lc, int mode, int j, bool need_ll, int nunits,
+                                          uint32_t epoch, double *s_red) {
+  const DevData *D = F.d;
+  FitCtl *ctl = F.ctl;
+  const int tid = threadIdx.x;
+  const double shift = F.shift;
+  const int T_ = nunits;
+  __threadfence();
+  // the step's scalars, loaded ahead of the reduction below (each would otherwise be a dependent
+  // round trip of thread 0 after it)
+  double dxj = 0.0, bj = 0.0, trj = 0.0, obj_prev = 0.0, sum_d = 0.0;
+  int pzj = 1, err = 0, state = 0, sweep = 0, np_ = 0;
+  if (tid == 0) {
+    if (j >= 0) {
+      dxj = D->dX[j];
+      bj = F.beta[j];
+      trj = F.trust[j];
+      pzj = F.penalize ? F.penalize[j] != 0 : 1;
+    }
+    err = ctl->error;
+    state = ctl->state;
+    sweep = ctl->sweep;
+    obj_prev = ctl->obj_prev;
+    sum_d = D->sum_d;
+    np_ = D->p;
+  }
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int u = tid; u < T_; u += NT) {
+    acc[0] += ld_relaxed_f64(&F.part[3 * u + 0]);
+    acc[1] += ld_relaxed_f64(&F.part[3 * u + 1]);
+    acc[2] += ld_relaxed_f64(&F.part[3 * u + 2]);
+  }
+  block_sum_nt<3, NT>(acc, s_red);
+  double extra[2] = {0.0, 0.0};   // beta'dX and the penalty, when the log-likelihood is due
+  if (need_ll) {
+    for (int jj = tid; jj < D->p; jj += NT) {
+      const double b = F.beta[jj];
+      extra[0] += b * D->dX[jj];
+      const bool pen = F.penalize ? F.penalize[jj] != 0 : true;
+      if (pen && F.penalty == COX_PEN_L1) extra[1] += F.lambda * fabs(b);
+      if (pen && F.penalty == COX_PEN_L2) extra[1] += b * b / (2.0 * F.l2_var);
+    }
+    block_sum_nt<2, NT>(extra, s_red);
+  }
+  if (tid == 0) {
+    const double G1 = acc[0], G2 = acc[1], LL = acc[2];
+    if (err != 0) {   // raised by this fit's work in this launch (every unit finished before the fence)
+      if (mode == kModeFit && state == kRunning) atomicSub(&lc->active, 1);
+      ctl->state = kError;
+    } else if (mode == kModeShard) {
+      ctl->out_g1 = G1;
+      ctl->out_g2 = G2;
+      ctl->out_ll = LL;
+      ctl->out_bdx = extra[0];
+    } else if (mode == kModeEval) {
+      ctl->out_g1 = -dxj + G1;
+      ctl->out_g2 = G2;
+      if (F.gout) { F.gout[2 * j] = -dxj + G1; F.gout[2 * j + 1] = G2; }
+    } else if (mode == kModeLL) {
+      ctl->out_ll = extra[0] - LL - shift * sum_d;
+    } else {
+      bool stop = false;
+      if (need_ll) {
+        const double ll = extra[0] - LL - shift * sum_d;
+        const double obj = -ll + extra[1];
+        ctl->loglik = ll;
+        ctl->obj = obj;
+        if (sweep > 0 && fabs(obj - obj_prev) <= F.tol * fabs(obj)) {
+          ctl->state = kConverged;
+          stop = true;
+        } else if (sweep >= F.max_sweeps) {
+          ctl->state = kMaxed;
+          stop = true;
+        }
+        if (stop) {
+          atomicSub(&lc->active, 1);
+          ctl->pend_j = -1;   // this launch's tiles already applied the pending update
+        } else {
+          ctl->obj_prev = obj;
+        }
+      }
+      if (!stop) {
+        const double g1 = -dxj + G1, g2 = G2;
+        double tr = trj;
+        const double s = ccd_step_rule(g1, g2, bj, &tr, F.penalty, F.lambda, F.l2_var, pzj);
+        F.trust[j] = tr;
+        if (s != 0.0) {
+          F.beta[j] = bj + s;
+          ctl->pend_j = j;
+          ctl->pend_db = s;
+        } else {
+          ctl->pend_j = -1;
+          ctl->pend_db = 0.0;
+        }
+        ctl->coord_updates += 1;
+        int jn = j + 1;
+        if (jn >= np_) {
+          jn = 0;
+          ctl->sweep = sweep + 1;
+          ctl->need_ll = 1;
+        } else {
+          ctl->need_ll = 0;
+        }
+        ctl->j = jn;
+      }
+    }
+    ctl->done_tiles = 0u;
+    ctl->epoch = epoch + 1u;
+  }
+}
+
 // value written at a position for exp(eta - shift); exits hold the negative
 template <class P>
 static __device__ __forceinline__ typename P::T make_v(double eta, double shift, bool exitp, int32_t *err) {

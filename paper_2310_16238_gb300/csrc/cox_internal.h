@@ -50,8 +50,8 @@ struct DevData {
   const int32_t *tile_k;  // [T+1] first stratum whose last position is in tile t
   const double *dX;       // [p] delta' X_j
   const uint32_t *exit_bits; // [ceil(M/32)] exit positions (counting process) or nullptr
-  const uint32_t *head_bits; // [ceil(M/32) + 64] bitmap of the tie-group read positions
-  const uint32_t *cut_bits;  // [ceil(M/32) + 64] bitmap of the stratum ends
+  const uint32_t *head_bits; // [ceil(M/32) + 128] bitmap of the tie-group read positions
+  const uint32_t *cut_bits;  // [ceil(M/32) + 128] bitmap of the stratum ends
 };
 
 // Mutable control block of one fit (written by the last CTA of each launch).
@@ -88,6 +88,16 @@ struct DevFit {
   double *part;           // [T*3] tile partials (G1, G2, LL)
   double *out_S0, *out_S1;// [G] optional per-group sums (diagnostics)
   double *gout;           // [2p] EVAL mode: g'(beta_j), g''(beta_j) per column
+  float *hscr;            // [6G] FP32C chunked kernel: compensated local sums (S0, S1[, S2]) of tie
+                          // groups whose risk set reaches past their chunk, kept until its carry arrives
+  const void *vmap;       // FP32C: device copy of the tensor map (CUtensorMap, 128 bytes) that views v
+                          // as rows of 32 floats, for the chunked kernel's tile copies
+  // copies of data pointers the chunked kernel reads first (one dependent load fewer than via d)
+  const int32_t *tile_lo, *tile_g, *col_tile, *head_d;
+  const int64_t *col_ptr;
+  const uint32_t *idx, *cut_bits, *head_bits;
+  const double *val;
+  int32_t T;
   int32_t penalty, max_sweeps;
   double lambda, l2_var, tol, shift;
 };
@@ -118,6 +128,15 @@ enum : int32_t { kModeFit = 0, kModeEval = 1, kModeLL = 2, kModeShard = 3 };
 struct WorkItem {
   int32_t f, t, lo, hi, ga, gb, pad_[2];
 };
+
+// One work item of the FP32C chunked kernel (ccd_chunk.cu), the same size as a WorkItem: chunk c
+// (tiles [ta, tb)) of fit f, whose work list holds its nc chunks in descending order.
+struct ChunkItem {
+  int32_t f, c, ta, tb, nc;
+  int32_t lo_last;        // first position of the chunk's last tile (tile tb - 1)
+  int32_t pad_[2];
+};
+static_assert(sizeof(ChunkItem) == sizeof(WorkItem), "chunk items share the work-list buffer");
 
 // Arguments of the resident kernel (ccd_resident.cu), passed by value.
 struct ResParams {
@@ -174,6 +193,16 @@ int launch_ccd(int precision, const DevFit *fits, const WorkItem *items, LaunchC
                int j_eval, int valued, void *stream, unsigned long long cond = 0);
 int ccd_max_grid(int precision, int valued);
 int ccd_tile(int precision);
+// The FP32C launches above run the chunked kernel (ccd_chunk.cu); its work items are ChunkItems.
+int launch_chunk(const DevFit *fits, const ChunkItem *items, LaunchCtl *lc, int grid, int mode, int j_eval, int valued,
+                 void *stream, unsigned long long cond);
+int chunk_max_grid(int valued);
+// Encodes (on the host) the tensor map of a fit's v for the chunked kernel's tile copies: n_floats
+// floats from v (16-byte aligned) as rows of 32, one copy = 128 rows, 128-byte swizzle. out: 128
+// bytes, 64-byte aligned. Returns COX_OK or COX_E_CUDA.
+int chunk_encode_vmap(void *v, int64_t n_floats, void *out);
+constexpr int kChunkTile = 4096;     // positions per tile of the chunked kernel
+constexpr int kChunkMaxTiles = 64;   // tiles per chunk
 int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream);
 int launch_fill_v(int precision, const DevFit *fit_dev, int64_t M, const uint32_t *exit_bits, void *stream);
 

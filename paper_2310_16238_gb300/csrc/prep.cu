@@ -1029,10 +1029,11 @@ int prepare_data(const cox_data *in, int precision, int tile_req, cudaStream_t s
   if (!cut_pos) return COX_E_OOM;
   if (K > 0) { count_launches(1); cut_build_kernel<<<grid_for(K), 256, 0, s>>>(int32_t(K), seg_start, counting, cut_pos); }
   D.cut_pos = cut_pos;
-  // the same positions as bitmaps over the risk sequence (the streaming kernel stages a tile's
-  // words beside its values); one padding word per 32 positions past the end
+  // the same positions as bitmaps over the risk sequence (the streaming kernels stage a tile's
+  // words beside its values: up to 128 words from a tile's first position, so 128 zero words
+  // follow the end)
   {
-    const int64_t words = (D.M + 31) / 32 + 64;
+    const int64_t words = (D.M + 31) / 32 + 128;
     uint32_t *hb = static_cast<uint32_t *>(B.get(words * sizeof(uint32_t)));
     uint32_t *cb = static_cast<uint32_t *>(B.get(words * sizeof(uint32_t)));
     if (!hb || !cb) return COX_E_OOM;

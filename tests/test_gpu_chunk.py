@@ -1,0 +1,126 @@
+"""The FP32C streaming kernel with chunks of several tiles, against the oracle.
+
+The kernel streams each fit as chunks of consecutive 4,096-position tiles, carrying sums from tile
+to tile inside a chunk and through one look-back between chunks; tie groups whose risk set runs
+past their chunk wait for its carry. On small data the library's own plan gives every chunk one
+tile, so these tests force 1 to 7 tiles per chunk (cox_debug_set_chunk_tiles): fits, gradients and
+log-likelihoods must match the oracle at the FP32C tolerances (beta 1e-5 relative to max |beta|,
+log-likelihood 1e-7 of its scale), whatever the chunk length -- on strata and tie groups that span
+chunks, counting-process sequences, head-capped tiles and a batch of uneven fits.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_16238_gb300 import synth
+from tests.cases import random_beta
+
+pytestmark = pytest.mark.gpu
+cox = pytest.importorskip("paper_2310_16238_gb300.cox")
+
+CHUNK_TILES = (1, 2, 3, 7)
+
+
+def _rel_beta(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)) if len(b) else 0.0
+
+
+def _ll_scale(data, beta, ll):
+    return max(abs(ll), float(np.sum(data.event)))
+
+
+@pytest.fixture
+def chunk_tiles(request):
+    cox.cox_debug_set_chunk_tiles(request.param)
+    yield request.param
+    cox.cox_debug_set_chunk_tiles(0)
+
+
+def _cases():
+    out = []
+    # one stratum over ~12 tiles: every chunk's groups wait for the next chunk's carry
+    d, o = synth.stratified_sparse(n=50000, p=12, k=1, n_support=5, event_frac=0.2, dens_lo=0.005, dens_hi=0.2,
+                                   admin_days=2000, lam_per_n=1e-4, seed=61)
+    out.append(("one_stratum_l1", d, o))
+    # many strata (ends inside and on the edges of tiles and chunks), L2
+    d, _ = synth.stratified_sparse(n=60000, p=10, k=40, n_support=5, event_frac=0.1, dens_lo=0.005, dens_hi=0.3,
+                                   admin_days=400, seed=62)
+    out.append(("many_strata_l2", d, synth.CoxOptions(penalty=synth.PEN_L2, l2_var=0.5, tol=1e-10)))
+    # counting process: exits carry -exp(eta)
+    d, o = synth.time_varying(n_subj=12000, p=10, k=3, density=0.05, event_frac=0.3, n_support=5, seed=63)
+    out.append(("counting_l2", d, o))
+    # more tie groups than a tile holds: shortened, head-capped tiles inside chunks
+    rng = np.random.default_rng(64)
+    n = 40000
+    d = synth.finalize(np.arange(n) + 1, np.ones(n, int), rng.integers(0, 2, n), None,
+                       [np.nonzero(rng.random(n) < 0.1)[0] for _ in range(4)], None, 4)
+    out.append(("head_capped", d, synth.CoxOptions(penalty=synth.PEN_L2, l2_var=1.0, tol=1e-10)))
+    # valued X
+    d, o = synth.plain_dense(n=30000, p=6, seed=65)
+    out.append(("dense_valued", d, o))
+    return out
+
+
+CASES = _cases()
+_ORACLE = {}
+
+
+def _oracle_fit(name, data, opts, max_sweeps=None):
+    """The oracle's fit, cached across chunk lengths (it does not depend on them)."""
+    key = (name, max_sweeps)
+    if key not in _ORACLE:
+        _ORACLE[key] = oracle.fit(data, opts, max_sweeps=max_sweeps)
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("chunk_tiles", CHUNK_TILES, indirect=True)
+@pytest.mark.parametrize("name,data,opts", CASES, ids=[c[0] for c in CASES])
+def test_fp32c_fit_with_multi_tile_chunks(name, data, opts, chunk_tiles):
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+        beta, info = h.fit()
+    ob, oinfo = _oracle_fit(name, data, opts, info["sweeps"])
+    ob2, oinfo2 = _oracle_fit(name, data, opts)
+    err = min(_rel_beta(beta, ob), _rel_beta(beta, ob2))
+    assert err <= 1e-5, (err, chunk_tiles)
+    assert abs(info["loglik"] - oinfo2["loglik"]) <= 1e-7 * _ll_scale(data, ob2, oinfo2["loglik"])
+
+
+@pytest.mark.parametrize("chunk_tiles", CHUNK_TILES, indirect=True)
+@pytest.mark.parametrize("name,data,opts", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_fp32c_gradient_and_loglik_with_multi_tile_chunks(name, data, opts, chunk_tiles):
+    beta = random_beta(data.p, 0.3, seed=7)
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+        g1, g2 = h.gradient(beta)
+        ll = h.loglik(beta)
+    o1, o2 = oracle.grad_hess(data, beta)
+    ol = oracle.loglik(data, beta)
+    assert np.max(np.abs(g1 - o1)) <= 1e-5 * max(1.0, np.max(np.abs(o1)))
+    assert np.max(np.abs(g2 - o2)) <= 1e-5 * max(1.0, np.max(np.abs(o2)))
+    assert abs(ll - ol) <= 1e-7 * _ll_scale(data, beta, ol)
+
+
+@pytest.mark.parametrize("chunk_tiles", (2, 5), indirect=True)
+def test_fp32c_batch_with_multi_tile_chunks(chunk_tiles):
+    """Uneven fits in one batched launch: each result within the FP32C tolerance of the oracle."""
+    sets = [CASES[0], CASES[1], CASES[2]]
+    hs = [cox.Handle(d, o, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) for _, d, o in sets]
+    try:
+        betas, infos = cox.batch_fit(hs)
+    finally:
+        for h in hs:
+            h.close()
+    for (name, d, o), b, i in zip(sets, betas, infos):
+        ob, _ = _oracle_fit(name, d, o, i["sweeps"])
+        ob2, oi2 = _oracle_fit(name, d, o)
+        assert min(_rel_beta(b, ob), _rel_beta(b, ob2)) <= 1e-5, name
+        assert abs(i["loglik"] - oi2["loglik"]) <= 1e-7 * _ll_scale(d, ob2, oi2["loglik"]), name
+
+
+def test_chunk_tiles_knob_rejects_bad_values():
+    with pytest.raises(cox.CoxError):
+        cox.cox_debug_set_chunk_tiles(65)
+    with pytest.raises(cox.CoxError):
+        cox.cox_debug_set_chunk_tiles(-1)
+    cox.cox_debug_set_chunk_tiles(0)

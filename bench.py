@@ -119,9 +119,16 @@ class ClockSampler:
 ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 
 # DRAM bytes (read + write) per coordinate step of a kernel, from one ncu capture of the same kernel
-# on the same workload (launch total / steps it ran); the summaries and the commands are in
-# profiles/. Keyed by (engine, workload, precision); absent = not captured for the current kernel.
-TRAFFIC = {}
+# on the same workload (launch total / steps it ran; the captures run `bench.py --workload probe`).
+# Keyed by (engine, workload, precision); absent = not captured for the current kernel.
+TRAFFIC = {
+    # --probe incr: 190.09 MB per 1-sweep launch of 2001 steps
+    ("incremental", "stratified_sparse", "fp64"): 190.09e6 / 2001,
+    # --probe stream_fp32c: an evaluation launch (a fit's launch adds the previous column's update, ~0.2 MB)
+    ("streaming", "time_varying", "fp32c"): 26.58e6,
+    # --probe stream_fp64: an evaluation launch
+    ("streaming", "time_varying", "fp64"): 47.03e6,
+}
 
 
 def aggregate_ranks(units_per_rank: float, ms_per_step: float, world: int, device):
@@ -565,6 +572,90 @@ def run_time_varying(args):
             "roofline": roof}
 
 
+def run_probe(args):
+    """Small single-kernel cases for profiler captures (no graph, so every launch is a plain kernel
+    launch a profiler can capture), timed with CUDA events:
+      stream_fp32c / stream_fp64  cox_gradient (one evaluation launch per column) of the streaming
+                                  kernels on time_varying(1e6 subjects, p=300, K=20)
+      segscan                     cox_segscan on 2^24 doubles with 1,000 segments
+      prep                        cox_create on the stratified sparse data of the default line
+      incr / resident             one incremental- / resident-engine fit (1 sweep) of that data
+      views                       a time-split view (cox_create_split) and a 5-fold CV path's subsets"""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    what = args.probe
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"metric": "probe", "probe": what, "unit": "us"}
+    with torch.cuda.stream(stream):
+        if what in ("stream_fp32c", "stream_fp64"):
+            d, o = synth.time_varying(n_subj=int(1_000_000 * args.scale), p=300, k=20)
+            prec = cox.COX_FP32C if what == "stream_fp32c" else cox.COX_FP64
+            beta = np.zeros(d.p)
+            beta[::7] = 0.05
+            with cox.Handle(d, o, precision=prec, engine=cox.COX_ENGINE_STREAM, stream=stream.cuda_stream) as h:
+                h.gradient(beta)
+                e0.record(stream)
+                h.gradient(beta)
+                e1.record(stream)
+                e1.synchronize()
+            out.update(value=1e3 * e0.elapsed_time(e1) / d.p, what="us per evaluation launch (one column)")
+        elif what == "segscan":
+            n = 1 << 24
+            g = torch.Generator(device="cuda").manual_seed(synth.SEED_BASE)
+            a = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+            f = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            f[torch.randint(0, n, (1000,), device="cuda", generator=g)] = 1
+            cox.cox_segscan(a, f, stream=stream.cuda_stream)
+            e0.record(stream)
+            for _ in range(3):
+                cox.cox_segscan(a, f, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            out.update(value=1e3 * e0.elapsed_time(e1) / 3, what="us per scan of 2^24 doubles")
+        elif what == "resident":
+            d, o, _ = headline_workload(args.scale)
+            o = dataclasses.replace(o, max_sweeps=1)
+            with cox.Handle(d, o, precision=cox.COX_FP64, engine=cox.COX_ENGINE_RESIDENT, stream=stream.cuda_stream) as h:
+                e0.record(stream)
+                beta, info = h.fit()
+                e1.record(stream)
+                e1.synchronize()
+            out.update(value=1e3 * e0.elapsed_time(e1), what="us per 1-sweep fit",
+                       engine=ENGINE_NAMES.get(info["engine"], "unknown"), steps=info["coord_updates"] + 1)
+        elif what == "views":
+            # the time-split view (a covariate split at two cut days) and a 5-fold CV path's row subsets
+            d, o = synth.time_varying(n_subj=int(200_000 * args.scale), p=50, k=5)
+            e0.record(stream)
+            with cox.Handle.split(d, [90, 365], tvc_cols=(0, 1), opts=o, stream=stream.cuda_stream) as h:
+                h.metadata()
+            d2, o2 = synth.stratified_sparse(n=int(200_000 * args.scale), p=100, k=10, seed=synth.SEED_BASE + 7)
+            fold = cox.make_folds(d2.n, 5, seed=7)
+            cox.cox_cv_path(d2, fold, [1e-2 * d2.n, 1e-3 * d2.n], o2, n_folds=5, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            out.update(value=1e3 * e0.elapsed_time(e1), what="us for the split view and the CV path")
+        elif what in ("prep", "incr"):
+            d, o, _ = headline_workload(args.scale)
+            if what == "prep":
+                e0.record(stream)
+                h = cox.Handle(d, o, precision=cox.COX_FP64, stream=stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+                h.close()
+                out.update(value=1e3 * e0.elapsed_time(e1), what="us per cox_create (host inputs)")
+            else:
+                o = dataclasses.replace(o, max_sweeps=1)
+                with cox.Handle(d, o, precision=cox.COX_FP64, stream=stream.cuda_stream) as h:
+                    e0.record(stream)
+                    beta, info = h.fit()
+                    e1.record(stream)
+                    e1.synchronize()
+                out.update(value=1e3 * e0.elapsed_time(e1), what="us per 1-sweep fit",
+                           engine=ENGINE_NAMES.get(info["engine"], "unknown"), steps=info["coord_updates"] + 1)
+    return out
+
+
 def run_cv(args):
     """10-fold cross-validation along an L1 path (the paper's tuning procedure, §3.2): a stratified
     sparse data set of 2e5 rows, p = 1000, 10 strata, 8 weights log-spaced from 1e-2 N down to
@@ -822,7 +913,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default="default",
-                    choices=["default", "time_varying", "cv", "e1", "batch", "serving"])
+                    choices=["default", "time_varying", "cv", "e1", "batch", "serving", "probe"])
+    ap.add_argument("--probe", default="stream_fp32c",
+                    choices=["stream_fp32c", "stream_fp64", "segscan", "prep", "incr", "resident", "views"],
+                    help="probe workload: one small single-kernel case for a profiler capture")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--pool", type=int, default=24)
@@ -839,7 +933,7 @@ def main():
         return
     if args.workload != "default":
         fn = {"time_varying": run_time_varying, "cv": run_cv, "e1": run_e1, "batch": run_batch,
-              "serving": run_serving}[args.workload]
+              "serving": run_serving, "probe": run_probe}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return
     # the oracle's iterate of the moving fit runs in its own process beside the GPU legs (started

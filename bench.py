@@ -465,8 +465,9 @@ def run_serving(args, sub=False):
             return synth.CoxOptions(penalty=synth.PEN_L1, lam=float(np.exp(rng.uniform(-10, -6))) * d.n, tol=1e-8)
         return synth.CoxOptions(penalty=synth.PEN_L2, l2_var=float(np.exp(rng.uniform(-2, 1))), tol=1e-8)
 
-    def drive(arrivals, timeout_s):
-        lat, waits, fails = [], [], 0
+    def drive(arrivals, timeout_s, fixed=None):
+        """Submit pool[k % len(pool)] at arrivals[k] (options `fixed[k]`, else a fresh draw)."""
+        lat, waits, fails, results = [], [], 0, {}
         with cox.Server(precision=prec) as srv:
             t_start = time.perf_counter()
             pending, k = {}, 0
@@ -474,7 +475,7 @@ def run_serving(args, sub=False):
                 now = time.perf_counter() - t_start
                 while k < len(arrivals) and arrivals[k] <= now:
                     r, (d, o) = pool[k % len(pool)]
-                    pending[srv.submit(d, options(r, d))] = k
+                    pending[srv.submit(d, fixed[k] if fixed else options(r, d))] = k
                     k += 1
                 for rid in list(pending):
                     try:
@@ -486,18 +487,41 @@ def run_serving(args, sub=False):
                     if res is not None:
                         lat.append(res[1]["total_ms"])
                         waits.append(res[1]["wait_ms"])
+                        results[pending[rid]] = res
                         del pending[rid]
                 time.sleep(0.002)
                 if now > timeout_s:
                     break
             elapsed = time.perf_counter() - t_start
             st = srv.stats()
-        return np.array(lat), np.array(waits), elapsed, st, fails
+        return np.array(lat), np.array(waits), elapsed, st, fails, results
 
     # capacity: every pool request submitted at t = 0
+    burst_opts = [options(r, d) for r, (d, _) in pool]
     with ClockSampler(0) as clk_b:
-        lat_b, _, el_b, _, _ = drive([0.0] * len(pool), 900.0)
+        lat_b, _, el_b, _, _, res_b = drive([0.0] * len(pool), 900.0, fixed=burst_opts)
     capacity = len(lat_b) / el_b
+    # the plain path on the same requests and options: one fit at a time, FP64 (AUTO engine)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk_p:
+        t0 = time.perf_counter()
+        plain = []
+        for (r, (d, _)), o in zip(pool, burst_opts):
+            with cox.Handle(d, o, precision=cox.COX_FP64) as h:
+                plain.append(h.fit())
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+    err, mism = 0.0, 0
+    for k, (b32, i32) in res_b.items():
+        b64, i64 = plain[k]
+        if i32["sweeps"] != i64["sweeps"]:   # stopped one sweep apart: compare at the server's sweep
+            mism += 1
+            d = pool[k][1][0]
+            o2 = dataclasses.replace(burst_opts[k], max_sweeps=int(i32["sweeps"]), tol=0.0)
+            with cox.Handle(d, o2, precision=cox.COX_FP64) as h:
+                b64, _ = h.fit()
+        den = max(np.max(np.abs(b64)), 1e-12) if np.any(b64) else 1.0
+        err = max(err, float(np.max(np.abs(np.asarray(b32) - b64)) / den))
     rate = 0.8 * capacity
     # a Poisson stream at 80 % of that capacity
     t, arr = 0.0, []
@@ -508,12 +532,17 @@ def run_serving(args, sub=False):
             break
         arr.append(t)
     with ClockSampler(0) as clk:
-        lat, waits, el, st, fails = drive(arr, args.duration * 6)
+        lat, waits, el, st, fails, _ = drive(arr, args.duration * 6)
     out = {"workload": "Poisson arrivals; requests rows logU[1e4,1e7], p logU[100,2e4], density logU[1e-4,1e-2], "
                        f"K U{{1..200}}, 50% counting-process, L1/L2 (a pool of {len(pool)} drawn on the device, no row cap)",
            "precision": "fp32c", "pool_rows": {"min": min(rows), "median": float(np.median(rows)), "max": max(rows)},
            "pool_nnz": {"median": float(np.median(nnz)), "max": max(nnz)}, "pool_generation_s": gen_s,
            "capacity_fits_per_s": capacity, "burst_requests": len(pool), "burst_s": el_b,
+           "plain_fp64": {"fits_per_s": len(pool) / plain_s, "seconds": plain_s,
+                          "engine": "AUTO per fit (one fit at a time, cox_create from the device arrays)",
+                          "clocks": clk_p.summary()},
+           "served_vs_plain": capacity / (len(pool) / plain_s),
+           "max_rel_beta_err_vs_plain_fp64": err, "sweep_mismatches_vs_plain_fp64": mism,
            "sustainable_rate": rate, "offered_rate_config": args.rate,
            "stream": {"duration_s": args.duration, "requests": len(arr), "completed": len(lat), "failed": fails,
                       "fits_per_s": len(lat) / el,

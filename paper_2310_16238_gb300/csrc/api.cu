@@ -1602,6 +1602,7 @@ struct Req {
   size_t footprint = 0;
   cox_handle *h = nullptr;
   int slot = -1;
+  bool incr = false;   // runs whole on the incremental kernel (between replays), not in the work list
   bool cancel = false;
   std::vector<double> beta;
   cox_fit_info info{};
@@ -1617,6 +1618,7 @@ struct cox_server {
   std::condition_variable cv_prep, cv_run, cv_done;
   std::deque<Req *> queue;
   std::vector<Req *> ready;
+  std::deque<Req *> incr_ready;   // prepared fits routed to the incremental kernel (counted in n_running)
   std::unordered_map<uint64_t, Req *> reqs;
   uint64_t next_id = 1;
   size_t bytes_in_use = 0;
@@ -1721,10 +1723,48 @@ void prep_loop(cox_server *S) {
     S->bytes_in_use = S->bytes_in_use - r->footprint + actual;
     r->footprint = actual;
     r->h = h;
-    r->state = kReady;
-    S->ready.push_back(r);
+    // a fit whose data qualify for the incremental kernel runs whole on it: O(groups + nonzeros)
+    // per coordinate against the work list's O(positions) (a launch of the list is latency-bound
+    // at ~20 us, however few positions its fits hold); the others batch in the list
+    r->incr = h->sd->prep.inc_T > 0;
+    if (r->incr) {
+      r->state = kInFlight;
+      S->incr_ready.push_back(r);
+      S->n_running++;
+    } else {
+      r->state = kReady;
+      S->ready.push_back(r);
+    }
     S->cv_run.notify_one();
   }
+}
+
+// One fit routed to the incremental kernel, run to its end on the run stream, and retired.
+void run_incr_fit(cox_server *S, Req *r) {
+  cox_handle *h = r->h;
+  h->stream = S->run_stream;
+  cox_fit_info info{};
+  std::vector<double> beta(static_cast<size_t>(std::max<int32_t>(D(h).p, 1)), 0.0);
+  int rc = r->cancel ? COX_E_INVALID : fit_incr(h, beta.data(), &info);
+  if (rc == COX_E_RANGE && init_state(h, nullptr) == COX_OK) {
+    // beyond the double-word range of the incremental sums: the work list (FP32C with a shift
+    // check, or FP64) takes the fit from the start
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->incr = false;
+    r->state = kReady;
+    S->n_running--;
+    S->ready.push_back(r);
+    return;
+  }
+  r->beta = beta;
+  r->info = info;
+  cox_destroy(h);
+  r->h = nullptr;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->n_running--;
+  S->bytes_in_use -= r->footprint;
+  S->step_launches += info.step_launches;
+  finish_locked(S, r, rc);
 }
 
 int rebuild_batch(cox_server *S) {
@@ -1808,6 +1848,19 @@ void run_loop(cox_server *S) {
       S->ready.clear();
       if (S->n_running == 0) continue;
     }
+    // one fit routed to the incremental kernel, then a replay of the work list (if it holds any)
+    Req *ri = nullptr;
+    bool listed = false;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (!S->incr_ready.empty()) {
+        ri = S->incr_ready.front();
+        S->incr_ready.pop_front();
+      }
+      for (Req *r : S->slots) listed = listed || r != nullptr;
+    }
+    if (ri) run_incr_fit(S, ri);
+    if (!listed) continue;
     // cancellations are honoured here, at a replay boundary
     std::vector<Req *> retire;
     bool waits_failed = false;   // a launch of the work list gave up a device-side wait
@@ -1854,6 +1907,7 @@ void run_loop(cox_server *S) {
         cudaMemcpy(r->beta.data(), r->h->hfit.beta, D(r->h).p * sizeof(double), cudaMemcpyDeviceToHost);
       r->info.sweeps = c.sweep;
       r->info.converged = c.state == kConverged;
+      r->info.engine = COX_ENGINE_STREAM;
       r->info.coord_updates = c.coord_updates;
       r->info.loglik = c.loglik;
       r->info.objective = c.obj;

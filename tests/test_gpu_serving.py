@@ -1,5 +1,6 @@
-"""The continuous-batching server (cox_server_*): results in the mix equal standalone fits,
-admission by memory footprint, cancellation."""
+"""The continuous-batching server (cox_server_*): results in the mix equal standalone fits on
+the engine the server gives each request (the incremental kernel when its data qualify, else the
+streaming work list), admission by memory footprint, cancellation."""
 from __future__ import annotations
 
 import threading
@@ -33,12 +34,20 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def _alone(d, o, precision=cox.COX_FP64):
+    """The request fitted on its own by the engine the server gives it: the incremental kernel
+    when the data qualify for it, else the streaming kernel."""
+    with cox.Handle(d, o, precision=precision) as h:
+        r = h.fit()
+    if r[1]["engine"] == cox.COX_ENGINE_INCR:
+        return r
+    with cox.Handle(d, o, precision=precision, engine=cox.COX_ENGINE_STREAM) as h:
+        return h.fit()
+
+
 def test_results_in_the_mix_equal_standalone_fits():
     reqs = _requests()
-    alone = []
-    for d, o in reqs:
-        with cox.Handle(d, o, engine=cox.COX_ENGINE_STREAM) as h:
-            alone.append(h.fit())
+    alone = [_alone(d, o) for d, o in reqs]
     # a budget that holds only a few requests at once, so that the queue, admission and
     # retirement all take part while the other fits are in flight
     budget = 6 * max(cox.cox_footprint(d, o) for d, o in reqs)
@@ -73,8 +82,7 @@ def test_concurrent_submitters_and_polling():
             t.join(120)
     assert len(results) == len(reqs)
     for k, (d, o) in enumerate(reqs):
-        with cox.Handle(d, o, engine=cox.COX_ENGINE_STREAM) as h:
-            b, info = h.fit()
+        b, info = _alone(d, o)
         assert _rel(results[k][0], b) <= 1e-12
 
 
@@ -134,10 +142,7 @@ def test_fp32c_results_in_the_mix_equal_standalone_fits():
     with the same precision, within the stated FP32C tolerance (1e-5 in beta, 1e-7 in the
     log-likelihood)."""
     reqs = _requests()
-    alone = []
-    for d, o in reqs:
-        with cox.Handle(d, o, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
-            alone.append(h.fit())
+    alone = [_alone(d, o, cox.COX_FP32C) for d, o in reqs]
     budget = 6 * max(cox.cox_footprint(d, o, cox.COX_FP32C) for d, o in reqs)
     with cox.Server(memory_budget=budget, max_active=5, precision=cox.COX_FP32C) as srv:
         ids = [srv.submit(d, o) for d, o in reqs]
@@ -146,3 +151,35 @@ def test_fp32c_results_in_the_mix_equal_standalone_fits():
         assert abs(ii["sweeps"] - info["sweeps"]) <= 1, (d.recipe, ii, info)
         assert _rel(bb, b) <= 1e-5, (d.recipe, _rel(bb, b))
         assert abs(ii["loglik"] - info["loglik"]) <= 1e-7 * _ll_scale(d, b, info["loglik"])
+
+
+def _mixed_size_requests():
+    """Requests of several sizes with binary X: the server runs each whole on the incremental
+    kernel (between replays of its work list) when its data qualify, else in the work list."""
+    out = _requests()[:4]
+    d, o = synth.stratified_sparse(n=300_000, p=8, k=20, n_support=4, event_frac=0.1, dens_lo=0.005, dens_hi=0.2,
+                                   admin_days=400, lam_per_n=1e-4, seed=400)
+    out.append((d, o))
+    d, o = synth.time_varying(n_subj=60_000, p=6, k=4, density=0.05, event_frac=0.3, n_support=3, seed=401)
+    out.append((d, o))
+    return out
+
+
+@pytest.mark.parametrize("precision,btol,ltol", [(cox.COX_FP64, 1e-9, 1e-11), (cox.COX_FP32C, 1e-5, 1e-7)],
+                         ids=["fp64", "fp32c"])
+def test_large_requests_run_on_the_incremental_kernel_and_match_the_oracle(precision, btol, ltol):
+    reqs = _mixed_size_requests()
+    with cox.Server(max_active=4, precision=precision) as srv:
+        ids = [srv.submit(d, o) for d, o in reqs]
+        got = [srv.wait(i, 300.0) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["running"] == 0 and st["bytes_in_use"] == 0
+    for (bb, ii), (d, o) in zip(got, reqs):
+        with cox.Handle(d, o, precision=precision) as h:   # AUTO: the engine the data qualify for
+            _, alone = h.fit()
+        want = cox.COX_ENGINE_INCR if alone["engine"] == cox.COX_ENGINE_INCR else cox.COX_ENGINE_STREAM
+        assert ii["engine"] == want, (d.recipe, ii["engine"], alone["engine"])
+        o_same = synth.CoxOptions(penalty=o.penalty, lam=o.lam, l2_var=o.l2_var, penalize=o.penalize, tol=0.0)
+        ob, oi = oracle.fit(d, o_same, max_sweeps=ii["sweeps"])
+        assert _rel(bb, ob) <= btol, (d.recipe, _rel(bb, ob))
+        assert abs(ii["loglik"] - oi["loglik"]) <= ltol * _ll_scale(d, ob, oi["loglik"]), (d.recipe, ii, oi)

@@ -551,14 +551,21 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     const int hopen = S.hopen;
     const int gac = S.tg[0], gbc = S.tg[nt];
     const int q0 = min(max(hopen, gac), gbc);   // deferred groups: [q0, gbc) (hopen is INT_MAX when none)
-    // each thread's first deferred group, loaded while warp 0 looks back
-    float2 pre_hs[NV];
-    int pre_d = 0;
-    if (q0 + tid < gbc) {
-      const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q0 + tid);
+    // while warp 0 looks back, the other warps copy the deferred groups' sums and event counts
+    // into the (now idle) tile buffers, when they fit there
+    const int ndef = gbc - q0;
+    constexpr int kDefCap = int(sizeof(S.v) / (NV * sizeof(float2) + sizeof(int32_t)));
+    float2 *dsum = reinterpret_cast<float2 *>(&S.v[0][0]);                  // [NV][kDefCap]
+    int32_t *dcnt = reinterpret_cast<int32_t *>(dsum + NV * kDefCap);      // [kDefCap]
+    const bool on_chip = ndef <= kDefCap;
+    if (on_chip && warp > 0) {
+      const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q0);
+#pragma unroll 4
+      for (int q = tid - 32; q < ndef; q += kCT - 32) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) pre_hs[i] = hs[i];
-      pre_d = F.head_d[q0 + tid];
+        for (int i = 0; i < NV; ++i) dsum[i * kDefCap + q] = hs[3 * q + i];
+        dcnt[q] = F.head_d[q0 + q];
+      }
     }
     uint64_t *cwd = reinterpret_cast<uint64_t *>(F.tval);   // per chunk: aggregate words 0..2, inclusive 3..5
     if (warp == 0) {
@@ -655,22 +662,17 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       Acc CR[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i) CR[i] = P::from64(S.cr[i]);
-      if (q0 + tid < gbc) {
-        Acc sh[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) sh[i] = P::comb(Acc{pre_hs[i].x, pre_hs[i].y}, CR[i]);
-        add_group<NV>(sh, pre_d, j, need_ll, g1q, g2q, llq, F, q0 + tid);
-      }
-      for (int q = q0 + tid + kCT; q < gbc; q += kCT) {
-        const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q);
+      const float2 *hs = reinterpret_cast<const float2 *>(F.hscr) + 3 * int64_t(q0);
+      for (int q = tid; q < ndef; q += kCT) {
         Acc sh[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-          const float2 f2 = hs[i];
+          const float2 f2 = on_chip ? dsum[i * kDefCap + q] : hs[3 * q + i];
           sh[i] = P::comb(Acc{f2.x, f2.y}, CR[i]);
         }
-        add_group<NV>(sh, F.head_d[q], j, need_ll, g1q, g2q, llq, F, q);
+        add_group<NV>(sh, on_chip ? dcnt[q] : F.head_d[q0 + q], j, need_ll, g1q, g2q, llq, F, q0 + q);
       }
+      fence_proxy_async_smem();   // the tile buffers are rewritten by the next chunk's copies
     }
 
     // ---- the chunk's partial, then the step by the CTA that finishes the fit's last chunk
@@ -696,7 +698,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     }
     __syncthreads();
     CHUNK_STAMP(5);
-    if (S.last) finish_launch_step<kCT>(F, lc, mode, j, need_ll, nc, epoch, S.scratch);
+    if (S.last) finish_launch_step<kCT, false>(F, lc, mode, j, need_ll, nc, epoch, S.scratch);
     __syncthreads();
     CHUNK_STAMP(6);
   }

@@ -183,7 +183,9 @@ static __device__ void block_sum_nt(double (&v)[NV], double *scratch /* [NV*32] 
 // partials (G1, G2, sum d log S0) summed in a fixed order, then by mode the evaluation result, the
 // log-likelihood, or the convergence test (once per sweep) and the coordinate step of §2.4 with
 // the update it leaves pending for the next launch. `nunits` partials sit in F.part[3u..3u+2].
-template <int NT>
+// kFence: the caller's completion count was relaxed, so the partials need an acquire fence here
+// (false where the count was an acquire-release atomic followed by a CTA barrier).
+template <int NT, bool kFence = true>
 static __device__ void finish_launch_step(const DevFit &F, LaunchCtl *lc, int mode, int j, bool need_ll, int nunits,
                                           uint32_t epoch, double *s_red) {
   const DevData *D = F.d;
@@ -191,7 +193,7 @@ static __device__ void finish_launch_step(const DevFit &F, LaunchCtl *lc, int mo
   const int tid = threadIdx.x;
   const double shift = F.shift;
   const int T_ = nunits;
-  __threadfence();
+  if constexpr (kFence) __threadfence();
   // the step's scalars, loaded ahead of the reduction below (each would otherwise be a dependent
   // round trip of thread 0 after it)
   double dxj = 0.0, bj = 0.0, trj = 0.0, obj_prev = 0.0, sum_d = 0.0;

@@ -83,7 +83,8 @@ struct ChunkSmem {
   uint16_t hpos[kHeadCap];                                 // the tile's tie-group positions
   Acc bs[4][kCT];                                          // S0 suffix of a thread's blocks right of block b
   Acc E[NV][kCT];                                          // each thread's carry from the chunk's later positions
-  uint8_t Eo[kCT], zf[kCT];                                // that carry runs to the chunk's end / thread has nonzeros
+  uint8_t Eo[kCT], zf[kCT];                                // that carry runs to the chunk's end / the thread's
+                                                           // column positions: 0 none, 1 some, 2 all (binary x)
   Acc wa[NV][kCW];                                         // warp sums from the warp's first position
   int32_t wf[kCW];                                         // warp holds a stratum end
   Acc cc[2][NV];                                           // the chunk carry into the current tile
@@ -346,9 +347,13 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       for (int off = 16; off > 0; off >>= 1) wpre += __shfl_xor_sync(0xffffffffu, wpre, off);
       const int hbase = wpre + hinc - hc;
 
-      // ---- S1 (S2) over the thread's nonzeros, right to left (reads v before it is overwritten)
+      // ---- S1 (S2) over the thread's nonzeros, right to left (reads v before it is overwritten).
+      //      A thread whose every position is a nonzero of a binary column takes S0's sums instead
+      //      (the same additions in the same order), so that a column that is nonzero everywhere
+      //      gives S1 bitwise equal to S0 (ratios of exactly 1, the paper's degenerate column).
+      const bool full = !vf && zm == 0xffffffffu;
       float a1 = 0.f, a2 = 0.f;
-      if (zm) {
+      if (zm && !full) {
         float r1 = 0.f, r2 = 0.f;
         int rank = hc;
         for (uint32_t m = zm | hm | cm; m;) {
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
         a1 = r1;
         a2 = r2;
       }
-      S.zf[tid] = zm != 0u;
+      S.zf[tid] = uint8_t(full ? 2 : (zm != 0u ? 1 : 0));
 
       // ---- S0: plain sums within blocks of 8, compensated above; partials replace v in place
       float x[kCI];
@@ -423,8 +428,8 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       // ---- warp segmented suffix scan of the thread sums (from each thread's first position)
       Acc I[NV];
       I[0] = run;
-      I[1] = Acc{a1, 0.f};
-      if constexpr (VAL) I[2] = Acc{a2, 0.f};
+      I[1] = full ? run : Acc{a1, 0.f};
+      if constexpr (VAL) I[2] = full ? run : Acc{a2, 0.f};
       int If = rf;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
@@ -519,11 +524,11 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
         const uint32_t upto = bl == 3 ? toend : (toend & ((1u << (8 * bl + 8)) - 1u));
         Acc sh[NV];
         sh[0] = Acc{S.v[b][swz(pos)], 0.f};
-        const bool z = S.zf[o] != 0;
-        sh[1] = Acc{z ? S.s1h[0][h] : 0.f, 0.f};
-        if constexpr (VAL) sh[2] = Acc{z ? S.s1h[1][h] : 0.f, 0.f};
-        int open = 0;
         if ((m & upto) == 0u) sh[0] = P::comb(sh[0], S.bs[bl][o]);
+        const int z = S.zf[o];
+        sh[1] = z == 2 ? sh[0] : Acc{z ? S.s1h[0][h] : 0.f, 0.f};
+        if constexpr (VAL) sh[2] = z == 2 ? sh[0] : Acc{z ? S.s1h[1][h] : 0.f, 0.f};
+        int open = 0;
         if ((m & toend) == 0u) {   // the risk set runs past the thread's positions
 #pragma unroll
           for (int i = 0; i < NV; ++i) sh[i] = P::comb(sh[i], S.E[i][o]);

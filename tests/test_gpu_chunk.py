@@ -124,3 +124,37 @@ def test_chunk_tiles_knob_rejects_bad_values():
     with pytest.raises(cox.CoxError):
         cox.cox_debug_set_chunk_tiles(-1)
     cox.cox_debug_set_chunk_tiles(0)
+
+
+def _edge_cases():
+    """The FP64 parity suite's edge cases (tests/test_gpu_parity.py), for the FP32C kernel."""
+    from tests.test_gpu_parity import _edge_cases as edges
+    return edges()
+
+
+EDGES = _edge_cases()
+
+
+@pytest.mark.parametrize("chunk_tiles", (0, 2), indirect=True)
+@pytest.mark.parametrize("name,data,opts", EDGES, ids=[c[0] for c in EDGES])
+def test_fp32c_edge_cases(name, data, opts, chunk_tiles):
+    """No events, every row tied, singleton strata, a dense / empty / one-row column, tie heads on
+    tile boundaries, head-capped tiles: the FP32C fit, gradient and log-likelihood against the
+    oracle at the FP32C tolerances, with the library's chunk plan and with 2 tiles per chunk."""
+    beta0 = random_beta(data.p, 0.2, seed=3)
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+        g1, g2 = h.gradient(beta0)
+        ll = h.loglik(beta0)
+        beta, info = h.fit()
+    o1, o2 = oracle.grad_hess(data, beta0)
+    ol = oracle.loglik(data, beta0)
+    assert np.max(np.abs(g1 - o1)) <= 1e-5 * max(1.0, np.max(np.abs(o1))), name
+    assert np.max(np.abs(g2 - o2)) <= 1e-5 * max(1.0, np.max(np.abs(o2))), name
+    assert abs(ll - ol) <= 1e-7 * max(_ll_scale(data, beta0, ol), 1.0), name
+    ob, _ = _oracle_fit(name, data, opts, info["sweeps"])
+    ob2, oi2 = _oracle_fit(name, data, opts)
+    if np.any(ob2):
+        assert min(_rel_beta(beta, ob), _rel_beta(beta, ob2)) <= 1e-5, name
+    else:
+        assert np.max(np.abs(beta)) <= 1e-7, name
+    assert abs(info["loglik"] - oi2["loglik"]) <= 1e-7 * max(_ll_scale(data, ob2, oi2["loglik"]), 1.0), name

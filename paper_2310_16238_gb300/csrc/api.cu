@@ -1475,28 +1475,56 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     if (D(hs[i]).p == 0 || D(hs[i]).T == 0) running[i] = 0;
   }
   if (!rc) rc = rebuild_items();
-  cudaGraphExec_t graph = nullptr;
+  // A fit can stop only at the first step of a sweep (where its objective is tested): launch s p
+  // (s >= 1, counted from 0) of a fit of p columns. The host runs segments of launches that end
+  // right after the next such launch of any running fit, so that a stopped fit's chunks leave the
+  // plan before the next launch. Graphs of 1, 2, 4, ... launches are captured once; a segment is
+  // the binary decomposition of its length.
   const int len = int(std::min<int64_t>(std::max<int64_t>(maxp, 32), 2048));
   const int grid = std::max(1, ccd_max_grid(precision, valued));
-  if (!rc) {
+  std::vector<cudaGraphExec_t> pow2;
+  while (!rc && (int64_t(1) << pow2.size()) <= len) {
+    const int k = 1 << pow2.size();
     cudaGraph_t g;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = cuda_fail(nullptr, "capture");
-    for (int i = 0; i < len && !rc; ++i)
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = cuda_fail(nullptr, "capture");
+      break;
+    }
+    for (int i = 0; i < k && !rc; ++i)
       if (launch_ccd(precision, fits, items, lc, grid, kModeFit, 0, valued, s)) rc = cuda_fail(nullptr, "capture launch");
     if (cudaStreamEndCapture(s, &g) != cudaSuccess && !rc) rc = cuda_fail(nullptr, "end capture");
     if (!rc) {
-      if (cudaGraphInstantiate(&graph, g, 0) != cudaSuccess) rc = cuda_fail(nullptr, "instantiate");
+      if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) rc = cuda_fail(nullptr, "instantiate");
       cudaGraphDestroy(g);
     }
+    if (!rc) pow2.push_back(ge);
   }
+  auto segment_end = [&](int64_t done) {   // launches done when the next segment ends
+    int64_t b = INT64_MAX;
+    for (int i = 0; i < n; ++i)
+      if (running[i]) {
+        const int64_t pi = D(hs[i]).p;
+        int64_t sw = std::max<int64_t>(1, done / pi);
+        while (sw * pi + 1 <= done) ++sw;
+        b = std::min(b, sw * pi + 1);
+      }
+    return std::min(b, done + 2 * int64_t(len));
+  };
   int64_t launched = 0;
   while (!rc) {
     int any = 0;
     for (int i = 0; i < n; ++i) any |= running[i];
     if (!any) break;
-    if (cudaGraphLaunch(graph, s) != cudaSuccess) { rc = cuda_fail(nullptr, "graph launch"); break; }
-    count_launches(len);
-    launched += len;
+    int64_t todo = segment_end(launched) - launched;
+    for (int k = int(pow2.size()) - 1; k >= 0 && todo > 0 && !rc; --k)
+      while (todo >= (int64_t(1) << k) && !rc) {
+        if (cudaGraphLaunch(pow2[size_t(k)], s) != cudaSuccess) rc = cuda_fail(nullptr, "graph launch");
+        count_launches(1 << k);
+        launched += 1 << k;
+        todo -= 1 << k;
+      }
+    if (rc) break;
     LaunchCtl lc_now{};
     if (cudaMemcpyAsync(hc, ctls, n * sizeof(FitCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&lc_now, lc, sizeof(LaunchCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1517,7 +1545,7 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     if (changed) rc = rebuild_items();
     if (launched > max_launches + len) { rc = fail(nullptr, COX_E_INVALID, "cox_batch_fit: launch bound exceeded"); break; }
   }
-  if (graph) cudaGraphExecDestroy(graph);
+  for (cudaGraphExec_t ge : pow2) cudaGraphExecDestroy(ge);
   int worst = rc;
   if (!rc) {
     for (int i = 0; i < n; ++i) {

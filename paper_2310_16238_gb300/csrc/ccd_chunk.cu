@@ -45,6 +45,7 @@ constexpr int kCT = 128;        // threads per CTA
 constexpr int kCI = 32;         // positions per thread
 constexpr int kCW = kCT / 32;   // warps per CTA
 constexpr int kPF = 2;          // events-per-group values each thread prefetches for its first groups
+constexpr int kES = 2 * kCT;    // column entries of the next tile copied ahead with its tile (2 per thread)
 #ifndef COXGB_CHUNK_MIN_CTAS
 #define COXGB_CHUNK_MIN_CTAS 4  // resident CTAs per SM the register allocation is held to
 #endif
@@ -78,6 +79,8 @@ struct ChunkSmem {
   float s1h[NV - 1][kHeadCap];                             // tie groups' thread-local S1 (and S2) sums
   uint32_t cw[2][kCT], hw[2][kCT];                         // stratum-end and tie-group bits per thread
   uint32_t nzw[3][kCT];                                    // column-j bits per thread, by tile mod 3
+  uint32_t ib[2][kES];                                     // column j's first entries of a staged tile
+  double vb[NV == 3 ? 2 : 1][NV == 3 ? kES : 1];           // their values (valued fits)
   int32_t tlo[kChunkMaxTiles + 1], tg[kChunkMaxTiles + 1]; // the chunk's tile positions and first groups
   int32_t ctj[kChunkMaxTiles + 1], ctp[kChunkMaxTiles + 1];// column j's / the pending column's first entries
   uint16_t hpos[kHeadCap];                                 // the tile's tie-group positions
@@ -202,7 +205,12 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     FitCtl *ctl = F.ctl;
     const int c = it.c, ta = it.ta, tb = it.tb, nc = it.nc, nt = tb - ta;
     const float *vg = static_cast<const float *>(F.v);   // the patch below reads v directly
-    auto stage = [&](int t, int lo) {   // tile t's values (one tensor copy) and bits, asynchronously
+    int j = -1;            // the launch's column (set once the fit's control block is read)
+    int64_t cbj = 0;       // its first entry
+    bool vf = false;       // valued fit (binary fits in a valued launch use x = 1)
+    // tile t's values (one tensor copy), bits and, once the tables are in (cols), the first kES of
+    // column j's entries in the tile (each thread copies, and later scatters, its own), asynchronously
+    auto stage = [&](int t, int lo, bool cols) {
       const int b = t & 1;
       if (tid == 0) {
         mbar_expect_tx(&S.mbar[b], uint32_t(kChunkTile * sizeof(float)));
@@ -210,19 +218,34 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       }
       cp_async4(&S.cw[b][tid], F.cut_bits + (lo >> 5) + tid);
       cp_async4(&S.hw[b][tid], F.head_bits + (lo >> 5) + tid);
+      if (cols && j >= 0) {
+        const int tq = t - ta;
+        const int64_t q0 = cbj + S.ctj[tq], q1 = cbj + S.ctj[tq + 1];
+#pragma unroll
+        for (int u = 0; u < kES / kCT; ++u) {
+          const int64_t q = q0 + tid + u * kCT;
+          if (q < q1) {
+            cp_async4(&S.ib[b][tid + u * kCT], F.idx + q);
+            if constexpr (VAL) {
+              if (vf) cp_async8(&S.vb[b][tid + u * kCT], F.val + q);
+            }
+          }
+        }
+      }
       cp_async_commit();
     };
     if (__syncthreads_or(tid == 0 && mode == kModeFit && ctl->state != kRunning)) continue;
-    stage(tb - 1, it.lo_last);   // the chunk's last tile, before its tables arrive
+    stage(tb - 1, it.lo_last, false);   // the chunk's last tile, before its tables arrive
     const int T_ = F.T;
-    const int j = (mode == kModeEval || mode == kModeShard) ? j_eval : (mode == kModeFit ? ctl->j : -1);
+    j = (mode == kModeEval || mode == kModeShard) ? j_eval : (mode == kModeFit ? ctl->j : -1);
     const bool need_ll = mode == kModeLL || ((mode == kModeFit || mode == kModeShard) && ctl->need_ll);
     const int pend_j = mode == kModeFit ? ctl->pend_j : -1;
     const double pend_db = ctl->pend_db;
     const uint32_t epoch = ctl->epoch;
     const uint32_t etag = epoch % 15u + 1u;   // never 0: zeroed words are never current
     const double shift = F.shift;
-    const bool vf = VAL && F.val != nullptr;   // binary fits in a valued launch use x = 1
+    vf = VAL && F.val != nullptr;
+    cbj = j >= 0 ? F.col_ptr[j] : 0;
 
     // ---- the chunk's tables
     for (int q = tid; q <= nt; q += kCT) {
@@ -239,15 +262,30 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     }
     __syncthreads();
 
-    auto scatter = [&](int t) {   // column j's entries of tile t -> per-thread bits (and values)
+    // column j's entries of tile t -> per-thread bits (and values): the thread's entries that
+    // stage() copied (staged), then any beyond them from global memory
+    auto scatter = [&](int t, bool staged) {
       if (j < 0) return;
-      const int tq = t - ta, lo = S.tlo[tq];
-      const int64_t cb = F.col_ptr[j];
-      for (int64_t q = cb + S.ctj[tq] + tid; q < cb + S.ctj[tq + 1]; q += kCT) {
+      const int tq = t - ta, lo = S.tlo[tq], b = t & 1;
+      const int64_t q1 = cbj + S.ctj[tq + 1];
+      int64_t q = cbj + S.ctj[tq] + tid;
+      if (staged) {
+#pragma unroll
+        for (int u = 0; u < kES / kCT; ++u, q += kCT) {
+          if (q < q1) {
+            const int e = int(S.ib[b][tid + u * kCT] & kPosMask) - lo;
+            atomicOr(&S.nzw[t % 3][e >> 5], 1u << (e & 31));
+            if constexpr (VAL) {
+              if (vf) S.xs[b][e] = float(S.vb[b][tid + u * kCT]);
+            }
+          }
+        }
+      }
+      for (; q < q1; q += kCT) {
         const int e = int(F.idx[q] & kPosMask) - lo;
         atomicOr(&S.nzw[t % 3][e >> 5], 1u << (e & 31));
         if constexpr (VAL) {
-          if (vf) S.xs[t & 1][e] = float(F.val[q]);
+          if (vf) S.xs[b][e] = float(F.val[q]);
         }
       }
     };
@@ -261,22 +299,39 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     if (pend_j >= 0) {
       const int64_t cb = F.col_ptr[pend_j];
       const int lo_l = S.tlo[nt - 1], hi_l = S.tlo[nt];
-      for (int64_t q = cb + S.ctp[0] + tid; q < cb + S.ctp[nt]; q += kCT) {
-        const uint32_t e = F.idx[q];
-        const int64_t pos = e & kPosMask;
-        const double x = F.val ? F.val[q] : 1.0;
-        const double et = __dadd_rn(F.eta[pos], __dmul_rn(x, pend_db));
-        F.eta[pos] = et;
-        const float nv = make_v<P>(et, shift, (e & kExitBit) != 0, &ctl->error);
-        static_cast<float *>(F.v)[pos] = nv;
-        if (pos >= lo_l && pos < hi_l) {
-          if (np < kKeep) {
+      const int64_t qa = cb + S.ctp[0], qb = cb + S.ctp[nt];
+      // kPU of the thread's entries at a time: their positions, then their eta, are loaded together
+      // (a chunk of many tiles holds several entries per thread; one at a time, each would cost two
+      // dependent round trips to memory)
+      constexpr int kPU = 4;
+      for (int64_t q0 = qa + tid; q0 < qb; q0 += kPU * kCT) {
+        uint32_t e[kPU];
+        double x[kPU], eo[kPU];
 #pragma unroll
-            for (int u = 0; u < kKeep; ++u)
-              if (u == np) { keep_pos[u] = int(pos - lo_l); keep_v[u] = nv; }
-            ++np;
-          } else {
-            overflow = true;
+        for (int u = 0; u < kPU; ++u) {
+          const int64_t q = q0 + int64_t(u) * kCT;
+          e[u] = q < qb ? F.idx[q] : 0u;
+          x[u] = F.val && q < qb ? F.val[q] : 1.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPU; ++u) eo[u] = q0 + int64_t(u) * kCT < qb ? F.eta[e[u] & kPosMask] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPU; ++u) {
+          if (q0 + int64_t(u) * kCT >= qb) break;
+          const int64_t pos = e[u] & kPosMask;
+          const double et = __dadd_rn(eo[u], __dmul_rn(x[u], pend_db));
+          F.eta[pos] = et;
+          const float nv = make_v<P>(et, shift, (e[u] & kExitBit) != 0, &ctl->error);
+          static_cast<float *>(F.v)[pos] = nv;
+          if (pos >= lo_l && pos < hi_l) {
+            if (np < kKeep) {
+#pragma unroll
+              for (int k = 0; k < kKeep; ++k)
+                if (k == np) { keep_pos[k] = int(pos - lo_l); keep_v[k] = nv; }
+              ++np;
+            } else {
+              overflow = true;
+            }
           }
         }
       }
@@ -285,7 +340,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       __threadfence();
       fence_proxy_async_global();
     }
-    scatter(tb - 1);
+    scatter(tb - 1, false);
     CHUNK_STAMP(1);
 
     int slot = 0;
@@ -322,9 +377,8 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
         }
         __syncthreads();
       }
-      if (t - 1 >= ta) stage(t - 1, S.tlo[tq - 1]);
+      if (t - 1 >= ta) stage(t - 1, S.tlo[tq - 1], true);
       S.nzw[(t + 1) % 3][tid] = 0u;   // tile t+1's bits are no longer read
-      if (t - 1 >= ta) scatter(t - 1);
       const int nh = gb - ga;
       int dpre[kPF];
 #pragma unroll
@@ -546,6 +600,12 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
         }
       }
       if (myopen != INT_MAX) atomicMin(&S.hopen, myopen);
+      // tile t-1's column bits (its entries were copied with the tile, a tile's work ago), ordered
+      // before their reads by the barrier at the top of the next iteration
+      if (t - 1 >= ta) {
+        cp_async_wait_all();
+        scatter(t - 1, true);
+      }
       fence_proxy_async_smem();   // this tile's buffer is rewritten by a later copy
       slot ^= 1;
     }

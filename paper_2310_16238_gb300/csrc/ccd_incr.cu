@@ -346,6 +346,31 @@ static __device__ void inc_load_list(const IncParams &prm, int t, int j, int lo,
   if (int(threadIdx.x) == th0) *cnt = n;
 }
 
+// inc_load_list for a column whose entry range in the tile (first entry qa, n entries) is known: the
+// positions are stored at once, eta and v at them are copied asynchronously (cp.async; each thread
+// waits for its own copies with cp_async_wait_all before the barrier that precedes their use).
+static __device__ void inc_load_list_async(const IncParams &prm, int64_t qa, int n, int lo, int npos, uint32_t *lp,
+                                           dw *lv, double *le, int *cnt, int th0, int nth, int *serr, int cap) {
+  const DevData &D = prm.D;
+  if (n > cap || n < 0) {
+    if (int(threadIdx.x) == th0) atomicCAS(serr, 0, COX_E_INVALID);
+    n = 0;
+  }
+#pragma unroll 1
+  for (int m = int(threadIdx.x) - th0; m >= 0 && m < n; m += nth) {
+    const uint32_t e = D.idx[qa + m];
+    int q = int(e & kPosMask) - lo;
+    if (q < 0 || q >= npos) {
+      atomicCAS(serr, 0, COX_E_INVALID);
+      q = 0;
+    }
+    lp[m] = uint32_t(q) | (e & kExitBit);
+    cp_async8(&lv[m], &prm.vdw[lo + q]);
+    cp_async8(&le[m], &prm.F.eta[lo + q]);
+  }
+  if (int(threadIdx.x) == th0) *cnt = n;
+}
+
 // Inclusive segmented suffix sum of one sequence held one element per thread (element k = thread
 // k, k < nact; later elements are 0 and end their segments); f = 1 marks the last element of a
 // segment. Warps past nact skip the arithmetic. Results go to out[k] for k < nact.
@@ -633,6 +658,11 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
   __shared__ double s_half_inv_var;
   __shared__ dw s_inv_var_dw, s_lambda_dw;
   __shared__ IncPre s_pre;
+  // the entry range in this tile of the column two steps ahead, fetched a step before its list:
+  // its first entry (col_ptr), the column's tile offsets (col_tile [t], [t + 1]), halt flag
+  __shared__ int64_t s_nbq[2];
+  __shared__ int32_t s_nbt[2][2];
+  __shared__ int32_t s_nbh[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const DevFit &F = prm.F;
@@ -797,6 +827,13 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       inc_load_list(prm, t, j2, lo, npos, lpos + 2 * LC, lv + 2 * LC, le + 2 * LC, &s_cnt[2], 0, kIncThreads, &s_err,
                     LC);
     }
+  }
+  if (tid == 0 && st.state == kRunning) {   // the range of the column the first step fetches
+    const int jf0 = (st.j + 2) % p;
+    s_nbq[0] = D.col_ptr[jf0];
+    s_nbt[0][0] = prm.col_tile[int64_t(jf0) * (C + 1) + t];
+    s_nbt[0][1] = prm.col_tile[int64_t(jf0) * (C + 1) + t + 1];
+    s_nbh[0] = prm.halt ? prm.halt[jf0] : 0;
   }
   __syncthreads();
   if (st.state == kRunning) {   // the first column's lookups (later ones are built a step ahead)
@@ -1084,8 +1121,9 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
     if (tid == 0 && s_err) atomicCAS(&ctl->error, 0, s_err);
     if (trace) trace[11] = uint64_t(clock64());
     // ---- 5. the inbox: one thread per writer; meanwhile the other threads fetch column j+2's
-    //         entries with eta and v as of this step's update
-    const int jf = (j + 2) % p;
+    //         entries (its range fetched a step ago) with eta and v as of this step's update,
+    //         copied asynchronously: the barrier after the inbox waits for no memory round trip
+    //         but the records'
     if (tid < C) {
       uint64_t r[kIncRec];
       unsigned polls = 0;
@@ -1124,11 +1162,19 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
 #pragma unroll 1
         for (int k = tid - C; k < nnx; k += kIncThreads - C) fce[k] = inc_seg_end(lp_n, nnx, k, cutb, cutp);
       }
-      if (prm.halt && prm.halt[jf]) {   // the launch ends before it
+      const int nb = base & 1;
+      if (tid == kIncThreads - 2) {   // the range of the column the next step fetches (j + 3)
+        const int jn3 = (j + 3) % p;
+        cp_async8(&s_nbq[nb ^ 1], D.col_ptr + jn3);
+        cp_async4(&s_nbt[nb ^ 1][0], prm.col_tile + int64_t(jn3) * (C + 1) + t);
+        cp_async4(&s_nbt[nb ^ 1][1], prm.col_tile + int64_t(jn3) * (C + 1) + t + 1);
+        s_nbh[nb ^ 1] = prm.halt ? prm.halt[jn3] : 0;
+      }
+      if (s_nbh[nb]) {   // the launch ends before it
         if (tid == C) s_cnt[sf] = 0;
       } else {
-        inc_load_list(prm, t, jf, lo, npos, lpos + sf * LC, lv + sf * LC, le + sf * LC, &s_cnt[sf], C, kIncThreads - C,
-                      &s_err, LC);
+        inc_load_list_async(prm, s_nbq[nb] + s_nbt[nb][0], s_nbt[nb][1] - s_nbt[nb][0], lo, npos, lpos + sf * LC,
+                            lv + sf * LC, le + sf * LC, &s_cnt[sf], C, kIncThreads - C, &s_err, LC);
       }
     }
     __syncthreads();
@@ -1233,6 +1279,7 @@ static __device__ __forceinline__ void incr_body(const IncParams &prm, const int
       st.epoch = epoch + 1u;
       if (trace) trace[15] = uint64_t(clock64());
     }
+    cp_async_wait_all();   // the fetched list's eta and v, the next range (issued during the inbox wait)
     __syncthreads();
     ++base;
   }

@@ -181,31 +181,41 @@ def dtype_of(engine, s_e):
 
 
 def roofline_of(engine, data, beta, G, K, s_e, step_us, wname, precision_name):
-    """Roofline of the coordinate-step kernel. `achieved` = the paper's dense method's algorithmic
-    bytes per coordinate step x the steps one launch runs / the launch's CUDA-event time, against
-    the measured HBM copy bandwidth. For the incremental kernel (which reads only the changed
-    positions) the line also gives its own bytes and the latency floor of a step."""
+    """Roofline of the coordinate-step kernel against the measured HBM copy bandwidth: `achieved` =
+    the kernel's algorithmic bytes per coordinate step x the steps one launch runs / the launch's
+    CUDA-event time. A dense engine's bytes are the paper's dense scan (every position read); the
+    incremental kernel's are its own (column j's entries and the changed positions), with the
+    latency floor of its step beside them and, labelled effective, the bandwidth the dense scan
+    would need to match its step time."""
     M = data.n if data.start is None else 2 * data.n
     nnz_mean = float(np.diff(data.col_ptr).mean())
     nnz_pos = nnz_mean * (2.0 if data.start is not None else 1.0)
     moved = bool(np.count_nonzero(beta) > 0)
     peak, src = hbm_peak()
     dense = dense_bytes_per_step(M, G, K, nnz_pos, s_e, moved)
-    achieved = dense / (step_us * 1e-6) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get((engine, wname.split()[0], precision_name)),
-            "kernel": f"coordinate step ({engine})", "step_us": step_us, "alg_bytes_per_step": dense,
-            "basis": "bytes of the paper's dense scan per coordinate step x steps per launch / launch time",
-            "peak_source": src}
-    if engine == "incremental":
-        own = incr_own_bytes_per_step(M, data.p, nnz_pos, s_e, moved)
-        own_gbs = own / (step_us * 1e-6) / 1e9
-        roof["own_bytes"] = {"per_step": own, "gbs": own_gbs, "frac": own_gbs / peak,
-                             "note": "the incremental kernel reads only column j's entries and the changed "
-                                     "positions; it is bound by the latency of its step, not by bytes"}
-        roof["latency"] = {"step_us": step_us, "floor_us": EXCHANGE_FLOOR_US, "frac": EXCHANGE_FLOOR_US / step_us,
-                           "floor": "one cross-SM exchange round trip per coordinate step"}
-    return roof
+    dense_gbs = dense / (step_us * 1e-6) / 1e9
+    traffic = TRAFFIC.get((engine, wname.split()[0], precision_name))
+    if engine != "incremental":
+        return {"bound": "hbm", "achieved": dense_gbs, "peak": peak, "unit": "GB/s", "frac": dense_gbs / peak,
+                "traffic": traffic, "kernel": f"coordinate step ({engine})", "step_us": step_us,
+                "alg_bytes_per_step": dense,
+                "basis": "bytes of the paper's dense scan per coordinate step x steps per launch / launch time",
+                "peak_source": src}
+    own = incr_own_bytes_per_step(M, data.p, nnz_pos, s_e, moved)
+    own_gbs = own / (step_us * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": own_gbs, "peak": peak, "unit": "GB/s", "frac": own_gbs / peak,
+            "traffic": traffic, "kernel": "coordinate step (incremental)", "step_us": step_us,
+            "alg_bytes_per_step": own,
+            "basis": "the incremental kernel's own bytes per coordinate step (column j's entries with eta "
+                     "and v, the update's writes, the dense refresh once per sweep) / step time",
+            "peak_source": src,
+            "binding": "latency, not bytes: a step is a chain of barrier-separated phases around one "
+                       "cross-SM exchange",
+            "latency": {"step_us": step_us, "floor_us": EXCHANGE_FLOOR_US, "frac": EXCHANGE_FLOOR_US / step_us,
+                        "floor": "one cross-SM exchange round trip per coordinate step"},
+            "effective_dense": {"achieved": dense_gbs, "frac": dense_gbs / peak, "alg_bytes_per_step": dense,
+                                "note": "effective, not moved: the bandwidth the paper's dense scan (every "
+                                        "position read per step) would need to match this step time"}}
 
 
 def _device_copy(data, dev):
@@ -399,6 +409,7 @@ def run_batch(args, sub=False):
                                (cox.COX_FP64, "batched_fp64", cox.COX_ENGINE_STREAM),
                                (cox.COX_FP64, "batched_incremental", cox.COX_ENGINE_AUTO)):
         tile = autotune.batch_tile(sets, prec) if engine == cox.COX_ENGINE_STREAM else 0
+        plan = autotune.batch_chunk_plan(sets) if prec == cox.COX_FP32C and engine == cox.COX_ENGINE_STREAM else None
         handles = []
         for d, ol in sets:
             base = cox.Handle(d, ol[0], precision=prec, tile=tile, engine=engine, stream=stream.cuda_stream)
@@ -411,6 +422,7 @@ def run_batch(args, sub=False):
         err, mism = errors(betas, infos)
         r = {"fits_per_s": n_fits / sec, "seconds": sec, "device_ms": dev_ms,
              "engine": ENGINE_NAMES.get(infos[0]["engine"], "unknown"), "tile": tile or None,
+             "chunks_per_cta": plan,
              "max_rel_beta_err_vs_plain_fp64": err, "sweep_mismatches_vs_plain_fp64": mism,
              "gpu_launches": int(launches),
              "speedup_vs_plain": (n_fits / sec) / out["plain_fp64"]["fits_per_s"], "clocks": clk.summary()}
@@ -431,6 +443,8 @@ def run_batch(args, sub=False):
         out[name] = r
         for hh in handles:
             hh.close()
+        if plan is not None:
+            cox.cox_set_chunk_plan(0)
     best = max(("batched_fp32c", "batched_fp64", "batched_incremental"), key=lambda k: out[k]["fits_per_s"])
     out["best"] = best
     out["fits_per_s"] = out[best]["fits_per_s"]

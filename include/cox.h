@@ -332,6 +332,22 @@ int cox_debug_set_wait_limit(long long clocks);
  * COX_E_INVALID for a value outside 0..64. */
 int cox_debug_set_chunk_tiles(int32_t tiles);
 
+/* Chunks per resident CTA in the FP32C streaming kernel's plans (1..8; 0 restores the library's
+ * default). With more than one, a CTA that finishes its chunk takes the next one of the work list,
+ * so that cheap chunks (fits whose step reads the tie groups' cached S0) free their CTAs for the
+ * others. A schedule parameter of the plan (chosen by the autotuner for batches): it changes the
+ * summation order only, not the method. Applies to work lists built afterwards, process-wide.
+ * Returns COX_OK, or COX_E_INVALID for a value outside 0..8. */
+int cox_set_chunk_plan(int32_t chunks_per_cta);
+
+/* The FP32C streaming kernel's cached-S0 path. A coordinate step of a fit whose eta has not changed
+ * since its previous step (that step's update was 0, as for every coefficient an L1 penalty keeps
+ * at 0) needs no new risk-set sums S0 at its tie groups (eq. parallel_d: the sums of exp(eta) are
+ * those of the previous step); the kernel keeps them from one step to the next and then computes
+ * only column j's S1 (S2) from the column's entries. On by default; `enable` = 0 turns it off for
+ * work lists built afterwards, process-wide (for tests that compare the two paths). Returns COX_OK. */
+int cox_debug_set_cached_s0(int32_t enable);
+
 /* ---------------------------------------------------------------- primitives
  * Segmented inclusive scan with the flag-value operator of §2.6 ("Efficient parallel
  * segmented-scan on GPUs"): out[i] = sum of a[k] for k from the last index h <= i with

@@ -27,7 +27,7 @@ COX_ENGINE_AUTO, COX_ENGINE_STREAM, COX_ENGINE_RESIDENT, COX_ENGINE_INCR = 0, 1,
 EXPORTS = ["cox_set_allocator", "cox_create", "cox_set_options", "cox_fit", "cox_loglik", "cox_gradient",
            "cox_risk_sums", "cox_metadata", "cox_dx", "cox_destroy", "cox_last_error", "cox_batch_fit",
            "cox_clone", "cox_footprint", "cox_launch_count", "cox_segscan", "cox_split_columns", "cox_create_split", "cox_cv_path",
-           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_debug_set_chunk_tiles", "cox_shard_setup", "cox_shard_head",
+           "cox_segscan_noalloc", "cox_debug_set_wait_limit", "cox_debug_set_chunk_tiles", "cox_set_chunk_plan", "cox_debug_set_cached_s0", "cox_shard_setup", "cox_shard_head",
            "cox_shard_partial", "cox_shard_step", "cox_shard_beta", "cox_server_create", "cox_server_submit", "cox_server_poll",
            "cox_server_wait", "cox_server_cancel", "cox_server_stats_get", "cox_server_destroy"]
 
@@ -129,6 +129,8 @@ def lib():
             L.cox_segscan_noalloc.argtypes = [vp, vp, i64, vp, vp]
             L.cox_debug_set_wait_limit.argtypes = [C.c_longlong]
             L.cox_debug_set_chunk_tiles.argtypes = [C.c_int32]
+            L.cox_set_chunk_plan.argtypes = [C.c_int32]
+            L.cox_debug_set_cached_s0.argtypes = [C.c_int32]
             L.cox_shard_setup.argtypes = [vp, vp, i32]
             L.cox_shard_head.argtypes = [vp, i32, vp]
             L.cox_shard_partial.argtypes = [vp, i32, vp, i32, vp]
@@ -413,6 +415,18 @@ def cox_debug_set_chunk_tiles(tiles: int) -> None:
     """Tiles per chunk of the FP32C streaming kernel for work lists built afterwards (0: the
     library's choice). For tests of multi-tile chunks on small data."""
     _check(lib().cox_debug_set_chunk_tiles(int(tiles)))
+
+
+def cox_set_chunk_plan(chunks_per_cta: int) -> None:
+    """Chunks per resident CTA in the FP32C streaming kernel's plans for work lists built
+    afterwards (0: the library's default; 1..8)."""
+    _check(lib().cox_set_chunk_plan(int(chunks_per_cta)))
+
+
+def cox_debug_set_cached_s0(enable: bool) -> None:
+    """Turn the FP32C streaming kernel's cached-S0 path on or off for work lists built afterwards
+    (on by default). For tests that compare it with the full pass."""
+    _check(lib().cox_debug_set_cached_s0(1 if enable else 0))
 
 
 def cox_segscan(a, head_flags, out=None, stream=None):

@@ -145,12 +145,18 @@ WorkItem work_item(const cox_handle *h, int f, int t) {
 
 // Tiles per chunk forced for every plan (0: automatic), set by cox_debug_set_chunk_tiles.
 std::atomic<int> g_chunk_tiles{0};
+// Chunks per resident CTA of the chunked kernel's plans (cox_set_chunk_plan): the kernel hands out
+// chunks past the first one per CTA in work-list order.
+std::atomic<int> g_chunks_per_cta{kChunksPerCtaDefault};
+// The chunked kernel's cached-S0 path admitted in plans built afterwards (cox_debug_set_cached_s0).
+std::atomic<int> g_cached_s0{1};
 
 // Chunk plan of the FP32C chunked kernel for fits of T[i] tiles sharing `slots` resident CTAs: the
 // smallest chunk length C (tiles, at most kChunkMaxTiles) for which the fits' chunk counts
 // ceil(T[i] / C) add up to at most `slots`, so one launch gives every CTA at most one chunk (the
 // kernel assigns chunks to CTAs statically). Returns each fit's chunk count.
 std::vector<int> plan_chunks(const std::vector<int64_t> &T, int slots) {
+  slots *= std::max(1, g_chunks_per_cta.load());
   auto total = [&](int64_t C) {
     int64_t s = 0;
     for (int64_t t : T) s += (t + C - 1) / C;
@@ -180,10 +186,16 @@ std::vector<WorkItem> fit_items(const cox_handle *h, int f, int nck) {
   std::vector<WorkItem> out;
   const int64_t T = D(h).T;
   if (h->sd->precision == COX_FP32C) {
-    const std::vector<int32_t> &lo = h->sd->prep.h_tile_lo;
+    const std::vector<int32_t> &lo = h->sd->prep.h_tile_lo, &tg = h->sd->prep.h_tile_g;
+    // the cached-S0 path's limits hold for every chunk of this plan (strata, tie groups per chunk)
+    int fast_ok = g_cached_s0.load() != 0 && D(h).K <= kChunkFastCuts;
+    for (int c = 0; c < nck && fast_ok; ++c) {
+      const int ta = int(int64_t(c) * T / nck), tb = int(int64_t(c + 1) * T / nck);
+      fast_ok = tg[size_t(tb)] - tg[size_t(ta)] <= kChunkFastH;
+    }
     for (int c = nck - 1; c >= 0; --c) {
       const int ta = int(int64_t(c) * T / nck), tb = int(int64_t(c + 1) * T / nck);
-      const ChunkItem ci{f, c, ta, tb, nck, lo[size_t(tb - 1)], {0, 0}};
+      const ChunkItem ci{f, c, ta, tb, nck, lo[size_t(tb - 1)], fast_ok, 0};
       WorkItem w;
       std::memcpy(&w, &ci, sizeof(w));
       out.push_back(w);
@@ -234,6 +246,7 @@ int alloc_fit_state(cox_handle *h) {
     h->hfit.head_bits = hd.head_bits;
     h->hfit.val = hd.val;
     h->hfit.T = hd.T;
+    h->hfit.p = hd.p;
   }
   h->ctl = static_cast<FitCtl *>(B.get(sizeof(FitCtl)));
   h->lc = static_cast<LaunchCtl *>(B.get(sizeof(LaunchCtl)));
@@ -1358,6 +1371,17 @@ int cox_debug_set_wait_limit(long long clocks) {
   return COX_OK;
 }
 
+int cox_debug_set_cached_s0(int32_t enable) {
+  g_cached_s0.store(enable != 0);
+  return COX_OK;
+}
+
+int cox_set_chunk_plan(int32_t chunks_per_cta) {
+  if (chunks_per_cta < 0 || chunks_per_cta > 8) return fail(nullptr, COX_E_INVALID, "cox_set_chunk_plan: 0 to 8");
+  g_chunks_per_cta.store(chunks_per_cta == 0 ? kChunksPerCtaDefault : chunks_per_cta);
+  return COX_OK;
+}
+
 int cox_debug_set_chunk_tiles(int32_t tiles) {
   if (tiles < 0 || tiles > kChunkMaxTiles) return fail(nullptr, COX_E_INVALID, "cox_debug_set_chunk_tiles: 0 to 64");
   g_chunk_tiles.store(tiles);
@@ -1457,6 +1481,8 @@ int cox_batch_fit(cox_handle *const *hs, int32_t n, const double *const *beta0, 
     for (int i = 0, r = 0; i < n; ++i)
       if (running[i]) {
         if (precision == COX_FP32C && clear_lookback(hs[i], s)) return cuda_fail(nullptr, "memset");
+        // the cached-S0 path was admitted under the old chunk layout: the next launch takes the full one
+        if (cudaMemsetAsync(&ctls[i].s0c_tag, 0, sizeof(uint32_t), s) != cudaSuccess) return cuda_fail(nullptr, "memset");
         lists.push_back(fit_items(hs[i], i, nck[r++]));
       }
     const std::vector<WorkItem> it = interleave(lists);
@@ -1811,6 +1837,8 @@ int rebuild_batch(cox_server *S) {
   for (size_t sl = 0, r = 0; sl < S->slots.size(); ++sl)
     if (Req *q = S->slots[sl]) {
       if (S->o.precision == COX_FP32C && clear_lookback(q->h, S->run_stream)) return COX_E_CUDA;
+      // the cached-S0 path was admitted under the old chunk layout: the next launch takes the full one
+      if (cudaMemsetAsync(&S->ctls[sl].s0c_tag, 0, sizeof(uint32_t), S->run_stream) != cudaSuccess) return COX_E_CUDA;
       lists.push_back(fit_items(q->h, int(sl), nck[r++]));
     }
   const std::vector<WorkItem> it = interleave(lists);

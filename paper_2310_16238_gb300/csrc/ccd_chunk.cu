@@ -92,7 +92,8 @@ struct ChunkSmem {
   int32_t wf[kCW];                                         // warp holds a stratum end
   Acc cc[2][NV];                                           // the chunk carry into the current tile
   int32_t ccf[2];                                          // that carry stopped at a stratum end
-  int32_t hopen, last;
+  int32_t hopen, last, next;
+  int32_t fsc[2][kCW];                                     // cached-S0 path: stratum ends / tie groups per warp
   uint64_t mbar[2];                                        // tile copy completion, per buffer
   double red[3][kCW];
   double scratch[3 * 32];
@@ -158,7 +159,7 @@ constexpr long long kTmaWait = 1ll << 32;
 // is due) from its risk-set sums sh = (S0, S1[, S2]).
 template <int NV>
 __device__ __forceinline__ void add_group(const Acc (&sh)[NV], int dgi, int j, bool need_ll, Acc &g1q, Acc &g2q,
-                                          double &llq, const DevFit &F, int gidx) {
+                                          double &llq, const DevFit &F, int gidx, bool cache) {
   const float S0 = sh[0].s + sh[0].c, S1 = sh[1].s + sh[1].c;
   const float fd = float(dgi);
   if (j >= 0) {
@@ -173,6 +174,352 @@ __device__ __forceinline__ void add_group(const Acc (&sh)[NV], int dgi, int j, b
     F.out_S0[gidx] = P::to64(sh[0]);
     F.out_S1[gidx] = P::to64(sh[1]);
   }
+  // the group's risk-set sum, kept for the fit's next launch (read when eta has not changed)
+  if (cache) reinterpret_cast<float2 *>(F.hscr)[3 * int64_t(gidx)] = make_float2(sh[0].s, sh[0].c);
+}
+
+// Warp 0: publish the chunk's aggregate (its sums from its first position up to its first stratum
+// end, final when a stratum ends in the chunk: AF) and, when need_lb, look back over the fit's later
+// chunks for the carry into the chunk's last stratum (epoch-tagged words: aggregate 0..2,
+// inclusive 3..5 per chunk). The carry goes to cr_out; a chunk without a stratum end then publishes
+// aggregate + carry as its inclusive value. A wait past `spin` clocks raises COX_E_TIMEOUT.
+template <int NV>
+__device__ void chunk_lookback(uint64_t *cwd, int c, int nc, const double (&agg)[NV], int AF, bool need_lb,
+                               uint32_t etag, long long spin, FitCtl *ctl, LaunchCtl *lc, double *cr_out) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + (AF ? 3 : 0) + i], tag_word(agg[i], etag));
+  double cr[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) cr[i] = 0.0;
+  if (need_lb) {
+    int base = c + 1;
+    const long long t0 = clock64();
+    bool timed_out = false;
+    for (;;) {
+      const int u = base + lane;
+      double val[NV];
+      int vi = 0, va = 0;
+      for (;;) {
+        vi = 0;
+        va = 0;
+        if (u < nc) {
+          uint64_t wv[NV];
+          bool ok = true;
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            wv[i] = ld_relaxed_u64(&cwd[6 * u + 3 + i]);
+            ok = ok && (wv[i] & 15u) == etag;
+          }
+          if (!ok) {
+            ok = true;
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+              wv[i] = ld_relaxed_u64(&cwd[6 * u + i]);
+              ok = ok && (wv[i] & 15u) == etag;
+            }
+            va = ok;
+          } else {
+            vi = 1;
+          }
+#pragma unroll
+          for (int i = 0; i < NV; ++i) val[i] = word_value(wv[i]);
+        } else {   // past the fit's last chunk
+          vi = 1;
+#pragma unroll
+          for (int i = 0; i < NV; ++i) val[i] = 0.0;
+        }
+        const uint32_t inv = __ballot_sync(0xffffffffu, !(vi || va));
+        const uint32_t inc = __ballot_sync(0xffffffffu, vi);
+        if (inv == 0u || (inc != 0u && __ffs(inc) < __ffs(inv))) break;
+        if (clock64() - t0 > spin) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (timed_out) {
+        if (lane == 0) {
+          atomicExch(&ctl->error, COX_E_TIMEOUT);
+          atomicExch(&lc->error, COX_E_TIMEOUT);
+        }
+        break;
+      }
+      const uint32_t inc = __ballot_sync(0xffffffffu, vi);
+      const int stop = inc ? __ffs(inc) - 1 : 31;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        double xv = lane <= stop ? val[i] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) xv += __shfl_down_sync(0xffffffffu, xv, off);
+        cr[i] += __shfl_sync(0xffffffffu, xv, 0);
+      }
+      if (inc) break;
+      base += 32;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) cr_out[i] = cr[i];
+    if (!AF && (need_lb || c + 1 == nc))
+#pragma unroll
+      for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + 3 + i], tag_word(agg[i] + cr[i], etag));
+  }
+}
+
+// ---- the cached-S0 path: a launch of a fit whose eta is unchanged since its previous launch (no
+// pending update) reads every tie group's S0 from that launch (kept beside the group's scratch) and
+// computes column j's S1 (S2) from its entries alone: per chunk O(entries + tie groups) instead of
+// a pass over every position. Its arrays lie over the tile buffers (and, valued, the value buffers).
+template <int NV>
+struct FastView {
+  uint32_t epos[kChunkFastE];         // column j's entries in the chunk: position from the chunk's first
+  uint16_t erk[kChunkFastE];          // their stratum rank in the chunk (stratum ends before them)
+  int32_t cut[kChunkFastCuts];        // the chunk's stratum ends (positions from its first)
+  uint16_t hcode[kChunkFastH];        // per tie group: its first entry at or after its position
+                                      // (bits 0-11), that entry lies in its stratum (bit 12), its
+                                      // stratum continues past the chunk (bit 13)
+  Acc es[NV - 1][kChunkFastE];        // x v (x^2 v) per entry, then their segmented suffix sums
+};
+static_assert(kChunkFastE <= 4096, "entry index in 12 bits");
+static_assert(sizeof(FastView<2>) <= sizeof(float) * 2 * kChunkTile, "cached-S0 arrays fit the tile buffers");
+static_assert(sizeof(FastView<3>) <= sizeof(float) * 4 * kChunkTile, "cached-S0 arrays fit the tile and value buffers");
+
+// The chunk's partial (G1, G2[, sum d log S0]) on the cached-S0 path, into g1q, g2q, llq. The
+// caller staged the chunk's last tile before it knew the path: its copy lands before the buffers
+// are reused. Limits (strata, tie groups, entries) are admitted by the host plan and the previous
+// launch; a chunk past them raises COX_E_INVALID and adds nothing.
+template <int NV>
+__device__ void fast_chunk(ChunkSmem<NV> &S, const DevFit &F, FitCtl *ctl, LaunchCtl *lc, int c, int nc, int nt, int tb,
+                           int j, int64_t cbj, bool vf, bool need_ll, uint32_t etag, long long spin, uint32_t &ph,
+                           bool &tma_late, Acc &g1q, Acc &g2q, double &llq) {
+  constexpr bool VAL = NV == 3;
+  constexpr int NS = NV - 1;
+  FastView<NV> &V = *reinterpret_cast<FastView<NV> *>(&S.v[0][0]);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P0 = S.tlo[0], span = S.tlo[nt] - P0;
+  const int W0 = P0 >> 5, nw = (span + 31) >> 5;     // the chunk's bitmap words (P0 is a multiple of 32)
+  const int wpt = (nw + kCT - 1) / kCT;                // a run of consecutive words per thread
+  const int wa = min(nw, tid * wpt), wb = min(nw, wa + wpt);
+  const int64_t q0 = cbj + S.ctj[0];
+  const int ne = S.ctj[nt] - S.ctj[0];
+  auto wmask = [&](int w) {
+    const int r = span - 32 * w;
+    return r >= 32 ? 0xffffffffu : ((1u << r) - 1u);
+  };
+  // 1. stratum ends and tie groups per thread; their bases over the CTA
+  int ncut = 0, nhd = 0;
+  for (int w = wa; w < wb; ++w) {
+    const uint32_t m = wmask(w);
+    ncut += __popc(F.cut_bits[W0 + w] & m);
+    nhd += __popc(F.head_bits[W0 + w] & m);
+  }
+  int ic = ncut, ih = nhd;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, ic, off), z = __shfl_up_sync(0xffffffffu, ih, off);
+    if (lane >= off) {
+      ic += y;
+      ih += z;
+    }
+  }
+  if (lane == 31) {
+    S.fsc[0][warp] = ic;
+    S.fsc[1][warp] = ih;
+  }
+  // the staged tile's copy lands before its buffer is reused
+  {
+    const int b = (tb - 1) & 1;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&S.mbar[b], (ph >> b) & 1u))
+      if (clock64() - t0 > kTmaWait) {
+        tma_late = true;
+        break;
+      }
+    ph ^= 1u << b;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  int cb = ic - ncut, hb = ih - nhd, nC = 0, nH = 0;
+#pragma unroll
+  for (int q = 0; q < kCW; ++q) {
+    if (q < warp) {
+      cb += S.fsc[0][q];
+      hb += S.fsc[1][q];
+    }
+    nC += S.fsc[0][q];
+    nH += S.fsc[1][q];
+  }
+  if (nC > kChunkFastCuts || nH > kChunkFastH || ne > kChunkFastE || ne < 0 || tma_late) {   // uniform
+    if (tid == 0) atomicCAS(&ctl->error, 0, tma_late ? COX_E_TIMEOUT : COX_E_INVALID);
+    if (warp == 0) {   // final zeros, so that no chunk of the fit waits for this one
+      const double z[NV] = {};
+      chunk_lookback<NV>(reinterpret_cast<uint64_t *>(F.tval), c, nc, z, 1, false, etag, spin, ctl, lc, S.cr);
+    }
+    return;
+  }
+  // 2. the stratum ends in order; column j's entries: positions, x v (x^2 v)
+  {
+    int k = cb;
+    for (int w = wa; w < wb; ++w)
+      for (uint32_t m = F.cut_bits[W0 + w] & wmask(w); m; m &= m - 1u) V.cut[k++] = 32 * w + __ffs(m) - 1;
+  }
+  const float *vg = static_cast<const float *>(F.v);
+  for (int k = tid; k < ne; k += kCT) {
+    const int pos = int(F.idx[q0 + k] & kPosMask) - P0;
+    V.epos[k] = uint32_t(pos);
+    const float vv = vg[P0 + pos];
+    const float x = vf ? float(F.val[q0 + k]) : 1.0f;
+    V.es[0][k] = Acc{x * vv, 0.f};
+    if constexpr (VAL) V.es[1][k] = Acc{x * (x * vv), 0.f};
+  }
+  __syncthreads();
+  for (int k = tid; k < ne; k += kCT) {   // stratum ends before each entry
+    const int pos = int(V.epos[k]);
+    int lo = 0, hi = nC;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (V.cut[mid] < pos) lo = mid + 1;
+      else hi = mid;
+    }
+    V.erk[k] = uint16_t(lo);
+  }
+  __syncthreads();
+  // 3. segmented suffix sums over the entries (a stratum end between two entries ends a segment),
+  //    compensated: thread-local runs over consecutive entries, a warp scan of the runs, the warps
+  const int me = (ne + kCT - 1) / kCT;
+  const int ka = min(ne, tid * me), kb = min(ne, ka + me);
+  auto seg_end = [&](int k) { return k == ne - 1 || V.erk[k] != V.erk[k + 1]; };
+  int brk = 0;
+  {
+    Acc run[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) run[i] = P::zero();
+    for (int k = kb - 1; k >= ka; --k) {
+      if (seg_end(k)) {
+        brk = 1;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) run[i] = V.es[i][k];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) run[i] = P::comb(V.es[i][k], run[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) V.es[i][k] = run[i];
+    }
+  }
+  Acc I[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) I[i] = ka < kb ? V.es[i][ka] : P::zero();
+  int If = brk;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    Acc y[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) y[i] = P::shfl_down(I[i], off);
+    const int yf = __shfl_down_sync(0xffffffffu, If, off);
+    if (lane + off < 32) {
+      if (!If) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) I[i] = P::comb(I[i], y[i]);
+      }
+      If |= yf;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) S.wa[i][warp] = I[i];
+    S.wf[warp] = If;
+  }
+  __syncthreads();
+  {
+    Acc Cw[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) Cw[i] = P::zero();
+    for (int q = kCW - 1; q > warp; --q) {
+      if (S.wf[q]) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Cw[i] = S.wa[i][q];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Cw[i] = P::comb(S.wa[i][q], Cw[i]);
+      }
+    }
+    Acc E[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) E[i] = P::shfl_down(I[i], 1);
+    const int Ef = __shfl_down_sync(0xffffffffu, If, 1);
+    if (lane == 31) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) E[i] = Cw[i];
+    } else if (!Ef) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) E[i] = P::comb(E[i], Cw[i]);
+    }
+    for (int k = kb - 1; k >= ka && !seg_end(k); --k)   // the entries after the thread's last segment end
+#pragma unroll
+      for (int i = 0; i < NS; ++i) V.es[i][k] = P::comb(V.es[i][k], E[i]);
+  }
+  __syncthreads();
+  // 4. warp 0 publishes the chunk's sums up to its first stratum end and looks back for the carry
+  //    into its last stratum (S0 is not carried: every chunk of the fit reads its groups' S0);
+  //    meanwhile every thread codes its tie groups
+  if (warp == 0) {
+    double agg[NV];
+    agg[0] = 0.0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) agg[i + 1] = (ne > 0 && V.erk[0] == 0) ? P::to64(V.es[i][0]) : 0.0;
+    chunk_lookback<NV>(reinterpret_cast<uint64_t *>(F.tval), c, nc, agg, nC > 0, c + 1 < nc, etag, spin, ctl, lc, S.cr);
+  }
+  {
+    int r = cb, o = hb;
+    int k = 0;
+    {
+      int hi = ne;
+      const int p0 = 32 * wa;
+      while (k < hi) {
+        const int mid = (k + hi) >> 1;
+        if (int(V.epos[mid]) < p0) k = mid + 1;
+        else hi = mid;
+      }
+    }
+    for (int w = wa; w < wb; ++w) {
+      const uint32_t msk = wmask(w);
+      const uint32_t hm = F.head_bits[W0 + w] & msk, cm = F.cut_bits[W0 + w] & msk;
+      for (uint32_t m = hm | cm; m; m &= m - 1u) {
+        const int bit = __ffs(m) - 1, pos = 32 * w + bit;
+        if ((hm >> bit) & 1u) {
+          while (k < ne && int(V.epos[k]) < pos) ++k;
+          const uint32_t in = (k < ne && int(V.erk[k]) == r) ? 1u : 0u;
+          V.hcode[o++] = uint16_t((k < ne ? k : 0) | (in << 12) | (uint32_t(r == nC) << 13));
+        }
+        if ((cm >> bit) & 1u) ++r;
+      }
+    }
+  }
+  __syncthreads();
+  // 5. the tie groups' terms (consecutive threads take consecutive groups)
+  Acc CR[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) CR[i] = P::from64(S.cr[i + 1]);
+  const float2 *s0c = reinterpret_cast<const float2 *>(F.hscr);
+  const int g0 = S.tg[0];
+#pragma unroll 2
+  for (int h = tid; h < nH; h += kCT) {
+    const int code = V.hcode[h], g = g0 + h;
+    const float2 z = s0c[3 * int64_t(g)];
+    const int dg = F.head_d[g];
+    Acc sh[NV];
+    sh[0] = Acc{z.x, z.y};
+#pragma unroll
+    for (int i = 0; i < NS; ++i) sh[i + 1] = (code & (1 << 12)) ? V.es[i][code & 4095] : P::zero();
+    if (code & (1 << 13))
+#pragma unroll
+      for (int i = 0; i < NS; ++i) sh[i + 1] = P::comb(sh[i + 1], CR[i]);
+    add_group<NV>(sh, dg, j, need_ll, g1q, g2q, llq, F, g, false);
+  }
+  fence_proxy_async_smem();   // the tile buffers are rewritten by the next chunk's copies
 }
 
 template <int NV, bool kCond>
@@ -198,7 +545,15 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       tid == 0 && *reinterpret_cast<volatile int32_t *>(&lc->error) == 0 &&
       (mode != kModeFit || *reinterpret_cast<volatile int32_t *>(&lc->active) > 0));
 
-  for (int w = blockIdx.x; active && w < n_items; w += gridDim.x) {
+  // a CTA's first item is its index; later ones are taken in work-list order from the launch's
+  // ticket (a look-back waits only for items earlier in the list, all held by running CTAs)
+  auto next_item = [&]() {
+    if (n_items <= int(gridDim.x)) return n_items;
+    if (tid == 0) S.next = int(gridDim.x) + int(atomicAdd(&lc->ticket, 1u));
+    __syncthreads();
+    return S.next;
+  };
+  for (int w = blockIdx.x; active && w < n_items; w = next_item()) {
     CHUNK_STAMP(0);
     if (w != int(blockIdx.x)) it = items[w];
     const DevFit &F = fits[it.f];
@@ -243,9 +598,16 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     const double pend_db = ctl->pend_db;
     const uint32_t epoch = ctl->epoch;
     const uint32_t etag = epoch % 15u + 1u;   // never 0: zeroed words are never current
+    const uint32_t s0tag = mode == kModeFit ? ctl->s0c_tag : 0u;
     const double shift = F.shift;
     vf = VAL && F.val != nullptr;
     cbj = j >= 0 ? F.col_ptr[j] : 0;
+    // the next column's entries in this chunk: whether the next launch's cached-S0 path admits it
+    int ent_next = 0;
+    if (mode == kModeFit && tid == 0 && j >= 0) {
+      const int32_t *ctn = F.col_tile + int64_t(j + 1 < F.p ? j + 1 : 0) * (T_ + 1);
+      ent_next = ctn[tb] - ctn[ta];
+    }
 
     // ---- the chunk's tables
     for (int q = tid; q <= nt; q += kCT) {
@@ -261,6 +623,15 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       S.hopen = INT_MAX;
     }
     __syncthreads();
+
+    // eta unchanged since the fit's previous launch (no pending update), which admitted the cached-S0
+    // path for this one: every chunk of the fit reads its tie groups' S0 from that launch
+    const bool fastfit = mode == kModeFit && pend_j < 0 && s0tag == epoch && it.fast_ok != 0;
+    Acc g1q = P::zero(), g2q = P::zero();
+    double llq = 0.0;
+    if (fastfit) {
+      fast_chunk<NV>(S, F, ctl, lc, c, nc, nt, tb, j, cbj, vf, need_ll, etag, spin, ph, tma_late, g1q, g2q, llq);
+    } else {
 
     // column j's entries of tile t -> per-thread bits (and values): the thread's entries that
     // stage() copied (staged), then any beyond them from global memory
@@ -344,8 +715,6 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     CHUNK_STAMP(1);
 
     int slot = 0;
-    Acc g1q = P::zero(), g2q = P::zero();
-    double llq = 0.0;
     for (int t = tb - 1; t >= ta; --t) {
       const int b = t & 1, tq = t - ta;
       const int lo = S.tlo[tq], hi = S.tlo[tq + 1], ga = S.tg[tq], gb = S.tg[tq + 1];
@@ -596,7 +965,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
           for (int i = 0; i < NV; ++i) hs[i] = make_float2(sh[i].s, sh[i].c);
           myopen = min(myopen, gidx);
         } else {
-          add_group<NV>(sh, dgi, j, need_ll, g1q, g2q, llq, F, gidx);
+          add_group<NV>(sh, dgi, j, need_ll, g1q, g2q, llq, F, gidx, mode == kModeFit);
         }
       }
       if (myopen != INT_MAX) atomicMin(&S.hopen, myopen);
@@ -638,86 +1007,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
 #pragma unroll
       for (int i = 0; i < NV; ++i) agg[i] = P::to64(S.cc[slot][i]);
       const int AF = S.ccf[slot];   // a stratum ends in the chunk: its sums from the first position are final
-      if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + (AF ? 3 : 0) + i], tag_word(agg[i], etag));
-      double cr[NV];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) cr[i] = 0.0;
-      const bool need_lb = c + 1 < nc && (hopen < gbc || !AF);
-      if (need_lb) {
-        int base = c + 1;
-        const long long t0 = clock64();
-        bool timed_out = false;
-        for (;;) {
-          const int u = base + lane;
-          double val[NV];
-          int vi = 0, va = 0;
-          for (;;) {
-            vi = 0;
-            va = 0;
-            if (u < nc) {
-              uint64_t wv[NV];
-              bool ok = true;
-#pragma unroll
-              for (int i = 0; i < NV; ++i) {
-                wv[i] = ld_relaxed_u64(&cwd[6 * u + 3 + i]);
-                ok = ok && (wv[i] & 15u) == etag;
-              }
-              if (!ok) {
-                ok = true;
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                  wv[i] = ld_relaxed_u64(&cwd[6 * u + i]);
-                  ok = ok && (wv[i] & 15u) == etag;
-                }
-                va = ok;
-              } else {
-                vi = 1;
-              }
-#pragma unroll
-              for (int i = 0; i < NV; ++i) val[i] = word_value(wv[i]);
-            } else {   // past the fit's last chunk
-              vi = 1;
-#pragma unroll
-              for (int i = 0; i < NV; ++i) val[i] = 0.0;
-            }
-            const uint32_t inv = __ballot_sync(0xffffffffu, !(vi || va));
-            const uint32_t inc = __ballot_sync(0xffffffffu, vi);
-            if (inv == 0u || (inc != 0u && __ffs(inc) < __ffs(inv))) break;
-            if (clock64() - t0 > spin) {
-              timed_out = true;
-              break;
-            }
-            __nanosleep(32);
-          }
-          if (timed_out) {
-            if (lane == 0) {
-              atomicExch(&ctl->error, COX_E_TIMEOUT);
-              atomicExch(&lc->error, COX_E_TIMEOUT);
-            }
-            break;
-          }
-          const uint32_t inc = __ballot_sync(0xffffffffu, vi);
-          const int stop = inc ? __ffs(inc) - 1 : 31;
-#pragma unroll
-          for (int i = 0; i < NV; ++i) {
-            double xv = lane <= stop ? val[i] : 0.0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) xv += __shfl_down_sync(0xffffffffu, xv, off);
-            cr[i] += __shfl_sync(0xffffffffu, xv, 0);
-          }
-          if (inc) break;
-          base += 32;
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) S.cr[i] = cr[i];
-        if (!AF && (need_lb || c + 1 == nc))
-#pragma unroll
-          for (int i = 0; i < NV; ++i) st_relaxed_u64(&cwd[6 * c + 3 + i], tag_word(agg[i] + cr[i], etag));
-      }
+      chunk_lookback<NV>(cwd, c, nc, agg, AF, c + 1 < nc && (hopen < gbc || !AF), etag, spin, ctl, lc, S.cr);
     }
     __syncthreads();
 
@@ -735,10 +1025,12 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
           const float2 f2 = on_chip ? dsum[i * kDefCap + q] : hs[3 * q + i];
           sh[i] = P::comb(Acc{f2.x, f2.y}, CR[i]);
         }
-        add_group<NV>(sh, on_chip ? dcnt[q] : F.head_d[q0 + q], j, need_ll, g1q, g2q, llq, F, q0 + q);
+        add_group<NV>(sh, on_chip ? dcnt[q] : F.head_d[q0 + q], j, need_ll, g1q, g2q, llq, F, q0 + q,
+                      mode == kModeFit);
       }
       fence_proxy_async_smem();   // the tile buffers are rewritten by the next chunk's copies
     }
+    }   // the full path
 
     // ---- the chunk's partial, then the step by the CTA that finishes the fit's last chunk
     double r[3] = {P::to64(g1q), P::to64(g2q), llq};
@@ -751,6 +1043,11 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       for (int i = 0; i < 3; ++i) S.red[i][warp] = r[i];
     __syncthreads();
     if (tid == 0) {
+      if (mode == kModeFit) {   // a chunk the next launch's cached-S0 path would not hold rules it out
+        const int span = S.tlo[nt] - S.tlo[0];
+        if (!it.fast_ok || ent_next > kChunkFastE || (F.val == nullptr && ent_next >= span))
+          atomicOr(&ctl->fast_no, 1u);
+      }
       double p0 = 0.0, p1 = 0.0, p2 = 0.0;
       for (int q = 0; q < kCW; ++q) { p0 += S.red[0][q]; p1 += S.red[1][q]; p2 += S.red[2][q]; }
       F.part[3 * c + 0] = p0;
@@ -763,7 +1060,13 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     }
     __syncthreads();
     CHUNK_STAMP(5);
-    if (S.last) finish_launch_step<kCT, false>(F, lc, mode, j, need_ll, nc, epoch, S.scratch);
+    if (S.last) {
+      if (mode == kModeFit && tid == 0) {   // every tie group's S0 now holds for the fit's eta
+        ctl->s0c_tag = ctl->fast_no == 0u ? epoch + 1u : 0u;
+        ctl->fast_no = 0u;
+      }
+      finish_launch_step<kCT, false>(F, lc, mode, j, need_ll, nc, epoch, S.scratch);
+    }
     __syncthreads();
     CHUNK_STAMP(6);
   }
@@ -779,16 +1082,21 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     }
     __syncthreads();
   }
-  if constexpr (kCond) {   // the last CTA of the launch ends the graph's loop when nothing is left
+  // the last CTA of the launch resets the ticket (when items were taken from it) and, in a graph's
+  // sweep loop, ends the loop when nothing is left
+  if (kCond || n_items > int(gridDim.x)) {
     if (tid == 0) {
       __threadfence();
       if (atomicAdd(&lc->exited, 1u) == gridDim.x - 1) {
         lc->exited = 0u;
-        if (mode == kModeFit && cond) {
-          const long long left = --lc->budget;
-          if (*reinterpret_cast<volatile int32_t *>(&lc->active) <= 0 || left <= 0 ||
-              *reinterpret_cast<volatile int32_t *>(&lc->error) != 0)
-            cudaGraphSetConditional(cond, 0u);
+        lc->ticket = 0u;
+        if constexpr (kCond) {
+          if (mode == kModeFit && cond) {
+            const long long left = --lc->budget;
+            if (*reinterpret_cast<volatile int32_t *>(&lc->active) <= 0 || left <= 0 ||
+                *reinterpret_cast<volatile int32_t *>(&lc->error) != 0)
+              cudaGraphSetConditional(cond, 0u);
+          }
         }
       }
     }

@@ -66,6 +66,9 @@ struct FitCtl {
   double obj_prev, obj, loglik;
   uint32_t epoch;         // launch counter (tags look-back statuses)
   uint32_t done_tiles;    // tiles finished in the current launch
+  uint32_t s0c_tag;       // FP32C chunked kernel: equals epoch when the tie groups' cached S0 holds for
+                          // this launch's eta and the launch may take the cached-S0 path (0: never)
+  uint32_t fast_no;       // chunks of the current launch that rule that path out for the next one
   int64_t coord_updates;
   double out_g1, out_g2;  // EVAL mode result
   double out_ll;          // LL mode result (shard mode: the tie groups' sum d log S0)
@@ -97,7 +100,7 @@ struct DevFit {
   const int64_t *col_ptr;
   const uint32_t *idx, *cut_bits, *head_bits;
   const double *val;
-  int32_t T;
+  int32_t T, p;
   int32_t penalty, max_sweeps;
   double lambda, l2_var, tol, shift;
 };
@@ -134,7 +137,8 @@ struct WorkItem {
 struct ChunkItem {
   int32_t f, c, ta, tb, nc;
   int32_t lo_last;        // first position of the chunk's last tile (tile tb - 1)
-  int32_t pad_[2];
+  int32_t fast_ok;        // the fit's chunks are within the cached-S0 path's limits (strata, tie groups)
+  int32_t pad_;
 };
 static_assert(sizeof(ChunkItem) == sizeof(WorkItem), "chunk items share the work-list buffer");
 
@@ -203,6 +207,12 @@ int chunk_max_grid(int valued);
 int chunk_encode_vmap(void *v, int64_t n_floats, void *out);
 constexpr int kChunkTile = 4096;     // positions per tile of the chunked kernel
 constexpr int kChunkMaxTiles = 64;   // tiles per chunk
+// Limits per chunk of the chunked kernel's cached-S0 path (shared memory): column entries, stratum
+// ends, tie groups.
+constexpr int kChunksPerCtaDefault = 1;   // chunks per resident CTA of a plan (cox_set_chunk_plan)
+constexpr int kChunkFastE = 1536;
+constexpr int kChunkFastCuts = 256;
+constexpr int kChunkFastH = 4096;
 int launch_column_update(int precision, const DevFit *fit_dev, int32_t j, double db, int64_t nnz_j, void *stream);
 int launch_fill_v(int precision, const DevFit *fit_dev, int64_t M, const uint32_t *exit_bits, void *stream);
 

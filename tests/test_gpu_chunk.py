@@ -158,3 +158,107 @@ def test_fp32c_edge_cases(name, data, opts, chunk_tiles):
     else:
         assert np.max(np.abs(beta)) <= 1e-7, name
     assert abs(info["loglik"] - oi2["loglik"]) <= 1e-7 * max(_ll_scale(data, ob2, oi2["loglik"]), 1.0), name
+
+
+# ---- the cached-S0 path: a step of a fit whose eta did not change since its previous step (that
+#      step's update was 0) reads its tie groups' S0 from that step and computes column j's S1 (S2)
+#      from the column's entries; with several chunks per CTA, CTAs take further chunks in list order
+@pytest.fixture
+def chunk_plan(request):
+    cox.cox_set_chunk_plan(request.param)
+    yield request.param
+    cox.cox_set_chunk_plan(0)
+
+
+def _l1_well_posed(name, data):
+    """L1 at a quantile of |g'(0)| over the columns such that some coefficients stay at 0, at least
+    two move, and none of those lands near 0 (at least 5 % of the largest): most steps leave eta
+    unchanged, and no coefficient sits at the edge of the active set, where FP32 rounding of the
+    gradient moves it by more than the FP32C tolerance."""
+    g1, _ = oracle.grad_hess(data, np.zeros(data.p))
+    for q in (0.5, 0.6, 0.7, 0.8, 0.9):
+        opts = synth.CoxOptions(penalty=synth.PEN_L1, lam=float(np.quantile(np.abs(g1), q)), tol=1e-8)
+        b, info = oracle.fit(data, opts)
+        nz = np.abs(b[b != 0.0])
+        if nz.size >= 2 and nz.size < data.p and nz.min() >= 0.05 * nz.max():
+            _ORACLE[(name, None)] = (b, info)
+            return name, data, opts
+    raise AssertionError(f"{name}: no well-posed L1 weight")
+
+
+_L1 = {}
+
+
+def _l1_case(name):
+    """The L1 cases, built on first use: one stratum, many strata, counting process, valued X."""
+    if name not in _L1:
+        base = {"many_strata_l1": CASES[1][1], "counting_l1": CASES[2][1], "dense_valued_l1": CASES[4][1]}
+        _L1[name] = CASES[0] if name == "one_stratum_l1" else _l1_well_posed(name, base[name])
+    return _L1[name]
+
+
+L1_NAMES = ("one_stratum_l1", "many_strata_l1", "counting_l1", "dense_valued_l1")
+
+
+@pytest.mark.parametrize("chunk_plan", (1, 3), indirect=True)
+@pytest.mark.parametrize("chunk_tiles", (1, 2), indirect=True)
+@pytest.mark.parametrize("case", L1_NAMES)
+def test_fp32c_cached_s0_path_matches_oracle(case, chunk_tiles, chunk_plan):
+    """L1 fits whose steps mostly leave eta unchanged, with one or three chunks per CTA, against the
+    oracle at the FP32C tolerances."""
+    name, data, opts = _l1_case(case)
+    with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+        beta, info = h.fit()
+    ob, _ = _oracle_fit(name, data, opts, info["sweeps"])
+    ob2, oi2 = _oracle_fit(name, data, opts)
+    assert np.any(ob2 == 0.0) and np.any(ob2 != 0.0), name   # the penalty keeps some coefficients at 0
+    assert min(_rel_beta(beta, ob), _rel_beta(beta, ob2)) <= 1e-5, (name, chunk_tiles, chunk_plan)
+    assert abs(info["loglik"] - oi2["loglik"]) <= 1e-7 * _ll_scale(data, ob2, oi2["loglik"]), name
+
+
+@pytest.mark.parametrize("chunk_tiles", (2,), indirect=True)
+def test_cached_s0_path_is_taken(chunk_tiles):
+    """The same L1 fit with the cached-S0 path and without it: both within the FP32C tolerance of the
+    oracle, and not bitwise equal (its S1 sums run in another order), so the path ran."""
+    name, data, opts = _l1_case("many_strata_l1")
+    out = []
+    try:
+        for enable in (True, False):
+            cox.cox_debug_set_cached_s0(enable)
+            with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+                out.append(h.fit())
+    finally:
+        cox.cox_debug_set_cached_s0(True)
+    ob2, oi2 = _oracle_fit(name, data, opts)
+    for beta, info in out:
+        ob, _ = _oracle_fit(name, data, opts, info["sweeps"])
+        assert min(_rel_beta(beta, ob), _rel_beta(beta, ob2)) <= 1e-5
+    assert not np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("chunk_plan", (3,), indirect=True)
+@pytest.mark.parametrize("chunk_tiles", (1, 2), indirect=True)
+def test_fp32c_batch_cached_s0_and_chunk_plan(chunk_tiles, chunk_plan):
+    """A batch of uneven L1 and L2 fits with three chunks per CTA: fits on the cached-S0 path and on
+    the full pass share launches; each result within the FP32C tolerance of the oracle."""
+    sets = [_l1_case("one_stratum_l1"), _l1_case("many_strata_l1"), _l1_case("counting_l1"), CASES[1],
+            _l1_case("dense_valued_l1")]
+    hs = [cox.Handle(d, o, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) for _, d, o in sets]
+    try:
+        betas, infos = cox.batch_fit(hs)
+    finally:
+        for h in hs:
+            h.close()
+    for (name, d, o), b, i in zip(sets, betas, infos):
+        ob, _ = _oracle_fit(name, d, o, i["sweeps"])
+        ob2, oi2 = _oracle_fit(name, d, o)
+        assert min(_rel_beta(b, ob), _rel_beta(b, ob2)) <= 1e-5, name
+        assert abs(i["loglik"] - oi2["loglik"]) <= 1e-7 * _ll_scale(d, ob2, oi2["loglik"]), name
+
+
+def test_chunk_plan_knob_rejects_bad_values():
+    with pytest.raises(cox.CoxError):
+        cox.cox_set_chunk_plan(9)
+    with pytest.raises(cox.CoxError):
+        cox.cox_set_chunk_plan(-1)
+    cox.cox_set_chunk_plan(0)

@@ -310,6 +310,7 @@ __device__ void fast_chunk(ChunkSmem<NV> &S, const DevFit &F, FitCtl *ctl, Launc
   };
   // 1. stratum ends and tie groups per thread; their bases over the CTA
   int ncut = 0, nhd = 0;
+#pragma unroll 4
   for (int w = wa; w < wb; ++w) {
     const uint32_t m = wmask(w);
     ncut += __popc(F.cut_bits[W0 + w] & m);
@@ -365,14 +366,29 @@ __device__ void fast_chunk(ChunkSmem<NV> &S, const DevFit &F, FitCtl *ctl, Launc
     for (int w = wa; w < wb; ++w)
       for (uint32_t m = F.cut_bits[W0 + w] & wmask(w); m; m &= m - 1u) V.cut[k++] = 32 * w + __ffs(m) - 1;
   }
+  // kFB entries per thread at a time: their positions, then v at them (and x), loaded together
+  constexpr int kFB = 4;
   const float *vg = static_cast<const float *>(F.v);
-  for (int k = tid; k < ne; k += kCT) {
-    const int pos = int(F.idx[q0 + k] & kPosMask) - P0;
-    V.epos[k] = uint32_t(pos);
-    const float vv = vg[P0 + pos];
-    const float x = vf ? float(F.val[q0 + k]) : 1.0f;
-    V.es[0][k] = Acc{x * vv, 0.f};
-    if constexpr (VAL) V.es[1][k] = Acc{x * (x * vv), 0.f};
+  for (int k0 = tid; k0 < ne; k0 += kFB * kCT) {
+    int pos[kFB];
+    float vv[kFB], x[kFB];
+#pragma unroll
+    for (int u = 0; u < kFB; ++u) {
+      const int k = k0 + u * kCT;
+      pos[u] = k < ne ? int(F.idx[q0 + k] & kPosMask) - P0 : 0;
+      x[u] = vf && k < ne ? float(F.val[q0 + k]) : 1.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kFB; ++u) vv[u] = k0 + u * kCT < ne ? vg[P0 + pos[u]] : 0.f;
+#pragma unroll
+    for (int u = 0; u < kFB; ++u) {
+      const int k = k0 + u * kCT;
+      if (k < ne) {
+        V.epos[k] = uint32_t(pos[u]);
+        V.es[0][k] = Acc{x[u] * vv[u], 0.f};
+        if constexpr (VAL) V.es[1][k] = Acc{x[u] * (x[u] * vv[u]), 0.f};
+      }
+    }
   }
   __syncthreads();
   for (int k = tid; k < ne; k += kCT) {   // stratum ends before each entry
@@ -484,6 +500,7 @@ __device__ void fast_chunk(ChunkSmem<NV> &S, const DevFit &F, FitCtl *ctl, Launc
         else hi = mid;
       }
     }
+#pragma unroll 2
     for (int w = wa; w < wb; ++w) {
       const uint32_t msk = wmask(w);
       const uint32_t hm = F.head_bits[W0 + w] & msk, cm = F.cut_bits[W0 + w] & msk;
@@ -505,19 +522,29 @@ __device__ void fast_chunk(ChunkSmem<NV> &S, const DevFit &F, FitCtl *ctl, Launc
   for (int i = 0; i < NS; ++i) CR[i] = P::from64(S.cr[i + 1]);
   const float2 *s0c = reinterpret_cast<const float2 *>(F.hscr);
   const int g0 = S.tg[0];
-#pragma unroll 2
-  for (int h = tid; h < nH; h += kCT) {
-    const int code = V.hcode[h], g = g0 + h;
-    const float2 z = s0c[3 * int64_t(g)];
-    const int dg = F.head_d[g];
-    Acc sh[NV];
-    sh[0] = Acc{z.x, z.y};
+  for (int h0 = tid; h0 < nH; h0 += kFB * kCT) {   // kFB groups per thread: their loads together
+    float2 z[kFB];
+    int dg[kFB];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) sh[i + 1] = (code & (1 << 12)) ? V.es[i][code & 4095] : P::zero();
-    if (code & (1 << 13))
+    for (int u = 0; u < kFB; ++u) {
+      const int h = h0 + u * kCT;
+      z[u] = h < nH ? s0c[3 * int64_t(g0 + h)] : make_float2(1.f, 0.f);
+      dg[u] = h < nH ? F.head_d[g0 + h] : 0;
+    }
 #pragma unroll
-      for (int i = 0; i < NS; ++i) sh[i + 1] = P::comb(sh[i + 1], CR[i]);
-    add_group<NV>(sh, dg, j, need_ll, g1q, g2q, llq, F, g, false);
+    for (int u = 0; u < kFB; ++u) {
+      const int h = h0 + u * kCT;
+      if (h >= nH) break;
+      const int code = V.hcode[h];
+      Acc sh[NV];
+      sh[0] = Acc{z[u].x, z[u].y};
+#pragma unroll
+      for (int i = 0; i < NS; ++i) sh[i + 1] = (code & (1 << 12)) ? V.es[i][code & 4095] : P::zero();
+      if (code & (1 << 13))
+#pragma unroll
+        for (int i = 0; i < NS; ++i) sh[i + 1] = P::comb(sh[i + 1], CR[i]);
+      add_group<NV>(sh, dg[u], j, need_ll, g1q, g2q, llq, F, g0 + h, false);
+    }
   }
   fence_proxy_async_smem();   // the tile buffers are rewritten by the next chunk's copies
 }

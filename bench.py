@@ -122,10 +122,10 @@ ENGINE_NAMES = {1: "streaming", 2: "resident", 3: "incremental"}
 # on the same workload (launch total / steps it ran; the captures run `bench.py --workload probe`).
 # Keyed by (engine, workload, precision); absent = not captured for the current kernel.
 TRAFFIC = {
-    # --probe incr: 190.09 MB per 1-sweep launch of 2001 steps
-    ("incremental", "stratified_sparse", "fp64"): 190.09e6 / 2001,
+    # --probe incr: 156.02 MB read + 33.95 MB written per 1-sweep launch of 2001 steps
+    ("incremental", "stratified_sparse", "fp64"): (156.023e6 + 33.954e6) / 2001,
     # --probe stream_fp32c: an evaluation launch (a fit's launch adds the previous column's update, ~0.2 MB)
-    ("streaming", "time_varying", "fp32c"): 26.58e6,
+    ("streaming", "time_varying", "fp32c"): 25.57e6,
     # --probe stream_fp64: an evaluation launch
     ("streaming", "time_varying", "fp64"): 47.03e6,
 }
@@ -156,7 +156,9 @@ def moving_options(n: int):
 
 def headline_config(wname: str) -> dict:
     """The workload the metric is quoted on (identical in both arms)."""
-    return {"workload": wname, "precision": "fp64 (tolerance vs the FP64 oracle: 1e-9 beta, 1e-11 log-likelihood)"}
+    return {"workload": wname,
+            "precision": "FP64-level: double-word FP32 sums and ratios (about 48-bit significands) with FP64 eta, "
+                         "beta and step; tolerance vs the FP64 oracle 1e-9 beta, 1e-11 log-likelihood"}
 
 
 def dense_bytes_per_step(M: int, G: int, K: int, nnz_pos: float, s_e: int, moved: bool) -> float:
@@ -623,7 +625,9 @@ def run_probe(args):
       segscan                     cox_segscan on 2^24 doubles with 1,000 segments
       prep                        cox_create on the stratified sparse data of the default line
       incr / resident             one incremental- / resident-engine fit (1 sweep) of that data
-      views                       a time-split view (cox_create_split) and a 5-fold CV path's subsets"""
+      views                       a time-split view (cox_create_split) and a 5-fold CV path's subsets
+      batch_fp32c                 one batched FP32C fit of the 256-fit batch workload (graph-replayed
+                                  launches of the chunked kernel; the first sweep's hold every fit)"""
     import torch
     from paper_2310_16238_gb300 import cox
     what = args.probe
@@ -678,6 +682,24 @@ def run_probe(args):
             e1.record(stream)
             e1.synchronize()
             out.update(value=1e3 * e0.elapsed_time(e1), what="us for the split view and the CV path")
+        elif what == "batch_fp32c":
+            sets = synth.batch_views(n_total=int(1_000_000 * args.scale), n_lo=1e4 * args.scale,
+                                     n_hi=1e6 * args.scale)
+            handles = []
+            for dd, ol in sets:
+                base = cox.Handle(dd, ol[0], precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM,
+                                  stream=stream.cuda_stream)
+                handles.append(base)
+                handles.extend(base.clone(oo) for oo in ol[1:])
+            e0.record(stream)
+            betas, infos = cox.batch_fit(handles)
+            e1.record(stream)
+            e1.synchronize()
+            for hh in handles:
+                hh.close()
+            out.update(value=1e3 * e0.elapsed_time(e1) / max(infos[0]["step_launches"], 1),
+                       what="us per batched launch (256 fits, averaged over the batch)",
+                       launches=int(infos[0]["step_launches"]))
         elif what in ("prep", "incr"):
             d, o, _ = headline_workload(args.scale)
             if what == "prep":
@@ -958,7 +980,7 @@ def main():
     ap.add_argument("--workload", default="default",
                     choices=["default", "time_varying", "cv", "e1", "batch", "serving", "probe"])
     ap.add_argument("--probe", default="stream_fp32c",
-                    choices=["stream_fp32c", "stream_fp64", "segscan", "prep", "incr", "resident", "views"],
+                    choices=["stream_fp32c", "stream_fp64", "segscan", "prep", "incr", "resident", "views", "batch_fp32c"],
                     help="probe workload: one small single-kernel case for a profiler capture")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=30.0)

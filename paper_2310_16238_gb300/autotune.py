@@ -1,7 +1,7 @@
 """Schedule autotuner for batched fits (streaming coordinate-step kernels).
 
-For a set of data sets and a precision it times short batched runs (one sweep) at each candidate
-schedule and returns the fastest:
+For a set of data sets and a precision it times short batched runs (at most two sweeps) at each
+candidate schedule and returns the fastest:
   * FP64 streaming kernel: the tile length (positions per work item);
   * FP32C chunked kernel: the chunks per resident CTA of its plans (one chunk per CTA, or several
     taken in work-list order, so that CTAs freed by cheap chunks take others). Its tiles are fixed
@@ -22,10 +22,12 @@ PLAN_CANDIDATES = (1, 2, 3)
 
 
 def _probe_handles(sets, precision, tile, every_option):
-    """One sweep of every fit (every option of each set when every_option, else its first)."""
+    """Every fit (every option of each set when every_option, else its first) for at most two
+    sweeps with its own tolerance: the first sweep of every fit and the second of those that go on,
+    as in the batch itself."""
     handles = []
     for d, olist in sets:
-        probe = [synth.CoxOptions(penalty=o.penalty, lam=o.lam, l2_var=o.l2_var, tol=0.0, max_sweeps=1)
+        probe = [synth.CoxOptions(penalty=o.penalty, lam=o.lam, l2_var=o.l2_var, tol=o.tol, max_sweeps=2)
                  for o in (olist if every_option else olist[:1])]
         base = cox.Handle(d, probe[0], precision=precision, tile=tile, engine=cox.COX_ENGINE_STREAM)
         handles.append(base)
@@ -40,7 +42,7 @@ def _time_batch(handles):
     return time.perf_counter() - t0
 
 
-def batch_tile(sets, precision, max_sweeps_probe: int = 1) -> int:
+def batch_tile(sets, precision) -> int:
     """Best tile length for fitting every (data, options) pair of ``sets`` together."""
     if len(CANDIDATES[precision]) == 1:
         return CANDIDATES[precision][0]

@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` is compiled in parallel with nvcc for ``sm_103a`` only, then linked
 into one shared library with a C ABI (declared in ``include/cox.h``). No torch types cross
 the ABI; the Python binding (``cox.py``) loads the library with ctypes.
+
+``python -m paper_2310_16238_gb300.build --trace`` builds the diagnostic variant
+(``_build/trace/libcoxgb.so``, compiled with -DCOXGB_TRACE: per-step phase stamps of the
+resident and incremental kernels, printed when COXGB_PHASE_TRACE=<steps> is set). The binding
+loads it instead of the default library when COXGB_LIBRARY names its path.
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcoxgb.so")
+TRACE_LIB = os.path.join(BUILD, "trace", "libcoxgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,11 +47,14 @@ def _stale(lib: str, sources) -> bool:
     return any(os.path.getmtime(s) > t for s in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), trace: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    if not force and not _stale(LIB, sources):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    lib = TRACE_LIB if trace else LIB
+    if trace:
+        extra = [*extra, "-DCOXGB_TRACE"]
+    if not force and not _stale(lib, sources):
+        return lib
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     exe = nvcc()
     objs = []
 
@@ -61,15 +70,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(sources))) as ex:
         objs = list(ex.map(compile_one, sources))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, trace="--trace" in sys.argv))

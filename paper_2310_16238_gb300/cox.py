@@ -15,7 +15,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libcoxgb.so")
+# the library (COXGB_LIBRARY: another build of it, such as the diagnostic one of build.py --trace)
+LIB_PATH = os.environ.get("COXGB_LIBRARY") or os.path.join(_HERE, "_build", "libcoxgb.so")
 
 COX_OK, COX_W_NOT_CONVERGED = 0, 1
 COX_E_INVALID, COX_E_UNSORTED, COX_E_OOM, COX_E_CUDA = -1, -2, -3, -4

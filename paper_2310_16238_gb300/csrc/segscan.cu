@@ -61,30 +61,54 @@ __device__ __forceinline__ double seg_ld_relaxed(const double *p) {
 }
 
 // status word: bit 0 aggregate published, bit 1 inclusive published, bit 2 tile holds a head
-__global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, const uint8_t *__restrict__ f,
-                                                              int64_t n, double *b, unsigned char *scratch,
-                                                              int64_t tiles, long long spin) {
+__device__ __forceinline__ double seg_ld_nc(const double2 *p, double &hi) {
+  const double2 x = __ldg(p);
+  hi = x.y;
+  return x.x;
+}
+
+__global__ void __launch_bounds__(kSegThreads, 3) segscan_kernel(const double *a, const uint8_t *__restrict__ f,
+                                                                 int64_t n, double *b, unsigned char *scratch,
+                                                                 int64_t tiles, long long spin) {
+  constexpr int kW = kSegThreads / 32;
   const SegScratchView S = seg_view(scratch, tiles);
   __shared__ int64_t s_tile;
-  __shared__ double s_wsum[kSegThreads / 32];
-  __shared__ int s_wflag[kSegThreads / 32];
-  __shared__ double s_wcar[kSegThreads / 32];
-  __shared__ int s_wcflag[kSegThreads / 32];
-  __shared__ double s_carry;
+  __shared__ double s_wsum[kW];
+  __shared__ int s_wflag[kW];
+  __shared__ double s_wex[kW];    // carry into each warp from the tile's earlier warps
+  __shared__ int s_wexf[kW];      // ... which stops at a head
+  __shared__ double s_carry;      // carry into the tile from earlier tiles
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // 16-byte loads and stores of a thread's 16 values and flags when every array is 16-byte aligned
+  const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(f) |
+                     reinterpret_cast<uintptr_t>(b)) & 15u) == 0u;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(S.ticket, 1u);
     __syncthreads();
     const int64_t t = s_tile;
     if (t >= tiles) break;
     const int64_t base = t * kSegTile + int64_t(tid) * kSegItems;
+    const bool full = vec && (t + 1) * kSegTile <= n;   // uniform over the tile
     double v[kSegItems];
     uint32_t fm = 0;
+    if (full) {
+      const double2 *a2 = reinterpret_cast<const double2 *>(a + base);
 #pragma unroll
-    for (int k = 0; k < kSegItems; ++k) {
-      const int64_t i = base + k;
-      v[k] = i < n ? a[i] : 0.0;
-      if (i < n && f[i]) fm |= 1u << k;
+      for (int k = 0; k < kSegItems / 2; ++k) v[2 * k] = seg_ld_nc(a2 + k, v[2 * k + 1]);
+      const uint4 fw = __ldg(reinterpret_cast<const uint4 *>(f + base));
+      const uint32_t w4[4] = {fw.x, fw.y, fw.z, fw.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // a nonzero flag byte -> its bit
+        const uint32_t m = __vcmpne4(w4[q], 0u);
+        fm |= (((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u)) << (4 * q);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSegItems; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < n ? a[i] : 0.0;
+        if (i < n && f[i]) fm |= 1u << k;
+      }
     }
     double acc = 0.0;
 #pragma unroll
@@ -104,57 +128,106 @@ __global__ void __launch_bounds__(kSegThreads) segscan_kernel(const double *a, c
         fl |= yf;
       }
     }
-    if (lane == 31) { s_wsum[warp] = x; s_wflag[warp] = fl; }
+    if (lane == 31) {
+      s_wsum[warp] = x;
+      s_wflag[warp] = fl;
+    }
     double ex = __shfl_up_sync(0xffffffffu, x, 1);
     int exf = __shfl_up_sync(0xffffffffu, fl, 1);
-    if (lane == 0) { ex = 0.0; exf = 0; }
+    if (lane == 0) {
+      ex = 0.0;
+      exf = 0;
+    }
     __syncthreads();
-    if (tid == 0) {
-      double c = 0.0;
-      int cf = 0;
-      for (int w = 0; w < kSegThreads / 32; ++w) {
-        s_wcar[w] = c;
-        s_wcflag[w] = cf;
-        if (s_wflag[w]) { c = s_wsum[w]; cf = 1; }
-        else c = c + s_wsum[w];
-      }
-      // tile aggregate: c with flag cf; publish, then look back over earlier tiles
-      S.agg[t] = c;
-      if (cf) S.incl[t] = c;
-      __threadfence();
-      seg_st_release(&S.status[t], cf ? (4u | 2u | 1u) : 1u);
-      double carry = 0.0;
-      if (t > 0) {
-        const long long t0 = clock64();
-        for (int64_t u = t - 1; u >= 0; --u) {
-          uint32_t st;
-          while (((st = seg_ld_acquire(&S.status[u])) & 3u) == 0u) {
-            if (clock64() - t0 > spin) { atomicExch(S.error, 1u); st = 2u; break; }
-            __nanosleep(32);
-          }
-          if (st & 2u) { carry = seg_ld_relaxed(&S.incl[u]) + carry; break; }
-          carry = seg_ld_relaxed(&S.agg[u]) + carry;
+    if (warp == 0) {
+      // the tile's warps combined by shuffles; the tile aggregate published; then one look-back
+      // over up to 32 earlier tiles at a time
+      double w = lane < kW ? s_wsum[lane] : 0.0;
+      int wf = lane < kW ? s_wflag[lane] : 0;
+#pragma unroll
+      for (int off = 1; off < kW; off <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, w, off);
+        const int yf = __shfl_up_sync(0xffffffffu, wf, off);
+        if (lane >= off) {
+          if (!wf) w = y + w;
+          wf |= yf;
         }
       }
-      s_carry = carry;
-      if (!cf) {
-        S.incl[t] = carry + c;
+      double we = __shfl_up_sync(0xffffffffu, w, 1);
+      int wef = __shfl_up_sync(0xffffffffu, wf, 1);
+      if (lane < kW) {
+        s_wex[lane] = lane == 0 ? 0.0 : we;
+        s_wexf[lane] = lane == 0 ? 0 : wef;
+      }
+      const double c = __shfl_sync(0xffffffffu, w, kW - 1);
+      const int cf = __shfl_sync(0xffffffffu, wf, kW - 1);
+      if (lane == 0) {
+        S.agg[t] = c;
+        if (cf) S.incl[t] = c;
         __threadfence();
-        seg_st_release(&S.status[t], 2u | 1u);
+        seg_st_release(&S.status[t], cf ? (4u | 2u | 1u) : 1u);
+      }
+      double carry = 0.0;
+      bool timed_out = false;
+      const long long t0 = clock64();
+      for (int64_t u0 = t - 1; u0 >= 0;) {
+        const int64_t u = u0 - lane;   // lane 0 the nearest earlier tile; before tile 0 an inclusive 0
+        uint32_t st = 2u;
+        int first = 32;
+        for (;;) {
+          st = u >= 0 ? seg_ld_acquire(&S.status[u]) : 2u;
+          const uint32_t inc = __ballot_sync(0xffffffffu, (st & 2u) != 0u);
+          const uint32_t pend = __ballot_sync(0xffffffffu, (st & 3u) == 0u);
+          first = inc ? __ffs(inc) - 1 : 32;
+          const uint32_t need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);   // lanes 0..first
+          if ((pend & need) == 0u) break;
+          if (clock64() - t0 > spin) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (timed_out) {
+          if (lane == 0) atomicExch(S.error, 1u);
+          break;
+        }
+        double val = 0.0;
+        if (lane <= first && u >= 0) val = lane == first ? seg_ld_relaxed(&S.incl[u]) : seg_ld_relaxed(&S.agg[u]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+        carry += val;
+        if (first < 32) break;
+        u0 -= 32;
+      }
+      if (lane == 0) {
+        s_carry = carry;
+        if (!cf) {
+          S.incl[t] = carry + c;
+          __threadfence();
+          seg_st_release(&S.status[t], 2u | 1u);
+        }
       }
     }
     __syncthreads();
     // exclusive carry of this thread: earlier threads of the warp, earlier warps, earlier tiles
     if (!exf) {
-      ex = s_wcar[warp] + ex;
-      exf = s_wcflag[warp];
+      ex = s_wex[warp] + ex;
+      exf = s_wexf[warp];
       if (!exf) ex = s_carry + ex;
     }
 #pragma unroll
-    for (int k = 0; k < kSegItems; ++k) {
+    for (int k = 0; k < kSegItems; ++k)
       if ((fm & ((2u << k) - 1u)) == 0u) v[k] = ex + v[k];
-      const int64_t i = base + k;
-      if (i < n) b[i] = v[k];
+    if (full) {
+      double2 *b2 = reinterpret_cast<double2 *>(b + base);
+#pragma unroll
+      for (int k = 0; k < kSegItems / 2; ++k) b2[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSegItems; ++k) {
+        const int64_t i = base + k;
+        if (i < n) b[i] = v[k];
+      }
     }
     __syncthreads();
   }

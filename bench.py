@@ -157,8 +157,9 @@ def moving_options(n: int):
 def headline_config(wname: str) -> dict:
     """The workload the metric is quoted on (identical in both arms)."""
     return {"workload": wname,
-            "precision": "FP64-level: double-word FP32 sums and ratios (about 48-bit significands) with FP64 eta, "
-                         "beta and step; tolerance vs the FP64 oracle 1e-9 beta, 1e-11 log-likelihood"}
+            "precision": "FP64-level results: tolerance vs the FP64 oracle 1e-9 beta, 1e-11 log-likelihood (the GPU "
+                         "path sums in double-word FP32, about 48-bit significands, with FP64 eta, beta and step; "
+                         "`dtype` gives each arm's arithmetic)"}
 
 
 def dense_bytes_per_step(M: int, G: int, K: int, nnz_pos: float, s_e: int, moved: bool) -> float:

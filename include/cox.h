@@ -353,7 +353,7 @@ int cox_debug_set_cached_s0(int32_t enable);
  * segmented-scan on GPUs"): out[i] = sum of a[k] for k from the last index h <= i with
  * head_flags[h] != 0 (or from 0) up to i. a, head_flags, out: device arrays of n elements
  * (out may alias a). Runs on `stream` (cudaStream_t, NULL = default) and returns after it
- * completed. Scratch for the single-pass look-back (about 20 bytes per 4096 elements) is
+ * completed. Scratch for the single-pass look-back (32 bytes per 4096 elements) is
  * taken from the library allocator for the duration of the call.
  * Errors: COX_E_INVALID (null/host pointers, n < 0), COX_E_OOM, COX_E_CUDA, COX_E_TIMEOUT. */
 int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *out, void *stream);
@@ -362,7 +362,7 @@ int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n, double *o
  * paper: it exists for callers that cannot allocate device memory while they run -- a host
  * program whose own memory pool must own every device byte, a real-time loop that cannot risk
  * an allocator call blocking or failing mid-run, a process held to a fixed memory budget.
- * Its scratch is one static device array of 81,936 bytes that every GPU loading this library
+ * Its scratch is one static device array of 131,088 bytes that every GPU loading this library
  * holds until the process exits; n is therefore limited to 16,777,216 values (COX_E_INVALID
  * beyond that). The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, and looks it up again if the device's

@@ -4,7 +4,7 @@
 // scans a tile of 4096 values in registers (16 consecutive values per thread), combines
 // threads with a warp-shuffle segmented scan, and takes its carry from earlier tiles by a
 // decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan with Decoupled
-// Look-back", 2016) over per-tile status words kept in scratch memory.
+// Look-back", 2016) over per-tile tagged records kept in scratch memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -22,45 +22,42 @@ constexpr int kSegThreads = 256;
 constexpr int kSegItems = 16;
 constexpr int kSegTile = kSegThreads * kSegItems;
 
-// Scratch layout (bytes): [0] ticket, [4] exited, [8] error, [16 .. 16+4T) status,
-// then aggregates (8T) and inclusive values (8T), 8-byte aligned.
+// Scratch layout (bytes): [0] ticket, [4] exited, [8] error, then per tile two records of 16 bytes,
+// its aggregate and its inclusive value. A record is two 64-bit words, (tag << 32) | the low and
+// (tag << 32) | the high 32 bits of the double: each word is stored and loaded whole, so a reader
+// that sees the tag in both words has the value (no fence to publish, no flag to acquire). The
+// whole scratch is zeroed before every call, so the tag is a constant.
+constexpr uint64_t kSegTag = 0x5ca1ull;
 struct SegScratchView {
-  uint32_t *ticket, *exited, *error, *status;
-  double *agg, *incl;
+  uint32_t *ticket, *exited, *error;
+  uint64_t *rec;   // [tile][2 records][2 words]
 };
 
-__host__ __device__ constexpr size_t seg_scratch_bytes(int64_t tiles) {
-  const size_t st = (16 + 4 * size_t(tiles) + 7) & ~size_t(7);
-  return st + 16 * size_t(tiles);
-}
+__host__ __device__ constexpr size_t seg_scratch_bytes(int64_t tiles) { return 16 + 32 * size_t(tiles); }
 
-__device__ inline SegScratchView seg_view(unsigned char *s, int64_t tiles) {
+__device__ inline SegScratchView seg_view(unsigned char *s, int64_t) {
   SegScratchView v;
   v.ticket = reinterpret_cast<uint32_t *>(s);
   v.exited = reinterpret_cast<uint32_t *>(s + 4);
   v.error = reinterpret_cast<uint32_t *>(s + 8);
-  v.status = reinterpret_cast<uint32_t *>(s + 16);
-  const size_t st = (16 + 4 * size_t(tiles) + 7) & ~size_t(7);
-  v.agg = reinterpret_cast<double *>(s + st);
-  v.incl = v.agg + tiles;
+  v.rec = reinterpret_cast<uint64_t *>(s + 16);
   return v;
 }
 
-__device__ __forceinline__ void seg_st_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void seg_put(uint64_t *r, double x) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const uint64_t w0 = (kSegTag << 32) | (b & 0xffffffffull), w1 = (kSegTag << 32) | (b >> 32);
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(r), "l"(w0), "l"(w1) : "memory");
 }
-__device__ __forceinline__ uint32_t seg_ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ double seg_ld_relaxed(const double *p) {
-  double v;
-  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-  return v;
+// the record's value when both words carry the tag
+__device__ __forceinline__ bool seg_get(const uint64_t *r, double *x) {
+  uint64_t w0, w1;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(r) : "memory");
+  if ((w0 >> 32) != kSegTag || (w1 >> 32) != kSegTag) return false;
+  *x = __longlong_as_double(static_cast<long long>((w1 << 32) | (w0 & 0xffffffffull)));
+  return true;
 }
 
-// status word: bit 0 aggregate published, bit 1 inclusive published, bit 2 tile holds a head
 __device__ __forceinline__ double seg_ld_nc(const double2 *p, double &hi) {
   const double2 x = __ldg(p);
   hi = x.y;
@@ -161,23 +158,24 @@ __global__ void __launch_bounds__(kSegThreads, 3) segscan_kernel(const double *a
       }
       const double c = __shfl_sync(0xffffffffu, w, kW - 1);
       const int cf = __shfl_sync(0xffffffffu, wf, kW - 1);
-      if (lane == 0) {
-        S.agg[t] = c;
-        if (cf) S.incl[t] = c;
-        __threadfence();
-        seg_st_release(&S.status[t], cf ? (4u | 2u | 1u) : 1u);
-      }
+      // a tile with a head publishes its sums from that head on as final (inclusive) at once
+      if (lane == 0) seg_put(S.rec + 4 * t + (cf ? 2 : 0), c);
       double carry = 0.0;
       bool timed_out = false;
       const long long t0 = clock64();
       for (int64_t u0 = t - 1; u0 >= 0;) {
         const int64_t u = u0 - lane;   // lane 0 the nearest earlier tile; before tile 0 an inclusive 0
-        uint32_t st = 2u;
+        double val = 0.0;
         int first = 32;
         for (;;) {
-          st = u >= 0 ? seg_ld_acquire(&S.status[u]) : 2u;
-          const uint32_t inc = __ballot_sync(0xffffffffu, (st & 2u) != 0u);
-          const uint32_t pend = __ballot_sync(0xffffffffu, (st & 3u) == 0u);
+          int vi = 1, va = 0;
+          val = 0.0;
+          if (u >= 0) {
+            vi = seg_get(S.rec + 4 * u + 2, &val);
+            if (!vi) va = seg_get(S.rec + 4 * u, &val);
+          }
+          const uint32_t inc = __ballot_sync(0xffffffffu, vi);
+          const uint32_t pend = __ballot_sync(0xffffffffu, !(vi || va));
           first = inc ? __ffs(inc) - 1 : 32;
           const uint32_t need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);   // lanes 0..first
           if ((pend & need) == 0u) break;
@@ -191,8 +189,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) segscan_kernel(const double *a
           if (lane == 0) atomicExch(S.error, 1u);
           break;
         }
-        double val = 0.0;
-        if (lane <= first && u >= 0) val = lane == first ? seg_ld_relaxed(&S.incl[u]) : seg_ld_relaxed(&S.agg[u]);
+        if (lane > first) val = 0.0;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
         carry += val;
@@ -201,11 +198,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) segscan_kernel(const double *a
       }
       if (lane == 0) {
         s_carry = carry;
-        if (!cf) {
-          S.incl[t] = carry + c;
-          __threadfence();
-          seg_st_release(&S.status[t], 2u | 1u);
-        }
+        if (!cf) seg_put(S.rec + 4 * t + 2, carry + c);
       }
     }
     __syncthreads();
@@ -263,7 +256,7 @@ static int seg_grid(int64_t tiles) {
   return int(tiles < cap ? tiles : cap);
 }
 
-// Runs the scan with scratch at `scratch` (already zeroed over its first 16 + 4T bytes).
+// Runs the scan with scratch at `scratch` (already zeroed: seg_scratch_bytes(T) bytes).
 static int segscan_run(const double *a, const uint8_t *f, int64_t n, double *b, unsigned char *scratch, int64_t tiles,
                        cudaStream_t s, std::string *err) {
   count_launches(1);
@@ -301,7 +294,7 @@ extern "C" int cox_segscan(const double *a, const uint8_t *head_flags, int64_t n
   const size_t bytes = seg_scratch_bytes(tiles);
   unsigned char *scratch = static_cast<unsigned char *>(dev_alloc(bytes));
   if (!scratch) return set_last_error(COX_E_OOM, "cox_segscan: scratch allocation failed");
-  rc = cudaMemsetAsync(scratch, 0, 16 + 4 * size_t(tiles), s) == cudaSuccess ? COX_OK : COX_E_CUDA;
+  rc = cudaMemsetAsync(scratch, 0, bytes, s) == cudaSuccess ? COX_OK : COX_E_CUDA;
   if (!rc) rc = segscan_run(a, head_flags, n, out, scratch, tiles, s, &err);
   else err = "cox_segscan: memset failed";
   cudaStreamSynchronize(s);
@@ -392,8 +385,8 @@ extern "C" int cox_segscan_noalloc(const double *a, const uint8_t *head_flags, i
   unsigned char *scratch = nullptr;
   if ((rc = static_scratch_address(&scratch, &err))) return set_last_error(rc, err.c_str());
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the array keeps the previous call's contents: clear the ticket, error and tile states
-  if (cudaMemsetAsync(scratch, 0, 16 + 4 * size_t(tiles), s) != cudaSuccess)
+  // the array keeps the previous call's contents: clear the ticket, error and the tiles' records
+  if (cudaMemsetAsync(scratch, 0, seg_scratch_bytes(tiles), s) != cudaSuccess)
     return set_last_error(COX_E_CUDA, "cox_segscan_noalloc: clearing the static scratch failed");
   rc = segscan_run(a, head_flags, n, out, scratch, tiles, s, &err);
   return rc ? set_last_error(rc, err.c_str()) : COX_OK;

@@ -72,13 +72,30 @@ void BufferSet::release() {
   for (auto &b : bufs) dev_free(b.first, b.second);
   bufs.clear();
   bytes_total = 0;
+  slab = nullptr;
+  slab_left = 0;
 }
 
 void *BufferSet::get(size_t bytes) {
+  const size_t r = ((bytes ? bytes : 1) + 255) & ~size_t(255);   // 256-byte aligned pieces
+  if (r <= kSlabMax) {
+    if (r > slab_left) {
+      void *s = dev_alloc(kSlabBytes);
+      if (!s) return nullptr;
+      bufs.emplace_back(s, kSlabBytes);
+      slab = static_cast<char *>(s);
+      slab_left = kSlabBytes;
+    }
+    void *p = slab;
+    slab += r;
+    slab_left -= r;
+    bytes_total += r;
+    return p;
+  }
   void *p = dev_alloc(bytes);
   if (p) {
     bufs.emplace_back(p, bytes);
-    bytes_total += (bytes + 255) & ~size_t(255);
+    bytes_total += r;
   }
   return p;
 }

@@ -22,10 +22,15 @@ void set_wait_limit(long long clocks);
 // Record `msg` as the calling thread's last error and return `code` (api.cu).
 int set_last_error(int code, const char *msg);
 
-// Owns device buffers; releases them on destruction.
+// Owns device buffers; releases them on destruction. Requests up to kSlabMax bytes are carved
+// from slabs of kSlabBytes (one allocator call for many small tables); larger ones are
+// allocations of their own. bytes_total counts the bytes handed out.
 struct BufferSet {
-  std::vector<std::pair<void *, size_t>> bufs;
+  static constexpr size_t kSlabBytes = size_t(1) << 20, kSlabMax = size_t(1) << 16;
+  std::vector<std::pair<void *, size_t>> bufs;   // the device allocations owned
   size_t bytes_total = 0;
+  char *slab = nullptr;    // the current slab's unused tail
+  size_t slab_left = 0;
   BufferSet() = default;
   BufferSet(const BufferSet &) = delete;
   BufferSet &operator=(const BufferSet &) = delete;

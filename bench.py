@@ -15,6 +15,9 @@ runs), so the same line also carries, as sub-results measured in the same run:
            one-fit-at-a-time FP64 path against the batched launches (compensated FP32
            streaming, FP64 streaming, FP64 incremental waves), with the HBM roofline of the
            batched streaming kernel;
+  counting_process  the counting-process fit (1e6 subjects, ~2.9e6 (start, stop] rows, p = 5000,
+           K = 20, L2), timed per fit;
+  plain    the small dense fit (N = 1000, p = 10), whole fits per step, against the FP64 oracle's;
   serving  Poisson fit requests (rows logU[1e4, 1e7], p logU[100, 2e4], density logU[1e-4,
            1e-2], 1-200 strata, half counting-process, L1 / L2) into the continuous-batching
            server: its capacity under a burst, then a stream at a sustainable rate with
@@ -343,6 +346,39 @@ def run_moving(args, data, ddev, stream, flush, G, K, oracle_result):
         out["vs_oracle"] = {"sweeps": 2, "max_rel_beta_err": float(np.max(np.abs(b2 - ob)) / max(np.max(np.abs(ob)), 1e-300)),
                             "rel_loglik_err": abs(i2["loglik"] - oll) / scale, "tolerance": {"beta": 1e-9, "loglik": 1e-11},
                             "oracle": "FP64 CPU oracle, the same fit after 2 sweeps (element by element)"}
+    return out
+
+
+def run_plain(args, stream, oracle_result):
+    """The small dense workload (N = 1000, p = 10 dense N(0,1) covariates, one stratum, L2): whole
+    fits (cox_create from host arrays + cox_fit + cox_destroy) per step, and the fit against the
+    FP64 oracle's at the same sweep count."""
+    import torch
+    from paper_2310_16238_gb300 import cox
+    data, opts = synth.plain_dense()
+    times, info, beta = [], None, None
+    for k in range(13):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = cox.cox_create(data, opts, precision=cox.COX_FP64, stream=stream.cuda_stream)
+        beta, info = cox.cox_fit(h)
+        cox.cox_destroy(h)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    engine = ENGINE_NAMES.get(info["engine"], "unknown")
+    out = {"workload": "plain_dense N=1000 p=10 dense N(0,1), 1 stratum, L2 var=1, tol 1e-8", "engine": engine,
+           "dtype": dtype_of(engine, 8), "fits": len(times), "ms_per_fit": ms, "fits_per_s": 1e3 / ms,
+           "coord_updates_per_s": info["coord_updates"] / (ms * 1e-3), "sweeps": info["sweeps"]}
+    if oracle_result is not None:
+        ob, oll, osw = oracle_result
+        out["vs_oracle"] = {"sweeps_gpu": int(info["sweeps"]), "sweeps_oracle": osw,
+                            "max_rel_beta_err": float(np.max(np.abs(beta - ob)) / max(np.max(np.abs(ob)), 1e-300)),
+                            "rel_loglik_err": abs(info["loglik"] - oll) / max(abs(oll), float(np.sum(data.event))),
+                            "tolerance": {"beta": 1e-9, "loglik": 1e-11},
+                            "oracle": "FP64 CPU oracle, the same fit to convergence"}
     return out
 
 
@@ -921,14 +957,17 @@ def cpu_baseline(scale, seconds):
 
 
 def _oracle_moving(q, scale):
-    """Child process: the oracle's two-sweep iterate of the moving fit (run beside the GPU legs)."""
+    """Child process (run beside the GPU legs): the oracle's two-sweep iterate of the moving fit,
+    then its fit of the small dense workload to convergence."""
     try:
         import oracle
         oracle.build()
         data, _, _ = headline_workload(scale)
         o = moving_options(data.n)
         b, info = oracle.fit(data, synth.CoxOptions(penalty=o.penalty, lam=o.lam, tol=0.0, max_sweeps=2), max_sweeps=2)
-        q.put((b, info["loglik"]))
+        d1, o1 = synth.plain_dense()
+        b1, i1 = oracle.fit(d1, o1)
+        q.put({"moving": (b, info["loglik"]), "plain": (b1, i1["loglik"], int(i1["sweeps"]))})
     except Exception as e:   # reported in the bench line, not fatal
         q.put(("error", repr(e)))
 
@@ -1023,17 +1062,20 @@ def main():
             res["batch"] = run_batch(args, sub=True)
             if not args.no_serving:
                 res["serving"] = run_serving(args, sub=True)
+            res["counting_process"] = run_time_varying(argparse.Namespace(**{**vars(args), "steps": 2, "warmup": 1,
+                                                                              "precision": "fp64", "engine": "auto"}))
             orc = None
             try:
                 got = q.get(timeout=900)
-                orc = None if (isinstance(got[0], str) and got[0] == "error") else got
+                orc = got if isinstance(got, dict) else None
                 if orc is None:
                     res["oracle_error"] = got[1]
             except Exception as e:
                 res["oracle_error"] = repr(e)
             if proc is not None:
                 proc.join(timeout=10)
-            res["moving"] = run_moving(args, data, ddev, stream, flush, G, K, orc)
+            res["moving"] = run_moving(args, data, ddev, stream, flush, G, K, orc["moving"] if orc else None)
+            res["plain"] = run_plain(args, stream, orc["plain"] if orc else None)
         if not args.no_cpu:
             res["cpu_baseline"] = cpu_baseline(args.scale, args.cpu_seconds)
         print(json.dumps(res), flush=True)

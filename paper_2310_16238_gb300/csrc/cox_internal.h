@@ -92,7 +92,8 @@ struct DevFit {
   double *out_S0, *out_S1;// [G] optional per-group sums (diagnostics)
   double *gout;           // [2p] EVAL mode: g'(beta_j), g''(beta_j) per column
   float *hscr;            // [6G] FP32C chunked kernel: compensated local sums (S0, S1[, S2]) of tie
-                          // groups whose risk set reaches past their chunk, kept until its carry arrives
+                          // groups whose risk set reaches past their chunk, kept until its carry arrives;
+                          // after a fit's launch each group's S0 slot holds its final S0 (the cached-S0 path)
   const void *vmap;       // FP32C: device copy of the tensor map (CUtensorMap, 128 bytes) that views v
                           // as rows of 32 floats, for the chunked kernel's tile copies
   // copies of data pointers the chunked kernel reads first (one dependent load fewer than via d)

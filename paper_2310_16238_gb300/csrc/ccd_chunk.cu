@@ -838,10 +838,16 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       for (int q = 0; q < kCI / 4; ++q) {
         const int ch = tid * (kCI / 4) + q;
         const float4 f = *reinterpret_cast<const float4 *>(&S.v[b][(ch ^ ((ch >> 3) & 7)) * 4]);
-        x[4 * q] = act ? f.x : 0.f;
-        x[4 * q + 1] = act ? f.y : 0.f;
-        x[4 * q + 2] = act ? f.z : 0.f;
-        x[4 * q + 3] = act ? f.w : 0.f;
+        x[4 * q] = f.x;
+        x[4 * q + 1] = f.y;
+        x[4 * q + 2] = f.z;
+        x[4 * q + 3] = f.w;
+      }
+      if (__any_sync(0xffffffffu, !act)) {   // the warp holding the tile's end (the staged window runs on)
+        if (!act) {
+#pragma unroll
+          for (int i = 0; i < kCI; ++i) x[i] = 0.f;
+        }
       }
       Acc run = P::zero();
       int rf = 0;

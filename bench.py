@@ -128,7 +128,7 @@ TRAFFIC = {
     # --probe incr: 156.02 MB read + 33.95 MB written per 1-sweep launch of 2001 steps
     ("incremental", "stratified_sparse", "fp64"): (156.023e6 + 33.954e6) / 2001,
     # --probe stream_fp32c: an evaluation launch (a fit's launch adds the previous column's update, ~0.2 MB)
-    ("streaming", "time_varying", "fp32c"): 25.57e6,
+    ("streaming", "time_varying", "fp32c"): 25.52e6,
     # --probe stream_fp64: an evaluation launch
     ("streaming", "time_varying", "fp64"): 47.03e6,
 }

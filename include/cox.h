@@ -344,7 +344,8 @@ int cox_set_chunk_plan(int32_t chunks_per_cta);
  * since its previous step (that step's update was 0, as for every coefficient an L1 penalty keeps
  * at 0) needs no new risk-set sums S0 at its tie groups (eq. parallel_d: the sums of exp(eta) are
  * those of the previous step); the kernel keeps them from one step to the next and then computes
- * only column j's S1 (S2) from the column's entries. On by default; `enable` = 0 turns it off for
+ * only column j's S1 (S2) from the column's entries; cox_gradient's evaluation launches (every
+ * column at one eta) read them too. On by default; `enable` = 0 turns it off for
  * work lists built afterwards, process-wide (for tests that compare the two paths). Returns COX_OK. */
 int cox_debug_set_cached_s0(int32_t enable);
 

@@ -625,13 +625,16 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     const double pend_db = ctl->pend_db;
     const uint32_t epoch = ctl->epoch;
     const uint32_t etag = epoch % 15u + 1u;   // never 0: zeroed words are never current
-    const uint32_t s0tag = mode == kModeFit ? ctl->s0c_tag : 0u;
+    // fit launches and evaluation launches (cox_gradient: columns in order at one eta) keep and
+    // read the tie groups' S0
+    const bool keeps_s0 = mode == kModeFit || mode == kModeEval;
+    const uint32_t s0tag = keeps_s0 ? ctl->s0c_tag : 0u;
     const double shift = F.shift;
     vf = VAL && F.val != nullptr;
     cbj = j >= 0 ? F.col_ptr[j] : 0;
     // the next column's entries in this chunk: whether the next launch's cached-S0 path admits it
     int ent_next = 0;
-    if (mode == kModeFit && tid == 0 && j >= 0) {
+    if (keeps_s0 && tid == 0 && j >= 0) {
       const int32_t *ctn = F.col_tile + int64_t(j + 1 < F.p ? j + 1 : 0) * (T_ + 1);
       ent_next = ctn[tb] - ctn[ta];
     }
@@ -653,7 +656,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
 
     // eta unchanged since the fit's previous launch (no pending update), which admitted the cached-S0
     // path for this one: every chunk of the fit reads its tie groups' S0 from that launch
-    const bool fastfit = mode == kModeFit && pend_j < 0 && s0tag == epoch && it.fast_ok != 0;
+    const bool fastfit = keeps_s0 && pend_j < 0 && s0tag == epoch && it.fast_ok != 0;
     Acc g1q = P::zero(), g2q = P::zero();
     double llq = 0.0;
     if (fastfit) {
@@ -998,7 +1001,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
           for (int i = 0; i < NV; ++i) hs[i] = make_float2(sh[i].s, sh[i].c);
           myopen = min(myopen, gidx);
         } else {
-          add_group<NV>(sh, dgi, j, need_ll, g1q, g2q, llq, F, gidx, mode == kModeFit);
+          add_group<NV>(sh, dgi, j, need_ll, g1q, g2q, llq, F, gidx, keeps_s0);
         }
       }
       if (myopen != INT_MAX) atomicMin(&S.hopen, myopen);
@@ -1059,7 +1062,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
           sh[i] = P::comb(Acc{f2.x, f2.y}, CR[i]);
         }
         add_group<NV>(sh, on_chip ? dcnt[q] : F.head_d[q0 + q], j, need_ll, g1q, g2q, llq, F, q0 + q,
-                      mode == kModeFit);
+                      keeps_s0);
       }
       fence_proxy_async_smem();   // the tile buffers are rewritten by the next chunk's copies
     }
@@ -1076,7 +1079,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
       for (int i = 0; i < 3; ++i) S.red[i][warp] = r[i];
     __syncthreads();
     if (tid == 0) {
-      if (mode == kModeFit) {   // a chunk the next launch's cached-S0 path would not hold rules it out
+      if (keeps_s0) {   // a chunk the next launch's cached-S0 path would not hold rules it out
         const int span = S.tlo[nt] - S.tlo[0];
         if (!it.fast_ok || ent_next > kChunkFastE || (F.val == nullptr && ent_next >= span))
           atomicOr(&ctl->fast_no, 1u);
@@ -1094,7 +1097,7 @@ __global__ void __launch_bounds__(kCT, COXGB_CHUNK_MIN_CTAS) chunk_kernel(const 
     __syncthreads();
     CHUNK_STAMP(5);
     if (S.last) {
-      if (mode == kModeFit && tid == 0) {   // every tie group's S0 now holds for the fit's eta
+      if (keeps_s0 && tid == 0) {   // every tie group's S0 now holds for the fit's eta
         ctl->s0c_tag = ctl->fast_no == 0u ? epoch + 1u : 0u;
         ctl->fast_no = 0u;
       }

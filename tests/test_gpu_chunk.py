@@ -262,3 +262,28 @@ def test_chunk_plan_knob_rejects_bad_values():
     with pytest.raises(cox.CoxError):
         cox.cox_set_chunk_plan(-1)
     cox.cox_set_chunk_plan(0)
+
+
+@pytest.mark.parametrize("chunk_tiles", (1, 2), indirect=True)
+@pytest.mark.parametrize("case", ("many_strata_l1", "counting_l1", "dense_valued_l1"))
+def test_gradient_on_the_cached_s0_path(case, chunk_tiles):
+    """cox_gradient evaluates every column at one eta: its launches after the first read the tie
+    groups' S0 kept from the first. With and without that path the gradient and the Hessian
+    diagonal match the oracle at the FP32C tolerance; on binary X the two differ in their last bits
+    (the path's S1 sums run in another order), so the path ran."""
+    _, data, opts = _l1_case(case)
+    beta = random_beta(data.p, 0.3, seed=11)
+    out = []
+    try:
+        for enable in (True, False):
+            cox.cox_debug_set_cached_s0(enable)
+            with cox.Handle(data, opts, precision=cox.COX_FP32C, engine=cox.COX_ENGINE_STREAM) as h:
+                out.append(h.gradient(beta))
+    finally:
+        cox.cox_debug_set_cached_s0(True)
+    o1, o2 = oracle.grad_hess(data, beta)
+    for g1, g2 in out:
+        assert np.max(np.abs(g1 - o1)) <= 1e-5 * max(1.0, np.max(np.abs(o1))), case
+        assert np.max(np.abs(g2 - o2)) <= 1e-5 * max(1.0, np.max(np.abs(o2))), case
+    if data.val is None:
+        assert not np.array_equal(out[0][0], out[1][0]), case
